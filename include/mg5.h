@@ -1,0 +1,229 @@
+/*
+ * mg5.h -- C ABI of the GB300 (sm_103a) nonlinear multigrid library for the
+ * nDGP fifth force.
+ *
+ * Paper: Barreira, Bose & Li, "Speeding up N-body simulations of modified
+ * gravity: Vainshtein screening models", arXiv:1511.08200.
+ *
+ * The library solves Eq. (eomvarphi),
+ *     lap(phi) + alpha [ (lap phi)^2 - (d_i d_j phi)^2 ] = s delta,
+ * alpha = r_c^2 / (3 beta a^2), s = 8 pi G a^2 rho_bar / (3 beta), on a
+ * periodic, uniform, cell-centred grid (the domain level of Sec. 3.1), by
+ * FAS multigrid V-cycles whose smoother solves each cell's equation exactly
+ * (the fixed point of the Newton update, Eq. newton).  It also provides the
+ * speed-up of Sec. 3.2: fine-level phi interpolated from the coarse level
+ * (mg5_refine_interpolate) instead of relaxed (mg5_relax_patch), and the
+ * force by central differences of phi at cell centres (mg5_force).
+ *
+ * Conventions shared by every entry point
+ *   - Fields are C-order arrays, index (i*N1 + j)*N2 + k, k fastest, i <-> x.
+ *   - Pointers to fields are DEVICE pointers (cudaMalloc / torch CUDA
+ *     tensors) unless MG5_HOST_IO is set where documented.  The caller owns
+ *     every input and output buffer; the context owns its scratch memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it; entry points that need a scalar on the host (the
+ *     convergence test) synchronise that stream and say so.
+ *   - Every entry point returns an mg5 status code; nothing is thrown across
+ *     the ABI.  On MG5_E_CUDA the text of the CUDA error is available from
+ *     mg5_last_error().
+ *   - Discrete operator (the reading of the paper's unstated discretisation):
+ *     D_aa = (phi[+e_a] + phi[-e_a] - 2 phi) / h^2,
+ *     D_ab = (phi[+a+b] - phi[+a-b] - phi[-a+b] + phi[-a-b]) / (4 h^2),
+ *     L = sum D_aa, (d_i d_j phi)^2 = sum D_aa^2 + 2 sum_{a<b} D_ab^2.
+ *   - On a periodic grid the discrete nonlinear term has a non-zero mean, so
+ *     the library solves  op(phi) = s delta + c  with mean(phi) = 0 and a
+ *     scalar c (the compatibility constant, reported in mg5_info).
+ * One context per host thread, or external locking.
+ */
+#ifndef MG5_H
+#define MG5_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define MG5_OK               0
+#define MG5_W_DISC_CLAMP     1   /* converged, but some cell had no real root (clamped, counted) */
+#define MG5_E_ARG           -1   /* bad size, pointer or parameter */
+#define MG5_E_OOM           -2   /* scratch would exceed the context's HBM budget */
+#define MG5_E_CUDA          -3   /* a CUDA call failed; see mg5_last_error */
+#define MG5_E_NOT_CONVERGED -4   /* max_cycles reached; phi holds the last iterate */
+#define MG5_E_DIVERGED      -5   /* residual grew 10x above its best after >= 3 cycles */
+#define MG5_E_NONFINITE     -6   /* NaN or Inf in the residual */
+
+/* ------------------------------------------------------------ precision */
+#define MG5_FP64  0   /* every kernel in FP64 */
+#define MG5_MIXED 1   /* FP64 residual + defect-correction outer loop around FP32 V-cycles */
+
+/* ------------------------------------------------------------ flags */
+#define MG5_WARM     1u   /* phi holds the initial guess (Sec. 3.1: zero or the previous step) */
+#define MG5_HOST_IO  2u   /* delta, phi, grad are HOST pointers; the library copies them */
+
+typedef struct mg5_ctx mg5_ctx;  /* opaque; owns the device hierarchy, resident between calls */
+
+/* Solver parameters.  alpha, s: coefficients of Eq. (eomvarphi) (see
+ * mg5_ndgp_coefficients); h: cell size; tol: stop when
+ * ||r - mean r||_2 <= tol ||s delta||_2 on the finest grid.
+ * nu1, nu2: pre-/post-smoothing sweeps; nu_coarse: sweep cap on the
+ * coarsest grid (which sweeps until its residual falls 1e-3);
+ * max_cycles: V-cycle cap (MG5_MIXED: cap on FP64 defect-correction steps);
+ * precision: MG5_FP64 or MG5_MIXED. */
+typedef struct {
+    double alpha, s, h, tol;
+    int nu1, nu2, nu_coarse, max_cycles;
+    int precision;
+    int inner_cycles;   /* MG5_MIXED: FP32 V-cycles per FP64 step (0 = default 3) */
+} mg5_params;
+
+/* Per-solve report, written on return (after the stream has synchronised). */
+typedef struct {
+    int status;              /* same as the return code */
+    int cycles;              /* V-cycles with coarse correction (all inner cycles in MG5_MIXED) */
+    int outer_iters;         /* MG5_MIXED: FP64 defect-correction steps; 0 otherwise */
+    int levels;              /* grids in the hierarchy */
+    int coarsest_n;          /* side of the coarsest grid */
+    int n_history;           /* valid entries of history */
+    double rel_residual;     /* final ||r||_2 / ||s delta||_2 (FP64) */
+    double compat_c;         /* compatibility constant c of the finest grid */
+    double phi_mean_removed; /* mean subtracted from phi at the end */
+    long long disc_clamped;  /* cells whose discriminant was clamped */
+    long long cell_updates;  /* cells relaxed: one per cell per full sweep, every grid */
+    double ms_total;         /* wall time of the call on the stream, ms */
+    double history[64];      /* relative residual per finest-level check */
+} mg5_info;
+
+/* ------------------------------------------------------------ utilities */
+
+int mg5_version(void);
+const char *mg5_status_string(int status);
+/* Number of CUDA kernel launches the library has enqueued in this process. */
+long long mg5_kernel_launches(void);
+
+/* Fill p with the defaults: nu1 = nu2 = 2, nu_coarse = 500, max_cycles = 100,
+ * tol = 1e-10, precision MG5_FP64; alpha, s, h set to 0. */
+int mg5_default_params(mg5_params *p);
+
+/* Coefficients of Eq. (eomvarphi) for the normal-branch nDGP background
+ * tuned to LCDM (Eq. dgpH), with beta(a) from Eq. (beta):
+ *   beta = 1 + 2 H r_c (1 + Hdot / (3 H^2)),
+ *   alpha = r_c^2 / (3 beta a^2)       [(Mpc/h)^2],
+ *   s = Omega_m0 H0^2 / (beta a)       [(h/Mpc)^2],   c = 1, H0 = 1/2997.92458 h/Mpc.
+ * a in (0, 1], omega_m0 in (0, 1], h0rc > 0.  Any output pointer may be NULL. */
+int mg5_ndgp_coefficients(double a, double omega_m0, double h0rc, double *beta,
+                          double *alpha, double *s);
+
+/* Device bytes of scratch a solve of side N at `precision` allocates
+ * (the HBM footprint used for admission). */
+int mg5_workspace_bytes(int N, int precision, size_t *bytes);
+
+/* ------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * scratch the context may hold (0 = no cap).  Returns MG5_E_ARG for a bad
+ * device, MG5_E_CUDA if the device cannot be used. */
+int mg5_create(mg5_ctx **ctx, int device, size_t hbm_budget_bytes);
+int mg5_destroy(mg5_ctx *ctx);
+const char *mg5_last_error(mg5_ctx *ctx);
+/* Scratch bytes the context currently holds. */
+size_t mg5_bytes_held(mg5_ctx *ctx);
+/* Release every cached hierarchy (scratch) the context holds. */
+int mg5_release(mg5_ctx *ctx);
+
+/* ------------------------------------------------------------ the hot path */
+
+/*
+ * Solve Eq. (eomvarphi) on the periodic N^3 domain grid (Sec. 3.1) and,
+ * optionally, return the central-difference gradient (Sec. 3.2).
+ *   delta : N^3 FP64, density contrast, read only.  Its mean is ignored
+ *           (the mean of the source is absorbed by c).
+ *   N     : even, >= 4; the grids halve while the half is even and >= 4; the
+ *           coarsest grid must be at most 32 (else MG5_E_ARG).
+ *   p     : parameters (alpha >= 0, s, h > 0, tol >= 0).
+ *   flags : MG5_WARM (phi is the initial guess, else zero), MG5_HOST_IO.
+ *   phi   : N^3 FP64, out: the solution with mean zero.
+ *   grad  : 3 N^3 FP64 (gx, gy, gz blocks, SoA) or NULL; grad = d phi / dx_a.
+ *           The fifth force on a particle is -grad / 2 (Eq. modpoisson).
+ *   info  : may be NULL.
+ * Synchronises `stream` once per V-cycle (the convergence test).
+ * Returns MG5_OK, MG5_W_DISC_CLAMP, MG5_E_NOT_CONVERGED (phi = last
+ * iterate), MG5_E_DIVERGED, MG5_E_NONFINITE, MG5_E_ARG, MG5_E_OOM, MG5_E_CUDA.
+ */
+int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p,
+                          unsigned flags, double *phi, double *grad, mg5_info *info,
+                          void *stream);
+
+/*
+ * Central-difference gradient (Sec. 3.2: the force is obtained by finite
+ * differencing phi at cell centres):
+ *   grad[a][cell] = (phi[cell + e_a] - phi[cell - e_a]) / (2 h).
+ *   phi  : box of dims[0] x dims[1] x dims[2] FP64 (device).
+ *   ghost: width of the ghost shell; the gradient is computed on the
+ *          interior (dims - 2 ghost) and written SoA, 3 blocks of that size.
+ *   periodic != 0: the box is a periodic cube (ghost must be 0).
+ *   Non-periodic boxes need ghost >= 1.
+ */
+int mg5_force(mg5_ctx *ctx, const double *phi, const int dims[3], int ghost, double h,
+              int periodic, double *grad, void *stream);
+
+/*
+ * Coarse-to-fine interpolation (Sec. 3.1: boundary values and initial guess
+ * of a refinement; Sec. 3.2: the truncated fine-level phi).
+ *   phi_coarse: Nc^3 periodic FP64 (device).
+ *   o[3], pn[3]: the patch covers coarse cells [o, o + pn) on each axis
+ *               (wrapping periodically); 0 <= o < Nc, 1 <= pn <= Nc.
+ *   ghost:      fine ghost cells on every side (0..4).
+ *   phi_fine:   out, (2 pn + 2 ghost) per axis, FP64 (device).
+ * Fine local index I sits at coarse coordinate x = o + (I - ghost + 1/2)/2
+ * (coarse centre m at m + 1/2) and gets the trilinear blend of the eight
+ * nearest coarse centres (weights 3/4 and 1/4 per axis).
+ */
+int mg5_refine_interpolate(mg5_ctx *ctx, const double *phi_coarse, int Nc, const int o[3],
+                           const int pn[3], int ghost, double *phi_fine, void *stream);
+
+/*
+ * Relax the refinement (the untruncated, "full" fine level of Sec. 3.2):
+ * solve op(phi) = s delta_fine + compat_c on the interior pf[0] x pf[1] x
+ * pf[2] of a box with a one-cell ghost shell whose values stay fixed
+ * (Dirichlet boundary values from the coarse level, Sec. 3.1).
+ *   delta_fine: pf[0]*pf[1]*pf[2] FP64 (device), the fine density contrast.
+ *   p         : alpha, s, h (the FINE cell size), tol (relative to
+ *               ||s delta_fine||_2), max_cycles (sweep cap / 10).
+ *   compat_c  : the coarse solve's c (keeps the background consistent).
+ *   phi_fine  : (pf + 2)^3 box (device): in, the initial guess and the fixed
+ *               ghost shell (from mg5_refine_interpolate with ghost = 1);
+ *               out, the relaxed interior (ghosts untouched).
+ * Each pf must be even and >= 4.  Synchronises `stream` at each convergence test.
+ */
+int mg5_relax_patch(mg5_ctx *ctx, const double *delta_fine, const int pf[3],
+                    const mg5_params *p, double compat_c, double *phi_fine,
+                    mg5_info *info, void *stream);
+
+/* ------------------------------------------------------------ single steps
+ * Each runs one kernel of the hot path on device buffers, for testing the
+ * steps one by one.  N is the periodic side (even); c is the compatibility
+ * constant the step uses; f is the right-hand side (s delta on the domain grid). */
+
+/* One snapshot red-black sweep (red = (i+j+k) even first; within a
+ * half-sweep every value read is the value from before that half-sweep):
+ * phi_out = sweep(phi_in).  phi_in and phi_out must not alias. */
+int mg5_step_sweep(mg5_ctx *ctx, const double *phi_in, double *phi_out, const double *f,
+                   double c, int N, double h, double alpha, void *stream);
+/* out = op(phi) = L + alpha ((2/3) L^2 - Sigma) */
+int mg5_step_operator(mg5_ctx *ctx, const double *phi, int N, double h, double alpha,
+                      double *out, void *stream);
+/* r = f + c - op(phi) */
+int mg5_step_residual(mg5_ctx *ctx, const double *phi, const double *f, double c, int N,
+                      double h, double alpha, double *r, void *stream);
+/* coarse = mean of the 8 children of each coarse cell; N = fine side */
+int mg5_step_restrict(mg5_ctx *ctx, const double *fine, int N, double *coarse, void *stream);
+/* fine += cell-centred trilinear interpolation of coarse; Nc = coarse side */
+int mg5_step_prolong_add(mg5_ctx *ctx, const double *coarse, int Nc, double *fine,
+                         void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG5_H */

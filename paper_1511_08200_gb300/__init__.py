@@ -1,0 +1,324 @@
+"""GB300-native nonlinear multigrid for the nDGP fifth force (arXiv:1511.08200).
+
+Thin ctypes binding of ``libmg5.so`` (C ABI declared in ``include/mg5.h``).
+The functions keep the C names without the ``mg5_`` prefix and only marshal
+arguments: every step of the solve runs in the library's CUDA kernels.
+Device fields are torch CUDA tensors (float64, C-contiguous); PyTorch is used
+for device memory and streams only.  There is no CPU fallback: if the
+library has not been built, importing this package raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libmg5.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(
+        "libmg5.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+        "(nvcc, sm_103a) before importing paper_1511_08200_gb300")
+
+_lib = ctypes.CDLL(_LIB_PATH)
+
+OK, W_DISC_CLAMP = 0, 1
+E_ARG, E_OOM, E_CUDA, E_NOT_CONVERGED, E_DIVERGED, E_NONFINITE = -1, -2, -3, -4, -5, -6
+FP64, MIXED = 0, 1
+WARM, HOST_IO = 1, 2
+
+_c_int, _c_double, _c_void_p, _c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+_c_uint = ctypes.c_uint
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("alpha", _c_double), ("s", _c_double), ("h", _c_double), ("tol", _c_double),
+                ("nu1", _c_int), ("nu2", _c_int), ("nu_coarse", _c_int), ("max_cycles", _c_int),
+                ("precision", _c_int), ("inner_cycles", _c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("status", _c_int), ("cycles", _c_int), ("outer_iters", _c_int),
+                ("levels", _c_int), ("coarsest_n", _c_int), ("n_history", _c_int),
+                ("rel_residual", _c_double), ("compat_c", _c_double),
+                ("phi_mean_removed", _c_double), ("disc_clamped", ctypes.c_longlong),
+                ("cell_updates", ctypes.c_longlong), ("ms_total", _c_double),
+                ("history", _c_double * 64)]
+
+
+@dataclass
+class Info:
+    status: int
+    cycles: int
+    outer_iters: int
+    levels: int
+    coarsest_n: int
+    rel_residual: float
+    compat_c: float
+    phi_mean_removed: float
+    disc_clamped: int
+    cell_updates: int
+    ms_total: float
+    history: list = field(default_factory=list)
+
+    @classmethod
+    def _from(cls, i: _Info) -> "Info":
+        return cls(i.status, i.cycles, i.outer_iters, i.levels, i.coarsest_n, i.rel_residual,
+                   i.compat_c, i.phi_mean_removed, i.disc_clamped, i.cell_updates, i.ms_total,
+                   [i.history[q] for q in range(min(i.n_history, 64))])
+
+
+_P = _c_void_p
+_I3 = ctypes.c_int * 3
+_sigs = {
+    "mg5_version": ([], _c_int),
+    "mg5_kernel_launches": ([], ctypes.c_longlong),
+    "mg5_status_string": ([_c_int], ctypes.c_char_p),
+    "mg5_default_params": ([_P], _c_int),
+    "mg5_ndgp_coefficients": ([_c_double, _c_double, _c_double, _P, _P, _P], _c_int),
+    "mg5_workspace_bytes": ([_c_int, _c_int, _P], _c_int),
+    "mg5_create": ([_P, _c_int, _c_size_t], _c_int),
+    "mg5_destroy": ([_P], _c_int),
+    "mg5_last_error": ([_P], ctypes.c_char_p),
+    "mg5_bytes_held": ([_P], _c_size_t),
+    "mg5_release": ([_P], _c_int),
+    "mg5_solve_fifth_force": ([_P, _P, _c_int, _P, _c_uint, _P, _P, _P, _P], _c_int),
+    "mg5_force": ([_P, _P, _I3, _c_int, _c_double, _c_int, _P, _P], _c_int),
+    "mg5_refine_interpolate": ([_P, _P, _c_int, _I3, _I3, _c_int, _P, _P], _c_int),
+    "mg5_relax_patch": ([_P, _P, _I3, _P, _c_double, _P, _P, _P], _c_int),
+    "mg5_step_sweep": ([_P, _P, _P, _P, _c_double, _c_int, _c_double, _c_double, _P], _c_int),
+    "mg5_step_operator": ([_P, _P, _c_int, _c_double, _c_double, _P, _P], _c_int),
+    "mg5_step_residual": ([_P, _P, _P, _c_double, _c_int, _c_double, _c_double, _P, _P], _c_int),
+    "mg5_step_restrict": ([_P, _P, _c_int, _P, _P], _c_int),
+    "mg5_step_prolong_add": ([_P, _P, _c_int, _P, _P], _c_int),
+}
+for _name, (_args, _res) in _sigs.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+
+class MG5Error(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("mg5 status %d (%s): %s" % (code, status_string(code), msg))
+        self.code = code
+
+
+def version() -> int:
+    return _lib.mg5_version()
+
+
+def kernel_launches() -> int:
+    """Kernel launches the library has enqueued in this process."""
+    return _lib.mg5_kernel_launches()
+
+
+def status_string(code: int) -> str:
+    return _lib.mg5_status_string(code).decode()
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _lib.mg5_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": FP64, "mixed": MIXED}[v]
+        setattr(p, k, v)
+    return p
+
+
+def ndgp_coefficients(a: float, omega_m0: float, h0rc: float):
+    """(beta, alpha, s) of Eq. (beta) / Eq. (eomvarphi) for the LCDM-matched nDGP background."""
+    b, al, s = _c_double(), _c_double(), _c_double()
+    rc = _lib.mg5_ndgp_coefficients(a, omega_m0, h0rc, ctypes.byref(b), ctypes.byref(al),
+                                    ctypes.byref(s))
+    if rc != OK:
+        raise MG5Error(rc, "bad cosmology")
+    return b.value, al.value, s.value
+
+
+def workspace_bytes(n: int, precision=FP64) -> int:
+    if isinstance(precision, str):
+        precision = {"fp64": FP64, "mixed": MIXED}[precision]
+    out = _c_size_t()
+    rc = _lib.mg5_workspace_bytes(n, precision, ctypes.byref(out))
+    if rc != OK:
+        raise MG5Error(rc, "bad size")
+    return out.value
+
+
+def _ptr(t) -> int:
+    """Device pointer of a torch CUDA tensor (float64, contiguous) or None."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Context:
+    """Owns the device hierarchy (mg5_ctx); one per thread."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self._h = _c_void_p()
+        rc = _lib.mg5_create(ctypes.byref(self._h), device, hbm_budget_bytes)
+        if rc != OK:
+            raise MG5Error(rc, "mg5_create failed")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            _lib.mg5_destroy(self._h)
+            self._h = _c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return _lib.mg5_last_error(self._h).decode()
+
+    def bytes_held(self) -> int:
+        return _lib.mg5_bytes_held(self._h)
+
+    def release(self):
+        _lib.mg5_release(self._h)
+
+    def _check(self, rc: int, allow=(OK,)):
+        if rc not in allow:
+            raise MG5Error(rc, self.last_error())
+        return rc
+
+    # ------------------------------------------------------------ hot path
+    def solve_fifth_force(self, delta, params: Params, phi=None, grad=None, warm=False,
+                          stream=None, raise_on_status=True):
+        """mg5_solve_fifth_force on device tensors.  phi (out, N^3) and grad
+        (out, 3 x N^3, optional) are allocated if not given.  Returns (phi, grad, Info)."""
+        import torch
+        n = int(delta.shape[0])
+        if phi is None:
+            phi = torch.zeros_like(delta)
+        info = _Info()
+        rc = _lib.mg5_solve_fifth_force(self._h, _ptr(delta), n, ctypes.byref(params),
+                                        WARM if warm else 0, _ptr(phi), _ptr(grad),
+                                        ctypes.byref(info), _stream(stream))
+        if raise_on_status:
+            self._check(rc, (OK, W_DISC_CLAMP))
+        elif rc in (E_ARG, E_OOM, E_CUDA):
+            self._check(rc)
+        return phi, grad, Info._from(info)
+
+    def solve_fifth_force_host(self, delta, params: Params, phi=None, grad=None, warm=False,
+                               stream=None, raise_on_status=True):
+        """Same call with HOST buffers (numpy float64 or pinned CPU tensors): the
+        library copies delta in and phi / grad out (MG5_HOST_IO)."""
+        n = int(delta.shape[0])
+        info = _Info()
+        flags = HOST_IO | (WARM if warm else 0)
+        rc = _lib.mg5_solve_fifth_force(self._h, _host_ptr(delta), n, ctypes.byref(params), flags,
+                                        _host_ptr(phi), _host_ptr(grad), ctypes.byref(info),
+                                        _stream(stream))
+        if raise_on_status:
+            self._check(rc, (OK, W_DISC_CLAMP))
+        return phi, grad, Info._from(info)
+
+    def force(self, phi, h: float, ghost: int = 0, periodic: bool = True, grad=None, stream=None):
+        import torch
+        dims = [int(x) for x in phi.shape]
+        inner = [d - 2 * ghost for d in dims]
+        if grad is None:
+            grad = torch.empty([3] + inner, dtype=phi.dtype, device=phi.device)
+        self._check(_lib.mg5_force(self._h, _ptr(phi), _I3(*dims), ghost, h, 1 if periodic else 0,
+                                   _ptr(grad), _stream(stream)))
+        return grad
+
+    def refine_interpolate(self, phi_coarse, origin, pn, ghost: int, out=None, stream=None):
+        import torch
+        nc = int(phi_coarse.shape[0])
+        dims = [2 * int(p) + 2 * ghost for p in pn]
+        if out is None:
+            out = torch.empty(dims, dtype=phi_coarse.dtype, device=phi_coarse.device)
+        self._check(_lib.mg5_refine_interpolate(self._h, _ptr(phi_coarse), nc, _I3(*origin),
+                                                _I3(*pn), ghost, _ptr(out), _stream(stream)))
+        return out
+
+    def relax_patch(self, delta_fine, params: Params, compat_c: float, phi_box, stream=None,
+                    raise_on_status=True):
+        """mg5_relax_patch: phi_box ((pf + 2)^3, ghosts fixed) is relaxed in place."""
+        pf = [int(x) for x in delta_fine.shape]
+        info = _Info()
+        rc = _lib.mg5_relax_patch(self._h, _ptr(delta_fine), _I3(*pf), ctypes.byref(params),
+                                  compat_c, _ptr(phi_box), ctypes.byref(info), _stream(stream))
+        if raise_on_status:
+            self._check(rc, (OK, W_DISC_CLAMP))
+        return phi_box, Info._from(info)
+
+    # ------------------------------------------------------------ single steps
+    def step_sweep(self, phi_in, f, c: float, h: float, alpha: float, out=None, stream=None):
+        import torch
+        out = torch.empty_like(phi_in) if out is None else out
+        self._check(_lib.mg5_step_sweep(self._h, _ptr(phi_in), _ptr(out), _ptr(f), c,
+                                        int(phi_in.shape[0]), h, alpha, _stream(stream)))
+        return out
+
+    def step_operator(self, phi, h: float, alpha: float, out=None, stream=None):
+        import torch
+        out = torch.empty_like(phi) if out is None else out
+        self._check(_lib.mg5_step_operator(self._h, _ptr(phi), int(phi.shape[0]), h, alpha,
+                                           _ptr(out), _stream(stream)))
+        return out
+
+    def step_residual(self, phi, f, c: float, h: float, alpha: float, out=None, stream=None):
+        import torch
+        out = torch.empty_like(phi) if out is None else out
+        self._check(_lib.mg5_step_residual(self._h, _ptr(phi), _ptr(f), c, int(phi.shape[0]), h,
+                                           alpha, _ptr(out), _stream(stream)))
+        return out
+
+    def step_restrict(self, fine, out=None, stream=None):
+        import torch
+        n = int(fine.shape[0])
+        out = torch.empty((n // 2,) * 3, dtype=fine.dtype, device=fine.device) if out is None else out
+        self._check(_lib.mg5_step_restrict(self._h, _ptr(fine), n, _ptr(out), _stream(stream)))
+        return out
+
+    def step_prolong_add(self, coarse, fine, stream=None):
+        self._check(_lib.mg5_step_prolong_add(self._h, _ptr(coarse), int(coarse.shape[0]),
+                                              _ptr(fine), _stream(stream)))
+        return fine
+
+
+def _host_ptr(a):
+    """Host pointer of a C-contiguous float64 numpy array or CPU tensor (None -> NULL)."""
+    if a is None:
+        return None
+    try:
+        import numpy as np
+        if isinstance(a, np.ndarray):
+            if not (a.dtype == np.float64 and a.flags.c_contiguous):
+                raise TypeError("expected a C-contiguous float64 array")
+            return a.ctypes.data
+    except ImportError:
+        pass
+    import torch
+    if isinstance(a, torch.Tensor) and not a.is_cuda and a.dtype == torch.float64 and a.is_contiguous():
+        return a.data_ptr()
+    raise TypeError("expected a host float64 buffer")
+
+
+__all__ = ["Context", "Params", "Info", "MG5Error", "default_params", "ndgp_coefficients",
+           "workspace_bytes", "status_string", "version", "FP64", "MIXED"]

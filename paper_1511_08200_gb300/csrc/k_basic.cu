@@ -1,0 +1,754 @@
+// k_basic.cu -- the plain (one thread per cell) kernels of the mg5 hot path:
+// snapshot red-black sweep, operator, residual (+ fused 8-child restriction),
+// FAS coarse right-hand side, trilinear prolongation + correction, the
+// single-CTA coarsest-grid solve, reductions, force, coarse->fine
+// interpolation and the Dirichlet patch sweep.
+//
+// Paper: arXiv:1511.08200, Eq. (eomvarphi), Eq. (newton), Sec. 3.1 (level
+// solve, V-cycles, boundary values from the coarser level), Sec. 3.2
+// (interpolated fine phi, force by central differences).
+#include "mg5_kernels.cuh"
+
+namespace mg5 {
+
+constexpr int kReduceGrid = kMaxPartials;  // reduction kernels use at most this many blocks
+
+// --------------------------------------------------------------------------
+// snapshot red-black sweep: two passes.
+// Red pass: red cells ((i+j+k) even) from `in`; black cells copied.
+// Black pass: faces (red, new) from `out`, edges (black, old) from `in`.
+// Each thread owns the pair (2kk, 2kk+1) of one row, one cell of each colour.
+// --------------------------------------------------------------------------
+template <typename T, bool BASE>
+__global__ void k_sweep_red(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ f,
+                            const double *__restrict__ cptr, int n, CoefT<T> cf,
+                            unsigned long long *clamp, const T *__restrict__ B)
+{
+    const int half = n >> 1;
+    const long long total = (long long)n * n * half;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int kk = (int)(t % half);
+    const long long q = t / half;
+    const int j = (int)(q % n), i = (int)(q / n);
+    const int par = (i + j) & 1;
+    const int kr = 2 * kk + par, kb = 2 * kk + 1 - par;
+    const Rows r = periodic_rows(n, i, j);
+    out[r.r00 + kb] = in[r.r00 + kb];
+    const int kp = (kr == n - 1) ? 0 : kr + 1, km = (kr == 0) ? n - 1 : kr - 1;
+    St<T> s, sb;
+    gather(in, in, r, kr, kp, km, s);
+    if constexpr (BASE)
+        gather(B, B, r, kr, kp, km, sb);
+    bool cl = false;
+    const T v = upd<T, BASE>(s, sb, f[r.r00 + kr] + (T)(*cptr), cf, cl);
+    out[r.r00 + kr] = v;
+    if (cl)
+        atomicAdd(clamp, 1ull);
+}
+
+template <typename T, bool BASE>
+__global__ void k_sweep_black(const T *__restrict__ in, T *out, const T *__restrict__ f,
+                              const double *__restrict__ cptr, int n, CoefT<T> cf,
+                              unsigned long long *clamp, const T *__restrict__ B)
+{
+    const int half = n >> 1;
+    const long long total = (long long)n * n * half;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int kk = (int)(t % half);
+    const long long q = t / half;
+    const int j = (int)(q % n), i = (int)(q / n);
+    const int kb = 2 * kk + 1 - ((i + j) & 1);
+    const Rows r = periodic_rows(n, i, j);
+    const int kp = (kb == n - 1) ? 0 : kb + 1, km = (kb == 0) ? n - 1 : kb - 1;
+    St<T> s, sb;
+    gather((const T *)out, in, r, kb, kp, km, s);
+    if constexpr (BASE)
+        gather(B, B, r, kb, kp, km, sb);
+    bool cl = false;
+    const T v = upd<T, BASE>(s, sb, f[r.r00 + kb] + (T)(*cptr), cf, cl);
+    out[r.r00 + kb] = v;
+    if (cl)
+        atomicAdd(clamp, 1ull);
+}
+
+template <typename T>
+cudaError_t launch_sweep(const T *in, T *out, const T *f, const double *cptr, int n, CoefT<T> cf,
+                         unsigned long long *clamp, cudaStream_t st, const T *B)
+{
+    const long long work = (long long)n * n * (n / 2);
+    const int g = blocks_for(work);
+    if (B) {
+        k_sweep_red<T, true><<<g, kBlock, 0, st>>>(in, out, f, cptr, n, cf, clamp, B);
+        k_sweep_black<T, true><<<g, kBlock, 0, st>>>(in, out, f, cptr, n, cf, clamp, B);
+    } else {
+        k_sweep_red<T, false><<<g, kBlock, 0, st>>>(in, out, f, cptr, n, cf, clamp, B);
+        k_sweep_black<T, false><<<g, kBlock, 0, st>>>(in, out, f, cptr, n, cf, clamp, B);
+    }
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// operator and residual
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void k_operator(const T *__restrict__ phi, int n, CoefT<T> cf, T *__restrict__ out)
+{
+    const long long total = (long long)n * n * n;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int k = (int)(t % n);
+    const long long q = t / n;
+    const int j = (int)(q % n), i = (int)(q / n);
+    const Rows r = periodic_rows(n, i, j);
+    const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
+    St<T> s;
+    gather(phi, phi, r, k, kp, km, s);
+    out[t] = cell_op(s, cf);
+}
+
+template <typename T>
+cudaError_t launch_operator(const T *phi, int n, CoefT<T> cf, T *out, cudaStream_t st)
+{
+    const long long work = (long long)n * n * n;
+    k_operator<T><<<blocks_for(work), kBlock, 0, st>>>(phi, n, cf, out);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_residual(const T *__restrict__ phi, const T *__restrict__ f,
+                           const double *__restrict__ cptr, int n, CoefT<T> cf, T *__restrict__ r_out,
+                           double2 *__restrict__ partials)
+{
+    const long long total = (long long)n * n * n;
+    const double c = *cptr;
+    double2 acc = make_double2(0.0, 0.0);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t % n);
+        const long long q = t / n;
+        const int j = (int)(q % n), i = (int)(q / n);
+        const Rows r = periodic_rows(n, i, j);
+        const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
+        St<T> s;
+        gather(phi, phi, r, k, kp, km, s);
+        const T res = f[t] + (T)c - cell_op(s, cf);
+        if (r_out)
+            r_out[t] = res;
+        acc.x += (double)res;
+        acc.y += (double)res * (double)res;
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0)
+        partials[blockIdx.x] = acc;
+}
+
+template <typename T>
+cudaError_t launch_residual(const T *phi, const T *f, const double *cptr, int n, CoefT<T> cf, T *r,
+                            double2 *partials, int *nblocks, cudaStream_t st)
+{
+    const long long work = (long long)n * n * n;
+    int g = blocks_for(work);
+    if (g > kReduceGrid)
+        g = kReduceGrid;
+    k_residual<T><<<g, kBlock, 0, st>>>(phi, f, cptr, n, cf, r, partials);
+    *nblocks = g;
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// Residual of the 8 children of each coarse cell, restricted with v.
+template <typename T, bool BASE>
+__global__ void k_resid_restrict(const T *__restrict__ v, const T *__restrict__ f,
+                                 const double *__restrict__ cptr, int n, CoefT<T> cf,
+                                 T *__restrict__ vc, T *__restrict__ v0c, T *__restrict__ rc,
+                                 double2 *__restrict__ partials, const T *__restrict__ B)
+{
+    const int nc = n >> 1;
+    const long long total = (long long)nc * nc * nc;
+    const double c = *cptr;
+    double2 acc = make_double2(0.0, 0.0);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int K = (int)(t % nc);
+        const long long q = t / nc;
+        const int J = (int)(q % nc), I = (int)(q / nc);
+        T sv = 0, sr = 0;
+#pragma unroll 2
+        for (int ch = 0; ch < 8; ++ch) {
+            const int i = 2 * I + (ch >> 2), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch & 1);
+            const Rows r = periodic_rows(n, i, j);
+            const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
+            St<T> s, sb;
+            gather(v, v, r, k, kp, km, s);
+            if constexpr (BASE)
+                gather(B, B, r, k, kp, km, sb);
+            const T res = f[r.r00 + k] + (T)c - opr<T, BASE>(s, sb, cf);
+            sv += s.c;
+            sr += res;
+            acc.x += (double)res;
+            acc.y += (double)res * (double)res;
+        }
+        const T mv = sv * (T)0.125;
+        vc[t] = mv;
+        v0c[t] = mv;
+        rc[t] = sr * (T)0.125;
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0)
+        partials[blockIdx.x] = acc;
+}
+
+template <typename T>
+cudaError_t launch_resid_restrict(const T *v, const T *f, const double *cptr, int n, CoefT<T> cf,
+                                  T *vc, T *v0c, T *rc, double2 *partials, int *nblocks,
+                                  cudaStream_t st, const T *B)
+{
+    const long long work = (long long)(n / 2) * (n / 2) * (n / 2);
+    int g = blocks_for(work);
+    if (g > kReduceGrid)
+        g = kReduceGrid;
+    if (B)
+        k_resid_restrict<T, true><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, partials, B);
+    else
+        k_resid_restrict<T, false><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, partials, B);
+    *nblocks = g;
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_restrict(const T *__restrict__ fine, int n, T *__restrict__ coarse)
+{
+    const int nc = n >> 1;
+    const long long total = (long long)nc * nc * nc;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int K = (int)(t % nc);
+    const long long q = t / nc;
+    const int J = (int)(q % nc), I = (int)(q / nc);
+    T s = 0;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+        const long long i = 2 * I + (ch >> 2), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch & 1);
+        s += fine[(i * n + j) * n + k];
+    }
+    coarse[t] = s * (T)0.125;
+}
+
+template <typename T>
+cudaError_t launch_restrict(const T *fine, int n, T *coarse, cudaStream_t st)
+{
+    const long long work = (long long)(n / 2) * (n / 2) * (n / 2);
+    k_restrict<T><<<blocks_for(work), kBlock, 0, st>>>(fine, n, coarse);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// fc = op_c(vc) + fc - m ; the coarse c restarts at zero.
+template <typename T, bool BASE>
+__global__ void k_coarse_rhs(const T *__restrict__ vc, T *__restrict__ fc,
+                             const double *__restrict__ m_fine, double *__restrict__ c_coarse,
+                             int nc, CoefT<T> cf, const T *__restrict__ B)
+{
+    const long long total = (long long)nc * nc * nc;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0)
+        *c_coarse = 0.0;
+    if (t >= total)
+        return;
+    const int k = (int)(t % nc);
+    const long long q = t / nc;
+    const int j = (int)(q % nc), i = (int)(q / nc);
+    const Rows r = periodic_rows(nc, i, j);
+    const int kp = (k == nc - 1) ? 0 : k + 1, km = (k == 0) ? nc - 1 : k - 1;
+    St<T> s, sb;
+    gather(vc, vc, r, k, kp, km, s);
+    if constexpr (BASE)
+        gather(B, B, r, k, kp, km, sb);
+    fc[t] = opr<T, BASE>(s, sb, cf) + fc[t] - (T)(*m_fine);
+}
+
+template <typename T>
+cudaError_t launch_coarse_rhs(const T *vc, T *fc, const double *m_fine, double *c_coarse, int nc,
+                              CoefT<T> cfc, cudaStream_t st, const T *B)
+{
+    const long long work = (long long)nc * nc * nc;
+    if (B)
+        k_coarse_rhs<T, true><<<blocks_for(work), kBlock, 0, st>>>(vc, fc, m_fine, c_coarse, nc, cfc, B);
+    else
+        k_coarse_rhs<T, false><<<blocks_for(work), kBlock, 0, st>>>(vc, fc, m_fine, c_coarse, nc, cfc, B);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// Cell-centred trilinear prolongation: along each axis a fine centre is a
+// quarter coarse cell from its parent, so it takes 3/4 of the parent and 1/4
+// of the parent's neighbour on its own side.
+template <typename T>
+__global__ void k_prolong_add(const T *__restrict__ vc, const T *__restrict__ v0c, int nc,
+                              T *__restrict__ vf, double *c_fine, const double *c_coarse)
+{
+    const int n = 2 * nc;
+    const long long total = (long long)n * n * n;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0 && c_fine && c_coarse)
+        *c_fine += *c_coarse;
+    if (t >= total)
+        return;
+    const int k = (int)(t % n);
+    const long long q = t / n;
+    const int j = (int)(q % n), i = (int)(q / n);
+    const int pi = i >> 1, pj = j >> 1, pk = k >> 1;
+    const int qi = (i & 1) ? (pi == nc - 1 ? 0 : pi + 1) : (pi == 0 ? nc - 1 : pi - 1);
+    const int qj = (j & 1) ? (pj == nc - 1 ? 0 : pj + 1) : (pj == 0 ? nc - 1 : pj - 1);
+    const int qk = (k & 1) ? (pk == nc - 1 ? 0 : pk + 1) : (pk == 0 ? nc - 1 : pk - 1);
+    const long long NC = nc;
+    const long long ri[2] = {(long long)pi * NC, (long long)qi * NC};
+    const long long rj[2] = {pj, qj};
+    const int kk[2] = {pk, qk};
+    const T w[2] = {(T)0.75, (T)0.25};
+    T acc = 0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int d = 0; d < 2; ++d) {
+                const long long idx = (ri[a] + rj[b]) * NC + kk[d];
+                const T e = v0c ? (vc[idx] - v0c[idx]) : vc[idx];
+                acc += (w[a] * w[b] * w[d]) * e;
+            }
+    vf[t] += acc;
+}
+
+template <typename T>
+cudaError_t launch_prolong_add(const T *vc, const T *v0c, int nc, T *vf, double *c_fine,
+                               const double *c_coarse, cudaStream_t st)
+{
+    const long long work = 8ll * nc * nc * nc;
+    k_prolong_add<T><<<blocks_for(work), kBlock, 0, st>>>(vc, v0c, nc, vf, c_fine, c_coarse);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// coarsest grid: one CTA.  Before each sweep: c = mean(op(v) - f) and the
+// residual norm; stop when it is <= rtol times the first one or after
+// nu_max sweeps.  Sweeps ping-pong A -> B (red) -> A (black) with barriers.
+// --------------------------------------------------------------------------
+constexpr int kCoarsestThreads = 1024;
+
+template <typename T, bool BASE>
+__global__ void __launch_bounds__(kCoarsestThreads)
+    k_coarsest(T *A, T *B, const T *f, int n, CoefT<T> cf, double *cptr, int nu_max, double rtol,
+               unsigned long long *clamp, int *sweeps_out, const T *__restrict__ base)
+{
+    __shared__ double bc_s[2];
+    const int n3 = n * n * n;
+    const double inv_n3 = 1.0 / (double)n3;
+    double r0 = -1.0, c = 0.0;
+    int it = 0;
+    unsigned long long my_clamps = 0;
+    for (; it < nu_max; ++it) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int p = threadIdx.x; p < n3; p += blockDim.x) {
+            const int k = p % n, j = (p / n) % n, i = p / (n * n);
+            const Rows r = periodic_rows(n, i, j);
+            const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
+            St<T> s, sb;
+            gather((const T *)A, (const T *)A, r, k, kp, km, s);
+            if constexpr (BASE)
+                gather(base, base, r, k, kp, km, sb);
+            const double res = (double)(f[p] - opr<T, BASE>(s, sb, cf));
+            acc.x += res;
+            acc.y += res * res;
+        }
+        acc = block_sum2(acc);
+        if (threadIdx.x == 0) {
+            bc_s[0] = acc.x;
+            bc_s[1] = acc.y;
+        }
+        __syncthreads();
+        const double m = bc_s[0] * inv_n3;
+        const double q2 = bc_s[1] - (double)n3 * m * m;
+        const double rn = sqrt(q2 > 0.0 ? q2 : 0.0);
+        __syncthreads();
+        c = -m;
+        if (r0 < 0.0)
+            r0 = rn;
+        if (rn <= rtol * r0)
+            break;
+        for (int colour = 0; colour < 2; ++colour) {
+            const T *src = colour == 0 ? A : B;
+            T *dst = colour == 0 ? B : A;
+            for (int p = threadIdx.x; p < n3; p += blockDim.x) {
+                const int k = p % n, j = (p / n) % n, i = p / (n * n);
+                if (((i + j + k) & 1) != colour) {
+                    dst[p] = src[p];
+                    continue;
+                }
+                const Rows r = periodic_rows(n, i, j);
+                const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
+                St<T> s, sb;
+                gather(src, src, r, k, kp, km, s);
+                if constexpr (BASE)
+                    gather(base, base, r, k, kp, km, sb);
+                bool cl = false;
+                dst[p] = upd<T, BASE>(s, sb, f[p] + (T)c, cf, cl);
+                my_clamps += cl ? 1ull : 0ull;
+            }
+            __syncthreads();
+        }
+    }
+    if (my_clamps)
+        atomicAdd(clamp, my_clamps);
+    if (threadIdx.x == 0) {
+        *cptr = c;
+        if (sweeps_out)
+            atomicAdd(sweeps_out, it);
+    }
+}
+
+template <typename T>
+cudaError_t launch_coarsest(T *v, T *tmp, const T *f, int n, CoefT<T> cf, double *cptr, int nu_max,
+                            double rtol, unsigned long long *clamp, int *sweeps, cudaStream_t st,
+                            const T *B)
+{
+    if (B)
+        k_coarsest<T, true><<<1, kCoarsestThreads, 0, st>>>(v, tmp, f, n, cf, cptr, nu_max, rtol,
+                                                            clamp, sweeps, B);
+    else
+        k_coarsest<T, false><<<1, kCoarsestThreads, 0, st>>>(v, tmp, f, n, cf, cptr, nu_max, rtol,
+                                                             clamp, sweeps, B);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// reductions
+// --------------------------------------------------------------------------
+__global__ void k_finalize(const double2 *__restrict__ partials, int nb, double ncells,
+                           LevelScal *ls, int mode)
+{
+    double2 acc = make_double2(0.0, 0.0);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        acc.x += partials[b].x;
+        acc.y += partials[b].y;
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x != 0)
+        return;
+    if (mode == FIN_RESID) {
+        const double m = acc.x / ncells;
+        const double q2 = acc.y - ncells * m * m;
+        ls->m = m;
+        ls->c -= m;
+        ls->rnorm = sqrt(q2 > 0.0 ? q2 : 0.0);
+        ls->rel = ls->fnorm > 0.0 ? ls->rnorm / ls->fnorm : ls->rnorm;
+        if (!isfinite(acc.x) || !isfinite(acc.y))
+            ls->rel = acc.y + acc.x;  // propagates NaN / Inf to the host check
+    } else if (mode == FIN_STATS) {
+        const double m = acc.x / ncells;
+        const double q2 = acc.y - ncells * m * m;
+        ls->m = m;
+        ls->rnorm = sqrt(q2 > 0.0 ? q2 : 0.0);
+        ls->rel = ls->fnorm > 0.0 ? ls->rnorm / ls->fnorm : ls->rnorm;
+        if (!isfinite(acc.x) || !isfinite(acc.y))
+            ls->rel = acc.y + acc.x;
+    } else if (mode == FIN_NORM) {
+        ls->m = acc.x / ncells;
+        ls->rnorm = sqrt(acc.y);
+        ls->rel = ls->fnorm > 0.0 ? ls->rnorm / ls->fnorm : ls->rnorm;
+        if (!isfinite(acc.x) || !isfinite(acc.y))
+            ls->rel = acc.y + acc.x;
+    } else if (mode == FIN_FNORM) {
+        ls->fnorm = sqrt(acc.y);
+    } else {
+        ls->mean = acc.x / ncells;
+    }
+}
+
+cudaError_t launch_finalize(const double2 *partials, int nb, double ncells, LevelScal *ls, int mode,
+                            cudaStream_t st)
+{
+    k_finalize<<<1, 1024, 0, st>>>(partials, nb, ncells, ls, mode);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+__global__ void k_scale(const double *__restrict__ delta, double s, double *__restrict__ f,
+                        long long n3, double2 *__restrict__ partials)
+{
+    double2 acc = make_double2(0.0, 0.0);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n3;
+         t += (long long)gridDim.x * blockDim.x) {
+        const double v = s * delta[t];
+        f[t] = v;
+        acc.y += v * v;
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0)
+        partials[blockIdx.x] = acc;
+}
+
+cudaError_t launch_scale(const double *delta, double s, double *f, long long n3, double2 *partials,
+                         int *nblocks, cudaStream_t st)
+{
+    int g = blocks_for(n3);
+    if (g > kReduceGrid)
+        g = kReduceGrid;
+    k_scale<<<g, kBlock, 0, st>>>(delta, s, f, n3, partials);
+    *nblocks = g;
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+__global__ void k_sum(const double *__restrict__ a, long long n3, double2 *__restrict__ partials)
+{
+    double2 acc = make_double2(0.0, 0.0);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n3;
+         t += (long long)gridDim.x * blockDim.x)
+        acc.x += a[t];
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0)
+        partials[blockIdx.x] = acc;
+}
+
+cudaError_t launch_sum(const double *phi, long long n3, double2 *partials, int *nblocks,
+                       cudaStream_t st)
+{
+    int g = blocks_for(n3);
+    if (g > kReduceGrid)
+        g = kReduceGrid;
+    k_sum<<<g, kBlock, 0, st>>>(phi, n3, partials);
+    *nblocks = g;
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+__global__ void k_sub_mean(double *__restrict__ a, long long n3, const double *__restrict__ mean)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n3)
+        a[t] -= *mean;
+}
+
+cudaError_t launch_sub_mean(double *phi, long long n3, const double *mean, cudaStream_t st)
+{
+    k_sub_mean<<<blocks_for(n3), kBlock, 0, st>>>(phi, n3, mean);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// force: central differences at cell centres (Sec. 3.2), SoA output
+// --------------------------------------------------------------------------
+__global__ void k_force(const double *__restrict__ phi, int d0, int d1, int d2, int g, double inv2h,
+                        int periodic, double *__restrict__ grad)
+{
+    const int n0 = d0 - 2 * g, n1 = d1 - 2 * g, n2 = d2 - 2 * g;
+    const long long total = (long long)n0 * n1 * n2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int k = (int)(t % n2);
+    const long long q = t / n2;
+    const int j = (int)(q % n1), i = (int)(q / n1);
+    const int I = i + g, J = j + g, K = k + g;
+    int ip = I + 1, im = I - 1, jp = J + 1, jm = J - 1, kp = K + 1, km = K - 1;
+    if (periodic) {
+        ip = ip == d0 ? 0 : ip;
+        im = im < 0 ? d0 - 1 : im;
+        jp = jp == d1 ? 0 : jp;
+        jm = jm < 0 ? d1 - 1 : jm;
+        kp = kp == d2 ? 0 : kp;
+        km = km < 0 ? d2 - 1 : km;
+    }
+    const long long D1 = d1, D2 = d2;
+    auto at = [&](int a, int b, int c) { return phi[((long long)a * D1 + b) * D2 + c]; };
+    grad[t] = (at(ip, J, K) - at(im, J, K)) * inv2h;
+    grad[total + t] = (at(I, jp, K) - at(I, jm, K)) * inv2h;
+    grad[2 * total + t] = (at(I, J, kp) - at(I, J, km)) * inv2h;
+}
+
+cudaError_t launch_force(const double *phi, int d0, int d1, int d2, int ghost, double h, int periodic,
+                         double *grad, cudaStream_t st)
+{
+    const long long work = (long long)(d0 - 2 * ghost) * (d1 - 2 * ghost) * (d2 - 2 * ghost);
+    k_force<<<blocks_for(work), kBlock, 0, st>>>(phi, d0, d1, d2, ghost, 0.5 / h, periodic, grad);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// coarse -> fine interpolation of phi (Sec. 3.1 / 3.2)
+// fine local index I (ghosts included) -> coarse coordinate x = o + (I - g + 1/2)/2;
+// t = x - 1/2 = o + (I - g)/2 - 1/4; i0 = floor(t), w = t - i0 in {1/4, 3/4}.
+// --------------------------------------------------------------------------
+__global__ void k_refine(const double *__restrict__ phic, int nc, int o0, int o1, int o2, int d0,
+                         int d1, int d2, int g, double *__restrict__ fine)
+{
+    const long long total = (long long)d0 * d1 * d2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int K = (int)(t % d2);
+    const long long q = t / d2;
+    const int J = (int)(q % d1), I = (int)(q / d1);
+    const int loc[3] = {I, J, K};
+    const int org[3] = {o0, o1, o2};
+    int lo[3], hi[3];
+    double w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        // 4 t = 4 o + 2 (I - g) - 1 is an exact integer
+        const int t4 = 4 * org[a] + 2 * (loc[a] - g) - 1;
+        const int i0 = (t4 >= 0) ? (t4 >> 2) : -((-t4 + 3) >> 2);
+        w[a] = (double)(t4 - 4 * i0) * 0.25;
+        int l = i0 % nc;
+        l = l < 0 ? l + nc : l;
+        lo[a] = l;
+        hi[a] = (l + 1 == nc) ? 0 : l + 1;
+    }
+    const long long NC = nc;
+    double v = 0.0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const double wt = (a ? w[0] : 1.0 - w[0]) * (b ? w[1] : 1.0 - w[1]) *
+                                  (c ? w[2] : 1.0 - w[2]);
+                const long long idx =
+                    ((long long)(a ? hi[0] : lo[0]) * NC + (b ? hi[1] : lo[1])) * NC +
+                    (c ? hi[2] : lo[2]);
+                v += wt * phic[idx];
+            }
+    fine[t] = v;
+}
+
+cudaError_t launch_refine(const double *phic, int nc, const int o[3], const int pn[3], int ghost,
+                          double *fine, cudaStream_t st)
+{
+    const int d0 = 2 * pn[0] + 2 * ghost, d1 = 2 * pn[1] + 2 * ghost, d2 = 2 * pn[2] + 2 * ghost;
+    const long long work = (long long)d0 * d1 * d2;
+    k_refine<<<blocks_for(work), kBlock, 0, st>>>(phic, nc, o[0], o[1], o[2], d0, d1, d2, ghost,
+                                                  fine);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Dirichlet patch: interior pf, box pf + 2, colour = parity of the interior index.
+// --------------------------------------------------------------------------
+__global__ void k_patch_half(const double *__restrict__ src_faces, const double *__restrict__ src_edges,
+                             double *dst, const double *__restrict__ fint, double rhs_add, int p0,
+                             int p1, int p2, CoefT<double> cf, int colour, int copy_other,
+                             unsigned long long *clamp)
+{
+    const long long total = (long long)p0 * p1 * p2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int k = (int)(t % p2);
+    const long long q = t / p2;
+    const int j = (int)(q % p1), i = (int)(q / p1);
+    const int d1 = p1 + 2, d2 = p2 + 2;
+    const Rows r = box_rows(d1, d2, i + 1, j + 1);
+    const int K = k + 1;
+    if (((i + j + k) & 1) != colour) {
+        if (copy_other)
+            dst[r.r00 + K] = src_faces[r.r00 + K];
+        return;
+    }
+    St<double> s;
+    gather(src_faces, src_edges, r, K, K + 1, K - 1, s);
+    bool cl = false;
+    dst[r.r00 + K] = cell_update(s, fint[t] + rhs_add, cf, cl);
+    if (cl)
+        atomicAdd(clamp, 1ull);
+}
+
+cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint, double rhs_add,
+                               const int pf[3], CoefT<double> cf, unsigned long long *clamp,
+                               cudaStream_t st)
+{
+    const long long work = (long long)pf[0] * pf[1] * pf[2];
+    const int g = blocks_for(work);
+    // red: from in (all), black copied; black: faces from out (new red), edges from in (old black)
+    k_patch_half<<<g, kBlock, 0, st>>>(in, in, out, fint, rhs_add, pf[0], pf[1], pf[2], cf, 0, 1,
+                                       clamp);
+    k_patch_half<<<g, kBlock, 0, st>>>(out, in, out, fint, rhs_add, pf[0], pf[1], pf[2], cf, 1, 0,
+                                       clamp);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+__global__ void k_patch_residual(const double *__restrict__ phi, const double *__restrict__ fint,
+                                 double rhs_add, int p0, int p1, int p2, CoefT<double> cf,
+                                 double2 *__restrict__ partials)
+{
+    const long long total = (long long)p0 * p1 * p2;
+    double2 acc = make_double2(0.0, 0.0);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t % p2);
+        const long long q = t / p2;
+        const int j = (int)(q % p1), i = (int)(q / p1);
+        const Rows r = box_rows(p1 + 2, p2 + 2, i + 1, j + 1);
+        St<double> s;
+        gather(phi, phi, r, k + 1, k + 2, k, s);
+        const double res = fint[t] + rhs_add - cell_op(s, cf);
+        acc.x += res;
+        acc.y += res * res;
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0)
+        partials[blockIdx.x] = acc;
+}
+
+cudaError_t launch_patch_residual(const double *phi, const double *fint, double rhs_add,
+                                  const int pf[3], CoefT<double> cf, double2 *partials, int *nblocks,
+                                  cudaStream_t st)
+{
+    const long long work = (long long)pf[0] * pf[1] * pf[2];
+    int g = blocks_for(work);
+    if (g > kReduceGrid)
+        g = kReduceGrid;
+    k_patch_residual<<<g, kBlock, 0, st>>>(phi, fint, rhs_add, pf[0], pf[1], pf[2], cf, partials);
+    *nblocks = g;
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// explicit instantiations
+#define MG5_INST(T)                                                                                \
+    template cudaError_t launch_sweep<T>(const T *, T *, const T *, const double *, int, CoefT<T>, \
+                                         unsigned long long *, cudaStream_t, const T *);           \
+    template cudaError_t launch_operator<T>(const T *, int, CoefT<T>, T *, cudaStream_t);          \
+    template cudaError_t launch_residual<T>(const T *, const T *, const double *, int, CoefT<T>,   \
+                                            T *, double2 *, int *, cudaStream_t);                  \
+    template cudaError_t launch_resid_restrict<T>(const T *, const T *, const double *, int,       \
+                                                  CoefT<T>, T *, T *, T *, double2 *, int *,       \
+                                                  cudaStream_t, const T *);                        \
+    template cudaError_t launch_restrict<T>(const T *, int, T *, cudaStream_t);                    \
+    template cudaError_t launch_coarse_rhs<T>(const T *, T *, const double *, double *, int,       \
+                                              CoefT<T>, cudaStream_t, const T *);                  \
+    template cudaError_t launch_prolong_add<T>(const T *, const T *, int, T *, double *,           \
+                                               const double *, cudaStream_t);                      \
+    template cudaError_t launch_coarsest<T>(T *, T *, const T *, int, CoefT<T>, double *, int,     \
+                                            double, unsigned long long *, int *, cudaStream_t,     \
+                                            const T *);
+MG5_INST(double)
+MG5_INST(float)
+
+}  // namespace mg5

@@ -1,0 +1,791 @@
+// mg5_capi.cu -- host engine and C ABI of the mg5 library (see include/mg5.h).
+//
+// The context owns, per grid size, a resident multigrid hierarchy (device
+// buffers), a partial-sum buffer for deterministic reductions and a block of
+// per-grid device scalars (c, residual mean and norm).  The V-cycle schedule
+// runs on the host and launches one kernel per step on the caller's stream;
+// the only device->host traffic inside a solve is one 8-byte residual read
+// per cycle (the convergence test of Sec. 3.1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mg5.h"
+#include "mg5_kernels.cuh"
+#include "mg5_mixed.cuh"
+
+using namespace mg5;
+
+namespace mg5 {
+static std::atomic<long long> g_launches{0};
+void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace mg5
+
+namespace {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxCoarsest = 32;
+constexpr double kCoarseRtol = 1e-3;
+
+struct Hier {
+    int N = 0;
+    int nlev = 0;
+    int n[kMaxLevels] = {};
+    double *v[kMaxLevels] = {};    // level iterate (level 0: caller's phi at run time)
+    double *tmp[kMaxLevels] = {};  // ping-pong partner
+    double *f[kMaxLevels] = {};    // right-hand side
+    double *v0[kMaxLevels] = {};   // restricted iterate before the coarse solve
+    size_t bytes = 0;
+};
+
+int num_levels(int N, int *sizes)
+{
+    int L = 0, n = N;
+    sizes[L++] = n;
+    while ((n / 2) % 2 == 0 && n / 2 >= 4 && L < kMaxLevels) {
+        n /= 2;
+        sizes[L++] = n;
+    }
+    return L;
+}
+
+size_t fp64_bytes(int N)
+{
+    int sz[kMaxLevels];
+    const int L = num_levels(N, sz);
+    size_t b = 2 * (size_t)N * N * N * sizeof(double);  // tmp + f on the finest grid
+    for (int l = 1; l < L; ++l)
+        b += 4 * (size_t)sz[l] * sz[l] * sz[l] * sizeof(double);
+    return b;
+}
+
+}  // namespace
+
+struct mg5_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t held = 0;
+    std::string err;
+    std::vector<Hier *> hiers;
+    std::vector<MixedHier *> mixed;
+    double2 *partials = nullptr;
+    LevelScal *ls = nullptr;        // kScalSlots slots
+    SolveCounters *cnt = nullptr;
+    double *h_rel = nullptr;        // pinned host scalars
+    // staging for MG5_HOST_IO and patch scratch
+    double *stage = nullptr;
+    size_t stage_bytes = 0;
+    double *patch = nullptr;
+    size_t patch_bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// ------------------------------------------------------------ helpers
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+            return MG5_E_CUDA;                                                             \
+        }                                                                                  \
+    } while (0)
+
+#define RET(x)                      \
+    do {                            \
+        int r_ = (x);               \
+        if (r_ != MG5_OK)           \
+            return r_;              \
+    } while (0)
+
+static int ctx_alloc(mg5_ctx *ctx, void **p, size_t bytes)
+{
+    if (ctx->budget && ctx->held + bytes > ctx->budget) {
+        ctx->err = "scratch would exceed the context's HBM budget";
+        return MG5_E_OOM;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? MG5_E_OOM : MG5_E_CUDA;
+    }
+    ctx->held += bytes;
+    return MG5_OK;
+}
+
+static void ctx_free(mg5_ctx *ctx, void *p, size_t bytes)
+{
+    if (p) {
+        cudaFree(p);
+        ctx->held -= bytes;
+    }
+}
+
+static void free_hier(mg5_ctx *ctx, Hier *h)
+{
+    const size_t n3 = (size_t)h->N * h->N * h->N * sizeof(double);
+    ctx_free(ctx, h->tmp[0], n3);
+    ctx_free(ctx, h->f[0], n3);
+    for (int l = 1; l < h->nlev; ++l) {
+        const size_t b = (size_t)h->n[l] * h->n[l] * h->n[l] * sizeof(double);
+        ctx_free(ctx, h->v[l], b);
+        ctx_free(ctx, h->tmp[l], b);
+        ctx_free(ctx, h->f[l], b);
+        ctx_free(ctx, h->v0[l], b);
+    }
+    delete h;
+}
+
+static int get_hier(mg5_ctx *ctx, int N, Hier **out)
+{
+    for (Hier *h : ctx->hiers)
+        if (h->N == N) {
+            *out = h;
+            return MG5_OK;
+        }
+    Hier *h = new Hier();
+    h->N = N;
+    h->nlev = num_levels(N, h->n);
+    int rc = MG5_OK;
+    const size_t n3 = (size_t)N * N * N * sizeof(double);
+    rc = ctx_alloc(ctx, (void **)&h->tmp[0], n3);
+    if (rc == MG5_OK)
+        rc = ctx_alloc(ctx, (void **)&h->f[0], n3);
+    for (int l = 1; l < h->nlev && rc == MG5_OK; ++l) {
+        const size_t b = (size_t)h->n[l] * h->n[l] * h->n[l] * sizeof(double);
+        rc = ctx_alloc(ctx, (void **)&h->v[l], b);
+        if (rc == MG5_OK)
+            rc = ctx_alloc(ctx, (void **)&h->tmp[l], b);
+        if (rc == MG5_OK)
+            rc = ctx_alloc(ctx, (void **)&h->f[l], b);
+        if (rc == MG5_OK)
+            rc = ctx_alloc(ctx, (void **)&h->v0[l], b);
+    }
+    if (rc != MG5_OK) {
+        free_hier(ctx, h);
+        return rc;
+    }
+    h->bytes = fp64_bytes(N);
+    ctx->hiers.push_back(h);
+    *out = h;
+    return MG5_OK;
+}
+
+static int ensure_buffer(mg5_ctx *ctx, double **buf, size_t *have, size_t need)
+{
+    if (*have >= need)
+        return MG5_OK;
+    ctx_free(ctx, *buf, *have);
+    *buf = nullptr;
+    *have = 0;
+    RET(ctx_alloc(ctx, (void **)buf, need));
+    *have = need;
+    return MG5_OK;
+}
+
+static int check_size(int N)
+{
+    if (N < 4 || (N & 1))
+        return MG5_E_ARG;
+    int sz[kMaxLevels];
+    const int L = num_levels(N, sz);
+    if (sz[L - 1] > kMaxCoarsest)
+        return MG5_E_ARG;
+    return MG5_OK;
+}
+
+static int check_params(const mg5_params *p)
+{
+    if (!p || !(p->h > 0.0) || !(p->alpha >= 0.0) || !std::isfinite(p->s) || !(p->tol >= 0.0) ||
+        p->nu1 < 0 || p->nu2 < 0 || p->nu_coarse < 0 || p->max_cycles < 0 ||
+        (p->precision != MG5_FP64 && p->precision != MG5_MIXED))
+        return MG5_E_ARG;
+    return MG5_OK;
+}
+
+// ------------------------------------------------------------ FP64 V-cycle engine
+
+namespace {
+
+struct Run64 {
+    mg5_ctx *ctx;
+    Hier *h;
+    const mg5_params *p;
+    cudaStream_t st;
+    double hl[kMaxLevels];  // cell size per level
+    long long cu = 0;       // cell updates of the non-coarsest sweeps
+
+    LevelScal *ls(int l) { return ctx->ls + l; }
+    double *c(int l) { return &ctx->ls[l].c; }
+    double *m(int l) { return &ctx->ls[l].m; }
+
+    int sweep(int l)
+    {
+        const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
+        cudaError_t e = launch_sweep<double>(h->v[l], h->tmp[l], h->f[l], c(l), h->n[l], cf,
+                                             &ctx->cnt->clamped, st);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("sweep: ") + cudaGetErrorString(e);
+            return MG5_E_CUDA;
+        }
+        std::swap(h->v[l], h->tmp[l]);
+        cu += (long long)h->n[l] * h->n[l] * h->n[l];
+        return MG5_OK;
+    }
+
+    // residual of level l, restricted onto l+1; finalize updates c_l and the norm
+    int resid_restrict(int l)
+    {
+        const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
+        int nb = 0;
+        mg5_ctx *ctx = this->ctx;
+        CK(launch_resid_restrict<double>(h->v[l], h->f[l], c(l), h->n[l], cf, h->v[l + 1],
+                                         h->v0[l + 1], h->f[l + 1], ctx->partials, &nb, st));
+        const double n3 = (double)h->n[l] * h->n[l] * h->n[l];
+        CK(launch_finalize(ctx->partials, nb, n3, ls(l), FIN_RESID, st));
+        return MG5_OK;
+    }
+
+    int residual_only(int l)
+    {
+        const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
+        int nb = 0;
+        mg5_ctx *ctx = this->ctx;
+        CK(launch_residual<double>(h->v[l], h->f[l], c(l), h->n[l], cf, nullptr, ctx->partials,
+                                   &nb, st));
+        const double n3 = (double)h->n[l] * h->n[l] * h->n[l];
+        CK(launch_finalize(ctx->partials, nb, n3, ls(l), FIN_RESID, st));
+        return MG5_OK;
+    }
+
+    int coarsest(int l)
+    {
+        const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
+        mg5_ctx *ctx = this->ctx;
+        CK(launch_coarsest<double>(h->v[l], h->tmp[l], h->f[l], h->n[l], cf, c(l), p->nu_coarse,
+                                   kCoarseRtol, &ctx->cnt->clamped, &ctx->cnt->coarse_sweeps, st));
+        return MG5_OK;
+    }
+
+    // coarse-grid correction for level l-1, entered with v[l] = v0[l] = R v[l-1]
+    // and f[l] = R r[l-1]
+    int coarse_visit(int l)
+    {
+        mg5_ctx *ctx = this->ctx;
+        const CoefT<double> cfc = make_coef<double>(hl[l], p->alpha);
+        CK(launch_coarse_rhs<double>(h->v[l], h->f[l], m(l - 1), c(l), h->n[l], cfc, st));
+        if (l == h->nlev - 1)
+            return coarsest(l);
+        for (int s = 0; s < p->nu1; ++s)
+            RET(sweep(l));
+        RET(resid_restrict(l));
+        RET(coarse_visit(l + 1));
+        CK(launch_prolong_add<double>(h->v[l + 1], h->v0[l + 1], h->n[l + 1], h->v[l], c(l),
+                                      c(l + 1), st));
+        for (int s = 0; s < p->nu2; ++s)
+            RET(sweep(l));
+        return MG5_OK;
+    }
+};
+
+}  // namespace
+
+// Plain FP64 solve on device buffers.  phi holds the initial guess.
+static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p, double *phi,
+                   mg5_info *info, cudaStream_t st)
+{
+    Hier *h = nullptr;
+    RET(get_hier(ctx, N, &h));
+    Run64 R{ctx, h, p, st, {}, 0};
+    for (int l = 0; l < h->nlev; ++l)
+        R.hl[l] = p->h * (double)(1 << l);
+    const long long n3 = (long long)N * N * N;
+    CK(cudaMemsetAsync(ctx->ls, 0, sizeof(LevelScal) * kScalSlots, st));
+    CK(cudaMemsetAsync(ctx->cnt, 0, sizeof(SolveCounters), st));
+    int nb = 0;
+    CK(launch_scale(delta, p->s, h->f[0], n3, ctx->partials, &nb, st));
+    CK(launch_finalize(ctx->partials, nb, (double)n3, ctx->ls, FIN_FNORM, st));
+    double *caller_phi = phi;
+    h->v[0] = phi;
+    // tmp[0] is the context's; v/tmp swap on every sweep
+    double *own_tmp = h->tmp[0];
+    int status = MG5_E_NOT_CONVERGED;
+    double best = INFINITY;
+    int cyc = 0;
+    for (;; ++cyc) {
+        if (h->nlev == 1) {
+            RET(R.coarsest(0));
+            RET(R.residual_only(0));
+        } else {
+            for (int s = 0; s < p->nu1; ++s)
+                RET(R.sweep(0));
+            RET(R.resid_restrict(0));
+        }
+        CK(cudaMemcpyAsync(ctx->h_rel, &ctx->ls[0].rel, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const double rel = *ctx->h_rel;
+        if (info && cyc < 64) {
+            info->history[cyc] = rel;
+            info->n_history = cyc + 1;
+        }
+        if (info)
+            info->rel_residual = rel;
+        if (!std::isfinite(rel)) {
+            status = MG5_E_NONFINITE;
+            break;
+        }
+        if (rel <= p->tol) {
+            status = MG5_OK;
+            break;
+        }
+        best = std::min(best, rel);
+        if (cyc >= 3 && rel > 10.0 * best) {
+            status = MG5_E_DIVERGED;
+            break;
+        }
+        if (cyc >= p->max_cycles) {
+            status = MG5_E_NOT_CONVERGED;
+            break;
+        }
+        if (h->nlev == 1)
+            continue;
+        RET(R.coarse_visit(1));
+        CK(launch_prolong_add<double>(h->v[1], h->v0[1], h->n[1], h->v[0], R.c(0), R.c(1), st));
+        for (int s = 0; s < p->nu2; ++s)
+            RET(R.sweep(0));
+    }
+    if (h->v[0] != caller_phi)
+        CK(cudaMemcpyAsync(caller_phi, h->v[0], n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // restore the hierarchy's own buffer in tmp[0]
+    h->v[0] = nullptr;
+    h->tmp[0] = own_tmp;
+    // gauge: subtract mean(phi)
+    CK(launch_sum(caller_phi, n3, ctx->partials, &nb, st));
+    CK(launch_finalize(ctx->partials, nb, (double)n3, ctx->ls, FIN_MEAN, st));
+    CK(launch_sub_mean(caller_phi, n3, &ctx->ls[0].mean, st));
+    if (info) {
+        info->cycles = cyc;
+        info->levels = h->nlev;
+        info->coarsest_n = h->n[h->nlev - 1];
+        info->cell_updates = R.cu;   // coarsest sweeps are added by the caller
+    }
+    return status;
+}
+
+// ------------------------------------------------------------ C ABI
+
+extern "C" {
+
+int mg5_version(void) { return 100; }
+
+long long mg5_kernel_launches(void) { return launches_total(); }
+
+const char *mg5_status_string(int s)
+{
+    switch (s) {
+    case MG5_OK: return "ok";
+    case MG5_W_DISC_CLAMP: return "converged with clamped discriminants";
+    case MG5_E_ARG: return "invalid argument";
+    case MG5_E_OOM: return "out of memory (HBM budget)";
+    case MG5_E_CUDA: return "CUDA error";
+    case MG5_E_NOT_CONVERGED: return "not converged within max_cycles";
+    case MG5_E_DIVERGED: return "diverged";
+    case MG5_E_NONFINITE: return "non-finite residual";
+    default: return "unknown status";
+    }
+}
+
+int mg5_default_params(mg5_params *p)
+{
+    if (!p)
+        return MG5_E_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->tol = 1e-10;
+    p->nu1 = 2;
+    p->nu2 = 2;
+    p->nu_coarse = 500;
+    p->max_cycles = 100;
+    p->precision = MG5_FP64;
+    return MG5_OK;
+}
+
+int mg5_ndgp_coefficients(double a, double omega_m0, double h0rc, double *beta, double *alpha,
+                          double *s)
+{
+    if (!(a > 0.0 && a <= 1.0) || !(omega_m0 > 0.0 && omega_m0 <= 1.0) || !(h0rc > 0.0))
+        return MG5_E_ARG;
+    const double H0 = 100.0 / 299792.458;  // h/Mpc, c = 1
+    const double a3 = a * a * a;
+    const double E2 = omega_m0 / a3 + 1.0 - omega_m0;  // (H/H0)^2 of the LCDM-matched background
+    const double E = std::sqrt(E2);
+    const double hdot_h2 = -1.5 * (omega_m0 / a3) / E2;  // Hdot/H^2 = (1/2) dlnH^2/dlna
+    const double b = 1.0 + 2.0 * (E * h0rc) * (1.0 + hdot_h2 / 3.0);
+    const double rc = h0rc / H0;
+    if (beta)
+        *beta = b;
+    if (alpha)
+        *alpha = rc * rc / (3.0 * b * a * a);
+    if (s)
+        *s = omega_m0 * H0 * H0 / (b * a);
+    return MG5_OK;
+}
+
+int mg5_workspace_bytes(int N, int precision, size_t *bytes)
+{
+    if (!bytes || check_size(N) != MG5_OK)
+        return MG5_E_ARG;
+    if (precision == MG5_FP64)
+        *bytes = fp64_bytes(N);
+    else if (precision == MG5_MIXED)
+        *bytes = mixed_bytes(N);
+    else
+        return MG5_E_ARG;
+    return MG5_OK;
+}
+
+int mg5_create(mg5_ctx **out, int device, size_t budget)
+{
+    if (!out)
+        return MG5_E_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return MG5_E_CUDA;
+    }
+    if (device < 0 || device >= ndev)
+        return MG5_E_ARG;
+    mg5_ctx *ctx = new (std::nothrow) mg5_ctx();
+    if (!ctx)
+        return MG5_E_OOM;
+    ctx->device = device;
+    ctx->budget = budget;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&ctx->partials, sizeof(double2) * kMaxPartials);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&ctx->ls, sizeof(LevelScal) * kScalSlots);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&ctx->cnt, sizeof(SolveCounters));
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&ctx->h_rel, 64 * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&ctx->ev0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&ctx->ev1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        mg5_destroy(ctx);
+        return MG5_E_CUDA;
+    }
+    *out = ctx;
+    return MG5_OK;
+}
+
+int mg5_release(mg5_ctx *ctx)
+{
+    if (!ctx)
+        return MG5_E_ARG;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (Hier *h : ctx->hiers)
+        free_hier(ctx, h);
+    ctx->hiers.clear();
+    for (MixedHier *m : ctx->mixed)
+        free_mixed(m, &ctx->held);
+    ctx->mixed.clear();
+    ctx_free(ctx, ctx->stage, ctx->stage_bytes);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    ctx_free(ctx, ctx->patch, ctx->patch_bytes);
+    ctx->patch = nullptr;
+    ctx->patch_bytes = 0;
+    return MG5_OK;
+}
+
+int mg5_destroy(mg5_ctx *ctx)
+{
+    if (!ctx)
+        return MG5_E_ARG;
+    mg5_release(ctx);
+    if (ctx->partials)
+        cudaFree(ctx->partials);
+    if (ctx->ls)
+        cudaFree(ctx->ls);
+    if (ctx->cnt)
+        cudaFree(ctx->cnt);
+    if (ctx->h_rel)
+        cudaFreeHost(ctx->h_rel);
+    if (ctx->ev0)
+        cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1)
+        cudaEventDestroy(ctx->ev1);
+    delete ctx;
+    return MG5_OK;
+}
+
+const char *mg5_last_error(mg5_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t mg5_bytes_held(mg5_ctx *ctx) { return ctx ? ctx->held : 0; }
+
+int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p,
+                          unsigned flags, double *phi, double *grad, mg5_info *info, void *stream)
+{
+    if (!ctx || !delta || !phi)
+        return MG5_E_ARG;
+    RET(check_size(N));
+    RET(check_params(p));
+    if (flags & ~(MG5_WARM | MG5_HOST_IO))
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (info)
+        std::memset(info, 0, sizeof(*info));
+    const long long n3 = (long long)N * N * N;
+    const size_t fb = (size_t)n3 * sizeof(double);
+    const double *d_delta = delta;
+    double *d_phi = phi, *d_grad = grad;
+    CK(cudaEventRecord(ctx->ev0, st));
+    if (flags & MG5_HOST_IO) {
+        RET(ensure_buffer(ctx, &ctx->stage, &ctx->stage_bytes, fb * (grad ? 5 : 2)));
+        d_phi = ctx->stage;
+        double *dd = ctx->stage + n3;
+        d_grad = grad ? ctx->stage + 2 * n3 : nullptr;
+        CK(cudaMemcpyAsync(dd, delta, fb, cudaMemcpyHostToDevice, st));
+        d_delta = dd;
+        if (flags & MG5_WARM)
+            CK(cudaMemcpyAsync(d_phi, phi, fb, cudaMemcpyHostToDevice, st));
+    }
+    if (!(flags & MG5_WARM))
+        CK(cudaMemsetAsync(d_phi, 0, fb, st));
+    int status;
+    if (p->precision == MG5_FP64) {
+        status = solve64(ctx, d_delta, N, p, d_phi, info, st);
+    } else {
+        MixedHier *mh = nullptr;
+        for (MixedHier *m : ctx->mixed)
+            if (m->N == N)
+                mh = m;
+        if (!mh) {
+            int rc = alloc_mixed(N, ctx->budget, &ctx->held, &mh, &ctx->err);
+            if (rc != MG5_OK)
+                return rc;
+            ctx->mixed.push_back(mh);
+        }
+        MixedShared sh{ctx->partials, ctx->ls, ctx->cnt, ctx->h_rel};
+        status = solve_mixed(mh, sh, d_delta, p, d_phi, info, st, &ctx->err);
+    }
+    if (status == MG5_E_CUDA || status == MG5_E_ARG || status == MG5_E_OOM)
+        return status;
+    if (d_grad)
+        CK(launch_force(d_phi, N, N, N, 0, p->h, 1, d_grad, st));
+    if (flags & MG5_HOST_IO) {
+        CK(cudaMemcpyAsync(phi, d_phi, fb, cudaMemcpyDeviceToHost, st));
+        if (grad)
+            CK(cudaMemcpyAsync(grad, d_grad, 3 * fb, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaEventRecord(ctx->ev1, st));
+    SolveCounters cnt;
+    CK(cudaMemcpyAsync(&cnt, ctx->cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    double tail[2];
+    CK(cudaMemcpyAsync(tail, &ctx->ls[0].c, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(tail + 1, &ctx->ls[0].mean, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (status == MG5_OK && cnt.clamped > 0)
+        status = MG5_W_DISC_CLAMP;
+    if (info) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        info->ms_total = ms;
+        info->status = status;
+        info->disc_clamped = (long long)cnt.clamped;
+        info->compat_c = tail[0];
+        info->phi_mean_removed = tail[1];
+        const long long nc = info->coarsest_n;
+        info->cell_updates += (long long)cnt.coarse_sweeps * nc * nc * nc;
+    }
+    return status;
+}
+
+int mg5_force(mg5_ctx *ctx, const double *phi, const int dims[3], int ghost, double h, int periodic,
+              double *grad, void *stream)
+{
+    if (!ctx || !phi || !dims || !grad || !(h > 0.0) || ghost < 0)
+        return MG5_E_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] - 2 * ghost < 1)
+            return MG5_E_ARG;
+    if (periodic && ghost != 0)
+        return MG5_E_ARG;
+    if (!periodic && ghost < 1)
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_force(phi, dims[0], dims[1], dims[2], ghost, h, periodic ? 1 : 0, grad,
+                    (cudaStream_t)stream));
+    return MG5_OK;
+}
+
+int mg5_refine_interpolate(mg5_ctx *ctx, const double *phic, int Nc, const int o[3], const int pn[3],
+                           int ghost, double *fine, void *stream)
+{
+    if (!ctx || !phic || !o || !pn || !fine || Nc < 1 || ghost < 0 || ghost > 4)
+        return MG5_E_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (o[a] < 0 || o[a] >= Nc || pn[a] < 1 || pn[a] > Nc)
+            return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_refine(phic, Nc, o, pn, ghost, fine, (cudaStream_t)stream));
+    return MG5_OK;
+}
+
+int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const mg5_params *p,
+                    double compat_c, double *phi, mg5_info *info, void *stream)
+{
+    if (!ctx || !delta_f || !pf || !phi)
+        return MG5_E_ARG;
+    RET(check_params(p));
+    for (int a = 0; a < 3; ++a)
+        if (pf[a] < 4 || (pf[a] & 1))
+            return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (info)
+        std::memset(info, 0, sizeof(*info));
+    const long long ni = (long long)pf[0] * pf[1] * pf[2];
+    const long long nb_box = (long long)(pf[0] + 2) * (pf[1] + 2) * (pf[2] + 2);
+    RET(ensure_buffer(ctx, &ctx->patch, &ctx->patch_bytes, (size_t)(ni + nb_box) * sizeof(double)));
+    double *fint = ctx->patch;
+    double *tmp = ctx->patch + ni;
+    CK(cudaEventRecord(ctx->ev0, st));
+    LevelScal *ls = ctx->ls + kPatchSlot;
+    CK(cudaMemsetAsync(ls, 0, sizeof(LevelScal), st));
+    CK(cudaMemsetAsync(ctx->cnt, 0, sizeof(SolveCounters), st));
+    int nb = 0;
+    CK(launch_scale(delta_f, p->s, fint, ni, ctx->partials, &nb, st));
+    CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_FNORM, st));
+    CK(cudaMemcpyAsync(tmp, phi, nb_box * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    const CoefT<double> cf = make_coef<double>(p->h, p->alpha);
+    const int check = 10;
+    const long long cap = (long long)std::max(p->max_cycles, 1) * check;
+    double *cur = phi, *oth = tmp;
+    long long sweeps = 0;
+    int status = MG5_E_NOT_CONVERGED;
+    int nchk = 0;
+    for (;;) {
+        CK(launch_patch_residual(cur, fint, compat_c, pf, cf, ctx->partials, &nb, st));
+        CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_NORM, st));
+        CK(cudaMemcpyAsync(ctx->h_rel, &ls->rel, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const double rel = *ctx->h_rel;
+        if (info) {
+            info->rel_residual = rel;
+            if (nchk < 64) {
+                info->history[nchk] = rel;
+                info->n_history = nchk + 1;
+            }
+        }
+        ++nchk;
+        if (!std::isfinite(rel)) {
+            status = MG5_E_NONFINITE;
+            break;
+        }
+        if (rel <= p->tol) {
+            status = MG5_OK;
+            break;
+        }
+        if (sweeps >= cap)
+            break;
+        for (int q = 0; q < check && sweeps < cap; ++q, ++sweeps) {
+            CK(launch_patch_sweep(cur, oth, fint, compat_c, pf, cf, &ctx->cnt->clamped, st));
+            std::swap(cur, oth);
+        }
+    }
+    if (cur != phi)
+        CK(cudaMemcpyAsync(phi, cur, nb_box * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaEventRecord(ctx->ev1, st));
+    SolveCounters cnt;
+    CK(cudaMemcpyAsync(&cnt, ctx->cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (status == MG5_OK && cnt.clamped > 0)
+        status = MG5_W_DISC_CLAMP;
+    if (info) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        info->ms_total = ms;
+        info->status = status;
+        info->cycles = (int)sweeps;
+        info->cell_updates = sweeps * ni;
+        info->disc_clamped = (long long)cnt.clamped;
+        info->compat_c = compat_c;
+    }
+    return status;
+}
+
+int mg5_step_sweep(mg5_ctx *ctx, const double *in, double *out, const double *f, double c, int N,
+                   double h, double alpha, void *stream)
+{
+    if (!ctx || !in || !out || !f || in == out || N < 2 || (N & 1) || !(h > 0.0))
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    double *cd = &ctx->ls[kStepSlot].c;
+    CK(cudaMemcpyAsync(cd, &c, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(launch_sweep<double>(in, out, f, cd, N, make_coef<double>(h, alpha), &ctx->cnt->clamped, st));
+    CK(cudaStreamSynchronize(st));
+    return MG5_OK;
+}
+
+int mg5_step_operator(mg5_ctx *ctx, const double *phi, int N, double h, double alpha, double *out,
+                      void *stream)
+{
+    if (!ctx || !phi || !out || N < 1 || !(h > 0.0))
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_operator<double>(phi, N, make_coef<double>(h, alpha), out, (cudaStream_t)stream));
+    return MG5_OK;
+}
+
+int mg5_step_residual(mg5_ctx *ctx, const double *phi, const double *f, double c, int N, double h,
+                      double alpha, double *r, void *stream)
+{
+    if (!ctx || !phi || !f || !r || N < 1 || !(h > 0.0))
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    double *cd = &ctx->ls[kStepSlot].c;
+    CK(cudaMemcpyAsync(cd, &c, sizeof(double), cudaMemcpyHostToDevice, st));
+    int nb = 0;
+    CK(launch_residual<double>(phi, f, cd, N, make_coef<double>(h, alpha), r, ctx->partials, &nb, st));
+    CK(cudaStreamSynchronize(st));
+    return MG5_OK;
+}
+
+int mg5_step_restrict(mg5_ctx *ctx, const double *fine, int N, double *coarse, void *stream)
+{
+    if (!ctx || !fine || !coarse || N < 2 || (N & 1))
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_restrict<double>(fine, N, coarse, (cudaStream_t)stream));
+    return MG5_OK;
+}
+
+int mg5_step_prolong_add(mg5_ctx *ctx, const double *coarse, int Nc, double *fine, void *stream)
+{
+    if (!ctx || !coarse || !fine || Nc < 1)
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(launch_prolong_add<double>(coarse, nullptr, Nc, fine, nullptr, nullptr, (cudaStream_t)stream));
+    return MG5_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,274 @@
+// mg5_dev.cuh -- device helpers shared by the mg5 kernels: the 19-point
+// stencil gather, the cell arithmetic of Eq. (eomvarphi) and deterministic
+// block reductions.
+//
+// The discrete operator: D_aa = (phi[+a] + phi[-a] - 2 phi)/h^2,
+// D_ab = (phi[+a+b] - phi[+a-b] - phi[-a+b] + phi[-a-b])/(4 h^2), L = sum D_aa.
+// (lap)^2 - (d_i d_j phi)^2 = (2/3) L^2 - Sigma with
+// Sigma = (1/3) sum_{a<b} (D_aa - D_bb)^2 + 2 sum_{a<b} D_ab^2, which does not
+// depend on the centre value (the centre cancels in D_aa - D_bb and is not
+// used by D_ab).  So with every neighbour fixed, the cell's equation
+// L + alpha((2/3) L^2 - Sigma) = rhs is a quadratic in L whose physical root
+// (continuous with alpha -> 0) is L = 2 b / (1 + sqrt(1 + 8 alpha b / 3)),
+// b = rhs + alpha Sigma, and phi_ijk = (sum of faces - h^2 L) / 6.
+// That value is the fixed point of the Newton update of Eq. (newton).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace mg5 {
+
+// Per-grid constants of the cell arithmetic.
+template <typename T>
+struct CoefT {
+    T h2;      // h^2
+    T inv_h2;  // 1/h^2
+    T a_h4;    // alpha / h^4
+    T k8;      // 8 alpha / 3
+    T k23;     // 2 alpha / 3
+};
+
+template <typename T>
+__host__ __device__ inline CoefT<T> make_coef(double h, double alpha)
+{
+    CoefT<T> c;
+    c.h2 = (T)(h * h);
+    c.inv_h2 = (T)(1.0 / (h * h));
+    c.a_h4 = (T)(alpha / (h * h * h * h));
+    c.k8 = (T)(8.0 * alpha / 3.0);
+    c.k23 = (T)(2.0 * alpha / 3.0);
+    return c;
+}
+
+// The 19 values the cell arithmetic reads: centre, 6 faces, 12 edges.
+template <typename T>
+struct St {
+    T c, xp, xm, yp, ym, zp, zm;
+    T xpyp, xpym, xmyp, xmym;
+    T xpzp, xpzm, xmzp, xmzm;
+    T ypzp, ypzm, ymzp, ymzm;
+};
+
+// Row offsets of the 9 (i', j') rows around (i, j); k offsets are added by the gather.
+struct Rows {
+    long long r00, rp0, rm0, r0p, r0m, rpp, rpm, rmp, rmm;
+};
+
+__device__ __forceinline__ Rows periodic_rows(int n, int i, int j)
+{
+    const int ip = (i == n - 1) ? 0 : i + 1, im = (i == 0) ? n - 1 : i - 1;
+    const int jp = (j == n - 1) ? 0 : j + 1, jm = (j == 0) ? n - 1 : j - 1;
+    const long long N = n;
+    Rows r;
+    r.r00 = ((long long)i * N + j) * N;
+    r.rp0 = ((long long)ip * N + j) * N;
+    r.rm0 = ((long long)im * N + j) * N;
+    r.r0p = ((long long)i * N + jp) * N;
+    r.r0m = ((long long)i * N + jm) * N;
+    r.rpp = ((long long)ip * N + jp) * N;
+    r.rpm = ((long long)ip * N + jm) * N;
+    r.rmp = ((long long)im * N + jp) * N;
+    r.rmm = ((long long)im * N + jm) * N;
+    return r;
+}
+
+// Box of dims (d0, d1, d2) without wrapping; (i, j) must have both neighbours.
+__device__ __forceinline__ Rows box_rows(int d1, int d2, int i, int j)
+{
+    const long long D1 = d1, D2 = d2;
+    Rows r;
+    r.r00 = ((long long)i * D1 + j) * D2;
+    r.rp0 = ((long long)(i + 1) * D1 + j) * D2;
+    r.rm0 = ((long long)(i - 1) * D1 + j) * D2;
+    r.r0p = ((long long)i * D1 + j + 1) * D2;
+    r.r0m = ((long long)i * D1 + j - 1) * D2;
+    r.rpp = ((long long)(i + 1) * D1 + j + 1) * D2;
+    r.rpm = ((long long)(i + 1) * D1 + j - 1) * D2;
+    r.rmp = ((long long)(i - 1) * D1 + j + 1) * D2;
+    r.rmm = ((long long)(i - 1) * D1 + j - 1) * D2;
+    return r;
+}
+
+// Faces (and the centre) from F, edges from E.
+template <typename T>
+__device__ __forceinline__ void gather(const T *F, const T *E, const Rows &r, int k, int kp,
+                                       int km, St<T> &s)
+{
+    s.c = F[r.r00 + k];
+    s.xp = F[r.rp0 + k];
+    s.xm = F[r.rm0 + k];
+    s.yp = F[r.r0p + k];
+    s.ym = F[r.r0m + k];
+    s.zp = F[r.r00 + kp];
+    s.zm = F[r.r00 + km];
+    s.xpyp = E[r.rpp + k];
+    s.xpym = E[r.rpm + k];
+    s.xmyp = E[r.rmp + k];
+    s.xmym = E[r.rmm + k];
+    s.xpzp = E[r.rp0 + kp];
+    s.xpzm = E[r.rp0 + km];
+    s.xmzp = E[r.rm0 + kp];
+    s.xmzm = E[r.rm0 + km];
+    s.ypzp = E[r.r0p + kp];
+    s.ypzm = E[r.r0p + km];
+    s.ymzp = E[r.r0m + kp];
+    s.ymzm = E[r.r0m + km];
+}
+
+// S = sum of the 6 faces; sig = Sigma * h^4.
+template <typename T>
+__device__ __forceinline__ void stencil_parts(const St<T> &s, T &S, T &sig)
+{
+    const T sx = s.xp + s.xm, sy = s.yp + s.ym, sz = s.zp + s.zm;
+    S = sx + sy + sz;
+    const T dxy = (s.xpyp - s.xpym) - (s.xmyp - s.xmym);
+    const T dxz = (s.xpzp - s.xpzm) - (s.xmzp - s.xmzm);
+    const T dyz = (s.ypzp - s.ypzm) - (s.ymzp - s.ymzm);
+    const T a = sx - sy, b = sx - sz, c = sy - sz;
+    sig = (a * a + b * b + c * c) * (T)(1.0 / 3.0) + (dxy * dxy + dxz * dxz + dyz * dyz) * (T)0.125;
+}
+
+// Physical root of (2 alpha/3) L^2 + L - b = 0; a negative discriminant is
+// clamped to zero and flagged.
+template <typename T>
+__device__ __forceinline__ T physical_root(T b, T k8, bool &clamped)
+{
+    T disc = (T)1 + k8 * b;
+    if (disc < (T)0) {
+        disc = (T)0;
+        clamped = true;
+    }
+    return (T)2 * b / ((T)1 + sqrt(disc));
+}
+
+// New centre value solving the cell's equation with op(...) = rhs.
+template <typename T>
+__device__ __forceinline__ T cell_update(const St<T> &s, T rhs, const CoefT<T> &cf, bool &clamped)
+{
+    T S, sig;
+    stencil_parts(s, S, sig);
+    const T b = rhs + cf.a_h4 * sig;
+    const T L = physical_root(b, cf.k8, clamped);
+    return (S - cf.h2 * L) * (T)(1.0 / 6.0);
+}
+
+// op(phi) at the cell = L + alpha((2/3) L^2 - Sigma).
+template <typename T>
+__device__ __forceinline__ T cell_op(const St<T> &s, const CoefT<T> &cf)
+{
+    T S, sig;
+    stencil_parts(s, S, sig);
+    const T L = (S - (T)6 * s.c) * cf.inv_h2;
+    return L + cf.k23 * L * L - cf.a_h4 * sig;
+}
+
+// ---- correction form (mixed precision) -------------------------------------
+// With a fixed base B and a correction e, op(B + e) - op(B) expands without
+// cancellation against op(B):
+//   L_e + alpha [ (4/3) L_B L_e + (2/3) L_e^2 - 2 Sigma(B, e) - Sigma(e) ],
+// Sigma(., .) the symmetric bilinear form of Sigma.  Sigma(B, e) and
+// Sigma(e) do not depend on e_ijk, so the cell equation is again a quadratic
+// in L_e:  (2 alpha/3) L_e^2 + beta' L_e - b' = 0, beta' = 1 + (4 alpha/3) L_B,
+// b' = rhs + alpha (2 Sigma(B, e) + Sigma(e)), physical root
+// L_e = 2 b' / (beta' + sqrt(beta'^2 + 8 alpha b' / 3)).
+template <typename T>
+struct Parts {
+    T S, a, b, c, dxy, dxz, dyz;  // S = faces; a,b,c = sx-sy, sx-sz, sy-sz
+};
+
+template <typename T>
+__device__ __forceinline__ Parts<T> parts_of(const St<T> &s)
+{
+    Parts<T> p;
+    const T sx = s.xp + s.xm, sy = s.yp + s.ym, sz = s.zp + s.zm;
+    p.S = sx + sy + sz;
+    p.a = sx - sy;
+    p.b = sx - sz;
+    p.c = sy - sz;
+    p.dxy = (s.xpyp - s.xpym) - (s.xmyp - s.xmym);
+    p.dxz = (s.xpzp - s.xpzm) - (s.xmzp - s.xmzm);
+    p.dyz = (s.ypzp - s.ypzm) - (s.ymzp - s.ymzm);
+    return p;
+}
+
+// Sigma(p, q) * h^4
+template <typename T>
+__device__ __forceinline__ T sig_bil(const Parts<T> &p, const Parts<T> &q)
+{
+    return (p.a * q.a + p.b * q.b + p.c * q.c) * (T)(1.0 / 3.0) +
+           (p.dxy * q.dxy + p.dxz * q.dxz + p.dyz * q.dyz) * (T)0.125;
+}
+
+template <typename T>
+__device__ __forceinline__ T cell_update_corr(const St<T> &e, const St<T> &B, T rhs,
+                                              const CoefT<T> &cf, bool &clamped)
+{
+    const Parts<T> pe = parts_of(e), pb = parts_of(B);
+    const T LB = (pb.S - (T)6 * B.c) * cf.inv_h2;
+    const T bp = (T)1 + (T)2 * cf.k23 * LB;
+    const T b = rhs + cf.a_h4 * ((T)2 * sig_bil(pb, pe) + sig_bil(pe, pe));
+    T disc = bp * bp + cf.k8 * b;
+    if (disc < (T)0) {
+        disc = (T)0;
+        clamped = true;
+    }
+    const T L = (T)2 * b / (bp + sqrt(disc));
+    return (pe.S - cf.h2 * L) * (T)(1.0 / 6.0);
+}
+
+template <typename T>
+__device__ __forceinline__ T cell_op_corr(const St<T> &e, const St<T> &B, const CoefT<T> &cf)
+{
+    const Parts<T> pe = parts_of(e), pb = parts_of(B);
+    const T LB = (pb.S - (T)6 * B.c) * cf.inv_h2;
+    const T Le = (pe.S - (T)6 * e.c) * cf.inv_h2;
+    return Le + cf.k23 * Le * ((T)2 * LB + Le) -
+           cf.a_h4 * ((T)2 * sig_bil(pb, pe) + sig_bil(pe, pe));
+}
+
+// Dispatch on the presence of a base field.
+template <typename T, bool BASE>
+__device__ __forceinline__ T upd(const St<T> &s, const St<T> &B, T rhs, const CoefT<T> &cf,
+                                 bool &clamped)
+{
+    if constexpr (BASE)
+        return cell_update_corr(s, B, rhs, cf, clamped);
+    else
+        return cell_update(s, rhs, cf, clamped);
+}
+
+template <typename T, bool BASE>
+__device__ __forceinline__ T opr(const St<T> &s, const St<T> &B, const CoefT<T> &cf)
+{
+    if constexpr (BASE)
+        return cell_op_corr(s, B, cf);
+    else
+        return cell_op(s, cf);
+}
+
+// Deterministic sum of a double2 over the block; the result is valid in thread 0.
+// Every thread of the block must call it.
+__device__ __forceinline__ double2 block_sum2(double2 v)
+{
+    __shared__ double2 smem_sum2[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0)
+        smem_sum2[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < nw ? smem_sum2[lane] : make_double2(0.0, 0.0);
+        for (int o = 16; o > 0; o >>= 1) {
+            v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+            v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+        }
+    }
+    return v;
+}
+
+}  // namespace mg5

@@ -1,0 +1,109 @@
+// mg5_kernels.cuh -- host-side launchers of the mg5 kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "mg5_dev.cuh"
+
+namespace mg5 {
+
+// Device scalars of one grid of the hierarchy.
+struct LevelScal {
+    double c;      // compatibility constant
+    double m;      // mean of the last residual (before projection)
+    double rnorm;  // ||r - m||_2 of the last residual
+    double rel;    // rnorm / fnorm (finest grid) or rnorm
+    double fnorm;  // ||f||_2 (finest grid)
+    double mean;   // scratch for the gauge (mean of phi)
+    double pad[2];
+};
+
+// Device counters shared by one solve.
+struct SolveCounters {
+    unsigned long long clamped;
+    int coarse_sweeps;
+    int pad;
+};
+
+constexpr int kBlock = 256;
+constexpr int kScalSlots = 48;   // LevelScal slots held by a context
+constexpr int kPatchSlot = 16;   // slot used by the patch relaxation
+constexpr int kStepSlot = 17;    // slot used by the single-step entry points
+constexpr int kInnerBase = 20;   // first slot of the mixed solve's FP32 grids
+constexpr int kMaxPartials = 8192;  // partial-sum slots per reduction
+
+// Number of blocks of kBlock threads to cover `work` items (capped for reductions).
+inline int blocks_for(long long work) { return (int)((work + kBlock - 1) / kBlock); }
+
+// Process-wide count of kernel launches the library has enqueued.
+void count_launch(long long n);
+long long launches_total();
+
+// finalize modes
+// FIN_RESID: m = mean r, c -= m, rnorm = ||r - m||, rel = rnorm / fnorm
+// FIN_STATS: as FIN_RESID but c is left alone
+// FIN_NORM:  rnorm = ||r|| (no projection), rel = rnorm / fnorm
+// FIN_FNORM: fnorm = sqrt(sum of the second component)
+// FIN_MEAN:  mean = sum of the first component / ncells
+enum FinalizeMode { FIN_RESID = 0, FIN_FNORM = 1, FIN_MEAN = 2, FIN_STATS = 3, FIN_NORM = 4 };
+
+// ---- FP64/FP32 periodic kernels (templates instantiated for double and float)
+// B (optional): base field of the correction form (mixed precision)
+template <typename T>
+cudaError_t launch_sweep(const T *in, T *out, const T *f, const double *cptr, int n,
+                         CoefT<T> cf, unsigned long long *clamp, cudaStream_t st,
+                         const T *B = nullptr);
+template <typename T>
+cudaError_t launch_operator(const T *phi, int n, CoefT<T> cf, T *out, cudaStream_t st);
+// r (nullable) = f + c - op(phi); partial sums (sum r, sum r^2) per block.
+template <typename T>
+cudaError_t launch_residual(const T *phi, const T *f, const double *cptr, int n, CoefT<T> cf,
+                            T *r, double2 *partials, int *nblocks, cudaStream_t st);
+// fused residual + 8-child restriction of v and r (vc and v0c get R v, rc gets R r).
+template <typename T>
+cudaError_t launch_resid_restrict(const T *v, const T *f, const double *cptr, int n,
+                                  CoefT<T> cf, T *vc, T *v0c, T *rc, double2 *partials,
+                                  int *nblocks, cudaStream_t st, const T *B = nullptr);
+// coarse = 8-child mean of fine
+template <typename T>
+cudaError_t launch_restrict(const T *fine, int n, T *coarse, cudaStream_t st);
+// fc = op_c(vc) + fc - m_fine ; c_coarse = 0
+template <typename T>
+cudaError_t launch_coarse_rhs(const T *vc, T *fc, const double *m_fine, double *c_coarse, int nc,
+                              CoefT<T> cfc, cudaStream_t st, const T *B = nullptr);
+// vf += P(vc - v0c) (v0c may be NULL: plain prolongation of vc); c_fine += c_coarse if both non-NULL
+template <typename T>
+cudaError_t launch_prolong_add(const T *vc, const T *v0c, int nc, T *vf, double *c_fine,
+                               const double *c_coarse, cudaStream_t st);
+// coarsest grid: sweeps until the residual falls by rtol or nu_max sweeps; one CTA.
+template <typename T>
+cudaError_t launch_coarsest(T *v, T *tmp, const T *f, int n, CoefT<T> cf, double *cptr, int nu_max,
+                            double rtol, unsigned long long *clamp, int *sweeps, cudaStream_t st,
+                            const T *B = nullptr);
+
+// ---- FP64 helpers
+cudaError_t launch_finalize(const double2 *partials, int nb, double ncells, LevelScal *ls,
+                            int mode, cudaStream_t st);
+// f = s * delta, partial sums (0, f^2)
+cudaError_t launch_scale(const double *delta, double s, double *f, long long n3, double2 *partials,
+                         int *nblocks, cudaStream_t st);
+// partial sums (phi, 0)
+cudaError_t launch_sum(const double *phi, long long n3, double2 *partials, int *nblocks,
+                       cudaStream_t st);
+// phi -= *mean
+cudaError_t launch_sub_mean(double *phi, long long n3, const double *mean, cudaStream_t st);
+cudaError_t launch_force(const double *phi, int d0, int d1, int d2, int ghost, double h,
+                         int periodic, double *grad, cudaStream_t st);
+cudaError_t launch_refine(const double *phic, int nc, const int o[3], const int pn[3], int ghost,
+                          double *fine, cudaStream_t st);
+// Dirichlet patch (interior pf, box pf + 2): one full sweep in -> out (out must hold the ghosts)
+cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint, double rhs_add,
+                               const int pf[3], CoefT<double> cf, unsigned long long *clamp,
+                               cudaStream_t st);
+// partial sums (r, r^2) of r = fint + rhs_add - op(phi) over the interior
+cudaError_t launch_patch_residual(const double *phi, const double *fint, double rhs_add,
+                                  const int pf[3], CoefT<double> cf, double2 *partials, int *nblocks,
+                                  cudaStream_t st);
+
+}  // namespace mg5

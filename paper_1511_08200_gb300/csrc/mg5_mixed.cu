@@ -1,0 +1,349 @@
+// mg5_mixed.cu -- mixed-precision solve: FP64 residual + defect correction
+// around FP32 FAS V-cycles on the correction equation (the FP32 kernels take
+// the correction form of the cell arithmetic, see mg5_dev.cuh).
+//
+// Outer step k:  r = s delta + c - op(phi) in FP64 (its mean m is projected
+// out; ||r - m|| / ||s delta|| is the stopping test), B = fp32(phi) restricted
+// to every grid, then `inner_cycles` FP32 V-cycles for
+//     op(B + e) - op(B) = r - m + c_e,   e = 0 at the start,
+// then phi += e and c += c_e in FP64.  Because only the residual and the
+// update are formed in FP64, the FP32 solve may stop at its own precision.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "mg5_mixed.cuh"
+
+namespace mg5 {
+
+namespace {
+
+constexpr double kCoarseRtol = 1e-3;
+
+int levels_of(int N, int *sz)
+{
+    int L = 0, n = N;
+    sz[L++] = n;
+    while ((n / 2) % 2 == 0 && n / 2 >= 4 && L < kMixMaxLevels) {
+        n /= 2;
+        sz[L++] = n;
+    }
+    return L;
+}
+
+// r32 = fp32(f + c - op(phi)) and B = fp32(phi), FP64 arithmetic; partial sums of r.
+__global__ void k_resid64_mixed(const double *__restrict__ phi, const double *__restrict__ f,
+                                const double *__restrict__ cptr, int n, CoefT<double> cf,
+                                float *__restrict__ r32, float *__restrict__ B,
+                                double2 *__restrict__ partials)
+{
+    const long long total = (long long)n * n * n;
+    const double c = *cptr;
+    double2 acc = make_double2(0.0, 0.0);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t % n);
+        const long long q = t / n;
+        const int j = (int)(q % n), i = (int)(q / n);
+        const Rows r = periodic_rows(n, i, j);
+        const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
+        St<double> s;
+        gather(phi, phi, r, k, kp, km, s);
+        const double res = f[t] + c - cell_op(s, cf);
+        r32[t] = (float)res;
+        B[t] = (float)s.c;
+        acc.x += res;
+        acc.y += res * res;
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0)
+        partials[blockIdx.x] = acc;
+}
+
+__global__ void k_update_mixed(double *__restrict__ phi, const float *__restrict__ e, long long n3)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n3)
+        phi[t] += (double)e[t];
+}
+
+// scalar bookkeeping: 0: a.c -= a.m ; 1: b.c = -a.m ; 2: a.c += b.c
+__global__ void k_scal(LevelScal *a, LevelScal *b, int op)
+{
+    if (op == 0)
+        a->c -= a->m;
+    else if (op == 1)
+        b->c = -a->m;
+    else
+        a->c += b->c;
+}
+
+struct RunMix {
+    MixedHier *h;
+    const MixedShared &sh;
+    const mg5_params *p;
+    cudaStream_t st;
+    std::string *err;
+    double hl[kMixMaxLevels];
+    long long cu = 0;  // cell updates of the non-coarsest sweeps
+
+    LevelScal *ls(int l) { return sh.ls + kInnerBase + l; }
+    double *c(int l) { return &ls(l)->c; }
+    double *m(int l) { return &ls(l)->m; }
+
+    int fail(const char *what, cudaError_t e)
+    {
+        *err = std::string(what) + ": " + cudaGetErrorString(e);
+        return MG5_E_CUDA;
+    }
+
+    int sweep(int l)
+    {
+        cudaError_t e = launch_sweep<float>(h->e[l], h->etmp[l], h->f[l], c(l), h->n[l],
+                                            make_coef<float>(hl[l], p->alpha), &sh.cnt->clamped, st,
+                                            h->B[l]);
+        if (e != cudaSuccess)
+            return fail("sweep32", e);
+        std::swap(h->e[l], h->etmp[l]);
+        cu += (long long)h->n[l] * h->n[l] * h->n[l];
+        return MG5_OK;
+    }
+
+    int coarsest(int l)
+    {
+        cudaError_t e = launch_coarsest<float>(h->e[l], h->etmp[l], h->f[l], h->n[l],
+                                               make_coef<float>(hl[l], p->alpha), c(l),
+                                               p->nu_coarse, kCoarseRtol, &sh.cnt->clamped,
+                                               &sh.cnt->coarse_sweeps, st, h->B[l]);
+        return e == cudaSuccess ? MG5_OK : fail("coarsest32", e);
+    }
+
+    int resid_restrict(int l)
+    {
+        int nb = 0;
+        cudaError_t e = launch_resid_restrict<float>(h->e[l], h->f[l], c(l), h->n[l],
+                                                     make_coef<float>(hl[l], p->alpha), h->e[l + 1],
+                                                     h->e0[l + 1], h->f[l + 1], sh.partials, &nb,
+                                                     st, h->B[l]);
+        if (e == cudaSuccess) {
+            const double n3 = (double)h->n[l] * h->n[l] * h->n[l];
+            e = launch_finalize(sh.partials, nb, n3, ls(l), FIN_RESID, st);
+        }
+        return e == cudaSuccess ? MG5_OK : fail("resid_restrict32", e);
+    }
+
+    int coarse_visit(int l)
+    {
+        cudaError_t e = launch_coarse_rhs<float>(h->e[l], h->f[l], m(l - 1), c(l), h->n[l],
+                                                 make_coef<float>(hl[l], p->alpha), st, h->B[l]);
+        if (e != cudaSuccess)
+            return fail("coarse_rhs32", e);
+        if (l == h->nlev - 1)
+            return coarsest(l);
+        for (int s = 0; s < p->nu1; ++s)
+            if (int rc = sweep(l))
+                return rc;
+        if (int rc = resid_restrict(l))
+            return rc;
+        if (int rc = coarse_visit(l + 1))
+            return rc;
+        e = launch_prolong_add<float>(h->e[l + 1], h->e0[l + 1], h->n[l + 1], h->e[l], c(l),
+                                      c(l + 1), st);
+        if (e != cudaSuccess)
+            return fail("prolong32", e);
+        for (int s = 0; s < p->nu2; ++s)
+            if (int rc = sweep(l))
+                return rc;
+        return MG5_OK;
+    }
+
+    // one inner V-cycle on the finest grid
+    int vcycle0()
+    {
+        if (h->nlev == 1)
+            return coarsest(0);
+        for (int s = 0; s < p->nu1; ++s)
+            if (int rc = sweep(0))
+                return rc;
+        if (int rc = resid_restrict(0))
+            return rc;
+        if (int rc = coarse_visit(1))
+            return rc;
+        cudaError_t e =
+            launch_prolong_add<float>(h->e[1], h->e0[1], h->n[1], h->e[0], c(0), c(1), st);
+        if (e != cudaSuccess)
+            return fail("prolong32", e);
+        for (int s = 0; s < p->nu2; ++s)
+            if (int rc = sweep(0))
+                return rc;
+        return MG5_OK;
+    }
+};
+
+}  // namespace
+
+size_t mixed_bytes(int N)
+{
+    int sz[kMixMaxLevels];
+    const int L = levels_of(N, sz);
+    const size_t n3 = (size_t)N * N * N;
+    size_t b = n3 * sizeof(double) + 4 * n3 * sizeof(float);
+    for (int l = 1; l < L; ++l)
+        b += 5 * (size_t)sz[l] * sz[l] * sz[l] * sizeof(float);
+    return b;
+}
+
+void free_mixed(MixedHier *m, size_t *held)
+{
+    if (!m)
+        return;
+    auto fr = [&](void *p) {
+        if (p)
+            cudaFree(p);
+    };
+    fr(m->f64);
+    for (int l = 0; l < m->nlev; ++l) {
+        fr(m->B[l]);
+        fr(m->e[l]);
+        fr(m->etmp[l]);
+        fr(m->f[l]);
+        fr(m->e0[l]);
+    }
+    *held -= m->bytes;
+    delete m;
+}
+
+int alloc_mixed(int N, size_t budget, size_t *held, MixedHier **out, std::string *err)
+{
+    const size_t need = mixed_bytes(N);
+    if (budget && *held + need > budget) {
+        *err = "scratch would exceed the context's HBM budget";
+        return MG5_E_OOM;
+    }
+    MixedHier *m = new MixedHier();
+    m->N = N;
+    m->nlev = levels_of(N, m->n);
+    m->bytes = need;
+    *held += need;
+    cudaError_t e = cudaMalloc((void **)&m->f64, (size_t)N * N * N * sizeof(double));
+    for (int l = 0; l < m->nlev && e == cudaSuccess; ++l) {
+        const size_t b = (size_t)m->n[l] * m->n[l] * m->n[l] * sizeof(float);
+        e = cudaMalloc((void **)&m->B[l], b);
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&m->e[l], b);
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&m->etmp[l], b);
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&m->f[l], b);
+        if (e == cudaSuccess && l > 0)
+            e = cudaMalloc((void **)&m->e0[l], b);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        free_mixed(m, held);
+        return e == cudaErrorMemoryAllocation ? MG5_E_OOM : MG5_E_CUDA;
+    }
+    *out = m;
+    return MG5_OK;
+}
+
+int solve_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const mg5_params *p,
+                double *phi, mg5_info *info, cudaStream_t st, std::string *err)
+{
+#define CKM(call)                                                           \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) {                                            \
+            *err = std::string(#call) + ": " + cudaGetErrorString(e_);      \
+            return MG5_E_CUDA;                                              \
+        }                                                                   \
+    } while (0)
+    const int N = h->N;
+    const long long n3 = (long long)N * N * N;
+    RunMix R{h, sh, p, st, err, {}, 0};
+    for (int l = 0; l < h->nlev; ++l)
+        R.hl[l] = p->h * (double)(1 << l);
+    const int inner = p->inner_cycles > 0 ? p->inner_cycles : 3;
+    CKM(cudaMemsetAsync(sh.ls, 0, sizeof(LevelScal) * kScalSlots, st));
+    CKM(cudaMemsetAsync(sh.cnt, 0, sizeof(SolveCounters), st));
+    int nb = 0;
+    CKM(launch_scale(delta, p->s, h->f64, n3, sh.partials, &nb, st));
+    CKM(launch_finalize(sh.partials, nb, (double)n3, sh.ls, FIN_FNORM, st));
+    const CoefT<double> cf64 = make_coef<double>(p->h, p->alpha);
+    int grid = blocks_for(n3);
+    if (grid > kMaxPartials)
+        grid = kMaxPartials;
+    int status = MG5_E_NOT_CONVERGED;
+    double best = INFINITY;
+    int outer = 0, inner_total = 0;
+    for (;; ++outer) {
+        k_resid64_mixed<<<grid, kBlock, 0, st>>>(phi, h->f64, &sh.ls[0].c, N, cf64, h->f[0], h->B[0],
+                                                  sh.partials);
+        count_launch(1);
+        CKM(cudaGetLastError());
+        CKM(launch_finalize(sh.partials, grid, (double)n3, sh.ls, FIN_STATS, st));
+        CKM(cudaMemcpyAsync(sh.h_rel, &sh.ls[0].rel, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CKM(cudaStreamSynchronize(st));
+        const double rel = *sh.h_rel;
+        if (info) {
+            if (outer < 64) {
+                info->history[outer] = rel;
+                info->n_history = outer + 1;
+            }
+            info->rel_residual = rel;
+        }
+        if (!std::isfinite(rel)) {
+            status = MG5_E_NONFINITE;
+            break;
+        }
+        if (rel <= p->tol) {
+            status = MG5_OK;
+            break;
+        }
+        best = std::min(best, rel);
+        if (outer >= 3 && rel > 10.0 * best) {
+            status = MG5_E_DIVERGED;
+            break;
+        }
+        if (outer >= p->max_cycles) {
+            status = MG5_E_NOT_CONVERGED;
+            break;
+        }
+        for (int l = 1; l < h->nlev; ++l)
+            CKM(launch_restrict<float>(h->B[l - 1], h->n[l - 1], h->B[l], st));
+        CKM(cudaMemsetAsync(h->e[0], 0, n3 * sizeof(float), st));
+        k_scal<<<1, 1, 0, st>>>(sh.ls, R.ls(0), 1);  // inner c = -m
+        count_launch(1);
+        CKM(cudaGetLastError());
+        for (int it = 0; it < inner; ++it) {
+            if (int rc = R.vcycle0())
+                return rc;
+            ++inner_total;
+        }
+        k_update_mixed<<<blocks_for(n3), kBlock, 0, st>>>(phi, h->e[0], n3);
+        count_launch(1);
+        CKM(cudaGetLastError());
+        k_scal<<<1, 1, 0, st>>>(sh.ls, R.ls(0), 2);  // c += c_e
+        count_launch(1);
+        CKM(cudaGetLastError());
+    }
+    // report the projected c of the returned phi
+    k_scal<<<1, 1, 0, st>>>(sh.ls, sh.ls, 0);
+    count_launch(1);
+    CKM(cudaGetLastError());
+    CKM(launch_sum(phi, n3, sh.partials, &nb, st));
+    CKM(launch_finalize(sh.partials, nb, (double)n3, sh.ls, FIN_MEAN, st));
+    CKM(launch_sub_mean(phi, n3, &sh.ls[0].mean, st));
+    if (info) {
+        info->cycles = inner_total;
+        info->outer_iters = outer;
+        info->cell_updates = R.cu;
+        info->levels = h->nlev;
+        info->coarsest_n = h->n[h->nlev - 1];
+    }
+    return status;
+#undef CKM
+}
+
+}  // namespace mg5

@@ -1,0 +1,99 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol
+include/mg5.h declares, and its host-only entry points behave."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    return ctypes.CDLL(os.path.join(ROOT, "paper_1511_08200_gb300", "libmg5.so"))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(mg5_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    d = _declared()
+    for must in ("mg5_solve_fifth_force", "mg5_refine_interpolate", "mg5_relax_patch", "mg5_force",
+                 "mg5_create", "mg5_destroy", "mg5_ndgp_coefficients"):
+        assert must in d
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_entry_points(lib):
+    lib.mg5_version.restype = ctypes.c_int
+    assert lib.mg5_version() >= 100
+    lib.mg5_status_string.restype = ctypes.c_char_p
+    lib.mg5_status_string.argtypes = [ctypes.c_int]
+    assert lib.mg5_status_string(0) == b"ok"
+    assert b"invalid" in lib.mg5_status_string(-1)
+
+
+def test_coefficients_match_oracle(lib):
+    import oracle
+    f = lib.mg5_ndgp_coefficients
+    f.argtypes = [ctypes.c_double] * 3 + [ctypes.c_void_p] * 3
+    f.restype = ctypes.c_int
+    for a, om, rc in [(1.0, 0.3, 1.0), (0.5, 0.269, 1.0), (0.25, 0.3, 3.0)]:
+        b, al, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        assert f(a, om, rc, ctypes.byref(b), ctypes.byref(al), ctypes.byref(s)) == 0
+        ob, oal, os_ = oracle.ndgp_coefficients(a, om, rc)
+        assert b.value == pytest.approx(ob, rel=1e-14)
+        assert al.value == pytest.approx(oal, rel=1e-14)
+        assert s.value == pytest.approx(os_, rel=1e-14)
+    b = ctypes.c_double()
+    assert f(0.0, 0.3, 1.0, ctypes.byref(b), None, None) == -1
+    assert f(1.0, 1.5, 1.0, ctypes.byref(b), None, None) == -1
+
+
+def test_workspace_bytes_and_size_rules(lib):
+    f = lib.mg5_workspace_bytes
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    out = ctypes.c_size_t()
+    assert f(32, 0, ctypes.byref(out)) == 0
+    # finest: tmp + f; coarse 16, 8, 4: v, tmp, f, v0
+    assert out.value == 8 * (2 * 32 ** 3 + 4 * (16 ** 3 + 8 ** 3 + 4 ** 3))
+    assert f(32, 1, ctypes.byref(out)) == 0 and out.value > 0
+    assert f(31, 0, ctypes.byref(out)) == -1          # odd
+    assert f(2, 0, ctypes.byref(out)) == -1           # too small
+    assert f(2 * 33, 0, ctypes.byref(out)) == -1      # coarsest 66 > 32
+    assert f(80, 0, ctypes.byref(out)) == 0           # 80 -> 40 -> 20 -> 10
+
+
+def test_context_without_device_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib.mg5_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t]
+    lib.mg5_create.restype = ctypes.c_int
+    h = ctypes.c_void_p()
+    rc = lib.mg5_create(ctypes.byref(h), 0, 0)
+    assert rc in (-1, -3) and not h.value
+
+
+def test_binding_imports_and_names(lib):
+    import paper_1511_08200_gb300 as mg
+    for name in ("solve_fifth_force", "refine_interpolate", "relax_patch", "force"):
+        assert hasattr(mg.Context, name)
+    p = mg.default_params(alpha=1.0, s=2.0, h=0.5)
+    assert (p.nu1, p.nu2, p.tol, p.precision) == (2, 2, 1e-10, mg.FP64)
+    assert mg.workspace_bytes(64, "mixed") > 0

@@ -1,0 +1,217 @@
+"""Solve-level parity: mg5_solve_fifth_force (FP64 and mixed), the force, the
+coarse->fine interpolation and the patch relaxation against the FP64 oracle.
+
+Bars (from the specification of the hot path): FP64 phi and force within
+relative L2 1e-10 of the oracle's converged discrete solution; mixed
+precision within 1e-6.  A residual tolerance of 1e-10 leaves phi about
+1.5e-10 from the exact discrete solution (the error / residual ratio of the
+V-cycle's last smooth modes), so the 1e-10 phi checks solve to 1e-12; the
+1e-10 runs are checked against the bound they imply.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+from tests.gpu_common import ctx_fixture, dev, host, nominal, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = ctx_fixture()
+    yield c
+    c.close()
+
+
+def _mg():
+    import paper_1511_08200_gb300 as mg
+    return mg
+
+
+def _solve(ctx, delta, alpha, s, h, tol, precision="fp64", grad=True, **kw):
+    import torch
+    mg = _mg()
+    p = mg.default_params(alpha=alpha, s=s, h=h, tol=tol, precision=precision, **kw)
+    d = dev(delta)
+    g = torch.empty((3,) + delta.shape, dtype=torch.float64, device="cuda") if grad else None
+    phi, g, info = ctx.solve_fifth_force(d, p, grad=g)
+    return host(phi), (host(g) if grad else None), info
+
+
+@pytest.mark.parametrize("n,sigma,seed", [(8, 1.0, 1), (16, 1.0, 2), (32, 1.0, 1), (48, 1.5, 3),
+                                          (64, 1.5, 4), (80, 1.0, 5)])
+def test_fp64_solve_matches_oracle(ctx, n, sigma, seed):
+    alpha, s, h = nominal()
+    delta = workload.lognormal_delta(n, sigma, seed)
+    phi, g, info = _solve(ctx, delta, alpha, s, h, 1e-12)
+    ref, rinfo = oracle.solve(delta, alpha, s, h, tol=1e-13)
+    assert info.status == 0, info
+    assert rel_l2(phi, ref) <= 1e-10
+    assert rel_l2(g, oracle.force(ref, h)) <= 1e-10
+    assert info.compat_c == pytest.approx(rinfo.compat_c, rel=1e-8, abs=1e-12 * abs(s))
+    assert info.levels == rinfo.levels and info.coarsest_n == rinfo.coarsest_n
+    assert abs(phi.mean()) <= 1e-14 * np.abs(phi).max()
+
+
+def test_fp64_config_32_tol_1e10(ctx):
+    """The 32^3 sigma = 1 workload at the stated tolerance: the oracle, recomputing
+    the residual of the GPU's phi, finds it below 1e-10; phi and the force lie
+    within the bound that residual implies, and the cycle count is the oracle's."""
+    alpha, s, h = nominal()
+    delta = workload.lognormal_delta(32, 1.0, 1)
+    phi, g, info = _solve(ctx, delta, alpha, s, h, 1e-10)
+    ref_tight, _ = oracle.solve(delta, alpha, s, h, tol=1e-13)
+    ref_same, rinfo = oracle.solve(delta, alpha, s, h, tol=1e-10)
+    r = oracle.residual(phi, s * delta, info.compat_c, h, alpha)
+    assert np.linalg.norm(r) / np.linalg.norm(s * delta) <= 1e-10
+    assert info.cycles == rinfo.cycles
+    assert rel_l2(phi, ref_same) <= 1e-12        # same algorithm, same stopping point
+    assert rel_l2(phi, ref_tight) <= 5e-10
+    assert rel_l2(g, oracle.force(ref_tight, h)) <= 5e-10
+
+
+def test_fp64_full_size_128(ctx):
+    """The 128^3 sigma = 1.5 coarse grid of the refinement workload, element by element."""
+    alpha, s, h = nominal()
+    coarse, patch, o = workload.patch_workload(256, 1.5, 2, 32)
+    h2 = 2 * (250.0 / 512)
+    phi, g, info = _solve(ctx, coarse, alpha, s, h2, 1e-12)
+    ref, _ = oracle.solve(coarse, alpha, s, h2, tol=1e-13)
+    assert info.status == 0
+    assert rel_l2(phi, ref) <= 1e-10
+    assert rel_l2(g, oracle.force(ref, h2)) <= 1e-10
+
+
+def test_linear_limit_alpha_zero(ctx):
+    alpha, s, h = 0.0, 1.0, 1.0
+    delta = workload.lognormal_delta(32, 1.0, 9)
+    phi, _, info = _solve(ctx, delta, alpha, s, h, 1e-12, grad=False)
+    ref, _ = oracle.solve(delta, alpha, s, h, tol=1e-13)
+    assert rel_l2(phi, ref) <= 1e-10
+    assert abs(info.compat_c) < 1e-13
+
+
+@pytest.mark.parametrize("n,sigma", [(32, 1.0), (64, 2.0), (96, 2.0)])
+def test_mixed_matches_fp64_oracle(ctx, n, sigma):
+    alpha, s, h = nominal()
+    delta = workload.lognormal_delta(n, sigma, 3)
+    phi, g, info = _solve(ctx, delta, alpha, s, h, 1e-8, precision="mixed")
+    ref, _ = oracle.solve(delta, alpha, s, h, tol=1e-13)
+    assert info.status == 0, info
+    assert info.rel_residual <= 1e-8
+    r = oracle.residual(phi, s * delta, info.compat_c, h, alpha)
+    assert np.linalg.norm(r) / np.linalg.norm(s * delta) <= 1e-8
+    assert rel_l2(phi, ref) <= 1e-6
+    assert rel_l2(g, oracle.force(ref, h)) <= 1e-6
+
+
+def test_warm_start_converges_at_once(ctx):
+    import torch
+    mg = _mg()
+    alpha, s, h = nominal()
+    delta = workload.lognormal_delta(16, 1.0, 4)
+    p = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-10)
+    d = dev(delta)
+    phi, _, info = ctx.solve_fifth_force(d, p)
+    phi2, _, info2 = ctx.solve_fifth_force(d, p, phi=phi.clone(), warm=True)
+    assert info2.cycles == 0 and info2.status == 0
+    assert torch.allclose(phi2, phi, rtol=0, atol=1e-12 * float(phi.abs().max()))
+
+
+def test_host_io_equals_device_path(ctx):
+    mg = _mg()
+    alpha, s, h = nominal()
+    delta = workload.lognormal_delta(32, 1.0, 6)
+    p = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-10)
+    phi_d, _, _ = ctx.solve_fifth_force(dev(delta), p)
+    phi_h = np.zeros_like(delta)
+    grad_h = np.zeros((3,) + delta.shape)
+    ctx.solve_fifth_force_host(delta, p, phi=phi_h, grad=grad_h)
+    assert np.array_equal(phi_h, host(phi_d))
+    assert rel_l2(grad_h, oracle.force(phi_h, h)) < 1e-13
+
+
+def test_status_codes(ctx):
+    import torch
+    mg = _mg()
+    alpha, s, h = nominal()
+    p = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-10)
+    d = dev(workload.lognormal_delta(16, 1.0, 1))
+    # not converged within the cap: phi is the last iterate, status reported
+    q = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-14, max_cycles=2)
+    _, _, info = ctx.solve_fifth_force(d, q, raise_on_status=False)
+    assert info.status == mg.E_NOT_CONVERGED and info.cycles == 2
+    # non-finite input
+    bad = d.clone()
+    bad[3, 4, 5] = float("nan")
+    _, _, info = ctx.solve_fifth_force(bad, p, raise_on_status=False)
+    assert info.status == mg.E_NONFINITE
+    # odd size and too-large coarsest grid
+    for n in (15, 66):
+        with pytest.raises(mg.MG5Error) as e:
+            ctx.solve_fifth_force(torch.zeros((n,) * 3, dtype=torch.float64, device="cuda"), p)
+        assert e.value.code == mg.E_ARG
+    # the context is still usable
+    _, _, info = ctx.solve_fifth_force(d, p)
+    assert info.status == 0
+
+
+def test_budget_is_enforced():
+    import torch
+    mg = _mg()
+    alpha, s, h = nominal()
+    small = mg.Context(0, hbm_budget_bytes=1 << 20)
+    p = mg.default_params(alpha=alpha, s=s, h=h)
+    with pytest.raises(mg.MG5Error) as e:
+        small.solve_fifth_force(torch.zeros((64,) * 3, dtype=torch.float64, device="cuda"), p)
+    assert e.value.code == mg.E_OOM
+    assert small.bytes_held() <= 1 << 20
+    small.close()
+
+
+def test_zero_source_gives_zero(ctx):
+    import torch
+    mg = _mg()
+    p = mg.default_params(alpha=0.1, s=1.0, h=1.0)
+    phi, _, info = ctx.solve_fifth_force(torch.zeros((8,) * 3, dtype=torch.float64, device="cuda"), p)
+    assert info.status == 0 and info.cycles == 0
+    assert float(phi.abs().max()) == 0.0
+
+
+def _patch_case(nc=32, pn=8, sigma=1.5, seed=7):
+    fine = workload.lognormal_delta(2 * nc, sigma, seed)
+    coarse = workload.block_mean(fine, 2)
+    o = workload.densest_window(coarse, pn)
+    idx = [(2 * o[a] + np.arange(2 * pn)) % (2 * nc) for a in range(3)]
+    return coarse, np.ascontiguousarray(fine[np.ix_(*idx)]), o
+
+
+def test_refine_and_relax_patch_match_oracle(ctx):
+    """Truncated (interpolated) vs relaxed fine phi on a 16^3 patch of a 32^3 grid."""
+    mg = _mg()
+    alpha, s, h = nominal()
+    coarse, dpatch, o = _patch_case()
+    pn = (8, 8, 8)
+    phic, _, info = _solve(ctx, coarse, alpha, s, h, 1e-12, grad=False)
+    ref_c, rinfo = oracle.solve(coarse, alpha, s, h, tol=1e-13)
+    box = ctx.refine_interpolate(dev(phic), o, pn, 1)
+    box_ref = oracle.refine_interpolate(ref_c, o, pn, 1)
+    assert rel_l2(host(box), box_ref) <= 1e-10
+    hf = h / 2
+    p = mg.default_params(alpha=alpha, s=s, h=hf, tol=1e-12, max_cycles=100000)
+    relaxed, pinfo = ctx.relax_patch(dev(dpatch), p, info.compat_c, box.clone())
+    ref_relaxed, nsw, rel = oracle.relax_patch(dpatch, box_ref, alpha, s, hf, rinfo.compat_c,
+                                               tol=1e-12)
+    assert pinfo.status == 0 and pinfo.rel_residual <= 1e-12
+    got = host(relaxed)
+    assert rel_l2(got, ref_relaxed) <= 1e-10
+    # ghosts untouched
+    assert np.array_equal(got[0], host(box)[0]) and np.array_equal(got[:, :, -1], host(box)[:, :, -1])
+    # forces on the patch interior: truncated (interpolated) vs full (relaxed)
+    g_tr = host(ctx.force(box, hf, ghost=1, periodic=False))
+    g_full = host(ctx.force(relaxed, hf, ghost=1, periodic=False))
+    assert rel_l2(g_tr, oracle.force(box_ref, hf, ghost=1, periodic=False)) <= 1e-10
+    assert rel_l2(g_full, oracle.force(ref_relaxed, hf, ghost=1, periodic=False)) <= 1e-10
+    assert 0 < rel_l2(g_tr, g_full) < 1.0

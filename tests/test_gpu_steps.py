@@ -1,0 +1,122 @@
+"""Per-kernel parity: each step of the hot path on the GPU (through the C ABI)
+against the oracle's step with the same semantics, FP64.
+
+Tolerances: the GPU and the oracle evaluate the same formula in FP64 with a
+different summation order, so per-cell results agree to a few ulps of the
+largest term; 1e-13 relative (max norm) leaves room for that and catches any
+dropped term, sign or index.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+from tests.gpu_common import ctx_fixture, dev, host, nominal
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [4, 8, 16, 34, 48]   # 34: not a multiple of the warp / tile widths
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = ctx_fixture()
+    yield c
+    c.close()
+
+
+def _field(n, seed):
+    return workload.smooth_periodic_field(n, 1e-6, seed) + 2e-7 * workload.lognormal_delta(n, 1.5, seed + 7)
+
+
+def _maxrel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_operator(ctx, n):
+    alpha, s, h = nominal()
+    phi = _field(n, 1)
+    got = host(ctx.step_operator(dev(phi), h, alpha))
+    assert _maxrel(got, oracle.operator(phi, h, alpha)) < 1e-13
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_residual(ctx, n):
+    alpha, s, h = nominal()
+    phi = _field(n, 2)
+    f = s * workload.lognormal_delta(n, 1.0, 3)
+    c = 3e-11
+    got = host(ctx.step_residual(dev(phi), dev(f), c, h, alpha))
+    ref = oracle.residual(phi, f, c, h, alpha)
+    assert np.abs(got - ref).max() < 1e-13 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("scale", [1.0, 30.0])
+def test_sweep(ctx, n, scale):
+    alpha, s, h = nominal()
+    phi = _field(n, 4)
+    f = s * scale * workload.lognormal_delta(n, 1.0, 5)
+    c = 1e-10
+    got = host(ctx.step_sweep(dev(phi), dev(f), c, h, alpha))
+    ref = oracle.sweep(phi, f, c, h, alpha)
+    assert _maxrel(got, ref) < 1e-13
+
+
+def test_sweep_repeated_matches(ctx):
+    """Ten sweeps in a row stay on the oracle's trajectory."""
+    alpha, s, h = nominal()
+    n = 16
+    phi = _field(n, 6)
+    f = s * workload.lognormal_delta(n, 1.0, 8)
+    g, r = dev(phi), phi
+    for _ in range(10):
+        g = ctx.step_sweep(g, dev(f), 0.0, h, alpha)
+        r = oracle.sweep(r, f, 0.0, h, alpha)
+    assert _maxrel(host(g), r) < 1e-12
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 34, 48])
+def test_restrict(ctx, n):
+    x = _field(n, 9)
+    got = host(ctx.step_restrict(dev(x)))
+    assert _maxrel(got, oracle.restrict(x)) < 1e-15
+
+
+@pytest.mark.parametrize("nc", [2, 4, 8, 17, 24])
+def test_prolong_add(ctx, nc):
+    c = _field(nc, 10)
+    f = _field(2 * nc, 11)
+    got = host(ctx.step_prolong_add(dev(c), dev(f)))
+    assert _maxrel(got, oracle.prolong_add(c, f)) < 1e-14
+
+
+@pytest.mark.parametrize("n", [8, 16, 34])
+def test_force_periodic(ctx, n):
+    h = 0.37
+    phi = _field(n, 12)
+    got = host(ctx.force(dev(phi), h))
+    assert _maxrel(got, oracle.force(phi, h)) < 1e-13
+
+
+@pytest.mark.parametrize("dims,g", [((10, 12, 14), 1), ((9, 8, 7), 2), ((66, 66, 66), 1)])
+def test_force_box(ctx, dims, g):
+    h = 0.25
+    rng = np.random.default_rng(1)
+    phi = rng.standard_normal(dims)
+    got = host(ctx.force(dev(phi), h, ghost=g, periodic=False))
+    assert _maxrel(got, oracle.force(phi, h, ghost=g, periodic=False)) < 1e-14
+
+
+@pytest.mark.parametrize("nc,o,pn,g", [
+    (16, (0, 0, 0), (16, 16, 16), 0),
+    (16, (3, 5, 7), (4, 6, 8), 1),
+    (16, (14, 15, 0), (5, 3, 4), 1),      # wraps across the periodic boundary
+    (12, (11, 0, 6), (12, 2, 3), 2),
+    (32, (20, 9, 31), (8, 8, 8), 1),
+])
+def test_refine_interpolate(ctx, nc, o, pn, g):
+    phic = _field(nc, 13)
+    got = host(ctx.refine_interpolate(dev(phic), o, pn, g))
+    assert _maxrel(got, oracle.refine_interpolate(phic, o, pn, g)) < 1e-15
