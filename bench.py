@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of the nDGP fifth-force hot path on one GB300 (or N replicas).
+
+One step is one pass of the whole path over the refinement workload:
+  coefficients (Eq. beta) -> FP64 FAS solve of the periodic 128^3 domain grid
+  to relative residual 1e-10 + force (Sec. 3.1) -> coarse->fine interpolation
+  onto the 2x-refined 64^3 patch over the densest 32^3 coarse cells + force
+  on it (the truncated fine level, Sec. 3.2) -> relaxation of the same patch
+  with the interpolated Dirichlet ghosts + force (the untruncated level) ->
+  mixed-precision (FP64 defect correction around FP32 V-cycles) solve of the
+  domain grid to 1e-8 + force.
+The metric is cell-updates/s over the step (one cell relaxed in one full
+red+black sweep, on every grid), with each phase's time-to-tolerance beside it.
+
+Inputs are synthetic (seeded lognormal Gaussian random fields standing in for
+the paper's N-body densities); they are resident in HBM before the timed
+region.  The L2 cache (129 MB) is flushed between timed steps by writing a
+512 MB buffer.  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "cell-updates/s & V-cycle time-to-tol (FP64 vs mixed/batched), % HBM peak; p50/p99"
+UNIT = "cell-updates/s"
+L_BOX = 250.0                  # Mpc/h, the paper's box (Sec. 4.1)
+N_FINE, SIGMA, SEED, PN = 256, 1.5, 2, 32
+N_COARSE = N_FINE // 2
+H_COARSE = L_BOX / N_COARSE    # the 128^3 grid of a 256^3-cell field: 1.95 Mpc/h
+TOL64, TOLMIX = 1e-10, 1e-8
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop
+
+# algorithmic work per cell of each kernel class: (bound, bytes, flops)
+#   sweep: read phi + f, write phi (the full red+black sweep of one cell);
+#   ~42 FP64 flops (FMA = 2) + 1 sqrt + 1 div per cell update
+WORK = {
+    "sweep64": ("alu", 24.0, 42.0),
+    "patch_sweep64": ("alu", 24.0, 42.0),
+    "resid_restrict64": ("alu", 18.0, 38.0),
+    "sweep32": ("hbm", 16.0, 60.0),          # correction form: read e, B, f; write e
+    "resid_restrict32": ("hbm", 12.5, 60.0),
+    "resid64_mixed": ("alu", 24.0, 36.0),     # read phi64, f64; write r32, B32
+    "update_mixed": ("hbm", 20.0, 1.0),
+    "force64": ("hbm", 32.0, 6.0),
+    "refine64": ("hbm", 9.0, 25.0),
+    "prolong64": ("hbm", 18.0, 20.0),
+    "prolong32": ("hbm", 9.0, 20.0),
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_inputs():
+    import workload
+    coarse, patch, origin = workload.patch_workload(N_FINE, SIGMA, SEED, PN)
+    return coarse, patch, origin
+
+
+# ---------------------------------------------------------------- our arm
+
+class Step:
+    def __init__(self, mg, ctx, torch, coarse, patch, origin, dev):
+        self.mg, self.ctx, self.torch = mg, ctx, torch
+        f64 = torch.float64
+        self.beta, self.alpha, self.s = mg.ndgp_coefficients(1.0, 0.3, 1.0)
+        self.origin = origin
+        self.d_c = torch.from_numpy(coarse).to(dev)
+        self.d_p = torch.from_numpy(patch).to(dev)
+        n, pf = N_COARSE, 2 * PN
+        self.phi = torch.zeros((n,) * 3, dtype=f64, device=dev)
+        self.grad = torch.empty((3,) + (n,) * 3, dtype=f64, device=dev)
+        self.phi_m = torch.zeros_like(self.phi)
+        self.grad_m = torch.empty_like(self.grad)
+        self.box = torch.empty((pf + 2,) * 3, dtype=f64, device=dev)
+        self.box_full = torch.empty_like(self.box)
+        self.g_tr = torch.empty((3,) + (pf,) * 3, dtype=f64, device=dev)
+        self.g_full = torch.empty_like(self.g_tr)
+        self.p64 = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE, tol=TOL64)
+        self.pmix = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE, tol=TOLMIX,
+                                      precision="mixed")
+        self.ppatch = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE / 2, tol=TOL64,
+                                        max_cycles=100000)
+
+    def run(self, host_io=None):
+        """One step; returns (cell updates, per-phase ms, infos)."""
+        torch, ctx = self.torch, self.ctx
+        st = torch.cuda.current_stream()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        # a1: coefficients of Eq. (beta) / Eq. (eomvarphi) at a = 1
+        self.beta, self.alpha, self.s = self.mg.ndgp_coefficients(1.0, 0.3, 1.0)
+        ev[0].record(st)
+        if host_io is None:
+            _, _, i64 = ctx.solve_fifth_force(self.d_c, self.p64, phi=self.phi, grad=self.grad)
+        else:
+            _, _, i64 = ctx.solve_fifth_force_host(host_io["delta"], self.p64, phi=host_io["phi"],
+                                                   grad=host_io["grad"])
+            self.phi.copy_(host_io["phi"], non_blocking=True)
+            self.d_p.copy_(host_io["patch"], non_blocking=True)
+        ev[1].record(st)
+        ctx.refine_interpolate(self.phi, self.origin, (PN, PN, PN), 1, out=self.box)
+        ctx.force(self.box, H_COARSE / 2, ghost=1, periodic=False, grad=self.g_tr)
+        ev[2].record(st)
+        self.box_full.copy_(self.box)
+        _, ip = ctx.relax_patch(self.d_p, self.ppatch, i64.compat_c, self.box_full)
+        ctx.force(self.box_full, H_COARSE / 2, ghost=1, periodic=False, grad=self.g_full)
+        ev[3].record(st)
+        _, _, im = ctx.solve_fifth_force(self.d_c, self.pmix, phi=self.phi_m, grad=self.grad_m)
+        ev[4].record(st)
+        if host_io is not None:
+            host_io["g_tr"].copy_(self.g_tr, non_blocking=True)
+            host_io["g_full"].copy_(self.g_full, non_blocking=True)
+            host_io["phi_m"].copy_(self.phi_m, non_blocking=True)
+            st.synchronize()
+        ev[4].synchronize()
+        ms = {"solve_fp64": ev[0].elapsed_time(ev[1]), "interpolate": ev[1].elapsed_time(ev[2]),
+              "relax_patch": ev[2].elapsed_time(ev[3]), "solve_mixed": ev[3].elapsed_time(ev[4])}
+        cu = i64.cell_updates + ip.cell_updates + im.cell_updates
+        return cu, ms, (i64, ip, im)
+
+
+def run_ours(args):
+    import torch
+    import paper_1511_08200_gb300 as mg
+    ws, rank, local = _dist()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    coarse, patch, origin = make_inputs()
+    ctx = mg.Context(local)
+    step = Step(mg, ctx, torch, coarse, patch, origin, dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        step.run()
+    torch.cuda.synchronize()
+    launches0 = mg.kernel_launches()
+    ctx.profile_enable(True)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    tot_ms, tot_cu, phase = 0.0, 0, {}
+    infos = None
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cu, ms, infos = step.run()
+        e1.record()
+        e1.synchronize()
+        tot_ms += e0.elapsed_time(e1)
+        tot_cu += cu
+        for k, v in ms.items():
+            phase[k] = phase.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    launches = mg.kernel_launches() - launches0
+    t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+    c = torch.tensor([float(tot_cu)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(c, op=torch.distributed.ReduceOp.SUM)
+    max_ms, all_cu = float(t.item()), float(c.item())
+
+    # e2e: the same step through the C ABI with HOST buffers (pinned), copies inside
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    hio = {"delta": pin(coarse), "patch": pin(patch),
+           "phi": torch.zeros(step.phi.shape, dtype=torch.float64).pin_memory(),
+           "grad": torch.zeros(step.grad.shape, dtype=torch.float64).pin_memory(),
+           "g_tr": torch.zeros(step.g_tr.shape, dtype=torch.float64).pin_memory(),
+           "g_full": torch.zeros(step.g_full.shape, dtype=torch.float64).pin_memory(),
+           "phi_m": torch.zeros(step.phi.shape, dtype=torch.float64).pin_memory()}
+    e2e_ms, e2e_cu = 0.0, 0
+    if not args.no_e2e:
+        step.run(hio)
+    for _ in range(0 if args.no_e2e else args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cu, _, _ = step.run(hio)
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_cu += cu
+    h2d = (hio["delta"].numel() + hio["patch"].numel()) * 8
+    d2h = (hio["phi"].numel() + hio["grad"].numel() + hio["g_tr"].numel() + hio["g_full"].numel()
+           + hio["phi_m"].numel()) * 8
+
+    if rank != 0:
+        return
+    i64, ip, im = infos
+    # truncation error (Eq. errors2 context): interpolated vs relaxed fine phi and force
+    box_tr, box_full = step.box[1:-1, 1:-1, 1:-1], step.box_full[1:-1, 1:-1, 1:-1]
+    dphi = float(torch.linalg.vector_norm(box_tr - box_full) / torch.linalg.vector_norm(box_full))
+    dg = float(torch.linalg.vector_norm(step.g_tr - step.g_full) / torch.linalg.vector_norm(step.g_full))
+    mixed_vs64 = float(torch.linalg.vector_norm(step.phi_m - step.phi) / torch.linalg.vector_norm(step.phi))
+    peaks = _peaks()
+    roof = roofline(prof, peaks, args.steps)
+    value = all_cu / (max_ms / 1e3)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "refine128: periodic 128^3 nDGP FP64 solve to 1e-10 (lognormal GRF "
+                               "sigma=1.5 at 256^3, seed 2, block-mean to 128^3, h=1.95 Mpc/h) + "
+                               "64^3 fine patch over the densest 32^3 cells (interpolated vs relaxed "
+                               "to 1e-10) + mixed-precision solve of the 128^3 grid to 1e-8",
+                   "n": N_COARSE, "patch": 2 * PN, "tol_fp64": TOL64, "tol_mixed": TOLMIX,
+                   "eps_alpha_s": step.alpha * step.s, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "time_to_tol_ms": {k: v / args.steps for k, v in phase.items()},
+        "solve": {"fp64_cycles": i64.cycles, "fp64_rel_residual": i64.rel_residual,
+                  "mixed_outer": im.outer_iters, "mixed_inner_cycles": im.cycles,
+                  "mixed_rel_residual": im.rel_residual, "patch_sweeps": ip.cycles,
+                  "mixed_vs_fp64_rel_l2": mixed_vs64},
+        "truncation": {"dphi_rel_l2": dphi, "dgrad_rel_l2": dg,
+                       "relax_over_interp_ms": phase.get("relax_patch", 0) / max(phase.get("interpolate", 1e-9), 1e-9)},
+        "roofline": roof,
+        "kernels": {k: {"ms": v[0] / args.steps, "launches": v[1] // args.steps}
+                    for k, v in prof.items() if v[1] > 0},
+        "clocks": clk,
+        "e2e": ({"value": e2e_cu / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                 "d2h_bytes_per_step": d2h} if e2e_ms > 0 else None),
+        "gpu_launches": launches,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(coarse, patch, origin, budget_s=args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+
+
+def roofline(prof: dict, peaks: dict, steps: int) -> dict:
+    """The kernel class with the most device time: algorithmic work / its event-timed duration."""
+    top = max(((k, v) for k, v in prof.items() if k in WORK and v[1] > 0), key=lambda kv: kv[1][0])
+    name, (ms, calls, cells) = top
+    bound, bpc, fpc = WORK[name]
+    sec = ms / 1e3
+    if bound == "hbm":
+        achieved = bpc * cells / sec / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        unit = "GB/s"
+    else:
+        achieved = fpc * cells / sec / 1e12
+        peak = FP64_PEAK_TFLOPS
+        unit = "TFLOP/s"
+    return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": None,
+            "avg_launch_ms": ms / max(calls, 1), "launches_per_step": calls / steps,
+            "alg_bytes_per_cell": bpc, "alg_flops_per_cell": fpc,
+            "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if bound == "hbm"
+            else "derived FP64: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (probe measured 1.195 TFLOP/s)"}
+
+
+# ---------------------------------------------------------------- the oracle on host cores
+
+def cpu_baseline(coarse, patch, origin, budget_s=20.0) -> dict:
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same step."""
+    import oracle
+    beta, alpha, s = oracle.ndgp_coefficients(1.0, 0.3, 1.0)
+    oracle.build()
+    cores = os.cpu_count()
+    t0 = time.perf_counter()
+    phi, info = oracle.solve(coarse, alpha, s, H_COARSE, tol=TOL64)
+    t_solve = time.perf_counter() - t0
+    box = oracle.refine_interpolate(phi, origin, (PN, PN, PN), 1)
+    left = max(budget_s - t_solve, 1.0)
+    # bounded patch relaxation: sweeps in batches of 10 until the budget is used
+    t1 = time.perf_counter()
+    sweeps = 0
+    while time.perf_counter() - t1 < left and sweeps < 100000:
+        box, nsw, rel = oracle.relax_patch(patch, box, alpha, s, H_COARSE / 2, info.compat_c,
+                                           tol=TOL64, max_sweeps=10, check=10)
+        sweeps += nsw
+        if rel <= TOL64 or nsw == 0:
+            break
+    t_patch = time.perf_counter() - t1
+    cu = info.cell_updates + sweeps * (2 * PN) ** 3
+    return {"value": cu / (t_solve + t_patch), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "FP64 oracle solve of the 128^3 grid to 1e-10 (%d cycles, %.1f s) + %d "
+                      "Dirichlet sweeps of the 64^3 patch (%.1f s); OpenMP over %d threads"
+                      % (info.cycles, t_solve, sweeps, t_patch, cores)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    coarse, patch, origin = make_inputs()
+    per_step = max(args.cpu_seconds / 2.0, 5.0)
+    for _ in range(args.warmup and 1):
+        cpu_baseline(coarse, patch, origin, budget_s=1.0)
+    vals, cus = [], 0.0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b = cpu_baseline(coarse, patch, origin, budget_s=per_step)
+        vals.append(b)
+    wall = time.perf_counter() - t0
+    v = float(np.mean([b["value"] for b in vals]))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "refine128 (bounded sample on host cores: the FP64 oracle)",
+                      "n": N_COARSE, "patch": 2 * PN},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                            "sample": vals[0]["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mg5", choices=["mg5", "ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -201,6 +201,17 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_fine, const int pf[3],
                     const mg5_params *p, double compat_c, double *phi_fine,
                     mg5_info *info, void *stream);
 
+/* ------------------------------------------------------------ tracing
+ * Per-kernel-class device time, measured with CUDA events recorded on the
+ * launching stream around each launch (off by default).  enable() also
+ * clears the totals; read() synchronises the device, then copies up to n
+ * totals (ms) and launch counts and returns the number of classes. */
+int mg5_profile_enable(mg5_ctx *ctx, int on);
+int mg5_profile_read(mg5_ctx *ctx, double *ms, long long *calls, int n);
+/* Cells processed per class (fine-grid cells of each launch), for roofline arithmetic. */
+int mg5_profile_units(mg5_ctx *ctx, double *units, int n);
+const char *mg5_profile_name(int k);
+
 /* ------------------------------------------------------------ single steps
  * Each runs one kernel of the hot path on device buffers, for testing the
  * steps one by one.  N is the periodic side (even); c is the compatibility

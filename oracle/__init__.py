@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 from dataclasses import dataclass, field
 
@@ -32,7 +33,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mg_oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+_LIB = os.path.join(_HERE, "liboracle.%s.so" % platform.machine())
 _lib = None
 
 
@@ -114,6 +115,7 @@ class _Info(ctypes.Structure):
         ("compat_c", ctypes.c_double),
         ("phi_mean_removed", ctypes.c_double),
         ("clamped", ctypes.c_longlong),
+        ("cell_updates", ctypes.c_longlong),
         ("history", ctypes.c_double * 128),
     ]
 
@@ -128,6 +130,7 @@ class SolveInfo:
     compat_c: float
     phi_mean_removed: float
     clamped: int
+    cell_updates: int = 0
     history: list = field(default_factory=list)
 
 
@@ -201,7 +204,7 @@ def solve(delta, alpha, s, h, tol=1e-10, nu1=2, nu2=2, nu_coarse=500, max_cycles
     hist = [info.history[q] for q in range(min(info.cycles + 1, 128))]
     return phi, SolveInfo(info.status, info.cycles, info.levels, info.coarsest_n,
                           info.rel_residual, info.compat_c, info.phi_mean_removed,
-                          info.clamped, hist)
+                          info.clamped, info.cell_updates, hist)
 
 
 def force(phi, h, ghost=0, periodic=True) -> np.ndarray:

@@ -227,6 +227,7 @@ double or_cell_update(const double *phi, int n, int i, int j, int k, double h,
 void or_sweep(double *phi, const double *f, double c, int n, double h, double alpha)
 {
     size_t nc = (size_t)n * n * n;
+    g_cell_updates += (long long)nc;
     double *snap = (double *)malloc(nc * sizeof(double));
     for (int colour = 0; colour < 2; ++colour) {
         memcpy(snap, phi, nc * sizeof(double));
@@ -358,8 +359,11 @@ typedef struct {
     double compat_c;
     double phi_mean_removed;
     long long clamped;
+    long long cell_updates;   /* bookkeeping: cells relaxed, one per cell per sweep */
     double history[128];
 } or_info;
+
+static long long g_cell_updates; /* bookkeeping only, reset by or_solve */
 
 /* coarse-grid relative reduction that ends the coarsest solve */
 #define OR_COARSE_RTOL 1e-3
@@ -453,6 +457,7 @@ int or_solve(const double *delta, int n, const or_params *p, double *phi, or_inf
         lv[0].f[q] = p->s * delta[q];
     double fnorm = norm2(lv[0].f, n3);
     g_clamped = 0;
+    g_cell_updates = 0;
     memset(info, 0, sizeof(*info));
     info->levels = nlev;
     info->coarsest_n = lv[nlev - 1].n;
@@ -528,6 +533,7 @@ int or_solve(const double *delta, int n, const or_params *p, double *phi, or_inf
     info->phi_mean_removed = pm;
     info->compat_c = lv[0].c;
     info->clamped = g_clamped;
+    info->cell_updates = g_cell_updates;
     for (int l = 0; l < nlev; ++l) {
         if (l > 0)
             free(lv[l].v);

@@ -87,6 +87,10 @@ _sigs = {
     "mg5_force": ([_P, _P, _I3, _c_int, _c_double, _c_int, _P, _P], _c_int),
     "mg5_refine_interpolate": ([_P, _P, _c_int, _I3, _I3, _c_int, _P, _P], _c_int),
     "mg5_relax_patch": ([_P, _P, _I3, _P, _c_double, _P, _P, _P], _c_int),
+    "mg5_profile_enable": ([_P, _c_int], _c_int),
+    "mg5_profile_read": ([_P, _P, _P, _c_int], _c_int),
+    "mg5_profile_name": ([_c_int], ctypes.c_char_p),
+    "mg5_profile_units": ([_P, _P, _c_int], _c_int),
     "mg5_step_sweep": ([_P, _P, _P, _P, _c_double, _c_int, _c_double, _c_double, _P], _c_int),
     "mg5_step_operator": ([_P, _P, _c_int, _c_double, _c_double, _P, _P], _c_int),
     "mg5_step_residual": ([_P, _P, _P, _c_double, _c_int, _c_double, _c_double, _P, _P], _c_int),
@@ -202,6 +206,22 @@ class Context:
         if rc not in allow:
             raise MG5Error(rc, self.last_error())
         return rc
+
+    # ------------------------------------------------------------ tracing
+    def profile_enable(self, on: bool = True):
+        self._check(_lib.mg5_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        """{kernel class: (total ms, launches, cells)} from CUDA events on the launching stream."""
+        n = 32
+        ms = (_c_double * n)()
+        calls = (ctypes.c_longlong * n)()
+        units = (_c_double * n)()
+        k = _lib.mg5_profile_read(self._h, ms, calls, n)
+        if k < 0:
+            self._check(k)
+        _lib.mg5_profile_units(self._h, units, n)
+        return {_lib.mg5_profile_name(i).decode(): (ms[i], calls[i], units[i]) for i in range(k)}
 
     # ------------------------------------------------------------ hot path
     def solve_fifth_force(self, delta, params: Params, phi=None, grad=None, warm=False,

@@ -10,13 +10,14 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import platform
 import subprocess
 import sys
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-OBJ = os.path.join(PKG, "_build")
+OBJ = os.path.join(PKG, "_build", platform.machine())   # objects per host architecture
 LIB = os.path.join(PKG, "libmg5.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -59,7 +60,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
             if verbose and msg:
                 print(msg, file=sys.stderr)
     objs = [os.path.join(OBJ, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    if force or jobs or not os.path.exists(LIB):
+    if force or jobs or not os.path.exists(LIB) or _needs(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
         cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
         if verbose:

@@ -21,6 +21,7 @@
 #include "mg5.h"
 #include "mg5_kernels.cuh"
 #include "mg5_mixed.cuh"
+#include "mg5_prof.cuh"
 
 using namespace mg5;
 
@@ -87,6 +88,7 @@ struct mg5_ctx {
     double *patch = nullptr;
     size_t patch_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    Profiler prof;
 };
 
 // ------------------------------------------------------------ helpers
@@ -232,6 +234,7 @@ struct Run64 {
     int sweep(int l)
     {
         const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
+        ProfScope ps(&ctx->prof, PK_SWEEP64, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
         cudaError_t e = launch_sweep<double>(h->v[l], h->tmp[l], h->f[l], c(l), h->n[l], cf,
                                              &ctx->cnt->clamped, st);
         if (e != cudaSuccess) {
@@ -249,8 +252,11 @@ struct Run64 {
         const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
         int nb = 0;
         mg5_ctx *ctx = this->ctx;
-        CK(launch_resid_restrict<double>(h->v[l], h->f[l], c(l), h->n[l], cf, h->v[l + 1],
-                                         h->v0[l + 1], h->f[l + 1], ctx->partials, &nb, st));
+        {
+            ProfScope ps(&ctx->prof, PK_RESTRICT64, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
+            CK(launch_resid_restrict<double>(h->v[l], h->f[l], c(l), h->n[l], cf, h->v[l + 1],
+                                             h->v0[l + 1], h->f[l + 1], ctx->partials, &nb, st));
+        }
         const double n3 = (double)h->n[l] * h->n[l] * h->n[l];
         CK(launch_finalize(ctx->partials, nb, n3, ls(l), FIN_RESID, st));
         return MG5_OK;
@@ -272,6 +278,7 @@ struct Run64 {
     {
         const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
         mg5_ctx *ctx = this->ctx;
+        ProfScope ps(&ctx->prof, PK_COARSEST64, st);
         CK(launch_coarsest<double>(h->v[l], h->tmp[l], h->f[l], h->n[l], cf, c(l), p->nu_coarse,
                                    kCoarseRtol, &ctx->cnt->clamped, &ctx->cnt->coarse_sweeps, st));
         return MG5_OK;
@@ -283,15 +290,21 @@ struct Run64 {
     {
         mg5_ctx *ctx = this->ctx;
         const CoefT<double> cfc = make_coef<double>(hl[l], p->alpha);
-        CK(launch_coarse_rhs<double>(h->v[l], h->f[l], m(l - 1), c(l), h->n[l], cfc, st));
+        {
+            ProfScope ps(&ctx->prof, PK_COARSE_RHS64, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
+            CK(launch_coarse_rhs<double>(h->v[l], h->f[l], m(l - 1), c(l), h->n[l], cfc, st));
+        }
         if (l == h->nlev - 1)
             return coarsest(l);
         for (int s = 0; s < p->nu1; ++s)
             RET(sweep(l));
         RET(resid_restrict(l));
         RET(coarse_visit(l + 1));
-        CK(launch_prolong_add<double>(h->v[l + 1], h->v0[l + 1], h->n[l + 1], h->v[l], c(l),
-                                      c(l + 1), st));
+        {
+            ProfScope ps(&ctx->prof, PK_PROLONG64, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
+            CK(launch_prolong_add<double>(h->v[l + 1], h->v0[l + 1], h->n[l + 1], h->v[l], c(l),
+                                          c(l + 1), st));
+        }
         for (int s = 0; s < p->nu2; ++s)
             RET(sweep(l));
         return MG5_OK;
@@ -302,7 +315,7 @@ struct Run64 {
 
 // Plain FP64 solve on device buffers.  phi holds the initial guess.
 static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p, double *phi,
-                   mg5_info *info, cudaStream_t st)
+                   bool warm, mg5_info *info, cudaStream_t st)
 {
     Hier *h = nullptr;
     RET(get_hier(ctx, N, &h));
@@ -317,13 +330,25 @@ static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p
     CK(launch_finalize(ctx->partials, nb, (double)n3, ctx->ls, FIN_FNORM, st));
     double *caller_phi = phi;
     h->v[0] = phi;
-    // tmp[0] is the context's; v/tmp swap on every sweep
-    double *own_tmp = h->tmp[0];
+    // tmp[0] is the context's; v/tmp swap on every sweep.  Every exit path
+    // hands tmp[0] back to the hierarchy.
+    struct Restore {
+        Hier *h;
+        double *own;
+        ~Restore()
+        {
+            h->v[0] = nullptr;
+            h->tmp[0] = own;
+        }
+    } restore{h, h->tmp[0]};
     int status = MG5_E_NOT_CONVERGED;
     double best = INFINITY;
     int cyc = 0;
+    bool pre_check = warm;  // a warm start is tested (and c set) before any smoothing
     for (;; ++cyc) {
-        if (h->nlev == 1) {
+        if (pre_check) {
+            RET(R.residual_only(0));
+        } else if (h->nlev == 1) {
             RET(R.coarsest(0));
             RET(R.residual_only(0));
         } else {
@@ -353,6 +378,11 @@ static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p
             status = MG5_E_DIVERGED;
             break;
         }
+        if (pre_check) {
+            pre_check = false;
+            --cyc;   // the check of the initial guess is not a cycle
+            continue;
+        }
         if (cyc >= p->max_cycles) {
             status = MG5_E_NOT_CONVERGED;
             break;
@@ -360,15 +390,15 @@ static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p
         if (h->nlev == 1)
             continue;
         RET(R.coarse_visit(1));
-        CK(launch_prolong_add<double>(h->v[1], h->v0[1], h->n[1], h->v[0], R.c(0), R.c(1), st));
+        {
+            ProfScope ps(&ctx->prof, PK_PROLONG64, st, (double)(h->n[0]) * (h->n[0]) * (h->n[0]));
+            CK(launch_prolong_add<double>(h->v[1], h->v0[1], h->n[1], h->v[0], R.c(0), R.c(1), st));
+        }
         for (int s = 0; s < p->nu2; ++s)
             RET(R.sweep(0));
     }
     if (h->v[0] != caller_phi)
         CK(cudaMemcpyAsync(caller_phi, h->v[0], n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    // restore the hierarchy's own buffer in tmp[0]
-    h->v[0] = nullptr;
-    h->tmp[0] = own_tmp;
     // gauge: subtract mean(phi)
     CK(launch_sum(caller_phi, n3, ctx->partials, &nb, st));
     CK(launch_finalize(ctx->partials, nb, (double)n3, ctx->ls, FIN_MEAN, st));
@@ -530,6 +560,7 @@ int mg5_destroy(mg5_ctx *ctx)
         cudaEventDestroy(ctx->ev0);
     if (ctx->ev1)
         cudaEventDestroy(ctx->ev1);
+    ctx->prof.destroy();
     delete ctx;
     return MG5_OK;
 }
@@ -537,6 +568,54 @@ int mg5_destroy(mg5_ctx *ctx)
 const char *mg5_last_error(mg5_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 size_t mg5_bytes_held(mg5_ctx *ctx) { return ctx ? ctx->held : 0; }
+
+static const char *kProfNames[PK_COUNT] = {
+    "sweep64", "resid_restrict64", "coarse_rhs64", "prolong64", "coarsest64",
+    "sweep32", "resid_restrict32", "coarse_rhs32", "prolong32", "coarsest32",
+    "resid64_mixed", "update_mixed", "patch_sweep64", "patch_resid64", "force64",
+    "refine64", "reduce"};
+
+int mg5_profile_enable(mg5_ctx *ctx, int on)
+{
+    if (!ctx)
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceSynchronize());
+    ctx->prof.resolve();
+    ctx->prof.reset();
+    ctx->prof.on = on != 0;
+    return MG5_OK;
+}
+
+int mg5_profile_units(mg5_ctx *ctx, double *units, int n)
+{
+    if (!ctx || n < 0)
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceSynchronize());
+    ctx->prof.resolve();
+    for (int k = 0; k < n && k < PK_COUNT; ++k)
+        units[k] = ctx->prof.units[k];
+    return PK_COUNT;
+}
+
+int mg5_profile_read(mg5_ctx *ctx, double *ms, long long *calls, int n)
+{
+    if (!ctx || n < 0)
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceSynchronize());
+    ctx->prof.resolve();
+    for (int k = 0; k < n && k < PK_COUNT; ++k) {
+        if (ms)
+            ms[k] = ctx->prof.ms[k];
+        if (calls)
+            calls[k] = ctx->prof.calls[k];
+    }
+    return PK_COUNT;
+}
+
+const char *mg5_profile_name(int k) { return (k >= 0 && k < PK_COUNT) ? kProfNames[k] : ""; }
 
 int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p,
                           unsigned flags, double *phi, double *grad, mg5_info *info, void *stream)
@@ -570,7 +649,7 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
         CK(cudaMemsetAsync(d_phi, 0, fb, st));
     int status;
     if (p->precision == MG5_FP64) {
-        status = solve64(ctx, d_delta, N, p, d_phi, info, st);
+        status = solve64(ctx, d_delta, N, p, d_phi, (flags & MG5_WARM) != 0, info, st);
     } else {
         MixedHier *mh = nullptr;
         for (MixedHier *m : ctx->mixed)
@@ -582,13 +661,15 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
                 return rc;
             ctx->mixed.push_back(mh);
         }
-        MixedShared sh{ctx->partials, ctx->ls, ctx->cnt, ctx->h_rel};
+        MixedShared sh{ctx->partials, ctx->ls, ctx->cnt, ctx->h_rel, &ctx->prof};
         status = solve_mixed(mh, sh, d_delta, p, d_phi, info, st, &ctx->err);
     }
     if (status == MG5_E_CUDA || status == MG5_E_ARG || status == MG5_E_OOM)
         return status;
-    if (d_grad)
+    if (d_grad) {
+        ProfScope ps(&ctx->prof, PK_FORCE, st, (double)n3);
         CK(launch_force(d_phi, N, N, N, 0, p->h, 1, d_grad, st));
+    }
     if (flags & MG5_HOST_IO) {
         CK(cudaMemcpyAsync(phi, d_phi, fb, cudaMemcpyDeviceToHost, st));
         if (grad)
@@ -601,6 +682,7 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
     CK(cudaMemcpyAsync(tail, &ctx->ls[0].c, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(tail + 1, &ctx->ls[0].mean, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    ctx->prof.resolve();
     if (status == MG5_OK && cnt.clamped > 0)
         status = MG5_W_DISC_CLAMP;
     if (info) {
@@ -630,6 +712,8 @@ int mg5_force(mg5_ctx *ctx, const double *phi, const int dims[3], int ghost, dou
     if (!periodic && ghost < 1)
         return MG5_E_ARG;
     CK(cudaSetDevice(ctx->device));
+    ProfScope ps(&ctx->prof, PK_FORCE, (cudaStream_t)stream,
+                 (double)(dims[0] - 2 * ghost) * (dims[1] - 2 * ghost) * (dims[2] - 2 * ghost));
     CK(launch_force(phi, dims[0], dims[1], dims[2], ghost, h, periodic ? 1 : 0, grad,
                     (cudaStream_t)stream));
     return MG5_OK;
@@ -644,6 +728,8 @@ int mg5_refine_interpolate(mg5_ctx *ctx, const double *phic, int Nc, const int o
         if (o[a] < 0 || o[a] >= Nc || pn[a] < 1 || pn[a] > Nc)
             return MG5_E_ARG;
     CK(cudaSetDevice(ctx->device));
+    ProfScope ps(&ctx->prof, PK_REFINE, (cudaStream_t)stream,
+                 (double)(2 * pn[0] + 2 * ghost) * (2 * pn[1] + 2 * ghost) * (2 * pn[2] + 2 * ghost));
     CK(launch_refine(phic, Nc, o, pn, ghost, fine, (cudaStream_t)stream));
     return MG5_OK;
 }
@@ -682,7 +768,10 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
     int status = MG5_E_NOT_CONVERGED;
     int nchk = 0;
     for (;;) {
-        CK(launch_patch_residual(cur, fint, compat_c, pf, cf, ctx->partials, &nb, st));
+        {
+            ProfScope ps(&ctx->prof, PK_PATCH_RESID, st, (double)ni);
+            CK(launch_patch_residual(cur, fint, compat_c, pf, cf, ctx->partials, &nb, st));
+        }
         CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_NORM, st));
         CK(cudaMemcpyAsync(ctx->h_rel, &ls->rel, sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -706,6 +795,7 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
         if (sweeps >= cap)
             break;
         for (int q = 0; q < check && sweeps < cap; ++q, ++sweeps) {
+            ProfScope ps(&ctx->prof, PK_PATCH_SWEEP, st, (double)ni);
             CK(launch_patch_sweep(cur, oth, fint, compat_c, pf, cf, &ctx->cnt->clamped, st));
             std::swap(cur, oth);
         }
@@ -716,6 +806,7 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
     SolveCounters cnt;
     CK(cudaMemcpyAsync(&cnt, ctx->cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    ctx->prof.resolve();
     if (status == MG5_OK && cnt.clamped > 0)
         status = MG5_W_DISC_CLAMP;
     if (info) {

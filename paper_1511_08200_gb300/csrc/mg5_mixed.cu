@@ -99,6 +99,7 @@ struct RunMix {
 
     int sweep(int l)
     {
+        ProfScope ps(sh.prof, PK_SWEEP32, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
         cudaError_t e = launch_sweep<float>(h->e[l], h->etmp[l], h->f[l], c(l), h->n[l],
                                             make_coef<float>(hl[l], p->alpha), &sh.cnt->clamped, st,
                                             h->B[l]);
@@ -111,6 +112,7 @@ struct RunMix {
 
     int coarsest(int l)
     {
+        ProfScope ps(sh.prof, PK_COARSEST32, st);
         cudaError_t e = launch_coarsest<float>(h->e[l], h->etmp[l], h->f[l], h->n[l],
                                                make_coef<float>(hl[l], p->alpha), c(l),
                                                p->nu_coarse, kCoarseRtol, &sh.cnt->clamped,
@@ -121,6 +123,7 @@ struct RunMix {
     int resid_restrict(int l)
     {
         int nb = 0;
+        ProfScope ps(sh.prof, PK_RESTRICT32, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
         cudaError_t e = launch_resid_restrict<float>(h->e[l], h->f[l], c(l), h->n[l],
                                                      make_coef<float>(hl[l], p->alpha), h->e[l + 1],
                                                      h->e0[l + 1], h->f[l + 1], sh.partials, &nb,
@@ -134,8 +137,12 @@ struct RunMix {
 
     int coarse_visit(int l)
     {
-        cudaError_t e = launch_coarse_rhs<float>(h->e[l], h->f[l], m(l - 1), c(l), h->n[l],
-                                                 make_coef<float>(hl[l], p->alpha), st, h->B[l]);
+        cudaError_t e;
+        {
+            ProfScope ps(sh.prof, PK_COARSE_RHS32, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
+            e = launch_coarse_rhs<float>(h->e[l], h->f[l], m(l - 1), c(l), h->n[l],
+                                         make_coef<float>(hl[l], p->alpha), st, h->B[l]);
+        }
         if (e != cudaSuccess)
             return fail("coarse_rhs32", e);
         if (l == h->nlev - 1)
@@ -147,8 +154,11 @@ struct RunMix {
             return rc;
         if (int rc = coarse_visit(l + 1))
             return rc;
-        e = launch_prolong_add<float>(h->e[l + 1], h->e0[l + 1], h->n[l + 1], h->e[l], c(l),
-                                      c(l + 1), st);
+        {
+            ProfScope ps(sh.prof, PK_PROLONG32, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
+            e = launch_prolong_add<float>(h->e[l + 1], h->e0[l + 1], h->n[l + 1], h->e[l], c(l),
+                                          c(l + 1), st);
+        }
         if (e != cudaSuccess)
             return fail("prolong32", e);
         for (int s = 0; s < p->nu2; ++s)
@@ -169,8 +179,11 @@ struct RunMix {
             return rc;
         if (int rc = coarse_visit(1))
             return rc;
-        cudaError_t e =
-            launch_prolong_add<float>(h->e[1], h->e0[1], h->n[1], h->e[0], c(0), c(1), st);
+        cudaError_t e;
+        {
+            ProfScope ps(sh.prof, PK_PROLONG32, st, (double)(h->n[0]) * (h->n[0]) * (h->n[0]));
+            e = launch_prolong_add<float>(h->e[1], h->e0[1], h->n[1], h->e[0], c(0), c(1), st);
+        }
         if (e != cudaSuccess)
             return fail("prolong32", e);
         for (int s = 0; s < p->nu2; ++s)
@@ -278,8 +291,11 @@ int solve_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const 
     double best = INFINITY;
     int outer = 0, inner_total = 0;
     for (;; ++outer) {
-        k_resid64_mixed<<<grid, kBlock, 0, st>>>(phi, h->f64, &sh.ls[0].c, N, cf64, h->f[0], h->B[0],
-                                                  sh.partials);
+        {
+            ProfScope ps(sh.prof, PK_RESID64_MIXED, st, (double)n3);
+            k_resid64_mixed<<<grid, kBlock, 0, st>>>(phi, h->f64, &sh.ls[0].c, N, cf64, h->f[0], h->B[0],
+                                                      sh.partials);
+        }
         count_launch(1);
         CKM(cudaGetLastError());
         CKM(launch_finalize(sh.partials, grid, (double)n3, sh.ls, FIN_STATS, st));
@@ -321,7 +337,10 @@ int solve_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const 
                 return rc;
             ++inner_total;
         }
-        k_update_mixed<<<blocks_for(n3), kBlock, 0, st>>>(phi, h->e[0], n3);
+        {
+            ProfScope ps(sh.prof, PK_UPDATE_MIXED, st, (double)n3);
+            k_update_mixed<<<blocks_for(n3), kBlock, 0, st>>>(phi, h->e[0], n3);
+        }
         count_launch(1);
         CKM(cudaGetLastError());
         k_scal<<<1, 1, 0, st>>>(sh.ls, R.ls(0), 2);  // c += c_e

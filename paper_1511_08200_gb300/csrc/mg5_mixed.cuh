@@ -8,6 +8,7 @@
 
 #include "mg5.h"
 #include "mg5_kernels.cuh"
+#include "mg5_prof.cuh"
 
 namespace mg5 {
 
@@ -32,6 +33,7 @@ struct MixedShared {
     LevelScal *ls;   // slot 0: FP64 finest; slots kInnerBase + l: inner grids
     SolveCounters *cnt;
     double *h_rel;   // pinned host scalar
+    Profiler *prof;
 };
 
 size_t mixed_bytes(int N);
