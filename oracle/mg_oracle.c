@@ -172,6 +172,7 @@ static double sigma_cell(const or_field *f, int i, int j, int k, double h)
 }
 
 static long long g_clamped; /* discriminant clamps, reset by the callers */
+static long long g_cell_updates; /* bookkeeping only: cells relaxed, reset by or_solve */
 
 /*
  * Solve  (2 alpha/3) L^2 + L - b = 0,  b = rhs + alpha Sigma,
@@ -362,8 +363,6 @@ typedef struct {
     long long cell_updates;   /* bookkeeping: cells relaxed, one per cell per sweep */
     double history[128];
 } or_info;
-
-static long long g_cell_updates; /* bookkeeping only, reset by or_solve */
 
 /* coarse-grid relative reduction that ends the coarsest solve */
 #define OR_COARSE_RTOL 1e-3
