@@ -190,12 +190,15 @@ int mg5_refine_interpolate(mg5_ctx *ctx, const double *phi_coarse, int Nc, const
  * (Dirichlet boundary values from the coarse level, Sec. 3.1).
  *   delta_fine: pf[0]*pf[1]*pf[2] FP64 (device), the fine density contrast.
  *   p         : alpha, s, h (the FINE cell size), tol (relative to
- *               ||s delta_fine||_2), max_cycles (sweep cap / 10).
+ *               ||s delta_fine||_2), nu1, nu2, nu_coarse, max_cycles (V-cycle cap).
  *   compat_c  : the coarse solve's c (keeps the background consistent).
  *   phi_fine  : (pf + 2)^3 box (device): in, the initial guess and the fixed
  *               ghost shell (from mg5_refine_interpolate with ghost = 1);
  *               out, the relaxed interior (ghosts untouched).
- * Each pf must be even and >= 4.  Synchronises `stream` at each convergence test.
+ * Solved by FAS V-cycles on the patch (interior halved while every side is
+ * even and the half >= 4; coarse ghost shells are means of the fine ghost
+ * cells they cover, so coarse corrections vanish on the boundary).  Each pf
+ * must be even and >= 2.  Synchronises `stream` once per V-cycle.
  */
 int mg5_relax_patch(mg5_ctx *ctx, const double *delta_fine, const int pf[3],
                     const mg5_params *p, double compat_c, double *phi_fine,
@@ -222,6 +225,16 @@ const char *mg5_profile_name(int k);
  * phi_out = sweep(phi_in).  phi_in and phi_out must not alias. */
 int mg5_step_sweep(mg5_ctx *ctx, const double *phi_in, double *phi_out, const double *f,
                    double c, int N, double h, double alpha, void *stream);
+/* The same sweep by the fused kernel (one read and one write of phi per cell). */
+int mg5_step_sweep_fused(mg5_ctx *ctx, const double *phi_in, double *phi_out, const double *f,
+                         double c, int N, double h, double alpha, void *stream);
+/* FP32 sweep of the mixed-precision inner solve.  With B == NULL it is the
+ * sweep above in FP32; with a base B it relaxes the correction e of
+ * op(B + e) - op(B) = f + c (B fixed).  variant 0: two-pass kernel,
+ * 1: fused kernel.  e_in and e_out must not alias. */
+int mg5_step_sweep_f32(mg5_ctx *ctx, const float *e_in, float *e_out, const float *f,
+                       const float *B, double c, int N, double h, double alpha, int variant,
+                       void *stream);
 /* out = op(phi) = L + alpha ((2/3) L^2 - Sigma) */
 int mg5_step_operator(mg5_ctx *ctx, const double *phi, int N, double h, double alpha,
                       double *out, void *stream);

@@ -92,6 +92,9 @@ _sigs = {
     "mg5_profile_name": ([_c_int], ctypes.c_char_p),
     "mg5_profile_units": ([_P, _P, _c_int], _c_int),
     "mg5_step_sweep": ([_P, _P, _P, _P, _c_double, _c_int, _c_double, _c_double, _P], _c_int),
+    "mg5_step_sweep_fused": ([_P, _P, _P, _P, _c_double, _c_int, _c_double, _c_double, _P], _c_int),
+    "mg5_step_sweep_f32": ([_P, _P, _P, _P, _P, _c_double, _c_int, _c_double, _c_double, _c_int, _P],
+                           _c_int),
     "mg5_step_operator": ([_P, _P, _c_int, _c_double, _c_double, _P, _P], _c_int),
     "mg5_step_residual": ([_P, _P, _P, _c_double, _c_int, _c_double, _c_double, _P, _P], _c_int),
     "mg5_step_restrict": ([_P, _P, _c_int, _P, _P], _c_int),
@@ -152,14 +155,14 @@ def workspace_bytes(n: int, precision=FP64) -> int:
     return out.value
 
 
-def _ptr(t) -> int:
-    """Device pointer of a torch CUDA tensor (float64, contiguous) or None."""
+def _ptr(t, dtype="float64") -> int:
+    """Device pointer of a contiguous torch CUDA tensor of the given dtype, or None."""
     if t is None:
         return None
     import torch
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
-            and t.is_contiguous()):
-        raise TypeError("expected a contiguous float64 CUDA tensor")
+    want = getattr(torch, dtype)
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == want and t.is_contiguous()):
+        raise TypeError("expected a contiguous %s CUDA tensor" % dtype)
     return t.data_ptr()
 
 
@@ -293,6 +296,23 @@ class Context:
         out = torch.empty_like(phi_in) if out is None else out
         self._check(_lib.mg5_step_sweep(self._h, _ptr(phi_in), _ptr(out), _ptr(f), c,
                                         int(phi_in.shape[0]), h, alpha, _stream(stream)))
+        return out
+
+    def step_sweep_fused(self, phi_in, f, c: float, h: float, alpha: float, out=None, stream=None):
+        import torch
+        out = torch.empty_like(phi_in) if out is None else out
+        self._check(_lib.mg5_step_sweep_fused(self._h, _ptr(phi_in), _ptr(out), _ptr(f), c,
+                                              int(phi_in.shape[0]), h, alpha, _stream(stream)))
+        return out
+
+    def step_sweep_f32(self, e_in, f, c: float, h: float, alpha: float, base=None, fused=False,
+                       out=None, stream=None):
+        import torch
+        out = torch.empty_like(e_in) if out is None else out
+        self._check(_lib.mg5_step_sweep_f32(self._h, _ptr(e_in, "float32"), _ptr(out, "float32"),
+                                            _ptr(f, "float32"), _ptr(base, "float32"), c,
+                                            int(e_in.shape[0]), h, alpha, 1 if fused else 0,
+                                            _stream(stream)))
         return out
 
     def step_operator(self, phi, h: float, alpha: float, out=None, stream=None):

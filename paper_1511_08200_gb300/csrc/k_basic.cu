@@ -485,13 +485,13 @@ cudaError_t launch_finalize(const double2 *partials, int nb, double ncells, Leve
 }
 
 __global__ void k_scale(const double *__restrict__ delta, double s, double *__restrict__ f,
-                        long long n3, double2 *__restrict__ partials)
+                        long long n3, double2 *__restrict__ partials, double add)
 {
     double2 acc = make_double2(0.0, 0.0);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n3;
          t += (long long)gridDim.x * blockDim.x) {
         const double v = s * delta[t];
-        f[t] = v;
+        f[t] = v + add;
         acc.y += v * v;
     }
     acc = block_sum2(acc);
@@ -500,12 +500,12 @@ __global__ void k_scale(const double *__restrict__ delta, double s, double *__re
 }
 
 cudaError_t launch_scale(const double *delta, double s, double *f, long long n3, double2 *partials,
-                         int *nblocks, cudaStream_t st)
+                         int *nblocks, cudaStream_t st, double add)
 {
     int g = blocks_for(n3);
     if (g > kReduceGrid)
         g = kReduceGrid;
-    k_scale<<<g, kBlock, 0, st>>>(delta, s, f, n3, partials);
+    k_scale<<<g, kBlock, 0, st>>>(delta, s, f, n3, partials, add);
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();

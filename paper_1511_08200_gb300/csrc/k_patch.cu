@@ -1,0 +1,264 @@
+// k_patch.cu -- kernels of the Dirichlet FAS multigrid on a refinement patch.
+//
+// A refinement of Sec. 3.1 has boundary values fixed by interpolation from
+// the coarser level: the patch is a box whose one-cell ghost shell holds
+// those values and is never relaxed.  Its FAS hierarchy halves the interior
+// (8-child mean for the iterate and the residual); the coarse boxes carry a
+// ghost shell too, filled once per solve by averaging the fine ghost cells
+// each coarse ghost cell covers.  The coarse iterate and its saved copy share
+// those ghosts, so the coarse correction vanishes there (homogeneous
+// Dirichlet) and the prolongation reads zero across the boundary.
+//
+// Box layout: interior dims (p0, p1, p2), box dims (p + 2), interior index
+// i <-> box index i + 1, C order.  Right-hand sides are interior-indexed.
+#include "mg5_kernels.cuh"
+
+namespace mg5 {
+
+__device__ __forceinline__ long long bidx(int i, int j, int k, int d1, int d2)
+{
+    return ((long long)i * d1 + j) * d2 + k;
+}
+
+// residual of the 8 interior children of each coarse interior cell, restricted
+// with v onto the coarse box interior (vc and v0c) and into fc (interior-indexed)
+__global__ void k_pbox_resid_restrict(const double *__restrict__ v, const double *__restrict__ f,
+                                      int p0, int p1, int p2, CoefT<double> cf,
+                                      double *__restrict__ vc, double *__restrict__ v0c,
+                                      double *__restrict__ fc, double2 *__restrict__ partials)
+{
+    const int q0 = p0 >> 1, q1 = p1 >> 1, q2 = p2 >> 1;
+    const long long total = (long long)q0 * q1 * q2;
+    double2 acc = make_double2(0.0, 0.0);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int K = (int)(t % q2);
+        const long long q = t / q2;
+        const int J = (int)(q % q1), I = (int)(q / q1);
+        double sv = 0.0, sr = 0.0;
+        for (int ch = 0; ch < 8; ++ch) {
+            const int i = 2 * I + (ch >> 2), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch & 1);
+            const Rows r = box_rows(p1 + 2, p2 + 2, i + 1, j + 1);
+            St<double> s;
+            gather(v, v, r, k + 1, k + 2, k, s);
+            const double res = f[((long long)i * p1 + j) * p2 + k] - cell_op(s, cf);
+            sv += s.c;
+            sr += res;
+            acc.x += res;
+            acc.y += res * res;
+        }
+        const long long cb = bidx(I + 1, J + 1, K + 1, q1 + 2, q2 + 2);
+        vc[cb] = 0.125 * sv;
+        v0c[cb] = 0.125 * sv;
+        fc[t] = 0.125 * sr;
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0)
+        partials[blockIdx.x] = acc;
+}
+
+// fc = op(vc) + fc on the coarse interior (fc holds the restricted residual)
+__global__ void k_pbox_coarse_rhs(const double *__restrict__ vc, double *__restrict__ fc, int q0,
+                                  int q1, int q2, CoefT<double> cf)
+{
+    const long long total = (long long)q0 * q1 * q2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int k = (int)(t % q2);
+    const long long q = t / q2;
+    const int j = (int)(q % q1), i = (int)(q / q1);
+    const Rows r = box_rows(q1 + 2, q2 + 2, i + 1, j + 1);
+    St<double> s;
+    gather(vc, vc, r, k + 1, k + 2, k, s);
+    fc[t] = cell_op(s, cf) + fc[t];
+}
+
+// fine interior += trilinear interpolation of (vc - v0c); the coarse ghosts
+// hold equal values in both, so the correction is zero across the boundary.
+__global__ void k_pbox_prolong(const double *__restrict__ vc, const double *__restrict__ v0c, int q0,
+                               int q1, int q2, double *__restrict__ vf)
+{
+    const int p0 = 2 * q0, p1 = 2 * q1, p2 = 2 * q2;
+    const long long total = (long long)p0 * p1 * p2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int k = (int)(t % p2);
+    const long long q = t / p2;
+    const int j = (int)(q % p1), i = (int)(q / p1);
+    // coarse box indices of the parent (+1 for the ghost offset) and of its neighbour
+    const int P[3] = {(i >> 1) + 1, (j >> 1) + 1, (k >> 1) + 1};
+    const int Q[3] = {(i & 1) ? P[0] + 1 : P[0] - 1, (j & 1) ? P[1] + 1 : P[1] - 1,
+                      (k & 1) ? P[2] + 1 : P[2] - 1};
+    const int d1 = q1 + 2, d2 = q2 + 2;
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const long long idx = bidx(a ? Q[0] : P[0], b ? Q[1] : P[1], c ? Q[2] : P[2], d1, d2);
+                const double w = (a ? 0.25 : 0.75) * (b ? 0.25 : 0.75) * (c ? 0.25 : 0.75);
+                acc += w * (vc[idx] - v0c[idx]);
+            }
+    vf[bidx(i + 1, j + 1, k + 1, p1 + 2, p2 + 2)] += acc;
+}
+
+// coarse box ghost cells: mean of the fine ghost cells each one covers
+// (per axis: coarse -1 -> fine -1; coarse q -> fine p; otherwise its two children)
+__global__ void k_pbox_ghosts(const double *__restrict__ fb, int p0, int p1, int p2,
+                              double *__restrict__ g1, double *__restrict__ g2,
+                              double *__restrict__ g3)
+{
+    const int q[3] = {p0 >> 1, p1 >> 1, p2 >> 1};
+    const int D0 = q[0] + 2, D1 = q[1] + 2, D2 = q[2] + 2;
+    const long long total = (long long)D0 * D1 * D2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int K = (int)(t % D2);
+    const long long qq = t / D2;
+    const int J = (int)(qq % D1), I = (int)(qq / D1);
+    const int loc[3] = {I - 1, J - 1, K - 1};  // coarse interior index, -1 .. q
+    bool ghost = false;
+    int lo[3], cnt[3];
+    for (int a = 0; a < 3; ++a) {
+        if (loc[a] < 0) {
+            ghost = true;
+            lo[a] = -1;
+            cnt[a] = 1;
+        } else if (loc[a] >= q[a]) {
+            ghost = true;
+            lo[a] = 2 * q[a];
+            cnt[a] = 1;
+        } else {
+            lo[a] = 2 * loc[a];
+            cnt[a] = 2;
+        }
+    }
+    if (!ghost)
+        return;
+    double s = 0.0;
+    for (int a = 0; a < cnt[0]; ++a)
+        for (int b = 0; b < cnt[1]; ++b)
+            for (int c = 0; c < cnt[2]; ++c)
+                s += fb[bidx(lo[0] + a + 1, lo[1] + b + 1, lo[2] + c + 1, p1 + 2, p2 + 2)];
+    const double g = s / (double)(cnt[0] * cnt[1] * cnt[2]);
+    g1[t] = g;
+    g2[t] = g;
+    g3[t] = g;
+}
+
+// Coarsest patch grid, one CTA: before each sweep the residual norm; stop at
+// rtol times the first one or after nu_max sweeps.  A -> B (red) -> A (black).
+__global__ void __launch_bounds__(1024)
+    k_pbox_coarsest(double *A, double *B, const double *__restrict__ f, int p0, int p1, int p2,
+                    CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
+                    int *sweeps_out)
+{
+    __shared__ double bc_s;
+    const int n3 = p0 * p1 * p2;
+    const int d1 = p1 + 2, d2 = p2 + 2;
+    double r0 = -1.0;
+    int it = 0;
+    unsigned long long my_clamps = 0;
+    for (; it < nu_max; ++it) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int p = threadIdx.x; p < n3; p += blockDim.x) {
+            const int k = p % p2, j = (p / p2) % p1, i = p / (p1 * p2);
+            const Rows r = box_rows(d1, d2, i + 1, j + 1);
+            St<double> s;
+            gather((const double *)A, (const double *)A, r, k + 1, k + 2, k, s);
+            const double res = f[p] - cell_op(s, cf);
+            acc.y += res * res;
+        }
+        acc = block_sum2(acc);
+        if (threadIdx.x == 0)
+            bc_s = acc.y;
+        __syncthreads();
+        const double rn = sqrt(bc_s);
+        __syncthreads();
+        if (r0 < 0.0)
+            r0 = rn;
+        if (rn <= rtol * r0)
+            break;
+        for (int colour = 0; colour < 2; ++colour) {
+            const double *src = colour == 0 ? A : B;
+            double *dst = colour == 0 ? B : A;
+            for (int p = threadIdx.x; p < n3; p += blockDim.x) {
+                const int k = p % p2, j = (p / p2) % p1, i = p / (p1 * p2);
+                const Rows r = box_rows(d1, d2, i + 1, j + 1);
+                if (((i + j + k) & 1) != colour) {
+                    dst[r.r00 + k + 1] = src[r.r00 + k + 1];
+                    continue;
+                }
+                St<double> s;
+                gather(src, src, r, k + 1, k + 2, k, s);
+                bool cl = false;
+                dst[r.r00 + k + 1] = cell_update(s, f[p], cf, cl);
+                my_clamps += cl ? 1ull : 0ull;
+            }
+            __syncthreads();
+        }
+    }
+    if (my_clamps)
+        atomicAdd(clamp, my_clamps);
+    if (threadIdx.x == 0 && sweeps_out)
+        atomicAdd(sweeps_out, it);
+}
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_pbox_resid_restrict(const double *v, const double *f, const int p[3],
+                                       CoefT<double> cf, double *vc, double *v0c, double *fc,
+                                       double2 *partials, int *nblocks, cudaStream_t st)
+{
+    const long long work = (long long)(p[0] / 2) * (p[1] / 2) * (p[2] / 2);
+    int g = blocks_for(work);
+    if (g > kMaxPartials)
+        g = kMaxPartials;
+    k_pbox_resid_restrict<<<g, kBlock, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc, v0c, fc, partials);
+    *nblocks = g;
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pbox_coarse_rhs(const double *vc, double *fc, const int q[3], CoefT<double> cf,
+                                   cudaStream_t st)
+{
+    const long long work = (long long)q[0] * q[1] * q[2];
+    k_pbox_coarse_rhs<<<blocks_for(work), kBlock, 0, st>>>(vc, fc, q[0], q[1], q[2], cf);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pbox_prolong(const double *vc, const double *v0c, const int q[3], double *vf,
+                                cudaStream_t st)
+{
+    const long long work = 8ll * q[0] * q[1] * q[2];
+    k_pbox_prolong<<<blocks_for(work), kBlock, 0, st>>>(vc, v0c, q[0], q[1], q[2], vf);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pbox_ghosts(const double *fine_box, const int p[3], double *g1, double *g2,
+                               double *g3, cudaStream_t st)
+{
+    const long long work = (long long)(p[0] / 2 + 2) * (p[1] / 2 + 2) * (p[2] / 2 + 2);
+    k_pbox_ghosts<<<blocks_for(work), kBlock, 0, st>>>(fine_box, p[0], p[1], p[2], g1, g2, g3);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pbox_coarsest(double *A, double *B, const double *f, const int p[3],
+                                 CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
+                                 int *sweeps, cudaStream_t st)
+{
+    k_pbox_coarsest<<<1, 1024, 0, st>>>(A, B, f, p[0], p[1], p[2], cf, nu_max, rtol, clamp, sweeps);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace mg5

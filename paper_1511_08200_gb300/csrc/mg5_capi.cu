@@ -48,6 +48,41 @@ struct Hier {
     size_t bytes = 0;
 };
 
+// Dirichlet patch hierarchy: interior dims halve while all are even and the half is >= 4.
+struct PatchHier {
+    int p[3] = {};
+    int nlev = 0;
+    int q[kMaxLevels][3] = {};
+    double *v[kMaxLevels] = {};    // boxes (level 0: caller's box at run time)
+    double *tmp[kMaxLevels] = {};
+    double *v0[kMaxLevels] = {};   // boxes, l >= 1
+    double *f[kMaxLevels] = {};    // interior-indexed right-hand sides
+    size_t bytes = 0;
+};
+
+int patch_levels(const int p[3], int q[][3])
+{
+    int L = 0;
+    int c[3] = {p[0], p[1], p[2]};
+    for (;;) {
+        q[L][0] = c[0];
+        q[L][1] = c[1];
+        q[L][2] = c[2];
+        ++L;
+        bool ok = L < kMaxLevels;
+        for (int a = 0; a < 3; ++a)
+            ok = ok && (c[a] % 2 == 0) && (c[a] / 2 >= 4);
+        if (!ok)
+            break;
+        for (int a = 0; a < 3; ++a)
+            c[a] /= 2;
+    }
+    return L;
+}
+
+size_t box_cells(const int q[3]) { return (size_t)(q[0] + 2) * (q[1] + 2) * (q[2] + 2); }
+size_t int_cells(const int q[3]) { return (size_t)q[0] * q[1] * q[2]; }
+
 int num_levels(int N, int *sizes)
 {
     int L = 0, n = N;
@@ -78,6 +113,7 @@ struct mg5_ctx {
     std::string err;
     std::vector<Hier *> hiers;
     std::vector<MixedHier *> mixed;
+    std::vector<PatchHier *> patches;
     double2 *partials = nullptr;
     LevelScal *ls = nullptr;        // kScalSlots slots
     SolveCounters *cnt = nullptr;
@@ -179,6 +215,55 @@ static int get_hier(mg5_ctx *ctx, int N, Hier **out)
     }
     h->bytes = fp64_bytes(N);
     ctx->hiers.push_back(h);
+    *out = h;
+    return MG5_OK;
+}
+
+static void free_patch(mg5_ctx *ctx, PatchHier *h)
+{
+    for (int l = 0; l < h->nlev; ++l) {
+        const size_t bb = box_cells(h->q[l]) * sizeof(double), ib = int_cells(h->q[l]) * sizeof(double);
+        if (l > 0) {
+            ctx_free(ctx, h->v[l], bb);
+            ctx_free(ctx, h->v0[l], bb);
+        }
+        ctx_free(ctx, h->tmp[l], bb);
+        ctx_free(ctx, h->f[l], ib);
+    }
+    delete h;
+}
+
+static int get_patch(mg5_ctx *ctx, const int p[3], PatchHier **out)
+{
+    for (PatchHier *h : ctx->patches)
+        if (h->p[0] == p[0] && h->p[1] == p[1] && h->p[2] == p[2]) {
+            *out = h;
+            return MG5_OK;
+        }
+    PatchHier *h = new PatchHier();
+    for (int a = 0; a < 3; ++a)
+        h->p[a] = p[a];
+    h->nlev = patch_levels(p, h->q);
+    int rc = MG5_OK;
+    for (int l = 0; l < h->nlev && rc == MG5_OK; ++l) {
+        const size_t bb = box_cells(h->q[l]) * sizeof(double), ib = int_cells(h->q[l]) * sizeof(double);
+        if (l > 0) {
+            rc = ctx_alloc(ctx, (void **)&h->v[l], bb);
+            if (rc == MG5_OK)
+                rc = ctx_alloc(ctx, (void **)&h->v0[l], bb);
+            h->bytes += 2 * bb;
+        }
+        if (rc == MG5_OK)
+            rc = ctx_alloc(ctx, (void **)&h->tmp[l], bb);
+        if (rc == MG5_OK)
+            rc = ctx_alloc(ctx, (void **)&h->f[l], ib);
+        h->bytes += bb + ib;
+    }
+    if (rc != MG5_OK) {
+        free_patch(ctx, h);
+        return rc;
+    }
+    ctx->patches.push_back(h);
     *out = h;
     return MG5_OK;
 }
@@ -534,6 +619,9 @@ int mg5_release(mg5_ctx *ctx)
     for (MixedHier *m : ctx->mixed)
         free_mixed(m, &ctx->held);
     ctx->mixed.clear();
+    for (PatchHier *ph : ctx->patches)
+        free_patch(ctx, ph);
+    ctx->patches.clear();
     ctx_free(ctx, ctx->stage, ctx->stage_bytes);
     ctx->stage = nullptr;
     ctx->stage_bytes = 0;
@@ -734,6 +822,76 @@ int mg5_refine_interpolate(mg5_ctx *ctx, const double *phic, int Nc, const int o
     return MG5_OK;
 }
 
+namespace {
+
+// FAS V-cycles on the Dirichlet patch hierarchy (ghost shells fixed).
+struct RunPatch {
+    mg5_ctx *ctx;
+    PatchHier *h;
+    const mg5_params *p;
+    cudaStream_t st;
+    double hl[kMaxLevels];
+    long long cu = 0;
+
+    int sweep(int l)
+    {
+        mg5_ctx *ctx = this->ctx;
+        const double cells = (double)int_cells(h->q[l]);
+        {
+            ProfScope ps(&ctx->prof, PK_PATCH_SWEEP, st, cells);
+            CK(launch_patch_sweep(h->v[l], h->tmp[l], h->f[l], 0.0, h->q[l],
+                                  make_coef<double>(hl[l], p->alpha), &ctx->cnt->clamped, st));
+        }
+        std::swap(h->v[l], h->tmp[l]);
+        cu += (long long)cells;
+        return MG5_OK;
+    }
+
+    int coarsest(int l)
+    {
+        mg5_ctx *ctx = this->ctx;
+        ProfScope ps(&ctx->prof, PK_COARSEST64, st);
+        CK(launch_pbox_coarsest(h->v[l], h->tmp[l], h->f[l], h->q[l],
+                                make_coef<double>(hl[l], p->alpha), p->nu_coarse, kCoarseRtol,
+                                &ctx->cnt->clamped, &ctx->cnt->coarse_sweeps, st));
+        return MG5_OK;
+    }
+
+    int resid_restrict(int l, bool finalize)
+    {
+        mg5_ctx *ctx = this->ctx;
+        int nb = 0;
+        {
+            ProfScope ps(&ctx->prof, PK_PATCH_RESID, st, (double)int_cells(h->q[l]));
+            CK(launch_pbox_resid_restrict(h->v[l], h->f[l], h->q[l],
+                                          make_coef<double>(hl[l], p->alpha), h->v[l + 1],
+                                          h->v0[l + 1], h->f[l + 1], ctx->partials, &nb, st));
+        }
+        if (finalize)
+            CK(launch_finalize(ctx->partials, nb, (double)int_cells(h->q[l]), ctx->ls + kPatchSlot,
+                               FIN_NORM, st));
+        return MG5_OK;
+    }
+
+    int coarse_visit(int l)
+    {
+        mg5_ctx *ctx = this->ctx;
+        CK(launch_pbox_coarse_rhs(h->v[l], h->f[l], h->q[l], make_coef<double>(hl[l], p->alpha), st));
+        if (l == h->nlev - 1)
+            return coarsest(l);
+        for (int s = 0; s < p->nu1; ++s)
+            RET(sweep(l));
+        RET(resid_restrict(l, false));
+        RET(coarse_visit(l + 1));
+        CK(launch_pbox_prolong(h->v[l + 1], h->v0[l + 1], h->q[l + 1], h->v[l], st));
+        for (int s = 0; s < p->nu2; ++s)
+            RET(sweep(l));
+        return MG5_OK;
+    }
+};
+
+}  // namespace
+
 int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const mg5_params *p,
                     double compat_c, double *phi, mg5_info *info, void *stream)
 {
@@ -741,49 +899,68 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
         return MG5_E_ARG;
     RET(check_params(p));
     for (int a = 0; a < 3; ++a)
-        if (pf[a] < 4 || (pf[a] & 1))
+        if (pf[a] < 2 || (pf[a] & 1))
             return MG5_E_ARG;
+    if (!std::isfinite(compat_c))
+        return MG5_E_ARG;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     if (info)
         std::memset(info, 0, sizeof(*info));
-    const long long ni = (long long)pf[0] * pf[1] * pf[2];
-    const long long nb_box = (long long)(pf[0] + 2) * (pf[1] + 2) * (pf[2] + 2);
-    RET(ensure_buffer(ctx, &ctx->patch, &ctx->patch_bytes, (size_t)(ni + nb_box) * sizeof(double)));
-    double *fint = ctx->patch;
-    double *tmp = ctx->patch + ni;
+    PatchHier *h = nullptr;
+    RET(get_patch(ctx, pf, &h));
+    const long long ni = (long long)int_cells(pf);
+    const long long nbox = (long long)box_cells(pf);
     CK(cudaEventRecord(ctx->ev0, st));
     LevelScal *ls = ctx->ls + kPatchSlot;
     CK(cudaMemsetAsync(ls, 0, sizeof(LevelScal), st));
     CK(cudaMemsetAsync(ctx->cnt, 0, sizeof(SolveCounters), st));
     int nb = 0;
-    CK(launch_scale(delta_f, p->s, fint, ni, ctx->partials, &nb, st));
+    // f0 = s delta + c; the tolerance is relative to ||s delta||
+    CK(launch_scale(delta_f, p->s, h->f[0], ni, ctx->partials, &nb, st, compat_c));
     CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_FNORM, st));
-    CK(cudaMemcpyAsync(tmp, phi, nb_box * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    const CoefT<double> cf = make_coef<double>(p->h, p->alpha);
-    const int check = 10;
-    const long long cap = (long long)std::max(p->max_cycles, 1) * check;
-    double *cur = phi, *oth = tmp;
-    long long sweeps = 0;
-    int status = MG5_E_NOT_CONVERGED;
-    int nchk = 0;
-    for (;;) {
+    // the ping-pong partner of the caller's box carries the same ghost shell
+    CK(cudaMemcpyAsync(h->tmp[0], phi, nbox * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (int l = 1; l < h->nlev; ++l)
+        CK(launch_pbox_ghosts(l == 1 ? phi : h->v[l - 1], h->q[l - 1], h->v[l], h->tmp[l], h->v0[l],
+                              st));
+    struct Restore {
+        PatchHier *h;
+        double *own;
+        ~Restore()
         {
-            ProfScope ps(&ctx->prof, PK_PATCH_RESID, st, (double)ni);
-            CK(launch_patch_residual(cur, fint, compat_c, pf, cf, ctx->partials, &nb, st));
+            h->v[0] = nullptr;
+            h->tmp[0] = own;
         }
-        CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_NORM, st));
+    } restore{h, h->tmp[0]};
+    h->v[0] = phi;
+    RunPatch R{ctx, h, p, st, {}, 0};
+    for (int l = 0; l < h->nlev; ++l)
+        R.hl[l] = p->h * (double)(1 << l);
+    int status = MG5_E_NOT_CONVERGED;
+    double best = INFINITY;
+    int cyc = 0;
+    for (;; ++cyc) {
+        if (h->nlev == 1) {
+            RET(R.coarsest(0));
+            CK(launch_patch_residual(h->v[0], h->f[0], 0.0, pf, make_coef<double>(p->h, p->alpha),
+                                     ctx->partials, &nb, st));
+            CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_NORM, st));
+        } else {
+            for (int s = 0; s < p->nu1; ++s)
+                RET(R.sweep(0));
+            RET(R.resid_restrict(0, true));
+        }
         CK(cudaMemcpyAsync(ctx->h_rel, &ls->rel, sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         const double rel = *ctx->h_rel;
         if (info) {
             info->rel_residual = rel;
-            if (nchk < 64) {
-                info->history[nchk] = rel;
-                info->n_history = nchk + 1;
+            if (cyc < 64) {
+                info->history[cyc] = rel;
+                info->n_history = cyc + 1;
             }
         }
-        ++nchk;
         if (!std::isfinite(rel)) {
             status = MG5_E_NONFINITE;
             break;
@@ -792,16 +969,22 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
             status = MG5_OK;
             break;
         }
-        if (sweeps >= cap)
+        best = std::min(best, rel);
+        if (cyc >= 3 && rel > 10.0 * best) {
+            status = MG5_E_DIVERGED;
             break;
-        for (int q = 0; q < check && sweeps < cap; ++q, ++sweeps) {
-            ProfScope ps(&ctx->prof, PK_PATCH_SWEEP, st, (double)ni);
-            CK(launch_patch_sweep(cur, oth, fint, compat_c, pf, cf, &ctx->cnt->clamped, st));
-            std::swap(cur, oth);
         }
+        if (cyc >= p->max_cycles)
+            break;
+        if (h->nlev == 1)
+            continue;
+        RET(R.coarse_visit(1));
+        CK(launch_pbox_prolong(h->v[1], h->v0[1], h->q[1], h->v[0], st));
+        for (int s = 0; s < p->nu2; ++s)
+            RET(R.sweep(0));
     }
-    if (cur != phi)
-        CK(cudaMemcpyAsync(phi, cur, nb_box * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (h->v[0] != phi)
+        CK(cudaMemcpyAsync(phi, h->v[0], nbox * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CK(cudaEventRecord(ctx->ev1, st));
     SolveCounters cnt;
     CK(cudaMemcpyAsync(&cnt, ctx->cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
@@ -814,8 +997,10 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
         cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
         info->ms_total = ms;
         info->status = status;
-        info->cycles = (int)sweeps;
-        info->cell_updates = sweeps * ni;
+        info->cycles = cyc;
+        info->levels = h->nlev;
+        info->coarsest_n = h->q[h->nlev - 1][0];
+        info->cell_updates = R.cu + (long long)cnt.coarse_sweeps * (long long)int_cells(h->q[h->nlev - 1]);
         info->disc_clamped = (long long)cnt.clamped;
         info->compat_c = compat_c;
     }
@@ -832,6 +1017,40 @@ int mg5_step_sweep(mg5_ctx *ctx, const double *in, double *out, const double *f,
     double *cd = &ctx->ls[kStepSlot].c;
     CK(cudaMemcpyAsync(cd, &c, sizeof(double), cudaMemcpyHostToDevice, st));
     CK(launch_sweep<double>(in, out, f, cd, N, make_coef<double>(h, alpha), &ctx->cnt->clamped, st));
+    CK(cudaStreamSynchronize(st));
+    return MG5_OK;
+}
+
+int mg5_step_sweep_f32(mg5_ctx *ctx, const float *in, float *out, const float *f, const float *B,
+                       double c, int N, double h, double alpha, int variant, void *stream)
+{
+    if (!ctx || !in || !out || !f || in == out || N < 2 || (N & 1) || !(h > 0.0) ||
+        (variant != 0 && variant != 1))
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    double *cd = &ctx->ls[kStepSlot].c;
+    CK(cudaMemcpyAsync(cd, &c, sizeof(double), cudaMemcpyHostToDevice, st));
+    const CoefT<float> cf = make_coef<float>(h, alpha);
+    if (variant == 1)
+        CK(launch_sweep_fused<float>(in, out, f, cd, N, cf, &ctx->cnt->clamped, st, B));
+    else
+        CK(launch_sweep<float>(in, out, f, cd, N, cf, &ctx->cnt->clamped, st, B));
+    CK(cudaStreamSynchronize(st));
+    return MG5_OK;
+}
+
+int mg5_step_sweep_fused(mg5_ctx *ctx, const double *in, double *out, const double *f, double c,
+                         int N, double h, double alpha, void *stream)
+{
+    if (!ctx || !in || !out || !f || in == out || N < 2 || (N & 1) || !(h > 0.0))
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    double *cd = &ctx->ls[kStepSlot].c;
+    CK(cudaMemcpyAsync(cd, &c, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(launch_sweep_fused<double>(in, out, f, cd, N, make_coef<double>(h, alpha), &ctx->cnt->clamped,
+                                  st));
     CK(cudaStreamSynchronize(st));
     return MG5_OK;
 }

@@ -54,6 +54,12 @@ template <typename T>
 cudaError_t launch_sweep(const T *in, T *out, const T *f, const double *cptr, int n,
                          CoefT<T> cf, unsigned long long *clamp, cudaStream_t st,
                          const T *B = nullptr);
+// fused red+black sweep (k_fused.cu): one read and one write of phi per cell
+template <typename T>
+cudaError_t launch_sweep_fused(const T *in, T *out, const T *f, const double *cptr, int n,
+                               CoefT<T> cf, unsigned long long *clamp, cudaStream_t st,
+                               const T *B = nullptr);
+constexpr int kFusedMinN = 32;   // smaller grids use the two-pass sweep
 template <typename T>
 cudaError_t launch_operator(const T *phi, int n, CoefT<T> cf, T *out, cudaStream_t st);
 // r (nullable) = f + c - op(phi); partial sums (sum r, sum r^2) per block.
@@ -85,9 +91,9 @@ cudaError_t launch_coarsest(T *v, T *tmp, const T *f, int n, CoefT<T> cf, double
 // ---- FP64 helpers
 cudaError_t launch_finalize(const double2 *partials, int nb, double ncells, LevelScal *ls,
                             int mode, cudaStream_t st);
-// f = s * delta, partial sums (0, f^2)
+// f = s * delta + add, partial sums (0, (s delta)^2)
 cudaError_t launch_scale(const double *delta, double s, double *f, long long n3, double2 *partials,
-                         int *nblocks, cudaStream_t st);
+                         int *nblocks, cudaStream_t st, double add = 0.0);
 // partial sums (phi, 0)
 cudaError_t launch_sum(const double *phi, long long n3, double2 *partials, int *nblocks,
                        cudaStream_t st);
@@ -105,5 +111,19 @@ cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint
 cudaError_t launch_patch_residual(const double *phi, const double *fint, double rhs_add,
                                   const int pf[3], CoefT<double> cf, double2 *partials, int *nblocks,
                                   cudaStream_t st);
+
+// ---- Dirichlet patch multigrid (k_patch.cu); p = fine interior dims, q = coarse interior dims
+cudaError_t launch_pbox_resid_restrict(const double *v, const double *f, const int p[3],
+                                       CoefT<double> cf, double *vc, double *v0c, double *fc,
+                                       double2 *partials, int *nblocks, cudaStream_t st);
+cudaError_t launch_pbox_coarse_rhs(const double *vc, double *fc, const int q[3], CoefT<double> cf,
+                                   cudaStream_t st);
+cudaError_t launch_pbox_prolong(const double *vc, const double *v0c, const int q[3], double *vf,
+                                cudaStream_t st);
+cudaError_t launch_pbox_ghosts(const double *fine_box, const int p[3], double *g1, double *g2,
+                               double *g3, cudaStream_t st);
+cudaError_t launch_pbox_coarsest(double *A, double *B, const double *f, const int p[3],
+                                 CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
+                                 int *sweeps, cudaStream_t st);
 
 }  // namespace mg5

@@ -100,9 +100,13 @@ struct RunMix {
     int sweep(int l)
     {
         ProfScope ps(sh.prof, PK_SWEEP32, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
-        cudaError_t e = launch_sweep<float>(h->e[l], h->etmp[l], h->f[l], c(l), h->n[l],
-                                            make_coef<float>(hl[l], p->alpha), &sh.cnt->clamped, st,
-                                            h->B[l]);
+        const CoefT<float> cf = make_coef<float>(hl[l], p->alpha);
+        cudaError_t e =
+            h->n[l] >= kFusedMinN
+                ? launch_sweep_fused<float>(h->e[l], h->etmp[l], h->f[l], c(l), h->n[l], cf,
+                                            &sh.cnt->clamped, st, h->B[l])
+                : launch_sweep<float>(h->e[l], h->etmp[l], h->f[l], c(l), h->n[l], cf,
+                                      &sh.cnt->clamped, st, h->B[l]);
         if (e != cudaSuccess)
             return fail("sweep32", e);
         std::swap(h->e[l], h->etmp[l]);

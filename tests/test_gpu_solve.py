@@ -215,3 +215,27 @@ def test_refine_and_relax_patch_match_oracle(ctx):
     assert rel_l2(g_tr, oracle.force(box_ref, hf, ghost=1, periodic=False)) <= 1e-10
     assert rel_l2(g_full, oracle.force(ref_relaxed, hf, ghost=1, periodic=False)) <= 1e-10
     assert 0 < rel_l2(g_tr, g_full) < 1.0
+
+
+def test_relax_patch_full_size_64(ctx):
+    """The 64^3 patch of the refinement workload (128^3 coarse grid), relaxed by the
+    patch multigrid, against the oracle's Gauss-Seidel relaxation of the same
+    Dirichlet problem, both to 1e-11."""
+    mg = _mg()
+    alpha, s, h = nominal()
+    coarse, dpatch, o = workload.patch_workload(256, 1.5, 2, 32)
+    hc = 250.0 / 128
+    ref_c, rinfo = oracle.solve(coarse, alpha, s, hc, tol=1e-13)
+    box_ref = oracle.refine_interpolate(ref_c, o, (32, 32, 32), 1)
+    box = dev(box_ref)
+    p = mg.default_params(alpha=alpha, s=s, h=hc / 2, tol=1e-11)
+    relaxed, pinfo = ctx.relax_patch(dev(dpatch), p, rinfo.compat_c, box)
+    assert pinfo.status == 0 and pinfo.cycles < 30
+    ref_relaxed, nsw, rel = oracle.relax_patch(dpatch, box_ref, alpha, s, hc / 2, rinfo.compat_c,
+                                               tol=1e-11)
+    assert rel <= 1e-11
+    got = host(relaxed)
+    assert rel_l2(got[1:-1, 1:-1, 1:-1], ref_relaxed[1:-1, 1:-1, 1:-1]) <= 1e-9
+    g = host(ctx.force(relaxed, hc / 2, ghost=1, periodic=False))
+    gref = oracle.force(ref_relaxed, hc / 2, ghost=1, periodic=False)
+    assert rel_l2(g, gref) <= 1e-9

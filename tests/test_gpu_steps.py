@@ -49,7 +49,7 @@ def test_residual(ctx, n):
     c = 3e-11
     got = host(ctx.step_residual(dev(phi), dev(f), c, h, alpha))
     ref = oracle.residual(phi, f, c, h, alpha)
-    assert np.abs(got - ref).max() < 1e-13 * np.abs(f).max()
+    assert _maxrel(got, ref) < 1e-13
 
 
 @pytest.mark.parametrize("n", SIZES)
@@ -120,3 +120,70 @@ def test_refine_interpolate(ctx, nc, o, pn, g):
     phic = _field(nc, 13)
     got = host(ctx.refine_interpolate(dev(phic), o, pn, g))
     assert _maxrel(got, oracle.refine_interpolate(phic, o, pn, g)) < 1e-15
+
+
+# ---------------------------------------------------------------- fused and FP32 sweeps
+
+FUSED_SIZES = [4, 8, 16, 32, 34, 48, 64, 80]   # 34, 48, 80: ragged tiles (tile 16 x 32)
+
+
+@pytest.mark.parametrize("n", FUSED_SIZES)
+def test_sweep_fused_fp64(ctx, n):
+    """The fused plane-marching kernel is the same snapshot red-black sweep."""
+    alpha, s, h = nominal()
+    phi = _field(n, 21)
+    f = s * 10.0 * workload.lognormal_delta(n, 1.5, 22)
+    c = 2e-10
+    got = host(ctx.step_sweep_fused(dev(phi), dev(f), c, h, alpha))
+    ref = oracle.sweep(phi, f, c, h, alpha)
+    assert _maxrel(got, ref) < 1e-13
+
+
+def _f32(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("n", [8, 16, 34, 64])
+@pytest.mark.parametrize("fused", [False, True])
+def test_sweep_fp32_plain(ctx, n, fused):
+    """Without a base the FP32 sweep is the oracle's sweep to FP32 rounding."""
+    alpha, s, h = nominal()
+    phi = _field(n, 23)
+    f = s * 5.0 * workload.lognormal_delta(n, 1.0, 24)
+    c = 1e-10
+    got = host(ctx.step_sweep_f32(_f32(phi), _f32(f), c, h, alpha, fused=fused)).astype(np.float64)
+    ref = oracle.sweep(phi, f, c, h, alpha)
+    # phi - h^2 L / 6: the FP32 error is a few ulps of phi
+    assert np.abs(got - ref).max() < 2e-6 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n", [8, 34, 64])
+@pytest.mark.parametrize("fused", [False, True])
+def test_sweep_fp32_correction_form(ctx, n, fused):
+    """With a base B, the FP32 sweep relaxes e in op(B + e) - op(B) = f + c: it must
+    equal the oracle's FP64 sweep of u = B + e with right-hand side op(B) + f, minus B."""
+    alpha, s, h = nominal()
+    B = _field(n, 25)
+    e = 1e-3 * _field(n, 26)
+    rhs = 1e-3 * s * 5.0 * workload.lognormal_delta(n, 1.0, 27)
+    c = 3e-13
+    got = host(ctx.step_sweep_f32(_f32(e), _f32(rhs), c, h, alpha, base=_f32(B),
+                                  fused=fused)).astype(np.float64)
+    Bq = np.asarray(B, dtype=np.float32).astype(np.float64)   # the base the kernel sees
+    eq = np.asarray(e, dtype=np.float32).astype(np.float64)
+    fq = np.asarray(rhs, dtype=np.float32).astype(np.float64)
+    u = oracle.sweep(Bq + eq, oracle.operator(Bq, h, alpha) + fq, c, h, alpha)
+    ref = u - Bq
+    assert np.abs(got - ref).max() < 1e-4 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n", [32, 48, 64, 96])
+def test_fused_matches_two_pass_fp32(ctx, n):
+    alpha, s, h = nominal()
+    B = _field(n, 28)
+    e = 1e-2 * _field(n, 29)
+    rhs = 1e-2 * s * workload.lognormal_delta(n, 1.0, 30)
+    a = host(ctx.step_sweep_f32(_f32(e), _f32(rhs), 0.0, h, alpha, base=_f32(B), fused=False))
+    b = host(ctx.step_sweep_f32(_f32(e), _f32(rhs), 0.0, h, alpha, base=_f32(B), fused=True))
+    assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max()
