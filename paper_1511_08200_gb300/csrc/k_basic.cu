@@ -680,15 +680,25 @@ __global__ void k_patch_half(const double *__restrict__ src_faces, const double 
 
 cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint, double rhs_add,
                                const int pf[3], CoefT<double> cf, unsigned long long *clamp,
-                               cudaStream_t st)
+                               cudaStream_t st, const double *v0, double w)
 {
     const long long work = (long long)pf[0] * pf[1] * pf[2];
     const int g = blocks_for(work);
     // red: from in (all), black copied; black: faces from out (new red), edges from in (old black)
     k_patch_half<<<g, kBlock, 0, st>>>(in, in, out, fint, rhs_add, pf[0], pf[1], pf[2], cf, 0, 1,
                                        clamp);
+    if (v0) {
+        cudaError_t e = launch_pbox_ghost_refresh(out, v0, pf, w, st);
+        if (e != cudaSuccess)
+            return e;
+    }
     k_patch_half<<<g, kBlock, 0, st>>>(out, in, out, fint, rhs_add, pf[0], pf[1], pf[2], cf, 1, 0,
                                        clamp);
+    if (v0) {
+        cudaError_t e = launch_pbox_ghost_refresh(out, v0, pf, w, st);
+        if (e != cudaSuccess)
+            return e;
+    }
     count_launch(2);
     return cudaGetLastError();
 }

@@ -4,10 +4,20 @@
 // the coarser level: the patch is a box whose one-cell ghost shell holds
 // those values and is never relaxed.  Its FAS hierarchy halves the interior
 // (8-child mean for the iterate and the residual); the coarse boxes carry a
-// ghost shell too, filled once per solve by averaging the fine ghost cells
-// each coarse ghost cell covers.  The coarse iterate and its saved copy share
-// those ghosts, so the coarse correction vanishes there (homogeneous
-// Dirichlet) and the prolongation reads zero across the boundary.
+// ghost shell too.  The saved coarse copy v0 keeps the ghosts filled once per
+// solve by averaging the fine ghost cells each coarse ghost cell covers; the
+// coarse iterate's ghosts follow the boundary condition of the correction
+// below, and the prolongation reads the correction across the boundary.
+//
+// The fine problem fixes its correction to zero at the fine ghost centres,
+// half a fine cell outside the first interior centre.  A coarse ghost centre
+// lies farther out, so on coarse grid l the ghost value of the iterate is
+// refreshed as  v0(g) + w^m (v(a) - v0(a)),  a the nearest interior cell, m the
+// number of axes on which g lies outside, w = -(2^(l-1) - 1/2) / (2^(l-1) + 1/2)
+// (-1/3 on grid 1): the linear extrapolation that puts the zero of the
+// correction at the fine ghost centre.  The prolongation then gives the first
+// fine cell 2/3 of its parent's correction, the linear interpolant between the
+// boundary and the parent centre.
 //
 // Box layout: interior dims (p0, p1, p2), box dims (p + 2), interior index
 // i <-> box index i + 1, C order.  Right-hand sides are interior-indexed.
@@ -74,8 +84,8 @@ __global__ void k_pbox_coarse_rhs(const double *__restrict__ vc, double *__restr
     fc[t] = cell_op(s, cf) + fc[t];
 }
 
-// fine interior += trilinear interpolation of (vc - v0c); the coarse ghosts
-// hold equal values in both, so the correction is zero across the boundary.
+// fine interior += trilinear interpolation of (vc - v0c), ghosts included (the
+// ghost correction is the extrapolated boundary value kept by the refresh).
 __global__ void k_pbox_prolong(const double *__restrict__ vc, const double *__restrict__ v0c, int q0,
                                int q1, int q2, double *__restrict__ vf)
 {
@@ -151,13 +161,55 @@ __global__ void k_pbox_ghosts(const double *__restrict__ fb, int p0, int p1, int
     g3[t] = g;
 }
 
+// ghost refresh of a coarse box: v(g) = v0(g) + w^m (v(a) - v0(a))
+__device__ __forceinline__ void ghost_refresh_cell(double *v, const double *v0, int I, int J, int K,
+                                                   int q0, int q1, int q2, double w)
+{
+    const int d1 = q1 + 2, d2 = q2 + 2;
+    int m = 0;
+    int a0 = I, a1 = J, a2 = K;
+    if (I == 0) { a0 = 1; ++m; } else if (I == q0 + 1) { a0 = q0; ++m; }
+    if (J == 0) { a1 = 1; ++m; } else if (J == q1 + 1) { a1 = q1; ++m; }
+    if (K == 0) { a2 = 1; ++m; } else if (K == q2 + 1) { a2 = q2; ++m; }
+    if (m == 0)
+        return;
+    const double wm = m == 1 ? w : (m == 2 ? w * w : w * w * w);
+    const long long g = bidx(I, J, K, d1, d2), a = bidx(a0, a1, a2, d1, d2);
+    v[g] = v0[g] + wm * (v[a] - v0[a]);
+}
+
+__global__ void k_pbox_ghost_refresh(double *__restrict__ v, const double *__restrict__ v0, int q0,
+                                     int q1, int q2, double w)
+{
+    const long long total = (long long)(q0 + 2) * (q1 + 2) * (q2 + 2);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int K = (int)(t % (q2 + 2));
+    const long long qq = t / (q2 + 2);
+    const int J = (int)(qq % (q1 + 2)), I = (int)(qq / (q1 + 2));
+    ghost_refresh_cell(v, v0, I, J, K, q0, q1, q2, w);
+}
+
 // Coarsest patch grid, one CTA: before each sweep the residual norm; stop at
 // rtol times the first one or after nu_max sweeps.  A -> B (red) -> A (black).
 __global__ void __launch_bounds__(1024)
     k_pbox_coarsest(double *A, double *B, const double *__restrict__ f, int p0, int p1, int p2,
                     CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
-                    int *sweeps_out)
+                    int *sweeps_out, const double *__restrict__ v0, double w)
 {
+    const int nbox = (p0 + 2) * (p1 + 2) * (p2 + 2);
+    // coarse grids keep their ghosts on the extrapolated boundary condition
+    auto refresh = [&](double *X) {
+        if (!v0)
+            return;
+        for (int g = threadIdx.x; g < nbox; g += blockDim.x) {
+            const int K = g % (p2 + 2), J = (g / (p2 + 2)) % (p1 + 2), I = g / ((p1 + 2) * (p2 + 2));
+            ghost_refresh_cell(X, v0, I, J, K, p0, p1, p2, w);
+        }
+        __syncthreads();
+    };
+    refresh(A);
     __shared__ double bc_s;
     const int n3 = p0 * p1 * p2;
     const int d1 = p1 + 2, d2 = p2 + 2;
@@ -201,6 +253,7 @@ __global__ void __launch_bounds__(1024)
                 my_clamps += cl ? 1ull : 0ull;
             }
             __syncthreads();
+            refresh(dst);
         }
     }
     if (my_clamps)
@@ -254,9 +307,19 @@ cudaError_t launch_pbox_ghosts(const double *fine_box, const int p[3], double *g
 
 cudaError_t launch_pbox_coarsest(double *A, double *B, const double *f, const int p[3],
                                  CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
-                                 int *sweeps, cudaStream_t st)
+                                 int *sweeps, cudaStream_t st, const double *v0, double w)
 {
-    k_pbox_coarsest<<<1, 1024, 0, st>>>(A, B, f, p[0], p[1], p[2], cf, nu_max, rtol, clamp, sweeps);
+    k_pbox_coarsest<<<1, 1024, 0, st>>>(A, B, f, p[0], p[1], p[2], cf, nu_max, rtol, clamp, sweeps,
+                                        v0, w);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pbox_ghost_refresh(double *v, const double *v0, const int q[3], double w,
+                                      cudaStream_t st)
+{
+    const long long work = (long long)(q[0] + 2) * (q[1] + 2) * (q[2] + 2);
+    k_pbox_ghost_refresh<<<blocks_for(work), kBlock, 0, st>>>(v, v0, q[0], q[1], q[2], w);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -833,6 +833,13 @@ struct RunPatch {
     double hl[kMaxLevels];
     long long cu = 0;
 
+    // extrapolation weight of the coarse ghosts on grid l >= 1 (see k_patch.cu)
+    static double ghost_w(int l)
+    {
+        const double a = (double)(1 << (l - 1));
+        return -(a - 0.5) / (a + 0.5);
+    }
+
     int sweep(int l)
     {
         mg5_ctx *ctx = this->ctx;
@@ -840,7 +847,8 @@ struct RunPatch {
         {
             ProfScope ps(&ctx->prof, PK_PATCH_SWEEP, st, cells);
             CK(launch_patch_sweep(h->v[l], h->tmp[l], h->f[l], 0.0, h->q[l],
-                                  make_coef<double>(hl[l], p->alpha), &ctx->cnt->clamped, st));
+                                  make_coef<double>(hl[l], p->alpha), &ctx->cnt->clamped, st,
+                                  l > 0 ? h->v0[l] : nullptr, l > 0 ? ghost_w(l) : 0.0));
         }
         std::swap(h->v[l], h->tmp[l]);
         cu += (long long)cells;
@@ -853,7 +861,8 @@ struct RunPatch {
         ProfScope ps(&ctx->prof, PK_COARSEST64, st);
         CK(launch_pbox_coarsest(h->v[l], h->tmp[l], h->f[l], h->q[l],
                                 make_coef<double>(hl[l], p->alpha), p->nu_coarse, kCoarseRtol,
-                                &ctx->cnt->clamped, &ctx->cnt->coarse_sweeps, st));
+                                &ctx->cnt->clamped, &ctx->cnt->coarse_sweeps, st,
+                                l > 0 ? h->v0[l] : nullptr, l > 0 ? ghost_w(l) : 0.0));
         return MG5_OK;
     }
 
@@ -876,6 +885,8 @@ struct RunPatch {
     int coarse_visit(int l)
     {
         mg5_ctx *ctx = this->ctx;
+        // v = v0 on entry: the refresh resets the ghosts to the fixed coarse values
+        CK(launch_pbox_ghost_refresh(h->v[l], h->v0[l], h->q[l], ghost_w(l), st));
         CK(launch_pbox_coarse_rhs(h->v[l], h->f[l], h->q[l], make_coef<double>(hl[l], p->alpha), st));
         if (l == h->nlev - 1)
             return coarsest(l);

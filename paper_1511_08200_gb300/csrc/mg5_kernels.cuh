@@ -103,10 +103,12 @@ cudaError_t launch_force(const double *phi, int d0, int d1, int d2, int ghost, d
                          int periodic, double *grad, cudaStream_t st);
 cudaError_t launch_refine(const double *phic, int nc, const int o[3], const int pn[3], int ghost,
                           double *fine, cudaStream_t st);
-// Dirichlet patch (interior pf, box pf + 2): one full sweep in -> out (out must hold the ghosts)
+// Dirichlet patch (interior pf, box pf + 2): one full sweep in -> out (out must hold the ghosts).
+// With v0 (coarse patch grids) the ghosts of out are refreshed after each half-sweep by the
+// extrapolated boundary condition of weight w (k_patch.cu).
 cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint, double rhs_add,
                                const int pf[3], CoefT<double> cf, unsigned long long *clamp,
-                               cudaStream_t st);
+                               cudaStream_t st, const double *v0 = nullptr, double w = 0.0);
 // partial sums (r, r^2) of r = fint + rhs_add - op(phi) over the interior
 cudaError_t launch_patch_residual(const double *phi, const double *fint, double rhs_add,
                                   const int pf[3], CoefT<double> cf, double2 *partials, int *nblocks,
@@ -124,6 +126,9 @@ cudaError_t launch_pbox_ghosts(const double *fine_box, const int p[3], double *g
                                double *g3, cudaStream_t st);
 cudaError_t launch_pbox_coarsest(double *A, double *B, const double *f, const int p[3],
                                  CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
-                                 int *sweeps, cudaStream_t st);
+                                 int *sweeps, cudaStream_t st, const double *v0 = nullptr,
+                                 double w = 0.0);
+cudaError_t launch_pbox_ghost_refresh(double *v, const double *v0, const int q[3], double w,
+                                      cudaStream_t st);
 
 }  // namespace mg5
