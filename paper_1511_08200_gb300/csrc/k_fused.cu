@@ -3,77 +3,94 @@
 //
 // A CTA owns a TJ x TK tile of (j, k) and marches along i over a chunk of
 // planes, keeping rings of planes in shared memory:
-//   old  : planes p-1 .. p+2 of the input, tile + 2 halo (snapshot values),
+//   old  : planes p-1 .. p+3 of the input, tile + 2 halo (snapshot values),
+//   fr   : the same planes of the right-hand side f,
 //   base : the same planes of the correction base B (mixed precision only),
 //   rnew : planes p-1 .. p+1 of the new red values, tile + 1 halo.
-// At plane p it first relaxes the red cells of plane p+1 (tile + 1 halo, from
+// At plane p it relaxes the red cells of plane p+1 (tile + 1 halo, from
 // `old`), then the black cells of plane p (faces from `rnew`, edges from
-// `old`), and writes both colours of plane p.  Every read of a same-colour
-// neighbour therefore sees the value from before its half-sweep, which is the
-// snapshot red-black sweep the oracle defines; the red halo is recomputed by
-// neighbouring tiles instead of exchanged.  Out of place: `in` and `out` must
-// not alias.  Periodic in i, j, k.
+// `old`), and writes both colours of plane p, while plane p+3 streams into
+// shared memory with cp.async.  Every read of a same-colour neighbour sees
+// the value from before its half-sweep: the snapshot red-black sweep the
+// oracle defines.  The red halo is recomputed by neighbouring tiles instead
+// of exchanged.  Out of place (`in` and `out` must not alias); periodic in
+// i, j, k; n must be a multiple of 16 / sizeof(T) (16-byte row chunks).
 #include "mg5_kernels.cuh"
 
 namespace mg5 {
 
-constexpr int FT_K = 32;           // tile along k (one warp)
-constexpr int FT_J = 16;           // tile along j
-constexpr int FT_THREADS = 256;
-constexpr int OK_ = FT_K + 4;      // old/base plane row length
-constexpr int OJ_ = FT_J + 4;
-constexpr int RK_ = FT_K + 2;      // rnew plane row length
+constexpr int FT_K = 32;                // tile along k
+constexpr int FT_J = 16;                // tile along j
+constexpr int FT_THREADS = 320;         // 306 red cells of the halo'd plane in one round
+constexpr int OROW = FT_K + 8;          // old/base row: k0 - 4 .. k0 + 35 (16-byte chunks)
+constexpr int OJ_ = FT_J + 4;           // rows j0 - 2 .. j0 + 17
+constexpr int OPL = OJ_ * OROW;         // elements of one old plane
+constexpr int RK_ = FT_K + 2;           // rnew row: k0 - 1 .. k0 + 32
 constexpr int RJ_ = FT_J + 2;
-constexpr int OPL = OJ_ * OK_;     // elements of one old plane
 constexpr int RPL = RJ_ * RK_;
+constexpr int NSLOT = 5;                // planes p-1 .. p+3
 
 template <typename T, bool BASE>
 struct FusedSmem {
-    T old[4][OPL];
-    T base[BASE ? 4 : 1][BASE ? OPL : 1];
+    T old[NSLOT][OPL];
+    T fr[NSLOT][OPL];                       // right-hand side planes, same layout
+    T base[BASE ? NSLOT : 1][BASE ? OPL : 1];
     T rnew[3][RPL];
 };
 
-template <typename T>
-__device__ __forceinline__ void load_plane(T *dst, const T *__restrict__ src, int n, int i, int j0,
-                                           int k0)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
-    const int ii = i < 0 ? i + n : (i >= n ? i - n : i);
-    const long long pbase = (long long)ii * n * n;
-    for (int e = threadIdx.x; e < OPL; e += FT_THREADS) {
-        const int jj = e / OK_, kk = e - jj * OK_;
-        int j = j0 - 2 + jj, k = k0 - 2 + kk;
-        j = ((j % n) + n) % n;
-        k = ((k % n) + n) % n;
-        dst[e] = src[pbase + (long long)j * n + k];
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ int wrap1(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+__device__ __forceinline__ int slot5(int q) { return ((q % NSLOT) + NSLOT) % NSLOT; }
+__device__ __forceinline__ int slot3(int q) { return ((q % 3) + 3) % 3; }
+
+// issue the 16-byte copies of plane q (rows j0-2 .. j0+17, k0-4 .. k0+35)
+template <typename T>
+__device__ __forceinline__ void issue_plane(T *dst, const T *__restrict__ src, int n, int q, int j0,
+                                            int k0)
+{
+    constexpr int EPC = 16 / sizeof(T);      // elements per chunk
+    constexpr int CPR = OROW / EPC;          // chunks per row
+    const long long pb = (long long)wrap1(q, n) * n * n;
+    for (int c = threadIdx.x; c < OJ_ * CPR; c += FT_THREADS) {
+        const int r = c / CPR, cc = c - r * CPR;
+        const int j = wrap1(j0 - 2 + r, n);
+        const int k = wrap1(k0 - 4 + cc * EPC, n);
+        cp_async16(dst + r * OROW + cc * EPC, src + pb + (long long)j * n + k);
     }
 }
 
-// gather the 19-point stencil around old-plane coordinates (jj, kk) of plane slot m
+// 19-point stencil around old-plane row jr, column kc
 template <typename T>
-__device__ __forceinline__ void gather_old(const T *pm, const T *p0, const T *pp, int jj, int kk,
+__device__ __forceinline__ void gather_old(const T *pm, const T *p0, const T *pp, int jr, int kc,
                                            St<T> &s)
 {
-    const int c = jj * OK_ + kk;
+    const int c = jr * OROW + kc;
     s.c = p0[c];
     s.xp = pp[c];
     s.xm = pm[c];
-    s.yp = p0[c + OK_];
-    s.ym = p0[c - OK_];
+    s.yp = p0[c + OROW];
+    s.ym = p0[c - OROW];
     s.zp = p0[c + 1];
     s.zm = p0[c - 1];
-    s.xpyp = pp[c + OK_];
-    s.xpym = pp[c - OK_];
-    s.xmyp = pm[c + OK_];
-    s.xmym = pm[c - OK_];
+    s.xpyp = pp[c + OROW];
+    s.xpym = pp[c - OROW];
+    s.xmyp = pm[c + OROW];
+    s.xmym = pm[c - OROW];
     s.xpzp = pp[c + 1];
     s.xpzm = pp[c - 1];
     s.xmzp = pm[c + 1];
     s.xmzm = pm[c - 1];
-    s.ypzp = p0[c + OK_ + 1];
-    s.ypzm = p0[c + OK_ - 1];
-    s.ymzp = p0[c - OK_ + 1];
-    s.ymzm = p0[c - OK_ - 1];
+    s.ypzp = p0[c + OROW + 1];
+    s.ypzm = p0[c + OROW - 1];
+    s.ymzp = p0[c - OROW + 1];
+    s.ymzm = p0[c - OROW - 1];
 }
 
 template <typename T, bool BASE>
@@ -90,56 +107,64 @@ __global__ void __launch_bounds__(FT_THREADS)
     const T cval = (T)(*cptr);
     bool clamped = false;
 
-    // relax the red cells of plane q on the tile + 1 halo into rnew[slot]
+    // red cells of plane q on the tile + 1 halo -> rnew[slot3(q)]
     auto red_plane = [&](int q) {
-        const int sm = ((q - 1) % 4 + 4) % 4, s0 = ((q % 4) + 4) % 4, sp = ((q + 1) % 4 + 4) % 4;
-        T *rn = S.rnew[((q % 3) + 3) % 3];
-        const int qq = q < 0 ? q + n : (q >= n ? q - n : q);
-        for (int e = threadIdx.x; e < RJ_ * (RK_ / 2); e += FT_THREADS) {
+        const T *om = S.old[slot5(q - 1)], *o0 = S.old[slot5(q)], *op = S.old[slot5(q + 1)];
+        T *rn = S.rnew[slot3(q)];
+        const int e = threadIdx.x;
+        if (e < RJ_ * (RK_ / 2)) {
             const int jj = e / (RK_ / 2), pr = e - jj * (RK_ / 2);
-            // red: (q + j + k) even with j = j0 - 1 + jj, k = k0 - 1 + kk
+            // red: (q + j + k) even, j = j0 - 1 + jj, k = k0 - 1 + kk
             const int kk = 2 * pr + ((q + j0 + jj + k0) & 1);
-            int j = j0 - 1 + jj, k = k0 - 1 + kk;
-            j = ((j % n) + n) % n;
-            k = ((k % n) + n) % n;
             St<T> s, sb;
-            gather_old(S.old[sm], S.old[s0], S.old[sp], jj + 1, kk + 1, s);
+            gather_old(om, o0, op, jj + 1, kk + 3, s);
             if constexpr (BASE)
-                gather_old(S.base[sm], S.base[s0], S.base[sp], jj + 1, kk + 1, sb);
-            const T rhs = f[((long long)qq * n + j) * n + k] + cval;
+                gather_old(S.base[slot5(q - 1)], S.base[slot5(q)], S.base[slot5(q + 1)], jj + 1,
+                           kk + 3, sb);
+            const T rhs = S.fr[slot5(q)][(jj + 1) * OROW + kk + 3] + cval;
             rn[jj * RK_ + kk] = upd<T, BASE>(s, sb, rhs, cf, clamped);
         }
     };
 
-    // prologue: old planes i0-2 .. i0+1, red planes i0-1 and i0
+    // prologue: planes i0-2 .. i0+1 (group 1), plane i0+2 (group 2)
     for (int q = i0 - 2; q <= i0 + 1; ++q) {
-        load_plane(S.old[((q % 4) + 4) % 4], in, n, q, j0, k0);
+        issue_plane(S.old[slot5(q)], in, n, q, j0, k0);
+        if (q >= i0 - 1)
+            issue_plane(S.fr[slot5(q)], f, n, q, j0, k0);
         if constexpr (BASE)
-            load_plane(S.base[((q % 4) + 4) % 4], B, n, q, j0, k0);
+            issue_plane(S.base[slot5(q)], B, n, q, j0, k0);
     }
+    cp_async_commit();
+    issue_plane(S.old[slot5(i0 + 2)], in, n, i0 + 2, j0, k0);
+    issue_plane(S.fr[slot5(i0 + 2)], f, n, i0 + 2, j0, k0);
+    if constexpr (BASE)
+        issue_plane(S.base[slot5(i0 + 2)], B, n, i0 + 2, j0, k0);
+    cp_async_commit();
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     __syncthreads();
     red_plane(i0 - 1);
     red_plane(i0);
 
     for (int p = i0; p < i1; ++p) {
-        __syncthreads();  // the slot of plane p-2 is free: black(p-1) has finished
-        load_plane(S.old[((p + 2) % 4)], in, n, p + 2, j0, k0);
+        cp_async_wait_all();   // plane p+2 has landed
+        __syncthreads();       // ... for every thread; iteration p-1 is finished everywhere
+        issue_plane(S.old[slot5(p + 3)], in, n, p + 3, j0, k0);
+        issue_plane(S.fr[slot5(p + 3)], f, n, p + 3, j0, k0);
         if constexpr (BASE)
-            load_plane(S.base[((p + 2) % 4)], B, n, p + 2, j0, k0);
-        __syncthreads();
+            issue_plane(S.base[slot5(p + 3)], B, n, p + 3, j0, k0);
+        cp_async_commit();
         red_plane(p + 1);
         __syncthreads();
-        // black cells of plane p over the tile; each thread owns the pair (2 pr, 2 pr + 1)
-        {
+        // black cells of plane p over the tile; thread -> the pair (2 pr, 2 pr + 1)
+        if (threadIdx.x < FT_J * (FT_K / 2)) {
             const int jj = threadIdx.x / (FT_K / 2), pr = threadIdx.x - jj * (FT_K / 2);
             const int j = j0 + jj, kp0 = k0 + 2 * pr;
-            const int bodd = (p + j + kp0 + 1) & 1;  // 0: black is the first of the pair
+            const int bodd = (p + j + kp0 + 1) & 1;  // 1: the black cell is the second of the pair
             const int kk = 2 * pr + bodd;            // tile-local k of the black cell
-            const T *om = S.old[(p + 3) % 4], *o0 = S.old[p % 4], *op = S.old[(p + 1) % 4];
-            const T *rm = S.rnew[(p + 2) % 3], *r0 = S.rnew[p % 3], *rp = S.rnew[(p + 1) % 3];
-            // faces (red, new) from rnew; edges (black, old) from old
-            const int cr = (jj + 1) * RK_ + (kk + 1);
-            const int co = (jj + 2) * OK_ + (kk + 2);
+            const T *om = S.old[slot5(p - 1)], *o0 = S.old[slot5(p)], *op = S.old[slot5(p + 1)];
+            const T *rm = S.rnew[slot3(p - 1)], *r0 = S.rnew[slot3(p)], *rp = S.rnew[slot3(p + 1)];
+            const int cr = (jj + 1) * RK_ + (kk + 1);   // rnew coordinates of the black cell
+            const int co = (jj + 2) * OROW + (kk + 4);  // old coordinates
             St<T> s;
             s.c = o0[co];
             s.xp = rp[cr];
@@ -148,53 +173,58 @@ __global__ void __launch_bounds__(FT_THREADS)
             s.ym = r0[cr - RK_];
             s.zp = r0[cr + 1];
             s.zm = r0[cr - 1];
-            s.xpyp = op[co + OK_];
-            s.xpym = op[co - OK_];
-            s.xmyp = om[co + OK_];
-            s.xmym = om[co - OK_];
+            s.xpyp = op[co + OROW];
+            s.xpym = op[co - OROW];
+            s.xmyp = om[co + OROW];
+            s.xmym = om[co - OROW];
             s.xpzp = op[co + 1];
             s.xpzm = op[co - 1];
             s.xmzp = om[co + 1];
             s.xmzm = om[co - 1];
-            s.ypzp = o0[co + OK_ + 1];
-            s.ypzm = o0[co + OK_ - 1];
-            s.ymzp = o0[co - OK_ + 1];
-            s.ymzm = o0[co - OK_ - 1];
+            s.ypzp = o0[co + OROW + 1];
+            s.ypzm = o0[co + OROW - 1];
+            s.ymzp = o0[co - OROW + 1];
+            s.ymzm = o0[co - OROW - 1];
             St<T> sb;
             if constexpr (BASE)
-                gather_old(S.base[(p + 3) % 4], S.base[p % 4], S.base[(p + 1) % 4], jj + 2, kk + 2, sb);
+                gather_old(S.base[slot5(p - 1)], S.base[slot5(p)], S.base[slot5(p + 1)], jj + 2,
+                           kk + 4, sb);
             if (j < n && kp0 < n) {
                 const long long row = ((long long)p * n + j) * n;
-                const T vb = upd<T, BASE>(s, sb, f[row + k0 + kk] + cval, cf, clamped);
+                const T vb = upd<T, BASE>(s, sb, S.fr[slot5(p)][co] + cval, cf, clamped);
                 const T vr = r0[(jj + 1) * RK_ + (2 * pr + 1 - bodd) + 1];
-                T v0 = bodd ? vr : vb;
-                T v1 = bodd ? vb : vr;
+                const T v0 = bodd ? vr : vb;
+                const T v1 = bodd ? vb : vr;
                 if constexpr (sizeof(T) == 4) {
-                    float2 w;
-                    w.x = (float)v0;
-                    w.y = (float)v1;
-                    *reinterpret_cast<float2 *>(out + row + kp0) = w;
+                    *reinterpret_cast<float2 *>(out + row + kp0) = make_float2((float)v0, (float)v1);
                 } else {
-                    double2 w;
-                    w.x = (double)v0;
-                    w.y = (double)v1;
-                    *reinterpret_cast<double2 *>(out + row + kp0) = w;
+                    *reinterpret_cast<double2 *>(out + row + kp0) = make_double2((double)v0, (double)v1);
                 }
             }
         }
     }
+    cp_async_wait_all();
     if (clamped)
         atomicAdd(clamp, 1ull);
+}
+
+// the fused kernel needs 16-byte row chunks: n a multiple of 16 / sizeof(T)
+template <typename T>
+bool fused_ok(int n)
+{
+    return n >= kFusedMinN && n % (int)(16 / sizeof(T)) == 0;
 }
 
 template <typename T>
 cudaError_t launch_sweep_fused(const T *in, T *out, const T *f, const double *cptr, int n,
                                CoefT<T> cf, unsigned long long *clamp, cudaStream_t st, const T *B)
 {
+    if (!fused_ok<T>(n))
+        return launch_sweep<T>(in, out, f, cptr, n, cf, clamp, st, B);
     const int tk = (n + FT_K - 1) / FT_K, tj = (n + FT_J - 1) / FT_J;
     const int tiles = tk * tj;
-    // enough CTAs to fill 152 SMs several times over, chunks of at least 8 planes
-    int chunks = (4 * 152 + tiles - 1) / tiles;
+    // enough CTAs for several waves over 152 SMs, chunks of at least 8 planes
+    int chunks = (8 * 152 + tiles - 1) / tiles;
     if (chunks > n / 8)
         chunks = n / 8;
     if (chunks < 1)
@@ -202,20 +232,26 @@ cudaError_t launch_sweep_fused(const T *in, T *out, const T *f, const double *cp
     const int ichunk = (n + chunks - 1) / chunks;
     chunks = (n + ichunk - 1) / ichunk;
     dim3 grid(tk, tj, chunks);
-    cudaError_t e;
+    static bool attr_set[2] = {false, false};
     if (B) {
         const size_t sm = sizeof(FusedSmem<T, true>);
-        e = cudaFuncSetAttribute(k_sweep_fused<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm);
-        if (e != cudaSuccess)
-            return e;
+        if (!attr_set[1]) {
+            cudaError_t e = cudaFuncSetAttribute(k_sweep_fused<T, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess)
+                return e;
+            attr_set[1] = true;
+        }
         k_sweep_fused<T, true><<<grid, FT_THREADS, sm, st>>>(in, out, f, B, cptr, n, ichunk, cf, clamp);
     } else {
         const size_t sm = sizeof(FusedSmem<T, false>);
-        e = cudaFuncSetAttribute(k_sweep_fused<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm);
-        if (e != cudaSuccess)
-            return e;
+        if (!attr_set[0]) {
+            cudaError_t e = cudaFuncSetAttribute(k_sweep_fused<T, false>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess)
+                return e;
+            attr_set[0] = true;
+        }
         k_sweep_fused<T, false><<<grid, FT_THREADS, sm, st>>>(in, out, f, B, cptr, n, ichunk, cf, clamp);
     }
     count_launch(1);

@@ -169,8 +169,10 @@ __device__ __forceinline__ T cell_op(const St<T> &s, const CoefT<T> &cf)
 // Sigma(., .) the symmetric bilinear form of Sigma.  Sigma(B, e) and
 // Sigma(e) do not depend on e_ijk, so the cell equation is again a quadratic
 // in L_e:  (2 alpha/3) L_e^2 + beta' L_e - b' = 0, beta' = 1 + (4 alpha/3) L_B,
-// b' = rhs + alpha (2 Sigma(B, e) + Sigma(e)), physical root
-// L_e = 2 b' / (beta' + sqrt(beta'^2 + 8 alpha b' / 3)).
+// b' = rhs + alpha (2 Sigma(B, e) + Sigma(e)), physical root (the one that
+// makes L_B + L_e the physical root of the full equation)
+// L_e = (sqrt(D) - beta') / (4 alpha / 3) = 2 b' / (beta' + sqrt(D)),
+// D = beta'^2 + 8 alpha b' / 3; the second form for beta' >= 0, the first otherwise.
 template <typename T>
 struct Parts {
     T S, a, b, c, dxy, dxz, dyz;  // S = faces; a,b,c = sx-sy, sx-sz, sy-sz
@@ -212,7 +214,10 @@ __device__ __forceinline__ T cell_update_corr(const St<T> &e, const St<T> &B, T 
         disc = (T)0;
         clamped = true;
     }
-    const T L = (T)2 * b / (bp + sqrt(disc));
+    // the same root in the form without cancellation for either sign of beta'
+    // (beta' < 0 needs alpha > 0, so k23 > 0 there)
+    const T sq = sqrt(disc);
+    const T L = bp >= (T)0 ? (T)2 * b / (bp + sq) : (sq - bp) / ((T)2 * cf.k23);
     return (pe.S - cf.h2 * L) * (T)(1.0 / 6.0);
 }
 

@@ -158,14 +158,34 @@ def test_sweep_fp32_plain(ctx, n, fused):
     assert np.abs(got - ref).max() < 2e-6 * np.abs(ref).max()
 
 
+def _base_field(n, seed, rough):
+    """A physical base: the linear (alpha = 0) potential of s delta, for which
+    1 + (4 alpha / 3) L_B = 1 + (4/3) eps delta stays positive (the physical branch)."""
+    from tests import _pins
+    alpha, s, h = nominal()
+    delta = workload.lognormal_delta(n, 1.0 + 0.5 * rough, seed)
+    B = _pins.fft_poisson(s * delta, h)
+    beta = 1 + 4 * alpha / 3 * _pins_lap(B, h)
+    assert beta.min() > 0.2, beta.min()
+    return B
+
+
+def _pins_lap(phi, h):
+    out = -6.0 * phi
+    for a in range(3):
+        out += np.roll(phi, 1, axis=a) + np.roll(phi, -1, axis=a)
+    return out / h ** 2
+
+
 @pytest.mark.parametrize("n", [8, 34, 64])
 @pytest.mark.parametrize("fused", [False, True])
-def test_sweep_fp32_correction_form(ctx, n, fused):
+@pytest.mark.parametrize("rough", [0.0, 1.0])
+def test_sweep_fp32_correction_form(ctx, n, fused, rough):
     """With a base B, the FP32 sweep relaxes e in op(B + e) - op(B) = f + c: it must
     equal the oracle's FP64 sweep of u = B + e with right-hand side op(B) + f, minus B."""
     alpha, s, h = nominal()
-    B = _field(n, 25)
-    e = 1e-3 * _field(n, 26)
+    B = _base_field(n, 25, rough)
+    e = 1e-3 * B * (1.0 + 0.1 * workload.lognormal_delta(n, 1.0, 26))
     rhs = 1e-3 * s * 5.0 * workload.lognormal_delta(n, 1.0, 27)
     c = 3e-13
     got = host(ctx.step_sweep_f32(_f32(e), _f32(rhs), c, h, alpha, base=_f32(B),
@@ -181,8 +201,8 @@ def test_sweep_fp32_correction_form(ctx, n, fused):
 @pytest.mark.parametrize("n", [32, 48, 64, 96])
 def test_fused_matches_two_pass_fp32(ctx, n):
     alpha, s, h = nominal()
-    B = _field(n, 28)
-    e = 1e-2 * _field(n, 29)
+    B = _base_field(n, 28, 1.0)
+    e = 1e-2 * B * (1.0 + 0.1 * workload.lognormal_delta(n, 1.0, 29))
     rhs = 1e-2 * s * workload.lognormal_delta(n, 1.0, 30)
     a = host(ctx.step_sweep_f32(_f32(e), _f32(rhs), 0.0, h, alpha, base=_f32(B), fused=False))
     b = host(ctx.step_sweep_f32(_f32(e), _f32(rhs), 0.0, h, alpha, base=_f32(B), fused=True))
