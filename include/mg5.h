@@ -204,6 +204,23 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_fine, const int pf[3],
                     const mg5_params *p, double compat_c, double *phi_fine,
                     mg5_info *info, void *stream);
 
+/*
+ * Solve many independent boxes in one call (batching).  Box i has side N[i],
+ * density delta[i], parameters p[i], output phi[i] and, if grad is not NULL,
+ * grad[i] (all device buffers, layouts as in mg5_solve_fifth_force; phi starts
+ * from zero).  When every box is MG5_MIXED the whole batch is ONE CUDA graph
+ * launch: a branch per box, each a WHILE loop of FP64 defect-correction steps
+ * around FP32 V-cycles whose continuation a device kernel decides, so boxes
+ * converge independently and overlap on the GPU with no host round trip.  The
+ * graph and the per-box hierarchies stay resident and are reused while the
+ * sizes, parameters and pointers are unchanged.  Otherwise the boxes are
+ * solved one after another.  info: nbox entries or NULL.  Returns the worst
+ * status over the boxes; synchronises `stream` once.
+ */
+int mg5_solve_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const int *N,
+                    const mg5_params *p, double *const *phi, double *const *grad, mg5_info *info,
+                    void *stream);
+
 /* ------------------------------------------------------------ tracing
  * Per-kernel-class device time, measured with CUDA events recorded on the
  * launching stream around each launch (off by default).  enable() also

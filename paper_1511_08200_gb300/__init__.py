@@ -87,6 +87,7 @@ _sigs = {
     "mg5_force": ([_P, _P, _I3, _c_int, _c_double, _c_int, _P, _P], _c_int),
     "mg5_refine_interpolate": ([_P, _P, _c_int, _I3, _I3, _c_int, _P, _P], _c_int),
     "mg5_relax_patch": ([_P, _P, _I3, _P, _c_double, _P, _P, _P], _c_int),
+    "mg5_solve_batch": ([_P, _c_int, _P, _P, _P, _P, _P, _P, _P], _c_int),
     "mg5_profile_enable": ([_P, _c_int], _c_int),
     "mg5_profile_read": ([_P, _P, _P, _c_int], _c_int),
     "mg5_profile_name": ([_c_int], ctypes.c_char_p),
@@ -258,6 +259,28 @@ class Context:
         if raise_on_status:
             self._check(rc, (OK, W_DISC_CLAMP))
         return phi, grad, Info._from(info)
+
+    def solve_batch(self, deltas, params, phis=None, grads=None, stream=None, raise_on_status=True):
+        """mg5_solve_batch: deltas / params / phis / grads are per-box lists (device
+        tensors; params a list of Params or one Params for all).  Returns (phis, grads, infos)."""
+        import torch
+        nb = len(deltas)
+        if isinstance(params, Params):
+            params = [params] * nb
+        if phis is None:
+            phis = [torch.zeros_like(d) for d in deltas]
+        P = ctypes.c_void_p * nb
+        parr = (Params * nb)(*params)
+        narr = (_c_int * nb)(*[int(d.shape[0]) for d in deltas])
+        garr = P(*[_ptr(g) for g in grads]) if grads is not None else None
+        infos = (_Info * nb)()
+        rc = _lib.mg5_solve_batch(self._h, nb, P(*[_ptr(d) for d in deltas]), narr, parr,
+                                  P(*[_ptr(x) for x in phis]), garr, infos, _stream(stream))
+        if raise_on_status:
+            self._check(rc, (OK, W_DISC_CLAMP))
+        elif rc in (E_ARG, E_OOM, E_CUDA):
+            self._check(rc)
+        return phis, grads, [Info._from(i) for i in infos]
 
     def force(self, phi, h: float, ghost: int = 0, periodic: bool = True, grad=None, stream=None):
         import torch

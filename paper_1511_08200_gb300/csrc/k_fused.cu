@@ -232,30 +232,36 @@ cudaError_t launch_sweep_fused(const T *in, T *out, const T *f, const double *cp
     const int ichunk = (n + chunks - 1) / chunks;
     chunks = (n + ichunk - 1) / ichunk;
     dim3 grid(tk, tj, chunks);
-    static bool attr_set[2] = {false, false};
-    if (B) {
-        const size_t sm = sizeof(FusedSmem<T, true>);
-        if (!attr_set[1]) {
-            cudaError_t e = cudaFuncSetAttribute(k_sweep_fused<T, true>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess)
-                return e;
-            attr_set[1] = true;
-        }
-        k_sweep_fused<T, true><<<grid, FT_THREADS, sm, st>>>(in, out, f, B, cptr, n, ichunk, cf, clamp);
-    } else {
-        const size_t sm = sizeof(FusedSmem<T, false>);
-        if (!attr_set[0]) {
-            cudaError_t e = cudaFuncSetAttribute(k_sweep_fused<T, false>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess)
-                return e;
-            attr_set[0] = true;
-        }
-        k_sweep_fused<T, false><<<grid, FT_THREADS, sm, st>>>(in, out, f, B, cptr, n, ichunk, cf, clamp);
-    }
+    // the shared-memory limits were raised by prepare_fused_kernels() at context creation
+    if (B)
+        k_sweep_fused<T, true><<<grid, FT_THREADS, sizeof(FusedSmem<T, true>), st>>>(
+            in, out, f, B, cptr, n, ichunk, cf, clamp);
+    else
+        k_sweep_fused<T, false><<<grid, FT_THREADS, sizeof(FusedSmem<T, false>), st>>>(
+            in, out, f, B, cptr, n, ichunk, cf, clamp);
     count_launch(1);
     return cudaGetLastError();
+}
+
+// set the dynamic shared-memory limits once, outside any stream capture
+cudaError_t prepare_fused_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_fused<float, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(FusedSmem<float, true>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep_fused<float, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(FusedSmem<float, false>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep_fused<double, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(FusedSmem<double, true>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep_fused<double, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(FusedSmem<double, false>));
+    return e;
 }
 
 template cudaError_t launch_sweep_fused<float>(const float *, float *, const float *, const double *,

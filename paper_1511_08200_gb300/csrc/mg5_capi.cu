@@ -106,6 +106,26 @@ size_t fp64_bytes(int N)
 
 }  // namespace
 
+// A captured batch: one graph with a branch per box (its own hierarchy,
+// scalars and partial sums), each branch a WHILE loop of defect-correction
+// steps whose condition a device kernel sets.
+struct BatchSet {
+    int nbox = 0;
+    std::vector<int> N;
+    std::vector<mg5_params> prm;
+    std::vector<const double *> delta;
+    std::vector<double *> phi, grad;
+    std::vector<MixedHier *> hier;
+    std::vector<double2 *> partials;
+    std::vector<LevelScal *> ls;
+    std::vector<SolveCounters *> cnt;
+    BoxCtl *ctl = nullptr;
+    std::vector<CaptureStats> stats;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t bytes = 0;
+};
+
 struct mg5_ctx {
     int device = 0;
     size_t budget = 0;
@@ -114,6 +134,7 @@ struct mg5_ctx {
     std::vector<Hier *> hiers;
     std::vector<MixedHier *> mixed;
     std::vector<PatchHier *> patches;
+    BatchSet *batch = nullptr;
     double2 *partials = nullptr;
     LevelScal *ls = nullptr;        // kScalSlots slots
     SolveCounters *cnt = nullptr;
@@ -266,6 +287,33 @@ static int get_patch(mg5_ctx *ctx, const int p[3], PatchHier **out)
     ctx->patches.push_back(h);
     *out = h;
     return MG5_OK;
+}
+
+static void free_batch(mg5_ctx *ctx)
+{
+    BatchSet *b = ctx->batch;
+    if (!b)
+        return;
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    if (b->graph)
+        cudaGraphDestroy(b->graph);
+    for (MixedHier *m : b->hier)
+        free_mixed(m, &ctx->held);
+    for (double2 *p : b->partials)
+        if (p)
+            cudaFree(p);
+    for (LevelScal *p : b->ls)
+        if (p)
+            cudaFree(p);
+    for (SolveCounters *p : b->cnt)
+        if (p)
+            cudaFree(p);
+    if (b->ctl)
+        cudaFree(b->ctl);
+    ctx->held -= b->bytes;
+    delete b;
+    ctx->batch = nullptr;
 }
 
 static int ensure_buffer(mg5_ctx *ctx, double **buf, size_t *have, size_t need)
@@ -598,6 +646,8 @@ int mg5_create(mg5_ctx **out, int device, size_t budget)
         e = cudaEventCreate(&ctx->ev0);
     if (e == cudaSuccess)
         e = cudaEventCreate(&ctx->ev1);
+    if (e == cudaSuccess)
+        e = prepare_fused_kernels();
     if (e != cudaSuccess) {
         cudaGetLastError();
         mg5_destroy(ctx);
@@ -622,6 +672,7 @@ int mg5_release(mg5_ctx *ctx)
     for (PatchHier *ph : ctx->patches)
         free_patch(ctx, ph);
     ctx->patches.clear();
+    free_batch(ctx);
     ctx_free(ctx, ctx->stage, ctx->stage_bytes);
     ctx->stage = nullptr;
     ctx->stage_bytes = 0;
@@ -1016,6 +1067,218 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
         info->compat_c = compat_c;
     }
     return status;
+}
+
+static bool same_params(const mg5_params &a, const mg5_params &b)
+{
+    return std::memcmp(&a, &b, sizeof(mg5_params)) == 0;
+}
+
+static bool batch_matches(const BatchSet *b, int nbox, const double *const *delta, const int *N,
+                          const mg5_params *p, double *const *phi, double *const *grad)
+{
+    if (!b || b->nbox != nbox)
+        return false;
+    for (int i = 0; i < nbox; ++i)
+        if (b->N[i] != N[i] || !same_params(b->prm[i], p[i]) || b->delta[i] != delta[i] ||
+            b->phi[i] != phi[i] || b->grad[i] != (grad ? grad[i] : nullptr))
+            return false;
+    return true;
+}
+
+static int build_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const int *N,
+                       const mg5_params *p, double *const *phi, double *const *grad)
+{
+    free_batch(ctx);
+    BatchSet *b = new BatchSet();
+    ctx->batch = b;
+    b->nbox = nbox;
+    b->N.assign(N, N + nbox);
+    b->prm.assign(p, p + nbox);
+    b->delta.assign(delta, delta + nbox);
+    b->phi.assign(phi, phi + nbox);
+    b->grad.resize(nbox);
+    for (int i = 0; i < nbox; ++i)
+        b->grad[i] = grad ? grad[i] : nullptr;
+    const size_t per_box = sizeof(double2) * kMaxPartials + sizeof(LevelScal) * kScalSlots +
+                           sizeof(SolveCounters);
+    b->bytes = per_box * nbox + sizeof(BoxCtl) * nbox;
+    if (ctx->budget && ctx->held + b->bytes > ctx->budget) {
+        ctx->err = "batch scratch would exceed the context's HBM budget";
+        free_batch(ctx);
+        return MG5_E_OOM;
+    }
+    ctx->held += b->bytes;
+    b->hier.assign(nbox, nullptr);
+    b->partials.assign(nbox, nullptr);
+    b->ls.assign(nbox, nullptr);
+    b->cnt.assign(nbox, nullptr);
+    b->stats.assign(nbox, CaptureStats{});
+    CK(cudaMalloc((void **)&b->ctl, sizeof(BoxCtl) * nbox));
+    for (int i = 0; i < nbox; ++i) {
+        int rc = alloc_mixed(N[i], ctx->budget, &ctx->held, &b->hier[i], &ctx->err);
+        if (rc != MG5_OK) {
+            free_batch(ctx);
+            return rc;
+        }
+        CK(cudaMalloc((void **)&b->partials[i], sizeof(double2) * kMaxPartials));
+        CK(cudaMalloc((void **)&b->ls[i], sizeof(LevelScal) * kScalSlots));
+        CK(cudaMalloc((void **)&b->cnt[i], sizeof(SolveCounters)));
+    }
+    // capture: fork one branch per box off a private origin stream
+    cudaStream_t origin = nullptr, body = nullptr;
+    std::vector<cudaStream_t> br(nbox, nullptr);
+    std::vector<cudaEvent_t> join(nbox, nullptr);
+    cudaEvent_t fork = nullptr;
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : join)
+            if (e)
+                cudaEventDestroy(e);
+        for (cudaStream_t q : br)
+            if (q)
+                cudaStreamDestroy(q);
+        if (fork)
+            cudaEventDestroy(fork);
+        if (body)
+            cudaStreamDestroy(body);
+        if (origin)
+            cudaStreamDestroy(origin);
+    };
+    const bool prof_on = ctx->prof.on;
+    ctx->prof.on = false;   // event records are not allowed inside loop bodies
+    const long long launches_before = launches_total();
+    int rc = MG5_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int i = 0; i < nbox && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(fork, origin);
+    for (int i = 0; i < nbox && e == cudaSuccess && rc == MG5_OK; ++i) {
+        e = cudaStreamWaitEvent(br[i], fork, 0);
+        if (e != cudaSuccess)
+            break;
+        MixedShared sh{b->partials[i], b->ls[i], b->cnt[i], ctx->h_rel, nullptr};
+        rc = capture_mixed(b->hier[i], sh, delta[i], &p[i], phi[i], b->grad[i], b->ctl + i, br[i],
+                           body, &b->stats[i], &ctx->err);
+        if (rc == MG5_OK) {
+            e = cudaEventRecord(join[i], br[i]);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(origin, join[i], 0);
+        }
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(origin, &g);
+    if (e == cudaSuccess)
+        e = e2;
+    ctx->prof.on = prof_on;
+    count_launch(launches_before - launches_total());   // captured, not enqueued
+    if (rc == MG5_OK && e == cudaSuccess) {
+        b->graph = g;
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+    } else if (g) {
+        cudaGraphDestroy(g);
+    }
+    cleanup();
+    if (rc != MG5_OK) {
+        free_batch(ctx);
+        return rc;
+    }
+    if (e != cudaSuccess) {
+        ctx->err = std::string("batch graph: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        free_batch(ctx);
+        return MG5_E_CUDA;
+    }
+    return MG5_OK;
+}
+
+int mg5_solve_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const int *N,
+                    const mg5_params *p, double *const *phi, double *const *grad, mg5_info *info,
+                    void *stream)
+{
+    if (!ctx || nbox < 1 || !delta || !N || !p || !phi)
+        return MG5_E_ARG;
+    bool all_mixed = true;
+    for (int i = 0; i < nbox; ++i) {
+        if (!delta[i] || !phi[i])
+            return MG5_E_ARG;
+        RET(check_size(N[i]));
+        RET(check_params(&p[i]));
+        all_mixed = all_mixed && p[i].precision == MG5_MIXED;
+    }
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (info)
+        std::memset(info, 0, sizeof(mg5_info) * nbox);
+    if (!all_mixed) {
+        // FP64 boxes: one host-driven solve after the other on the caller's stream
+        int worst = MG5_OK;
+        for (int i = 0; i < nbox; ++i) {
+            int rc = mg5_solve_fifth_force(ctx, delta[i], N[i], &p[i], 0, phi[i],
+                                           grad ? grad[i] : nullptr, info ? info + i : nullptr,
+                                           stream);
+            if (rc == MG5_E_CUDA || rc == MG5_E_ARG || rc == MG5_E_OOM)
+                return rc;
+            if (rc < 0 || (worst == MG5_OK && rc > 0))
+                worst = rc;
+        }
+        return worst;
+    }
+    if (!batch_matches(ctx->batch, nbox, delta, N, p, phi, grad))
+        RET(build_batch(ctx, nbox, delta, N, p, phi, grad));
+    BatchSet *b = ctx->batch;
+    CK(cudaEventRecord(ctx->ev0, st));
+    CK(cudaGraphLaunch(b->exec, st));
+    CK(cudaEventRecord(ctx->ev1, st));
+    std::vector<BoxCtl> ctl(nbox);
+    CK(cudaMemcpyAsync(ctl.data(), b->ctl, sizeof(BoxCtl) * nbox, cudaMemcpyDeviceToHost, st));
+    std::vector<SolveCounters> cnt(nbox);
+    std::vector<LevelScal> ls0(nbox);
+    for (int i = 0; i < nbox; ++i) {
+        CK(cudaMemcpyAsync(&cnt[i], b->cnt[i], sizeof(SolveCounters), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&ls0[i], b->ls[i], sizeof(LevelScal), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    int worst = MG5_OK;
+    for (int i = 0; i < nbox; ++i) {
+        const CaptureStats &cs = b->stats[i];
+        count_launch(cs.launches_fixed + cs.launches_per_iter * ctl[i].outer);
+        int status = ctl[i].status;
+        if (status == MG5_OK && cnt[i].clamped > 0)
+            status = MG5_W_DISC_CLAMP;
+        if (status < 0 || (worst == MG5_OK && status > 0))
+            worst = status;
+        if (info) {
+            mg5_info &o = info[i];
+            o.status = status;
+            o.outer_iters = ctl[i].outer;
+            o.cycles = ctl[i].outer * cs.inner;
+            o.levels = b->hier[i]->nlev;
+            o.coarsest_n = b->hier[i]->n[o.levels - 1];
+            o.n_history = ctl[i].nhist;
+            for (int k = 0; k < ctl[i].nhist && k < 64; ++k)
+                o.history[k] = ctl[i].hist[k];
+            o.rel_residual = ctl[i].rel;
+            o.compat_c = ls0[i].c;
+            o.phi_mean_removed = ls0[i].mean;
+            o.disc_clamped = (long long)cnt[i].clamped;
+            const long long nc = o.coarsest_n;
+            o.cell_updates = cs.cells_per_iter * ctl[i].outer + (long long)cnt[i].coarse_sweeps * nc * nc * nc;
+            o.ms_total = ms;
+        }
+    }
+    return worst;
 }
 
 int mg5_step_sweep(mg5_ctx *ctx, const double *in, double *out, const double *f, double c, int N,

@@ -60,6 +60,7 @@ cudaError_t launch_sweep_fused(const T *in, T *out, const T *f, const double *cp
                                CoefT<T> cf, unsigned long long *clamp, cudaStream_t st,
                                const T *B = nullptr);
 constexpr int kFusedMinN = 32;   // smaller grids use the two-pass sweep
+cudaError_t prepare_fused_kernels();
 template <typename T>
 cudaError_t launch_operator(const T *phi, int n, CoefT<T> cf, T *out, cudaStream_t st);
 // r (nullable) = f + c - op(phi); partial sums (sum r, sum r^2) per block.

@@ -265,9 +265,8 @@ int alloc_mixed(int N, size_t budget, size_t *held, MixedHier **out, std::string
     return MG5_OK;
 }
 
-int solve_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const mg5_params *p,
-                double *phi, mg5_info *info, cudaStream_t st, std::string *err)
-{
+// ---------------------------------------------------------------- phases
+
 #define CKM(call)                                                           \
     do {                                                                    \
         cudaError_t e_ = (call);                                            \
@@ -276,33 +275,102 @@ int solve_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const 
             return MG5_E_CUDA;                                              \
         }                                                                   \
     } while (0)
-    const int N = h->N;
-    const long long n3 = (long long)N * N * N;
-    RunMix R{h, sh, p, st, err, {}, 0};
-    for (int l = 0; l < h->nlev; ++l)
-        R.hl[l] = p->h * (double)(1 << l);
-    const int inner = p->inner_cycles > 0 ? p->inner_cycles : 3;
+
+namespace {
+
+// f64 = s delta, ||f64||, scalars and counters cleared
+int phase_setup(MixedHier *h, const MixedShared &sh, const double *delta, const mg5_params *p,
+                cudaStream_t st, std::string *err)
+{
+    const long long n3 = (long long)h->N * h->N * h->N;
     CKM(cudaMemsetAsync(sh.ls, 0, sizeof(LevelScal) * kScalSlots, st));
     CKM(cudaMemsetAsync(sh.cnt, 0, sizeof(SolveCounters), st));
     int nb = 0;
     CKM(launch_scale(delta, p->s, h->f64, n3, sh.partials, &nb, st));
     CKM(launch_finalize(sh.partials, nb, (double)n3, sh.ls, FIN_FNORM, st));
-    const CoefT<double> cf64 = make_coef<double>(p->h, p->alpha);
+    return MG5_OK;
+}
+
+// r32 = fp32(s delta + c - op(phi)) and B = fp32(phi) in FP64 arithmetic; stats of r
+int phase_residual(MixedHier *h, const MixedShared &sh, const mg5_params *p, double *phi,
+                   cudaStream_t st, std::string *err)
+{
+    const int N = h->N;
+    const long long n3 = (long long)N * N * N;
     int grid = blocks_for(n3);
     if (grid > kMaxPartials)
         grid = kMaxPartials;
+    {
+        ProfScope ps(sh.prof, PK_RESID64_MIXED, st, (double)n3);
+        k_resid64_mixed<<<grid, kBlock, 0, st>>>(phi, h->f64, &sh.ls[0].c, N,
+                                                  make_coef<double>(p->h, p->alpha), h->f[0],
+                                                  h->B[0], sh.partials);
+    }
+    count_launch(1);
+    CKM(cudaGetLastError());
+    CKM(launch_finalize(sh.partials, grid, (double)n3, sh.ls, FIN_STATS, st));
+    return MG5_OK;
+}
+
+// restrict the base, `inner` FP32 V-cycles on the correction, phi += e, c += c_e
+int phase_work(RunMix &R, double *phi, int inner, std::string *err)
+{
+    MixedHier *h = R.h;
+    const MixedShared &sh = R.sh;
+    cudaStream_t st = R.st;
+    const long long n3 = (long long)h->N * h->N * h->N;
+    for (int l = 1; l < h->nlev; ++l)
+        CKM(launch_restrict<float>(h->B[l - 1], h->n[l - 1], h->B[l], st));
+    CKM(cudaMemsetAsync(h->e[0], 0, n3 * sizeof(float), st));
+    k_scal<<<1, 1, 0, st>>>(sh.ls, R.ls(0), 1);  // inner c = -m
+    count_launch(1);
+    CKM(cudaGetLastError());
+    for (int it = 0; it < inner; ++it)
+        if (int rc = R.vcycle0())
+            return rc;
+    {
+        ProfScope ps(sh.prof, PK_UPDATE_MIXED, st, (double)n3);
+        k_update_mixed<<<blocks_for(n3), kBlock, 0, st>>>(phi, h->e[0], n3);
+    }
+    count_launch(1);
+    CKM(cudaGetLastError());
+    k_scal<<<1, 1, 0, st>>>(sh.ls, R.ls(0), 2);  // c += c_e
+    count_launch(1);
+    CKM(cudaGetLastError());
+    return MG5_OK;
+}
+
+// report the projected c, gauge phi to mean zero
+int phase_finish(MixedHier *h, const MixedShared &sh, double *phi, cudaStream_t st, std::string *err)
+{
+    const long long n3 = (long long)h->N * h->N * h->N;
+    k_scal<<<1, 1, 0, st>>>(sh.ls, sh.ls, 0);
+    count_launch(1);
+    CKM(cudaGetLastError());
+    int nb = 0;
+    CKM(launch_sum(phi, n3, sh.partials, &nb, st));
+    CKM(launch_finalize(sh.partials, nb, (double)n3, sh.ls, FIN_MEAN, st));
+    CKM(launch_sub_mean(phi, n3, &sh.ls[0].mean, st));
+    return MG5_OK;
+}
+
+}  // namespace
+
+int solve_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const mg5_params *p,
+                double *phi, mg5_info *info, cudaStream_t st, std::string *err)
+{
+    RunMix R{h, sh, p, st, err, {}, 0};
+    for (int l = 0; l < h->nlev; ++l)
+        R.hl[l] = p->h * (double)(1 << l);
+    const int inner = p->inner_cycles > 0 ? p->inner_cycles : 3;
+    if (int rc = phase_setup(h, sh, delta, p, st, err))
+        return rc;
     int status = MG5_E_NOT_CONVERGED;
     double best = INFINITY;
-    int outer = 0, inner_total = 0;
+    int outer = 0;
     for (;; ++outer) {
-        {
-            ProfScope ps(sh.prof, PK_RESID64_MIXED, st, (double)n3);
-            k_resid64_mixed<<<grid, kBlock, 0, st>>>(phi, h->f64, &sh.ls[0].c, N, cf64, h->f[0], h->B[0],
-                                                      sh.partials);
-        }
-        count_launch(1);
-        CKM(cudaGetLastError());
-        CKM(launch_finalize(sh.partials, grid, (double)n3, sh.ls, FIN_STATS, st));
+        if (int rc = phase_residual(h, sh, p, phi, st, err))
+            return rc;
         CKM(cudaMemcpyAsync(sh.h_rel, &sh.ls[0].rel, sizeof(double), cudaMemcpyDeviceToHost, st));
         CKM(cudaStreamSynchronize(st));
         const double rel = *sh.h_rel;
@@ -330,43 +398,146 @@ int solve_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const 
             status = MG5_E_NOT_CONVERGED;
             break;
         }
-        for (int l = 1; l < h->nlev; ++l)
-            CKM(launch_restrict<float>(h->B[l - 1], h->n[l - 1], h->B[l], st));
-        CKM(cudaMemsetAsync(h->e[0], 0, n3 * sizeof(float), st));
-        k_scal<<<1, 1, 0, st>>>(sh.ls, R.ls(0), 1);  // inner c = -m
-        count_launch(1);
-        CKM(cudaGetLastError());
-        for (int it = 0; it < inner; ++it) {
-            if (int rc = R.vcycle0())
-                return rc;
-            ++inner_total;
-        }
-        {
-            ProfScope ps(sh.prof, PK_UPDATE_MIXED, st, (double)n3);
-            k_update_mixed<<<blocks_for(n3), kBlock, 0, st>>>(phi, h->e[0], n3);
-        }
-        count_launch(1);
-        CKM(cudaGetLastError());
-        k_scal<<<1, 1, 0, st>>>(sh.ls, R.ls(0), 2);  // c += c_e
-        count_launch(1);
-        CKM(cudaGetLastError());
+        if (int rc = phase_work(R, phi, inner, err))
+            return rc;
     }
-    // report the projected c of the returned phi
-    k_scal<<<1, 1, 0, st>>>(sh.ls, sh.ls, 0);
-    count_launch(1);
-    CKM(cudaGetLastError());
-    CKM(launch_sum(phi, n3, sh.partials, &nb, st));
-    CKM(launch_finalize(sh.partials, nb, (double)n3, sh.ls, FIN_MEAN, st));
-    CKM(launch_sub_mean(phi, n3, &sh.ls[0].mean, st));
+    if (int rc = phase_finish(h, sh, phi, st, err))
+        return rc;
     if (info) {
-        info->cycles = inner_total;
+        info->cycles = outer * inner;
         info->outer_iters = outer;
-        info->cell_updates = R.cu;
         info->levels = h->nlev;
         info->coarsest_n = h->n[h->nlev - 1];
+        info->cell_updates = R.cu;
     }
     return status;
-#undef CKM
 }
+
+// ---------------------------------------------------------------- graph form
+
+// Decides after each FP64 residual whether the defect-correction loop goes on,
+// with the host loop's rules; sets the WHILE node's condition.
+__global__ void k_mixed_check(const LevelScal *__restrict__ ls0, BoxCtl *ctl,
+                              cudaGraphConditionalHandle hnd)
+{
+    const double rel = ls0->rel;
+    const int k = ctl->outer;
+    if (k < 64) {
+        ctl->hist[k] = rel;
+        ctl->nhist = k + 1;
+    }
+    ctl->rel = rel;
+    int stop = 0, status = MG5_E_NOT_CONVERGED;
+    if (!isfinite(rel)) {
+        stop = 1;
+        status = MG5_E_NONFINITE;
+    } else if (rel <= ctl->tol) {
+        stop = 1;
+        status = MG5_OK;
+    } else {
+        if (rel < ctl->best)
+            ctl->best = rel;
+        if (k >= 3 && rel > 10.0 * ctl->best) {
+            stop = 1;
+            status = MG5_E_DIVERGED;
+        } else if (k >= ctl->max_outer) {
+            stop = 1;
+            status = MG5_E_NOT_CONVERGED;
+        }
+    }
+    if (stop) {
+        ctl->status = status;
+        cudaGraphSetConditional(hnd, 0);
+    } else {
+        ctl->outer = k + 1;
+        cudaGraphSetConditional(hnd, 1);
+    }
+}
+
+__global__ void k_ctl_init(BoxCtl *ctl, double tol, int max_outer)
+{
+    ctl->tol = tol;
+    ctl->max_outer = max_outer;
+    ctl->outer = 0;
+    ctl->status = MG5_E_NOT_CONVERGED;
+    ctl->nhist = 0;
+    ctl->best = INFINITY;
+    ctl->rel = 0.0;
+}
+
+int capture_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const mg5_params *p,
+                  double *phi, double *grad, BoxCtl *ctl, cudaStream_t st, cudaStream_t st_body,
+                  CaptureStats *stats, std::string *err)
+{
+    RunMix R{h, sh, p, st, err, {}, 0};
+    for (int l = 0; l < h->nlev; ++l)
+        R.hl[l] = p->h * (double)(1 << l);
+    const int inner = p->inner_cycles > 0 ? p->inner_cycles : 3;
+    const long long L0 = launches_total();
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    CKM(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) {
+        *err = "capture_mixed: stream is not capturing";
+        return MG5_E_ARG;
+    }
+    cudaGraphConditionalHandle hnd;
+    CKM(cudaGraphConditionalHandleCreate(&hnd, graph, 0, cudaGraphCondAssignDefault));
+    k_ctl_init<<<1, 1, 0, st>>>(ctl, p->tol, p->max_cycles);
+    CKM(cudaGetLastError());
+    const long long n3 = (long long)h->N * h->N * h->N;
+    CKM(cudaMemsetAsync(phi, 0, n3 * sizeof(double), st));
+    if (int rc = phase_setup(h, sh, delta, p, st, err))
+        return rc;
+    if (int rc = phase_residual(h, sh, p, phi, st, err))
+        return rc;
+    k_mixed_check<<<1, 1, 0, st>>>(sh.ls, ctl, hnd);
+    CKM(cudaGetLastError());
+    // the WHILE node, after everything captured so far on st
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    CKM(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CKM(cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CKM(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    const long long L1 = launches_total();
+    // body: one defect-correction step and the next residual + check
+    CKM(cudaStreamBeginCaptureToGraph(st_body, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal));
+    RunMix B{h, sh, p, st_body, err, {}, 0};
+    for (int l = 0; l < h->nlev; ++l)
+        B.hl[l] = R.hl[l];
+    int rc = phase_work(B, phi, inner, err);
+    if (rc == MG5_OK)
+        rc = phase_residual(h, sh, p, phi, st_body, err);
+    if (rc == MG5_OK) {
+        k_mixed_check<<<1, 1, 0, st_body>>>(sh.ls, ctl, hnd);
+        if (cudaGetLastError() != cudaSuccess)
+            rc = MG5_E_CUDA;
+    }
+    cudaGraph_t g_out = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st_body, &g_out);
+    if (rc != MG5_OK)
+        return rc;
+    CKM(e);
+    const long long L2 = launches_total();
+    if (int rc2 = phase_finish(h, sh, phi, st, err))
+        return rc2;
+    if (grad)
+        CKM(launch_force(phi, h->N, h->N, h->N, 0, p->h, 1, grad, st));
+    stats->launches_fixed = (L1 - L0) + (launches_total() - L2);
+    stats->launches_per_iter = L2 - L1;
+    stats->cells_per_iter = B.cu;
+    stats->inner = inner;
+    return MG5_OK;
+}
+
+#undef CKM
 
 }  // namespace mg5

@@ -36,11 +36,38 @@ struct MixedShared {
     Profiler *prof;
 };
 
+// Per-box loop control of the graph form (device memory).
+struct BoxCtl {
+    double tol;
+    int max_outer;
+    int outer;       // defect-correction steps done
+    int status;
+    int nhist;
+    double best;
+    double rel;
+    double hist[64];
+};
+
+// What one captured solve costs per WHILE iteration (host bookkeeping).
+struct CaptureStats {
+    long long launches_fixed;     // kernels outside the loop
+    long long launches_per_iter;  // kernels of one loop body
+    long long cells_per_iter;     // cell updates of one loop body (coarsest grids excluded)
+    int inner;
+};
+
 size_t mixed_bytes(int N);
 int alloc_mixed(int N, size_t budget, size_t *held, MixedHier **out, std::string *err);
 void free_mixed(MixedHier *m, size_t *held);
 // phi: device FP64 N^3 initial guess in, mean-zero solution out.
 int solve_mixed(MixedHier *m, const MixedShared &sh, const double *delta, const mg5_params *p,
                 double *phi, mg5_info *info, cudaStream_t st, std::string *err);
+// Record, into the graph being captured on `st`, a whole mixed solve (phi
+// zero start) with its defect-correction loop as a WHILE node whose body is
+// captured on `st_body`; then gauge and (if grad) the force.  The loop state
+// lands in *ctl.
+int capture_mixed(MixedHier *m, const MixedShared &sh, const double *delta, const mg5_params *p,
+                  double *phi, double *grad, BoxCtl *ctl, cudaStream_t st, cudaStream_t st_body,
+                  CaptureStats *stats, std::string *err);
 
 }  // namespace mg5

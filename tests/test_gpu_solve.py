@@ -239,3 +239,56 @@ def test_relax_patch_full_size_64(ctx):
     g = host(ctx.force(relaxed, hc / 2, ghost=1, periodic=False))
     gref = oracle.force(ref_relaxed, hc / 2, ghost=1, periodic=False)
     assert rel_l2(g, gref) <= 1e-9
+
+
+def _batch_boxes(nbox, seed0=1000):
+    """A small version of the batched workload: sizes from {32, 48, 64}, alpha log-uniform."""
+    rng = np.random.Generator(np.random.PCG64(seed0))
+    alpha, s, h = nominal()
+    out = []
+    for b in range(nbox):
+        n = int(rng.choice([32, 48, 64]))
+        a = alpha * 10 ** rng.uniform(-1, 1)
+        out.append((n, workload.lognormal_delta(n, 1.0, seed0 + b), a))
+    return out, s, h
+
+
+def test_batch_equals_alone_and_oracle(ctx):
+    """Every box solved inside the batch graph gives the same result as the box
+    solved alone (same kernels, same order: bit-identical), and matches the FP64
+    oracle within 1e-6."""
+    import torch
+    mg = _mg()
+    boxes, s, h = _batch_boxes(6)
+    deltas = [dev(d) for _, d, _ in boxes]
+    params = [mg.default_params(alpha=a, s=s, h=h, tol=1e-8, precision="mixed") for _, _, a in boxes]
+    grads = [torch.empty((3,) + d.shape, dtype=torch.float64, device="cuda") for d in deltas]
+    phis, grads, infos = ctx.solve_batch(deltas, params, grads=grads)
+    for i, (n, d, a) in enumerate(boxes):
+        assert infos[i].status == 0, infos[i]
+        alone, g_alone, ia = ctx.solve_fifth_force(deltas[i], params[i],
+                                                   grad=torch.empty_like(grads[i]))
+        assert torch.equal(phis[i], alone)
+        assert torch.equal(grads[i], g_alone)
+        assert infos[i].outer_iters == ia.outer_iters and infos[i].cell_updates == ia.cell_updates
+        ref, _ = oracle.solve(d, a, s, h, tol=1e-13)
+        assert rel_l2(host(phis[i]), ref) <= 1e-6
+    # the same call again reuses the resident graph and gives the same answer
+    phis2, _, infos2 = ctx.solve_batch(deltas, params, phis=[torch.empty_like(x) for x in phis],
+                                       grads=grads)
+    for a, b in zip(phis, phis2):
+        assert torch.equal(a, b)
+
+
+def test_batch_mixed_status_per_box(ctx):
+    """A box that cannot converge within its cap reports it; the others are unaffected."""
+    import torch
+    mg = _mg()
+    boxes, s, h = _batch_boxes(3, seed0=2000)
+    deltas = [dev(d) for _, d, _ in boxes]
+    params = [mg.default_params(alpha=a, s=s, h=h, tol=1e-8, precision="mixed") for _, _, a in boxes]
+    params[1] = mg.default_params(alpha=boxes[1][2], s=s, h=h, tol=1e-14, max_cycles=1,
+                                  precision="mixed")
+    phis, _, infos = ctx.solve_batch(deltas, params, raise_on_status=False)
+    assert infos[0].status == 0 and infos[2].status == 0
+    assert infos[1].status == mg.E_NOT_CONVERGED and infos[1].outer_iters == 1
