@@ -68,7 +68,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -83,7 +83,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
@@ -138,9 +138,18 @@ def make_inputs():
 # ---------------------------------------------------------------- our arm
 
 class Step:
-    def __init__(self, mg, ctx, torch, coarse, patch, origin, dev):
-        self.mg, self.ctx, self.torch = mg, ctx, torch
+    """One pass of the path.  The mixed-precision solve of the domain grid does not
+    depend on the FP64 chain (solve -> interpolate -> relax), so it runs on a second
+    stream with its own context, concurrently: the FP64 chain keeps the FP64 pipes
+    busy while the mixed solve's FP32 kernels use the memory system."""
+
+    def __init__(self, mg, torch, coarse, patch, origin, dev):
+        self.mg, self.torch = mg, torch
         f64 = torch.float64
+        self.ctx = mg.Context(dev.index or 0)
+        self.ctx2 = mg.Context(dev.index or 0)
+        self.s1 = torch.cuda.Stream(device=dev)
+        self.s2 = torch.cuda.Stream(device=dev)
         self.beta, self.alpha, self.s = mg.ndgp_coefficients(1.0, 0.3, 1.0)
         self.origin = origin
         self.d_c = torch.from_numpy(coarse).to(dev)
@@ -157,44 +166,69 @@ class Step:
         self.p64 = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE, tol=TOL64)
         self.pmix = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE, tol=TOLMIX,
                                       precision="mixed")
-        self.ppatch = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE / 2, tol=TOL64,
-                                        max_cycles=100000)
+        self.ppatch = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE / 2, tol=TOL64)
+        torch.cuda.synchronize()
+
+    def profile(self, on):
+        self.ctx.profile_enable(on)
+        self.ctx2.profile_enable(on)
+
+    def profile_read(self):
+        a, b = self.ctx.profile_read(), self.ctx2.profile_read()
+        return {k: (a[k][0] + b[k][0], a[k][1] + b[k][1], a[k][2] + b[k][2]) for k in a}
 
     def run(self, host_io=None):
-        """One step; returns (cell updates, per-phase ms, infos)."""
+        """One step; returns (cell updates, per-phase ms, infos, step ms on the device)."""
         torch, ctx = self.torch, self.ctx
-        st = torch.cuda.current_stream()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-        # a1: coefficients of Eq. (beta) / Eq. (eomvarphi) at a = 1
-        self.beta, self.alpha, self.s = self.mg.ndgp_coefficients(1.0, 0.3, 1.0)
-        ev[0].record(st)
-        if host_io is None:
-            _, _, i64 = ctx.solve_fifth_force(self.d_c, self.p64, phi=self.phi, grad=self.grad)
-        else:
-            _, _, i64 = ctx.solve_fifth_force_host(host_io["delta"], self.p64, phi=host_io["phi"],
-                                                   grad=host_io["grad"])
-            self.phi.copy_(host_io["phi"], non_blocking=True)
-            self.d_p.copy_(host_io["patch"], non_blocking=True)
-        ev[1].record(st)
-        ctx.refine_interpolate(self.phi, self.origin, (PN, PN, PN), 1, out=self.box)
-        ctx.force(self.box, H_COARSE / 2, ghost=1, periodic=False, grad=self.g_tr)
-        ev[2].record(st)
-        self.box_full.copy_(self.box)
-        _, ip = ctx.relax_patch(self.d_p, self.ppatch, i64.compat_c, self.box_full)
-        ctx.force(self.box_full, H_COARSE / 2, ghost=1, periodic=False, grad=self.g_full)
-        ev[3].record(st)
-        _, _, im = ctx.solve_fifth_force(self.d_c, self.pmix, phi=self.phi_m, grad=self.grad_m)
-        ev[4].record(st)
-        if host_io is not None:
-            host_io["g_tr"].copy_(self.g_tr, non_blocking=True)
-            host_io["g_full"].copy_(self.g_full, non_blocking=True)
-            host_io["phi_m"].copy_(self.phi_m, non_blocking=True)
-            st.synchronize()
+        s1, s2 = self.s1, self.s2
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        out = {}
+
+        def mixed():
+            with torch.cuda.stream(s2):
+                s2.wait_event(ev[0])
+                ev[5].record(s2)
+                _, _, out["im"] = self.ctx2.solve_fifth_force(self.d_c, self.pmix, phi=self.phi_m,
+                                                              grad=self.grad_m, stream=s2)
+                ev[6].record(s2)
+
+        with torch.cuda.stream(s1):
+            # a1: coefficients of Eq. (beta) / Eq. (eomvarphi) at a = 1
+            self.beta, self.alpha, self.s = self.mg.ndgp_coefficients(1.0, 0.3, 1.0)
+            ev[0].record(s1)
+            th = threading.Thread(target=mixed)
+            th.start()
+            if host_io is None:
+                _, _, i64 = ctx.solve_fifth_force(self.d_c, self.p64, phi=self.phi, grad=self.grad,
+                                                  stream=s1)
+            else:
+                _, _, i64 = ctx.solve_fifth_force_host(host_io["delta"], self.p64,
+                                                       phi=host_io["phi"], grad=host_io["grad"],
+                                                       stream=s1)
+                self.phi.copy_(host_io["phi"], non_blocking=True)
+                self.d_p.copy_(host_io["patch"], non_blocking=True)
+            ev[1].record(s1)
+            ctx.refine_interpolate(self.phi, self.origin, (PN, PN, PN), 1, out=self.box, stream=s1)
+            ctx.force(self.box, H_COARSE / 2, ghost=1, periodic=False, grad=self.g_tr, stream=s1)
+            ev[2].record(s1)
+            self.box_full.copy_(self.box)
+            _, ip = ctx.relax_patch(self.d_p, self.ppatch, i64.compat_c, self.box_full, stream=s1)
+            ctx.force(self.box_full, H_COARSE / 2, ghost=1, periodic=False, grad=self.g_full,
+                      stream=s1)
+            ev[3].record(s1)
+            th.join()
+            s1.wait_event(ev[6])
+            if host_io is not None:
+                host_io["g_tr"].copy_(self.g_tr, non_blocking=True)
+                host_io["g_full"].copy_(self.g_full, non_blocking=True)
+                host_io["phi_m"].copy_(self.phi_m, non_blocking=True)
+            ev[4].record(s1)
         ev[4].synchronize()
+        im = out["im"]
         ms = {"solve_fp64": ev[0].elapsed_time(ev[1]), "interpolate": ev[1].elapsed_time(ev[2]),
-              "relax_patch": ev[2].elapsed_time(ev[3]), "solve_mixed": ev[3].elapsed_time(ev[4])}
+              "relax_patch": ev[2].elapsed_time(ev[3]), "solve_mixed": ev[5].elapsed_time(ev[6])}
         cu = i64.cell_updates + ip.cell_updates + im.cell_updates
-        return cu, ms, (i64, ip, im)
+        return cu, ms, (i64, ip, im), ev[0].elapsed_time(ev[4])
 
 
 def run_ours(args):
@@ -207,40 +241,40 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     coarse, patch, origin = make_inputs()
-    ctx = mg.Context(local)
-    step = Step(mg, ctx, torch, coarse, patch, origin, dev)
+    step = Step(mg, torch, coarse, patch, origin, dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         step.run()
     torch.cuda.synchronize()
-    launches0 = mg.kernel_launches()
-    ctx.profile_enable(True)
     clocks = ClockSampler(local)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    launches0 = mg.kernel_launches()
     tot_ms, tot_cu, phase = 0.0, 0, {}
     infos = None
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        cu, ms, infos = step.run()
-        e1.record()
-        e1.synchronize()
-        tot_ms += e0.elapsed_time(e1)
+        cu, ms, infos, step_ms = step.run()
+        tot_ms += step_ms
         tot_cu += cu
         for k, v in ms.items():
             phase[k] = phase.get(k, 0.0) + v
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    launches = mg.kernel_launches() - launches0
     if ws > 1:
         torch.distributed.barrier()
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
-    launches = mg.kernel_launches() - launches0
+    # the same steps again with the library's event profiler on (per-kernel device time)
+    step.profile(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        step.run()
+    prof = step.profile_read()
+    step.profile(False)
+    clk = clocks.stop()
     t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
     c = torch.tensor([float(tot_cu)], dtype=torch.float64, device=dev)
     if ws > 1:
@@ -263,7 +297,7 @@ def run_ours(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        cu, _, _ = step.run(hio)
+        cu, _, _, _ = step.run(hio)
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_cu += cu
@@ -289,14 +323,15 @@ def run_ours(args):
         "config": {"workload": "refine128: periodic 128^3 nDGP FP64 solve to 1e-10 (lognormal GRF "
                                "sigma=1.5 at 256^3, seed 2, block-mean to 128^3, h=1.95 Mpc/h) + "
                                "64^3 fine patch over the densest 32^3 cells (interpolated vs relaxed "
-                               "to 1e-10) + mixed-precision solve of the 128^3 grid to 1e-8",
+                               "to 1e-10) + mixed-precision solve of the 128^3 grid to 1e-8 "
+                               "(second stream, concurrent)",
                    "n": N_COARSE, "patch": 2 * PN, "tol_fp64": TOL64, "tol_mixed": TOLMIX,
                    "eps_alpha_s": step.alpha * step.s, "l2": "flushed between steps (512 MB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "time_to_tol_ms": {k: v / args.steps for k, v in phase.items()},
         "solve": {"fp64_cycles": i64.cycles, "fp64_rel_residual": i64.rel_residual,
                   "mixed_outer": im.outer_iters, "mixed_inner_cycles": im.cycles,
-                  "mixed_rel_residual": im.rel_residual, "patch_sweeps": ip.cycles,
+                  "mixed_rel_residual": im.rel_residual, "patch_cycles": ip.cycles,
                   "mixed_vs_fp64_rel_l2": mixed_vs64},
         "truncation": {"dphi_rel_l2": dphi, "dgrad_rel_l2": dg,
                        "relax_over_interp_ms": phase.get("relax_patch", 0) / max(phase.get("interpolate", 1e-9), 1e-9)},
@@ -395,7 +430,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mg5", choices=["mg5", "ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

@@ -131,6 +131,9 @@ const char *mg5_last_error(mg5_ctx *ctx);
 size_t mg5_bytes_held(mg5_ctx *ctx);
 /* Release every cached hierarchy (scratch) the context holds. */
 int mg5_release(mg5_ctx *ctx);
+/* Bytes a solve of side N at `precision` would add to the context: 0 when its
+ * hierarchy is already resident, else mg5_workspace_bytes. */
+int mg5_cached_bytes(mg5_ctx *ctx, int N, int precision, size_t *extra);
 
 /* ------------------------------------------------------------ the hot path */
 
@@ -220,6 +223,43 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_fine, const int pf[3],
 int mg5_solve_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const int *N,
                     const mg5_params *p, double *const *phi, double *const *grad, mg5_info *info,
                     void *stream);
+
+/* ------------------------------------------------------------ serving
+ * A continuous-batching solve server: `slots` worker threads, each with its
+ * own context (resident hierarchies) and CUDA stream.  Requests are admitted
+ * in arrival order when a worker is free and the HBM the request adds fits
+ * hbm_budget_bytes next to what all workers hold (0 = no cap); idle workers
+ * drop cached hierarchies when an admission waits for memory.  Admitted solves
+ * run concurrently.  Results are deterministic: the same alone and in the mix. */
+typedef struct mg5_server mg5_server;
+
+typedef struct {
+    const double *delta;     /* device, N^3, read until the request completes */
+    int N;
+    mg5_params params;
+    double *phi;             /* device, N^3, written (zero start) */
+    double *grad;            /* device, 3 N^3, or NULL */
+    unsigned long long tag;  /* caller's identifier, echoed in the completion */
+} mg5_request;
+
+typedef struct {
+    unsigned long long tag;
+    int status;
+    int pad;
+    double t_submit, t_admit, t_done;   /* seconds on the server clock */
+    mg5_info info;
+} mg5_completion;
+
+int mg5_server_create(mg5_server **srv, int device, int slots, size_t hbm_budget_bytes);
+/* Enqueue (thread-safe, non-blocking).  MG5_E_OOM if the request alone exceeds the budget. */
+int mg5_server_submit(mg5_server *srv, const mg5_request *req);
+/* Move up to max completions into out, waiting up to wait_ms for the first; returns the count. */
+int mg5_server_poll(mg5_server *srv, mg5_completion *out, int max, int wait_ms);
+int mg5_server_pending(mg5_server *srv, int *queued, int *running);
+double mg5_server_clock(mg5_server *srv);
+size_t mg5_server_bytes_held(mg5_server *srv);
+/* Finish every queued request, stop the workers, free everything. */
+int mg5_server_destroy(mg5_server *srv);
 
 /* ------------------------------------------------------------ tracing
  * Per-kernel-class device time, measured with CUDA events recorded on the

@@ -69,6 +69,17 @@ class Info:
                    [i.history[q] for q in range(min(i.n_history, 64))])
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [("delta", _c_void_p), ("N", _c_int), ("params", Params), ("phi", _c_void_p),
+                ("grad", _c_void_p), ("tag", ctypes.c_ulonglong)]
+
+
+class _Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_ulonglong), ("status", _c_int), ("pad", _c_int),
+                ("t_submit", _c_double), ("t_admit", _c_double), ("t_done", _c_double),
+                ("info", _Info)]
+
+
 _P = _c_void_p
 _I3 = ctypes.c_int * 3
 _sigs = {
@@ -88,6 +99,14 @@ _sigs = {
     "mg5_refine_interpolate": ([_P, _P, _c_int, _I3, _I3, _c_int, _P, _P], _c_int),
     "mg5_relax_patch": ([_P, _P, _I3, _P, _c_double, _P, _P, _P], _c_int),
     "mg5_solve_batch": ([_P, _c_int, _P, _P, _P, _P, _P, _P, _P], _c_int),
+    "mg5_cached_bytes": ([_P, _c_int, _c_int, _P], _c_int),
+    "mg5_server_create": ([_P, _c_int, _c_int, _c_size_t], _c_int),
+    "mg5_server_submit": ([_P, _P], _c_int),
+    "mg5_server_poll": ([_P, _P, _c_int, _c_int], _c_int),
+    "mg5_server_pending": ([_P, _P, _P], _c_int),
+    "mg5_server_clock": ([_P], _c_double),
+    "mg5_server_bytes_held": ([_P], _c_size_t),
+    "mg5_server_destroy": ([_P], _c_int),
     "mg5_profile_enable": ([_P, _c_int], _c_int),
     "mg5_profile_read": ([_P, _P, _P, _c_int], _c_int),
     "mg5_profile_name": ([_c_int], ctypes.c_char_p),
@@ -202,6 +221,13 @@ class Context:
 
     def bytes_held(self) -> int:
         return _lib.mg5_bytes_held(self._h)
+
+    def cached_bytes(self, n: int, precision=FP64) -> int:
+        if isinstance(precision, str):
+            precision = {"fp64": FP64, "mixed": MIXED}[precision]
+        out = _c_size_t()
+        self._check(_lib.mg5_cached_bytes(self._h, n, precision, ctypes.byref(out)))
+        return out.value
 
     def release(self):
         _lib.mg5_release(self._h)
@@ -365,6 +391,69 @@ class Context:
         return fine
 
 
+@dataclass
+class Completion:
+    tag: int
+    status: int
+    t_submit: float
+    t_admit: float
+    t_done: float
+    info: Info
+
+
+class Server:
+    """mg5_server: continuous-batching solves on `slots` workers (own context + stream
+    each), admitted in arrival order by HBM footprint.  Tensors passed to submit()
+    must stay alive until their completion is polled."""
+
+    def __init__(self, device: int = 0, slots: int = 4, hbm_budget_bytes: int = 0):
+        self._h = _c_void_p()
+        rc = _lib.mg5_server_create(ctypes.byref(self._h), device, slots, hbm_budget_bytes)
+        if rc != OK:
+            raise MG5Error(rc, "mg5_server_create failed")
+        self._keep = {}
+
+    def submit(self, delta, params: Params, phi, grad=None, tag: int = 0):
+        req = _Request(_ptr(delta), int(delta.shape[0]), params, _ptr(phi), _ptr(grad), tag)
+        rc = _lib.mg5_server_submit(self._h, ctypes.byref(req))
+        if rc != OK:
+            raise MG5Error(rc, "submit rejected")
+        self._keep[tag] = (delta, phi, grad)
+
+    def poll(self, max_n: int = 64, wait_ms: int = 0):
+        buf = (_Completion * max_n)()
+        n = _lib.mg5_server_poll(self._h, buf, max_n, wait_ms)
+        if n < 0:
+            raise MG5Error(n, "poll failed")
+        out = []
+        for c in buf[:n]:
+            self._keep.pop(c.tag, None)
+            out.append(Completion(c.tag, c.status, c.t_submit, c.t_admit, c.t_done, Info._from(c.info)))
+        return out
+
+    def pending(self):
+        q, r = _c_int(), _c_int()
+        _lib.mg5_server_pending(self._h, ctypes.byref(q), ctypes.byref(r))
+        return q.value, r.value
+
+    def clock(self) -> float:
+        return _lib.mg5_server_clock(self._h)
+
+    def bytes_held(self) -> int:
+        return _lib.mg5_server_bytes_held(self._h)
+
+    def close(self):
+        if self._h:
+            _lib.mg5_server_destroy(self._h)
+            self._h = _c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def _host_ptr(a):
     """Host pointer of a C-contiguous float64 numpy array or CPU tensor (None -> NULL)."""
     if a is None:
@@ -383,5 +472,6 @@ def _host_ptr(a):
     raise TypeError("expected a host float64 buffer")
 
 
-__all__ = ["Context", "Params", "Info", "MG5Error", "default_params", "ndgp_coefficients",
+__all__ = ["Context", "Server", "Completion", "Params", "Info", "MG5Error", "default_params",
+           "ndgp_coefficients",
            "workspace_bytes", "status_string", "version", "FP64", "MIXED"]

@@ -708,6 +708,23 @@ const char *mg5_last_error(mg5_ctx *ctx) { return ctx ? ctx->err.c_str() : "null
 
 size_t mg5_bytes_held(mg5_ctx *ctx) { return ctx ? ctx->held : 0; }
 
+int mg5_cached_bytes(mg5_ctx *ctx, int N, int precision, size_t *extra)
+{
+    if (!ctx || !extra)
+        return MG5_E_ARG;
+    RET(mg5_workspace_bytes(N, precision, extra));
+    if (precision == MG5_FP64) {
+        for (Hier *h : ctx->hiers)
+            if (h->N == N)
+                *extra = 0;
+    } else {
+        for (MixedHier *m : ctx->mixed)
+            if (m->N == N)
+                *extra = 0;
+    }
+    return MG5_OK;
+}
+
 static const char *kProfNames[PK_COUNT] = {
     "sweep64", "resid_restrict64", "coarse_rhs64", "prolong64", "coarsest64",
     "sweep32", "resid_restrict32", "coarse_rhs32", "prolong32", "coarsest32",

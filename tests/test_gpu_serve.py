@@ -1,0 +1,85 @@
+"""Serving: the continuous-batching server gives each request the same result
+alone and in the mix, admits by HBM footprint, and reports timestamps."""
+import numpy as np
+import pytest
+
+import workload
+from tests.gpu_common import ctx_fixture, dev, nominal
+
+pytestmark = pytest.mark.gpu
+
+
+def _mg():
+    import paper_1511_08200_gb300 as mg
+    return mg
+
+
+def _requests(seed=7):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    alpha, s, h = nominal()
+    reqs = []
+    for t in range(10):
+        n = int(rng.choice([32, 48, 64, 96]))
+        sigma = float(rng.uniform(0.5, 2.0))
+        tol = 1e-6 if rng.uniform() < 0.5 else 1e-8
+        reqs.append((t, n, workload.lognormal_delta(n, sigma, 500 + t), tol))
+    return reqs, alpha, s, h
+
+
+def test_server_same_alone_and_in_mix():
+    import torch
+    mg = _mg()
+    ctx = ctx_fixture()
+    reqs, alpha, s, h = _requests()
+    srv = mg.Server(0, slots=4)
+    deltas, phis, params = {}, {}, {}
+    for tag, n, d, tol in reqs:
+        deltas[tag] = dev(d)
+        phis[tag] = torch.full_like(deltas[tag], float("nan"))
+        params[tag] = mg.default_params(alpha=alpha, s=s, h=h, tol=tol, precision="mixed")
+        srv.submit(deltas[tag], params[tag], phis[tag], tag=tag)
+    got = {}
+    while len(got) < len(reqs):
+        for c in srv.poll(wait_ms=2000):
+            got[c.tag] = c
+    srv.close()
+    for tag, n, d, tol in reqs:
+        c = got[tag]
+        assert c.status == 0, c
+        assert c.t_submit <= c.t_admit <= c.t_done
+        assert c.info.rel_residual <= tol
+        alone, _, ia = ctx.solve_fifth_force(deltas[tag], params[tag])
+        assert torch.equal(alone, phis[tag])
+        assert ia.cell_updates == c.info.cell_updates
+    ctx.close()
+
+
+def test_server_respects_hbm_budget():
+    """With a budget below two 96^3 hierarchies, requests still all complete, one
+    at a time, and the held bytes never exceed the budget at the end."""
+    import torch
+    mg = _mg()
+    alpha, s, h = nominal()
+    one = mg.workspace_bytes(96, "mixed")
+    budget = int(1.5 * one)
+    srv = mg.Server(0, slots=3, hbm_budget_bytes=budget)
+    d = dev(workload.lognormal_delta(96, 1.0, 3))
+    p = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-6, precision="mixed")
+    phis = [torch.zeros_like(d) for _ in range(4)]
+    for t in range(4):
+        srv.submit(d, p, phis[t], tag=t)
+    done = []
+    while len(done) < 4:
+        done += srv.poll(wait_ms=2000)
+    assert all(c.status == 0 for c in done)
+    assert srv.bytes_held() <= budget
+    # the admissions did not overlap: each starts after an earlier one finished
+    ivs = sorted((c.t_admit, c.t_done) for c in done)
+    for a, b in zip(ivs, ivs[1:]):
+        assert b[0] >= a[1] - 1e-3
+    with pytest.raises(mg.MG5Error):
+        srv.submit(dev(np.zeros((256,) * 3)), p, torch.zeros((256,) * 3, dtype=torch.float64,
+                                                               device="cuda"), tag=99)
+    srv.close()
+    for x in phis[1:]:
+        assert torch.equal(x, phis[0])
