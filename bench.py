@@ -3,7 +3,7 @@
 
 One step is one pass of the whole path over the refinement workload:
   coefficients (Eq. beta) -> FP64 FAS solve of the periodic 128^3 domain grid
-  to relative residual 1e-10 + force (Sec. 3.1) -> coarse->fine interpolation
+  (full-multigrid start) to relative residual 1e-10 + force (Sec. 3.1) -> coarse->fine interpolation
   onto the 2x-refined 64^3 patch over the densest 32^3 coarse cells + force
   on it (the truncated fine level, Sec. 3.2) -> relaxation of the same patch
   with the interpolated Dirichlet ghosts + force (the untruncated level) ->
@@ -200,11 +200,11 @@ class Step:
             th.start()
             if host_io is None:
                 _, _, i64 = ctx.solve_fifth_force(self.d_c, self.p64, phi=self.phi, grad=self.grad,
-                                                  stream=s1)
+                                                  stream=s1, fmg=True)
             else:
                 _, _, i64 = ctx.solve_fifth_force_host(host_io["delta"], self.p64,
                                                        phi=host_io["phi"], grad=host_io["grad"],
-                                                       stream=s1)
+                                                       stream=s1, fmg=True)
                 self.phi.copy_(host_io["phi"], non_blocking=True)
                 self.d_p.copy_(host_io["patch"], non_blocking=True)
             ev[1].record(s1)
@@ -343,9 +343,124 @@ def run_ours(args):
                  "d2h_bytes_per_step": d2h} if e2e_ms > 0 else None),
         "gpu_launches": launches,
     }
+    if not args.no_batch:
+        out["batch"] = run_batch(mg, torch, dev, step.alpha, step.s)
+    if args.serve_seconds > 0:
+        out["serving"] = run_serving(mg, torch, dev, step.alpha, step.s, args.serve_seconds)
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(coarse, patch, origin, budget_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
+
+
+def run_batch(mg, torch, dev, alpha, s, reps=5):
+    """The batched workload: 96 boxes, sizes uniform from {32,48,64,96,128}, seeds 1000 + b,
+    alpha log-uniform in [0.1, 10] x nominal, mixed precision to 1e-8, solved as ONE
+    CUDA-graph launch; compared with the same boxes solved one after another."""
+    import workload
+    rng = np.random.Generator(np.random.PCG64(4))
+    sizes = rng.choice(np.asarray([32, 48, 64, 96, 128]), size=96)
+    scales = 10.0 ** rng.uniform(-1.0, 1.0, size=96)
+    deltas = [workload.lognormal_delta_torch(int(n), 1.0, 1000 + b, dev) for b, n in enumerate(sizes)]
+    params = [mg.default_params(alpha=alpha * float(a), s=s, h=L_BOX / 512, tol=TOLMIX,
+                                precision="mixed") for a in scales]
+    phis = [torch.zeros_like(d) for d in deltas]
+    grads = [torch.empty((3,) + d.shape, dtype=torch.float64, device=dev) for d in deltas]
+    ctx = mg.Context(dev.index or 0)
+    t0 = time.perf_counter()
+    ctx.solve_batch(deltas, params, phis=phis, grads=grads)          # capture + first launch
+    build_s = time.perf_counter() - t0
+    ms, cu = [], 0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, infos = ctx.solve_batch(deltas, params, phis=phis, grads=grads)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        cu = sum(i.cell_updates for i in infos)
+    seq_ms = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for d, p, x, g in zip(deltas, params, phis, grads):
+            ctx.solve_fifth_force(d, p, phi=x, grad=g)
+        e1.record()
+        e1.synchronize()
+        seq_ms.append(e0.elapsed_time(e1))
+    t = float(np.median(ms))
+    cells = int(sum(int(n) ** 3 for n in sizes))
+    worst = max(i.rel_residual for i in infos)
+    ctx.close()
+    return {"boxes": 96, "cells": cells, "ms_per_batch": t, "cell_updates_per_s": cu / (t / 1e3),
+            "time_to_tol_ms": t, "sequential_ms": float(np.median(seq_ms)),
+            "graph_build_s": build_s, "max_rel_residual": worst,
+            "outer_iters": [i.outer_iters for i in infos][:8], "dtype": "f32+f64"}
+
+
+def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=8, warm_s=None):
+    """Poisson arrivals at `rate` req/s for `seconds`: sides 16 round(10^U(log 32, log 256)/16),
+    sigma ~ U(0.5, 2), tol 1e-6 or 1e-8 with p = 1/2, mixed precision; admitted by HBM footprint.
+    Latency = completion - arrival (server clock); the first fifth of the run is discarded."""
+    import workload
+    rng = np.random.Generator(np.random.PCG64(5))
+    count = int(rate * seconds * 1.2) + 8
+    gaps = rng.exponential(1.0 / rate, size=count)
+    sizes = workload.serving_sizes(rng, count)
+    sig_bucket = rng.integers(0, 4, size=count)            # sigma in {0.5, 1.0, 1.5, 2.0}
+    tols = np.where(rng.uniform(size=count) < 0.5, 1e-6, 1e-8)
+    pool = {}
+    for n in sorted(set(int(x) for x in sizes)):
+        for b in range(4):
+            pool[(n, b)] = workload.lognormal_delta_torch(n, 0.5 + 0.5 * b, 5000 + 7 * n + b, dev)
+    budget = int(torch.cuda.get_device_properties(dev).total_memory * 0.5)
+    srv = mg.Server(dev.index or 0, slots=slots, hbm_budget_bytes=budget)
+    # warm the workers' hierarchies on every size once (not timed)
+    for i, n in enumerate(sorted(set(int(x) for x in sizes))):
+        p = mg.default_params(alpha=alpha, s=s, h=L_BOX / 512, tol=1e-6, precision="mixed")
+        srv.submit(pool[(n, 0)], p, torch.zeros_like(pool[(n, 0)]), tag=10 ** 9 + i)
+    while srv.pending() != (0, 0):
+        srv.poll(wait_ms=50)
+    srv.poll(max_n=1000)
+    done = {}
+    t_start = srv.clock()
+    t_next = t_start
+    i = 0
+    while True:
+        now = srv.clock()
+        if now - t_start >= seconds:
+            break
+        if now >= t_next and i < count:
+            n = int(sizes[i])
+            p = mg.default_params(alpha=alpha, s=s, h=L_BOX / 512, tol=float(tols[i]), precision="mixed")
+            d = pool[(n, int(sig_bucket[i]))]
+            srv.submit(d, p, torch.empty_like(d), tag=i)
+            t_next += gaps[i]
+            i += 1
+            continue
+        for c in srv.poll(wait_ms=0):
+            done[c.tag] = c
+        time.sleep(max(0.0, min(t_next - srv.clock(), 0.0005)))
+    submitted = i
+    while len(done) < submitted:
+        for c in srv.poll(wait_ms=100):
+            done[c.tag] = c
+    srv.close()
+    warm = seconds / 5.0 if warm_s is None else warm_s
+    rows = [c for c in done.values() if c.t_submit - t_start >= warm]
+    lat = np.array([(c.t_done - c.t_submit) * 1e3 for c in rows])
+    t_first = min(c.t_submit for c in rows)
+    t_last = max(c.t_done for c in rows)
+    cu = sum(c.info.cell_updates for c in rows)
+    ok = sum(1 for c in rows if c.status in (0, 1))
+    return {"offered_req_per_s": rate, "seconds": seconds, "slots": slots, "requests": len(rows),
+            "completed_ok": ok, "throughput_req_per_s": len(rows) / (t_last - t_first),
+            "cell_updates_per_s": cu / (t_last - t_first),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean()), "max": float(lat.max())},
+            "mean_cells_per_request": float(np.mean([int(sizes[c.tag]) ** 3 for c in rows])),
+            "hbm_budget_bytes": budget}
 
 
 def roofline(prof: dict, peaks: dict, steps: int) -> dict:
@@ -436,6 +551,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 96-box batched workload")
+    ap.add_argument("--serve-seconds", type=float, default=6.0,
+                    help="length of the serving run (0 skips it)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -61,6 +61,8 @@ extern "C" {
 /* ------------------------------------------------------------ flags */
 #define MG5_WARM     1u   /* phi holds the initial guess (Sec. 3.1: zero or the previous step) */
 #define MG5_HOST_IO  2u   /* delta, phi, grad are HOST pointers; the library copies them */
+#define MG5_FMG      4u   /* MG5_FP64 from zero: full-multigrid start (rhs restricted down, coarsest
+                             solved, one V-cycle per finer grid on the interpolated solution) */
 
 typedef struct mg5_ctx mg5_ctx;  /* opaque; owns the device hierarchy, resident between calls */
 
@@ -145,7 +147,7 @@ int mg5_cached_bytes(mg5_ctx *ctx, int N, int precision, size_t *extra);
  *   N     : even, >= 4; the grids halve while the half is even and >= 4; the
  *           coarsest grid must be at most 32 (else MG5_E_ARG).
  *   p     : parameters (alpha >= 0, s, h > 0, tol >= 0).
- *   flags : MG5_WARM (phi is the initial guess, else zero), MG5_HOST_IO.
+ *   flags : MG5_WARM (phi is the initial guess, else zero), MG5_HOST_IO, MG5_FMG.
  *   phi   : N^3 FP64, out: the solution with mean zero.
  *   grad  : 3 N^3 FP64 (gx, gy, gz blocks, SoA) or NULL; grad = d phi / dx_a.
  *           The fifth force on a particle is -grad / 2 (Eq. modpoisson).

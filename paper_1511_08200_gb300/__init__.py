@@ -26,7 +26,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 OK, W_DISC_CLAMP = 0, 1
 E_ARG, E_OOM, E_CUDA, E_NOT_CONVERGED, E_DIVERGED, E_NONFINITE = -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
-WARM, HOST_IO = 1, 2
+WARM, HOST_IO, FMG_START = 1, 2, 4
 
 _c_int, _c_double, _c_void_p, _c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 _c_uint = ctypes.c_uint
@@ -255,7 +255,7 @@ class Context:
 
     # ------------------------------------------------------------ hot path
     def solve_fifth_force(self, delta, params: Params, phi=None, grad=None, warm=False,
-                          stream=None, raise_on_status=True):
+                          stream=None, raise_on_status=True, fmg=False):
         """mg5_solve_fifth_force on device tensors.  phi (out, N^3) and grad
         (out, 3 x N^3, optional) are allocated if not given.  Returns (phi, grad, Info)."""
         import torch
@@ -263,9 +263,9 @@ class Context:
         if phi is None:
             phi = torch.zeros_like(delta)
         info = _Info()
-        rc = _lib.mg5_solve_fifth_force(self._h, _ptr(delta), n, ctypes.byref(params),
-                                        WARM if warm else 0, _ptr(phi), _ptr(grad),
-                                        ctypes.byref(info), _stream(stream))
+        flags = (WARM if warm else 0) | (FMG_START if fmg else 0)
+        rc = _lib.mg5_solve_fifth_force(self._h, _ptr(delta), n, ctypes.byref(params), flags,
+                                        _ptr(phi), _ptr(grad), ctypes.byref(info), _stream(stream))
         if raise_on_status:
             self._check(rc, (OK, W_DISC_CLAMP))
         elif rc in (E_ARG, E_OOM, E_CUDA):
@@ -273,12 +273,12 @@ class Context:
         return phi, grad, Info._from(info)
 
     def solve_fifth_force_host(self, delta, params: Params, phi=None, grad=None, warm=False,
-                               stream=None, raise_on_status=True):
+                               stream=None, raise_on_status=True, fmg=False):
         """Same call with HOST buffers (numpy float64 or pinned CPU tensors): the
         library copies delta in and phi / grad out (MG5_HOST_IO)."""
         n = int(delta.shape[0])
         info = _Info()
-        flags = HOST_IO | (WARM if warm else 0)
+        flags = HOST_IO | (WARM if warm else 0) | (FMG_START if fmg else 0)
         rc = _lib.mg5_solve_fifth_force(self._h, _host_ptr(delta), n, ctypes.byref(params), flags,
                                         _host_ptr(phi), _host_ptr(grad), ctypes.byref(info),
                                         _stream(stream))

@@ -442,13 +442,52 @@ struct Run64 {
             RET(sweep(l));
         return MG5_OK;
     }
+
+    // one V-cycle with grid l as the finest grid (its f holds that grid's own rhs)
+    int vcycle_top(int l)
+    {
+        mg5_ctx *ctx = this->ctx;
+        for (int s = 0; s < p->nu1; ++s)
+            RET(sweep(l));
+        RET(resid_restrict(l));
+        RET(coarse_visit(l + 1));
+        CK(launch_prolong_add<double>(h->v[l + 1], h->v0[l + 1], h->n[l + 1], h->v[l], c(l),
+                                      c(l + 1), st));
+        for (int s = 0; s < p->nu2; ++s)
+            RET(sweep(l));
+        return MG5_OK;
+    }
+
+    // Full-multigrid start: the rhs restricted down the hierarchy, the coarsest
+    // problem solved, then on each finer grid the interpolated coarse solution
+    // (and c) improved by one V-cycle; the finest grid receives the interpolant.
+    int fmg()
+    {
+        mg5_ctx *ctx = this->ctx;
+        const int L = h->nlev;
+        for (int l = 1; l < L; ++l)
+            CK(launch_restrict<double>(h->f[l - 1], h->n[l - 1], h->f[l], st));
+        const size_t nL = (size_t)h->n[L - 1] * h->n[L - 1] * h->n[L - 1];
+        CK(cudaMemsetAsync(h->v[L - 1], 0, nL * sizeof(double), st));
+        RET(coarsest(L - 1));
+        for (int l = L - 2; l >= 0; --l) {
+            const size_t nl = (size_t)h->n[l] * h->n[l] * h->n[l];
+            CK(cudaMemsetAsync(h->v[l], 0, nl * sizeof(double), st));
+            CK(cudaMemsetAsync(c(l), 0, sizeof(double), st));
+            CK(launch_prolong_add<double>(h->v[l + 1], nullptr, h->n[l + 1], h->v[l], c(l), c(l + 1),
+                                          st));
+            if (l > 0)
+                RET(vcycle_top(l));
+        }
+        return MG5_OK;
+    }
 };
 
 }  // namespace
 
 // Plain FP64 solve on device buffers.  phi holds the initial guess.
 static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p, double *phi,
-                   bool warm, mg5_info *info, cudaStream_t st)
+                   bool warm, bool fmg, mg5_info *info, cudaStream_t st)
 {
     Hier *h = nullptr;
     RET(get_hier(ctx, N, &h));
@@ -474,6 +513,8 @@ static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p
             h->tmp[0] = own;
         }
     } restore{h, h->tmp[0]};
+    if (fmg && !warm && h->nlev > 1)
+        RET(R.fmg());
     int status = MG5_E_NOT_CONVERGED;
     double best = INFINITY;
     int cyc = 0;
@@ -780,7 +821,7 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
         return MG5_E_ARG;
     RET(check_size(N));
     RET(check_params(p));
-    if (flags & ~(MG5_WARM | MG5_HOST_IO))
+    if (flags & ~(MG5_WARM | MG5_HOST_IO | MG5_FMG))
         return MG5_E_ARG;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
@@ -805,7 +846,8 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
         CK(cudaMemsetAsync(d_phi, 0, fb, st));
     int status;
     if (p->precision == MG5_FP64) {
-        status = solve64(ctx, d_delta, N, p, d_phi, (flags & MG5_WARM) != 0, info, st);
+        status = solve64(ctx, d_delta, N, p, d_phi, (flags & MG5_WARM) != 0, (flags & MG5_FMG) != 0,
+                         info, st);
     } else {
         MixedHier *mh = nullptr;
         for (MixedHier *m : ctx->mixed)

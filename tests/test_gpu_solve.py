@@ -55,6 +55,21 @@ def test_fp64_solve_matches_oracle(ctx, n, sigma, seed):
     assert abs(phi.mean()) <= 1e-14 * np.abs(phi).max()
 
 
+@pytest.mark.parametrize("n,sigma", [(32, 1.0), (48, 1.5), (128, 1.5)])
+def test_fp64_fmg_start_matches_oracle(ctx, n, sigma):
+    """The full-multigrid start reaches the same discrete solution in fewer cycles."""
+    mg = _mg()
+    alpha, s, h = nominal()
+    delta = workload.lognormal_delta(n, sigma, 11)
+    p = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-12)
+    phi, _, info = ctx.solve_fifth_force(dev(delta), p, fmg=True)
+    _, _, plain = ctx.solve_fifth_force(dev(delta), p)
+    ref, _ = oracle.solve(delta, alpha, s, h, tol=1e-13)
+    assert info.status == 0
+    assert rel_l2(host(phi), ref) <= 1e-10
+    assert info.cycles < plain.cycles
+
+
 def test_fp64_config_32_tol_1e10(ctx):
     """The 32^3 sigma = 1 workload at the stated tolerance: the oracle, recomputing
     the residual of the GPU's phi, finds it below 1e-10; phi and the force lie

@@ -121,3 +121,32 @@ def batch_workload(nbox: int = 96, seed0: int = 1000, sizes=(32, 48, 64, 96, 128
         n = int(ns[b])
         boxes.append((n, lognormal_delta(n, sigma, seed0 + b), alpha_nominal * float(scales[b])))
     return boxes
+
+
+def lognormal_delta_torch(n: int, sigma: float, seed: int, device="cuda"):
+    """The same recipe on the GPU with torch's seeded generator (for large batched and
+    serving inputs; its numbers differ from the numpy generator's)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    w = torch.randn((n, n, n), generator=g, device=device, dtype=torch.float64)
+    wk = torch.fft.rfftn(w)
+    fi = torch.fft.fftfreq(n, device=device, dtype=torch.float64) * n
+    fk = torch.fft.rfftfreq(n, device=device, dtype=torch.float64) * n
+    n2 = fi[:, None, None] ** 2 + fi[None, :, None] ** 2 + fk[None, None, :] ** 2
+    k = 2.0 * torch.pi * torch.sqrt(n2) / n
+    amp = torch.where((k > 0) & (k <= torch.pi), 1.0 / torch.clamp(k, min=1e-30), torch.zeros_like(k))
+    gr = torch.fft.irfftn(wk * amp, s=(n, n, n))
+    gr -= gr.mean()
+    sd = gr.std(unbiased=False)
+    if float(sd) > 0:
+        gr *= sigma / sd
+    one_plus = torch.exp(gr - 0.5 * sigma * sigma)
+    one_plus /= one_plus.mean()
+    return (one_plus - 1.0).contiguous()
+
+
+def serving_sizes(rng, count: int):
+    """Grid sides for the serving stream: 16 round(10^U(log10 32, log10 256) / 16)."""
+    u = rng.uniform(np.log10(32.0), np.log10(256.0), size=count)
+    return (16 * np.round(10.0 ** u / 16.0)).astype(int)
