@@ -307,3 +307,31 @@ def test_batch_mixed_status_per_box(ctx):
     phis, _, infos = ctx.solve_batch(deltas, params, raise_on_status=False)
     assert infos[0].status == 0 and infos[2].status == 0
     assert infos[1].status == mg.E_NOT_CONVERGED and infos[1].outer_iters == 1
+
+
+def test_mixed_512_full_size():
+    """The 512^3 sigma = 2 mixed-precision workload: the FP64 oracle recomputes the
+    residual of the GPU result cell by cell over the whole grid (<= 1e-8), and the
+    result matches the GPU FP64 solve (itself oracle-parity tested) within 1e-6,
+    over the whole grid and on the 128^3 subvolume at the origin."""
+    import torch
+    mg = _mg()
+    alpha, s, h = nominal()
+    n = 512
+    delta = workload.lognormal_delta(n, 2.0, 3)
+    ctx = mg.Context(0)
+    d = dev(delta)
+    pm = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-8, precision="mixed")
+    phim, _, im = ctx.solve_fifth_force(d, pm)
+    assert im.status == 0 and im.rel_residual <= 1e-8
+    got = host(phim)
+    r = oracle.residual(got, s * delta, im.compat_c, h, alpha)
+    assert np.linalg.norm(r) / np.linalg.norm(s * delta) <= 1e-8
+    p64 = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-11)
+    phi64, _, i64 = ctx.solve_fifth_force(d, p64, fmg=True)
+    ref = host(phi64)
+    assert rel_l2(got, ref) <= 1e-6
+    assert rel_l2(got[:128, :128, :128], ref[:128, :128, :128]) <= 1e-6
+    ctx.close()
+    del phim, phi64, d
+    torch.cuda.empty_cache()
