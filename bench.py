@@ -129,6 +129,19 @@ def _dist():
     return ws, rank, local
 
 
+def aggregate_replicas(ms: float, cells: float, device, world_size: int):
+    """Replicas only: every rank solves its own copy of the workload; the job time is
+    the slowest rank's and the work is the sum over ranks (no data-path collective)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(cells)], dtype=torch.float64, device=device)
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def make_inputs():
     import workload
     coarse, patch, origin = workload.patch_workload(N_FINE, SIGMA, SEED, PN)
@@ -275,12 +288,7 @@ def run_ours(args):
     prof = step.profile_read()
     step.profile(False)
     clk = clocks.stop()
-    t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-    c = torch.tensor([float(tot_cu)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(c, op=torch.distributed.ReduceOp.SUM)
-    max_ms, all_cu = float(t.item()), float(c.item())
+    max_ms, all_cu = aggregate_replicas(tot_ms, tot_cu, dev, ws)
 
     # e2e: the same step through the C ABI with HOST buffers (pinned), copies inside
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731

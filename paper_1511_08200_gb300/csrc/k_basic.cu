@@ -343,16 +343,38 @@ cudaError_t launch_prolong_add(const T *vc, const T *v0c, int nc, T *vf, double 
 // coarsest grid: one CTA.  Before each sweep: c = mean(op(v) - f) and the
 // residual norm; stop when it is <= rtol times the first one or after
 // nu_max sweeps.  Sweeps ping-pong A -> B (red) -> A (black) with barriers.
+// Grids up to kCoarsestSmemCells cells run entirely in shared memory.
 // --------------------------------------------------------------------------
 constexpr int kCoarsestThreads = 1024;
+constexpr int kCoarsestSmemCells = 1024;   // 4 arrays x 1024 x 8 B = 32 KB
 
 template <typename T, bool BASE>
 __global__ void __launch_bounds__(kCoarsestThreads)
     k_coarsest(T *A, T *B, const T *f, int n, CoefT<T> cf, double *cptr, int nu_max, double rtol,
                unsigned long long *clamp, int *sweeps_out, const T *__restrict__ base)
 {
+    extern __shared__ __align__(16) unsigned char cs_raw[];
     __shared__ double bc_s[2];
     const int n3 = n * n * n;
+    const bool in_smem = n3 <= kCoarsestSmemCells;
+    T *a = A, *b = B;
+    const T *ff = f, *bs = base;
+    if (in_smem) {
+        T *sm = reinterpret_cast<T *>(cs_raw);
+        a = sm;
+        b = sm + n3;
+        T *sf = sm + 2 * n3;
+        T *sbase = sm + 3 * n3;
+        for (int p = threadIdx.x; p < n3; p += blockDim.x) {
+            a[p] = A[p];
+            sf[p] = f[p];
+            if constexpr (BASE)
+                sbase[p] = base[p];
+        }
+        ff = sf;
+        bs = sbase;
+        __syncthreads();
+    }
     const double inv_n3 = 1.0 / (double)n3;
     double r0 = -1.0, c = 0.0;
     int it = 0;
@@ -364,10 +386,10 @@ __global__ void __launch_bounds__(kCoarsestThreads)
             const Rows r = periodic_rows(n, i, j);
             const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
             St<T> s, sb;
-            gather((const T *)A, (const T *)A, r, k, kp, km, s);
+            gather((const T *)a, (const T *)a, r, k, kp, km, s);
             if constexpr (BASE)
-                gather(base, base, r, k, kp, km, sb);
-            const double res = (double)(f[p] - opr<T, BASE>(s, sb, cf));
+                gather(bs, bs, r, k, kp, km, sb);
+            const double res = (double)(ff[p] - opr<T, BASE>(s, sb, cf));
             acc.x += res;
             acc.y += res * res;
         }
@@ -387,8 +409,8 @@ __global__ void __launch_bounds__(kCoarsestThreads)
         if (rn <= rtol * r0)
             break;
         for (int colour = 0; colour < 2; ++colour) {
-            const T *src = colour == 0 ? A : B;
-            T *dst = colour == 0 ? B : A;
+            const T *src = colour == 0 ? a : b;
+            T *dst = colour == 0 ? b : a;
             for (int p = threadIdx.x; p < n3; p += blockDim.x) {
                 const int k = p % n, j = (p / n) % n, i = p / (n * n);
                 if (((i + j + k) & 1) != colour) {
@@ -400,14 +422,17 @@ __global__ void __launch_bounds__(kCoarsestThreads)
                 St<T> s, sb;
                 gather(src, src, r, k, kp, km, s);
                 if constexpr (BASE)
-                    gather(base, base, r, k, kp, km, sb);
+                    gather(bs, bs, r, k, kp, km, sb);
                 bool cl = false;
-                dst[p] = upd<T, BASE>(s, sb, f[p] + (T)c, cf, cl);
+                dst[p] = upd<T, BASE>(s, sb, ff[p] + (T)c, cf, cl);
                 my_clamps += cl ? 1ull : 0ull;
             }
             __syncthreads();
         }
     }
+    if (in_smem)
+        for (int p = threadIdx.x; p < n3; p += blockDim.x)
+            A[p] = a[p];
     if (my_clamps)
         atomicAdd(clamp, my_clamps);
     if (threadIdx.x == 0) {
@@ -422,12 +447,17 @@ cudaError_t launch_coarsest(T *v, T *tmp, const T *f, int n, CoefT<T> cf, double
                             double rtol, unsigned long long *clamp, int *sweeps, cudaStream_t st,
                             const T *B)
 {
+    const int n3 = n * n * n;
+    int threads = ((n3 + 31) / 32) * 32;
+    if (threads > kCoarsestThreads)
+        threads = kCoarsestThreads;
+    const size_t sm = n3 <= kCoarsestSmemCells ? (size_t)4 * n3 * sizeof(T) : 0;
     if (B)
-        k_coarsest<T, true><<<1, kCoarsestThreads, 0, st>>>(v, tmp, f, n, cf, cptr, nu_max, rtol,
-                                                            clamp, sweeps, B);
+        k_coarsest<T, true><<<1, threads, sm, st>>>(v, tmp, f, n, cf, cptr, nu_max, rtol, clamp,
+                                                    sweeps, B);
     else
-        k_coarsest<T, false><<<1, kCoarsestThreads, 0, st>>>(v, tmp, f, n, cf, cptr, nu_max, rtol,
-                                                             clamp, sweeps, B);
+        k_coarsest<T, false><<<1, threads, sm, st>>>(v, tmp, f, n, cf, cptr, nu_max, rtol, clamp,
+                                                     sweeps, B);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -128,17 +128,53 @@ __device__ __forceinline__ void stencil_parts(const St<T> &s, T &S, T &sig)
     sig = (a * a + b * b + c * c) * (T)(1.0 / 3.0) + (dxy * dxy + dxz * dxz + dyz * dyz) * (T)0.125;
 }
 
-// Physical root of (2 alpha/3) L^2 + L - b = 0; a negative discriminant is
-// clamped to zero and flagged.
-template <typename T>
-__device__ __forceinline__ T physical_root(T b, T k8, bool &clamped)
+// Physical root of (2 alpha/3) L^2 + L - b = 0, L = 2b / (1 + sqrt(1 + 8 alpha b / 3));
+// a negative discriminant is clamped to zero (L = 2b) and flagged.
+//
+// FP32: the closed form with the fast approximate square root and divide (the
+// FP32 inner solve of the mixed mode needs ~1e-6, not correct rounding).
+// FP64: GB300 executes FP64 at 1/64 of the FP32 rate, and the IEEE square root
+// and divide sequences would be ~40% of the cell's FP64 instructions.  The root
+// is instead estimated in FP32 and refined by two Newton steps of the quadratic
+// q(L) = (2 alpha/3) L^2 + L - b (the update of Eq. newton) in FP64, with the
+// FP32 reciprocal of q'(L) held fixed: the relative error goes ~1e-7 -> ~1e-14
+// -> below FP64 rounding.
+__device__ __forceinline__ float physical_root(float b, float k8, bool &clamped)
 {
-    T disc = (T)1 + k8 * b;
-    if (disc < (T)0) {
-        disc = (T)0;
+    float disc = fmaf(k8, b, 1.0f);
+    if (disc <= 0.0f) {
+        clamped = clamped || disc < 0.0f;
+        return 2.0f * b;
+    }
+    return __fdividef(2.0f * b, 1.0f + disc * rsqrtf(disc));
+}
+
+__device__ __forceinline__ double physical_root(double b, double k8, bool &clamped)
+{
+#ifdef MG5_IEEE_ROOT
+    double disc = 1.0 + k8 * b;
+    if (disc < 0.0) {
+        disc = 0.0;
         clamped = true;
     }
-    return (T)2 * b / ((T)1 + sqrt(disc));
+    return 2.0 * b / (1.0 + sqrt(disc));
+#else
+    const double disc = fma(k8, b, 1.0);
+    if (disc < 0.0) {
+        clamped = true;
+        return 2.0 * b;
+    }
+    if (disc < 1e-3)   // near the double root Newton slows down: closed form
+        return 2.0 * b / (1.0 + sqrt(disc));
+    const float bf = (float)b;
+    const float df = fmaxf(fmaf((float)k8, bf, 1.0f), 0.0f);
+    double L = (double)__fdividef(2.0f * bf, 1.0f + sqrtf(df));
+    const double k23 = 0.25 * k8;  // 2 alpha / 3
+    const double r = (double)__frcp_rn((float)fma(2.0 * k23, L, 1.0));
+    L = fma(-fma(fma(k23, L, 1.0), L, -b), r, L);
+    L = fma(-fma(fma(k23, L, 1.0), L, -b), r, L);
+    return L;
+#endif
 }
 
 // New centre value solving the cell's equation with op(...) = rhs.
