@@ -354,7 +354,8 @@ def run_ours(args):
     if not args.no_batch:
         out["batch"] = run_batch(mg, torch, dev, step.alpha, step.s)
     if args.serve_seconds > 0:
-        out["serving"] = run_serving(mg, torch, dev, step.alpha, step.s, args.serve_seconds)
+        out["serving"] = run_serving(mg, torch, dev, step.alpha, step.s, args.serve_seconds,
+                                     slots=args.serve_slots)
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(coarse, patch, origin, budget_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
@@ -407,7 +408,7 @@ def run_batch(mg, torch, dev, alpha, s, reps=5):
             "outer_iters": [i.outer_iters for i in infos][:8], "dtype": "f32+f64"}
 
 
-def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=8, warm_s=None):
+def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=None):
     """Poisson arrivals at `rate` req/s for `seconds`: sides 16 round(10^U(log 32, log 256)/16),
     sigma ~ U(0.5, 2), tol 1e-6 or 1e-8 with p = 1/2, mixed precision; admitted by HBM footprint.
     Latency = completion - arrival (server clock); the first fifth of the run is discarded."""
@@ -618,6 +619,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-box batched workload")
+    ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-seconds", type=float, default=6.0,
                     help="length of the serving run (0 skips it)")
     args = ap.parse_args()

@@ -291,49 +291,83 @@ cudaError_t launch_coarse_rhs(const T *vc, T *fc, const double *m_fine, double *
 
 // Cell-centred trilinear prolongation: along each axis a fine centre is a
 // quarter coarse cell from its parent, so it takes 3/4 of the parent and 1/4
-// of the parent's neighbour on its own side.
+// of the parent's neighbour on its own side.  One thread per coarse cell reads
+// the 3x3x3 coarse neighbourhood once and writes its 8 children, applying the
+// separable weights along k, then j, then i; the two children along k are one
+// vector read-modify-write.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+
 template <typename T>
 __global__ void k_prolong_add(const T *__restrict__ vc, const T *__restrict__ v0c, int nc,
                               T *__restrict__ vf, double *c_fine, const double *c_coarse)
 {
-    const int n = 2 * nc;
-    const long long total = (long long)n * n * n;
+    const long long total = (long long)nc * nc * nc;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0 && c_fine && c_coarse)
         *c_fine += *c_coarse;
     if (t >= total)
         return;
-    const int k = (int)(t % n);
-    const long long q = t / n;
-    const int j = (int)(q % n), i = (int)(q / n);
-    const int pi = i >> 1, pj = j >> 1, pk = k >> 1;
-    const int qi = (i & 1) ? (pi == nc - 1 ? 0 : pi + 1) : (pi == 0 ? nc - 1 : pi - 1);
-    const int qj = (j & 1) ? (pj == nc - 1 ? 0 : pj + 1) : (pj == 0 ? nc - 1 : pj - 1);
-    const int qk = (k & 1) ? (pk == nc - 1 ? 0 : pk + 1) : (pk == 0 ? nc - 1 : pk - 1);
+    const int K = (int)(t % nc);
+    const long long q = t / nc;
+    const int J = (int)(q % nc), I = (int)(q / nc);
     const long long NC = nc;
-    const long long ri[2] = {(long long)pi * NC, (long long)qi * NC};
-    const long long rj[2] = {pj, qj};
-    const int kk[2] = {pk, qk};
-    const T w[2] = {(T)0.75, (T)0.25};
-    T acc = 0;
+    int ii[3], jj[3], kk[3];
+    ii[0] = I == 0 ? nc - 1 : I - 1, ii[1] = I, ii[2] = I == nc - 1 ? 0 : I + 1;
+    jj[0] = J == 0 ? nc - 1 : J - 1, jj[1] = J, jj[2] = J == nc - 1 ? 0 : J + 1;
+    kk[0] = K == 0 ? nc - 1 : K - 1, kk[1] = K, kk[2] = K == nc - 1 ? 0 : K + 1;
+    const T w0 = (T)0.75, w1 = (T)0.25;
+    // along k: Z[a][b][c] for child c (0: 2K, 1: 2K+1)
+    T Z[3][3][2];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < 3; ++b) {
+            const long long row = ((long long)ii[a] * NC + jj[b]) * NC;
+            T e[3];
 #pragma unroll
-            for (int d = 0; d < 2; ++d) {
-                const long long idx = (ri[a] + rj[b]) * NC + kk[d];
-                const T e = v0c ? (vc[idx] - v0c[idx]) : vc[idx];
-                acc += (w[a] * w[b] * w[d]) * e;
+            for (int c = 0; c < 3; ++c)
+                e[c] = v0c ? vc[row + kk[c]] - v0c[row + kk[c]] : vc[row + kk[c]];
+            Z[a][b][0] = w0 * e[1] + w1 * e[0];
+            Z[a][b][1] = w0 * e[1] + w1 * e[2];
+        }
+    const int n = 2 * nc;
+#pragma unroll
+    for (int ci = 0; ci < 2; ++ci)
+#pragma unroll
+        for (int cj = 0; cj < 2; ++cj) {
+            T out[2];
+#pragma unroll
+            for (int ck = 0; ck < 2; ++ck) {
+                T y[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    y[a] = w0 * Z[a][1][ck] + w1 * Z[a][cj ? 2 : 0][ck];
+                out[ck] = w0 * y[1] + w1 * y[ci ? 2 : 0];
             }
-    vf[t] += acc;
+            const long long f = ((long long)(2 * I + ci) * n + (2 * J + cj)) * n + 2 * K;
+            using V = typename Vec2<T>::type;
+            V *p = reinterpret_cast<V *>(vf + f);
+            V v = *p;
+            v.x += out[0];
+            v.y += out[1];
+            *p = v;
+        }
 }
 
 template <typename T>
 cudaError_t launch_prolong_add(const T *vc, const T *v0c, int nc, T *vf, double *c_fine,
                                const double *c_coarse, cudaStream_t st)
 {
-    const long long work = 8ll * nc * nc * nc;
+    const long long work = (long long)nc * nc * nc;
     k_prolong_add<T><<<blocks_for(work), kBlock, 0, st>>>(vc, v0c, nc, vf, c_fine, c_coarse);
     count_launch(1);
     return cudaGetLastError();

@@ -111,9 +111,14 @@ __global__ void __launch_bounds__(FT_THREADS)
     auto red_plane = [&](int q) {
         const T *om = S.old[slot5(q - 1)], *o0 = S.old[slot5(q)], *op = S.old[slot5(q + 1)];
         T *rn = S.rnew[slot3(q)];
+        // rows of 16 pairs per half-warp (a half-warp's cells sit in one row, 2 apart;
+        // the two halves of a warp take rows of opposite parity, so with even row
+        // strides the 32 lanes hit 32 distinct banks), then the 17th pair of each row
         const int e = threadIdx.x;
         if (e < RJ_ * (RK_ / 2)) {
-            const int jj = e / (RK_ / 2), pr = e - jj * (RK_ / 2);
+            const int main_n = RJ_ * 16;
+            const int jj = e < main_n ? e >> 4 : e - main_n;
+            const int pr = e < main_n ? (e & 15) : 16;
             // red: (q + j + k) even, j = j0 - 1 + jj, k = k0 - 1 + kk
             const int kk = 2 * pr + ((q + j0 + jj + k0) & 1);
             St<T> s, sb;
