@@ -63,6 +63,11 @@ extern "C" {
 #define MG5_HOST_IO  2u   /* delta, phi, grad are HOST pointers; the library copies them */
 #define MG5_FMG      4u   /* MG5_FP64 from zero: full-multigrid start (rhs restricted down, coarsest
                              solved, one V-cycle per finer grid on the interpolated solution) */
+#define MG5_GRAPH    8u   /* MG5_MIXED from zero as ONE CUDA-graph launch: the context captures, per
+                             (N, parameters, grad or not), the whole solve with its defect-correction
+                             loop as a device-controlled WHILE node, with its own hierarchy and
+                             staging buffers, and replays it (copy in, launch, copy out, one sync).
+                             Not with MG5_WARM or MG5_HOST_IO. */
 
 typedef struct mg5_ctx mg5_ctx;  /* opaque; owns the device hierarchy, resident between calls */
 
@@ -136,6 +141,8 @@ int mg5_release(mg5_ctx *ctx);
 /* Bytes a solve of side N at `precision` would add to the context: 0 when its
  * hierarchy is already resident, else mg5_workspace_bytes. */
 int mg5_cached_bytes(mg5_ctx *ctx, int N, int precision, size_t *extra);
+/* Bytes an MG5_GRAPH solve of (N, *p, grad or not) would add: 0 when its graph is cached. */
+int mg5_graph_cached_bytes(mg5_ctx *ctx, int N, const mg5_params *p, int with_grad, size_t *extra);
 
 /* ------------------------------------------------------------ the hot path */
 
@@ -147,7 +154,7 @@ int mg5_cached_bytes(mg5_ctx *ctx, int N, int precision, size_t *extra);
  *   N     : even, >= 4; the grids halve while the half is even and >= 4; the
  *           coarsest grid must be at most 32 (else MG5_E_ARG).
  *   p     : parameters (alpha >= 0, s, h > 0, tol >= 0).
- *   flags : MG5_WARM (phi is the initial guess, else zero), MG5_HOST_IO, MG5_FMG.
+ *   flags : MG5_WARM (phi is the initial guess, else zero), MG5_HOST_IO, MG5_FMG, MG5_GRAPH.
  *   phi   : N^3 FP64, out: the solution with mean zero.
  *   grad  : 3 N^3 FP64 (gx, gy, gz blocks, SoA) or NULL; grad = d phi / dx_a.
  *           The fifth force on a particle is -grad / 2 (Eq. modpoisson).

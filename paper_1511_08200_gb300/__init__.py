@@ -26,7 +26,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 OK, W_DISC_CLAMP = 0, 1
 E_ARG, E_OOM, E_CUDA, E_NOT_CONVERGED, E_DIVERGED, E_NONFINITE = -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
-WARM, HOST_IO, FMG_START = 1, 2, 4
+WARM, HOST_IO, FMG_START, GRAPH = 1, 2, 4, 8
 
 _c_int, _c_double, _c_void_p, _c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 _c_uint = ctypes.c_uint
@@ -100,6 +100,7 @@ _sigs = {
     "mg5_relax_patch": ([_P, _P, _I3, _P, _c_double, _P, _P, _P], _c_int),
     "mg5_solve_batch": ([_P, _c_int, _P, _P, _P, _P, _P, _P, _P], _c_int),
     "mg5_cached_bytes": ([_P, _c_int, _c_int, _P], _c_int),
+    "mg5_graph_cached_bytes": ([_P, _c_int, _P, _c_int, _P], _c_int),
     "mg5_server_create": ([_P, _c_int, _c_int, _c_size_t], _c_int),
     "mg5_server_submit": ([_P, _P], _c_int),
     "mg5_server_poll": ([_P, _P, _c_int, _c_int], _c_int),
@@ -255,7 +256,7 @@ class Context:
 
     # ------------------------------------------------------------ hot path
     def solve_fifth_force(self, delta, params: Params, phi=None, grad=None, warm=False,
-                          stream=None, raise_on_status=True, fmg=False):
+                          stream=None, raise_on_status=True, fmg=False, graph=False):
         """mg5_solve_fifth_force on device tensors.  phi (out, N^3) and grad
         (out, 3 x N^3, optional) are allocated if not given.  Returns (phi, grad, Info)."""
         import torch
@@ -263,7 +264,7 @@ class Context:
         if phi is None:
             phi = torch.zeros_like(delta)
         info = _Info()
-        flags = (WARM if warm else 0) | (FMG_START if fmg else 0)
+        flags = (WARM if warm else 0) | (FMG_START if fmg else 0) | (GRAPH if graph else 0)
         rc = _lib.mg5_solve_fifth_force(self._h, _ptr(delta), n, ctypes.byref(params), flags,
                                         _ptr(phi), _ptr(grad), ctypes.byref(info), _stream(stream))
         if raise_on_status:

@@ -126,6 +126,27 @@ struct BatchSet {
     size_t bytes = 0;
 };
 
+// A mixed solve of one size and parameter set captured as a graph (defect-correction
+// loop as a WHILE node), with its own hierarchy, scalars and staging buffers.
+struct GraphEntry {
+    int N = 0;
+    mg5_params prm{};
+    bool grad = false;
+    MixedHier *hier = nullptr;
+    double2 *partials = nullptr;
+    LevelScal *ls = nullptr;
+    SolveCounters *cnt = nullptr;
+    BoxCtl *ctl = nullptr;
+    double *delta = nullptr, *phi = nullptr, *gout = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CaptureStats stats{};
+    size_t bytes = 0;
+    unsigned long long last_use = 0;
+};
+
+constexpr size_t kGraphCacheMax = 48;
+
 struct mg5_ctx {
     int device = 0;
     size_t budget = 0;
@@ -135,6 +156,8 @@ struct mg5_ctx {
     std::vector<MixedHier *> mixed;
     std::vector<PatchHier *> patches;
     BatchSet *batch = nullptr;
+    std::vector<GraphEntry *> graphs;
+    unsigned long long graph_clock = 0;
     double2 *partials = nullptr;
     LevelScal *ls = nullptr;        // kScalSlots slots
     SolveCounters *cnt = nullptr;
@@ -149,6 +172,12 @@ struct mg5_ctx {
 };
 
 // ------------------------------------------------------------ helpers
+
+extern "C" {  // defined further down, inside the ABI block
+static bool same_params(const mg5_params &a, const mg5_params &b);
+static int solve_graph(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p, double *phi,
+                       double *grad, mg5_info *info, cudaStream_t st);
+}
 
 #define CK(call)                                                                           \
     do {                                                                                   \
@@ -314,6 +343,29 @@ static void free_batch(mg5_ctx *ctx)
     ctx->held -= b->bytes;
     delete b;
     ctx->batch = nullptr;
+}
+
+static size_t graph_entry_bytes(int N, bool grad)
+{
+    const size_t n3 = (size_t)N * N * N;
+    return mixed_bytes(N) + n3 * sizeof(double) * (grad ? 5 : 2) + sizeof(double2) * kMaxPartials +
+           sizeof(LevelScal) * kScalSlots + sizeof(SolveCounters) + sizeof(BoxCtl);
+}
+
+static void free_graph_entry(mg5_ctx *ctx, GraphEntry *g)
+{
+    if (g->exec)
+        cudaGraphExecDestroy(g->exec);
+    if (g->graph)
+        cudaGraphDestroy(g->graph);
+    if (g->hier)
+        free_mixed(g->hier, &ctx->held);
+    for (void *p : {(void *)g->partials, (void *)g->ls, (void *)g->cnt, (void *)g->ctl,
+                    (void *)g->delta, (void *)g->phi, (void *)g->gout})
+        if (p)
+            cudaFree(p);
+    ctx->held -= g->bytes;   // the hierarchy's own bytes were returned by free_mixed
+    delete g;
 }
 
 static int ensure_buffer(mg5_ctx *ctx, double **buf, size_t *have, size_t need)
@@ -714,6 +766,9 @@ int mg5_release(mg5_ctx *ctx)
         free_patch(ctx, ph);
     ctx->patches.clear();
     free_batch(ctx);
+    for (GraphEntry *g : ctx->graphs)
+        free_graph_entry(ctx, g);
+    ctx->graphs.clear();
     ctx_free(ctx, ctx->stage, ctx->stage_bytes);
     ctx->stage = nullptr;
     ctx->stage_bytes = 0;
@@ -763,6 +818,18 @@ int mg5_cached_bytes(mg5_ctx *ctx, int N, int precision, size_t *extra)
             if (m->N == N)
                 *extra = 0;
     }
+    return MG5_OK;
+}
+
+int mg5_graph_cached_bytes(mg5_ctx *ctx, int N, const mg5_params *p, int with_grad, size_t *extra)
+{
+    if (!ctx || !p || !extra)
+        return MG5_E_ARG;
+    RET(check_size(N));
+    *extra = graph_entry_bytes(N, with_grad != 0);
+    for (GraphEntry *g : ctx->graphs)
+        if (g->N == N && g->grad == (with_grad != 0) && same_params(g->prm, *p))
+            *extra = 0;
     return MG5_OK;
 }
 
@@ -821,7 +888,9 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
         return MG5_E_ARG;
     RET(check_size(N));
     RET(check_params(p));
-    if (flags & ~(MG5_WARM | MG5_HOST_IO | MG5_FMG))
+    if (flags & ~(MG5_WARM | MG5_HOST_IO | MG5_FMG | MG5_GRAPH))
+        return MG5_E_ARG;
+    if ((flags & MG5_GRAPH) && (p->precision != MG5_MIXED || (flags & (MG5_WARM | MG5_HOST_IO))))
         return MG5_E_ARG;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
@@ -845,6 +914,20 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
     if (!(flags & MG5_WARM))
         CK(cudaMemsetAsync(d_phi, 0, fb, st));
     int status;
+    if (flags & MG5_GRAPH) {
+        status = solve_graph(ctx, d_delta, N, p, d_phi, d_grad, info, st);
+        if (status == MG5_E_CUDA || status == MG5_E_ARG || status == MG5_E_OOM)
+            return status;
+        CK(cudaEventRecord(ctx->ev1, st));
+        CK(cudaStreamSynchronize(st));
+        if (info) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            info->ms_total = ms;
+            info->status = status;
+        }
+        return status;
+    }
     if (p->precision == MG5_FP64) {
         status = solve64(ctx, d_delta, N, p, d_phi, (flags & MG5_WARM) != 0, (flags & MG5_FMG) != 0,
                          info, st);
@@ -1131,6 +1214,143 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
 static bool same_params(const mg5_params &a, const mg5_params &b)
 {
     return std::memcmp(&a, &b, sizeof(mg5_params)) == 0;
+}
+
+// Find the cached graph for (N, params, grad) or capture a new one (evicting the
+// least recently used entries while the budget would be exceeded).
+static int get_graph_entry(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, GraphEntry **out)
+{
+    for (GraphEntry *g : ctx->graphs)
+        if (g->N == N && g->grad == grad && same_params(g->prm, *p)) {
+            g->last_use = ++ctx->graph_clock;
+            *out = g;
+            return MG5_OK;
+        }
+    const size_t need = graph_entry_bytes(N, grad);
+    while (!ctx->graphs.empty() &&
+           (ctx->graphs.size() >= kGraphCacheMax || (ctx->budget && ctx->held + need > ctx->budget))) {
+        auto it = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                   [](GraphEntry *a, GraphEntry *b) { return a->last_use < b->last_use; });
+        CK(cudaDeviceSynchronize());
+        free_graph_entry(ctx, *it);
+        ctx->graphs.erase(it);
+    }
+    if (ctx->budget && ctx->held + need > ctx->budget) {
+        ctx->err = "graph solve would exceed the context's HBM budget";
+        return MG5_E_OOM;
+    }
+    GraphEntry *g = new GraphEntry();
+    g->N = N;
+    g->prm = *p;
+    g->grad = grad;
+    g->bytes = need - mixed_bytes(N);
+    ctx->held += g->bytes;
+    int rc = alloc_mixed(N, 0, &ctx->held, &g->hier, &ctx->err);
+    const size_t n3 = (size_t)N * N * N;
+    cudaError_t e = rc == MG5_OK ? cudaSuccess : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->partials, sizeof(double2) * kMaxPartials);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->ls, sizeof(LevelScal) * kScalSlots);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->cnt, sizeof(SolveCounters));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->ctl, sizeof(BoxCtl));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->delta, n3 * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->phi, n3 * sizeof(double));
+    if (e == cudaSuccess && grad)
+        e = cudaMalloc((void **)&g->gout, 3 * n3 * sizeof(double));
+    cudaStream_t origin = nullptr, body = nullptr;
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking);
+    const bool prof_on = ctx->prof.on;
+    const long long l0 = launches_total();
+    if (e == cudaSuccess) {
+        ctx->prof.on = false;
+        e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            MixedShared sh{g->partials, g->ls, g->cnt, ctx->h_rel, nullptr};
+            rc = capture_mixed(g->hier, sh, g->delta, p, g->phi, g->gout, g->ctl, origin, body,
+                               &g->stats, &ctx->err);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(origin, &graph);
+            if (rc == MG5_OK && e2 == cudaSuccess) {
+                g->graph = graph;
+                e = cudaGraphInstantiate(&g->exec, graph, 0);
+            } else {
+                if (graph)
+                    cudaGraphDestroy(graph);
+                if (e2 != cudaSuccess)
+                    e = e2;
+            }
+        }
+        ctx->prof.on = prof_on;
+        count_launch(l0 - launches_total());   // captured, not enqueued
+    }
+    if (origin)
+        cudaStreamDestroy(origin);
+    if (body)
+        cudaStreamDestroy(body);
+    if (rc == MG5_OK && e != cudaSuccess) {
+        ctx->err = std::string("graph solve: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        rc = e == cudaErrorMemoryAllocation ? MG5_E_OOM : MG5_E_CUDA;
+    }
+    if (rc != MG5_OK) {
+        free_graph_entry(ctx, g);
+        return rc;
+    }
+    g->last_use = ++ctx->graph_clock;
+    ctx->graphs.push_back(g);
+    *out = g;
+    return MG5_OK;
+}
+
+// MG5_MIXED from zero through the cached graph: copy in, one graph launch, copy out.
+static int solve_graph(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p, double *phi,
+                       double *grad, mg5_info *info, cudaStream_t st)
+{
+    GraphEntry *g = nullptr;
+    RET(get_graph_entry(ctx, N, p, grad != nullptr, &g));
+    const size_t n3 = (size_t)N * N * N;
+    CK(cudaMemcpyAsync(g->delta, delta, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaGraphLaunch(g->exec, st));
+    CK(cudaMemcpyAsync(phi, g->phi, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (grad)
+        CK(cudaMemcpyAsync(grad, g->gout, 3 * n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    BoxCtl ctl;
+    SolveCounters cnt;
+    LevelScal ls0;
+    CK(cudaMemcpyAsync(&ctl, g->ctl, sizeof(BoxCtl), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&cnt, g->cnt, sizeof(SolveCounters), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&ls0, g->ls, sizeof(LevelScal), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    count_launch(g->stats.launches_fixed + g->stats.launches_per_iter * ctl.outer);
+    int status = ctl.status;
+    if (info) {
+        info->status = status;
+        info->outer_iters = ctl.outer;
+        info->cycles = ctl.outer * g->stats.inner;
+        info->levels = g->hier->nlev;
+        info->coarsest_n = g->hier->n[info->levels - 1];
+        info->n_history = ctl.nhist;
+        for (int k = 0; k < ctl.nhist && k < 64; ++k)
+            info->history[k] = ctl.hist[k];
+        info->rel_residual = ctl.rel;
+        info->compat_c = ls0.c;
+        info->phi_mean_removed = ls0.mean;
+        const long long nc = info->coarsest_n;
+        info->cell_updates =
+            g->stats.cells_per_iter * ctl.outer + (long long)cnt.coarse_sweeps * nc * nc * nc;
+        info->disc_clamped = (long long)cnt.clamped;
+    }
+    if (status == MG5_OK && cnt.clamped > 0)
+        status = MG5_W_DISC_CLAMP;
+    return status;
 }
 
 static bool batch_matches(const BatchSet *b, int nbox, const double *const *delta, const int *N,

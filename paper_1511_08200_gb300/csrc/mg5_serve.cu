@@ -8,7 +8,8 @@
 // what every worker holds; if not, the worker first drops its own cached
 // hierarchies, then waits for others to finish.  Admitted solves run
 // concurrently on their workers' streams, so requests that arrive while
-// others are on the GPU start as soon as a slot and memory free up.  Every
+// others are on the GPU start as soon as a slot and memory free up.  Mixed
+// solves run as cached CUDA graphs (mg5_solve_fifth_force with MG5_GRAPH).  Every
 // solve is deterministic (fixed-order reductions, no state shared between
 // workers), so a result is the same alone and in the mix.
 #include <cuda_runtime.h>
@@ -88,8 +89,10 @@ static void worker_main(mg5_server *srv, int w)
                 }
                 const mg5_request &r = srv->queue.front().req;
                 size_t extra = 0;
-                if (rc_init == MG5_OK && srv->budget &&
-                    mg5_cached_bytes(ctx, r.N, r.params.precision, &extra) == MG5_OK) {
+                const int rcb = r.params.precision == MG5_MIXED
+                                    ? mg5_graph_cached_bytes(ctx, r.N, &r.params, r.grad != nullptr, &extra)
+                                    : mg5_cached_bytes(ctx, r.N, r.params.precision, &extra);
+                if (rc_init == MG5_OK && srv->budget && rcb == MG5_OK) {
                     size_t total = 0;
                     for (size_t b : srv->held)
                         total += b;
@@ -122,7 +125,9 @@ static void worker_main(mg5_server *srv, int w)
         if (rc_init != MG5_OK) {
             c.status = rc_init;
         } else {
-            c.status = mg5_solve_fifth_force(ctx, job.req.delta, job.req.N, &job.req.params, 0,
+            // mixed solves replay a cached CUDA graph (one launch, one synchronisation)
+            const unsigned flags = job.req.params.precision == MG5_MIXED ? MG5_GRAPH : 0u;
+            c.status = mg5_solve_fifth_force(ctx, job.req.delta, job.req.N, &job.req.params, flags,
                                              job.req.phi, job.req.grad, &c.info, (void *)st);
         }
         c.t_done = now_s() - srv->t0;

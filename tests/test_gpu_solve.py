@@ -335,3 +335,30 @@ def test_mixed_512_full_size():
     ctx.close()
     del phim, phi64, d
     torch.cuda.empty_cache()
+
+
+def test_graph_solve_equals_host_driven(ctx):
+    """MG5_GRAPH replays a captured solve: bit-identical to the host-driven mixed solve,
+    on the first call (capture) and on cache hits; other parameters make a new entry."""
+    import torch
+    mg = _mg()
+    alpha, s, h = nominal()
+    for n, sigma, tol in ((32, 1.0, 1e-8), (48, 2.0, 1e-6), (96, 1.5, 1e-8)):
+        d = dev(workload.lognormal_delta(n, sigma, 21))
+        p = mg.default_params(alpha=alpha, s=s, h=h, tol=tol, precision="mixed")
+        ref, gref, iref = ctx.solve_fifth_force(d, p, grad=torch.empty((3,) + d.shape, dtype=torch.float64, device="cuda"))
+        for _ in range(2):
+            phi, g, info = ctx.solve_fifth_force(d, p, graph=True,
+                                                 grad=torch.empty((3,) + d.shape, dtype=torch.float64, device="cuda"))
+            assert torch.equal(phi, ref) and torch.equal(g, gref)
+            assert info.outer_iters == iref.outer_iters and info.cell_updates == iref.cell_updates
+            assert info.rel_residual == iref.rel_residual and info.status == 0
+    # a different input through a cached graph
+    d2 = dev(workload.lognormal_delta(32, 1.0, 22))
+    p = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-8, precision="mixed")
+    ref2, _, _ = ctx.solve_fifth_force(d2, p)
+    phi2, _, _ = ctx.solve_fifth_force(d2, p, graph=True,
+                                       grad=torch.empty((3,) + d2.shape, dtype=torch.float64, device="cuda"))
+    assert torch.equal(phi2, ref2)
+    with pytest.raises(mg.MG5Error):
+        ctx.solve_fifth_force(d2, mg.default_params(alpha=alpha, s=s, h=h), graph=True)   # FP64: not allowed
