@@ -53,9 +53,21 @@ WORK = {
     "resid64_mixed": ("alu", 24.0, 36.0),     # read phi64, f64; write r32, B32
     "update_mixed": ("hbm", 20.0, 1.0),
     "force64": ("hbm", 32.0, 6.0),
+    "sweep64_coarse": ("alu", 24.0, 42.0),
+    "sweep32_coarse": ("hbm", 16.0, 60.0),
+    "patch_sweep64_coarse": ("alu", 24.0, 42.0),
     "refine64": ("hbm", 9.0, 25.0),
     "prolong64": ("hbm", 18.0, 20.0),
     "prolong32": ("hbm", 9.0, 20.0),
+}
+
+
+# DRAM bytes per cell measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch / its cells), for the kernel as it stands; a launch's traffic = this x its cells.
+#   sweep32: k_sweep_fused<float,1>, 256^3 finest-grid launch: 278.1 MB / 16.78 M cells
+#            (profiles/sweep32_fused_mixed256.md)
+TRAFFIC_PER_CELL = {
+    "sweep32": 278.1e6 / 256 ** 3,
 }
 
 
@@ -486,8 +498,10 @@ def roofline(prof: dict, peaks: dict, steps: int) -> dict:
         achieved = fpc * cells / sec / 1e12
         peak = FP64_PEAK_TFLOPS
         unit = "TFLOP/s"
+    tpc = TRAFFIC_PER_CELL.get(name)
+    traffic = tpc * cells / max(calls, 1) if tpc is not None else None
     return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic,
             "avg_launch_ms": ms / max(calls, 1), "launches_per_step": calls / steps,
             "alg_bytes_per_cell": bpc, "alg_flops_per_cell": fpc,
             "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if bound == "hbm"

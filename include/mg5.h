@@ -141,6 +141,8 @@ int mg5_release(mg5_ctx *ctx);
 /* Bytes a solve of side N at `precision` would add to the context: 0 when its
  * hierarchy is already resident, else mg5_workspace_bytes. */
 int mg5_cached_bytes(mg5_ctx *ctx, int N, int precision, size_t *extra);
+/* Device bytes one cached MG5_GRAPH solve of side N holds (hierarchy, staging, graph state). */
+int mg5_graph_workspace_bytes(int N, int with_grad, size_t *bytes);
 /* Bytes an MG5_GRAPH solve of (N, *p, grad or not) would add: 0 when its graph is cached. */
 int mg5_graph_cached_bytes(mg5_ctx *ctx, int N, const mg5_params *p, int with_grad, size_t *extra);
 
@@ -260,7 +262,8 @@ typedef struct {
 } mg5_completion;
 
 int mg5_server_create(mg5_server **srv, int device, int slots, size_t hbm_budget_bytes);
-/* Enqueue (thread-safe, non-blocking).  MG5_E_OOM if the request alone exceeds the budget. */
+/* Enqueue (thread-safe, non-blocking).  MG5_E_OOM if the request alone exceeds the budget
+ * (a request that cannot fit even with every worker idle and empty completes with MG5_E_OOM). */
 int mg5_server_submit(mg5_server *srv, const mg5_request *req);
 /* Move up to max completions into out, waiting up to wait_ms for the first; returns the count. */
 int mg5_server_poll(mg5_server *srv, mg5_completion *out, int max, int wait_ms);

@@ -101,6 +101,7 @@ _sigs = {
     "mg5_solve_batch": ([_P, _c_int, _P, _P, _P, _P, _P, _P, _P], _c_int),
     "mg5_cached_bytes": ([_P, _c_int, _c_int, _P], _c_int),
     "mg5_graph_cached_bytes": ([_P, _c_int, _P, _c_int, _P], _c_int),
+    "mg5_graph_workspace_bytes": ([_c_int, _c_int, _P], _c_int),
     "mg5_server_create": ([_P, _c_int, _c_int, _c_size_t], _c_int),
     "mg5_server_submit": ([_P, _P], _c_int),
     "mg5_server_poll": ([_P, _P, _c_int, _c_int], _c_int),
@@ -164,6 +165,15 @@ def ndgp_coefficients(a: float, omega_m0: float, h0rc: float):
     if rc != OK:
         raise MG5Error(rc, "bad cosmology")
     return b.value, al.value, s.value
+
+
+def graph_workspace_bytes(n: int, with_grad: bool = False) -> int:
+    """Device bytes one cached MG5_GRAPH solve of side n holds."""
+    out = _c_size_t()
+    rc = _lib.mg5_graph_workspace_bytes(n, 1 if with_grad else 0, ctypes.byref(out))
+    if rc != OK:
+        raise MG5Error(rc, "bad size")
+    return out.value
 
 
 def workspace_bytes(n: int, precision=FP64) -> int:

@@ -193,26 +193,51 @@ __global__ void k_pbox_ghost_refresh(double *__restrict__ v, const double *__res
 
 // Coarsest patch grid, one CTA: before each sweep the residual norm; stop at
 // rtol times the first one or after nu_max sweeps.  A -> B (red) -> A (black).
+// Boxes up to kPboxSmemCells cells run in shared memory.
+constexpr int kPboxSmemCells = 1024;
+
 __global__ void __launch_bounds__(1024)
     k_pbox_coarsest(double *A, double *B, const double *__restrict__ f, int p0, int p1, int p2,
                     CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
                     int *sweeps_out, const double *__restrict__ v0, double w)
 {
-    const int nbox = (p0 + 2) * (p1 + 2) * (p2 + 2);
-    // coarse grids keep their ghosts on the extrapolated boundary condition
-    auto refresh = [&](double *X) {
-        if (!v0)
-            return;
-        for (int g = threadIdx.x; g < nbox; g += blockDim.x) {
-            const int K = g % (p2 + 2), J = (g / (p2 + 2)) % (p1 + 2), I = g / ((p1 + 2) * (p2 + 2));
-            ghost_refresh_cell(X, v0, I, J, K, p0, p1, p2, w);
-        }
-        __syncthreads();
-    };
-    refresh(A);
+    extern __shared__ __align__(16) unsigned char pb_raw[];
     __shared__ double bc_s;
     const int n3 = p0 * p1 * p2;
     const int d1 = p1 + 2, d2 = p2 + 2;
+    const int nbox = (p0 + 2) * d1 * d2;
+    const bool in_smem = nbox <= kPboxSmemCells;
+    double *a = A, *b = B;
+    const double *ff = f, *g0 = v0;
+    if (in_smem) {
+        double *sm = reinterpret_cast<double *>(pb_raw);
+        a = sm;
+        b = sm + nbox;
+        double *sf = sm + 2 * nbox;
+        double *sv0 = sm + 3 * nbox;
+        for (int q = threadIdx.x; q < nbox; q += blockDim.x) {
+            a[q] = A[q];
+            b[q] = B[q];
+            if (v0)
+                sv0[q] = v0[q];
+            if (q < n3)
+                sf[q] = f[q];
+        }
+        ff = sf;
+        g0 = v0 ? sv0 : nullptr;
+        __syncthreads();
+    }
+    // coarse grids keep their ghosts on the extrapolated boundary condition
+    auto refresh = [&](double *X) {
+        if (!g0)
+            return;
+        for (int g = threadIdx.x; g < nbox; g += blockDim.x) {
+            const int K = g % d2, J = (g / d2) % d1, I = g / (d1 * d2);
+            ghost_refresh_cell(X, g0, I, J, K, p0, p1, p2, w);
+        }
+        __syncthreads();
+    };
+    refresh(a);
     double r0 = -1.0;
     int it = 0;
     unsigned long long my_clamps = 0;
@@ -222,8 +247,8 @@ __global__ void __launch_bounds__(1024)
             const int k = p % p2, j = (p / p2) % p1, i = p / (p1 * p2);
             const Rows r = box_rows(d1, d2, i + 1, j + 1);
             St<double> s;
-            gather((const double *)A, (const double *)A, r, k + 1, k + 2, k, s);
-            const double res = f[p] - cell_op(s, cf);
+            gather((const double *)a, (const double *)a, r, k + 1, k + 2, k, s);
+            const double res = ff[p] - cell_op(s, cf);
             acc.y += res * res;
         }
         acc = block_sum2(acc);
@@ -237,8 +262,8 @@ __global__ void __launch_bounds__(1024)
         if (rn <= rtol * r0)
             break;
         for (int colour = 0; colour < 2; ++colour) {
-            const double *src = colour == 0 ? A : B;
-            double *dst = colour == 0 ? B : A;
+            const double *src = colour == 0 ? a : b;
+            double *dst = colour == 0 ? b : a;
             for (int p = threadIdx.x; p < n3; p += blockDim.x) {
                 const int k = p % p2, j = (p / p2) % p1, i = p / (p1 * p2);
                 const Rows r = box_rows(d1, d2, i + 1, j + 1);
@@ -249,12 +274,16 @@ __global__ void __launch_bounds__(1024)
                 St<double> s;
                 gather(src, src, r, k + 1, k + 2, k, s);
                 bool cl = false;
-                dst[r.r00 + k + 1] = cell_update(s, f[p], cf, cl);
+                dst[r.r00 + k + 1] = cell_update(s, ff[p], cf, cl);
                 my_clamps += cl ? 1ull : 0ull;
             }
             __syncthreads();
             refresh(dst);
         }
+    }
+    if (in_smem) {
+        for (int q = threadIdx.x; q < nbox; q += blockDim.x)
+            A[q] = a[q];
     }
     if (my_clamps)
         atomicAdd(clamp, my_clamps);
@@ -309,8 +338,14 @@ cudaError_t launch_pbox_coarsest(double *A, double *B, const double *f, const in
                                  CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
                                  int *sweeps, cudaStream_t st, const double *v0, double w)
 {
-    k_pbox_coarsest<<<1, 1024, 0, st>>>(A, B, f, p[0], p[1], p[2], cf, nu_max, rtol, clamp, sweeps,
-                                        v0, w);
+    const int n3 = p[0] * p[1] * p[2];
+    const int nbox = (p[0] + 2) * (p[1] + 2) * (p[2] + 2);
+    int threads = ((n3 + 31) / 32) * 32;
+    if (threads > 1024)
+        threads = 1024;
+    const size_t sm = nbox <= kPboxSmemCells ? (size_t)4 * nbox * sizeof(double) : 0;
+    k_pbox_coarsest<<<1, threads, sm, st>>>(A, B, f, p[0], p[1], p[2], cf, nu_max, rtol, clamp,
+                                            sweeps, v0, w);
     count_launch(1);
     return cudaGetLastError();
 }

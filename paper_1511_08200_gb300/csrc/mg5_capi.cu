@@ -419,7 +419,7 @@ struct Run64 {
     int sweep(int l)
     {
         const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
-        ProfScope ps(&ctx->prof, PK_SWEEP64, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
+        ProfScope ps(&ctx->prof, l == 0 ? PK_SWEEP64 : PK_SWEEP64C, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
         cudaError_t e = launch_sweep<double>(h->v[l], h->tmp[l], h->f[l], c(l), h->n[l], cf,
                                              &ctx->cnt->clamped, st);
         if (e != cudaSuccess) {
@@ -821,6 +821,15 @@ int mg5_cached_bytes(mg5_ctx *ctx, int N, int precision, size_t *extra)
     return MG5_OK;
 }
 
+int mg5_graph_workspace_bytes(int N, int with_grad, size_t *bytes)
+{
+    if (!bytes)
+        return MG5_E_ARG;
+    RET(check_size(N));
+    *bytes = graph_entry_bytes(N, with_grad != 0);
+    return MG5_OK;
+}
+
 int mg5_graph_cached_bytes(mg5_ctx *ctx, int N, const mg5_params *p, int with_grad, size_t *extra)
 {
     if (!ctx || !p || !extra)
@@ -837,7 +846,7 @@ static const char *kProfNames[PK_COUNT] = {
     "sweep64", "resid_restrict64", "coarse_rhs64", "prolong64", "coarsest64",
     "sweep32", "resid_restrict32", "coarse_rhs32", "prolong32", "coarsest32",
     "resid64_mixed", "update_mixed", "patch_sweep64", "patch_resid64", "force64",
-    "refine64", "reduce"};
+    "refine64", "reduce", "sweep64_coarse", "sweep32_coarse", "patch_sweep64_coarse"};
 
 int mg5_profile_enable(mg5_ctx *ctx, int on)
 {
@@ -1038,7 +1047,7 @@ struct RunPatch {
         mg5_ctx *ctx = this->ctx;
         const double cells = (double)int_cells(h->q[l]);
         {
-            ProfScope ps(&ctx->prof, PK_PATCH_SWEEP, st, cells);
+            ProfScope ps(&ctx->prof, l == 0 ? PK_PATCH_SWEEP : PK_PATCH_SWEEPC, st, cells);
             CK(launch_patch_sweep(h->v[l], h->tmp[l], h->f[l], 0.0, h->q[l],
                                   make_coef<double>(hl[l], p->alpha), &ctx->cnt->clamped, st,
                                   l > 0 ? h->v0[l] : nullptr, l > 0 ? ghost_w(l) : 0.0));

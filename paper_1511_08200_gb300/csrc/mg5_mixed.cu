@@ -99,7 +99,7 @@ struct RunMix {
 
     int sweep(int l)
     {
-        ProfScope ps(sh.prof, PK_SWEEP32, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
+        ProfScope ps(sh.prof, l == 0 ? PK_SWEEP32 : PK_SWEEP32C, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
         const CoefT<float> cf = make_coef<float>(hl[l], p->alpha);
         cudaError_t e =
             h->n[l] >= kFusedMinN

@@ -10,7 +10,7 @@
 namespace mg5 {
 
 enum ProfKernel {
-    PK_SWEEP64 = 0,      // one full snapshot red-black sweep, FP64 (2 launches)
+    PK_SWEEP64 = 0,      // one full snapshot red-black sweep on the finest grid, FP64 (2 launches)
     PK_RESTRICT64,       // residual + 8-child restriction, FP64
     PK_COARSE_RHS64,
     PK_PROLONG64,
@@ -27,6 +27,9 @@ enum ProfKernel {
     PK_FORCE,
     PK_REFINE,
     PK_REDUCE,           // finalize / sums / scale / gauge
+    PK_SWEEP64C,         // the same sweeps on the coarse grids of the hierarchy
+    PK_SWEEP32C,
+    PK_PATCH_SWEEPC,
     PK_COUNT
 };
 

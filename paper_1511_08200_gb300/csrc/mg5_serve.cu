@@ -38,6 +38,15 @@ struct Job {
     double t_submit;
 };
 
+// The footprint a request needs on a worker that holds nothing: the cached
+// graph of a mixed solve, the hierarchy of an FP64 solve.
+int request_bytes(const mg5_request &r, size_t *need)
+{
+    if (r.params.precision == MG5_MIXED)
+        return mg5_graph_workspace_bytes(r.N, r.grad != nullptr, need);
+    return mg5_workspace_bytes(r.N, r.params.precision, need);
+}
+
 }  // namespace
 
 struct mg5_server {
@@ -99,6 +108,21 @@ static void worker_main(mg5_server *srv, int w)
                     if (total + extra > srv->budget) {
                         if (srv->held[w] > 0) {
                             release_own(lk);
+                            continue;
+                        }
+                        if (srv->running == 0 && total == 0) {
+                            // cannot fit on an empty server: complete it as out of memory
+                            mg5_completion c;
+                            std::memset(&c, 0, sizeof(c));
+                            c.tag = srv->queue.front().req.tag;
+                            c.t_submit = srv->queue.front().t_submit;
+                            c.t_admit = c.t_done = now_s() - srv->t0;
+                            c.status = MG5_E_OOM;
+                            c.info.status = MG5_E_OOM;
+                            srv->queue.pop_front();
+                            srv->pressure = false;
+                            srv->done.push_back(c);
+                            srv->cv_done.notify_all();
                             continue;
                         }
                         srv->pressure = true;
@@ -177,7 +201,7 @@ int mg5_server_submit(mg5_server *s, const mg5_request *req)
     if (!s || !req || !req->delta || !req->phi)
         return MG5_E_ARG;
     size_t need = 0;
-    if (mg5_workspace_bytes(req->N, req->params.precision, &need) != MG5_OK)
+    if (request_bytes(*req, &need) != MG5_OK)
         return MG5_E_ARG;
     if (s->budget && need > s->budget)
         return MG5_E_OOM;   // could never be admitted

@@ -60,7 +60,7 @@ def test_server_respects_hbm_budget():
     import torch
     mg = _mg()
     alpha, s, h = nominal()
-    one = mg.workspace_bytes(96, "mixed")
+    one = mg.graph_workspace_bytes(96)     # a served mixed solve holds its cached graph
     budget = int(1.5 * one)
     srv = mg.Server(0, slots=3, hbm_budget_bytes=budget)
     d = dev(workload.lognormal_delta(96, 1.0, 3))
@@ -81,5 +81,10 @@ def test_server_respects_hbm_budget():
         srv.submit(dev(np.zeros((256,) * 3)), p, torch.zeros((256,) * 3, dtype=torch.float64,
                                                                device="cuda"), tag=99)
     srv.close()
+    # a budget below one request: it completes as out of memory instead of waiting
+    tiny = mg.Server(0, slots=2, hbm_budget_bytes=one // 2)
+    with pytest.raises(mg.MG5Error):
+        tiny.submit(d, p, torch.zeros_like(d), tag=1)
+    tiny.close()
     for x in phis[1:]:
         assert torch.equal(x, phis[0])
