@@ -53,6 +53,7 @@ extern "C" {
 #define MG5_E_NOT_CONVERGED -4   /* max_cycles reached; phi holds the last iterate */
 #define MG5_E_DIVERGED      -5   /* residual grew 10x above its best after >= 3 cycles */
 #define MG5_E_NONFINITE     -6   /* NaN or Inf in the residual */
+#define MG5_E_TOO_LARGE     -7   /* the grid exceeds an entry point's fixed scratch */
 
 /* ------------------------------------------------------------ precision */
 #define MG5_FP64  0   /* every kernel in FP64 */
@@ -272,6 +273,27 @@ double mg5_server_clock(mg5_server *srv);
 size_t mg5_server_bytes_held(mg5_server *srv);
 /* Finish every queued request, stop the workers, free everything. */
 int mg5_server_destroy(mg5_server *srv);
+
+/* ------------------------------------------------------------ without allocation
+ * For callers that cannot allocate device memory (code running inside a memory
+ * pool or allocator it does not own, inside regions where an allocation would
+ * synchronise the device or break an enclosing capture, or hosts that only
+ * lend buffers they own).  This entry point has no counterpart in the paper:
+ * it is the residual norm of the solve's stopping test (no context needed).
+ *   out (device, 3 doubles) = mean r, ||r - mean r||_2, ||r||_2 for
+ *   r = f + c - op(phi) on the periodic N^3 grid, op the operator of Eq. (eomvarphi)
+ *   (phi, f: device, N^3 doubles, row-major, not modified; c, h, alpha as in the solve).
+ * Its block partial sums live in a fixed file-scope device array of 8192
+ * double2 (128 KiB), held by every GPU that loads the library until the
+ * process exits: N^3 may be at most mg5_residual_norm_noalloc_max_cells()
+ * (2,097,152, i.e. N <= 128); larger grids return MG5_E_TOO_LARGE.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array,
+ * so calls that overlap on the GPU (different streams, concurrent threads)
+ * race; each call overwrites every slot it reads.  No cudaMalloc, no cudaFree. */
+int mg5_residual_norm_noalloc(const double *phi, const double *f, double c, int N, double h,
+                              double alpha, double *out, void *stream);
+long long mg5_residual_norm_noalloc_max_cells(void);
 
 /* ------------------------------------------------------------ tracing
  * Per-kernel-class device time, measured with CUDA events recorded on the

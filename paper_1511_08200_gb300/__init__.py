@@ -24,7 +24,7 @@ if not os.path.exists(_LIB_PATH):
 _lib = ctypes.CDLL(_LIB_PATH)
 
 OK, W_DISC_CLAMP = 0, 1
-E_ARG, E_OOM, E_CUDA, E_NOT_CONVERGED, E_DIVERGED, E_NONFINITE = -1, -2, -3, -4, -5, -6
+E_ARG, E_OOM, E_CUDA, E_NOT_CONVERGED, E_DIVERGED, E_NONFINITE, E_TOO_LARGE = -1, -2, -3, -4, -5, -6, -7
 FP64, MIXED = 0, 1
 WARM, HOST_IO, FMG_START, GRAPH = 1, 2, 4, 8
 
@@ -109,6 +109,8 @@ _sigs = {
     "mg5_server_clock": ([_P], _c_double),
     "mg5_server_bytes_held": ([_P], _c_size_t),
     "mg5_server_destroy": ([_P], _c_int),
+    "mg5_residual_norm_noalloc": ([_P, _P, _c_double, _c_int, _c_double, _c_double, _P, _P], _c_int),
+    "mg5_residual_norm_noalloc_max_cells": ([], ctypes.c_longlong),
     "mg5_profile_enable": ([_P, _c_int], _c_int),
     "mg5_profile_read": ([_P, _P, _P, _c_int], _c_int),
     "mg5_profile_name": ([_c_int], ctypes.c_char_p),
@@ -463,6 +465,24 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def residual_norm_noalloc(phi, f, c: float, h: float, alpha: float, out=None, stream=None):
+    """mg5_residual_norm_noalloc: (mean r, ||r - mean r||, ||r||) of r = f + c - op(phi) into a
+    3-element float64 device tensor, with no device allocation by the library (its partial
+    sums live in a fixed device array; N^3 <= residual_norm_noalloc_max_cells())."""
+    import torch
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device=phi.device)
+    rc = _lib.mg5_residual_norm_noalloc(_ptr(phi), _ptr(f), c, int(phi.shape[0]), h, alpha,
+                                        _ptr(out), _stream(stream))
+    if rc != OK:
+        raise MG5Error(rc, "residual_norm_noalloc")
+    return out
+
+
+def residual_norm_noalloc_max_cells() -> int:
+    return _lib.mg5_residual_norm_noalloc_max_cells()
 
 
 def _host_ptr(a):

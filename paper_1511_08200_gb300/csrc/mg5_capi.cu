@@ -657,6 +657,7 @@ const char *mg5_status_string(int s)
     case MG5_E_NOT_CONVERGED: return "not converged within max_cycles";
     case MG5_E_DIVERGED: return "diverged";
     case MG5_E_NONFINITE: return "non-finite residual";
+    case MG5_E_TOO_LARGE: return "grid exceeds the entry point's fixed scratch";
     default: return "unknown status";
     }
 }
