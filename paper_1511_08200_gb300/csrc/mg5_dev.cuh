@@ -26,17 +26,26 @@ struct CoefT {
     T a_h4;    // alpha / h^4
     T k8;      // 8 alpha / 3
     T k23;     // 2 alpha / 3
+    T s23;     // (2/3) alpha / h^4: weight of t = a^2 + b c in alpha Sigma
+    T s8;      // alpha / (8 h^4): weight of d2 = sum (4 h^2 D_ab)^2 in alpha Sigma
+    float k8f;   // 8 alpha / 3, for the FP32 estimate of the FP64 root
+    float k43f;  // 4 alpha / 3 (slope of the quadratic is 1 + k43 L)
 };
 
 template <typename T>
 __host__ __device__ inline CoefT<T> make_coef(double h, double alpha)
 {
     CoefT<T> c;
+    const double h4 = h * h * h * h;
     c.h2 = (T)(h * h);
     c.inv_h2 = (T)(1.0 / (h * h));
-    c.a_h4 = (T)(alpha / (h * h * h * h));
+    c.a_h4 = (T)(alpha / h4);
     c.k8 = (T)(8.0 * alpha / 3.0);
     c.k23 = (T)(2.0 * alpha / 3.0);
+    c.s23 = (T)(2.0 * alpha / (3.0 * h4));
+    c.s8 = (T)(alpha / (8.0 * h4));
+    c.k8f = (float)(8.0 * alpha / 3.0);
+    c.k43f = (float)(4.0 * alpha / 3.0);
     return c;
 }
 
@@ -115,17 +124,22 @@ __device__ __forceinline__ void gather(const T *F, const T *E, const Rows &r, in
     s.ymzm = E[r.r0m + km];
 }
 
-// S = sum of the 6 faces; sig = Sigma * h^4.
+// S = sum of the 6 faces; t and d2 with Sigma h^4 = (2/3) t + d2 / 8:
+// a = sx - sy, b = sx - sz, c = sy - sz (sx = faces along x, ...) satisfy c = b - a,
+// so (1/3)(a^2 + b^2 + c^2) = (2/3)(a^2 + b c) = (2/3) t; d2 = dxy^2 + dxz^2 + dyz^2
+// with dab = 4 h^2 D_ab.  Every term is a difference of neighbours: no cancellation
+// against the (much larger) field values.
 template <typename T>
-__device__ __forceinline__ void stencil_parts(const St<T> &s, T &S, T &sig)
+__device__ __forceinline__ void stencil_parts(const St<T> &s, T &S, T &t, T &d2)
 {
     const T sx = s.xp + s.xm, sy = s.yp + s.ym, sz = s.zp + s.zm;
     S = sx + sy + sz;
+    const T a = sx - sy, b = sx - sz, c = sy - sz;
+    t = a * a + b * c;
     const T dxy = (s.xpyp - s.xpym) - (s.xmyp - s.xmym);
     const T dxz = (s.xpzp - s.xpzm) - (s.xmzp - s.xmzm);
     const T dyz = (s.ypzp - s.ypzm) - (s.ymzp - s.ymzm);
-    const T a = sx - sy, b = sx - sz, c = sy - sz;
-    sig = (a * a + b * b + c * c) * (T)(1.0 / 3.0) + (dxy * dxy + dxz * dxz + dyz * dyz) * (T)0.125;
+    d2 = dxy * dxy + dxz * dxz + dyz * dyz;
 }
 
 // Physical root of (2 alpha/3) L^2 + L - b = 0, L = 2b / (1 + sqrt(1 + 8 alpha b / 3));
@@ -138,7 +152,10 @@ __device__ __forceinline__ void stencil_parts(const St<T> &s, T &S, T &sig)
 // is instead estimated in FP32 and refined by two Newton steps of the quadratic
 // q(L) = (2 alpha/3) L^2 + L - b (the update of Eq. newton) in FP64, with the
 // FP32 reciprocal of q'(L) held fixed: the relative error goes ~1e-7 -> ~1e-14
-// -> below FP64 rounding.
+// -> below FP64 rounding.  The branch tests also run in FP32: the FP32
+// discriminant is within ~1e-7 of the FP64 one, so df >= 4e-3 guarantees the
+// FP64 discriminant is above 1e-3, where Newton converges as stated; below it
+// (near the double root, or clamped) the closed form runs in FP64.
 __device__ __forceinline__ float physical_root(float b, float k8, bool &clamped)
 {
     float disc = fmaf(k8, b, 1.0f);
@@ -149,30 +166,36 @@ __device__ __forceinline__ float physical_root(float b, float k8, bool &clamped)
     return __fdividef(2.0f * b, 1.0f + disc * rsqrtf(disc));
 }
 
-__device__ __forceinline__ double physical_root(double b, double k8, bool &clamped)
+__device__ __forceinline__ float physical_root(float b, const CoefT<float> &cf, bool &clamped)
+{
+    return physical_root(b, cf.k8, clamped);
+}
+
+__device__ __forceinline__ double physical_root(double b, const CoefT<double> &cf, bool &clamped)
 {
 #ifdef MG5_IEEE_ROOT
-    double disc = 1.0 + k8 * b;
+    double disc = 1.0 + cf.k8 * b;
     if (disc < 0.0) {
         disc = 0.0;
         clamped = true;
     }
     return 2.0 * b / (1.0 + sqrt(disc));
 #else
-    const double disc = fma(k8, b, 1.0);
-    if (disc < 0.0) {
-        clamped = true;
-        return 2.0 * b;
-    }
-    if (disc < 1e-3)   // near the double root Newton slows down: closed form
-        return 2.0 * b / (1.0 + sqrt(disc));
     const float bf = (float)b;
-    const float df = fmaxf(fmaf((float)k8, bf, 1.0f), 0.0f);
-    double L = (double)__fdividef(2.0f * bf, 1.0f + sqrtf(df));
-    const double k23 = 0.25 * k8;  // 2 alpha / 3
-    const double r = (double)__frcp_rn((float)fma(2.0 * k23, L, 1.0));
-    L = fma(-fma(fma(k23, L, 1.0), L, -b), r, L);
-    L = fma(-fma(fma(k23, L, 1.0), L, -b), r, L);
+    const float df = fmaf(cf.k8f, bf, 1.0f);
+    if (df < 4e-3f) {
+        const double disc = fma(cf.k8, b, 1.0);
+        if (disc < 0.0) {
+            clamped = true;
+            return 2.0 * b;
+        }
+        return 2.0 * b / (1.0 + sqrt(disc));
+    }
+    const float Lf = __fdividef(2.0f * bf, 1.0f + sqrtf(df));
+    const double r = (double)__frcp_rn(fmaf(cf.k43f, Lf, 1.0f));
+    double L = (double)Lf;
+    L = fma(-fma(fma(cf.k23, L, 1.0), L, -b), r, L);
+    L = fma(-fma(fma(cf.k23, L, 1.0), L, -b), r, L);
     return L;
 #endif
 }
@@ -181,10 +204,10 @@ __device__ __forceinline__ double physical_root(double b, double k8, bool &clamp
 template <typename T>
 __device__ __forceinline__ T cell_update(const St<T> &s, T rhs, const CoefT<T> &cf, bool &clamped)
 {
-    T S, sig;
-    stencil_parts(s, S, sig);
-    const T b = rhs + cf.a_h4 * sig;
-    const T L = physical_root(b, cf.k8, clamped);
+    T S, t, d2;
+    stencil_parts(s, S, t, d2);
+    const T b = rhs + cf.s8 * d2 + cf.s23 * t;   // rhs + alpha Sigma
+    const T L = physical_root(b, cf, clamped);
     return (S - cf.h2 * L) * (T)(1.0 / 6.0);
 }
 
@@ -192,10 +215,10 @@ __device__ __forceinline__ T cell_update(const St<T> &s, T rhs, const CoefT<T> &
 template <typename T>
 __device__ __forceinline__ T cell_op(const St<T> &s, const CoefT<T> &cf)
 {
-    T S, sig;
-    stencil_parts(s, S, sig);
+    T S, t, d2;
+    stencil_parts(s, S, t, d2);
     const T L = (S - (T)6 * s.c) * cf.inv_h2;
-    return L + cf.k23 * L * L - cf.a_h4 * sig;
+    return L + cf.k23 * L * L - cf.s8 * d2 - cf.s23 * t;
 }
 
 // ---- correction form (mixed precision) -------------------------------------
