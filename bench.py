@@ -267,6 +267,15 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     coarse, patch, origin = make_inputs()
     step = Step(mg, torch, coarse, patch, origin, dev)
+    tune = {}
+    if not args.no_autotune:
+        # sweep schedules of every grid side, timed before the warm-up (not in the timed region)
+        t0 = time.perf_counter()
+        step.ctx.autotune(N_COARSE, "fp64")
+        step.ctx2.autotune(N_COARSE, "mixed")
+        tune = {"seconds": time.perf_counter() - t0,
+                "fp64": schedules(mg, dev.index or 0, "fp64", N_COARSE),
+                "mixed": schedules(mg, dev.index or 0, "mixed", N_COARSE)}
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         step.run()
@@ -362,18 +371,70 @@ def run_ours(args):
         "e2e": ({"value": e2e_cu / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                  "d2h_bytes_per_step": d2h} if e2e_ms > 0 else None),
         "gpu_launches": launches,
+        "autotune": tune or None,
     }
+    out["geff"] = geff_report(step)
     if not args.no_batch:
-        out["batch"] = run_batch(mg, torch, dev, step.alpha, step.s)
+        out["batch"] = run_batch(mg, torch, dev, step.alpha, step.s, autotune=not args.no_autotune)
     if args.serve_seconds > 0:
         out["serving"] = run_serving(mg, torch, dev, step.alpha, step.s, args.serve_seconds,
-                                     slots=args.serve_slots)
+                                     slots=args.serve_slots, autotune=not args.no_autotune)
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(coarse, patch, origin, budget_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
 
 
-def run_batch(mg, torch, dev, alpha, s, reps=5):
+def geff_report(step):
+    """Eq. (errors2) quantities on the refinement workload (once, outside the timed region):
+    the GR force from the same engine at alpha = 0 with source (3 beta / 2) s delta
+    (Eq. modpoisson), on the domain grid and relaxed on the patch like the fifth force;
+    F5 = grad(phi) / 2.  Reports F5/F_GR on the domain and on the patch (screening lowers it
+    below the linear value 1/(3 beta)), eps_trunc = |F5_trunc - F5_full| / |F5_full| and
+    the G_eff error it causes, |F5_trunc - F5_full| / |F_GR| = (F5_full/F_GR) eps_trunc."""
+    mg, torch, ctx = step.mg, step.torch, step.ctx
+    n, pf = N_COARSE, 2 * PN
+    s_gr = 1.5 * step.beta * step.s
+    p_gr = mg.default_params(alpha=0.0, s=s_gr, h=H_COARSE, tol=TOL64)
+    p_grp = mg.default_params(alpha=0.0, s=s_gr, h=H_COARSE / 2, tol=TOL64)
+    psi = torch.zeros_like(step.phi)
+    g_psi = torch.empty_like(step.grad)
+    _, _, ig = ctx.solve_fifth_force(step.d_c, p_gr, phi=psi, grad=g_psi)
+    box = torch.empty_like(step.box)
+    ctx.refine_interpolate(psi, step.origin, (PN, PN, PN), 1, out=box)
+    ctx.relax_patch(step.d_p, p_grp, ig.compat_c, box)
+    g_gr = torch.empty_like(step.g_full)
+    ctx.force(box, H_COARSE / 2, ghost=1, periodic=False, grad=g_gr)
+    torch.cuda.synchronize()
+    mag = lambda g: torch.linalg.vector_norm(g, dim=0)
+    r_dom = 0.5 * mag(step.grad) / mag(g_psi)
+    r_full = 0.5 * mag(step.g_full) / mag(g_gr)
+    r_tr = 0.5 * mag(step.g_tr) / mag(g_gr)
+    d5 = 0.5 * mag(step.g_tr - step.g_full)
+    eps = d5 / (0.5 * mag(step.g_full))
+    dgeff = d5 / mag(g_gr)
+    q = lambda t: [float(x) for x in torch.quantile(t.flatten()[::7].float(), torch.tensor([0.5, 0.99], device=t.device))]
+    return {"linear_ratio_1_over_3beta": 1.0 / (3.0 * step.beta),
+            "f5_over_fgr_domain_p50_p99": q(r_dom), "f5_over_fgr_patch_p50_p99": q(r_full),
+            "f5_over_fgr_patch_trunc_p50_p99": q(r_tr),
+            "eps_trunc_rel_l2": float(torch.linalg.vector_norm(step.g_tr - step.g_full)
+                                      / torch.linalg.vector_norm(step.g_full)),
+            "eps_trunc_p50_p99": q(eps),
+            "geff_error_p50_p99": q(dgeff),
+            "gr_cycles": ig.cycles}
+
+
+def schedules(mg, device, prec, n):
+    """The sweep schedule of every non-coarsest grid side of n's hierarchy, as text."""
+    out = {}
+    while n % 2 == 0 and n // 2 >= 4:
+        sch, tuned = mg.schedule_get(device, prec, n)
+        txt = ("fused/%d" % sch.chunk) if sch.form == mg.SWEEP_FUSED else ("two-pass/%d" % sch.block)
+        out[str(n)] = txt + ("" if tuned else " (default)")
+        n //= 2
+    return out
+
+
+def run_batch(mg, torch, dev, alpha, s, reps=5, autotune=True):
     """The batched workload: 96 boxes, sizes uniform from {32,48,64,96,128}, seeds 1000 + b,
     alpha log-uniform in [0.1, 10] x nominal, mixed precision to 1e-8, solved as ONE
     CUDA-graph launch; compared with the same boxes solved one after another."""
@@ -387,6 +448,11 @@ def run_batch(mg, torch, dev, alpha, s, reps=5):
     phis = [torch.zeros_like(d) for d in deltas]
     grads = [torch.empty((3,) + d.shape, dtype=torch.float64, device=dev) for d in deltas]
     ctx = mg.Context(dev.index or 0)
+    t0 = time.perf_counter()
+    if autotune:
+        for n in sorted(set(int(x) for x in sizes)):
+            ctx.autotune(n, "mixed")
+    tune_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     ctx.solve_batch(deltas, params, phis=phis, grads=grads)          # capture + first launch
     build_s = time.perf_counter() - t0
@@ -416,11 +482,12 @@ def run_batch(mg, torch, dev, alpha, s, reps=5):
     ctx.close()
     return {"boxes": 96, "cells": cells, "ms_per_batch": t, "cell_updates_per_s": cu / (t / 1e3),
             "time_to_tol_ms": t, "sequential_ms": float(np.median(seq_ms)),
-            "graph_build_s": build_s, "max_rel_residual": worst,
+            "graph_build_s": build_s, "autotune_s": tune_s, "max_rel_residual": worst,
             "outer_iters": [i.outer_iters for i in infos][:8], "dtype": "f32+f64"}
 
 
-def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=None):
+def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=None,
+                autotune=True):
     """Poisson arrivals at `rate` req/s for `seconds`: sides 16 round(10^U(log 32, log 256)/16),
     sigma ~ U(0.5, 2), tol 1e-6 or 1e-8 with p = 1/2, mixed precision; admitted by HBM footprint.
     Latency = completion - arrival (server clock); the first fifth of the run is discarded."""
@@ -436,11 +503,19 @@ def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=
         for b in range(4):
             pool[(n, b)] = workload.lognormal_delta_torch(n, 0.5 + 0.5 * b, 5000 + 7 * n + b, dev)
     budget = int(torch.cuda.get_device_properties(dev).total_memory * 0.5)
+    if autotune:   # the schedule table is process-wide: the server's captures read it
+        tctx = mg.Context(dev.index or 0)
+        for n in sorted(set(int(x) for x in sizes)):
+            tctx.autotune(n, "mixed")
+        tctx.close()
     srv = mg.Server(dev.index or 0, slots=slots, hbm_budget_bytes=budget)
-    # warm the workers' hierarchies on every size once (not timed)
+    # warm the server's graph pool (two entries per (size, tolerance): its cap) before timing
     for i, n in enumerate(sorted(set(int(x) for x in sizes))):
-        p = mg.default_params(alpha=alpha, s=s, h=L_BOX / 512, tol=1e-6, precision="mixed")
-        srv.submit(pool[(n, 0)], p, torch.zeros_like(pool[(n, 0)]), tag=10 ** 9 + i)
+        for j, tol in enumerate((1e-6, 1e-8)):
+            p = mg.default_params(alpha=alpha, s=s, h=L_BOX / 512, tol=tol, precision="mixed")
+            for r in range(2):
+                srv.submit(pool[(n, 0)], p, torch.zeros_like(pool[(n, 0)]),
+                           tag=10 ** 9 + 4 * i + 2 * j + r)
     while srv.pending() != (0, 0):
         srv.poll(wait_ms=50)
     srv.poll(max_n=1000)
@@ -467,6 +542,7 @@ def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=
     while len(done) < submitted:
         for c in srv.poll(wait_ms=100):
             done[c.tag] = c
+    stats = srv.stats()
     srv.close()
     warm = seconds / 5.0 if warm_s is None else warm_s
     rows = [c for c in done.values() if c.t_submit - t_start >= warm]
@@ -481,7 +557,7 @@ def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(lat.mean()), "max": float(lat.max())},
             "mean_cells_per_request": float(np.mean([int(sizes[c.tag]) ** 3 for c in rows])),
-            "hbm_budget_bytes": budget}
+            "hbm_budget_bytes": budget, "server": stats}
 
 
 def roofline(prof: dict, peaks: dict, steps: int) -> dict:
@@ -555,6 +631,11 @@ def run_mixed_workload(args):
     grad = torch.empty((3,) + d.shape, dtype=torch.float64, device=dev)
     ctx = mg.Context(local)
     p = mg.default_params(alpha=alpha, s=s, h=L_BOX / 512, tol=TOLMIX, precision="mixed")
+    tune = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        ctx.autotune(n, "mixed")
+        tune = {"seconds": time.perf_counter() - t0, "mixed": schedules(mg, local, "mixed", n)}
     for _ in range(args.warmup):
         ctx.solve_fifth_force(d, p, phi=phi, grad=grad)
     torch.cuda.synchronize()
@@ -590,7 +671,7 @@ def run_mixed_workload(args):
            "roofline": roofline(prof, _peaks(), args.steps),
            "kernels": {k: {"ms": v[0] / args.steps, "launches": v[1] // args.steps}
                        for k, v in prof.items() if v[1] > 0},
-           "clocks": clk}
+           "clocks": clk, "autotune": tune}
     print(json.dumps(out), flush=True)
 
 
@@ -633,7 +714,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-box batched workload")
-    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default sweep schedules instead of the tuned ones")
     ap.add_argument("--serve-seconds", type=float, default=6.0,
                     help="length of the serving run (0 skips it)")
     args = ap.parse_args()

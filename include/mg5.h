@@ -47,6 +47,7 @@ extern "C" {
 /* ------------------------------------------------------------ status codes */
 #define MG5_OK               0
 #define MG5_W_DISC_CLAMP     1   /* converged, but some cell had no real root (clamped, counted) */
+#define MG5_W_UNTUNED        2   /* mg5_schedule_get: no tuned entry, *out is the default */
 #define MG5_E_ARG           -1   /* bad size, pointer or parameter */
 #define MG5_E_OOM           -2   /* scratch would exceed the context's HBM budget */
 #define MG5_E_CUDA          -3   /* a CUDA call failed; see mg5_last_error */
@@ -139,6 +140,15 @@ const char *mg5_last_error(mg5_ctx *ctx);
 size_t mg5_bytes_held(mg5_ctx *ctx);
 /* Release every cached hierarchy (scratch) the context holds. */
 int mg5_release(mg5_ctx *ctx);
+/* How the context's solves wait for the GPU on the host (the per-cycle residual
+ * read and the end of a solve): on = 1 sleeps on a blocking-sync event, on = 0
+ * (default) spins, which answers sooner but holds a CPU core.  Many threads
+ * solving at once on few cores (the server's workers) should sleep. */
+int mg5_set_blocking_wait(mg5_ctx *ctx, int on);
+/* on = 1: a solve (or batch, or MG5_GRAPH capture) first tunes the sweep schedule
+ * of every grid side of its hierarchy that has no entry yet (mg5_autotune), before
+ * any capture begins.  Default 0: untuned sides use the default schedule. */
+int mg5_set_autotune(mg5_ctx *ctx, int on);
 /* Bytes a solve of side N at `precision` would add to the context: 0 when its
  * hierarchy is already resident, else mg5_workspace_bytes. */
 int mg5_cached_bytes(mg5_ctx *ctx, int N, int precision, size_t *extra);
@@ -236,6 +246,46 @@ int mg5_solve_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const in
                     const mg5_params *p, double *const *phi, double *const *grad, mg5_info *info,
                     void *stream);
 
+/* ------------------------------------------------------------ autotuner
+ * The smoother's schedule changes speed, not values: the two-pass sweep (a red
+ * and a black kernel, `block` threads per block) or the fused plane-march
+ * (one kernel, each CTA marching over `chunk` planes; 0 = enough CTAs for
+ * several waves) apply the same cell update of Sec. 3.1 to the same snapshot.
+ * The table is process-wide, keyed by (device, precision, grid side n); solves,
+ * batch captures and MG5_GRAPH captures read it when they start (a captured
+ * graph keeps the schedule it was captured with).  Defaults: FP64 two-pass with
+ * 256 threads; the mixed mode's FP32 correction form fused where n >= 32 and
+ * n % 4 == 0. */
+#define MG5_SWEEP_TWO_PASS 0
+#define MG5_SWEEP_FUSED    1
+typedef struct {
+    int form;    /* MG5_SWEEP_TWO_PASS or MG5_SWEEP_FUSED */
+    int block;   /* threads per block of the two-pass kernels (32 .. 1024, a multiple of 32) */
+    int chunk;   /* planes per CTA of the fused kernel (0 = automatic) */
+    float ms;    /* the tuner's median time of one sweep (0 when set by hand) */
+} mg5_schedule;
+/* Time every candidate schedule (two-pass with 64/128/256/512 threads, fused with
+ * 8/16/32 planes where it fits) on a synthetic field of each grid side of the
+ * hierarchy of N (coarsest excluded) on ctx's device and stream, and record the
+ * fastest; sides already in the table are kept.  Synchronises `stream`; must not
+ * run during a stream capture.  Allocates (and frees) 3-4 grids of the side. */
+int mg5_autotune(mg5_ctx *ctx, int N, int precision, void *stream);
+/* The schedule of (device, precision, n): MG5_OK if tuned or set, MG5_W_UNTUNED
+ * with the default in *out otherwise. */
+int mg5_schedule_get(int device, int precision, int n, mg5_schedule *out);
+/* Set a schedule by hand (MG5_E_ARG for an invalid one). */
+int mg5_schedule_set(int device, int precision, int n, const mg5_schedule *s);
+/* Forget every entry (all devices). */
+int mg5_tune_clear(void);
+/* Write the table as JSON lines ({"gpu", "precision", "n", "form", "block",
+ * "chunk", "ms"}), keyed by the GPU's name so a table tuned on one GPU model
+ * loads on any GPU of that model. */
+int mg5_tune_save(const char *path);
+/* Apply the lines of a saved table whose GPU name matches a visible device:
+ * returns how many entries were applied (>= 0), MG5_E_ARG for an unreadable
+ * file or a malformed line (the well-formed lines are still applied). */
+int mg5_tune_load(const char *path);
+
 /* ------------------------------------------------------------ serving
  * A continuous-batching solve server: `slots` worker threads, each with its
  * own context (resident hierarchies) and CUDA stream.  Requests are admitted
@@ -272,6 +322,15 @@ int mg5_server_pending(mg5_server *srv, int *queued, int *running);
 double mg5_server_clock(mg5_server *srv);
 size_t mg5_server_bytes_held(mg5_server *srv);
 /* Finish every queued request, stop the workers, free everything. */
+/* Counters of a server since creation: captured graphs built, the seconds spent
+ * building them (allocation + capture + instantiation), idle entries evicted for
+ * memory, requests that ran host-driven because no graph could be built, and
+ * admissions that had to wait for memory. */
+typedef struct {
+    long long builds, evictions, fallbacks, memory_waits, completed;
+    double build_seconds;
+} mg5_server_stats;
+int mg5_server_get_stats(mg5_server *s, mg5_server_stats *out);
 int mg5_server_destroy(mg5_server *srv);
 
 /* ------------------------------------------------------------ without allocation

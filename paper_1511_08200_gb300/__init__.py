@@ -23,7 +23,8 @@ if not os.path.exists(_LIB_PATH):
 
 _lib = ctypes.CDLL(_LIB_PATH)
 
-OK, W_DISC_CLAMP = 0, 1
+OK, W_DISC_CLAMP, W_UNTUNED = 0, 1, 2
+SWEEP_TWO_PASS, SWEEP_FUSED = 0, 1
 E_ARG, E_OOM, E_CUDA, E_NOT_CONVERGED, E_DIVERGED, E_NONFINITE, E_TOO_LARGE = -1, -2, -3, -4, -5, -6, -7
 FP64, MIXED = 0, 1
 WARM, HOST_IO, FMG_START, GRAPH = 1, 2, 4, 8
@@ -74,10 +75,21 @@ class _Request(ctypes.Structure):
                 ("grad", _c_void_p), ("tag", ctypes.c_ulonglong)]
 
 
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("builds", ctypes.c_longlong), ("evictions", ctypes.c_longlong),
+                ("fallbacks", ctypes.c_longlong), ("memory_waits", ctypes.c_longlong),
+                ("completed", ctypes.c_longlong), ("build_seconds", _c_double)]
+
+
 class _Completion(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_ulonglong), ("status", _c_int), ("pad", _c_int),
                 ("t_submit", _c_double), ("t_admit", _c_double), ("t_done", _c_double),
                 ("info", _Info)]
+
+
+class Schedule(ctypes.Structure):
+    """mg5_schedule: how one grid side is swept (form, two-pass block, fused chunk, tuned ms)."""
+    _fields_ = [("form", _c_int), ("block", _c_int), ("chunk", _c_int), ("ms", ctypes.c_float)]
 
 
 _P = _c_void_p
@@ -109,6 +121,15 @@ _sigs = {
     "mg5_server_clock": ([_P], _c_double),
     "mg5_server_bytes_held": ([_P], _c_size_t),
     "mg5_server_destroy": ([_P], _c_int),
+    "mg5_server_get_stats": ([_P, _P], _c_int),
+    "mg5_set_blocking_wait": ([_P, _c_int], _c_int),
+    "mg5_set_autotune": ([_P, _c_int], _c_int),
+    "mg5_autotune": ([_P, _c_int, _c_int, _P], _c_int),
+    "mg5_schedule_get": ([_c_int, _c_int, _c_int, _P], _c_int),
+    "mg5_schedule_set": ([_c_int, _c_int, _c_int, _P], _c_int),
+    "mg5_tune_clear": ([], _c_int),
+    "mg5_tune_save": ([ctypes.c_char_p], _c_int),
+    "mg5_tune_load": ([ctypes.c_char_p], _c_int),
     "mg5_residual_norm_noalloc": ([_P, _P, _c_double, _c_int, _c_double, _c_double, _P, _P], _c_int),
     "mg5_residual_norm_noalloc_max_cells": ([], ctypes.c_longlong),
     "mg5_profile_enable": ([_P, _c_int], _c_int),
@@ -178,6 +199,46 @@ def graph_workspace_bytes(n: int, with_grad: bool = False) -> int:
     return out.value
 
 
+def _prec(precision) -> int:
+    if isinstance(precision, str):
+        return {"fp64": FP64, "mixed": MIXED}[precision]
+    return int(precision)
+
+
+def schedule_get(device: int, precision, n: int):
+    """mg5_schedule_get: (Schedule, tuned?) of (device, precision, n)."""
+    out = Schedule()
+    rc = _lib.mg5_schedule_get(device, _prec(precision), n, ctypes.byref(out))
+    if rc not in (OK, W_UNTUNED):
+        raise MG5Error(rc, "schedule_get")
+    return out, rc == OK
+
+
+def schedule_set(device: int, precision, n: int, form: int, block: int = 256, chunk: int = 0):
+    s = Schedule(form, block, chunk, 0.0)
+    rc = _lib.mg5_schedule_set(device, _prec(precision), n, ctypes.byref(s))
+    if rc != OK:
+        raise MG5Error(rc, "schedule_set")
+
+
+def tune_clear():
+    _lib.mg5_tune_clear()
+
+
+def tune_save(path: str):
+    rc = _lib.mg5_tune_save(str(path).encode())
+    if rc != OK:
+        raise MG5Error(rc, "tune_save %s" % path)
+
+
+def tune_load(path: str) -> int:
+    """Applies a saved table; returns the number of entries that matched a visible GPU."""
+    rc = _lib.mg5_tune_load(str(path).encode())
+    if rc < 0:
+        raise MG5Error(rc, "tune_load %s" % path)
+    return rc
+
+
 def workspace_bytes(n: int, precision=FP64) -> int:
     if isinstance(precision, str):
         precision = {"fp64": FP64, "mixed": MIXED}[precision]
@@ -244,6 +305,18 @@ class Context:
 
     def release(self):
         _lib.mg5_release(self._h)
+
+    def set_autotune(self, on: bool = True):
+        """mg5_set_autotune: tune untuned grid sides before each solve / batch capture."""
+        self._check(_lib.mg5_set_autotune(self._h, 1 if on else 0))
+
+    def autotune(self, n: int, precision="fp64", stream=None):
+        """mg5_autotune: time the sweep schedules of every grid side of n's hierarchy."""
+        self._check(_lib.mg5_autotune(self._h, n, _prec(precision), _stream(stream)))
+
+    def set_blocking_wait(self, on: bool = True):
+        """mg5_set_blocking_wait: sleep (True) or spin (False, default) while waiting for the GPU."""
+        self._check(_lib.mg5_set_blocking_wait(self._h, 1 if on else 0))
 
     def _check(self, rc: int, allow=(OK,)):
         if rc not in allow:
@@ -454,6 +527,14 @@ class Server:
 
     def bytes_held(self) -> int:
         return _lib.mg5_server_bytes_held(self._h)
+
+    def stats(self) -> dict:
+        """mg5_server_get_stats: builds, evictions, fallbacks, memory waits, completed, build seconds."""
+        st = _ServerStats()
+        rc = _lib.mg5_server_get_stats(self._h, ctypes.byref(st))
+        if rc != OK:
+            raise MG5Error(rc, "server stats")
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
 
     def close(self):
         if self._h:

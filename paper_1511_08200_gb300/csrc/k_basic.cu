@@ -77,16 +77,18 @@ __global__ void k_sweep_black(const T *__restrict__ in, T *out, const T *__restr
 
 template <typename T>
 cudaError_t launch_sweep(const T *in, T *out, const T *f, const double *cptr, int n, CoefT<T> cf,
-                         unsigned long long *clamp, cudaStream_t st, const T *B)
+                         unsigned long long *clamp, cudaStream_t st, const T *B, int block)
 {
+    if (block < 32 || block > 1024 || block % 32)
+        return cudaErrorInvalidValue;
     const long long work = (long long)n * n * (n / 2);
-    const int g = blocks_for(work);
+    const int g = (int)((work + block - 1) / block);
     if (B) {
-        k_sweep_red<T, true><<<g, kBlock, 0, st>>>(in, out, f, cptr, n, cf, clamp, B);
-        k_sweep_black<T, true><<<g, kBlock, 0, st>>>(in, out, f, cptr, n, cf, clamp, B);
+        k_sweep_red<T, true><<<g, block, 0, st>>>(in, out, f, cptr, n, cf, clamp, B);
+        k_sweep_black<T, true><<<g, block, 0, st>>>(in, out, f, cptr, n, cf, clamp, B);
     } else {
-        k_sweep_red<T, false><<<g, kBlock, 0, st>>>(in, out, f, cptr, n, cf, clamp, B);
-        k_sweep_black<T, false><<<g, kBlock, 0, st>>>(in, out, f, cptr, n, cf, clamp, B);
+        k_sweep_red<T, false><<<g, block, 0, st>>>(in, out, f, cptr, n, cf, clamp, B);
+        k_sweep_black<T, false><<<g, block, 0, st>>>(in, out, f, cptr, n, cf, clamp, B);
     }
     count_launch(2);
     return cudaGetLastError();
@@ -807,7 +809,7 @@ cudaError_t launch_patch_residual(const double *phi, const double *fint, double 
 // explicit instantiations
 #define MG5_INST(T)                                                                                \
     template cudaError_t launch_sweep<T>(const T *, T *, const T *, const double *, int, CoefT<T>, \
-                                         unsigned long long *, cudaStream_t, const T *);           \
+                                         unsigned long long *, cudaStream_t, const T *, int);      \
     template cudaError_t launch_operator<T>(const T *, int, CoefT<T>, T *, cudaStream_t);          \
     template cudaError_t launch_residual<T>(const T *, const T *, const double *, int, CoefT<T>,   \
                                             T *, double2 *, int *, cudaStream_t);                  \

@@ -48,8 +48,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 __device__ __forceinline__ int wrap1(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 __device__ __forceinline__ int slot5(int q) { return ((q % NSLOT) + NSLOT) % NSLOT; }
-__device__ __forceinline__ int slot3(int q) { return ((q % 3) + 3) % 3; }
 
+__device__ __forceinline__ int slot3(int q) { return ((q % 3) + 3) % 3; }
 // issue the 16-byte copies of plane q (rows j0-2 .. j0+17, k0-4 .. k0+35)
 template <typename T>
 __device__ __forceinline__ void issue_plane(T *dst, const T *__restrict__ src, int n, int q, int j0,
@@ -213,29 +213,28 @@ __global__ void __launch_bounds__(FT_THREADS)
         atomicAdd(clamp, 1ull);
 }
 
-// the fused kernel needs 16-byte row chunks: n a multiple of 16 / sizeof(T)
-template <typename T>
-bool fused_ok(int n)
-{
-    return n >= kFusedMinN && n % (int)(16 / sizeof(T)) == 0;
-}
-
 template <typename T>
 cudaError_t launch_sweep_fused(const T *in, T *out, const T *f, const double *cptr, int n,
-                               CoefT<T> cf, unsigned long long *clamp, cudaStream_t st, const T *B)
+                               CoefT<T> cf, unsigned long long *clamp, cudaStream_t st, const T *B,
+                               int chunk)
 {
     if (!fused_ok<T>(n))
         return launch_sweep<T>(in, out, f, cptr, n, cf, clamp, st, B);
     const int tk = (n + FT_K - 1) / FT_K, tj = (n + FT_J - 1) / FT_J;
     const int tiles = tk * tj;
-    // enough CTAs for several waves over 152 SMs, chunks of at least 8 planes
-    int chunks = (8 * 152 + tiles - 1) / tiles;
-    if (chunks > n / 8)
-        chunks = n / 8;
-    if (chunks < 1)
-        chunks = 1;
-    const int ichunk = (n + chunks - 1) / chunks;
-    chunks = (n + ichunk - 1) / ichunk;
+    int ichunk = chunk;
+    if (ichunk <= 0) {
+        // enough CTAs for several waves over 152 SMs, chunks of at least 8 planes
+        int chunks = (8 * 152 + tiles - 1) / tiles;
+        if (chunks > n / 8)
+            chunks = n / 8;
+        if (chunks < 1)
+            chunks = 1;
+        ichunk = (n + chunks - 1) / chunks;
+    }
+    if (ichunk > n)
+        ichunk = n;
+    const int chunks = (n + ichunk - 1) / ichunk;
     dim3 grid(tk, tj, chunks);
     // the shared-memory limits were raised by prepare_fused_kernels() at context creation
     if (B)
@@ -271,9 +270,9 @@ cudaError_t prepare_fused_kernels()
 
 template cudaError_t launch_sweep_fused<float>(const float *, float *, const float *, const double *,
                                                int, CoefT<float>, unsigned long long *, cudaStream_t,
-                                               const float *);
+                                               const float *, int);
 template cudaError_t launch_sweep_fused<double>(const double *, double *, const double *,
                                                 const double *, int, CoefT<double>,
-                                                unsigned long long *, cudaStream_t, const double *);
+                                                unsigned long long *, cudaStream_t, const double *, int);
 
 }  // namespace mg5

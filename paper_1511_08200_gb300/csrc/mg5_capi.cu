@@ -21,6 +21,7 @@
 #include "mg5.h"
 #include "mg5_kernels.cuh"
 #include "mg5_mixed.cuh"
+#include "mg5_pool.h"
 #include "mg5_prof.cuh"
 
 using namespace mg5;
@@ -128,24 +129,32 @@ struct BatchSet {
 
 // A mixed solve of one size and parameter set captured as a graph (defect-correction
 // loop as a WHILE node), with its own hierarchy, scalars and staging buffers.
+struct GraphReadback {
+    BoxCtl ctl;
+    SolveCounters cnt;
+    LevelScal ls0;
+};
+
 struct GraphEntry {
     int N = 0;
     mg5_params prm{};
     bool grad = false;
+    bool busy = false;
     MixedHier *hier = nullptr;
     double2 *partials = nullptr;
     LevelScal *ls = nullptr;
     SolveCounters *cnt = nullptr;
     BoxCtl *ctl = nullptr;
     double *delta = nullptr, *phi = nullptr, *gout = nullptr;
+    GraphReadback *rb = nullptr;   // pinned host copy of the control state
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     CaptureStats stats{};
-    size_t bytes = 0;
+    size_t bytes = 0;              // device bytes, hierarchy included
     unsigned long long last_use = 0;
 };
 
-constexpr size_t kGraphCacheMax = 48;
+constexpr size_t kGraphCacheMax = 48;   // entries per context on the single-caller path
 
 struct mg5_ctx {
     int device = 0;
@@ -168,6 +177,9 @@ struct mg5_ctx {
     double *patch = nullptr;
     size_t patch_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t evb = nullptr;      // blocking-sync event: host waits sleep instead of spinning
+    bool blocking = false;
+    bool autotune = false;          // tune untuned grid sides before a solve
     Profiler prof;
 };
 
@@ -194,6 +206,30 @@ static int solve_graph(mg5_ctx *ctx, const double *delta, int N, const mg5_param
         if (r_ != MG5_OK)           \
             return r_;              \
     } while (0)
+
+// Host wait for st on this context's solve paths (spin, or sleep when set to blocking).
+static cudaError_t ctx_wait(mg5_ctx *ctx, cudaStream_t st)
+{
+    return host_wait(st, ctx->blocking ? ctx->evb : nullptr);
+}
+
+// Tune the sweep schedule of every non-coarsest grid side of N's hierarchy not in the table.
+static int ctx_autotune(mg5_ctx *ctx, int N, int precision, cudaStream_t st)
+{
+    int sz[kMaxLevels];
+    const int L = num_levels(N, sz);
+    for (int l = 0; l + 1 < L; ++l) {
+        if (sweep_tuned(ctx->device, precision, sz[l]))
+            continue;
+        const cudaError_t e = tune_side(ctx->device, precision, sz[l], st, nullptr);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("autotune: ") + cudaGetErrorString(e);
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? MG5_E_OOM : MG5_E_CUDA;
+        }
+    }
+    return MG5_OK;
+}
 
 static int ctx_alloc(mg5_ctx *ctx, void **p, size_t bytes)
 {
@@ -352,22 +388,6 @@ static size_t graph_entry_bytes(int N, bool grad)
            sizeof(LevelScal) * kScalSlots + sizeof(SolveCounters) + sizeof(BoxCtl);
 }
 
-static void free_graph_entry(mg5_ctx *ctx, GraphEntry *g)
-{
-    if (g->exec)
-        cudaGraphExecDestroy(g->exec);
-    if (g->graph)
-        cudaGraphDestroy(g->graph);
-    if (g->hier)
-        free_mixed(g->hier, &ctx->held);
-    for (void *p : {(void *)g->partials, (void *)g->ls, (void *)g->cnt, (void *)g->ctl,
-                    (void *)g->delta, (void *)g->phi, (void *)g->gout})
-        if (p)
-            cudaFree(p);
-    ctx->held -= g->bytes;   // the hierarchy's own bytes were returned by free_mixed
-    delete g;
-}
-
 static int ensure_buffer(mg5_ctx *ctx, double **buf, size_t *have, size_t need)
 {
     if (*have >= need)
@@ -420,8 +440,9 @@ struct Run64 {
     {
         const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
         ProfScope ps(&ctx->prof, l == 0 ? PK_SWEEP64 : PK_SWEEP64C, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
-        cudaError_t e = launch_sweep<double>(h->v[l], h->tmp[l], h->f[l], c(l), h->n[l], cf,
-                                             &ctx->cnt->clamped, st);
+        cudaError_t e = launch_sweep_sched<double>(sweep_schedule(ctx->device, MG5_FP64, h->n[l]),
+                                                   h->v[l], h->tmp[l], h->f[l], c(l), h->n[l], cf,
+                                                   &ctx->cnt->clamped, st);
         if (e != cudaSuccess) {
             ctx->err = std::string("sweep: ") + cudaGetErrorString(e);
             return MG5_E_CUDA;
@@ -583,7 +604,7 @@ static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p
             RET(R.resid_restrict(0));
         }
         CK(cudaMemcpyAsync(ctx->h_rel, &ctx->ls[0].rel, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        CK(ctx_wait(ctx, st));
         const double rel = *ctx->h_rel;
         if (info && cyc < 64) {
             info->history[cyc] = rel;
@@ -741,6 +762,8 @@ int mg5_create(mg5_ctx **out, int device, size_t budget)
     if (e == cudaSuccess)
         e = cudaEventCreate(&ctx->ev1);
     if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&ctx->evb, cudaEventBlockingSync | cudaEventDisableTiming);
+    if (e == cudaSuccess)
         e = prepare_fused_kernels();
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -767,8 +790,10 @@ int mg5_release(mg5_ctx *ctx)
         free_patch(ctx, ph);
     ctx->patches.clear();
     free_batch(ctx);
-    for (GraphEntry *g : ctx->graphs)
-        free_graph_entry(ctx, g);
+    for (GraphEntry *g : ctx->graphs) {
+        ctx->held -= g->bytes;
+        graph_free(g);
+    }
     ctx->graphs.clear();
     ctx_free(ctx, ctx->stage, ctx->stage_bytes);
     ctx->stage = nullptr;
@@ -796,6 +821,8 @@ int mg5_destroy(mg5_ctx *ctx)
         cudaEventDestroy(ctx->ev0);
     if (ctx->ev1)
         cudaEventDestroy(ctx->ev1);
+    if (ctx->evb)
+        cudaEventDestroy(ctx->evb);
     ctx->prof.destroy();
     delete ctx;
     return MG5_OK;
@@ -804,6 +831,31 @@ int mg5_destroy(mg5_ctx *ctx)
 const char *mg5_last_error(mg5_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 size_t mg5_bytes_held(mg5_ctx *ctx) { return ctx ? ctx->held : 0; }
+
+int mg5_set_autotune(mg5_ctx *ctx, int on)
+{
+    if (!ctx)
+        return MG5_E_ARG;
+    ctx->autotune = on != 0;
+    return MG5_OK;
+}
+
+int mg5_autotune(mg5_ctx *ctx, int N, int precision, void *stream)
+{
+    if (!ctx || (precision != MG5_FP64 && precision != MG5_MIXED))
+        return MG5_E_ARG;
+    RET(check_size(N));
+    CK(cudaSetDevice(ctx->device));
+    return ctx_autotune(ctx, N, precision, (cudaStream_t)stream);
+}
+
+int mg5_set_blocking_wait(mg5_ctx *ctx, int on)
+{
+    if (!ctx)
+        return MG5_E_ARG;
+    ctx->blocking = on != 0;
+    return MG5_OK;
+}
 
 int mg5_cached_bytes(mg5_ctx *ctx, int N, int precision, size_t *extra)
 {
@@ -838,7 +890,7 @@ int mg5_graph_cached_bytes(mg5_ctx *ctx, int N, const mg5_params *p, int with_gr
     RET(check_size(N));
     *extra = graph_entry_bytes(N, with_grad != 0);
     for (GraphEntry *g : ctx->graphs)
-        if (g->N == N && g->grad == (with_grad != 0) && same_params(g->prm, *p))
+        if (!g->busy && g->N == N && g->grad == (with_grad != 0) && same_params(g->prm, *p))
             *extra = 0;
     return MG5_OK;
 }
@@ -910,6 +962,8 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
     const size_t fb = (size_t)n3 * sizeof(double);
     const double *d_delta = delta;
     double *d_phi = phi, *d_grad = grad;
+    if (ctx->autotune)
+        RET(ctx_autotune(ctx, N, p->precision, st));
     CK(cudaEventRecord(ctx->ev0, st));
     if (flags & MG5_HOST_IO) {
         RET(ensure_buffer(ctx, &ctx->stage, &ctx->stage_bytes, fb * (grad ? 5 : 2)));
@@ -929,7 +983,7 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
         if (status == MG5_E_CUDA || status == MG5_E_ARG || status == MG5_E_OOM)
             return status;
         CK(cudaEventRecord(ctx->ev1, st));
-        CK(cudaStreamSynchronize(st));
+        CK(ctx_wait(ctx, st));
         if (info) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
@@ -952,7 +1006,8 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
                 return rc;
             ctx->mixed.push_back(mh);
         }
-        MixedShared sh{ctx->partials, ctx->ls, ctx->cnt, ctx->h_rel, &ctx->prof};
+        MixedShared sh{ctx->partials, ctx->ls, ctx->cnt, ctx->h_rel, &ctx->prof,
+                       ctx->blocking ? ctx->evb : nullptr};
         status = solve_mixed(mh, sh, d_delta, p, d_phi, info, st, &ctx->err);
     }
     if (status == MG5_E_CUDA || status == MG5_E_ARG || status == MG5_E_OOM)
@@ -972,7 +1027,7 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
     double tail[2];
     CK(cudaMemcpyAsync(tail, &ctx->ls[0].c, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(tail + 1, &ctx->ls[0].mean, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(ctx_wait(ctx, st));
     ctx->prof.resolve();
     if (status == MG5_OK && cnt.clamped > 0)
         status = MG5_W_DISC_CLAMP;
@@ -1166,7 +1221,7 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
             RET(R.resid_restrict(0, true));
         }
         CK(cudaMemcpyAsync(ctx->h_rel, &ls->rel, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        CK(ctx_wait(ctx, st));
         const double rel = *ctx->h_rel;
         if (info) {
             info->rel_residual = rel;
@@ -1202,7 +1257,7 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
     CK(cudaEventRecord(ctx->ev1, st));
     SolveCounters cnt;
     CK(cudaMemcpyAsync(&cnt, ctx->cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(ctx_wait(ctx, st));
     ctx->prof.resolve();
     if (status == MG5_OK && cnt.clamped > 0)
         status = MG5_W_DISC_CLAMP;
@@ -1226,36 +1281,94 @@ static bool same_params(const mg5_params &a, const mg5_params &b)
     return std::memcmp(&a, &b, sizeof(mg5_params)) == 0;
 }
 
-// Find the cached graph for (N, params, grad) or capture a new one (evicting the
-// least recently used entries while the budget would be exceeded).
-static int get_graph_entry(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, GraphEntry **out)
+}  // extern "C"
+
+namespace mg5 {
+
+size_t graph_bytes(int N, bool grad) { return graph_entry_bytes(N, grad); }
+
+size_t graph_held(mg5_ctx *ctx)
+{
+    size_t t = 0;
+    for (GraphEntry *g : ctx->graphs)
+        t += g->bytes;
+    return t;
+}
+
+GraphEntry *graph_checkout(mg5_ctx *ctx, int N, const mg5_params *p, bool grad)
 {
     for (GraphEntry *g : ctx->graphs)
-        if (g->N == N && g->grad == grad && same_params(g->prm, *p)) {
+        if (!g->busy && g->N == N && g->grad == grad && same_params(g->prm, *p)) {
+            g->busy = true;
             g->last_use = ++ctx->graph_clock;
-            *out = g;
-            return MG5_OK;
+            return g;
         }
-    const size_t need = graph_entry_bytes(N, grad);
-    while (!ctx->graphs.empty() &&
-           (ctx->graphs.size() >= kGraphCacheMax || (ctx->budget && ctx->held + need > ctx->budget))) {
-        auto it = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
-                                   [](GraphEntry *a, GraphEntry *b) { return a->last_use < b->last_use; });
-        CK(cudaDeviceSynchronize());
-        free_graph_entry(ctx, *it);
-        ctx->graphs.erase(it);
-    }
-    if (ctx->budget && ctx->held + need > ctx->budget) {
-        ctx->err = "graph solve would exceed the context's HBM budget";
-        return MG5_E_OOM;
+    return nullptr;
+}
+
+int graph_count(mg5_ctx *ctx, int N, const mg5_params *p, bool grad)
+{
+    int c = 0;
+    for (GraphEntry *g : ctx->graphs)
+        c += g->N == N && g->grad == grad && same_params(g->prm, *p);
+    return c;
+}
+
+void graph_insert(mg5_ctx *ctx, GraphEntry *g)
+{
+    g->busy = true;
+    g->last_use = ++ctx->graph_clock;
+    ctx->graphs.push_back(g);
+    ctx->held += g->bytes;
+}
+
+GraphEntry *graph_take_idle(mg5_ctx *ctx)
+{
+    auto best = ctx->graphs.end();
+    for (auto it = ctx->graphs.begin(); it != ctx->graphs.end(); ++it)
+        if (!(*it)->busy && (best == ctx->graphs.end() || (*it)->last_use < (*best)->last_use))
+            best = it;
+    if (best == ctx->graphs.end())
+        return nullptr;
+    GraphEntry *g = *best;
+    ctx->graphs.erase(best);
+    ctx->held -= g->bytes;
+    return g;
+}
+
+void graph_free(GraphEntry *g)
+{
+    if (g->exec)
+        cudaGraphExecDestroy(g->exec);
+    if (g->graph)
+        cudaGraphDestroy(g->graph);
+    size_t hb = 0;
+    if (g->hier)
+        free_mixed(g->hier, &hb);
+    for (void *p : {(void *)g->partials, (void *)g->ls, (void *)g->cnt, (void *)g->ctl,
+                    (void *)g->delta, (void *)g->phi, (void *)g->gout})
+        if (p)
+            cudaFree(p);
+    if (g->rb)
+        cudaFreeHost(g->rb);
+    delete g;
+}
+
+int graph_build(int device, int N, const mg5_params *p, bool grad, GraphEntry **out,
+                std::string *err)
+{
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        *err = "graph solve: cannot select the device";
+        return MG5_E_CUDA;
     }
     GraphEntry *g = new GraphEntry();
     g->N = N;
     g->prm = *p;
     g->grad = grad;
-    g->bytes = need - mixed_bytes(N);
-    ctx->held += g->bytes;
-    int rc = alloc_mixed(N, 0, &ctx->held, &g->hier, &ctx->err);
+    size_t hb = 0;
+    int rc = alloc_mixed(N, 0, &hb, &g->hier, err);
     const size_t n3 = (size_t)N * N * N;
     cudaError_t e = rc == MG5_OK ? cudaSuccess : cudaErrorMemoryAllocation;
     if (e == cudaSuccess)
@@ -1272,20 +1385,21 @@ static int get_graph_entry(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, 
         e = cudaMalloc((void **)&g->phi, n3 * sizeof(double));
     if (e == cudaSuccess && grad)
         e = cudaMalloc((void **)&g->gout, 3 * n3 * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&g->rb, sizeof(GraphReadback));
+    g->bytes = graph_entry_bytes(N, grad);
     cudaStream_t origin = nullptr, body = nullptr;
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking);
-    const bool prof_on = ctx->prof.on;
     const long long l0 = launches_total();
     if (e == cudaSuccess) {
-        ctx->prof.on = false;
         e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            MixedShared sh{g->partials, g->ls, g->cnt, ctx->h_rel, nullptr};
+            MixedShared sh{g->partials, g->ls, g->cnt, nullptr, nullptr};
             rc = capture_mixed(g->hier, sh, g->delta, p, g->phi, g->gout, g->ctl, origin, body,
-                               &g->stats, &ctx->err);
+                               &g->stats, err);
             cudaGraph_t graph = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(origin, &graph);
             if (rc == MG5_OK && e2 == cudaSuccess) {
@@ -1298,7 +1412,6 @@ static int get_graph_entry(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, 
                     e = e2;
             }
         }
-        ctx->prof.on = prof_on;
         count_launch(l0 - launches_total());   // captured, not enqueued
     }
     if (origin)
@@ -1306,39 +1419,49 @@ static int get_graph_entry(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, 
     if (body)
         cudaStreamDestroy(body);
     if (rc == MG5_OK && e != cudaSuccess) {
-        ctx->err = std::string("graph solve: ") + cudaGetErrorString(e);
-        cudaGetLastError();
+        *err = std::string("graph solve: ") + cudaGetErrorString(e);
         rc = e == cudaErrorMemoryAllocation ? MG5_E_OOM : MG5_E_CUDA;
     }
+    cudaGetLastError();
     if (rc != MG5_OK) {
-        free_graph_entry(ctx, g);
+        graph_free(g);
         return rc;
     }
-    g->last_use = ++ctx->graph_clock;
-    ctx->graphs.push_back(g);
     *out = g;
     return MG5_OK;
 }
 
-// MG5_MIXED from zero through the cached graph: copy in, one graph launch, copy out.
-static int solve_graph(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p, double *phi,
-                       double *grad, mg5_info *info, cudaStream_t st)
+int graph_enqueue(GraphEntry *g, const double *delta, double *phi, double *grad, cudaStream_t st,
+                  std::string *err)
 {
-    GraphEntry *g = nullptr;
-    RET(get_graph_entry(ctx, N, p, grad != nullptr, &g));
-    const size_t n3 = (size_t)N * N * N;
-    CK(cudaMemcpyAsync(g->delta, delta, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CK(cudaGraphLaunch(g->exec, st));
-    CK(cudaMemcpyAsync(phi, g->phi, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    if (grad)
-        CK(cudaMemcpyAsync(grad, g->gout, 3 * n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    BoxCtl ctl;
-    SolveCounters cnt;
-    LevelScal ls0;
-    CK(cudaMemcpyAsync(&ctl, g->ctl, sizeof(BoxCtl), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&cnt, g->cnt, sizeof(SolveCounters), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&ls0, g->ls, sizeof(LevelScal), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    const size_t n3 = (size_t)g->N * g->N * g->N;
+    cudaError_t e = cudaMemcpyAsync(g->delta, delta, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaGraphLaunch(g->exec, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(phi, g->phi, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && grad)
+        e = cudaMemcpyAsync(grad, g->gout, 3 * n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&g->rb->ctl, g->ctl, sizeof(BoxCtl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&g->rb->cnt, g->cnt, sizeof(SolveCounters), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&g->rb->ls0, g->ls, sizeof(LevelScal), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) {
+        *err = std::string("graph solve: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return MG5_E_CUDA;
+    }
+    return MG5_OK;
+}
+
+void graph_checkin(GraphEntry *g) { g->busy = false; }
+
+int graph_finish(GraphEntry *g, mg5_info *info)
+{
+    const BoxCtl &ctl = g->rb->ctl;
+    const SolveCounters &cnt = g->rb->cnt;
     count_launch(g->stats.launches_fixed + g->stats.launches_per_iter * ctl.outer);
     int status = ctl.status;
     if (info) {
@@ -1351,8 +1474,8 @@ static int solve_graph(mg5_ctx *ctx, const double *delta, int N, const mg5_param
         for (int k = 0; k < ctl.nhist && k < 64; ++k)
             info->history[k] = ctl.hist[k];
         info->rel_residual = ctl.rel;
-        info->compat_c = ls0.c;
-        info->phi_mean_removed = ls0.mean;
+        info->compat_c = g->rb->ls0.c;
+        info->phi_mean_removed = g->rb->ls0.mean;
         const long long nc = info->coarsest_n;
         info->cell_updates =
             g->stats.cells_per_iter * ctl.outer + (long long)cnt.coarse_sweeps * nc * nc * nc;
@@ -1360,7 +1483,58 @@ static int solve_graph(mg5_ctx *ctx, const double *delta, int N, const mg5_param
     }
     if (status == MG5_OK && cnt.clamped > 0)
         status = MG5_W_DISC_CLAMP;
+    g->busy = false;
     return status;
+}
+
+}  // namespace mg5
+
+extern "C" {
+
+// The cached graph for (N, params, grad), or a new capture (evicting the least
+// recently used entries while the cache is full or the budget would be exceeded).
+static int get_graph_entry(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, GraphEntry **out)
+{
+    if ((*out = graph_checkout(ctx, N, p, grad)))
+        return MG5_OK;
+    const size_t need = graph_entry_bytes(N, grad);
+    while (ctx->graphs.size() >= kGraphCacheMax || (ctx->budget && ctx->held + need > ctx->budget)) {
+        GraphEntry *v = graph_take_idle(ctx);   // every entry is idle: this context's solves have synchronised
+        if (!v)
+            break;
+        graph_free(v);
+    }
+    if (ctx->budget && ctx->held + need > ctx->budget) {
+        ctx->err = "graph solve would exceed the context's HBM budget";
+        return MG5_E_OOM;
+    }
+    const bool prof_on = ctx->prof.on;
+    ctx->prof.on = false;
+    GraphEntry *g = nullptr;
+    const int rc = graph_build(ctx->device, N, p, grad, &g, &ctx->err);
+    ctx->prof.on = prof_on;
+    RET(rc);
+    graph_insert(ctx, g);
+    *out = g;
+    return MG5_OK;
+}
+
+// MG5_MIXED from zero through the cached graph: copy in, one graph launch, copy out.
+static int solve_graph(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p, double *phi,
+                       double *grad, mg5_info *info, cudaStream_t st)
+{
+    GraphEntry *g = nullptr;
+    RET(get_graph_entry(ctx, N, p, grad != nullptr, &g));
+    int rc = graph_enqueue(g, delta, phi, grad, st, &ctx->err);
+    if (rc == MG5_OK && ctx_wait(ctx, st) != cudaSuccess) {
+        ctx->err = std::string("graph solve: ") + cudaGetErrorString(cudaGetLastError());
+        rc = MG5_E_CUDA;
+    }
+    if (rc != MG5_OK) {
+        graph_checkin(g);
+        return rc;
+    }
+    return graph_finish(g, info);
 }
 
 static bool batch_matches(const BatchSet *b, int nbox, const double *const *delta, const int *N,
@@ -1522,8 +1696,12 @@ int mg5_solve_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const in
         }
         return worst;
     }
-    if (!batch_matches(ctx->batch, nbox, delta, N, p, phi, grad))
+    if (!batch_matches(ctx->batch, nbox, delta, N, p, phi, grad)) {
+        if (ctx->autotune)
+            for (int i = 0; i < nbox; ++i)
+                RET(ctx_autotune(ctx, N[i], MG5_MIXED, st));
         RET(build_batch(ctx, nbox, delta, N, p, phi, grad));
+    }
     BatchSet *b = ctx->batch;
     CK(cudaEventRecord(ctx->ev0, st));
     CK(cudaGraphLaunch(b->exec, st));

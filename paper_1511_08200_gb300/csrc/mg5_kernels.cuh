@@ -50,17 +50,48 @@ enum FinalizeMode { FIN_RESID = 0, FIN_FNORM = 1, FIN_MEAN = 2, FIN_STATS = 3, F
 
 // ---- FP64/FP32 periodic kernels (templates instantiated for double and float)
 // B (optional): base field of the correction form (mixed precision)
+// two-pass sweep (red kernel, black kernel) with `block` threads per block
 template <typename T>
 cudaError_t launch_sweep(const T *in, T *out, const T *f, const double *cptr, int n,
                          CoefT<T> cf, unsigned long long *clamp, cudaStream_t st,
-                         const T *B = nullptr);
-// fused red+black sweep (k_fused.cu): one read and one write of phi per cell
+                         const T *B = nullptr, int block = kBlock);
+// fused red+black sweep (k_fused.cu): one read and one write of phi per cell; each CTA
+// marches over `chunk` planes (0: enough CTAs for several waves)
 template <typename T>
 cudaError_t launch_sweep_fused(const T *in, T *out, const T *f, const double *cptr, int n,
                                CoefT<T> cf, unsigned long long *clamp, cudaStream_t st,
-                               const T *B = nullptr);
+                               const T *B = nullptr, int chunk = 0);
 constexpr int kFusedMinN = 32;   // smaller grids use the two-pass sweep
+// the fused kernel needs 16-byte row chunks: n a multiple of 16 / sizeof(T)
+template <typename T>
+inline bool fused_ok(int n)
+{
+    return n >= kFusedMinN && n % (int)(16 / sizeof(T)) == 0;
+}
 cudaError_t prepare_fused_kernels();
+
+// How one grid side is swept (speed only: every schedule computes the same values).
+struct SweepSchedule {
+    int form = 0;     // 0: two-pass, 1: fused
+    int block = kBlock;
+    int chunk = 0;
+    float ms = 0.f;   // tuned time of one sweep (0: not measured)
+};
+// The schedule of (device, precision, side): the tuned one, else the default
+// (FP64 two-pass; the mixed mode's FP32 correction form fused where it fits).
+SweepSchedule sweep_schedule(int device, int precision, int n);
+bool sweep_tuned(int device, int precision, int n);
+// time the candidates for (device, precision, n) on st and record the fastest (mg5_tune.cu)
+cudaError_t tune_side(int device, int precision, int n, cudaStream_t st, SweepSchedule *out);
+template <typename T>
+cudaError_t launch_sweep_sched(const SweepSchedule &s, const T *in, T *out, const T *f,
+                               const double *cptr, int n, CoefT<T> cf, unsigned long long *clamp,
+                               cudaStream_t st, const T *B = nullptr)
+{
+    if (s.form == 1 && fused_ok<T>(n))
+        return launch_sweep_fused<T>(in, out, f, cptr, n, cf, clamp, st, B, s.chunk);
+    return launch_sweep<T>(in, out, f, cptr, n, cf, clamp, st, B, s.block);
+}
 template <typename T>
 cudaError_t launch_operator(const T *phi, int n, CoefT<T> cf, T *out, cudaStream_t st);
 // r (nullable) = f + c - op(phi); partial sums (sum r, sum r^2) per block.

@@ -101,12 +101,11 @@ struct RunMix {
     {
         ProfScope ps(sh.prof, l == 0 ? PK_SWEEP32 : PK_SWEEP32C, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
         const CoefT<float> cf = make_coef<float>(hl[l], p->alpha);
-        cudaError_t e =
-            h->n[l] >= kFusedMinN
-                ? launch_sweep_fused<float>(h->e[l], h->etmp[l], h->f[l], c(l), h->n[l], cf,
-                                            &sh.cnt->clamped, st, h->B[l])
-                : launch_sweep<float>(h->e[l], h->etmp[l], h->f[l], c(l), h->n[l], cf,
-                                      &sh.cnt->clamped, st, h->B[l]);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaError_t e = launch_sweep_sched<float>(sweep_schedule(dev, MG5_MIXED, h->n[l]), h->e[l],
+                                                  h->etmp[l], h->f[l], c(l), h->n[l], cf,
+                                                  &sh.cnt->clamped, st, h->B[l]);
         if (e != cudaSuccess)
             return fail("sweep32", e);
         std::swap(h->e[l], h->etmp[l]);
@@ -372,7 +371,7 @@ int solve_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const 
         if (int rc = phase_residual(h, sh, p, phi, st, err))
             return rc;
         CKM(cudaMemcpyAsync(sh.h_rel, &sh.ls[0].rel, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CKM(cudaStreamSynchronize(st));
+        CKM(host_wait(st, sh.wait_ev));
         const double rel = *sh.h_rel;
         if (info) {
             if (outer < 64) {

@@ -34,7 +34,17 @@ struct MixedShared {
     SolveCounters *cnt;
     double *h_rel;   // pinned host scalar
     Profiler *prof;
+    cudaEvent_t wait_ev = nullptr;   // blocking-sync event for host waits (nullptr: spin on the stream)
 };
+
+// Wait until st has drained: sleep on `ev` (a blocking-sync event) when given, else spin.
+inline cudaError_t host_wait(cudaStream_t st, cudaEvent_t ev)
+{
+    if (!ev)
+        return cudaStreamSynchronize(st);
+    cudaError_t e = cudaEventRecord(ev, st);
+    return e == cudaSuccess ? cudaEventSynchronize(ev) : e;
+}
 
 // Per-box loop control of the graph form (device memory).
 struct BoxCtl {

@@ -97,3 +97,37 @@ def test_binding_imports_and_names(lib):
     p = mg.default_params(alpha=1.0, s=2.0, h=0.5)
     assert (p.nu1, p.nu2, p.tol, p.precision) == (2, 2, 1e-10, mg.FP64)
     assert mg.workspace_bytes(64, "mixed") > 0
+
+
+def test_schedule_table_host_logic(lib, tmp_path):
+    """The autotuner's table without a GPU: defaults, hand-set entries, validation,
+    and the JSON-lines file round trip (entries for GPUs not present are skipped)."""
+    import json
+    import paper_1511_08200_gb300 as mg
+    mg.tune_clear()
+    s, tuned = mg.schedule_get(0, "fp64", 64)
+    assert not tuned and (s.form, s.block) == (mg.SWEEP_TWO_PASS, 256)
+    s, tuned = mg.schedule_get(0, "mixed", 64)
+    assert not tuned and s.form == mg.SWEEP_FUSED          # fits the fused kernel
+    s, _ = mg.schedule_get(0, "mixed", 16)
+    assert s.form == mg.SWEEP_TWO_PASS                     # below the fused kernel's minimum
+    mg.schedule_set(0, "mixed", 64, mg.SWEEP_TWO_PASS, block=128)
+    s, tuned = mg.schedule_get(0, "mixed", 64)
+    assert tuned and (s.form, s.block) == (mg.SWEEP_TWO_PASS, 128)
+    for bad in (dict(form=mg.SWEEP_TWO_PASS, block=33), dict(form=7), dict(form=1, chunk=-1)):
+        with pytest.raises(mg.MG5Error):
+            mg.schedule_set(0, "fp64", 32, **bad)
+    path = tmp_path / "tune.jsonl"
+    mg.tune_save(path)
+    rows = [json.loads(x) for x in path.read_text().splitlines()]
+    assert rows == [{"gpu": rows[0]["gpu"], "precision": "mixed", "n": 64, "form": "two-pass",
+                     "block": 128, "chunk": 0, "ms": 0}]
+    mg.tune_clear()
+    assert not mg.schedule_get(0, "mixed", 64)[1]
+    import torch
+    if not torch.cuda.is_available():
+        assert mg.tune_load(path) == 0                     # no GPU of that name here
+    (tmp_path / "bad.jsonl").write_text("not a table\n")
+    with pytest.raises(mg.MG5Error):
+        mg.tune_load(tmp_path / "bad.jsonl")
+    mg.tune_clear()

@@ -88,3 +88,27 @@ def test_server_respects_hbm_budget():
     tiny.close()
     for x in phis[1:]:
         assert torch.equal(x, phis[0])
+
+
+def test_server_shares_captured_graphs_between_workers():
+    """Requests of one key, one after another, reuse a single pooled graph whichever
+    worker takes them: the server holds exactly one entry's bytes."""
+    import torch
+    mg = _mg()
+    alpha, s, h = nominal()
+    srv = mg.Server(0, slots=3)
+    d = dev(workload.lognormal_delta(48, 1.0, 11))
+    p = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-8, precision="mixed")
+    outs = []
+    for t in range(6):
+        phi = torch.zeros_like(d)
+        srv.submit(d, p, phi, tag=t)
+        got = []
+        while not got:
+            got = srv.poll(wait_ms=2000)
+        assert got[0].status == 0 and got[0].tag == t
+        outs.append(phi)
+    assert srv.bytes_held() == mg.graph_workspace_bytes(48)
+    srv.close()
+    for x in outs[1:]:
+        assert torch.equal(x, outs[0])
