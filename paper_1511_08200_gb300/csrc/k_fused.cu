@@ -49,7 +49,18 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ int wrap1(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 __device__ __forceinline__ int slot5(int q) { return ((q % NSLOT) + NSLOT) % NSLOT; }
 
-__device__ __forceinline__ int slot3(int q) { return ((q % 3) + 3) % 3; }
+// Ring slots of planes q-1, q, q+1 (q >= -2 here): one unsigned division, then increments.
+struct Ring {
+    int m, z, p;
+};
+template <int K>
+__device__ __forceinline__ Ring ring(int q)
+{
+    const int m = (int)((unsigned)(q - 1 + 3 * K) % (unsigned)K);
+    const int z = m == K - 1 ? 0 : m + 1;
+    return Ring{m, z, z == K - 1 ? 0 : z + 1};
+}
+
 // issue the 16-byte copies of plane q (rows j0-2 .. j0+17, k0-4 .. k0+35)
 template <typename T>
 __device__ __forceinline__ void issue_plane(T *dst, const T *__restrict__ src, int n, int q, int j0,
@@ -109,8 +120,9 @@ __global__ void __launch_bounds__(FT_THREADS)
 
     // red cells of plane q on the tile + 1 halo -> rnew[slot3(q)]
     auto red_plane = [&](int q) {
-        const T *om = S.old[slot5(q - 1)], *o0 = S.old[slot5(q)], *op = S.old[slot5(q + 1)];
-        T *rn = S.rnew[slot3(q)];
+        const Ring r5 = ring<NSLOT>(q);
+        const T *om = S.old[r5.m], *o0 = S.old[r5.z], *op = S.old[r5.p];
+        T *rn = S.rnew[ring<3>(q).z];
         // rows of 16 pairs per half-warp (a half-warp's cells sit in one row, 2 apart;
         // the two halves of a warp take rows of opposite parity, so with even row
         // strides the 32 lanes hit 32 distinct banks), then the 17th pair of each row
@@ -124,9 +136,8 @@ __global__ void __launch_bounds__(FT_THREADS)
             St<T> s, sb;
             gather_old(om, o0, op, jj + 1, kk + 3, s);
             if constexpr (BASE)
-                gather_old(S.base[slot5(q - 1)], S.base[slot5(q)], S.base[slot5(q + 1)], jj + 1,
-                           kk + 3, sb);
-            const T rhs = S.fr[slot5(q)][(jj + 1) * OROW + kk + 3] + cval;
+                gather_old(S.base[r5.m], S.base[r5.z], S.base[r5.p], jj + 1, kk + 3, sb);
+            const T rhs = S.fr[r5.z][(jj + 1) * OROW + kk + 3] + cval;
             rn[jj * RK_ + kk] = upd<T, BASE>(s, sb, rhs, cf, clamped);
         }
     };
@@ -166,8 +177,9 @@ __global__ void __launch_bounds__(FT_THREADS)
             const int j = j0 + jj, kp0 = k0 + 2 * pr;
             const int bodd = (p + j + kp0 + 1) & 1;  // 1: the black cell is the second of the pair
             const int kk = 2 * pr + bodd;            // tile-local k of the black cell
-            const T *om = S.old[slot5(p - 1)], *o0 = S.old[slot5(p)], *op = S.old[slot5(p + 1)];
-            const T *rm = S.rnew[slot3(p - 1)], *r0 = S.rnew[slot3(p)], *rp = S.rnew[slot3(p + 1)];
+            const Ring r5 = ring<NSLOT>(p), r3 = ring<3>(p);
+            const T *om = S.old[r5.m], *o0 = S.old[r5.z], *op = S.old[r5.p];
+            const T *rm = S.rnew[r3.m], *r0 = S.rnew[r3.z], *rp = S.rnew[r3.p];
             const int cr = (jj + 1) * RK_ + (kk + 1);   // rnew coordinates of the black cell
             const int co = (jj + 2) * OROW + (kk + 4);  // old coordinates
             St<T> s;
@@ -192,11 +204,10 @@ __global__ void __launch_bounds__(FT_THREADS)
             s.ymzm = o0[co - OROW - 1];
             St<T> sb;
             if constexpr (BASE)
-                gather_old(S.base[slot5(p - 1)], S.base[slot5(p)], S.base[slot5(p + 1)], jj + 2,
-                           kk + 4, sb);
+                gather_old(S.base[r5.m], S.base[r5.z], S.base[r5.p], jj + 2, kk + 4, sb);
             if (j < n && kp0 < n) {
                 const long long row = ((long long)p * n + j) * n;
-                const T vb = upd<T, BASE>(s, sb, S.fr[slot5(p)][co] + cval, cf, clamped);
+                const T vb = upd<T, BASE>(s, sb, S.fr[r5.z][co] + cval, cf, clamped);
                 const T vr = r0[(jj + 1) * RK_ + (2 * pr + 1 - bodd) + 1];
                 const T v0 = bodd ? vr : vb;
                 const T v1 = bodd ? vb : vr;

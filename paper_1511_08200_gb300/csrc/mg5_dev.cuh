@@ -30,6 +30,9 @@ struct CoefT {
     T s8;      // alpha / (8 h^4): weight of d2 = sum (4 h^2 D_ab)^2 in alpha Sigma
     float k8f;   // 8 alpha / 3, for the FP32 estimate of the FP64 root
     float k43f;  // 4 alpha / 3 (slope of the quadratic is 1 + k43 L)
+    T s3;        // alpha / (3 h^4): weight of the (a, b, c) terms of alpha Sigma(., .)
+    T k43h;      // (4 alpha / 3) / h^2: beta' = 1 + k43h (S_B - 6 B_c)
+    T inv2k23;   // 1 / (2 k23) (0 when alpha = 0, where it is never used)
 };
 
 template <typename T>
@@ -46,6 +49,9 @@ __host__ __device__ inline CoefT<T> make_coef(double h, double alpha)
     c.s8 = (T)(alpha / (8.0 * h4));
     c.k8f = (float)(8.0 * alpha / 3.0);
     c.k43f = (float)(4.0 * alpha / 3.0);
+    c.s3 = (T)(alpha / (3.0 * h4));
+    c.k43h = (T)(4.0 * alpha / (3.0 * h * h));
+    c.inv2k23 = (T)(alpha > 0.0 ? 3.0 / (4.0 * alpha) : 0.0);
     return c;
 }
 
@@ -278,6 +284,48 @@ __device__ __forceinline__ T cell_update_corr(const St<T> &e, const St<T> &B, T 
     const T sq = sqrt(disc);
     const T L = bp >= (T)0 ? (T)2 * b / (bp + sq) : (sq - bp) / ((T)2 * cf.k23);
     return (pe.S - cf.h2 * L) * (T)(1.0 / 6.0);
+}
+
+// FP32 correction form, the inner sweep of the mixed mode.  The same update as the
+// template above, arranged for issue rate: the parts of e and of B are computed as
+// pairs by the packed FP32 instructions (two lanes per instruction on sm_100 and
+// later); 2 Sigma(B, e) + Sigma(e) = sum_t w_t e_t (2 B_t + e_t) as one sum with
+// its weights folded into the per-grid constants; the root with the fast square
+// root and divide (the inner solve needs ~1e-6, the FP64 outer loop corrects it).
+__device__ __forceinline__ float2 pk_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pk_sub(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+
+__device__ __forceinline__ float cell_update_corr(const St<float> &e, const St<float> &B, float rhs,
+                                                  const CoefT<float> &cf, bool &clamped)
+{
+    const auto pr = [](float x, float y) { return make_float2(x, y); };   // (e, B)
+    const float2 sx = pk_add(pr(e.xp, B.xp), pr(e.xm, B.xm));
+    const float2 sy = pk_add(pr(e.yp, B.yp), pr(e.ym, B.ym));
+    const float2 sz = pk_add(pr(e.zp, B.zp), pr(e.zm, B.zm));
+    const float2 S = pk_add(pk_add(sx, sy), sz);
+    const float2 a = pk_sub(sx, sy), b = pk_sub(sx, sz), c = pk_sub(sy, sz);
+    const float2 dxy = pk_sub(pk_sub(pr(e.xpyp, B.xpyp), pr(e.xpym, B.xpym)),
+                              pk_sub(pr(e.xmyp, B.xmyp), pr(e.xmym, B.xmym)));
+    const float2 dxz = pk_sub(pk_sub(pr(e.xpzp, B.xpzp), pr(e.xpzm, B.xpzm)),
+                              pk_sub(pr(e.xmzp, B.xmzp), pr(e.xmzm, B.xmzm)));
+    const float2 dyz = pk_sub(pk_sub(pr(e.ypzp, B.ypzp), pr(e.ypzm, B.ypzm)),
+                              pk_sub(pr(e.ymzp, B.ymzp), pr(e.ymzm, B.ymzm)));
+    const float bp = fmaf(cf.k43h, fmaf(-6.0f, B.c, S.y), 1.0f);   // beta' = 1 + (4 alpha/3) L_B
+    const float X = a.x * fmaf(2.0f, a.y, a.x) + b.x * fmaf(2.0f, b.y, b.x) + c.x * fmaf(2.0f, c.y, c.x);
+    const float Y = dxy.x * fmaf(2.0f, dxy.y, dxy.x) + dxz.x * fmaf(2.0f, dxz.y, dxz.x) +
+                    dyz.x * fmaf(2.0f, dyz.y, dyz.x);
+    const float bq = rhs + cf.s3 * X + cf.s8 * Y;                   // b'
+    float disc = fmaf(bp, bp, cf.k8 * bq);
+    if (disc < 0.0f) {
+        disc = 0.0f;
+        clamped = true;
+    }
+    const float sq = disc > 0.0f ? disc * rsqrtf(disc) : 0.0f;
+    const float L = bp >= 0.0f ? __fdividef(2.0f * bq, bp + sq) : (sq - bp) * cf.inv2k23;
+    return (S.x - cf.h2 * L) * (1.0f / 6.0f);
 }
 
 template <typename T>
