@@ -70,6 +70,7 @@ def _load():
     lib.or_solve.restype = i
     lib.or_force.argtypes = [P, P, i, d, i, P]
     lib.or_refine_interpolate.argtypes = [P, i, P, P, i, P]
+    lib.or_refine_cubic.argtypes = [P, i, P, P, i, P]
     lib.or_patch_residual.argtypes = [P, P, d, P, d, d, P]
     lib.or_relax_patch.argtypes = [P, P, d, d, d, d, d, i, i, P, P]
     lib.or_relax_patch.restype = i
@@ -223,6 +224,16 @@ def refine_interpolate(phic, origin, pn, ghost) -> np.ndarray:
     dims = tuple(2 * int(x) + 2 * ghost for x in pn_)
     out = np.empty(dims)
     _load().or_refine_interpolate(_p(phic), phic.shape[0], _p(o), _p(pn_), ghost, _p(out))
+    return out
+
+
+def refine_cubic(phic, origin, pn, ghost) -> np.ndarray:
+    """Tricubic (4-point Lagrange per axis) variant of refine_interpolate (an extension)."""
+    phic = _f64(phic)
+    o, pn_ = _i3(origin), _i3(pn)
+    dims = tuple(2 * int(x) + 2 * ghost for x in pn_)
+    out = np.empty(dims)
+    _load().or_refine_cubic(_p(phic), phic.shape[0], _p(o), _p(pn_), ghost, _p(out))
     return out
 
 

@@ -612,6 +612,49 @@ void or_refine_interpolate(const double *phic, int nc, const int o[3], const int
             }
 }
 
+/*
+ * Higher-order variant of the same interpolation (an extension, not in the
+ * paper): per axis the 4-point Lagrange polynomial through the coarse centres
+ * i0 - 1 .. i0 + 2 around the fine centre, evaluated at its offset w from i0;
+ * the tensor product of the three axes.  Reproduces cubic polynomials.
+ */
+static double lagrange4(int k, double w)
+{
+    switch (k) {
+    case 0: return -w * (w - 1.0) * (w - 2.0) / 6.0;
+    case 1: return (w + 1.0) * (w - 1.0) * (w - 2.0) / 2.0;
+    case 2: return -(w + 1.0) * w * (w - 2.0) / 2.0;
+    default: return (w + 1.0) * w * (w - 1.0) / 6.0;
+    }
+}
+
+void or_refine_cubic(const double *phic, int nc, const int o[3], const int pn[3], int g,
+                     double *fine)
+{
+    int d[3];
+    for (int a = 0; a < 3; ++a)
+        d[a] = 2 * pn[a] + 2 * g;
+    for (int I = 0; I < d[0]; ++I)
+        for (int J = 0; J < d[1]; ++J)
+            for (int K = 0; K < d[2]; ++K) {
+                int loc[3] = {I, J, K};
+                int i0[3];
+                double w[3];
+                for (int a = 0; a < 3; ++a) {
+                    double t = o[a] + (loc[a] - g + 0.5) / 2.0 - 0.5;
+                    i0[a] = (int)floor(t);
+                    w[a] = t - i0[a];
+                }
+                double v = 0.0;
+                for (int a = 0; a < 4; ++a)
+                    for (int b = 0; b < 4; ++b)
+                        for (int c = 0; c < 4; ++c)
+                            v += lagrange4(a, w[0]) * lagrange4(b, w[1]) * lagrange4(c, w[2]) *
+                                 per(phic, nc, i0[0] - 1 + a, i0[1] - 1 + b, i0[2] - 1 + c);
+                fine[((size_t)I * d[1] + J) * d[2] + K] = v;
+            }
+}
+
 /* ------------------------------------------------------------------ */
 /* patch relaxation with fixed (Dirichlet) ghost values (Sec. 3.1)      */
 /* ------------------------------------------------------------------ */

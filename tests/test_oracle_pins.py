@@ -426,6 +426,37 @@ def test_refine_interpolate_translation_invariance():
     assert np.abs(a - b).max() < 1e-14
 
 
+def test_refine_cubic_reproduces_cubics_and_constants():
+    """The tricubic variant (4-point Lagrange per axis, an extension) is exact for any cubic
+    polynomial where its stencil does not wrap, and keeps constants."""
+    nc = 20
+    c = np.full((nc,) * 3, -1.75)
+    assert np.allclose(oracle.refine_cubic(c, (3, 7, 11), (4, 5, 3), 1), -1.75, atol=1e-14)
+    i = np.arange(nc) + 0.5
+    I, J, K = np.meshgrid(i, i, i, indexing="ij")
+    cub = lambda x, y, z: 0.02 * x ** 3 - 0.1 * x * y * z + 0.5 * y ** 2 - 0.03 * z ** 3 + x * z + 1.0
+    o, pn, g = (4, 5, 6), (5, 4, 6), 1
+    f = oracle.refine_cubic(cub(I, J, K), o, pn, g)
+    loc = [o[a] + (np.arange(2 * pn[a] + 2 * g) - g + 0.5) / 2 for a in range(3)]
+    X, Y, Z = np.meshgrid(*loc, indexing="ij")
+    assert np.abs(f - cub(X, Y, Z)).max() < 1e-11
+    # trilinear is not exact on the same cubic (the pin discriminates the two)
+    assert np.abs(oracle.refine_interpolate(cub(I, J, K), o, pn, g) - cub(X, Y, Z)).max() > 1e-3
+
+
+def test_refine_cubic_one_dimensional_weights():
+    """1-D closed form: the fine child a quarter cell right of coarse centre i (w = 1/4 from i)
+    gets (-7 phi_{i-1} + 105 phi_i + 35 phi_{i+1} - 5 phi_{i+2}) / 128."""
+    nc = 16
+    rng = np.random.default_rng(8)
+    line = rng.standard_normal(nc)
+    c = np.broadcast_to(line[:, None, None], (nc,) * 3).copy()
+    f = oracle.refine_cubic(c, (0, 0, 0), (nc, 1, 1), 0)
+    right = f[1::2, 0, 0]                       # fine cells at coarse coordinate i + 3/4
+    ref = (-7 * np.roll(line, 1) + 105 * line + 35 * np.roll(line, -1) - 5 * np.roll(line, -2)) / 128
+    assert np.abs(right - ref).max() < 1e-14
+
+
 # ---------------------------------------------------------------- patch relaxation
 
 def test_relax_patch_manufactured_dirichlet():
