@@ -67,7 +67,7 @@ WORK = {
 #   sweep32: k_sweep_fused<float,1>, 256^3 finest-grid launch: 278.1 MB / 16.78 M cells
 #            (profiles/sweep32_fused_mixed256.md)
 TRAFFIC_PER_CELL = {
-    "sweep32": 278.1e6 / 256 ** 3,
+    "sweep32": 279.0e6 / 256 ** 3,
 }
 
 
@@ -374,6 +374,11 @@ def run_ours(args):
         "autotune": tune or None,
     }
     out["geff"] = geff_report(step)
+    if not args.no_truncation_levels:
+        try:
+            out["truncation_levels"] = truncation_levels_report(mg, torch, dev)
+        except mg.MG5Error as e:   # reported, not fatal to the bench line
+            out["truncation_levels"] = {"error": str(e)}
     if not args.no_batch:
         out["batch"] = run_batch(mg, torch, dev, step.alpha, step.s, autotune=not args.no_autotune)
     if args.serve_seconds > 0:
@@ -413,7 +418,19 @@ def geff_report(step):
     eps = d5 / (0.5 * mag(step.g_full))
     dgeff = d5 / mag(g_gr)
     q = lambda t: [float(x) for x in torch.quantile(t.flatten()[::7].float(), torch.tensor([0.5, 0.99], device=t.device))]
+    # interpolation variants of the truncated level, each against the relaxed force:
+    # tricubic phi (an extension), and the coarse force interpolated directly (the
+    # Fig. amr caption's wording) instead of differencing the interpolated phi
+    rl2 = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    box_c = ctx.refine_interpolate_cubic(step.phi, step.origin, (PN, PN, PN), 1)
+    g_cub = ctx.force(box_c, H_COARSE / 2, ghost=1, periodic=False)
+    g_fi = torch.stack([ctx.refine_interpolate(step.grad[a].contiguous(), step.origin, (PN, PN, PN), 0)
+                        for a in range(3)])
+    torch.cuda.synchronize()
+    variants = {"phi_trilinear": rl2(step.g_tr, step.g_full), "phi_tricubic": rl2(g_cub, step.g_full),
+                "force_trilinear": rl2(g_fi, step.g_full)}
     return {"linear_ratio_1_over_3beta": 1.0 / (3.0 * step.beta),
+            "eps_trunc_rel_l2_by_interpolant": variants,
             "f5_over_fgr_domain_p50_p99": q(r_dom), "f5_over_fgr_patch_p50_p99": q(r_full),
             "f5_over_fgr_patch_trunc_p50_p99": q(r_tr),
             "eps_trunc_rel_l2": float(torch.linalg.vector_norm(step.g_tr - step.g_full)
@@ -421,6 +438,78 @@ def geff_report(step):
             "eps_trunc_p50_p99": q(eps),
             "geff_error_p50_p99": q(dgeff),
             "gr_cycles": ig.cycles}
+
+
+def nested_chain(ctx, mg, torch, d_levels, origins, spacings, phi_dom, alpha, s, compat_c, T, tol):
+    """phi on every refinement of a nested hierarchy: relaxed (mg5_relax_patch) on levels
+    < T, the coarse-to-fine interpolant of its parent (mg5_refine_interpolate[_box]) on levels
+    >= T (the truncation of Sec. 3.2 at l_trunc = l_d + T).  Returns the level boxes."""
+    boxes = [None]
+    for lev in range(1, len(d_levels)):
+        pn = (int(d_levels[lev].shape[0]) // 2,) * 3
+        if lev == 1:
+            box = ctx.refine_interpolate(phi_dom, origins[1], pn, 1)
+        else:
+            box = ctx.refine_interpolate_box(boxes[lev - 1], 1, origins[lev], pn, 1)
+        if lev < T:
+            p = mg.default_params(alpha=alpha, s=s, h=spacings[lev], tol=tol, max_cycles=200)
+            ctx.relax_patch(d_levels[lev], p, compat_c, box)
+        boxes.append(box)
+    return boxes
+
+
+def truncation_levels_report(mg, torch, dev, n_dom=128, levels=4, pn=16):
+    """The multi-level truncation analogue of the paper's Table 1 / Fig. ratio (once, not
+    timed in the step): a 128^3 domain plus 4 nested 2x refinements (32^3 each) around an
+    NFW halo (M200 = 1e14 M_sun/h, c = 5) on the lognormal background; phi relaxed on every
+    level (full) or truncated at l_trunc = l_d + T (levels >= T interpolated), T = 1, 2, 4;
+    the GR force relaxed on every level.  Per level: median F5/F_GR (full), eps_trunc and
+    the G_eff error of Eq. errors2; GPU time of each chain."""
+    import workload
+    deltas, origins, spacings = workload.nested_halo_workload(n_dom, 250.0, levels, pn)
+    beta, alpha, s = mg.ndgp_coefficients(1.0, 0.3, 1.0)
+    d = [torch.from_numpy(x).to(dev) for x in deltas]
+    ctx = mg.Context(dev.index or 0)
+    tol = 1e-8
+    p = mg.default_params(alpha=alpha, s=s, h=spacings[0], tol=tol)
+    phi, _, i5 = ctx.solve_fifth_force(d[0], p)
+    s_gr = 1.5 * beta * s
+    pg = mg.default_params(alpha=0.0, s=s_gr, h=spacings[0], tol=tol)
+    psi, _, ig = ctx.solve_fifth_force(d[0], pg)
+    mag = lambda g: torch.linalg.vector_norm(g, dim=0)
+    force = lambda b, h: ctx.force(b, h, ghost=1, periodic=False)
+    gr = nested_chain(ctx, mg, torch, d, origins, spacings, psi, 0.0, s_gr, ig.compat_c,
+                      levels + 1, tol)
+    f_gr = [None] + [mag(force(gr[l], spacings[l])) for l in range(1, levels + 1)]
+    chains, ms = {}, {}
+    for T in (levels + 1, 1, 2, 4):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        boxes = nested_chain(ctx, mg, torch, d, origins, spacings, phi, alpha, s, i5.compat_c, T, tol)
+        g5 = [None] + [0.5 * force(boxes[l], spacings[l]) for l in range(1, levels + 1)]
+        e1.record()
+        e1.synchronize()
+        chains[T], ms[T] = g5, e0.elapsed_time(e1)
+    full = chains[levels + 1]
+    q = lambda t: [float(x) for x in torch.quantile(t.flatten().float(),
+                                                    torch.tensor([0.5, 0.99], device=t.device))]
+    out = {"levels": levels, "spacing_mpc_h": spacings, "box_cells": 2 * pn,
+           "f5_over_fgr_p50_by_level": [float(torch.median(mag(full[l]) / f_gr[l]))
+                                        for l in range(1, levels + 1)],
+           "linear_ratio": 1.0 / (3.0 * beta), "chain_ms": {}, "eps_trunc_rel_l2": {},
+           "geff_error_p50_p99": {}}
+    for T in (1, 2, 4):
+        key = "l_trunc=l_d+%d" % T
+        out["chain_ms"][key] = ms[T]
+        out["eps_trunc_rel_l2"][key] = [
+            float(torch.linalg.vector_norm(chains[T][l] - full[l]) / torch.linalg.vector_norm(full[l]))
+            for l in range(1, levels + 1)]
+        out["geff_error_p50_p99"][key] = [q(mag(chains[T][l] - full[l]) / f_gr[l])
+                                         for l in range(1, levels + 1)]
+    out["chain_ms"]["full"] = ms[levels + 1]
+    ctx.close()
+    return out
 
 
 def schedules(mg, device, prec, n):
@@ -715,6 +804,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-box batched workload")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--no-truncation-levels", action="store_true",
+                    help="skip the nested multi-level truncation report")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default sweep schedules instead of the tuned ones")
     ap.add_argument("--serve-seconds", type=float, default=6.0,

@@ -84,7 +84,7 @@ typedef struct {
     double alpha, s, h, tol;
     int nu1, nu2, nu_coarse, max_cycles;
     int precision;
-    int inner_cycles;   /* MG5_MIXED: FP32 V-cycles per FP64 step (0 = default 3) */
+    int inner_cycles;   /* MG5_MIXED: FP32 V-cycles per FP64 step (0 = 4 if tol < 1e-7, else 3) */
 } mg5_params;
 
 /* Per-solve report, written on return (after the stream has synchronised). */
@@ -101,6 +101,7 @@ typedef struct {
     long long disc_clamped;  /* cells whose discriminant was clamped */
     long long cell_updates;  /* cells relaxed: one per cell per full sweep, every grid */
     double ms_total;         /* wall time of the call on the stream, ms */
+    long long coarse_sweeps; /* sweeps of the coarsest-grid solves, summed over its visits */
     double history[64];      /* relative residual per finest-level check */
 } mg5_info;
 
@@ -207,6 +208,32 @@ int mg5_force(mg5_ctx *ctx, const double *phi, const int dims[3], int ghost, dou
  */
 int mg5_refine_interpolate(mg5_ctx *ctx, const double *phi_coarse, int Nc, const int o[3],
                            const int pn[3], int ghost, double *phi_fine, void *stream);
+
+/*
+ * Tricubic variant of mg5_refine_interpolate (an extension; the paper interpolates
+ * without naming an order): per axis the 4-point Lagrange polynomial through the
+ * coarse centres around the fine centre (weights (-7, 105, 35, -5)/128 a quarter
+ * cell right of a centre, mirrored three quarters right), tensor product over the
+ * axes; exact for cubic polynomials.  Same arguments as mg5_refine_interpolate;
+ * Nc >= 4.
+ */
+int mg5_refine_interpolate_cubic(mg5_ctx *ctx, const double *phi_coarse, int Nc, const int o[3],
+                                 const int pn[3], int ghost, double *phi_fine, void *stream);
+
+/*
+ * The same interpolation from a refinement's box instead of the periodic domain:
+ * the next level of a nested hierarchy of refinements (Sec. 3.1, Fig. amr: each
+ * refinement takes its boundary values and initial guess from its parent).
+ *   box:    parent phi (device FP64), dims bd[3] including a ghost shell of pg
+ *           cells; interior cell m of axis a is box index m + pg.
+ *   o, pn:  the child covers parent interior cells [o, o + pn), inside the interior.
+ *   ghost:  fine ghost cells on every side (0..4).
+ * Every parent centre the trilinear stencil reaches must lie in the box (for
+ * ghost = 1 a parent ghost shell of one cell suffices); MG5_E_ARG otherwise.
+ */
+int mg5_refine_interpolate_box(mg5_ctx *ctx, const double *box, const int bd[3], int pg,
+                               const int o[3], const int pn[3], int ghost, double *phi_fine,
+                               void *stream);
 
 /*
  * Relax the refinement (the untruncated, "full" fine level of Sec. 3.2):

@@ -45,7 +45,7 @@ class _Info(ctypes.Structure):
                 ("rel_residual", _c_double), ("compat_c", _c_double),
                 ("phi_mean_removed", _c_double), ("disc_clamped", ctypes.c_longlong),
                 ("cell_updates", ctypes.c_longlong), ("ms_total", _c_double),
-                ("history", _c_double * 64)]
+                ("coarse_sweeps", ctypes.c_longlong), ("history", _c_double * 64)]
 
 
 @dataclass
@@ -61,13 +61,14 @@ class Info:
     disc_clamped: int
     cell_updates: int
     ms_total: float
+    coarse_sweeps: int = 0
     history: list = field(default_factory=list)
 
     @classmethod
     def _from(cls, i: _Info) -> "Info":
         return cls(i.status, i.cycles, i.outer_iters, i.levels, i.coarsest_n, i.rel_residual,
                    i.compat_c, i.phi_mean_removed, i.disc_clamped, i.cell_updates, i.ms_total,
-                   [i.history[q] for q in range(min(i.n_history, 64))])
+                   i.coarse_sweeps, [i.history[q] for q in range(min(i.n_history, 64))])
 
 
 class _Request(ctypes.Structure):
@@ -109,6 +110,8 @@ _sigs = {
     "mg5_solve_fifth_force": ([_P, _P, _c_int, _P, _c_uint, _P, _P, _P, _P], _c_int),
     "mg5_force": ([_P, _P, _I3, _c_int, _c_double, _c_int, _P, _P], _c_int),
     "mg5_refine_interpolate": ([_P, _P, _c_int, _I3, _I3, _c_int, _P, _P], _c_int),
+    "mg5_refine_interpolate_cubic": ([_P, _P, _c_int, _I3, _I3, _c_int, _P, _P], _c_int),
+    "mg5_refine_interpolate_box": ([_P, _P, _I3, _c_int, _I3, _I3, _c_int, _P, _P], _c_int),
     "mg5_relax_patch": ([_P, _P, _I3, _P, _c_double, _P, _P, _P], _c_int),
     "mg5_solve_batch": ([_P, _c_int, _P, _P, _P, _P, _P, _P, _P], _c_int),
     "mg5_cached_bytes": ([_P, _c_int, _c_int, _P], _c_int),
@@ -412,6 +415,29 @@ class Context:
             out = torch.empty(dims, dtype=phi_coarse.dtype, device=phi_coarse.device)
         self._check(_lib.mg5_refine_interpolate(self._h, _ptr(phi_coarse), nc, _I3(*origin),
                                                 _I3(*pn), ghost, _ptr(out), _stream(stream)))
+        return out
+
+    def refine_interpolate_cubic(self, phi_coarse, origin, pn, ghost: int, out=None, stream=None):
+        """mg5_refine_interpolate_cubic: the tricubic variant of refine_interpolate."""
+        import torch
+        nc = int(phi_coarse.shape[0])
+        dims = [2 * int(p) + 2 * ghost for p in pn]
+        if out is None:
+            out = torch.empty(dims, dtype=phi_coarse.dtype, device=phi_coarse.device)
+        self._check(_lib.mg5_refine_interpolate_cubic(self._h, _ptr(phi_coarse), nc, _I3(*origin),
+                                                      _I3(*pn), ghost, _ptr(out), _stream(stream)))
+        return out
+
+    def refine_interpolate_box(self, box, pg: int, origin, pn, ghost: int, out=None, stream=None):
+        """mg5_refine_interpolate_box: child window [origin, origin + pn) of a parent box
+        (dims box.shape, interior offset pg) -> fine box (2 pn + 2 ghost per axis)."""
+        import torch
+        dims = [2 * int(p) + 2 * ghost for p in pn]
+        if out is None:
+            out = torch.empty(dims, dtype=box.dtype, device=box.device)
+        self._check(_lib.mg5_refine_interpolate_box(self._h, _ptr(box), _I3(*[int(x) for x in box.shape]),
+                                                    pg, _I3(*origin), _I3(*pn), ghost, _ptr(out),
+                                                    _stream(stream)))
         return out
 
     def relax_patch(self, delta_fine, params: Params, compat_c: float, phi_box, stream=None,

@@ -659,8 +659,17 @@ cudaError_t launch_force(const double *phi, int d0, int d1, int d2, int ghost, d
 // fine local index I (ghosts included) -> coarse coordinate x = o + (I - g + 1/2)/2;
 // t = x - 1/2 = o + (I - g)/2 - 1/4; i0 = floor(t), w = t - i0 in {1/4, 3/4}.
 // --------------------------------------------------------------------------
-__global__ void k_refine(const double *__restrict__ phic, int nc, int o0, int o1, int o2, int d0,
-                         int d1, int d2, int g, double *__restrict__ fine)
+// Source grid of the interpolation: a periodic cube (nc^3), or a box of dims c[3]
+// whose interior starts at offset `pg` on every axis (no wrap; the caller checks
+// that every stencil cell lies inside the box).
+struct RefineSrc {
+    int c0, c1, c2;   // dims of the stored array
+    int pg;           // interior offset (0 for the periodic cube)
+    int periodic;     // 1: wrap indices modulo c (cube)
+};
+
+__global__ void k_refine(const double *__restrict__ phic, RefineSrc src, int o0, int o1, int o2,
+                         int d0, int d1, int d2, int g, double *__restrict__ fine)
 {
     const long long total = (long long)d0 * d1 * d2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -671,6 +680,7 @@ __global__ void k_refine(const double *__restrict__ phic, int nc, int o0, int o1
     const int J = (int)(q % d1), I = (int)(q / d1);
     const int loc[3] = {I, J, K};
     const int org[3] = {o0, o1, o2};
+    const int dim[3] = {src.c0, src.c1, src.c2};
     int lo[3], hi[3];
     double w[3];
 #pragma unroll
@@ -679,12 +689,17 @@ __global__ void k_refine(const double *__restrict__ phic, int nc, int o0, int o1
         const int t4 = 4 * org[a] + 2 * (loc[a] - g) - 1;
         const int i0 = (t4 >= 0) ? (t4 >> 2) : -((-t4 + 3) >> 2);
         w[a] = (double)(t4 - 4 * i0) * 0.25;
-        int l = i0 % nc;
-        l = l < 0 ? l + nc : l;
-        lo[a] = l;
-        hi[a] = (l + 1 == nc) ? 0 : l + 1;
+        if (src.periodic) {
+            int l = i0 % dim[a];
+            l = l < 0 ? l + dim[a] : l;
+            lo[a] = l;
+            hi[a] = (l + 1 == dim[a]) ? 0 : l + 1;
+        } else {
+            lo[a] = i0 + src.pg;
+            hi[a] = i0 + 1 + src.pg;
+        }
     }
-    const long long NC = nc;
+    const long long C1 = src.c1, C2 = src.c2;
     double v = 0.0;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -695,7 +710,7 @@ __global__ void k_refine(const double *__restrict__ phic, int nc, int o0, int o1
                 const double wt = (a ? w[0] : 1.0 - w[0]) * (b ? w[1] : 1.0 - w[1]) *
                                   (c ? w[2] : 1.0 - w[2]);
                 const long long idx =
-                    ((long long)(a ? hi[0] : lo[0]) * NC + (b ? hi[1] : lo[1])) * NC +
+                    ((long long)(a ? hi[0] : lo[0]) * C1 + (b ? hi[1] : lo[1])) * C2 +
                     (c ? hi[2] : lo[2]);
                 v += wt * phic[idx];
             }
@@ -707,7 +722,76 @@ cudaError_t launch_refine(const double *phic, int nc, const int o[3], const int 
 {
     const int d0 = 2 * pn[0] + 2 * ghost, d1 = 2 * pn[1] + 2 * ghost, d2 = 2 * pn[2] + 2 * ghost;
     const long long work = (long long)d0 * d1 * d2;
-    k_refine<<<blocks_for(work), kBlock, 0, st>>>(phic, nc, o[0], o[1], o[2], d0, d1, d2, ghost,
+    const RefineSrc src{nc, nc, nc, 0, 1};
+    k_refine<<<blocks_for(work), kBlock, 0, st>>>(phic, src, o[0], o[1], o[2], d0, d1, d2, ghost,
+                                                  fine);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+// Tricubic variant (periodic source): per axis the fine centre sits a quarter cell right
+// (w = 1/4) or three quarters right (w = 3/4) of coarse centre i0; the 4-point Lagrange
+// weights on i0 - 1 .. i0 + 2 are then (-7, 105, 35, -5) / 128 or (-5, 35, 105, -7) / 128.
+__global__ void k_refine_cubic(const double *__restrict__ phic, int nc, int o0, int o1, int o2,
+                               int d0, int d1, int d2, int g, double *__restrict__ fine)
+{
+    const long long total = (long long)d0 * d1 * d2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total)
+        return;
+    const int K = (int)(t % d2);
+    const long long q = t / d2;
+    const int J = (int)(q % d1), I = (int)(q / d1);
+    const int loc[3] = {I, J, K};
+    const int org[3] = {o0, o1, o2};
+    int idx[3][4];
+    double w[3][4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int t4 = 4 * org[a] + 2 * (loc[a] - g) - 1;   // 4 (coarse coordinate - 1/2)
+        const int i0 = (t4 >= 0) ? (t4 >> 2) : -((-t4 + 3) >> 2);
+        const bool quarter = (t4 - 4 * i0) == 1;
+        w[a][0] = (quarter ? -7.0 : -5.0) / 128.0;
+        w[a][1] = (quarter ? 105.0 : 35.0) / 128.0;
+        w[a][2] = (quarter ? 35.0 : 105.0) / 128.0;
+        w[a][3] = (quarter ? -5.0 : -7.0) / 128.0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            int l = (i0 - 1 + m) % nc;
+            idx[a][m] = l < 0 ? l + nc : l;
+        }
+    }
+    const long long NC = nc;
+    double v = 0.0;
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+            const long long row = ((long long)idx[0][a] * NC + idx[1][b]) * NC;
+            const double wab = w[0][a] * w[1][b];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                v += wab * w[2][c] * phic[row + idx[2][c]];
+        }
+    fine[t] = v;
+}
+
+cudaError_t launch_refine_cubic(const double *phic, int nc, const int o[3], const int pn[3], int ghost,
+                                double *fine, cudaStream_t st)
+{
+    const int d0 = 2 * pn[0] + 2 * ghost, d1 = 2 * pn[1] + 2 * ghost, d2 = 2 * pn[2] + 2 * ghost;
+    const long long work = (long long)d0 * d1 * d2;
+    k_refine_cubic<<<blocks_for(work), kBlock, 0, st>>>(phic, nc, o[0], o[1], o[2], d0, d1, d2,
+                                                        ghost, fine);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_box(const double *box, const int bd[3], int pg, const int o[3],
+                              const int pn[3], int ghost, double *fine, cudaStream_t st)
+{
+    const int d0 = 2 * pn[0] + 2 * ghost, d1 = 2 * pn[1] + 2 * ghost, d2 = 2 * pn[2] + 2 * ghost;
+    const long long work = (long long)d0 * d1 * d2;
+    const RefineSrc src{bd[0], bd[1], bd[2], pg, 0};
+    k_refine<<<blocks_for(work), kBlock, 0, st>>>(box, src, o[0], o[1], o[2], d0, d1, d2, ghost,
                                                   fine);
     count_launch(1);
     return cudaGetLastError();

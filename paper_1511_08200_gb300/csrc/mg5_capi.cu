@@ -1041,6 +1041,7 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
         info->phi_mean_removed = tail[1];
         const long long nc = info->coarsest_n;
         info->cell_updates += (long long)cnt.coarse_sweeps * nc * nc * nc;
+        info->coarse_sweeps = cnt.coarse_sweeps;
     }
     return status;
 }
@@ -1077,6 +1078,48 @@ int mg5_refine_interpolate(mg5_ctx *ctx, const double *phic, int Nc, const int o
     ProfScope ps(&ctx->prof, PK_REFINE, (cudaStream_t)stream,
                  (double)(2 * pn[0] + 2 * ghost) * (2 * pn[1] + 2 * ghost) * (2 * pn[2] + 2 * ghost));
     CK(launch_refine(phic, Nc, o, pn, ghost, fine, (cudaStream_t)stream));
+    return MG5_OK;
+}
+
+int mg5_refine_interpolate_cubic(mg5_ctx *ctx, const double *phic, int Nc, const int o[3],
+                                 const int pn[3], int ghost, double *fine, void *stream)
+{
+    if (!ctx || !phic || !o || !pn || !fine || Nc < 4 || ghost < 0 || ghost > 4)
+        return MG5_E_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (o[a] < 0 || o[a] >= Nc || pn[a] < 1 || pn[a] > Nc)
+            return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    ProfScope ps(&ctx->prof, PK_REFINE, (cudaStream_t)stream,
+                 (double)(2 * pn[0] + 2 * ghost) * (2 * pn[1] + 2 * ghost) * (2 * pn[2] + 2 * ghost));
+    CK(launch_refine_cubic(phic, Nc, o, pn, ghost, fine, (cudaStream_t)stream));
+    return MG5_OK;
+}
+
+static int floor_div4(int x) { return x >= 0 ? x / 4 : -((-x + 3) / 4); }
+
+int mg5_refine_interpolate_box(mg5_ctx *ctx, const double *box, const int bd[3], int pg,
+                               const int o[3], const int pn[3], int ghost, double *fine,
+                               void *stream)
+{
+    if (!ctx || !box || !bd || !o || !pn || !fine || pg < 0 || ghost < 0 || ghost > 4)
+        return MG5_E_ARG;
+    for (int a = 0; a < 3; ++a) {
+        const int D = bd[a] - 2 * pg;
+        if (D < 1 || o[a] < 0 || pn[a] < 1 || o[a] + pn[a] > D)
+            return MG5_E_ARG;
+        // every coarse centre the trilinear stencil touches must lie in the box
+        const int lo = floor_div4(4 * o[a] - 2 * ghost - 1);
+        const int hi = floor_div4(4 * o[a] + 2 * (2 * pn[a] + ghost - 1) - 1) + 1;
+        if (lo + pg < 0 || hi + pg > bd[a] - 1) {
+            ctx->err = "refine_interpolate_box: the window and its fine ghosts reach outside the box";
+            return MG5_E_ARG;
+        }
+    }
+    CK(cudaSetDevice(ctx->device));
+    ProfScope ps(&ctx->prof, PK_REFINE, (cudaStream_t)stream,
+                 (double)(2 * pn[0] + 2 * ghost) * (2 * pn[1] + 2 * ghost) * (2 * pn[2] + 2 * ghost));
+    CK(launch_refine_box(box, bd, pg, o, pn, ghost, fine, (cudaStream_t)stream));
     return MG5_OK;
 }
 
@@ -1270,6 +1313,7 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
         info->levels = h->nlev;
         info->coarsest_n = h->q[h->nlev - 1][0];
         info->cell_updates = R.cu + (long long)cnt.coarse_sweeps * (long long)int_cells(h->q[h->nlev - 1]);
+        info->coarse_sweeps = cnt.coarse_sweeps;
         info->disc_clamped = (long long)cnt.clamped;
         info->compat_c = compat_c;
     }
@@ -1479,6 +1523,7 @@ int graph_finish(GraphEntry *g, mg5_info *info)
         const long long nc = info->coarsest_n;
         info->cell_updates =
             g->stats.cells_per_iter * ctl.outer + (long long)cnt.coarse_sweeps * nc * nc * nc;
+        info->coarse_sweeps = cnt.coarse_sweeps;
         info->disc_clamped = (long long)cnt.clamped;
     }
     if (status == MG5_OK && cnt.clamped > 0)
@@ -1742,6 +1787,7 @@ int mg5_solve_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const in
             o.disc_clamped = (long long)cnt[i].clamped;
             const long long nc = o.coarsest_n;
             o.cell_updates = cs.cells_per_iter * ctl[i].outer + (long long)cnt[i].coarse_sweeps * nc * nc * nc;
+            o.coarse_sweeps = cnt[i].coarse_sweeps;
             o.ms_total = ms;
         }
     }

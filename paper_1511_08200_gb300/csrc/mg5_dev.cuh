@@ -298,26 +298,47 @@ __device__ __forceinline__ float2 pk_sub(float2 a, float2 b)
     return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
 }
 
-__device__ __forceinline__ float cell_update_corr(const St<float> &e, const St<float> &B, float rhs,
-                                                  const CoefT<float> &cf, bool &clamped)
+// Parts of e and B as (e, B) pairs, and the merged form
+// X = sum_{a,b,c} e_t (2 B_t + e_t), Y = sum_{dxy,dxz,dyz} e_t (2 B_t + e_t).
+struct Parts2 {
+    float2 S, a, b, c, dxy, dxz, dyz;
+};
+
+__device__ __forceinline__ Parts2 parts2_of(const St<float> &e, const St<float> &B)
 {
     const auto pr = [](float x, float y) { return make_float2(x, y); };   // (e, B)
+    Parts2 q;
     const float2 sx = pk_add(pr(e.xp, B.xp), pr(e.xm, B.xm));
     const float2 sy = pk_add(pr(e.yp, B.yp), pr(e.ym, B.ym));
     const float2 sz = pk_add(pr(e.zp, B.zp), pr(e.zm, B.zm));
-    const float2 S = pk_add(pk_add(sx, sy), sz);
-    const float2 a = pk_sub(sx, sy), b = pk_sub(sx, sz), c = pk_sub(sy, sz);
-    const float2 dxy = pk_sub(pk_sub(pr(e.xpyp, B.xpyp), pr(e.xpym, B.xpym)),
-                              pk_sub(pr(e.xmyp, B.xmyp), pr(e.xmym, B.xmym)));
-    const float2 dxz = pk_sub(pk_sub(pr(e.xpzp, B.xpzp), pr(e.xpzm, B.xpzm)),
-                              pk_sub(pr(e.xmzp, B.xmzp), pr(e.xmzm, B.xmzm)));
-    const float2 dyz = pk_sub(pk_sub(pr(e.ypzp, B.ypzp), pr(e.ypzm, B.ypzm)),
-                              pk_sub(pr(e.ymzp, B.ymzp), pr(e.ymzm, B.ymzm)));
-    const float bp = fmaf(cf.k43h, fmaf(-6.0f, B.c, S.y), 1.0f);   // beta' = 1 + (4 alpha/3) L_B
-    const float X = a.x * fmaf(2.0f, a.y, a.x) + b.x * fmaf(2.0f, b.y, b.x) + c.x * fmaf(2.0f, c.y, c.x);
-    const float Y = dxy.x * fmaf(2.0f, dxy.y, dxy.x) + dxz.x * fmaf(2.0f, dxz.y, dxz.x) +
-                    dyz.x * fmaf(2.0f, dyz.y, dyz.x);
-    const float bq = rhs + cf.s3 * X + cf.s8 * Y;                   // b'
+    q.S = pk_add(pk_add(sx, sy), sz);
+    q.a = pk_sub(sx, sy);
+    q.b = pk_sub(sx, sz);
+    q.c = pk_sub(sy, sz);
+    q.dxy = pk_sub(pk_sub(pr(e.xpyp, B.xpyp), pr(e.xpym, B.xpym)),
+                   pk_sub(pr(e.xmyp, B.xmyp), pr(e.xmym, B.xmym)));
+    q.dxz = pk_sub(pk_sub(pr(e.xpzp, B.xpzp), pr(e.xpzm, B.xpzm)),
+                   pk_sub(pr(e.xmzp, B.xmzp), pr(e.xmzm, B.xmzm)));
+    q.dyz = pk_sub(pk_sub(pr(e.ypzp, B.ypzp), pr(e.ypzm, B.ypzm)),
+                   pk_sub(pr(e.ymzp, B.ymzp), pr(e.ymzm, B.ymzm)));
+    return q;
+}
+
+// alpha (2 Sigma(B, e) + Sigma(e)), the weights folded into s3 = alpha / (3 h^4), s8 = alpha / (8 h^4)
+__device__ __forceinline__ float sigma_corr(const Parts2 &q, const CoefT<float> &cf)
+{
+    const auto t = [](float2 v) { return v.x * fmaf(2.0f, v.y, v.x); };
+    const float X = t(q.a) + t(q.b) + t(q.c);
+    const float Y = t(q.dxy) + t(q.dxz) + t(q.dyz);
+    return cf.s3 * X + cf.s8 * Y;
+}
+
+__device__ __forceinline__ float cell_update_corr(const St<float> &e, const St<float> &B, float rhs,
+                                                  const CoefT<float> &cf, bool &clamped)
+{
+    const Parts2 q = parts2_of(e, B);
+    const float bp = fmaf(cf.k43h, fmaf(-6.0f, B.c, q.S.y), 1.0f);   // beta' = 1 + (4 alpha/3) L_B
+    const float bq = rhs + sigma_corr(q, cf);                        // b'
     float disc = fmaf(bp, bp, cf.k8 * bq);
     if (disc < 0.0f) {
         disc = 0.0f;
@@ -325,7 +346,17 @@ __device__ __forceinline__ float cell_update_corr(const St<float> &e, const St<f
     }
     const float sq = disc > 0.0f ? disc * rsqrtf(disc) : 0.0f;
     const float L = bp >= 0.0f ? __fdividef(2.0f * bq, bp + sq) : (sq - bp) * cf.inv2k23;
-    return (S.x - cf.h2 * L) * (1.0f / 6.0f);
+    return (q.S.x - cf.h2 * L) * (1.0f / 6.0f);
+}
+
+// op(B + e) - op(B) in FP32: L_e + (2 alpha / 3) L_e (2 L_B + L_e) - alpha (2 Sigma(B, e) + Sigma(e))
+__device__ __forceinline__ float cell_op_corr(const St<float> &e, const St<float> &B,
+                                              const CoefT<float> &cf)
+{
+    const Parts2 q = parts2_of(e, B);
+    const float LB = fmaf(-6.0f, B.c, q.S.y) * cf.inv_h2;
+    const float Le = fmaf(-6.0f, e.c, q.S.x) * cf.inv_h2;
+    return Le + cf.k23 * Le * fmaf(2.0f, LB, Le) - sigma_corr(q, cf);
 }
 
 template <typename T>

@@ -135,6 +135,12 @@ cudaError_t launch_force(const double *phi, int d0, int d1, int d2, int ghost, d
                          int periodic, double *grad, cudaStream_t st);
 cudaError_t launch_refine(const double *phic, int nc, const int o[3], const int pn[3], int ghost,
                           double *fine, cudaStream_t st);
+// tricubic variant (4-point Lagrange per axis), periodic source
+cudaError_t launch_refine_cubic(const double *phic, int nc, const int o[3], const int pn[3],
+                                int ghost, double *fine, cudaStream_t st);
+// the same interpolation from a box of dims bd whose interior starts at offset pg (no wrap)
+cudaError_t launch_refine_box(const double *box, const int bd[3], int pg, const int o[3],
+                              const int pn[3], int ghost, double *fine, cudaStream_t st);
 // Dirichlet patch (interior pf, box pf + 2): one full sweep in -> out (out must hold the ghosts).
 // With v0 (coarse patch grids) the ghosts of out are refreshed after each half-sweep by the
 // extrapolated boundary condition of weight w (k_patch.cu).

@@ -361,7 +361,7 @@ int solve_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const 
     RunMix R{h, sh, p, st, err, {}, 0};
     for (int l = 0; l < h->nlev; ++l)
         R.hl[l] = p->h * (double)(1 << l);
-    const int inner = p->inner_cycles > 0 ? p->inner_cycles : 3;
+    const int inner = inner_cycles_for(p);
     if (int rc = phase_setup(h, sh, delta, p, st, err))
         return rc;
     int status = MG5_E_NOT_CONVERGED;
@@ -471,7 +471,7 @@ int capture_mixed(MixedHier *h, const MixedShared &sh, const double *delta, cons
     RunMix R{h, sh, p, st, err, {}, 0};
     for (int l = 0; l < h->nlev; ++l)
         R.hl[l] = p->h * (double)(1 << l);
-    const int inner = p->inner_cycles > 0 ? p->inner_cycles : 3;
+    const int inner = inner_cycles_for(p);
     const long long L0 = launches_total();
     cudaStreamCaptureStatus cs;
     cudaGraph_t graph = nullptr;

@@ -37,6 +37,17 @@ struct MixedShared {
     cudaEvent_t wait_ev = nullptr;   // blocking-sync event for host waits (nullptr: spin on the stream)
 };
 
+// FP32 V-cycles per FP64 defect-correction step: the caller's count, else 4 below
+// a relative tolerance of 1e-7 and 3 above.  Measured at 512^3: a step of 3 cycles
+// reduces the residual ~2e-3, of 4 ~6e-5 (FP32 bounds a step near 3e-5), so 1e-8
+// takes two steps of 4 (8 cycles, 3 FP64 residuals) instead of three of 3 (9, 4).
+inline int inner_cycles_for(const mg5_params *p)
+{
+    if (p->inner_cycles > 0)
+        return p->inner_cycles;
+    return p->tol < 1e-7 ? 4 : 3;
+}
+
 // Wait until st has drained: sleep on `ev` (a blocking-sync event) when given, else spin.
 inline cudaError_t host_wait(cudaStream_t st, cudaEvent_t ev)
 {

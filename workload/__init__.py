@@ -150,3 +150,115 @@ def serving_sizes(rng, count: int):
     """Grid sides for the serving stream: 16 round(10^U(log10 32, log10 256) / 16)."""
     u = rng.uniform(np.log10(32.0), np.log10(256.0), size=count)
     return (16 * np.round(10.0 ** u / 16.0)).astype(int)
+
+
+# ---------------------------------------------------------------------------
+# Nested refinements around one halo (the multi-level truncation workload).
+#
+# The paper's refinement levels follow collapsed haloes (Sec. 4.1, Table 1:
+# truncation at l_d + 1 .. l_d + 4).  Stand-in: a lognormal background (as
+# above, generated at twice the domain resolution and block-averaged, then
+# trilinearly interpolated below that scale) plus one NFW halo (Navarro, Frenk
+# & White profile; M200 from R200 = (3 M / (4 pi 200 rho_crit))^(1/3),
+# concentration c) placed at the densest window of the background.  Every level
+# gets delta as the average over ss^3 sub-points of each cell; one constant
+# (minus the halo's mean over the box) keeps mean(delta) = 0 on the domain.
+# ---------------------------------------------------------------------------
+RHO_CRIT = 2.775e11   # h^2 M_sun / Mpc^3
+
+
+def nfw_delta(r: np.ndarray, m200: float, conc: float, omega_m: float = 0.3) -> np.ndarray:
+    """rho_NFW(r) / rho_bar (Mpc/h, M_sun/h); the cusp is capped at r = r_s / 50, zero beyond R200."""
+    r200 = (3.0 * m200 / (4.0 * np.pi * 200.0 * RHO_CRIT)) ** (1.0 / 3.0)
+    rs = r200 / conc
+    rho_s = (200.0 / 3.0) * RHO_CRIT * conc ** 3 / (np.log1p(conc) - conc / (1.0 + conc))
+    x = np.maximum(r, rs / 50.0) / rs
+    rho = rho_s / (x * (1.0 + x) ** 2)
+    return np.where(r < r200, rho, 0.0) / (omega_m * RHO_CRIT)
+
+
+def _trilinear_periodic(field: np.ndarray, pts: np.ndarray, cell: float) -> np.ndarray:
+    """Periodic trilinear interpolation of a cell-centred cube at points (..., 3)."""
+    n = field.shape[0]
+    u = pts / cell - 0.5
+    i0 = np.floor(u).astype(np.int64)
+    w = u - i0
+    out = np.zeros(pts.shape[:-1])
+    for a in (0, 1):
+        for b in (0, 1):
+            for c in (0, 1):
+                wt = ((w[..., 0] if a else 1 - w[..., 0]) * (w[..., 1] if b else 1 - w[..., 1])
+                      * (w[..., 2] if c else 1 - w[..., 2]))
+                out += wt * field[(i0[..., 0] + a) % n, (i0[..., 1] + b) % n, (i0[..., 2] + c) % n]
+    return out
+
+
+def _cell_average(f, x0: np.ndarray, h: float, dims, ss: int) -> np.ndarray:
+    """Mean of f over ss^3 sub-points of each cell of a box with corner x0, spacing h."""
+    acc = np.zeros(dims)
+    offs = (np.arange(ss) + 0.5) / ss
+    idx = np.stack(np.meshgrid(*[np.arange(d) for d in dims], indexing="ij"), axis=-1)
+    for ox in offs:
+        for oy in offs:
+            for oz in offs:
+                acc += f(x0 + h * (idx + np.array([ox, oy, oz])))
+    return acc / ss ** 3
+
+
+def nested_halo_workload(n_dom: int = 128, box: float = 250.0, levels: int = 4, pn: int = 16,
+                         m200: float = 1e14, conc: float = 5.0, sigma: float = 1.5, seed: int = 2,
+                         ss: int = 2):
+    """Domain delta (n_dom^3, periodic) and `levels` nested refinements around one halo.
+
+    Level l >= 1 is a (2 pn)^3 box at spacing box / n_dom / 2^l covering parent interior
+    cells [o_l, o_l + pn) of level l - 1 (the domain window may wrap), centred on the
+    halo.  Returns (deltas, origins, spacings): deltas[0] the domain, deltas[l] the
+    level-l interior, origins[l] the window of level l in its parent (origins[0] = None).
+    """
+    bg = block_mean(lognormal_delta(2 * n_dom, sigma, seed), 2)
+    h0 = box / n_dom
+    r200 = (3.0 * m200 / (4.0 * np.pi * 200.0 * RHO_CRIT)) ** (1.0 / 3.0)
+    o = densest_window(bg, 8)
+    centre = (np.asarray(o, dtype=np.float64) + 4.0) * h0
+
+    def halo(p):
+        d = ((p - centre + box / 2) % box) - box / 2          # minimum image
+        return nfw_delta(np.linalg.norm(d, axis=-1), m200, conc)
+
+    def halo_on(corner, h, dims, wrap):
+        """Cell averages of the halo on a grid, evaluated only on cells near it."""
+        out = np.zeros(dims)
+        reach = int(np.ceil(r200 / h)) + 2
+        c = np.floor((centre - corner) / h).astype(np.int64)
+        rng = [np.arange(c[a] - reach, c[a] + reach + 1) for a in range(3)]
+        if not wrap:
+            rng = [r[(r >= 0) & (r < dims[a])] for a, r in enumerate(rng)]
+        if any(len(r) == 0 for r in rng):
+            return out
+        sub = _cell_average(halo, corner + h * np.array([r[0] for r in rng]), h,
+                            tuple(len(r) for r in rng), ss)
+        ix = np.ix_(*[r % dims[a] if wrap else r for a, r in enumerate(rng)])
+        out[ix] += sub
+        return out
+
+    halo_dom = halo_on(np.zeros(3), h0, (n_dom,) * 3, True)
+    offset = -halo_dom.mean()
+    deltas, origins, spacings = [np.ascontiguousarray(bg + halo_dom + offset)], [None], [h0]
+    corner, h = np.zeros(3), h0
+    for lev in range(1, levels + 1):
+        # the window of pn parent cells whose centre is nearest the halo centre
+        oc = np.round((centre - corner) / h - pn / 2.0).astype(np.int64)
+        if lev == 1:
+            oc = oc % n_dom
+        else:
+            oc = np.clip(oc, 0, 2 * pn - pn)
+        corner = corner + oc * h
+        h = h / 2.0
+        dims = (2 * pn,) * 3
+        idx = np.stack(np.meshgrid(*[np.arange(2 * pn)] * 3, indexing="ij"), axis=-1)
+        bgf = _trilinear_periodic(bg, (corner + h * (idx + 0.5)) % box, h0)
+        d = bgf + halo_on(corner, h, dims, False) + offset
+        deltas.append(np.ascontiguousarray(d))
+        origins.append(tuple(int(x) for x in oc))
+        spacings.append(h)
+    return deltas, origins, spacings
