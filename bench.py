@@ -68,6 +68,7 @@ WORK = {
 #            (profiles/sweep32_fused_mixed256.md)
 TRAFFIC_PER_CELL = {
     "sweep32": 279.0e6 / 256 ** 3,
+    "sweep64": 84.1e6 / 128 ** 3,          # red + black launch, cold-cache ncu capture at 128^3
 }
 
 

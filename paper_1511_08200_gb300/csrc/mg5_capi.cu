@@ -1008,7 +1008,7 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
         }
         MixedShared sh{ctx->partials, ctx->ls, ctx->cnt, ctx->h_rel, &ctx->prof,
                        ctx->blocking ? ctx->evb : nullptr};
-        status = solve_mixed(mh, sh, d_delta, p, d_phi, info, st, &ctx->err);
+        status = solve_mixed(mh, sh, d_delta, p, d_phi, info, st, &ctx->err, !(flags & MG5_WARM));
     }
     if (status == MG5_E_CUDA || status == MG5_E_ARG || status == MG5_E_OOM)
         return status;

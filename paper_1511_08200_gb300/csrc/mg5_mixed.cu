@@ -32,6 +32,9 @@ int levels_of(int N, int *sz)
 }
 
 // r32 = fp32(f + c - op(phi)) and B = fp32(phi), FP64 arithmetic; partial sums of r.
+// ZERO: phi = 0 (a solve from zero), where op(0) = 0 exactly: r = f + c without the
+// stencil (the same values; a memory-bound pass instead of an FP64-bound one).
+template <bool ZERO>
 __global__ void k_resid64_mixed(const double *__restrict__ phi, const double *__restrict__ f,
                                 const double *__restrict__ cptr, int n, CoefT<double> cf,
                                 float *__restrict__ r32, float *__restrict__ B,
@@ -42,6 +45,14 @@ __global__ void k_resid64_mixed(const double *__restrict__ phi, const double *__
     double2 acc = make_double2(0.0, 0.0);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
+        if constexpr (ZERO) {
+            const double res = f[t] + c;
+            r32[t] = (float)res;
+            B[t] = 0.0f;
+            acc.x += res;
+            acc.y += res * res;
+            continue;
+        }
         const int k = (int)(t % n);
         const long long q = t / n;
         const int j = (int)(q % n), i = (int)(q / n);
@@ -292,7 +303,7 @@ int phase_setup(MixedHier *h, const MixedShared &sh, const double *delta, const 
 
 // r32 = fp32(s delta + c - op(phi)) and B = fp32(phi) in FP64 arithmetic; stats of r
 int phase_residual(MixedHier *h, const MixedShared &sh, const mg5_params *p, double *phi,
-                   cudaStream_t st, std::string *err)
+                   cudaStream_t st, std::string *err, bool zero = false)
 {
     const int N = h->N;
     const long long n3 = (long long)N * N * N;
@@ -301,9 +312,13 @@ int phase_residual(MixedHier *h, const MixedShared &sh, const mg5_params *p, dou
         grid = kMaxPartials;
     {
         ProfScope ps(sh.prof, PK_RESID64_MIXED, st, (double)n3);
-        k_resid64_mixed<<<grid, kBlock, 0, st>>>(phi, h->f64, &sh.ls[0].c, N,
-                                                  make_coef<double>(p->h, p->alpha), h->f[0],
-                                                  h->B[0], sh.partials);
+        const CoefT<double> cf = make_coef<double>(p->h, p->alpha);
+        if (zero)
+            k_resid64_mixed<true><<<grid, kBlock, 0, st>>>(phi, h->f64, &sh.ls[0].c, N, cf,
+                                                           h->f[0], h->B[0], sh.partials);
+        else
+            k_resid64_mixed<false><<<grid, kBlock, 0, st>>>(phi, h->f64, &sh.ls[0].c, N, cf,
+                                                            h->f[0], h->B[0], sh.partials);
     }
     count_launch(1);
     CKM(cudaGetLastError());
@@ -356,7 +371,7 @@ int phase_finish(MixedHier *h, const MixedShared &sh, double *phi, cudaStream_t 
 }  // namespace
 
 int solve_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const mg5_params *p,
-                double *phi, mg5_info *info, cudaStream_t st, std::string *err)
+                double *phi, mg5_info *info, cudaStream_t st, std::string *err, bool zero_start)
 {
     RunMix R{h, sh, p, st, err, {}, 0};
     for (int l = 0; l < h->nlev; ++l)
@@ -368,7 +383,7 @@ int solve_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const 
     double best = INFINITY;
     int outer = 0;
     for (;; ++outer) {
-        if (int rc = phase_residual(h, sh, p, phi, st, err))
+        if (int rc = phase_residual(h, sh, p, phi, st, err, zero_start && outer == 0))
             return rc;
         CKM(cudaMemcpyAsync(sh.h_rel, &sh.ls[0].rel, sizeof(double), cudaMemcpyDeviceToHost, st));
         CKM(host_wait(st, sh.wait_ev));
@@ -488,7 +503,7 @@ int capture_mixed(MixedHier *h, const MixedShared &sh, const double *delta, cons
     CKM(cudaMemsetAsync(phi, 0, n3 * sizeof(double), st));
     if (int rc = phase_setup(h, sh, delta, p, st, err))
         return rc;
-    if (int rc = phase_residual(h, sh, p, phi, st, err))
+    if (int rc = phase_residual(h, sh, p, phi, st, err, true))   // phi was zeroed above
         return rc;
     k_mixed_check<<<1, 1, 0, st>>>(sh.ls, ctl, hnd);
     CKM(cudaGetLastError());

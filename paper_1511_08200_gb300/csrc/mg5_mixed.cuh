@@ -81,8 +81,9 @@ size_t mixed_bytes(int N);
 int alloc_mixed(int N, size_t budget, size_t *held, MixedHier **out, std::string *err);
 void free_mixed(MixedHier *m, size_t *held);
 // phi: device FP64 N^3 initial guess in, mean-zero solution out.
+// zero_start: phi holds zeros (not a warm start), so the first residual skips the stencil
 int solve_mixed(MixedHier *m, const MixedShared &sh, const double *delta, const mg5_params *p,
-                double *phi, mg5_info *info, cudaStream_t st, std::string *err);
+                double *phi, mg5_info *info, cudaStream_t st, std::string *err, bool zero_start);
 // Record, into the graph being captured on `st`, a whole mixed solve (phi
 // zero start) with its defect-correction loop as a WHILE node whose body is
 // captured on `st_body`; then gauge and (if grad) the force.  The loop state
