@@ -193,9 +193,13 @@ class Step:
         self.pmix = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE, tol=TOLMIX,
                                       precision="mixed")
         self.ppatch = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE / 2, tol=TOL64)
+        self.graph = True
         torch.cuda.synchronize()
 
     def profile(self, on):
+        # events around each launch cannot sit inside a graph: the profiled pass runs the same
+        # kernels host-driven, the timed pass replays the captured FP64 solve
+        self.graph = not on
         self.ctx.profile_enable(on)
         self.ctx2.profile_enable(on)
 
@@ -226,7 +230,7 @@ class Step:
             th.start()
             if host_io is None:
                 _, _, i64 = ctx.solve_fifth_force(self.d_c, self.p64, phi=self.phi, grad=self.grad,
-                                                  stream=s1, fmg=True)
+                                                  stream=s1, fmg=True, graph=self.graph)
             else:
                 _, _, i64 = ctx.solve_fifth_force_host(host_io["delta"], self.p64,
                                                        phi=host_io["phi"], grad=host_io["grad"],

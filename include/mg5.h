@@ -65,11 +65,14 @@ extern "C" {
 #define MG5_HOST_IO  2u   /* delta, phi, grad are HOST pointers; the library copies them */
 #define MG5_FMG      4u   /* MG5_FP64 from zero: full-multigrid start (rhs restricted down, coarsest
                              solved, one V-cycle per finer grid on the interpolated solution) */
-#define MG5_GRAPH    8u   /* MG5_MIXED from zero as ONE CUDA-graph launch: the context captures, per
-                             (N, parameters, grad or not), the whole solve with its defect-correction
-                             loop as a device-controlled WHILE node, with its own hierarchy and
-                             staging buffers, and replays it (copy in, launch, copy out, one sync).
-                             Not with MG5_WARM or MG5_HOST_IO. */
+#define MG5_GRAPH    8u   /* A solve from zero as ONE CUDA-graph launch: the context captures, per
+                             (N, parameters, grad or not, MG5_FMG or not), the whole solve with its
+                             loop (MG5_MIXED: the defect correction; MG5_FP64: the V-cycle) as a
+                             device-controlled WHILE node, with its own hierarchy and staging
+                             buffers, and replays it (copy in, launch, copy out, one sync): the same
+                             kernels as the host-driven solve, without a host round trip per cycle.
+                             Not with MG5_WARM or MG5_HOST_IO; MG5_FP64 needs nu1 + nu2 even and
+                             N with two grids or more (MG5_E_ARG otherwise). */
 
 typedef struct mg5_ctx mg5_ctx;  /* opaque; owns the device hierarchy, resident between calls */
 

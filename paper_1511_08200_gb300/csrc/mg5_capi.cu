@@ -139,8 +139,10 @@ struct GraphEntry {
     int N = 0;
     mg5_params prm{};
     bool grad = false;
+    bool fmg = false;              // FP64 form: full-multigrid start
     bool busy = false;
-    MixedHier *hier = nullptr;
+    MixedHier *hier = nullptr;     // MG5_MIXED
+    Hier *hier64 = nullptr;        // MG5_FP64
     double2 *partials = nullptr;
     LevelScal *ls = nullptr;
     SolveCounters *cnt = nullptr;
@@ -188,7 +190,7 @@ struct mg5_ctx {
 extern "C" {  // defined further down, inside the ABI block
 static bool same_params(const mg5_params &a, const mg5_params &b);
 static int solve_graph(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p, double *phi,
-                       double *grad, mg5_info *info, cudaStream_t st);
+                       double *grad, bool fmg, mg5_info *info, cudaStream_t st);
 }
 
 #define CK(call)                                                                           \
@@ -268,6 +270,45 @@ static void free_hier(mg5_ctx *ctx, Hier *h)
         ctx_free(ctx, h->v0[l], b);
     }
     delete h;
+}
+
+// An FP64 hierarchy owned by a captured graph (plain allocations, counted by the entry).
+static void free_hier_raw(Hier *h)
+{
+    if (!h)
+        return;
+    for (void *q : {(void *)h->tmp[0], (void *)h->f[0]})
+        if (q)
+            cudaFree(q);
+    for (int l = 1; l < h->nlev; ++l)
+        for (void *q : {(void *)h->v[l], (void *)h->tmp[l], (void *)h->f[l], (void *)h->v0[l]})
+            if (q)
+                cudaFree(q);
+    delete h;
+}
+
+static cudaError_t alloc_hier_raw(int N, Hier **out)
+{
+    Hier *h = new Hier();
+    h->N = N;
+    h->nlev = num_levels(N, h->n);
+    const size_t n3 = (size_t)N * N * N * sizeof(double);
+    cudaError_t e = cudaMalloc((void **)&h->tmp[0], n3);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&h->f[0], n3);
+    for (int l = 1; l < h->nlev && e == cudaSuccess; ++l) {
+        const size_t b = (size_t)h->n[l] * h->n[l] * h->n[l] * sizeof(double);
+        for (double **q : {&h->v[l], &h->tmp[l], &h->f[l], &h->v0[l]})
+            if (e == cudaSuccess)
+                e = cudaMalloc((void **)q, b);
+    }
+    if (e != cudaSuccess) {
+        free_hier_raw(h);
+        return e;
+    }
+    h->bytes = fp64_bytes(N);
+    *out = h;
+    return cudaSuccess;
 }
 
 static int get_hier(mg5_ctx *ctx, int N, Hier **out)
@@ -381,6 +422,13 @@ static void free_batch(mg5_ctx *ctx)
     ctx->batch = nullptr;
 }
 
+static size_t graph_entry_bytes64(int N, bool grad)
+{
+    const size_t n3 = (size_t)N * N * N;
+    return fp64_bytes(N) + n3 * sizeof(double) * (grad ? 5 : 2) + sizeof(double2) * kMaxPartials +
+           sizeof(LevelScal) * kScalSlots + sizeof(SolveCounters) + sizeof(BoxCtl);
+}
+
 static size_t graph_entry_bytes(int N, bool grad)
 {
     const size_t n3 = (size_t)N * N * N;
@@ -431,10 +479,21 @@ struct Run64 {
     cudaStream_t st;
     double hl[kMaxLevels];  // cell size per level
     long long cu = 0;       // cell updates of the non-coarsest sweeps
+    // device scratch: the context's, or a captured graph's own
+    LevelScal *lsb = nullptr;
+    SolveCounters *cntb = nullptr;
+    double2 *partb = nullptr;
 
-    LevelScal *ls(int l) { return ctx->ls + l; }
-    double *c(int l) { return &ctx->ls[l].c; }
-    double *m(int l) { return &ctx->ls[l].m; }
+    void bind_ctx_scratch()
+    {
+        lsb = ctx->ls;
+        cntb = ctx->cnt;
+        partb = ctx->partials;
+    }
+    bool bound() const { return lsb && cntb && partb; }
+    LevelScal *ls(int l) { return lsb + l; }
+    double *c(int l) { return &lsb[l].c; }
+    double *m(int l) { return &lsb[l].m; }
 
     int sweep(int l)
     {
@@ -442,7 +501,7 @@ struct Run64 {
         ProfScope ps(&ctx->prof, l == 0 ? PK_SWEEP64 : PK_SWEEP64C, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
         cudaError_t e = launch_sweep_sched<double>(sweep_schedule(ctx->device, MG5_FP64, h->n[l]),
                                                    h->v[l], h->tmp[l], h->f[l], c(l), h->n[l], cf,
-                                                   &ctx->cnt->clamped, st);
+                                                   &cntb->clamped, st);
         if (e != cudaSuccess) {
             ctx->err = std::string("sweep: ") + cudaGetErrorString(e);
             return MG5_E_CUDA;
@@ -461,10 +520,10 @@ struct Run64 {
         {
             ProfScope ps(&ctx->prof, PK_RESTRICT64, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
             CK(launch_resid_restrict<double>(h->v[l], h->f[l], c(l), h->n[l], cf, h->v[l + 1],
-                                             h->v0[l + 1], h->f[l + 1], ctx->partials, &nb, st));
+                                             h->v0[l + 1], h->f[l + 1], partb, &nb, st));
         }
         const double n3 = (double)h->n[l] * h->n[l] * h->n[l];
-        CK(launch_finalize(ctx->partials, nb, n3, ls(l), FIN_RESID, st));
+        CK(launch_finalize(partb, nb, n3, ls(l), FIN_RESID, st));
         return MG5_OK;
     }
 
@@ -473,10 +532,10 @@ struct Run64 {
         const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
         int nb = 0;
         mg5_ctx *ctx = this->ctx;
-        CK(launch_residual<double>(h->v[l], h->f[l], c(l), h->n[l], cf, nullptr, ctx->partials,
+        CK(launch_residual<double>(h->v[l], h->f[l], c(l), h->n[l], cf, nullptr, partb,
                                    &nb, st));
         const double n3 = (double)h->n[l] * h->n[l] * h->n[l];
-        CK(launch_finalize(ctx->partials, nb, n3, ls(l), FIN_RESID, st));
+        CK(launch_finalize(partb, nb, n3, ls(l), FIN_RESID, st));
         return MG5_OK;
     }
 
@@ -486,7 +545,7 @@ struct Run64 {
         mg5_ctx *ctx = this->ctx;
         ProfScope ps(&ctx->prof, PK_COARSEST64, st);
         CK(launch_coarsest<double>(h->v[l], h->tmp[l], h->f[l], h->n[l], cf, c(l), p->nu_coarse,
-                                   kCoarseRtol, &ctx->cnt->clamped, &ctx->cnt->coarse_sweeps, st));
+                                   kCoarseRtol, &cntb->clamped, &cntb->coarse_sweeps, st));
         return MG5_OK;
     }
 
@@ -565,6 +624,11 @@ static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p
     Hier *h = nullptr;
     RET(get_hier(ctx, N, &h));
     Run64 R{ctx, h, p, st, {}, 0};
+    R.bind_ctx_scratch();
+    if (!R.bound()) {
+        ctx->err = "solve64: context scratch not allocated";
+        return MG5_E_ARG;
+    }
     for (int l = 0; l < h->nlev; ++l)
         R.hl[l] = p->h * (double)(1 << l);
     const long long n3 = (long long)N * N * N;
@@ -888,7 +952,8 @@ int mg5_graph_cached_bytes(mg5_ctx *ctx, int N, const mg5_params *p, int with_gr
     if (!ctx || !p || !extra)
         return MG5_E_ARG;
     RET(check_size(N));
-    *extra = graph_entry_bytes(N, with_grad != 0);
+    *extra = p->precision == MG5_FP64 ? graph_entry_bytes64(N, with_grad != 0)
+                                       : graph_entry_bytes(N, with_grad != 0);
     for (GraphEntry *g : ctx->graphs)
         if (!g->busy && g->N == N && g->grad == (with_grad != 0) && same_params(g->prm, *p))
             *extra = 0;
@@ -952,8 +1017,15 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
     RET(check_params(p));
     if (flags & ~(MG5_WARM | MG5_HOST_IO | MG5_FMG | MG5_GRAPH))
         return MG5_E_ARG;
-    if ((flags & MG5_GRAPH) && (p->precision != MG5_MIXED || (flags & (MG5_WARM | MG5_HOST_IO))))
+    if ((flags & MG5_GRAPH) && (flags & (MG5_WARM | MG5_HOST_IO)))
         return MG5_E_ARG;
+    if ((flags & MG5_GRAPH) && p->precision == MG5_FP64) {
+        int sz[kMaxLevels];
+        if (num_levels(N, sz) < 2 || (p->nu1 + p->nu2) % 2) {
+            ctx->err = "MG5_GRAPH with MG5_FP64 needs two grids or more and nu1 + nu2 even";
+            return MG5_E_ARG;
+        }
+    }
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     if (info)
@@ -979,7 +1051,7 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
         CK(cudaMemsetAsync(d_phi, 0, fb, st));
     int status;
     if (flags & MG5_GRAPH) {
-        status = solve_graph(ctx, d_delta, N, p, d_phi, d_grad, info, st);
+        status = solve_graph(ctx, d_delta, N, p, d_phi, d_grad, (flags & MG5_FMG) != 0, info, st);
         if (status == MG5_E_CUDA || status == MG5_E_ARG || status == MG5_E_OOM)
             return status;
         CK(cudaEventRecord(ctx->ev1, st));
@@ -1389,6 +1461,7 @@ void graph_free(GraphEntry *g)
     size_t hb = 0;
     if (g->hier)
         free_mixed(g->hier, &hb);
+    free_hier_raw(g->hier64);
     for (void *p : {(void *)g->partials, (void *)g->ls, (void *)g->cnt, (void *)g->ctl,
                     (void *)g->delta, (void *)g->phi, (void *)g->gout})
         if (p)
@@ -1510,10 +1583,10 @@ int graph_finish(GraphEntry *g, mg5_info *info)
     int status = ctl.status;
     if (info) {
         info->status = status;
-        info->outer_iters = ctl.outer;
+        info->outer_iters = g->hier ? ctl.outer : 0;
         info->cycles = ctl.outer * g->stats.inner;
-        info->levels = g->hier->nlev;
-        info->coarsest_n = g->hier->n[info->levels - 1];
+        info->levels = g->hier ? g->hier->nlev : g->hier64->nlev;
+        info->coarsest_n = g->hier ? g->hier->n[info->levels - 1] : g->hier64->n[info->levels - 1];
         info->n_history = ctl.nhist;
         for (int k = 0; k < ctl.nhist && k < 64; ++k)
             info->history[k] = ctl.hist[k];
@@ -1521,8 +1594,8 @@ int graph_finish(GraphEntry *g, mg5_info *info)
         info->compat_c = g->rb->ls0.c;
         info->phi_mean_removed = g->rb->ls0.mean;
         const long long nc = info->coarsest_n;
-        info->cell_updates =
-            g->stats.cells_per_iter * ctl.outer + (long long)cnt.coarse_sweeps * nc * nc * nc;
+        info->cell_updates = g->stats.cells_fixed + g->stats.cells_per_iter * ctl.outer +
+                             (long long)cnt.coarse_sweeps * nc * nc * nc;
         info->coarse_sweeps = cnt.coarse_sweeps;
         info->disc_clamped = (long long)cnt.clamped;
     }
@@ -1536,13 +1609,200 @@ int graph_finish(GraphEntry *g, mg5_info *info)
 
 extern "C" {
 
+// The FP64 solve from zero as one graph: f = s delta and ||f||, optional full-multigrid start,
+// the first pre-smoothing and residual check, then the V-cycle as a WHILE node whose body is
+// the coarse-grid correction, the post- and the next pre-smoothing and the check; the gauge and
+// the force after it.  The body swaps every grid's buffers an even number of times (nu1 + nu2
+// even), so the pointers it was captured with hold on every pass.
+static int capture_fp64(mg5_ctx *ctx, GraphEntry *g, const mg5_params *p, cudaStream_t st,
+                        cudaStream_t body_st)
+{
+    Hier *h = g->hier64;
+    const int N = h->N;
+    const long long n3 = (long long)N * N * N;
+    Run64 R{ctx, h, p, st, {}, 0};
+    R.lsb = g->ls;
+    R.cntb = g->cnt;
+    R.partb = g->partials;
+    if (!R.bound() || !g->ctl || !g->phi || !g->delta) {
+        ctx->err = "capture_fp64: entry scratch not allocated";
+        return MG5_E_ARG;
+    }
+    for (int l = 0; l < h->nlev; ++l)
+        R.hl[l] = p->h * (double)(1 << l);
+    const long long L0 = launches_total();
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) {
+        ctx->err = "capture_fp64: stream is not capturing";
+        return MG5_E_ARG;
+    }
+    cudaGraphConditionalHandle hnd;
+    CK(cudaGraphConditionalHandleCreate(&hnd, graph, 0, cudaGraphCondAssignDefault));
+    CK(launch_ctl_init(g->ctl, p->tol, p->max_cycles, st));
+    CK(cudaMemsetAsync(g->ls, 0, sizeof(LevelScal) * kScalSlots, st));
+    CK(cudaMemsetAsync(g->cnt, 0, sizeof(SolveCounters), st));
+    int nb = 0;
+    CK(launch_scale(g->delta, p->s, h->f[0], n3, g->partials, &nb, st));
+    CK(launch_finalize(g->partials, nb, (double)n3, g->ls, FIN_FNORM, st));
+    CK(cudaMemsetAsync(g->phi, 0, n3 * sizeof(double), st));
+    h->v[0] = g->phi;
+    if (g->fmg)
+        RET(R.fmg());
+    for (int k = 0; k < p->nu1; ++k)
+        RET(R.sweep(0));
+    RET(R.resid_restrict(0));
+    CK(launch_loop_check(g->ls, g->ctl, hnd, st));
+    const long long cells_fixed = R.cu;
+    // the WHILE node after everything captured so far
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    const long long L1 = launches_total();
+    CK(cudaStreamBeginCaptureToGraph(body_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    double *const v0_start = h->v[0];
+    Run64 B = R;
+    B.st = body_st;
+    B.cu = 0;
+    int rc = B.coarse_visit(1);
+    if (rc == MG5_OK) {
+        const cudaError_t e = launch_prolong_add<double>(h->v[1], h->v0[1], h->n[1], h->v[0], B.c(0),
+                                                         B.c(1), body_st);
+        rc = e == cudaSuccess ? MG5_OK : MG5_E_CUDA;
+    }
+    for (int k = 0; k < p->nu2 && rc == MG5_OK; ++k)
+        rc = B.sweep(0);
+    for (int k = 0; k < p->nu1 && rc == MG5_OK; ++k)
+        rc = B.sweep(0);
+    if (rc == MG5_OK)
+        rc = B.resid_restrict(0);
+    if (rc == MG5_OK && launch_loop_check(g->ls, g->ctl, hnd, body_st) != cudaSuccess)
+        rc = MG5_E_CUDA;
+    cudaGraph_t g_out = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(body_st, &g_out);
+    RET(rc);
+    CK(e_end);
+    if (h->v[0] != v0_start) {
+        ctx->err = "capture_fp64: the loop body does not return the grids to their buffers";
+        return MG5_E_ARG;
+    }
+    const long long L2 = launches_total();
+    // the iterate is in h->v[0]: bring it to the entry's phi, then the gauge and the force
+    if (h->v[0] != g->phi)
+        CK(cudaMemcpyAsync(g->phi, h->v[0], n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(launch_sum(g->phi, n3, g->partials, &nb, st));
+    CK(launch_finalize(g->partials, nb, (double)n3, g->ls, FIN_MEAN, st));
+    CK(launch_sub_mean(g->phi, n3, &g->ls[0].mean, st));
+    if (g->gout)
+        CK(launch_force(g->phi, N, N, N, 0, p->h, 1, g->gout, st));
+    g->stats.launches_fixed = (L1 - L0) + (launches_total() - L2);
+    g->stats.launches_per_iter = L2 - L1;
+    g->stats.cells_per_iter = B.cu;
+    g->stats.cells_fixed = cells_fixed;
+    g->stats.inner = 1;
+    return MG5_OK;
+}
+
+// Build an FP64 entry: its own hierarchy, scalars and staging, the capture, the instantiation.
+static int graph_build64(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, bool fmg,
+                         GraphEntry **out)
+{
+    *out = nullptr;
+    GraphEntry *g = new GraphEntry();
+    g->N = N;
+    g->prm = *p;
+    g->grad = grad;
+    g->fmg = fmg;
+    const size_t n3 = (size_t)N * N * N;
+    cudaError_t e = alloc_hier_raw(N, &g->hier64);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->partials, sizeof(double2) * kMaxPartials);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->ls, sizeof(LevelScal) * kScalSlots);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->cnt, sizeof(SolveCounters));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->ctl, sizeof(BoxCtl));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->delta, n3 * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&g->phi, n3 * sizeof(double));
+    if (e == cudaSuccess && grad)
+        e = cudaMalloc((void **)&g->gout, 3 * n3 * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&g->rb, sizeof(GraphReadback));
+    g->bytes = graph_entry_bytes64(N, grad);
+    cudaStream_t origin = nullptr, body = nullptr;
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking);
+    int rc = e == cudaSuccess ? MG5_OK : (e == cudaErrorMemoryAllocation ? MG5_E_OOM : MG5_E_CUDA);
+    if (rc != MG5_OK)
+        ctx->err = std::string("graph solve: ") + cudaGetErrorString(e);
+    const long long l0 = launches_total();
+    const bool prof_on = ctx->prof.on;
+    if (rc == MG5_OK) {
+        ctx->prof.on = false;
+        e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = capture_fp64(ctx, g, p, origin, body);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(origin, &graph);
+            if (rc == MG5_OK && e2 == cudaSuccess) {
+                g->graph = graph;
+                e = cudaGraphInstantiate(&g->exec, graph, 0);
+            } else {
+                if (graph)
+                    cudaGraphDestroy(graph);
+                if (e2 != cudaSuccess)
+                    e = e2;
+            }
+        }
+        ctx->prof.on = prof_on;
+        count_launch(l0 - launches_total());   // captured, not enqueued
+        if (rc == MG5_OK && e != cudaSuccess) {
+            ctx->err = std::string("graph solve: ") + cudaGetErrorString(e);
+            rc = MG5_E_CUDA;
+        }
+    }
+    if (origin)
+        cudaStreamDestroy(origin);
+    if (body)
+        cudaStreamDestroy(body);
+    cudaGetLastError();
+    if (rc != MG5_OK) {
+        graph_free(g);
+        return rc;
+    }
+    *out = g;
+    return MG5_OK;
+}
+
 // The cached graph for (N, params, grad), or a new capture (evicting the least
 // recently used entries while the cache is full or the budget would be exceeded).
-static int get_graph_entry(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, GraphEntry **out)
+static int get_graph_entry(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, bool fmg,
+                           GraphEntry **out)
 {
-    if ((*out = graph_checkout(ctx, N, p, grad)))
-        return MG5_OK;
-    const size_t need = graph_entry_bytes(N, grad);
+    for (GraphEntry *g : ctx->graphs)
+        if (!g->busy && g->N == N && g->grad == grad && g->fmg == fmg && same_params(g->prm, *p)) {
+            g->busy = true;
+            g->last_use = ++ctx->graph_clock;
+            *out = g;
+            return MG5_OK;
+        }
+    const bool fp64 = p->precision == MG5_FP64;
+    const size_t need = fp64 ? graph_entry_bytes64(N, grad) : graph_entry_bytes(N, grad);
     while (ctx->graphs.size() >= kGraphCacheMax || (ctx->budget && ctx->held + need > ctx->budget)) {
         GraphEntry *v = graph_take_idle(ctx);   // every entry is idle: this context's solves have synchronised
         if (!v)
@@ -1553,11 +1813,16 @@ static int get_graph_entry(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, 
         ctx->err = "graph solve would exceed the context's HBM budget";
         return MG5_E_OOM;
     }
-    const bool prof_on = ctx->prof.on;
-    ctx->prof.on = false;
     GraphEntry *g = nullptr;
-    const int rc = graph_build(ctx->device, N, p, grad, &g, &ctx->err);
-    ctx->prof.on = prof_on;
+    int rc;
+    if (fp64) {
+        rc = graph_build64(ctx, N, p, grad, fmg, &g);
+    } else {
+        const bool prof_on = ctx->prof.on;
+        ctx->prof.on = false;
+        rc = graph_build(ctx->device, N, p, grad, &g, &ctx->err);
+        ctx->prof.on = prof_on;
+    }
     RET(rc);
     graph_insert(ctx, g);
     *out = g;
@@ -1566,10 +1831,10 @@ static int get_graph_entry(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, 
 
 // MG5_MIXED from zero through the cached graph: copy in, one graph launch, copy out.
 static int solve_graph(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p, double *phi,
-                       double *grad, mg5_info *info, cudaStream_t st)
+                       double *grad, bool fmg, mg5_info *info, cudaStream_t st)
 {
     GraphEntry *g = nullptr;
-    RET(get_graph_entry(ctx, N, p, grad != nullptr, &g));
+    RET(get_graph_entry(ctx, N, p, grad != nullptr, fmg, &g));
     int rc = graph_enqueue(g, delta, phi, grad, st, &ctx->err);
     if (rc == MG5_OK && ctx_wait(ctx, st) != cudaSuccess) {
         ctx->err = std::string("graph solve: ") + cudaGetErrorString(cudaGetLastError());

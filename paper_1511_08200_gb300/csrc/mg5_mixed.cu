@@ -479,6 +479,21 @@ __global__ void k_ctl_init(BoxCtl *ctl, double tol, int max_outer)
     ctl->rel = 0.0;
 }
 
+cudaError_t launch_ctl_init(BoxCtl *ctl, double tol, int max_outer, cudaStream_t st)
+{
+    k_ctl_init<<<1, 1, 0, st>>>(ctl, tol, max_outer);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_check(const LevelScal *ls0, BoxCtl *ctl, cudaGraphConditionalHandle hnd,
+                              cudaStream_t st)
+{
+    k_mixed_check<<<1, 1, 0, st>>>(ls0, ctl, hnd);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
 int capture_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const mg5_params *p,
                   double *phi, double *grad, BoxCtl *ctl, cudaStream_t st, cudaStream_t st_body,
                   CaptureStats *stats, std::string *err)
@@ -549,6 +564,7 @@ int capture_mixed(MixedHier *h, const MixedShared &sh, const double *delta, cons
     stats->launches_per_iter = L2 - L1;
     stats->cells_per_iter = B.cu;
     stats->inner = inner;
+    stats->cells_fixed = 0;
     return MG5_OK;
 }
 

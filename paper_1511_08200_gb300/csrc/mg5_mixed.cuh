@@ -75,7 +75,15 @@ struct CaptureStats {
     long long launches_per_iter;  // kernels of one loop body
     long long cells_per_iter;     // cell updates of one loop body (coarsest grids excluded)
     int inner;
+    long long cells_fixed;        // cell updates outside the loop (FP64 form: start and first smoothing)
 };
+
+// The graph form's loop control (mg5_mixed.cu): reset the control block; after each
+// finest-grid residual record it and set the WHILE condition by the host loop's rules
+// (stop at rel <= tol, on a non-finite or diverging residual, or after max_outer checks).
+cudaError_t launch_ctl_init(BoxCtl *ctl, double tol, int max_outer, cudaStream_t st);
+cudaError_t launch_loop_check(const LevelScal *ls0, BoxCtl *ctl, cudaGraphConditionalHandle hnd,
+                              cudaStream_t st);
 
 size_t mixed_bytes(int N);
 int alloc_mixed(int N, size_t budget, size_t *held, MixedHier **out, std::string *err);

@@ -360,5 +360,30 @@ def test_graph_solve_equals_host_driven(ctx):
     phi2, _, _ = ctx.solve_fifth_force(d2, p, graph=True,
                                        grad=torch.empty((3,) + d2.shape, dtype=torch.float64, device="cuda"))
     assert torch.equal(phi2, ref2)
-    with pytest.raises(mg.MG5Error):
-        ctx.solve_fifth_force(d2, mg.default_params(alpha=alpha, s=s, h=h), graph=True)   # FP64: not allowed
+    with pytest.raises(mg.MG5Error):   # FP64 needs nu1 + nu2 even (the loop body's buffer swaps)
+        ctx.solve_fifth_force(d2, mg.default_params(alpha=alpha, s=s, h=h, nu1=1), graph=True)
+
+
+@pytest.mark.parametrize("n,fmg", [(32, False), (64, True), (128, True)])
+def test_fp64_graph_solve_equals_host_driven(ctx, n, fmg):
+    """The FP64 solve captured with its V-cycle loop as a WHILE node runs the same kernels as
+    the host-driven solve: bit-identical phi and force, cycles and cell updates, on the
+    capture and on a cache hit, and it matches the oracle."""
+    import torch
+    mg = _mg()
+    alpha, s, h = nominal()
+    delta = workload.lognormal_delta(n, 1.5, 31)
+    d = dev(delta)
+    p = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-10)
+    g0 = torch.empty((3,) + d.shape, dtype=torch.float64, device="cuda")
+    ref, gref, iref = ctx.solve_fifth_force(d, p, grad=g0, fmg=fmg)
+    for _ in range(2):
+        g1 = torch.empty_like(g0)
+        phi, g, info = ctx.solve_fifth_force(d, p, graph=True, fmg=fmg, grad=g1)
+        assert torch.equal(phi, ref) and torch.equal(g, gref)
+        assert (info.cycles, info.cell_updates, info.coarse_sweeps) == \
+            (iref.cycles, iref.cell_updates, iref.coarse_sweeps)
+        assert info.rel_residual == iref.rel_residual and info.status == 0
+    if n <= 64:
+        oref, _ = oracle.solve(delta, alpha, s, h, tol=1e-12)
+        assert rel_l2(host(phi), oref) <= 1e-9
