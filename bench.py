@@ -242,7 +242,8 @@ class Step:
             ctx.force(self.box, H_COARSE / 2, ghost=1, periodic=False, grad=self.g_tr, stream=s1)
             ev[2].record(s1)
             self.box_full.copy_(self.box)
-            _, ip = ctx.relax_patch(self.d_p, self.ppatch, i64.compat_c, self.box_full, stream=s1)
+            _, ip = ctx.relax_patch(self.d_p, self.ppatch, i64.compat_c, self.box_full, stream=s1,
+                                    graph=self.graph)
             ctx.force(self.box_full, H_COARSE / 2, ghost=1, periodic=False, grad=self.g_full,
                       stream=s1)
             ev[3].record(s1)

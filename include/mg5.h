@@ -258,6 +258,14 @@ int mg5_refine_interpolate_box(mg5_ctx *ctx, const double *box, const int bd[3],
 int mg5_relax_patch(mg5_ctx *ctx, const double *delta_fine, const int pf[3],
                     const mg5_params *p, double compat_c, double *phi_fine,
                     mg5_info *info, void *stream);
+/* mg5_relax_patch as ONE CUDA-graph launch: the context captures, per (pf, parameters), the
+ * whole relaxation with its V-cycle loop as a device-controlled WHILE node (own hierarchy and
+ * staging; compat_c is passed to the device on each call) and replays it: copy in, launch, copy
+ * out, one synchronisation.  The same kernels as mg5_relax_patch, bit-identical results.  Needs
+ * a patch hierarchy of two grids or more and nu1 + nu2 even (MG5_E_ARG otherwise). */
+int mg5_relax_patch_graph(mg5_ctx *ctx, const double *delta_fine, const int pf[3],
+                          const mg5_params *p, double compat_c, double *phi_fine,
+                          mg5_info *info, void *stream);
 
 /*
  * Solve many independent boxes in one call (batching).  Box i has side N[i],

@@ -113,6 +113,7 @@ _sigs = {
     "mg5_refine_interpolate_cubic": ([_P, _P, _c_int, _I3, _I3, _c_int, _P, _P], _c_int),
     "mg5_refine_interpolate_box": ([_P, _P, _I3, _c_int, _I3, _I3, _c_int, _P, _P], _c_int),
     "mg5_relax_patch": ([_P, _P, _I3, _P, _c_double, _P, _P, _P], _c_int),
+    "mg5_relax_patch_graph": ([_P, _P, _I3, _P, _c_double, _P, _P, _P], _c_int),
     "mg5_solve_batch": ([_P, _c_int, _P, _P, _P, _P, _P, _P, _P], _c_int),
     "mg5_cached_bytes": ([_P, _c_int, _c_int, _P], _c_int),
     "mg5_graph_cached_bytes": ([_P, _c_int, _P, _c_int, _P], _c_int),
@@ -441,12 +442,14 @@ class Context:
         return out
 
     def relax_patch(self, delta_fine, params: Params, compat_c: float, phi_box, stream=None,
-                    raise_on_status=True):
-        """mg5_relax_patch: phi_box ((pf + 2)^3, ghosts fixed) is relaxed in place."""
+                    raise_on_status=True, graph=False):
+        """mg5_relax_patch (graph=True: mg5_relax_patch_graph): phi_box ((pf + 2)^3, ghosts
+        fixed) is relaxed in place."""
         pf = [int(x) for x in delta_fine.shape]
         info = _Info()
-        rc = _lib.mg5_relax_patch(self._h, _ptr(delta_fine), _I3(*pf), ctypes.byref(params),
-                                  compat_c, _ptr(phi_box), ctypes.byref(info), _stream(stream))
+        fn = _lib.mg5_relax_patch_graph if graph else _lib.mg5_relax_patch
+        rc = fn(self._h, _ptr(delta_fine), _I3(*pf), ctypes.byref(params),
+                compat_c, _ptr(phi_box), ctypes.byref(info), _stream(stream))
         if raise_on_status:
             self._check(rc, (OK, W_DISC_CLAMP))
         return phi_box, Info._from(info)

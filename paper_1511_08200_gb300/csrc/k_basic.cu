@@ -381,7 +381,7 @@ cudaError_t launch_prolong_add(const T *vc, const T *v0c, int nc, T *vf, double 
 // nu_max sweeps.  Sweeps ping-pong A -> B (red) -> A (black) with barriers.
 // Grids up to kCoarsestSmemCells cells run entirely in shared memory.
 // --------------------------------------------------------------------------
-constexpr int kCoarsestThreads = 1024;
+constexpr int kCoarsestThreads = 512;   // 128 registers a thread: stencil offsets stay in registers
 constexpr int kCoarsestSmemCells = 1024;   // 4 arrays x 1024 x 8 B = 32 KB
 
 template <typename T, bool BASE>
@@ -415,6 +415,68 @@ __global__ void __launch_bounds__(kCoarsestThreads)
     double r0 = -1.0, c = 0.0;
     int it = 0;
     unsigned long long my_clamps = 0;
+    if (in_smem && n3 <= (int)blockDim.x) {
+        // one cell per thread: its stencil offsets, colour and f once, then only the
+        // arithmetic and the barriers per iteration (the same values as the loop below)
+        const int p = threadIdx.x;
+        const bool mine = p < n3;
+        Nbr nb{};
+        int colour_me = 0;
+        T fme = (T)0;
+        if (mine) {
+            const int k = p % n, j = (p / n) % n, i = p / (n * n);
+            const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
+            nb = nbr_of(periodic_rows(n, i, j), k, kp, km);
+            colour_me = (i + j + k) & 1;
+            fme = ff[p];
+        }
+        for (; it < nu_max; ++it) {
+            double2 acc = make_double2(0.0, 0.0);
+            if (mine) {
+                St<T> s, sb;
+                gather_nbr((const T *)a, nb, s);
+                if constexpr (BASE)
+                    gather_nbr(bs, nb, sb);
+                const double res = (double)(fme - opr<T, BASE>(s, sb, cf));
+                acc.x = res;
+                acc.y = res * res;
+            }
+            acc = block_sum2(acc);
+            if (threadIdx.x == 0) {
+                bc_s[0] = acc.x;
+                bc_s[1] = acc.y;
+            }
+            __syncthreads();
+            const double m = bc_s[0] * inv_n3;
+            const double q2 = bc_s[1] - (double)n3 * m * m;
+            const double rn = sqrt(q2 > 0.0 ? q2 : 0.0);
+            __syncthreads();
+            c = -m;
+            if (r0 < 0.0)
+                r0 = rn;
+            if (rn <= rtol * r0)
+                break;
+            for (int colour = 0; colour < 2; ++colour) {
+                const T *src = colour == 0 ? a : b;
+                T *dst = colour == 0 ? b : a;
+                if (mine) {
+                    if (colour_me != colour) {
+                        dst[p] = src[p];
+                    } else {
+                        St<T> s, sb;
+                        gather_nbr(src, nb, s);
+                        if constexpr (BASE)
+                            gather_nbr(bs, nb, sb);
+                        bool cl = false;
+                        dst[p] = upd<T, BASE>(s, sb, fme + (T)c, cf, cl);
+                        my_clamps += cl ? 1ull : 0ull;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        nu_max = 0;   // skip the general loop
+    }
     for (; it < nu_max; ++it) {
         double2 acc = make_double2(0.0, 0.0);
         for (int p = threadIdx.x; p < n3; p += blockDim.x) {
@@ -551,8 +613,11 @@ cudaError_t launch_finalize(const double2 *partials, int nb, double ncells, Leve
 }
 
 __global__ void k_scale(const double *__restrict__ delta, double s, double *__restrict__ f,
-                        long long n3, double2 *__restrict__ partials, double add)
+                        long long n3, double2 *__restrict__ partials, double add,
+                        const double *__restrict__ add_dev)
 {
+    if (add_dev)
+        add = *add_dev;
     double2 acc = make_double2(0.0, 0.0);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n3;
          t += (long long)gridDim.x * blockDim.x) {
@@ -566,12 +631,12 @@ __global__ void k_scale(const double *__restrict__ delta, double s, double *__re
 }
 
 cudaError_t launch_scale(const double *delta, double s, double *f, long long n3, double2 *partials,
-                         int *nblocks, cudaStream_t st, double add)
+                         int *nblocks, cudaStream_t st, double add, const double *add_dev)
 {
     int g = blocks_for(n3);
     if (g > kReduceGrid)
         g = kReduceGrid;
-    k_scale<<<g, kBlock, 0, st>>>(delta, s, f, n3, partials, add);
+    k_scale<<<g, kBlock, 0, st>>>(delta, s, f, n3, partials, add, add_dev);
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();

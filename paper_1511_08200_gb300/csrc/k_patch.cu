@@ -195,8 +195,9 @@ __global__ void k_pbox_ghost_refresh(double *__restrict__ v, const double *__res
 // rtol times the first one or after nu_max sweeps.  A -> B (red) -> A (black).
 // Boxes up to kPboxSmemCells cells run in shared memory.
 constexpr int kPboxSmemCells = 1024;
+constexpr int kPboxThreads = 512;   // 128 registers a thread: stencil offsets stay in registers
 
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kPboxThreads)
     k_pbox_coarsest(double *A, double *B, const double *__restrict__ f, int p0, int p1, int p2,
                     CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
                     int *sweeps_out, const double *__restrict__ v0, double w)
@@ -241,6 +242,90 @@ __global__ void __launch_bounds__(1024)
     double r0 = -1.0;
     int it = 0;
     unsigned long long my_clamps = 0;
+    constexpr int kOwnGhosts = 8;
+    if (in_smem && n3 <= (int)blockDim.x && nbox <= kOwnGhosts * (int)blockDim.x) {
+        // one interior cell per thread and at most kOwnGhosts box cells: stencil offsets,
+        // colour, f and the ghost-refresh terms once (the same values as the loop below)
+        const int p = threadIdx.x;
+        const bool mine = p < n3;
+        Nbr nb{};
+        int colour_me = 0, cbox = 0;
+        double fme = 0.0;
+        if (mine) {
+            const int k = p % p2, j = (p / p2) % p1, i = p / (p1 * p2);
+            nb = nbr_of(box_rows(d1, d2, i + 1, j + 1), k + 1, k + 2, k);
+            colour_me = (i + j + k) & 1;
+            cbox = nb.o[0];
+            fme = ff[p];
+        }
+        // slot e covers box cell threadIdx.x + e * blockDim.x; gi < 0: not a ghost (or none)
+        int gi[kOwnGhosts], ga[kOwnGhosts];
+        double gw[kOwnGhosts];
+#pragma unroll
+        for (int e = 0; e < kOwnGhosts; ++e) {
+            gi[e] = -1;
+            ga[e] = 0;
+            gw[e] = 0.0;
+            const int q = threadIdx.x + e * blockDim.x;
+            if (!g0 || q >= nbox)
+                continue;
+            const int K = q % d2, J = (q / d2) % d1, I = q / (d1 * d2);
+            int m = 0, a0 = I, a1 = J, a2 = K;
+            if (I == 0) { a0 = 1; ++m; } else if (I == p0 + 1) { a0 = p0; ++m; }
+            if (J == 0) { a1 = 1; ++m; } else if (J == p1 + 1) { a1 = p1; ++m; }
+            if (K == 0) { a2 = 1; ++m; } else if (K == p2 + 1) { a2 = p2; ++m; }
+            if (m == 0)
+                continue;
+            gi[e] = q;
+            ga[e] = (a0 * d1 + a1) * d2 + a2;
+            gw[e] = m == 1 ? w : (m == 2 ? w * w : w * w * w);
+        }
+        auto refresh_own = [&](double *X) {
+#pragma unroll
+            for (int e = 0; e < kOwnGhosts; ++e)
+                if (gi[e] >= 0)
+                    X[gi[e]] = g0[gi[e]] + gw[e] * (X[ga[e]] - g0[ga[e]]);
+            __syncthreads();
+        };
+        for (; it < nu_max; ++it) {
+            double2 acc = make_double2(0.0, 0.0);
+            if (mine) {
+                St<double> s;
+                gather_nbr((const double *)a, nb, s);
+                const double res = fme - cell_op(s, cf);
+                acc.y = res * res;
+            }
+            acc = block_sum2(acc);
+            if (threadIdx.x == 0)
+                bc_s = acc.y;
+            __syncthreads();
+            const double rn = sqrt(bc_s);
+            __syncthreads();
+            if (r0 < 0.0)
+                r0 = rn;
+            if (rn <= rtol * r0)
+                break;
+            for (int colour = 0; colour < 2; ++colour) {
+                const double *src = colour == 0 ? a : b;
+                double *dst = colour == 0 ? b : a;
+                if (mine) {
+                    if (colour_me != colour) {
+                        dst[cbox] = src[cbox];
+                    } else {
+                        St<double> s;
+                        gather_nbr(src, nb, s);
+                        bool cl = false;
+                        dst[cbox] = cell_update(s, fme, cf, cl);
+                        my_clamps += cl ? 1ull : 0ull;
+                    }
+                }
+                __syncthreads();
+                if (g0)
+                    refresh_own(dst);
+            }
+        }
+        nu_max = 0;   // skip the general loop
+    }
     for (; it < nu_max; ++it) {
         double2 acc = make_double2(0.0, 0.0);
         for (int p = threadIdx.x; p < n3; p += blockDim.x) {
@@ -341,8 +426,8 @@ cudaError_t launch_pbox_coarsest(double *A, double *B, const double *f, const in
     const int n3 = p[0] * p[1] * p[2];
     const int nbox = (p[0] + 2) * (p[1] + 2) * (p[2] + 2);
     int threads = ((n3 + 31) / 32) * 32;
-    if (threads > 1024)
-        threads = 1024;
+    if (threads > kPboxThreads)
+        threads = kPboxThreads;
     const size_t sm = nbox <= kPboxSmemCells ? (size_t)4 * nbox * sizeof(double) : 0;
     k_pbox_coarsest<<<1, threads, sm, st>>>(A, B, f, p[0], p[1], p[2], cf, nu_max, rtol, clamp,
                                             sweeps, v0, w);

@@ -133,6 +133,7 @@ struct GraphReadback {
     BoxCtl ctl;
     SolveCounters cnt;
     LevelScal ls0;
+    double c_in;   // patch form: the compatibility constant of this call (host -> device)
 };
 
 struct GraphEntry {
@@ -143,6 +144,9 @@ struct GraphEntry {
     bool busy = false;
     MixedHier *hier = nullptr;     // MG5_MIXED
     Hier *hier64 = nullptr;        // MG5_FP64
+    PatchHier *hierp = nullptr;    // Dirichlet patch relaxation (pf in pdims)
+    int pdims[3] = {0, 0, 0};
+    double *cdev = nullptr;        // patch form: device copy of the compatibility constant
     double2 *partials = nullptr;
     LevelScal *ls = nullptr;
     SolveCounters *cnt = nullptr;
@@ -358,6 +362,48 @@ static void free_patch(mg5_ctx *ctx, PatchHier *h)
         ctx_free(ctx, h->f[l], ib);
     }
     delete h;
+}
+
+// A patch hierarchy owned by a captured graph (plain allocations, counted by the entry).
+static void free_patch_raw(PatchHier *h)
+{
+    if (!h)
+        return;
+    for (int l = 0; l < h->nlev; ++l)
+        for (void *q : {(void *)h->v0[l], (void *)h->tmp[l], (void *)h->f[l],
+                        l > 0 ? (void *)h->v[l] : nullptr})
+            if (q)
+                cudaFree(q);
+    delete h;
+}
+
+static cudaError_t alloc_patch_raw(const int p[3], PatchHier **out)
+{
+    PatchHier *h = new PatchHier();
+    for (int a = 0; a < 3; ++a)
+        h->p[a] = p[a];
+    h->nlev = patch_levels(p, h->q);
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < h->nlev && e == cudaSuccess; ++l) {
+        const size_t bb = box_cells(h->q[l]) * sizeof(double), ib = int_cells(h->q[l]) * sizeof(double);
+        if (l > 0) {
+            e = cudaMalloc((void **)&h->v[l], bb);
+            if (e == cudaSuccess)
+                e = cudaMalloc((void **)&h->v0[l], bb);
+            h->bytes += 2 * bb;
+        }
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&h->tmp[l], bb);
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&h->f[l], ib);
+        h->bytes += bb + ib;
+    }
+    if (e != cudaSuccess) {
+        free_patch_raw(h);
+        return e;
+    }
+    *out = h;
+    return cudaSuccess;
 }
 
 static int get_patch(mg5_ctx *ctx, const int p[3], PatchHier **out)
@@ -1170,6 +1216,8 @@ int mg5_refine_interpolate_cubic(mg5_ctx *ctx, const double *phic, int Nc, const
 
 static int floor_div4(int x) { return x >= 0 ? x / 4 : -((-x + 3) / 4); }
 
+
+
 int mg5_refine_interpolate_box(mg5_ctx *ctx, const double *box, const int bd[3], int pg,
                                const int o[3], const int pn[3], int ghost, double *fine,
                                void *stream)
@@ -1205,6 +1253,18 @@ struct RunPatch {
     cudaStream_t st;
     double hl[kMaxLevels];
     long long cu = 0;
+    // device scratch: the context's (its patch slot), or a captured graph's own
+    LevelScal *lsp = nullptr;
+    SolveCounters *cntb = nullptr;
+    double2 *partb = nullptr;
+
+    void bind_ctx_scratch()
+    {
+        lsp = ctx->ls + kPatchSlot;
+        cntb = ctx->cnt;
+        partb = ctx->partials;
+    }
+    bool bound() const { return lsp && cntb && partb; }
 
     // extrapolation weight of the coarse ghosts on grid l >= 1 (see k_patch.cu)
     static double ghost_w(int l)
@@ -1220,7 +1280,7 @@ struct RunPatch {
         {
             ProfScope ps(&ctx->prof, l == 0 ? PK_PATCH_SWEEP : PK_PATCH_SWEEPC, st, cells);
             CK(launch_patch_sweep(h->v[l], h->tmp[l], h->f[l], 0.0, h->q[l],
-                                  make_coef<double>(hl[l], p->alpha), &ctx->cnt->clamped, st,
+                                  make_coef<double>(hl[l], p->alpha), &cntb->clamped, st,
                                   l > 0 ? h->v0[l] : nullptr, l > 0 ? ghost_w(l) : 0.0));
         }
         std::swap(h->v[l], h->tmp[l]);
@@ -1234,7 +1294,7 @@ struct RunPatch {
         ProfScope ps(&ctx->prof, PK_COARSEST64, st);
         CK(launch_pbox_coarsest(h->v[l], h->tmp[l], h->f[l], h->q[l],
                                 make_coef<double>(hl[l], p->alpha), p->nu_coarse, kCoarseRtol,
-                                &ctx->cnt->clamped, &ctx->cnt->coarse_sweeps, st,
+                                &cntb->clamped, &cntb->coarse_sweeps, st,
                                 l > 0 ? h->v0[l] : nullptr, l > 0 ? ghost_w(l) : 0.0));
         return MG5_OK;
     }
@@ -1247,10 +1307,10 @@ struct RunPatch {
             ProfScope ps(&ctx->prof, PK_PATCH_RESID, st, (double)int_cells(h->q[l]));
             CK(launch_pbox_resid_restrict(h->v[l], h->f[l], h->q[l],
                                           make_coef<double>(hl[l], p->alpha), h->v[l + 1],
-                                          h->v0[l + 1], h->f[l + 1], ctx->partials, &nb, st));
+                                          h->v0[l + 1], h->f[l + 1], partb, &nb, st));
         }
         if (finalize)
-            CK(launch_finalize(ctx->partials, nb, (double)int_cells(h->q[l]), ctx->ls + kPatchSlot,
+            CK(launch_finalize(partb, nb, (double)int_cells(h->q[l]), lsp,
                                FIN_NORM, st));
         return MG5_OK;
     }
@@ -1319,6 +1379,11 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
     } restore{h, h->tmp[0]};
     h->v[0] = phi;
     RunPatch R{ctx, h, p, st, {}, 0};
+    R.bind_ctx_scratch();
+    if (!R.bound()) {
+        ctx->err = "relax_patch: context scratch not allocated";
+        return MG5_E_ARG;
+    }
     for (int l = 0; l < h->nlev; ++l)
         R.hl[l] = p->h * (double)(1 << l);
     int status = MG5_E_NOT_CONVERGED;
@@ -1392,6 +1457,270 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
     return status;
 }
 
+static size_t patch_entry_bytes(const int pf[3], size_t hier_bytes)
+{
+    return hier_bytes + (box_cells(pf) + int_cells(pf)) * sizeof(double) +
+           sizeof(double2) * kMaxPartials + sizeof(LevelScal) * kScalSlots + sizeof(SolveCounters) +
+           sizeof(BoxCtl) + sizeof(double);
+}
+
+// The patch relaxation as one graph: f = s delta + c (c read on the device), the coarse ghost
+// shells from the entry's box, the first smoothing and check, then the V-cycle as a WHILE node
+// (body: coarse-grid correction, post- and next pre-smoothing, check).  As for the periodic FP64
+// graph the body swaps each grid's buffers nu1 + nu2 times (even).
+static int capture_patch(mg5_ctx *ctx, GraphEntry *g, const mg5_params *p, cudaStream_t st,
+                         cudaStream_t body_st);
+
+}  // extern "C"
+
+namespace {
+
+int capture_patch_impl(mg5_ctx *ctx, GraphEntry *g, const mg5_params *p, cudaStream_t st,
+                       cudaStream_t body_st)
+{
+    PatchHier *h = g->hierp;
+    const int *pf = g->pdims;
+    const long long ni = (long long)int_cells(pf), nbox = (long long)box_cells(pf);
+    RunPatch R{ctx, h, p, st, {}, 0};
+    R.lsp = g->ls;
+    R.cntb = g->cnt;
+    R.partb = g->partials;
+    if (!R.bound() || !g->ctl || !g->phi || !g->delta || !g->cdev) {
+        ctx->err = "capture_patch: entry scratch not allocated";
+        return MG5_E_ARG;
+    }
+    for (int l = 0; l < h->nlev; ++l)
+        R.hl[l] = p->h * (double)(1 << l);
+    const long long L0 = launches_total();
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) {
+        ctx->err = "capture_patch: stream is not capturing";
+        return MG5_E_ARG;
+    }
+    cudaGraphConditionalHandle hnd;
+    CK(cudaGraphConditionalHandleCreate(&hnd, graph, 0, cudaGraphCondAssignDefault));
+    CK(launch_ctl_init(g->ctl, p->tol, p->max_cycles, st));
+    CK(cudaMemsetAsync(g->ls, 0, sizeof(LevelScal) * kScalSlots, st));
+    CK(cudaMemsetAsync(g->cnt, 0, sizeof(SolveCounters), st));
+    int nb = 0;
+    CK(launch_scale(g->delta, p->s, h->f[0], ni, g->partials, &nb, st, 0.0, g->cdev));
+    CK(launch_finalize(g->partials, nb, (double)ni, g->ls, FIN_FNORM, st));
+    CK(cudaMemcpyAsync(h->tmp[0], g->phi, nbox * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (int l = 1; l < h->nlev; ++l)
+        CK(launch_pbox_ghosts(l == 1 ? g->phi : h->v[l - 1], h->q[l - 1], h->v[l], h->tmp[l],
+                              h->v0[l], st));
+    h->v[0] = g->phi;
+    for (int k = 0; k < p->nu1; ++k)
+        RET(R.sweep(0));
+    RET(R.resid_restrict(0, true));
+    CK(launch_loop_check(g->ls, g->ctl, hnd, st));
+    const long long cells_fixed = R.cu;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    const long long L1 = launches_total();
+    CK(cudaStreamBeginCaptureToGraph(body_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    double *const v0_start = h->v[0];
+    RunPatch B = R;
+    B.st = body_st;
+    B.cu = 0;
+    int rc = B.coarse_visit(1);
+    if (rc == MG5_OK && launch_pbox_prolong(h->v[1], h->v0[1], h->q[1], h->v[0], body_st) != cudaSuccess)
+        rc = MG5_E_CUDA;
+    for (int k = 0; k < p->nu2 && rc == MG5_OK; ++k)
+        rc = B.sweep(0);
+    for (int k = 0; k < p->nu1 && rc == MG5_OK; ++k)
+        rc = B.sweep(0);
+    if (rc == MG5_OK)
+        rc = B.resid_restrict(0, true);
+    if (rc == MG5_OK && launch_loop_check(g->ls, g->ctl, hnd, body_st) != cudaSuccess)
+        rc = MG5_E_CUDA;
+    cudaGraph_t g_out = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(body_st, &g_out);
+    RET(rc);
+    CK(e_end);
+    if (h->v[0] != v0_start) {
+        ctx->err = "capture_patch: the loop body does not return the grids to their buffers";
+        return MG5_E_ARG;
+    }
+    const long long L2 = launches_total();
+    if (h->v[0] != g->phi)
+        CK(cudaMemcpyAsync(g->phi, h->v[0], nbox * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    g->stats.launches_fixed = (L1 - L0) + (launches_total() - L2);
+    g->stats.launches_per_iter = L2 - L1;
+    g->stats.cells_per_iter = B.cu;
+    g->stats.cells_fixed = cells_fixed;
+    g->stats.inner = 1;
+    return MG5_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+static int capture_patch(mg5_ctx *ctx, GraphEntry *g, const mg5_params *p, cudaStream_t st,
+                         cudaStream_t body_st)
+{
+    return capture_patch_impl(ctx, g, p, st, body_st);
+}
+
+int mg5_relax_patch_graph(mg5_ctx *ctx, const double *delta_f, const int pf[3], const mg5_params *p,
+                          double compat_c, double *phi, mg5_info *info, void *stream)
+{
+    if (!ctx || !delta_f || !pf || !phi)
+        return MG5_E_ARG;
+    RET(check_params(p));
+    for (int a = 0; a < 3; ++a)
+        if (pf[a] < 2 || (pf[a] & 1))
+            return MG5_E_ARG;
+    if (!std::isfinite(compat_c))
+        return MG5_E_ARG;
+    int q[kMaxLevels][3];
+    if (patch_levels(pf, q) < 2 || (p->nu1 + p->nu2) % 2) {
+        ctx->err = "relax_patch_graph needs two grids or more and nu1 + nu2 even";
+        return MG5_E_ARG;
+    }
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (info)
+        std::memset(info, 0, sizeof(*info));
+    const long long ni = (long long)int_cells(pf), nbox = (long long)box_cells(pf);
+    // the cached entry for (pf, params), or a new capture
+    GraphEntry *g = nullptr;
+    for (GraphEntry *x : ctx->graphs)
+        if (!x->busy && x->hierp && x->pdims[0] == pf[0] && x->pdims[1] == pf[1] &&
+            x->pdims[2] == pf[2] && same_params(x->prm, *p)) {
+            g = x;
+            break;
+        }
+    if (!g) {
+        while (ctx->graphs.size() >= kGraphCacheMax) {
+            GraphEntry *v = graph_take_idle(ctx);
+            if (!v)
+                break;
+            graph_free(v);
+        }
+        g = new GraphEntry();
+        g->prm = *p;
+        for (int a = 0; a < 3; ++a)
+            g->pdims[a] = pf[a];
+        cudaError_t e = alloc_patch_raw(pf, &g->hierp);
+        const size_t need = patch_entry_bytes(pf, g->hierp ? g->hierp->bytes : 0);
+        if (e == cudaSuccess && ctx->budget && ctx->held + need > ctx->budget)
+            e = cudaErrorMemoryAllocation;
+        for (void **q2 : {(void **)&g->partials, (void **)&g->ls, (void **)&g->cnt, (void **)&g->ctl,
+                          (void **)&g->delta, (void **)&g->phi, (void **)&g->cdev}) {
+            if (e != cudaSuccess)
+                break;
+            size_t b = q2 == (void **)&g->partials ? sizeof(double2) * kMaxPartials
+                     : q2 == (void **)&g->ls       ? sizeof(LevelScal) * kScalSlots
+                     : q2 == (void **)&g->cnt      ? sizeof(SolveCounters)
+                     : q2 == (void **)&g->ctl      ? sizeof(BoxCtl)
+                     : q2 == (void **)&g->delta    ? ni * sizeof(double)
+                     : q2 == (void **)&g->phi      ? nbox * sizeof(double)
+                                                   : sizeof(double);
+            e = cudaMalloc(q2, b);
+        }
+        if (e == cudaSuccess)
+            e = cudaMallocHost((void **)&g->rb, sizeof(GraphReadback));
+        g->bytes = need;
+        cudaStream_t origin = nullptr, body = nullptr;
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking);
+        int rc = e == cudaSuccess ? MG5_OK : (e == cudaErrorMemoryAllocation ? MG5_E_OOM : MG5_E_CUDA);
+        if (rc != MG5_OK)
+            ctx->err = std::string("relax_patch_graph: ") + cudaGetErrorString(e);
+        const long long l0 = launches_total();
+        const bool prof_on = ctx->prof.on;
+        if (rc == MG5_OK) {
+            ctx->prof.on = false;
+            e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                rc = capture_patch(ctx, g, p, origin, body);
+                cudaGraph_t graph = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(origin, &graph);
+                if (rc == MG5_OK && e2 == cudaSuccess) {
+                    g->graph = graph;
+                    e = cudaGraphInstantiate(&g->exec, graph, 0);
+                } else {
+                    if (graph)
+                        cudaGraphDestroy(graph);
+                    if (e2 != cudaSuccess)
+                        e = e2;
+                }
+            }
+            ctx->prof.on = prof_on;
+            count_launch(l0 - launches_total());
+            if (rc == MG5_OK && e != cudaSuccess) {
+                ctx->err = std::string("relax_patch_graph: ") + cudaGetErrorString(e);
+                rc = MG5_E_CUDA;
+            }
+        }
+        if (origin)
+            cudaStreamDestroy(origin);
+        if (body)
+            cudaStreamDestroy(body);
+        cudaGetLastError();
+        if (rc != MG5_OK) {
+            graph_free(g);
+            return rc;
+        }
+        graph_insert(ctx, g);
+    } else {
+        g->busy = true;
+        g->last_use = ++ctx->graph_clock;
+    }
+    CK(cudaEventRecord(ctx->ev0, st));
+    g->rb->c_in = compat_c;
+    int rc = MG5_OK;
+    cudaError_t e = cudaMemcpyAsync(g->cdev, &g->rb->c_in, sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->delta, delta_f, ni * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->phi, phi, nbox * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaGraphLaunch(g->exec, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(phi, g->phi, nbox * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&g->rb->ctl, g->ctl, sizeof(BoxCtl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&g->rb->cnt, g->cnt, sizeof(SolveCounters), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&g->rb->ls0, g->ls, sizeof(LevelScal), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(ctx->ev1, st);
+    if (e == cudaSuccess)
+        e = ctx_wait(ctx, st);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("relax_patch_graph: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        graph_checkin(g);
+        return MG5_E_CUDA;
+    }
+    rc = graph_finish(g, info);
+    if (info) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        info->ms_total = ms;
+        info->compat_c = compat_c;
+    }
+    return rc;
+}
+
 static bool same_params(const mg5_params &a, const mg5_params &b)
 {
     return std::memcmp(&a, &b, sizeof(mg5_params)) == 0;
@@ -1462,6 +1791,9 @@ void graph_free(GraphEntry *g)
     if (g->hier)
         free_mixed(g->hier, &hb);
     free_hier_raw(g->hier64);
+    free_patch_raw(g->hierp);
+    if (g->cdev)
+        cudaFree(g->cdev);
     for (void *p : {(void *)g->partials, (void *)g->ls, (void *)g->cnt, (void *)g->ctl,
                     (void *)g->delta, (void *)g->phi, (void *)g->gout})
         if (p)
@@ -1585,8 +1917,13 @@ int graph_finish(GraphEntry *g, mg5_info *info)
         info->status = status;
         info->outer_iters = g->hier ? ctl.outer : 0;
         info->cycles = ctl.outer * g->stats.inner;
-        info->levels = g->hier ? g->hier->nlev : g->hier64->nlev;
-        info->coarsest_n = g->hier ? g->hier->n[info->levels - 1] : g->hier64->n[info->levels - 1];
+        if (g->hierp) {
+            info->levels = g->hierp->nlev;
+            info->coarsest_n = g->hierp->q[info->levels - 1][0];
+        } else {
+            info->levels = g->hier ? g->hier->nlev : g->hier64->nlev;
+            info->coarsest_n = g->hier ? g->hier->n[info->levels - 1] : g->hier64->n[info->levels - 1];
+        }
         info->n_history = ctl.nhist;
         for (int k = 0; k < ctl.nhist && k < 64; ++k)
             info->history[k] = ctl.hist[k];
@@ -1594,8 +1931,10 @@ int graph_finish(GraphEntry *g, mg5_info *info)
         info->compat_c = g->rb->ls0.c;
         info->phi_mean_removed = g->rb->ls0.mean;
         const long long nc = info->coarsest_n;
+        const long long coarse_cells =
+            g->hierp ? (long long)int_cells(g->hierp->q[g->hierp->nlev - 1]) : nc * nc * nc;
         info->cell_updates = g->stats.cells_fixed + g->stats.cells_per_iter * ctl.outer +
-                             (long long)cnt.coarse_sweeps * nc * nc * nc;
+                             (long long)cnt.coarse_sweeps * coarse_cells;
         info->coarse_sweeps = cnt.coarse_sweeps;
         info->disc_clamped = (long long)cnt.clamped;
     }

@@ -130,6 +130,64 @@ __device__ __forceinline__ void gather(const T *F, const T *E, const Rows &r, in
     s.ymzm = E[r.r0m + km];
 }
 
+// The 19 offsets of a cell's stencil within one array (St order), for kernels that
+// visit the same cell many times (the single-CTA coarsest-grid solves) and compute
+// them once instead of on every visit.
+struct Nbr {
+    int o[19];
+};
+
+__device__ __forceinline__ Nbr nbr_of(const Rows &r, int k, int kp, int km)
+{
+    Nbr b;
+    const int r00 = (int)r.r00, rp0 = (int)r.rp0, rm0 = (int)r.rm0, r0p = (int)r.r0p,
+              r0m = (int)r.r0m;
+    b.o[0] = r00 + k;
+    b.o[1] = rp0 + k;
+    b.o[2] = rm0 + k;
+    b.o[3] = r0p + k;
+    b.o[4] = r0m + k;
+    b.o[5] = r00 + kp;
+    b.o[6] = r00 + km;
+    b.o[7] = (int)r.rpp + k;
+    b.o[8] = (int)r.rpm + k;
+    b.o[9] = (int)r.rmp + k;
+    b.o[10] = (int)r.rmm + k;
+    b.o[11] = rp0 + kp;
+    b.o[12] = rp0 + km;
+    b.o[13] = rm0 + kp;
+    b.o[14] = rm0 + km;
+    b.o[15] = r0p + kp;
+    b.o[16] = r0p + km;
+    b.o[17] = r0m + kp;
+    b.o[18] = r0m + km;
+    return b;
+}
+
+template <typename T>
+__device__ __forceinline__ void gather_nbr(const T *a, const Nbr &b, St<T> &s)
+{
+    s.c = a[b.o[0]];
+    s.xp = a[b.o[1]];
+    s.xm = a[b.o[2]];
+    s.yp = a[b.o[3]];
+    s.ym = a[b.o[4]];
+    s.zp = a[b.o[5]];
+    s.zm = a[b.o[6]];
+    s.xpyp = a[b.o[7]];
+    s.xpym = a[b.o[8]];
+    s.xmyp = a[b.o[9]];
+    s.xmym = a[b.o[10]];
+    s.xpzp = a[b.o[11]];
+    s.xpzm = a[b.o[12]];
+    s.xmzp = a[b.o[13]];
+    s.xmzm = a[b.o[14]];
+    s.ypzp = a[b.o[15]];
+    s.ypzm = a[b.o[16]];
+    s.ymzp = a[b.o[17]];
+    s.ymzm = a[b.o[18]];
+}
+
 // S = sum of the 6 faces; t and d2 with Sigma h^4 = (2/3) t + d2 / 8:
 // a = sx - sy, b = sx - sz, c = sy - sz (sx = faces along x, ...) satisfy c = b - a,
 // so (1/3)(a^2 + b^2 + c^2) = (2/3)(a^2 + b c) = (2/3) t; d2 = dxy^2 + dxz^2 + dyz^2

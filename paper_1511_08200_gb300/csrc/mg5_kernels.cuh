@@ -123,9 +123,10 @@ cudaError_t launch_coarsest(T *v, T *tmp, const T *f, int n, CoefT<T> cf, double
 // ---- FP64 helpers
 cudaError_t launch_finalize(const double2 *partials, int nb, double ncells, LevelScal *ls,
                             int mode, cudaStream_t st);
-// f = s * delta + add, partial sums (0, (s delta)^2)
+// f = s * delta + add (add read from add_dev on the device when given), partial sums (0, (s delta)^2)
 cudaError_t launch_scale(const double *delta, double s, double *f, long long n3, double2 *partials,
-                         int *nblocks, cudaStream_t st, double add = 0.0);
+                         int *nblocks, cudaStream_t st, double add = 0.0,
+                         const double *add_dev = nullptr);
 // partial sums (phi, 0)
 cudaError_t launch_sum(const double *phi, long long n3, double2 *partials, int *nblocks,
                        cudaStream_t st);

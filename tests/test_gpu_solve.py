@@ -387,3 +387,28 @@ def test_fp64_graph_solve_equals_host_driven(ctx, n, fmg):
     if n <= 64:
         oref, _ = oracle.solve(delta, alpha, s, h, tol=1e-12)
         assert rel_l2(host(phi), oref) <= 1e-9
+
+
+def test_relax_patch_graph_equals_host_driven(ctx):
+    """mg5_relax_patch_graph replays the captured patch relaxation: bit-identical to
+    mg5_relax_patch, on the capture and on cache hits with a new compat_c and a new box."""
+    import torch
+    mg = _mg()
+    alpha, s, h = nominal()
+    coarse, dpatch, o = _patch_case()
+    phic, _, info = _solve(ctx, coarse, alpha, s, h, 1e-12, grad=False)
+    pn = (8, 8, 8)
+    box = ctx.refine_interpolate(dev(phic), o, pn, 1)
+    p = mg.default_params(alpha=alpha, s=s, h=h / 2, tol=1e-12, max_cycles=200)
+    d = dev(dpatch)
+    for c, scale in ((info.compat_c, 1.0), (info.compat_c, 1.0), (1.5 * info.compat_c, 1.01)):
+        b0 = (box * scale).contiguous()
+        ref, iref = ctx.relax_patch(d, p, c, b0.clone())
+        got, ig = ctx.relax_patch(d, p, c, b0.clone(), graph=True)
+        assert torch.equal(ref, got)
+        assert (ig.cycles, ig.cell_updates, ig.coarse_sweeps, ig.status) == \
+            (iref.cycles, iref.cell_updates, iref.coarse_sweeps, iref.status)
+        assert ig.rel_residual == iref.rel_residual
+    with pytest.raises(mg.MG5Error):   # nu1 + nu2 odd
+        ctx.relax_patch(d, mg.default_params(alpha=alpha, s=s, h=h / 2, nu2=1), info.compat_c,
+                        box.clone(), graph=True)
