@@ -36,7 +36,7 @@ _c_uint = ctypes.c_uint
 class Params(ctypes.Structure):
     _fields_ = [("alpha", _c_double), ("s", _c_double), ("h", _c_double), ("tol", _c_double),
                 ("nu1", _c_int), ("nu2", _c_int), ("nu_coarse", _c_int), ("max_cycles", _c_int),
-                ("precision", _c_int), ("inner_cycles", _c_int)]
+                ("precision", _c_int), ("inner_cycles", _c_int), ("omega", _c_double)]
 
 
 class _Info(ctypes.Structure):

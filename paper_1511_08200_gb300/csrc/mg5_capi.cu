@@ -509,7 +509,8 @@ static int check_params(const mg5_params *p)
 {
     if (!p || !(p->h > 0.0) || !(p->alpha >= 0.0) || !std::isfinite(p->s) || !(p->tol >= 0.0) ||
         p->nu1 < 0 || p->nu2 < 0 || p->nu_coarse < 0 || p->max_cycles < 0 ||
-        (p->precision != MG5_FP64 && p->precision != MG5_MIXED))
+        (p->precision != MG5_FP64 && p->precision != MG5_MIXED) || !(p->omega >= 0.0) ||
+        !(p->omega < 2.0))
         return MG5_E_ARG;
     return MG5_OK;
 }
@@ -543,7 +544,7 @@ struct Run64 {
 
     int sweep(int l)
     {
-        const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
+        const CoefT<double> cf = make_coef<double>(hl[l], p->alpha, omega_of(p));
         ProfScope ps(&ctx->prof, l == 0 ? PK_SWEEP64 : PK_SWEEP64C, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
         cudaError_t e = launch_sweep_sched<double>(sweep_schedule(ctx->device, MG5_FP64, h->n[l]),
                                                    h->v[l], h->tmp[l], h->f[l], c(l), h->n[l], cf,
@@ -587,7 +588,7 @@ struct Run64 {
 
     int coarsest(int l)
     {
-        const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
+        const CoefT<double> cf = make_coef<double>(hl[l], p->alpha, omega_of(p));
         mg5_ctx *ctx = this->ctx;
         ProfScope ps(&ctx->prof, PK_COARSEST64, st);
         CK(launch_coarsest<double>(h->v[l], h->tmp[l], h->f[l], h->n[l], cf, c(l), p->nu_coarse,
@@ -1280,7 +1281,7 @@ struct RunPatch {
         {
             ProfScope ps(&ctx->prof, l == 0 ? PK_PATCH_SWEEP : PK_PATCH_SWEEPC, st, cells);
             CK(launch_patch_sweep(h->v[l], h->tmp[l], h->f[l], 0.0, h->q[l],
-                                  make_coef<double>(hl[l], p->alpha), &cntb->clamped, st,
+                                  make_coef<double>(hl[l], p->alpha, omega_of(p)), &cntb->clamped, st,
                                   l > 0 ? h->v0[l] : nullptr, l > 0 ? ghost_w(l) : 0.0));
         }
         std::swap(h->v[l], h->tmp[l]);
@@ -1293,7 +1294,7 @@ struct RunPatch {
         mg5_ctx *ctx = this->ctx;
         ProfScope ps(&ctx->prof, PK_COARSEST64, st);
         CK(launch_pbox_coarsest(h->v[l], h->tmp[l], h->f[l], h->q[l],
-                                make_coef<double>(hl[l], p->alpha), p->nu_coarse, kCoarseRtol,
+                                make_coef<double>(hl[l], p->alpha, omega_of(p)), p->nu_coarse, kCoarseRtol,
                                 &cntb->clamped, &cntb->coarse_sweeps, st,
                                 l > 0 ? h->v0[l] : nullptr, l > 0 ? ghost_w(l) : 0.0));
         return MG5_OK;

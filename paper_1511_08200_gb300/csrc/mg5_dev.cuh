@@ -33,10 +33,11 @@ struct CoefT {
     T s3;        // alpha / (3 h^4): weight of the (a, b, c) terms of alpha Sigma(., .)
     T k43h;      // (4 alpha / 3) / h^2: beta' = 1 + k43h (S_B - 6 B_c)
     T inv2k23;   // 1 / (2 k23) (0 when alpha = 0, where it is never used)
+    T om1;       // omega - 1: a smoothing update is v + omega (v_root - v)
 };
 
 template <typename T>
-__host__ __device__ inline CoefT<T> make_coef(double h, double alpha)
+__host__ __device__ inline CoefT<T> make_coef(double h, double alpha, double omega = 1.0)
 {
     CoefT<T> c;
     const double h4 = h * h * h * h;
@@ -52,6 +53,7 @@ __host__ __device__ inline CoefT<T> make_coef(double h, double alpha)
     c.s3 = (T)(alpha / (3.0 * h4));
     c.k43h = (T)(4.0 * alpha / (3.0 * h * h));
     c.inv2k23 = (T)(alpha > 0.0 ? 3.0 / (4.0 * alpha) : 0.0);
+    c.om1 = (T)(omega - 1.0);
     return c;
 }
 
@@ -272,7 +274,8 @@ __device__ __forceinline__ T cell_update(const St<T> &s, T rhs, const CoefT<T> &
     stencil_parts(s, S, t, d2);
     const T b = rhs + cf.s8 * d2 + cf.s23 * t;   // rhs + alpha Sigma
     const T L = physical_root(b, cf, clamped);
-    return (S - cf.h2 * L) * (T)(1.0 / 6.0);
+    const T v = (S - cf.h2 * L) * (T)(1.0 / 6.0);
+    return cf.om1 != (T)0 ? v + cf.om1 * (v - s.c) : v;
 }
 
 // op(phi) at the cell = L + alpha((2/3) L^2 - Sigma).
@@ -341,7 +344,8 @@ __device__ __forceinline__ T cell_update_corr(const St<T> &e, const St<T> &B, T 
     // (beta' < 0 needs alpha > 0, so k23 > 0 there)
     const T sq = sqrt(disc);
     const T L = bp >= (T)0 ? (T)2 * b / (bp + sq) : (sq - bp) / ((T)2 * cf.k23);
-    return (pe.S - cf.h2 * L) * (T)(1.0 / 6.0);
+    const T v = (pe.S - cf.h2 * L) * (T)(1.0 / 6.0);
+    return cf.om1 != (T)0 ? v + cf.om1 * (v - e.c) : v;
 }
 
 // FP32 correction form, the inner sweep of the mixed mode.  The same update as the
@@ -404,7 +408,8 @@ __device__ __forceinline__ float cell_update_corr(const St<float> &e, const St<f
     }
     const float sq = disc > 0.0f ? disc * rsqrtf(disc) : 0.0f;
     const float L = bp >= 0.0f ? __fdividef(2.0f * bq, bp + sq) : (sq - bp) * cf.inv2k23;
-    return (q.S.x - cf.h2 * L) * (1.0f / 6.0f);
+    const float v = (q.S.x - cf.h2 * L) * (1.0f / 6.0f);
+    return cf.om1 != 0.0f ? v + cf.om1 * (v - e.c) : v;
 }
 
 // op(B + e) - op(B) in FP32: L_e + (2 alpha / 3) L_e (2 L_B + L_e) - alpha (2 Sigma(B, e) + Sigma(e))

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "mg5.h"
 #include "mg5_dev.cuh"
 
 namespace mg5 {
@@ -35,6 +36,16 @@ constexpr int kMaxPartials = 8192;  // partial-sum slots per reduction
 
 // Number of blocks of kBlock threads to cover `work` items (capped for reductions).
 inline int blocks_for(long long work) { return (int)((work + kBlock - 1) / kBlock); }
+
+// The smoother's relaxation weight of a parameter set (0 selects the default: 1.3 for the FP64
+// solves, whose V-cycle count it cuts; 1 for the mixed mode, whose inner cycle count is fixed
+// and whose FP32 correction sweeps gain nothing from it).
+inline double omega_of(const mg5_params *p)
+{
+    if (p->omega > 0.0)
+        return p->omega;
+    return p->precision == MG5_FP64 ? 1.3 : 1.0;
+}
 
 // Process-wide count of kernel launches the library has enqueued.
 void count_launch(long long n);

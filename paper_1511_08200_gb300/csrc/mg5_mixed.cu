@@ -111,7 +111,7 @@ struct RunMix {
     int sweep(int l)
     {
         ProfScope ps(sh.prof, l == 0 ? PK_SWEEP32 : PK_SWEEP32C, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
-        const CoefT<float> cf = make_coef<float>(hl[l], p->alpha);
+        const CoefT<float> cf = make_coef<float>(hl[l], p->alpha, omega_of(p));
         int dev = 0;
         cudaGetDevice(&dev);
         cudaError_t e = launch_sweep_sched<float>(sweep_schedule(dev, MG5_MIXED, h->n[l]), h->e[l],
@@ -128,7 +128,7 @@ struct RunMix {
     {
         ProfScope ps(sh.prof, PK_COARSEST32, st);
         cudaError_t e = launch_coarsest<float>(h->e[l], h->etmp[l], h->f[l], h->n[l],
-                                               make_coef<float>(hl[l], p->alpha), c(l),
+                                               make_coef<float>(hl[l], p->alpha, omega_of(p)), c(l),
                                                p->nu_coarse, kCoarseRtol, &sh.cnt->clamped,
                                                &sh.cnt->coarse_sweeps, st, h->B[l]);
         return e == cudaSuccess ? MG5_OK : fail("coarsest32", e);

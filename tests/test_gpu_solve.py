@@ -57,7 +57,8 @@ def test_fp64_solve_matches_oracle(ctx, n, sigma, seed):
 
 @pytest.mark.parametrize("n,sigma", [(32, 1.0), (48, 1.5), (128, 1.5)])
 def test_fp64_fmg_start_matches_oracle(ctx, n, sigma):
-    """The full-multigrid start reaches the same discrete solution in fewer cycles."""
+    """The full-multigrid start reaches the same discrete solution in no more cycles (with the
+    default over-relaxed smoother a V-cycle is strong enough that it often saves none)."""
     mg = _mg()
     alpha, s, h = nominal()
     delta = workload.lognormal_delta(n, sigma, 11)
@@ -67,7 +68,7 @@ def test_fp64_fmg_start_matches_oracle(ctx, n, sigma):
     ref, _ = oracle.solve(delta, alpha, s, h, tol=1e-13)
     assert info.status == 0
     assert rel_l2(host(phi), ref) <= 1e-10
-    assert info.cycles < plain.cycles
+    assert info.cycles <= plain.cycles
 
 
 def test_fp64_config_32_tol_1e10(ctx):
@@ -76,7 +77,7 @@ def test_fp64_config_32_tol_1e10(ctx):
     within the bound that residual implies, and the cycle count is the oracle's."""
     alpha, s, h = nominal()
     delta = workload.lognormal_delta(32, 1.0, 1)
-    phi, g, info = _solve(ctx, delta, alpha, s, h, 1e-10)
+    phi, g, info = _solve(ctx, delta, alpha, s, h, 1e-10, omega=1.0)   # the oracle's smoother
     ref_tight, _ = oracle.solve(delta, alpha, s, h, tol=1e-13)
     ref_same, rinfo = oracle.solve(delta, alpha, s, h, tol=1e-10)
     r = oracle.residual(phi, s * delta, info.compat_c, h, alpha)
@@ -412,3 +413,23 @@ def test_relax_patch_graph_equals_host_driven(ctx):
     with pytest.raises(mg.MG5Error):   # nu1 + nu2 odd
         ctx.relax_patch(d, mg.default_params(alpha=alpha, s=s, h=h / 2, nu2=1), info.compat_c,
                         box.clone(), graph=True)
+
+
+@pytest.mark.parametrize("prec,w,tol,bar", [("fp64", 0.0, 1e-11, 1e-9), ("mixed", 1.3, 1e-8, 1e-6)])
+def test_relaxation_weight_same_solution(ctx, prec, w, tol, bar):
+    """The smoother's weight changes the iteration, not the discrete problem: an over-relaxed
+    smoother (the FP64 default 1.3; 1.3 set by hand in the mixed mode) reaches the plain
+    update's (omega = 1) solution; in FP64 it takes fewer V-cycles."""
+    mg = _mg()
+    alpha, s, h = nominal()
+    d = dev(workload.lognormal_delta(64, 1.5, 41))
+    p1 = mg.default_params(alpha=alpha, s=s, h=h, tol=tol, precision=prec, omega=1.0)
+    p2 = mg.default_params(alpha=alpha, s=s, h=h, tol=tol, precision=prec, omega=w)
+    a, _, ia = ctx.solve_fifth_force(d, p1)
+    b, _, ib = ctx.solve_fifth_force(d, p2)
+    assert ia.status == 0 and ib.status == 0
+    assert rel_l2(host(b), host(a)) <= bar
+    if prec == "fp64":
+        assert ib.cycles < ia.cycles
+    with pytest.raises(mg.MG5Error):
+        ctx.solve_fifth_force(d, mg.default_params(alpha=alpha, s=s, h=h, omega=2.0))
