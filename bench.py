@@ -44,18 +44,20 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x
 # algorithmic work per cell of each kernel class: (bound, bytes, flops)
 #   sweep: read phi + f, write phi (the full red+black sweep of one cell);
 #   ~42 FP64 flops (FMA = 2) + 1 sqrt + 1 div per cell update
+# FP64 smoother flops per cell: the stencil parts, the root (FP32 seed + two FP64 Newton steps)
+# and the relaxed final update (omega v_root + (1 - omega) v)
 WORK = {
-    "sweep64": ("alu", 24.0, 42.0),
-    "patch_sweep64": ("alu", 24.0, 42.0),
+    "sweep64": ("alu", 24.0, 44.0),
+    "patch_sweep64": ("alu", 24.0, 44.0),
     "resid_restrict64": ("alu", 18.0, 38.0),
     "sweep32": ("hbm", 16.0, 60.0),          # correction form: read e, B, f; write e
     "resid_restrict32": ("hbm", 12.5, 60.0),
     "resid64_mixed": ("alu", 24.0, 36.0),     # read phi64, f64; write r32, B32
     "update_mixed": ("hbm", 20.0, 1.0),
     "force64": ("hbm", 32.0, 6.0),
-    "sweep64_coarse": ("alu", 24.0, 42.0),
+    "sweep64_coarse": ("alu", 24.0, 44.0),
     "sweep32_coarse": ("hbm", 16.0, 60.0),
-    "patch_sweep64_coarse": ("alu", 24.0, 42.0),
+    "patch_sweep64_coarse": ("alu", 24.0, 44.0),
     "refine64": ("hbm", 9.0, 25.0),
     "prolong64": ("hbm", 18.0, 20.0),
     "prolong32": ("hbm", 9.0, 20.0),
@@ -64,11 +66,12 @@ WORK = {
 
 # DRAM bytes per cell measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch / its cells), for the kernel as it stands; a launch's traffic = this x its cells.
-#   sweep32: k_sweep_fused<float,1>, 256^3 finest-grid launch: 278.1 MB / 16.78 M cells
+#   sweep32: k_sweep_fused<float,1>, 256^3 finest-grid launch: 279.0 MB / 16.78 M cells
 #            (profiles/sweep32_fused_mixed256.md)
+#   sweep64: k_sweep_red + k_sweep_black<double,0>, 128^3 finest grid (profiles/sweep64_refine128.md)
 TRAFFIC_PER_CELL = {
     "sweep32": 279.0e6 / 256 ** 3,
-    "sweep64": 84.1e6 / 128 ** 3,          # red + black launch, cold-cache ncu capture at 128^3
+    "sweep64": 84.4e6 / 128 ** 3,          # red + black launch, cold-cache ncu capture at 128^3
 }
 
 

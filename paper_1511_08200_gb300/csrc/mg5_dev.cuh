@@ -34,6 +34,8 @@ struct CoefT {
     T k43h;      // (4 alpha / 3) / h^2: beta' = 1 + k43h (S_B - 6 B_c)
     T inv2k23;   // 1 / (2 k23) (0 when alpha = 0, where it is never used)
     T om1;       // omega - 1: a smoothing update is v + omega (v_root - v)
+    T w6;        // omega / 6: ... = (omega / 6) (S - h^2 L) + (1 - omega) v
+    T omc;       // 1 - omega
 };
 
 template <typename T>
@@ -54,6 +56,8 @@ __host__ __device__ inline CoefT<T> make_coef(double h, double alpha, double ome
     c.k43h = (T)(4.0 * alpha / (3.0 * h * h));
     c.inv2k23 = (T)(alpha > 0.0 ? 3.0 / (4.0 * alpha) : 0.0);
     c.om1 = (T)(omega - 1.0);
+    c.w6 = (T)(omega / 6.0);
+    c.omc = (T)(1.0 - omega);
     return c;
 }
 
@@ -274,8 +278,8 @@ __device__ __forceinline__ T cell_update(const St<T> &s, T rhs, const CoefT<T> &
     stencil_parts(s, S, t, d2);
     const T b = rhs + cf.s8 * d2 + cf.s23 * t;   // rhs + alpha Sigma
     const T L = physical_root(b, cf, clamped);
-    const T v = (S - cf.h2 * L) * (T)(1.0 / 6.0);
-    return cf.om1 != (T)0 ? v + cf.om1 * (v - s.c) : v;
+    const T r6 = S - cf.h2 * L;   // 6 v_root
+    return cf.om1 != (T)0 ? cf.w6 * r6 + cf.omc * s.c : r6 * (T)(1.0 / 6.0);
 }
 
 // op(phi) at the cell = L + alpha((2/3) L^2 - Sigma).
@@ -344,8 +348,8 @@ __device__ __forceinline__ T cell_update_corr(const St<T> &e, const St<T> &B, T 
     // (beta' < 0 needs alpha > 0, so k23 > 0 there)
     const T sq = sqrt(disc);
     const T L = bp >= (T)0 ? (T)2 * b / (bp + sq) : (sq - bp) / ((T)2 * cf.k23);
-    const T v = (pe.S - cf.h2 * L) * (T)(1.0 / 6.0);
-    return cf.om1 != (T)0 ? v + cf.om1 * (v - e.c) : v;
+    const T r6 = pe.S - cf.h2 * L;
+    return cf.om1 != (T)0 ? cf.w6 * r6 + cf.omc * e.c : r6 * (T)(1.0 / 6.0);
 }
 
 // FP32 correction form, the inner sweep of the mixed mode.  The same update as the
@@ -408,8 +412,8 @@ __device__ __forceinline__ float cell_update_corr(const St<float> &e, const St<f
     }
     const float sq = disc > 0.0f ? disc * rsqrtf(disc) : 0.0f;
     const float L = bp >= 0.0f ? __fdividef(2.0f * bq, bp + sq) : (sq - bp) * cf.inv2k23;
-    const float v = (q.S.x - cf.h2 * L) * (1.0f / 6.0f);
-    return cf.om1 != 0.0f ? v + cf.om1 * (v - e.c) : v;
+    const float r6 = q.S.x - cf.h2 * L;
+    return cf.om1 != 0.0f ? cf.w6 * r6 + cf.omc * e.c : r6 * (1.0f / 6.0f);
 }
 
 // op(B + e) - op(B) in FP32: L_e + (2 alpha / 3) L_e (2 L_B + L_e) - alpha (2 Sigma(B, e) + Sigma(e))
