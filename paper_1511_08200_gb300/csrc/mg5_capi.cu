@@ -46,6 +46,7 @@ struct Hier {
     double *tmp[kMaxLevels] = {};  // ping-pong partner
     double *f[kMaxLevels] = {};    // right-hand side
     double *v0[kMaxLevels] = {};   // restricted iterate before the coarse solve
+    double2 *spec[2] = {};         // coarsest-grid DFT work (coarsest side >= kSpectralMinSide)
     size_t bytes = 0;
 };
 
@@ -102,6 +103,8 @@ size_t fp64_bytes(int N)
     size_t b = 2 * (size_t)N * N * N * sizeof(double);  // tmp + f on the finest grid
     for (int l = 1; l < L; ++l)
         b += 4 * (size_t)sz[l] * sz[l] * sz[l] * sizeof(double);
+    if (L > 1 && sz[L - 1] >= kSpectralMinSide)
+        b += 2 * (size_t)sz[L - 1] * sz[L - 1] * sz[L - 1] * sizeof(double2);
     return b;
 }
 
@@ -273,6 +276,9 @@ static void free_hier(mg5_ctx *ctx, Hier *h)
         ctx_free(ctx, h->f[l], b);
         ctx_free(ctx, h->v0[l], b);
     }
+    const int nc = h->n[h->nlev - 1];
+    for (double2 *q : {h->spec[0], h->spec[1]})
+        ctx_free(ctx, q, (size_t)nc * nc * nc * sizeof(double2));
     delete h;
 }
 
@@ -288,6 +294,9 @@ static void free_hier_raw(Hier *h)
         for (void *q : {(void *)h->v[l], (void *)h->tmp[l], (void *)h->f[l], (void *)h->v0[l]})
             if (q)
                 cudaFree(q);
+    for (void *q : {(void *)h->spec[0], (void *)h->spec[1]})
+        if (q)
+            cudaFree(q);
     delete h;
 }
 
@@ -306,6 +315,11 @@ static cudaError_t alloc_hier_raw(int N, Hier **out)
             if (e == cudaSuccess)
                 e = cudaMalloc((void **)q, b);
     }
+    const int nc = h->n[h->nlev - 1];
+    if (e == cudaSuccess && h->nlev > 1 && nc >= kSpectralMinSide)
+        for (double2 **q : {&h->spec[0], &h->spec[1]})
+            if (e == cudaSuccess)
+                e = cudaMalloc((void **)q, (size_t)nc * nc * nc * sizeof(double2));
     if (e != cudaSuccess) {
         free_hier_raw(h);
         return e;
@@ -340,6 +354,11 @@ static int get_hier(mg5_ctx *ctx, int N, Hier **out)
         if (rc == MG5_OK)
             rc = ctx_alloc(ctx, (void **)&h->v0[l], b);
     }
+    const int ncs = h->n[h->nlev - 1];
+    if (rc == MG5_OK && h->nlev > 1 && ncs >= kSpectralMinSide)
+        for (double2 **q : {&h->spec[0], &h->spec[1]})
+            if (rc == MG5_OK)
+                rc = ctx_alloc(ctx, (void **)q, (size_t)ncs * ncs * ncs * sizeof(double2));
     if (rc != MG5_OK) {
         free_hier(ctx, h);
         return rc;
@@ -591,6 +610,12 @@ struct Run64 {
         const CoefT<double> cf = make_coef<double>(hl[l], p->alpha, omega_of(p));
         mg5_ctx *ctx = this->ctx;
         ProfScope ps(&ctx->prof, PK_COARSEST64, st);
+        if (h->spec[0] && h->n[l] >= kSpectralMinSide) {
+            CK(launch_coarsest_spectral<double>(h->v[l], h->tmp[l], h->f[l], h->n[l], cf, ls(l),
+                                                kSpectralIters, &cntb->clamped, &cntb->coarse_sweeps,
+                                                partb, h->spec[0], h->spec[1], st));
+            return MG5_OK;
+        }
         CK(launch_coarsest<double>(h->v[l], h->tmp[l], h->f[l], h->n[l], cf, c(l), p->nu_coarse,
                                    kCoarseRtol, &cntb->clamped, &cntb->coarse_sweeps, st));
         return MG5_OK;

@@ -125,6 +125,16 @@ cudaError_t launch_coarse_rhs(const T *vc, T *fc, const double *m_fine, double *
 template <typename T>
 cudaError_t launch_prolong_add(const T *vc, const T *v0c, int nc, T *vf, double *c_fine,
                                const double *c_coarse, cudaStream_t st);
+// coarsest grids of more than kSpectralMinSide^3 cells (k_spectral.cu): `iters` times the
+// residual, its exact periodic-Laplacian solve by DFT added, two red-black sweeps; w0, w1 are
+// complex work arrays of n^3 (double2 for T = double, float2 for float)
+constexpr int kSpectralMinSide = 7;
+constexpr int kSpectralIters = 4;
+template <typename T>
+cudaError_t launch_coarsest_spectral(T *v, T *tmp, const T *f, int n, CoefT<T> cf, LevelScal *ls,
+                                     int iters, unsigned long long *clamp, int *sweeps,
+                                     double2 *partials, void *w0, void *w1, cudaStream_t st,
+                                     const T *B = nullptr);
 // coarsest grid: sweeps until the residual falls by rtol or nu_max sweeps; one CTA.
 template <typename T>
 cudaError_t launch_coarsest(T *v, T *tmp, const T *f, int n, CoefT<T> cf, double *cptr, int nu_max,

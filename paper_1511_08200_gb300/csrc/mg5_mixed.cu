@@ -127,6 +127,13 @@ struct RunMix {
     int coarsest(int l)
     {
         ProfScope ps(sh.prof, PK_COARSEST32, st);
+        if (h->spec[0] && h->n[l] >= kSpectralMinSide) {
+            const cudaError_t e = launch_coarsest_spectral<float>(
+                h->e[l], h->etmp[l], h->f[l], h->n[l], make_coef<float>(hl[l], p->alpha, omega_of(p)),
+                ls(l), kSpectralIters, &sh.cnt->clamped, &sh.cnt->coarse_sweeps, sh.partials,
+                h->spec[0], h->spec[1], st, h->B[l]);
+            return e == cudaSuccess ? MG5_OK : fail("coarsest32", e);
+        }
         cudaError_t e = launch_coarsest<float>(h->e[l], h->etmp[l], h->f[l], h->n[l],
                                                make_coef<float>(hl[l], p->alpha, omega_of(p)), c(l),
                                                p->nu_coarse, kCoarseRtol, &sh.cnt->clamped,
@@ -217,6 +224,8 @@ size_t mixed_bytes(int N)
     size_t b = n3 * sizeof(double) + 4 * n3 * sizeof(float);
     for (int l = 1; l < L; ++l)
         b += 5 * (size_t)sz[l] * sz[l] * sz[l] * sizeof(float);
+    if (L > 1 && sz[L - 1] >= kSpectralMinSide)
+        b += 2 * (size_t)sz[L - 1] * sz[L - 1] * sz[L - 1] * sizeof(float2);
     return b;
 }
 
@@ -236,6 +245,8 @@ void free_mixed(MixedHier *m, size_t *held)
         fr(m->f[l]);
         fr(m->e0[l]);
     }
+    fr(m->spec[0]);
+    fr(m->spec[1]);
     *held -= m->bytes;
     delete m;
 }
@@ -265,6 +276,11 @@ int alloc_mixed(int N, size_t budget, size_t *held, MixedHier **out, std::string
         if (e == cudaSuccess && l > 0)
             e = cudaMalloc((void **)&m->e0[l], b);
     }
+    const int nc = m->n[m->nlev - 1];
+    if (e == cudaSuccess && m->nlev > 1 && nc >= kSpectralMinSide)
+        for (float2 **q : {&m->spec[0], &m->spec[1]})
+            if (e == cudaSuccess)
+                e = cudaMalloc((void **)q, (size_t)nc * nc * nc * sizeof(float2));
     if (e != cudaSuccess) {
         cudaGetLastError();
         *err = std::string("cudaMalloc: ") + cudaGetErrorString(e);

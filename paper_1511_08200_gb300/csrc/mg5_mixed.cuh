@@ -24,6 +24,7 @@ struct MixedHier {
     float *etmp[kMixMaxLevels] = {};    // ping-pong partner
     float *f[kMixMaxLevels] = {};       // right-hand side of the correction equation
     float *e0[kMixMaxLevels] = {};      // restricted correction before the coarse solve
+    float2 *spec[2] = {};               // coarsest-grid DFT work (coarsest side >= kSpectralMinSide)
     size_t bytes = 0;
 };
 

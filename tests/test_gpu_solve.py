@@ -433,3 +433,19 @@ def test_relaxation_weight_same_solution(ctx, prec, w, tol, bar):
         assert ib.cycles < ia.cycles
     with pytest.raises(mg.MG5Error):
         ctx.solve_fifth_force(d, mg.default_params(alpha=alpha, s=s, h=h, omega=2.0))
+
+
+@pytest.mark.parametrize("n,prec,tol,bar", [(144, "fp64", 1e-10, 1e-9), (176, "mixed", 1e-8, 1e-6)])
+def test_spectral_coarsest_grid(ctx, n, prec, tol, bar):
+    """Sides 16 x odd stop halving at a coarsest grid of (2 x odd)^3 (here 18^3 and 22^3), which
+    the coarsest solve handles with its DFT-preconditioned iteration: the solve converges in a
+    V-cycle count like the power-of-two sizes' and matches the oracle."""
+    alpha, s, h = nominal()
+    delta = workload.lognormal_delta(n, 1.5, 51)
+    phi, _, info = _solve(ctx, delta, alpha, s, h, tol, precision=prec, grad=False)
+    assert info.status == 0
+    assert info.coarsest_n == 2 * (n // 16) > 6
+    assert info.rel_residual <= tol
+    assert info.cycles <= (10 if prec == "fp64" else 12)
+    ref, _ = oracle.solve(delta, alpha, s, h, tol=1e-11)
+    assert rel_l2(phi, ref) <= bar
