@@ -237,7 +237,7 @@ class Step:
             else:
                 _, _, i64 = ctx.solve_fifth_force_host(host_io["delta"], self.p64,
                                                        phi=host_io["phi"], grad=host_io["grad"],
-                                                       stream=s1, fmg=True)
+                                                       stream=s1, fmg=True, graph=self.graph)
                 self.phi.copy_(host_io["phi"], non_blocking=True)
                 self.d_p.copy_(host_io["patch"], non_blocking=True)
             ev[1].record(s1)

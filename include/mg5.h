@@ -71,7 +71,8 @@ extern "C" {
                              device-controlled WHILE node, with its own hierarchy and staging
                              buffers, and replays it (copy in, launch, copy out, one sync): the same
                              kernels as the host-driven solve, without a host round trip per cycle.
-                             Not with MG5_WARM or MG5_HOST_IO; MG5_FP64 needs nu1 + nu2 even and
+                             Not with MG5_WARM (with MG5_HOST_IO the host buffers are staged in and
+                             out around the replay); MG5_FP64 needs nu1 + nu2 even and
                              N with two grids or more (MG5_E_ARG otherwise). */
 
 typedef struct mg5_ctx mg5_ctx;  /* opaque; owns the device hierarchy, resident between calls */

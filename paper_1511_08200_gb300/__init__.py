@@ -363,12 +363,13 @@ class Context:
         return phi, grad, Info._from(info)
 
     def solve_fifth_force_host(self, delta, params: Params, phi=None, grad=None, warm=False,
-                               stream=None, raise_on_status=True, fmg=False):
+                               stream=None, raise_on_status=True, fmg=False, graph=False):
         """Same call with HOST buffers (numpy float64 or pinned CPU tensors): the
-        library copies delta in and phi / grad out (MG5_HOST_IO)."""
+        library copies delta in and phi / grad out (MG5_HOST_IO); graph=True replays
+        the captured solve between the copies (MG5_GRAPH)."""
         n = int(delta.shape[0])
         info = _Info()
-        flags = HOST_IO | (WARM if warm else 0) | (FMG_START if fmg else 0)
+        flags = HOST_IO | (WARM if warm else 0) | (FMG_START if fmg else 0) | (GRAPH if graph else 0)
         rc = _lib.mg5_solve_fifth_force(self._h, _host_ptr(delta), n, ctypes.byref(params), flags,
                                         _host_ptr(phi), _host_ptr(grad), ctypes.byref(info),
                                         _stream(stream))

@@ -1089,7 +1089,7 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
     RET(check_params(p));
     if (flags & ~(MG5_WARM | MG5_HOST_IO | MG5_FMG | MG5_GRAPH))
         return MG5_E_ARG;
-    if ((flags & MG5_GRAPH) && (flags & (MG5_WARM | MG5_HOST_IO)))
+    if ((flags & MG5_GRAPH) && (flags & MG5_WARM))
         return MG5_E_ARG;
     if ((flags & MG5_GRAPH) && p->precision == MG5_FP64) {
         int sz[kMaxLevels];
@@ -1126,6 +1126,11 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
         status = solve_graph(ctx, d_delta, N, p, d_phi, d_grad, (flags & MG5_FMG) != 0, info, st);
         if (status == MG5_E_CUDA || status == MG5_E_ARG || status == MG5_E_OOM)
             return status;
+        if (flags & MG5_HOST_IO) {
+            CK(cudaMemcpyAsync(phi, d_phi, fb, cudaMemcpyDeviceToHost, st));
+            if (grad)
+                CK(cudaMemcpyAsync(grad, d_grad, 3 * fb, cudaMemcpyDeviceToHost, st));
+        }
         CK(cudaEventRecord(ctx->ev1, st));
         CK(ctx_wait(ctx, st));
         if (info) {

@@ -147,6 +147,17 @@ def test_host_io_equals_device_path(ctx):
     ctx.solve_fifth_force_host(delta, p, phi=phi_h, grad=grad_h)
     assert np.array_equal(phi_h, host(phi_d))
     assert rel_l2(grad_h, oracle.force(phi_h, h)) < 1e-13
+    # host buffers around a graph replay (FP64 and mixed): the device path's values
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-8)):
+        q = mg.default_params(alpha=alpha, s=s, h=h, tol=tol, precision=prec)
+        ref, _, iref = ctx.solve_fifth_force(dev(delta), q, fmg=prec == "fp64")
+        for _ in range(2):
+            ph = np.zeros_like(delta)
+            gh = np.zeros((3,) + delta.shape)
+            _, _, ig = ctx.solve_fifth_force_host(delta, q, phi=ph, grad=gh, fmg=prec == "fp64",
+                                                  graph=True)
+            assert np.array_equal(ph, host(ref)) and ig.cycles == iref.cycles
+            assert rel_l2(gh, oracle.force(ph, h)) < 1e-13
 
 
 def test_status_codes(ctx):
