@@ -20,6 +20,9 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
   force              pinned: closed form on Fourier modes
   refine_interpolate pinned: constants, linear fields, 1-D closed form
   relax_patch        pinned: manufactured Dirichlet solution
+  relax_patch_masked pinned: all-ones mask = relax_patch, empty mask = identity, a box
+                     mask = relax_patch of the sub-box, alpha = 0 = sparse direct solve
+  parent_force_mask  pinned: hand-placed parents (wrap included), constant ratios
 """
 from __future__ import annotations
 
@@ -75,6 +78,9 @@ def _load():
     lib.or_relax_patch.argtypes = [P, P, d, d, d, d, d, i, i, P, P]
     lib.or_relax_patch.restype = i
     lib.or_patch_sweep.argtypes = [P, P, d, P, d, d]
+    lib.or_parent_force_mask.argtypes = [P, P, i, P, P, d, P]
+    lib.or_relax_patch_masked.argtypes = [P, P, d, d, d, d, P, d, i, i, P, P]
+    lib.or_relax_patch_masked.restype = i
     lib.or_clamped.restype = ll
     _lib = lib
     return lib
@@ -261,6 +267,31 @@ def relax_patch(delta_f, phi_box, alpha, s, h, c, tol=1e-10, max_sweeps=200000, 
     rel = np.zeros(1)
     nsw = _load().or_relax_patch(_p(delta_f), _p(pf), alpha, s, h, c, tol, max_sweeps, check,
                                  _p(out), _p(rel))
+    return out, int(nsw), float(rel[0])
+
+
+def parent_force_mask(grad_phi, grad_gr, origin, pn, theta) -> np.ndarray:
+    """Sec. 3.3 parent criterion: uint8 mask of the (2 pn) fine interior, 1 where
+    |grad(phi)/2| > theta |grad(Psi_GR)| at the parent cell (SoA gradients, 3 x Nc^3)."""
+    grad_phi, grad_gr = _f64(grad_phi), _f64(grad_gr)
+    nc = grad_phi.shape[-1]
+    o, pn_ = _i3(origin), _i3(pn)
+    out = np.empty(tuple(2 * int(x) for x in pn_), dtype=np.uint8)
+    _load().or_parent_force_mask(_p(grad_phi), _p(grad_gr), nc, _p(o), _p(pn_), theta, _p(out))
+    return out
+
+
+def relax_patch_masked(delta_f, phi_box, mask, alpha, s, h, c, tol=1e-10, max_sweeps=200000,
+                       check=10):
+    """relax_patch iterating only the cells with mask != 0; returns (phi_box, sweeps, rel)."""
+    delta_f = _f64(delta_f)
+    out = _f64(phi_box).copy()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    assert m.shape == delta_f.shape
+    pf = _i3(delta_f.shape)
+    rel = np.zeros(1)
+    nsw = _load().or_relax_patch_masked(_p(delta_f), _p(pf), alpha, s, h, c, _p(m), tol,
+                                        max_sweeps, check, _p(out), _p(rel))
     return out, int(nsw), float(rel[0])
 
 

@@ -662,9 +662,12 @@ void or_refine_cubic(const double *phic, int nc, const int o[3], const int pn[3]
 /*
  * One snapshot red-black sweep on the interior of a box with a ghost shell
  * of width 1: dims d = pf + 2.  Colour is the parity of the interior index.
+ * mask (interior-indexed, may be NULL = every cell): cells with mask 0 are
+ * not relaxed and keep their values (Sec. 3.3: iterations on some cells of a
+ * level only).
  */
 static void patch_sweep(double *phi, const double *f, double c, const int d[3], double h,
-                        double alpha)
+                        double alpha, const unsigned char *mask)
 {
     size_t nc = (size_t)d[0] * d[1] * d[2];
     double *snap = (double *)malloc(nc * sizeof(double));
@@ -679,6 +682,8 @@ static void patch_sweep(double *phi, const double *f, double c, const int d[3], 
                         continue;
                     size_t bq = ((size_t)i * d[1] + j) * d[2] + k;
                     size_t iq = ((size_t)(i - 1) * (d[1] - 2) + (j - 1)) * (d[2] - 2) + (k - 1);
+                    if (mask && !mask[iq])
+                        continue;
                     phi[bq] = cell_update(&sf, i, j, k, h, alpha, f[iq] + c);
                 }
     }
@@ -726,7 +731,7 @@ int or_relax_patch(const double *delta_f, const int pf[3], double alpha, double 
         if (rel <= tol || sweeps >= max_sweeps || !isfinite(rel))
             break;
         for (int q = 0; q < check && sweeps < max_sweeps; ++q, ++sweeps)
-            patch_sweep(phi, f, c, d, h, alpha);
+            patch_sweep(phi, f, c, d, h, alpha, NULL);
     }
     if (rel_out)
         *rel_out = rel;
@@ -740,7 +745,85 @@ void or_patch_sweep(double *phi, const double *f, double c, const int pf[3], dou
                     double alpha)
 {
     int d[3] = {pf[0] + 2, pf[1] + 2, pf[2] + 2};
-    patch_sweep(phi, f, c, d, h, alpha);
+    patch_sweep(phi, f, c, d, h, alpha, NULL);
+}
+
+/* ------------------------------------------------------------------ */
+/* position-dependent truncation (Sec. 3.3)                            */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The parent criterion of Sec. 3.3: a fine cell of a refinement is iterated
+ * only while the fifth force on its parent (the coarse cell that was refined)
+ * is still large compared with normal gravity.  F5 = grad(phi)/2 (Sec. 3.2),
+ * F_GR = grad(Psi_GR); both by central differences on the periodic coarse grid
+ * (or_force layout: SoA, 3 blocks of Nc^3).  The patch covers coarse cells
+ * [o, o + pn) per axis (wrapping); fine interior cell (I, J, K) of the
+ * (2 pn)^3 interior has parent (o + I/2, o + J/2, o + K/2) mod Nc.
+ *   mask = 1  where |F5| > theta |F_GR| at the parent, else 0
+ * (no division: a parent with F_GR = 0 is iterated if F5 != 0).
+ */
+void or_parent_force_mask(const double *grad_phi, const double *grad_gr, int nc,
+                          const int o[3], const int pn[3], double theta, unsigned char *mask)
+{
+    size_t n3 = (size_t)nc * nc * nc;
+    int P[3] = {2 * pn[0], 2 * pn[1], 2 * pn[2]};
+    for (int I = 0; I < P[0]; ++I)
+        for (int J = 0; J < P[1]; ++J)
+            for (int K = 0; K < P[2]; ++K) {
+                size_t pc = pidx(nc, wrap(o[0] + I / 2, nc), wrap(o[1] + J / 2, nc),
+                                 wrap(o[2] + K / 2, nc));
+                double f5 = 0.0, fg = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    double x = 0.5 * grad_phi[a * n3 + pc], y = grad_gr[a * n3 + pc];
+                    f5 += x * x;
+                    fg += y * y;
+                }
+                mask[((size_t)I * P[1] + J) * P[2] + K] = sqrt(f5) > theta * sqrt(fg) ? 1 : 0;
+            }
+}
+
+/*
+ * or_relax_patch with iterations on the cells of `mask` only (Sec. 3.3): the
+ * cells with mask 0 keep their entry values (the interpolated coarse phi) and
+ * act, like the ghost shell, as fixed values for their iterated neighbours.
+ * The residual and the source norm are taken over the iterated cells:
+ * sweeps until ||r||_mask <= tol ||s delta_f||_mask.  Returns the sweeps made.
+ */
+int or_relax_patch_masked(const double *delta_f, const int pf[3], double alpha, double s,
+                          double h, double c, const unsigned char *mask, double tol,
+                          int max_sweeps, int check, double *phi, double *rel_out)
+{
+    int d[3] = {pf[0] + 2, pf[1] + 2, pf[2] + 2};
+    size_t ni = (size_t)pf[0] * pf[1] * pf[2];
+    double *f = (double *)malloc(ni * sizeof(double));
+    double *fm = (double *)malloc(ni * sizeof(double));
+    double *r = (double *)malloc(ni * sizeof(double));
+    for (size_t q = 0; q < ni; ++q) {
+        f[q] = s * delta_f[q];
+        fm[q] = mask[q] ? f[q] : 0.0;
+    }
+    double fn = norm2(fm, ni);
+    int sweeps = 0;
+    double rel = INFINITY;
+    g_clamped = 0;
+    for (;;) {
+        or_patch_residual(phi, f, c, pf, h, alpha, r);
+        for (size_t q = 0; q < ni; ++q)
+            if (!mask[q])
+                r[q] = 0.0;
+        rel = fn > 0.0 ? norm2(r, ni) / fn : norm2(r, ni);
+        if (rel <= tol || sweeps >= max_sweeps || !isfinite(rel))
+            break;
+        for (int q = 0; q < check && sweeps < max_sweeps; ++q, ++sweeps)
+            patch_sweep(phi, f, c, d, h, alpha, mask);
+    }
+    if (rel_out)
+        *rel_out = rel;
+    free(f);
+    free(fm);
+    free(r);
+    return sweeps;
 }
 
 long long or_clamped(void)

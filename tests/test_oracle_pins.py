@@ -496,3 +496,133 @@ def test_patch_sweep_snapshot_semantics():
         base[p] = phi1[p]
         lhs = _pins.op_matrix_box(base, h, alpha)[tuple(q - 1 for q in p)]
         assert lhs == pytest.approx(f[tuple(q - 1 for q in p)] + c, abs=1e-12)
+
+
+# --------------------------------------------------------------------------
+# position-dependent truncation (Sec. 3.3): masked patch relaxation, parent mask
+# --------------------------------------------------------------------------
+
+def _masked_case(pf, seed, h=0.5, alpha=0.08, s=1.5, c=0.02):
+    rng = np.random.default_rng(seed)
+    dims = tuple(x + 2 for x in pf)
+    box = 0.05 * rng.standard_normal(dims)
+    delta = 0.2 * rng.standard_normal(pf)
+    return box, delta, h, alpha, s, c
+
+
+def test_relax_patch_masked_all_ones_is_relax_patch():
+    box, delta, h, alpha, s, c = _masked_case((8, 10, 6), 11)
+    ones = np.ones(delta.shape, np.uint8)
+    a, na, ra = oracle.relax_patch(delta, box, alpha, s, h, c, tol=1e-9)
+    b, nb, rb = oracle.relax_patch_masked(delta, box, ones, alpha, s, h, c, tol=1e-9)
+    assert na == nb and ra == rb
+    assert np.array_equal(a, b)
+
+
+def test_relax_patch_masked_empty_mask_is_identity():
+    box, delta, h, alpha, s, c = _masked_case((6, 6, 8), 12)
+    out, nsw, rel = oracle.relax_patch_masked(delta, box, np.zeros(delta.shape, np.uint8),
+                                              alpha, s, h, c, tol=1e-9)
+    assert nsw == 0 and rel == 0.0
+    assert np.array_equal(out, box)
+
+
+def test_relax_patch_masked_box_is_sub_patch():
+    """A mask that is one sub-box [a, b) of the interior relaxes exactly as that sub-box
+    solved as its own patch, its ghost shell the surrounding (fixed) cells; the offset a has
+    an even sum so the red-black colours agree."""
+    pf = (12, 10, 14)
+    box, delta, h, alpha, s, c = _masked_case(pf, 13)
+    a, b = (1, 3, 2), (9, 9, 12)
+    mask = np.zeros(pf, np.uint8)
+    mask[a[0]:b[0], a[1]:b[1], a[2]:b[2]] = 1
+    out, nsw, rel = oracle.relax_patch_masked(delta, box, mask, alpha, s, h, c, tol=1e-10)
+    sub_box = box[a[0]:b[0] + 2, a[1]:b[1] + 2, a[2]:b[2] + 2]
+    sub_delta = delta[a[0]:b[0], a[1]:b[1], a[2]:b[2]]
+    ref, nref, rref = oracle.relax_patch(sub_delta, sub_box, alpha, s, h, c, tol=1e-10)
+    assert nsw == nref and rel == rref and nsw > 0
+    assert np.array_equal(out[a[0]:b[0] + 2, a[1]:b[1] + 2, a[2]:b[2] + 2], ref)
+    keep = np.ones(box.shape, bool)
+    keep[a[0] + 1:b[0] + 1, a[1] + 1:b[1] + 1, a[2] + 1:b[2] + 1] = False
+    assert np.array_equal(out[keep], box[keep])
+
+
+def test_relax_patch_masked_linear_matches_sparse_direct_solve():
+    """alpha = 0: the masked problem is the 7-point Poisson equation on the masked cells
+    with every other cell a known value; scipy's sparse direct solve gives it exactly."""
+    sp = pytest.importorskip("scipy.sparse")
+    spla = pytest.importorskip("scipy.sparse.linalg")
+    pf = (8, 8, 10)
+    box, delta, h, _, s, c = _masked_case(pf, 14)
+    rng = np.random.default_rng(15)
+    mask = (rng.random(pf) < 0.55).astype(np.uint8)
+    out, nsw, rel = oracle.relax_patch_masked(delta, box, mask, 0.0, s, h, c, tol=1e-13)
+    assert rel <= 1e-13
+    act = np.argwhere(mask != 0)
+    idx = -np.ones(pf, int)
+    idx[tuple(act.T)] = np.arange(len(act))
+    rows, cols, vals = [], [], []
+    rhs = (s * delta[tuple(act.T)] + c) * h * h
+    for r, p in enumerate(act):
+        rows.append(r); cols.append(r); vals.append(-6.0)
+        for d in range(3):
+            for sg in (-1, 1):
+                q = p.copy(); q[d] += sg
+                inside = all(0 <= q[e] < pf[e] for e in range(3))
+                if inside and mask[tuple(q)]:
+                    rows.append(r); cols.append(int(idx[tuple(q)])); vals.append(1.0)
+                else:
+                    rhs[r] -= box[tuple(q + 1)]
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(len(act), len(act)))
+    x = spla.spsolve(A, rhs)
+    got = out[1:-1, 1:-1, 1:-1][tuple(act.T)]
+    assert np.abs(got - x).max() < 1e-10 * max(1.0, np.abs(x).max())
+    unmasked = np.ones(box.shape, bool)
+    unmasked[1:-1, 1:-1, 1:-1] = mask != 0
+    assert np.array_equal(out[~unmasked], box[~unmasked])
+
+
+def test_relax_patch_masked_nonlinear_converges_on_mask():
+    pf = (10, 8, 8)
+    box, delta, h, alpha, s, c = _masked_case(pf, 16)
+    rng = np.random.default_rng(17)
+    mask = (rng.random(pf) < 0.4).astype(np.uint8)
+    out, nsw, rel = oracle.relax_patch_masked(delta, box, mask, alpha, s, h, c, tol=1e-11)
+    assert rel <= 1e-11 and nsw > 0
+    r = s * delta + c - _pins.op_matrix_box(out, h, alpha)
+    fm = np.where(mask != 0, s * delta, 0.0)
+    assert np.linalg.norm(np.where(mask != 0, r, 0.0)) <= 1.5e-11 * np.linalg.norm(fm)
+    # the masked-out cells still carry their (nonzero) residual: they were not iterated
+    assert np.linalg.norm(np.where(mask == 0, r, 0.0)) > 1e3 * 1e-11 * np.linalg.norm(fm)
+
+
+def test_parent_force_mask_places_children():
+    """One parent cell with F5/F_GR above theta: exactly its 2x2x2 children are marked,
+    at the fine indices the patch origin puts them (the patch wraps the periodic grid)."""
+    nc, o, pn = 6, (4, 1, 5), (3, 2, 3)
+    gphi = np.zeros((3, nc, nc, nc))
+    ggr = np.ones((3, nc, nc, nc))
+    # |F5| = |grad phi|/2; everywhere ratio 0.1, at coarse cell (0, 2, 0) ratio 0.5
+    gphi[:] = 2 * 0.1
+    gphi[:, 0, 2, 0] = 2 * 0.5
+    m = oracle.parent_force_mask(gphi, ggr, o, pn, 0.3)
+    assert m.shape == (6, 4, 6) and m.dtype == np.uint8
+    # coarse (0, 2, 0) = patch-local (2, 1, 1): 0 = (4 + 2) mod 6, 2 = 1 + 1, 0 = (5 + 1) mod 6
+    want = np.zeros((6, 4, 6), np.uint8)
+    want[4:6, 2:4, 2:4] = 1
+    assert np.array_equal(m, want)
+
+
+def test_parent_force_mask_constant_ratio_and_zero_gravity():
+    nc = 4
+    rng = np.random.default_rng(18)
+    ggr = rng.standard_normal((3, nc, nc, nc))
+    gphi = 2 * 0.25 * ggr[[1, 2, 0]]           # |F5| = 0.25 |F_GR| (components permuted)
+    o, pn = (0, 0, 0), (4, 4, 4)
+    assert oracle.parent_force_mask(gphi, ggr, o, pn, 0.2).all()
+    assert not oracle.parent_force_mask(gphi, ggr, o, pn, 0.3).any()
+    # F_GR = 0: iterated exactly where F5 != 0
+    gphi2 = np.zeros_like(gphi)
+    gphi2[0, 1, 1, 1] = 1e-30
+    m = oracle.parent_force_mask(gphi2, np.zeros_like(ggr), o, pn, 0.5)
+    assert m.sum() == 8 and m[2:4, 2:4, 2:4].all()
