@@ -41,11 +41,14 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile mg_oracle.c into liboracle.so next to it (gcc, -O2, OpenMP)."""
+    """Compile mg_oracle.c into liboracle.so next to it (gcc, -O2, OpenMP).  No contraction
+    into fused multiply-adds: every product and sum is rounded as written, the same on
+    x86 (no FMA at the default target) and on Arm (FMA by default)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(
-            ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+            ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o",
+             tmp, _SRC, "-lm"]
         )
         os.replace(tmp, _LIB)
     return _LIB
@@ -78,7 +81,7 @@ def _load():
     lib.or_relax_patch.argtypes = [P, P, d, d, d, d, d, i, i, P, P]
     lib.or_relax_patch.restype = i
     lib.or_patch_sweep.argtypes = [P, P, d, P, d, d]
-    lib.or_parent_force_mask.argtypes = [P, P, i, P, P, d, P]
+    lib.or_parent_force_mask.argtypes = [P, P, P, i, P, P, d, P]
     lib.or_relax_patch_masked.argtypes = [P, P, d, d, d, d, P, d, i, i, P, P]
     lib.or_relax_patch_masked.restype = i
     lib.or_clamped.restype = ll
@@ -270,14 +273,16 @@ def relax_patch(delta_f, phi_box, alpha, s, h, c, tol=1e-10, max_sweeps=200000, 
     return out, int(nsw), float(rel[0])
 
 
-def parent_force_mask(grad_phi, grad_gr, origin, pn, theta) -> np.ndarray:
+def parent_force_mask(grad_phi, grad_gr, origin, pn, theta, periodic=True) -> np.ndarray:
     """Sec. 3.3 parent criterion: uint8 mask of the (2 pn) fine interior, 1 where
-    |grad(phi)/2| > theta |grad(Psi_GR)| at the parent cell (SoA gradients, 3 x Nc^3)."""
+    |grad(phi)/2| > theta |grad(Psi_GR)| at the parent cell.  Gradients SoA (3, *pd) on the
+    periodic domain (periodic=True) or on a refinement's interior (no wrap)."""
     grad_phi, grad_gr = _f64(grad_phi), _f64(grad_gr)
-    nc = grad_phi.shape[-1]
+    pd = _i3(grad_phi.shape[1:])
     o, pn_ = _i3(origin), _i3(pn)
     out = np.empty(tuple(2 * int(x) for x in pn_), dtype=np.uint8)
-    _load().or_parent_force_mask(_p(grad_phi), _p(grad_gr), nc, _p(o), _p(pn_), theta, _p(out))
+    _load().or_parent_force_mask(_p(grad_phi), _p(grad_gr), _p(pd), 1 if periodic else 0, _p(o),
+                                 _p(pn_), theta, _p(out))
     return out
 
 

@@ -756,23 +756,28 @@ void or_patch_sweep(double *phi, const double *f, double c, const int pf[3], dou
  * The parent criterion of Sec. 3.3: a fine cell of a refinement is iterated
  * only while the fifth force on its parent (the coarse cell that was refined)
  * is still large compared with normal gravity.  F5 = grad(phi)/2 (Sec. 3.2),
- * F_GR = grad(Psi_GR); both by central differences on the periodic coarse grid
- * (or_force layout: SoA, 3 blocks of Nc^3).  The patch covers coarse cells
- * [o, o + pn) per axis (wrapping); fine interior cell (I, J, K) of the
- * (2 pn)^3 interior has parent (o + I/2, o + J/2, o + K/2) mod Nc.
+ * F_GR = grad(Psi_GR); both given on the parent grid as SoA, 3 blocks of
+ * pd[0] x pd[1] x pd[2] (or_force layout).  The parent is the periodic domain
+ * (periodic != 0: indices wrap) or a refinement's interior (periodic = 0).
+ * The refinement covers parent cells [o, o + pn) per axis; fine interior cell
+ * (I, J, K) of the (2 pn) interior has parent (o + I/2, o + J/2, o + K/2).
  *   mask = 1  where |F5| > theta |F_GR| at the parent, else 0
  * (no division: a parent with F_GR = 0 is iterated if F5 != 0).
  */
-void or_parent_force_mask(const double *grad_phi, const double *grad_gr, int nc,
-                          const int o[3], const int pn[3], double theta, unsigned char *mask)
+void or_parent_force_mask(const double *grad_phi, const double *grad_gr, const int pd[3],
+                          int periodic, const int o[3], const int pn[3], double theta,
+                          unsigned char *mask)
 {
-    size_t n3 = (size_t)nc * nc * nc;
+    size_t n3 = (size_t)pd[0] * pd[1] * pd[2];
     int P[3] = {2 * pn[0], 2 * pn[1], 2 * pn[2]};
     for (int I = 0; I < P[0]; ++I)
         for (int J = 0; J < P[1]; ++J)
             for (int K = 0; K < P[2]; ++K) {
-                size_t pc = pidx(nc, wrap(o[0] + I / 2, nc), wrap(o[1] + J / 2, nc),
-                                 wrap(o[2] + K / 2, nc));
+                int c[3] = {o[0] + I / 2, o[1] + J / 2, o[2] + K / 2};
+                if (periodic)
+                    for (int a = 0; a < 3; ++a)
+                        c[a] = wrap(c[a], pd[a]);
+                size_t pc = ((size_t)c[0] * pd[1] + c[1]) * pd[2] + c[2];
                 double f5 = 0.0, fg = 0.0;
                 for (int a = 0; a < 3; ++a) {
                     double x = 0.5 * grad_phi[a * n3 + pc], y = grad_gr[a * n3 + pc];

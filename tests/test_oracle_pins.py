@@ -621,8 +621,26 @@ def test_parent_force_mask_constant_ratio_and_zero_gravity():
     o, pn = (0, 0, 0), (4, 4, 4)
     assert oracle.parent_force_mask(gphi, ggr, o, pn, 0.2).all()
     assert not oracle.parent_force_mask(gphi, ggr, o, pn, 0.3).any()
+    # a refinement's interior as the parent (no wrap): the window of the periodic case
+    m_per = oracle.parent_force_mask(gphi, ggr, (1, 0, 1), (2, 3, 3), 0.2 * 1.0)
+    m_box = oracle.parent_force_mask(gphi, ggr, (1, 0, 1), (2, 3, 3), 0.2, periodic=False)
+    assert np.array_equal(m_per, m_box)
     # F_GR = 0: iterated exactly where F5 != 0
     gphi2 = np.zeros_like(gphi)
     gphi2[0, 1, 1, 1] = 1e-30
     m = oracle.parent_force_mask(gphi2, np.zeros_like(ggr), o, pn, 0.5)
     assert m.sum() == 8 and m[2:4, 2:4, 2:4].all()
+
+
+def test_parent_force_mask_box_parent_places_children():
+    """A non-cubic refinement interior (5 x 6 x 7) as the parent: the children of a hand-placed
+    parent (3, 1, 4) of the window starting at (2, 0, 3) sit at fine (2:4, 2:4, 2:4)."""
+    pd = (5, 6, 7)
+    gphi = np.full((3,) + pd, 2 * 0.1)
+    ggr = np.ones((3,) + pd)
+    gphi[:, 3, 1, 4] = 2 * 0.5
+    gphi[:, 4, 5, 6] = 2 * 0.5          # outside the window: must not appear
+    m = oracle.parent_force_mask(gphi, ggr, (2, 0, 3), (3, 2, 4), 0.3, periodic=False)
+    want = np.zeros((6, 4, 8), np.uint8)
+    want[2:4, 2:4, 2:4] = 1
+    assert np.array_equal(m, want)
