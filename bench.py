@@ -241,6 +241,7 @@ class Step:
                 self.phi.copy_(host_io["phi"], non_blocking=True)
                 self.d_p.copy_(host_io["patch"], non_blocking=True)
             ev[1].record(s1)
+            self.compat_c = i64.compat_c
             ctx.refine_interpolate(self.phi, self.origin, (PN, PN, PN), 1, out=self.box, stream=s1)
             ctx.force(self.box, H_COARSE / 2, ghost=1, periodic=False, grad=self.g_tr, stream=s1)
             ev[2].record(s1)
@@ -385,6 +386,11 @@ def run_ours(args):
     out["geff"] = geff_report(step)
     if not args.no_truncation_levels:
         try:
+            out["masked_truncation"] = masked_truncation_report(step)
+        except mg.MG5Error as e:   # reported, not fatal to the bench line
+            out["masked_truncation"] = {"error": str(e)}
+    if not args.no_truncation_levels:
+        try:
             out["truncation_levels"] = truncation_levels_report(mg, torch, dev)
         except mg.MG5Error as e:   # reported, not fatal to the bench line
             out["truncation_levels"] = {"error": str(e)}
@@ -419,6 +425,7 @@ def geff_report(step):
     g_gr = torch.empty_like(step.g_full)
     ctx.force(box, H_COARSE / 2, ghost=1, periodic=False, grad=g_gr)
     torch.cuda.synchronize()
+    step.g_gr_dom, step.g_gr_patch = g_psi, g_gr      # reused by masked_truncation_report
     mag = lambda g: torch.linalg.vector_norm(g, dim=0)
     r_dom = 0.5 * mag(step.grad) / mag(g_psi)
     r_full = 0.5 * mag(step.g_full) / mag(g_gr)
@@ -449,6 +456,65 @@ def geff_report(step):
             "gr_cycles": ig.cycles}
 
 
+def masked_truncation_report(step, quantiles=(0.25, 0.5, 0.75, 0.9), reps=3):
+    """Position-dependent truncation (Sec. 3.3) on the refinement workload (once, outside
+    the timed region): the 64^3 patch iterates a fine cell only where its parent's
+    F5/F_GR (domain grid, F5 = grad(phi)/2, F_GR from the alpha = 0 solve of geff_report)
+    exceeds theta; the other cells keep the interpolated phi.  Per theta (quantiles of the
+    ratio over the patch's parents): masked fraction, V-cycles, device time of the masked
+    relaxation (library events, best of `reps`) against the full relaxation, and the force
+    error against the fully relaxed patch: eps_trunc = |F5 - F5_full| / |F5_full| and the
+    G_eff error |F5 - F5_full| / |F_GR| (Eq. errors2)."""
+    mg, torch, ctx = step.mg, step.torch, step.ctx
+    pn = (PN, PN, PN)
+    hf = H_COARSE / 2
+    mag = lambda g: torch.linalg.vector_norm(g, dim=0)
+    ratio = 0.5 * mag(step.grad) / mag(step.g_gr_dom)
+    n = ratio.shape[0]
+    idx = [torch.arange(step.origin[a], step.origin[a] + PN, device=ratio.device) % n for a in range(3)]
+    par = ratio[idx[0]][:, idx[1]][:, :, idx[2]].flatten()
+    box0 = torch.empty_like(step.box)
+    ctx.refine_interpolate(step.phi, step.origin, pn, 1, out=box0)
+    g_full, g_gr = step.g_full, step.g_gr_patch
+    nf = float(torch.linalg.vector_norm(g_full))
+
+    def run(mask):
+        best, info, out = float("inf"), None, None
+        for _ in range(reps):
+            out = box0.clone()
+            if mask is None:
+                _, info = ctx.relax_patch(step.d_p, step.ppatch, step.compat_c, out)
+            else:
+                _, info = ctx.relax_patch_masked(step.d_p, mask, step.ppatch, step.compat_c, out)
+            best = min(best, info.ms_total)
+        return out, info, best
+
+    _, ifull, ms_full = run(None)
+    rows = []
+    for q in quantiles:
+        theta = float(torch.quantile(par.float(), q))
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        mask, cnt = ctx.parent_force_mask(step.grad, step.g_gr_dom, step.origin, pn, theta,
+                                          count=True)
+        t1.record()
+        torch.cuda.synchronize()
+        out, info, ms = run(mask)
+        g = ctx.force(out, hf, ghost=1, periodic=False)
+        d5 = 0.5 * mag(g - g_full)
+        dge = (d5 / mag(g_gr)).flatten()
+        qq = torch.quantile(dge[::7].float(), torch.tensor([0.5, 0.99], device=dge.device))
+        rows.append({"theta": theta, "theta_over_linear": theta * 3.0 * step.beta,
+                     "masked_fraction": cnt / float((2 * PN) ** 3), "cycles": info.cycles,
+                     "ms": ms, "mask_ms": t0.elapsed_time(t1),
+                     "eps_trunc_rel_l2": float(torch.linalg.vector_norm(g - g_full)) / nf,
+                     "geff_error_p50_p99_max": [float(qq[0]), float(qq[1]), float(dge.max())]})
+    eps_tr = float(torch.linalg.vector_norm(step.g_tr - g_full)) / nf
+    return {"patch": [2 * PN] * 3, "full_ms": ms_full, "full_cycles": ifull.cycles,
+            "all_truncated_eps_rel_l2": eps_tr, "by_theta": rows}
+
+
 def nested_chain(ctx, mg, torch, d_levels, origins, spacings, phi_dom, alpha, s, compat_c, T, tol):
     """phi on every refinement of a nested hierarchy: relaxed (mg5_relax_patch) on levels
     < T, the coarse-to-fine interpolant of its parent (mg5_refine_interpolate[_box]) on levels
@@ -465,6 +531,36 @@ def nested_chain(ctx, mg, torch, d_levels, origins, spacings, phi_dom, alpha, s,
             ctx.relax_patch(d_levels[lev], p, compat_c, box)
         boxes.append(box)
     return boxes
+
+
+def masked_chain(ctx, mg, torch, d_levels, origins, spacings, phi_dom, g5_dom, ggr, alpha, s,
+                 compat_c, theta, tol):
+    """The position-dependent truncation of Sec. 3.3 on a nested hierarchy: on every level
+    l >= 1 a fine cell is relaxed only where its parent's F5/F_GR exceeds theta
+    (mg5_parent_force_mask on the parent's forces: the periodic domain for l = 1, the
+    parent refinement's interior below; ggr[l] the GR force vectors per level), the other
+    cells keep the interpolated parent phi (mg5_relax_patch_masked; an empty mask skips the
+    relaxation, a full one runs the unmasked one).  Returns (boxes, masked fraction per level)."""
+    boxes, fracs = [None], []
+    g_par = g5_dom
+    for lev in range(1, len(d_levels)):
+        pn = (int(d_levels[lev].shape[0]) // 2,) * 3
+        if lev == 1:
+            box = ctx.refine_interpolate(phi_dom, origins[1], pn, 1)
+        else:
+            box = ctx.refine_interpolate_box(boxes[lev - 1], 1, origins[lev], pn, 1)
+        mask, cnt = ctx.parent_force_mask(g_par, ggr[lev - 1], origins[lev], pn, theta,
+                                          periodic=(lev == 1), count=True)
+        ncell = 8 * pn[0] * pn[1] * pn[2]
+        p = mg.default_params(alpha=alpha, s=s, h=spacings[lev], tol=tol, max_cycles=200)
+        if cnt == ncell:
+            ctx.relax_patch(d_levels[lev], p, compat_c, box)
+        elif cnt > 0:
+            ctx.relax_patch_masked(d_levels[lev], mask, p, compat_c, box)
+        fracs.append(cnt / float(ncell))
+        boxes.append(box)
+        g_par = ctx.force(box, spacings[lev], ghost=1, periodic=False)
+    return boxes, fracs
 
 
 def truncation_levels_report(mg, torch, dev, n_dom=128, levels=4, pn=16):
@@ -489,7 +585,8 @@ def truncation_levels_report(mg, torch, dev, n_dom=128, levels=4, pn=16):
     force = lambda b, h: ctx.force(b, h, ghost=1, periodic=False)
     gr = nested_chain(ctx, mg, torch, d, origins, spacings, psi, 0.0, s_gr, ig.compat_c,
                       levels + 1, tol)
-    f_gr = [None] + [mag(force(gr[l], spacings[l])) for l in range(1, levels + 1)]
+    ggr = [ctx.force(psi, spacings[0])] + [force(gr[l], spacings[l]) for l in range(1, levels + 1)]
+    f_gr = [None] + [mag(ggr[l]) for l in range(1, levels + 1)]
     chains, ms = {}, {}
     for T in (levels + 1, 1, 2, 4):
         torch.cuda.synchronize()
@@ -517,6 +614,25 @@ def truncation_levels_report(mg, torch, dev, n_dom=128, levels=4, pn=16):
         out["geff_error_p50_p99"][key] = [q(mag(chains[T][l] - full[l]) / f_gr[l])
                                          for l in range(1, levels + 1)]
     out["chain_ms"]["full"] = ms[levels + 1]
+    # position-dependent truncation (Sec. 3.3): thresholds as fractions of the linear ratio
+    g5_dom = ctx.force(phi, spacings[0])
+    out["masked"] = {}
+    for frac in (0.97, 0.93, 0.85):
+        theta = frac / (3.0 * beta)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        boxes, fr = masked_chain(ctx, mg, torch, d, origins, spacings, phi, g5_dom, ggr, alpha, s,
+                                 i5.compat_c, theta, tol)
+        g5 = [None] + [0.5 * force(boxes[l], spacings[l]) for l in range(1, levels + 1)]
+        e1.record()
+        e1.synchronize()
+        out["masked"]["theta=%.2f/(3beta)" % frac] = {
+            "chain_ms": e0.elapsed_time(e1), "masked_fraction_by_level": fr,
+            "eps_trunc_rel_l2": [float(torch.linalg.vector_norm(g5[l] - full[l])
+                                       / torch.linalg.vector_norm(full[l]))
+                                 for l in range(1, levels + 1)],
+            "geff_error_p50_p99": [q(mag(g5[l] - full[l]) / f_gr[l]) for l in range(1, levels + 1)]}
     ctx.close()
     return out
 

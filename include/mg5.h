@@ -275,6 +275,46 @@ int mg5_relax_patch_graph(mg5_ctx *ctx, const double *delta_fine, const int pf[3
                           mg5_info *info, void *stream);
 
 /*
+ * Position-dependent truncation (Sec. 3.3, the criterion proposed for screening
+ * that does not follow the refinement): iterate a fine cell only while the
+ * fifth force on its parent cell is still large.
+ *
+ * mg5_parent_force_mask builds the mask of a refinement from the parent level:
+ *   grad_phi, grad_gr: gradients of phi and of the GR potential Psi_GR on the
+ *            parent grid of dims pd, SoA 3 x pd[0] x pd[1] x pd[2] FP64 (device;
+ *            the layout mg5_force writes, for the periodic domain or, with
+ *            ghost = 1, for the interior of a refinement's box).
+ *   periodic: != 0: the parent is the periodic domain (indices wrap;
+ *            0 <= o < pd, 1 <= pn <= pd); 0: a refinement's interior
+ *            (0 <= o, o + pn <= pd).
+ *   o, pn:   the refinement covers parent cells [o, o + pn) per axis.
+ *   theta:   threshold on |F5| / |F_GR|, F5 = grad(phi)/2 (Sec. 3.2), >= 0.
+ *   mask:    out, (2 pn[0]) x (2 pn[1]) x (2 pn[2]) bytes (device), C order:
+ *            1 where |F5| > theta |F_GR| at the cell's parent (compared without
+ *            division: a parent with F_GR = 0 counts as large when F5 != 0),
+ *            else 0.
+ *   count:   if not NULL, out: the number of 1 entries (synchronises `stream`).
+ *
+ * mg5_relax_patch_masked is mg5_relax_patch iterating only the cells whose
+ * mask byte is nonzero:
+ *   mask: pf[0]*pf[1]*pf[2] bytes (device), interior-indexed like delta_fine.
+ * Cells with mask 0 keep the values phi_fine holds on entry (the interpolated
+ * parent phi) and act as fixed values for their iterated neighbours, like the
+ * ghost shell.  Convergence: ||r|| <= tol ||s delta_fine|| with both norms over
+ * the masked cells (an empty mask returns at once with 0 cycles).  The V-cycle
+ * keeps a mask per grid: a coarse cell is relaxed only if all 8 of its children
+ * are, residuals of unmasked cells restrict as zero and corrections reach masked
+ * cells only.  Same other arguments, errors and synchronisation as
+ * mg5_relax_patch; info->cell_updates counts every interior cell the sweeps visit.
+ */
+int mg5_parent_force_mask(mg5_ctx *ctx, const double *grad_phi, const double *grad_gr,
+                          const int pd[3], int periodic, const int o[3], const int pn[3],
+                          double theta, unsigned char *mask, long long *count, void *stream);
+int mg5_relax_patch_masked(mg5_ctx *ctx, const double *delta_fine, const int pf[3],
+                           const unsigned char *mask, const mg5_params *p, double compat_c,
+                           double *phi_fine, mg5_info *info, void *stream);
+
+/*
  * Solve many independent boxes in one call (batching).  Box i has side N[i],
  * density delta[i], parameters p[i], output phi[i] and, if grad is not NULL,
  * grad[i] (all device buffers, layouts as in mg5_solve_fifth_force; phi starts

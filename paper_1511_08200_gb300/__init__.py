@@ -114,6 +114,9 @@ _sigs = {
     "mg5_refine_interpolate_box": ([_P, _P, _I3, _c_int, _I3, _I3, _c_int, _P, _P], _c_int),
     "mg5_relax_patch": ([_P, _P, _I3, _P, _c_double, _P, _P, _P], _c_int),
     "mg5_relax_patch_graph": ([_P, _P, _I3, _P, _c_double, _P, _P, _P], _c_int),
+    "mg5_relax_patch_masked": ([_P, _P, _I3, _P, _P, _c_double, _P, _P, _P], _c_int),
+    "mg5_parent_force_mask": ([_P, _P, _P, _I3, _c_int, _I3, _I3, _c_double, _P,
+                               ctypes.POINTER(ctypes.c_longlong), _P], _c_int),
     "mg5_solve_batch": ([_P, _c_int, _P, _P, _P, _P, _P, _P, _P], _c_int),
     "mg5_cached_bytes": ([_P, _c_int, _c_int, _P], _c_int),
     "mg5_graph_cached_bytes": ([_P, _c_int, _P, _c_int, _P], _c_int),
@@ -454,6 +457,40 @@ class Context:
         if raise_on_status:
             self._check(rc, (OK, W_DISC_CLAMP))
         return phi_box, Info._from(info)
+
+    def relax_patch_masked(self, delta_fine, mask, params: Params, compat_c: float, phi_box,
+                           stream=None, raise_on_status=True):
+        """mg5_relax_patch_masked: relax only the cells of `mask` (uint8, shape of delta_fine);
+        the others keep their values (Sec. 3.3)."""
+        pf = [int(x) for x in delta_fine.shape]
+        if tuple(mask.shape) != tuple(pf):
+            raise ValueError("mask must have the shape of delta_fine")
+        info = _Info()
+        rc = _lib.mg5_relax_patch_masked(self._h, _ptr(delta_fine), _I3(*pf), _ptr(mask, "uint8"),
+                                         ctypes.byref(params), compat_c, _ptr(phi_box),
+                                         ctypes.byref(info), _stream(stream))
+        if raise_on_status:
+            self._check(rc, (OK, W_DISC_CLAMP))
+        return phi_box, Info._from(info)
+
+    def parent_force_mask(self, grad_phi, grad_gr, origin, pn, theta: float, periodic=True,
+                          out=None, count=False, stream=None):
+        """mg5_parent_force_mask: uint8 mask of the (2 pn) fine interior, 1 where
+        |grad(phi)/2| > theta |grad(Psi_GR)| at the parent cell (gradients (3, *pd) on the
+        periodic domain, or on a refinement's interior with periodic=False).  Returns the
+        mask, or (mask, number of ones) with count=True."""
+        import torch
+        pd = [int(x) for x in grad_phi.shape[1:]]
+        dims = [2 * int(p) for p in pn]
+        if out is None:
+            out = torch.empty(dims, dtype=torch.uint8, device=grad_phi.device)
+        n = ctypes.c_longlong(0)
+        self._check(_lib.mg5_parent_force_mask(self._h, _ptr(grad_phi), _ptr(grad_gr), _I3(*pd),
+                                               1 if periodic else 0, _I3(*origin), _I3(*pn),
+                                               theta, _ptr(out, "uint8"),
+                                               ctypes.byref(n) if count else None,
+                                               _stream(stream)))
+        return (out, int(n.value)) if count else out
 
     # ------------------------------------------------------------ single steps
     def step_sweep(self, phi_in, f, c: float, h: float, alpha: float, out=None, stream=None):

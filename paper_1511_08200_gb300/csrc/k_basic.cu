@@ -865,10 +865,12 @@ cudaError_t launch_refine_box(const double *box, const int bd[3], int pg, const 
 // --------------------------------------------------------------------------
 // Dirichlet patch: interior pf, box pf + 2, colour = parity of the interior index.
 // --------------------------------------------------------------------------
+// MASKED: interior cells with mask 0 are not relaxed (they keep their values)
+template <bool MASKED>
 __global__ void k_patch_half(const double *__restrict__ src_faces, const double *__restrict__ src_edges,
                              double *dst, const double *__restrict__ fint, double rhs_add, int p0,
                              int p1, int p2, CoefT<double> cf, int colour, int copy_other,
-                             unsigned long long *clamp)
+                             unsigned long long *clamp, const unsigned char *__restrict__ mask)
 {
     const long long total = (long long)p0 * p1 * p2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -880,7 +882,8 @@ __global__ void k_patch_half(const double *__restrict__ src_faces, const double 
     const int d1 = p1 + 2, d2 = p2 + 2;
     const Rows r = box_rows(d1, d2, i + 1, j + 1);
     const int K = k + 1;
-    if (((i + j + k) & 1) != colour) {
+    // the red pass (copy_other) carries every cell it does not relax into dst
+    if (((i + j + k) & 1) != colour || (MASKED && !mask[t])) {
         if (copy_other)
             dst[r.r00 + K] = src_faces[r.r00 + K];
         return;
@@ -895,20 +898,27 @@ __global__ void k_patch_half(const double *__restrict__ src_faces, const double 
 
 cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint, double rhs_add,
                                const int pf[3], CoefT<double> cf, unsigned long long *clamp,
-                               cudaStream_t st, const double *v0, double w)
+                               cudaStream_t st, const double *v0, double w,
+                               const unsigned char *mask)
 {
     const long long work = (long long)pf[0] * pf[1] * pf[2];
     const int g = blocks_for(work);
+    auto half = [&](const double *faces, int colour, int copy_other) {
+        if (mask)
+            k_patch_half<true><<<g, kBlock, 0, st>>>(faces, in, out, fint, rhs_add, pf[0], pf[1],
+                                                     pf[2], cf, colour, copy_other, clamp, mask);
+        else
+            k_patch_half<false><<<g, kBlock, 0, st>>>(faces, in, out, fint, rhs_add, pf[0], pf[1],
+                                                      pf[2], cf, colour, copy_other, clamp, mask);
+    };
     // red: from in (all), black copied; black: faces from out (new red), edges from in (old black)
-    k_patch_half<<<g, kBlock, 0, st>>>(in, in, out, fint, rhs_add, pf[0], pf[1], pf[2], cf, 0, 1,
-                                       clamp);
+    half(in, 0, 1);
     if (v0) {
         cudaError_t e = launch_pbox_ghost_refresh(out, v0, pf, w, st);
         if (e != cudaSuccess)
             return e;
     }
-    k_patch_half<<<g, kBlock, 0, st>>>(out, in, out, fint, rhs_add, pf[0], pf[1], pf[2], cf, 1, 0,
-                                       clamp);
+    half(out, 1, 0);
     if (v0) {
         cudaError_t e = launch_pbox_ghost_refresh(out, v0, pf, w, st);
         if (e != cudaSuccess)
@@ -918,14 +928,17 @@ cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint
     return cudaGetLastError();
 }
 
+template <bool MASKED>
 __global__ void k_patch_residual(const double *__restrict__ phi, const double *__restrict__ fint,
                                  double rhs_add, int p0, int p1, int p2, CoefT<double> cf,
-                                 double2 *__restrict__ partials)
+                                 double2 *__restrict__ partials, const unsigned char *__restrict__ mask)
 {
     const long long total = (long long)p0 * p1 * p2;
     double2 acc = make_double2(0.0, 0.0);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
+        if (MASKED && !mask[t])
+            continue;
         const int k = (int)(t % p2);
         const long long q = t / p2;
         const int j = (int)(q % p1), i = (int)(q / p1);
@@ -943,13 +956,18 @@ __global__ void k_patch_residual(const double *__restrict__ phi, const double *_
 
 cudaError_t launch_patch_residual(const double *phi, const double *fint, double rhs_add,
                                   const int pf[3], CoefT<double> cf, double2 *partials, int *nblocks,
-                                  cudaStream_t st)
+                                  cudaStream_t st, const unsigned char *mask)
 {
     const long long work = (long long)pf[0] * pf[1] * pf[2];
     int g = blocks_for(work);
     if (g > kReduceGrid)
         g = kReduceGrid;
-    k_patch_residual<<<g, kBlock, 0, st>>>(phi, fint, rhs_add, pf[0], pf[1], pf[2], cf, partials);
+    if (mask)
+        k_patch_residual<true><<<g, kBlock, 0, st>>>(phi, fint, rhs_add, pf[0], pf[1], pf[2], cf,
+                                                     partials, mask);
+    else
+        k_patch_residual<false><<<g, kBlock, 0, st>>>(phi, fint, rhs_add, pf[0], pf[1], pf[2], cf,
+                                                      partials, mask);
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();

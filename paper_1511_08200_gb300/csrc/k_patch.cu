@@ -31,11 +31,14 @@ __device__ __forceinline__ long long bidx(int i, int j, int k, int d1, int d2)
 }
 
 // residual of the 8 interior children of each coarse interior cell, restricted
-// with v onto the coarse box interior (vc and v0c) and into fc (interior-indexed)
+// with v onto the coarse box interior (vc and v0c) and into fc (interior-indexed).
+// MASKED: the residual of a child with mask 0 (not iterated) counts as zero.
+template <bool MASKED>
 __global__ void k_pbox_resid_restrict(const double *__restrict__ v, const double *__restrict__ f,
                                       int p0, int p1, int p2, CoefT<double> cf,
                                       double *__restrict__ vc, double *__restrict__ v0c,
-                                      double *__restrict__ fc, double2 *__restrict__ partials)
+                                      double *__restrict__ fc, double2 *__restrict__ partials,
+                                      const unsigned char *__restrict__ mask)
 {
     const int q0 = p0 >> 1, q1 = p1 >> 1, q2 = p2 >> 1;
     const long long total = (long long)q0 * q1 * q2;
@@ -51,7 +54,8 @@ __global__ void k_pbox_resid_restrict(const double *__restrict__ v, const double
             const Rows r = box_rows(p1 + 2, p2 + 2, i + 1, j + 1);
             St<double> s;
             gather(v, v, r, k + 1, k + 2, k, s);
-            const double res = f[((long long)i * p1 + j) * p2 + k] - cell_op(s, cf);
+            const long long fi = ((long long)i * p1 + j) * p2 + k;
+            const double res = (MASKED && !mask[fi]) ? 0.0 : f[fi] - cell_op(s, cf);
             sv += s.c;
             sr += res;
             acc.x += res;
@@ -86,13 +90,16 @@ __global__ void k_pbox_coarse_rhs(const double *__restrict__ vc, double *__restr
 
 // fine interior += trilinear interpolation of (vc - v0c), ghosts included (the
 // ghost correction is the extrapolated boundary value kept by the refresh).
+// MASKED: cells with mask 0 keep their values.
+template <bool MASKED>
 __global__ void k_pbox_prolong(const double *__restrict__ vc, const double *__restrict__ v0c, int q0,
-                               int q1, int q2, double *__restrict__ vf)
+                               int q1, int q2, double *__restrict__ vf,
+                               const unsigned char *__restrict__ mask)
 {
     const int p0 = 2 * q0, p1 = 2 * q1, p2 = 2 * q2;
     const long long total = (long long)p0 * p1 * p2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total)
+    if (t >= total || (MASKED && !mask[t]))
         return;
     const int k = (int)(t % p2);
     const long long q = t / p2;
@@ -193,14 +200,17 @@ __global__ void k_pbox_ghost_refresh(double *__restrict__ v, const double *__res
 
 // Coarsest patch grid, one CTA: before each sweep the residual norm; stop at
 // rtol times the first one or after nu_max sweeps.  A -> B (red) -> A (black).
-// Boxes up to kPboxSmemCells cells run in shared memory.
+// Boxes up to kPboxSmemCells cells run in shared memory.  MASKED: cells with mask 0
+// are neither relaxed nor counted in the residual norm.
 constexpr int kPboxSmemCells = 1024;
 constexpr int kPboxThreads = 512;   // 128 registers a thread: stencil offsets stay in registers
 
+template <bool MASKED>
 __global__ void __launch_bounds__(kPboxThreads)
     k_pbox_coarsest(double *A, double *B, const double *__restrict__ f, int p0, int p1, int p2,
                     CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
-                    int *sweeps_out, const double *__restrict__ v0, double w)
+                    int *sweeps_out, const double *__restrict__ v0, double w,
+                    const unsigned char *__restrict__ mask)
 {
     extern __shared__ __align__(16) unsigned char pb_raw[];
     __shared__ double bc_s;
@@ -248,6 +258,7 @@ __global__ void __launch_bounds__(kPboxThreads)
         // colour, f and the ghost-refresh terms once (the same values as the loop below)
         const int p = threadIdx.x;
         const bool mine = p < n3;
+        const bool active = mine && (!MASKED || mask[p]);
         Nbr nb{};
         int colour_me = 0, cbox = 0;
         double fme = 0.0;
@@ -289,7 +300,7 @@ __global__ void __launch_bounds__(kPboxThreads)
         };
         for (; it < nu_max; ++it) {
             double2 acc = make_double2(0.0, 0.0);
-            if (mine) {
+            if (active) {
                 St<double> s;
                 gather_nbr((const double *)a, nb, s);
                 const double res = fme - cell_op(s, cf);
@@ -309,7 +320,7 @@ __global__ void __launch_bounds__(kPboxThreads)
                 const double *src = colour == 0 ? a : b;
                 double *dst = colour == 0 ? b : a;
                 if (mine) {
-                    if (colour_me != colour) {
+                    if (colour_me != colour || !active) {
                         dst[cbox] = src[cbox];
                     } else {
                         St<double> s;
@@ -329,6 +340,8 @@ __global__ void __launch_bounds__(kPboxThreads)
     for (; it < nu_max; ++it) {
         double2 acc = make_double2(0.0, 0.0);
         for (int p = threadIdx.x; p < n3; p += blockDim.x) {
+            if (MASKED && !mask[p])
+                continue;
             const int k = p % p2, j = (p / p2) % p1, i = p / (p1 * p2);
             const Rows r = box_rows(d1, d2, i + 1, j + 1);
             St<double> s;
@@ -352,7 +365,7 @@ __global__ void __launch_bounds__(kPboxThreads)
             for (int p = threadIdx.x; p < n3; p += blockDim.x) {
                 const int k = p % p2, j = (p / p2) % p1, i = p / (p1 * p2);
                 const Rows r = box_rows(d1, d2, i + 1, j + 1);
-                if (((i + j + k) & 1) != colour) {
+                if (((i + j + k) & 1) != colour || (MASKED && !mask[p])) {
                     dst[r.r00 + k + 1] = src[r.r00 + k + 1];
                     continue;
                 }
@@ -380,13 +393,19 @@ __global__ void __launch_bounds__(kPboxThreads)
 
 cudaError_t launch_pbox_resid_restrict(const double *v, const double *f, const int p[3],
                                        CoefT<double> cf, double *vc, double *v0c, double *fc,
-                                       double2 *partials, int *nblocks, cudaStream_t st)
+                                       double2 *partials, int *nblocks, cudaStream_t st,
+                                       const unsigned char *mask)
 {
     const long long work = (long long)(p[0] / 2) * (p[1] / 2) * (p[2] / 2);
     int g = blocks_for(work);
     if (g > kMaxPartials)
         g = kMaxPartials;
-    k_pbox_resid_restrict<<<g, kBlock, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc, v0c, fc, partials);
+    if (mask)
+        k_pbox_resid_restrict<true><<<g, kBlock, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc, v0c, fc,
+                                                          partials, mask);
+    else
+        k_pbox_resid_restrict<false><<<g, kBlock, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc, v0c, fc,
+                                                           partials, mask);
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();
@@ -402,10 +421,15 @@ cudaError_t launch_pbox_coarse_rhs(const double *vc, double *fc, const int q[3],
 }
 
 cudaError_t launch_pbox_prolong(const double *vc, const double *v0c, const int q[3], double *vf,
-                                cudaStream_t st)
+                                cudaStream_t st, const unsigned char *mask)
 {
     const long long work = 8ll * q[0] * q[1] * q[2];
-    k_pbox_prolong<<<blocks_for(work), kBlock, 0, st>>>(vc, v0c, q[0], q[1], q[2], vf);
+    if (mask)
+        k_pbox_prolong<true><<<blocks_for(work), kBlock, 0, st>>>(vc, v0c, q[0], q[1], q[2], vf,
+                                                                  mask);
+    else
+        k_pbox_prolong<false><<<blocks_for(work), kBlock, 0, st>>>(vc, v0c, q[0], q[1], q[2], vf,
+                                                                   mask);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -421,7 +445,8 @@ cudaError_t launch_pbox_ghosts(const double *fine_box, const int p[3], double *g
 
 cudaError_t launch_pbox_coarsest(double *A, double *B, const double *f, const int p[3],
                                  CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
-                                 int *sweeps, cudaStream_t st, const double *v0, double w)
+                                 int *sweeps, cudaStream_t st, const double *v0, double w,
+                                 const unsigned char *mask)
 {
     const int n3 = p[0] * p[1] * p[2];
     const int nbox = (p[0] + 2) * (p[1] + 2) * (p[2] + 2);
@@ -429,8 +454,12 @@ cudaError_t launch_pbox_coarsest(double *A, double *B, const double *f, const in
     if (threads > kPboxThreads)
         threads = kPboxThreads;
     const size_t sm = nbox <= kPboxSmemCells ? (size_t)4 * nbox * sizeof(double) : 0;
-    k_pbox_coarsest<<<1, threads, sm, st>>>(A, B, f, p[0], p[1], p[2], cf, nu_max, rtol, clamp,
-                                            sweeps, v0, w);
+    if (mask)
+        k_pbox_coarsest<true><<<1, threads, sm, st>>>(A, B, f, p[0], p[1], p[2], cf, nu_max, rtol,
+                                                      clamp, sweeps, v0, w, mask);
+    else
+        k_pbox_coarsest<false><<<1, threads, sm, st>>>(A, B, f, p[0], p[1], p[2], cf, nu_max, rtol,
+                                                       clamp, sweeps, v0, w, mask);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -59,6 +59,7 @@ struct PatchHier {
     double *tmp[kMaxLevels] = {};
     double *v0[kMaxLevels] = {};   // boxes, l >= 1
     double *f[kMaxLevels] = {};    // interior-indexed right-hand sides
+    unsigned char *mk[kMaxLevels] = {};   // coarse masks (l >= 1) of masked relaxations, lazily
     size_t bytes = 0;
 };
 
@@ -379,8 +380,21 @@ static void free_patch(mg5_ctx *ctx, PatchHier *h)
         }
         ctx_free(ctx, h->tmp[l], bb);
         ctx_free(ctx, h->f[l], ib);
+        if (h->mk[l])
+            ctx_free(ctx, h->mk[l], int_cells(h->q[l]));
     }
     delete h;
+}
+
+// the coarse masks of a context-owned patch hierarchy (allocated on first use)
+static int get_patch_masks(mg5_ctx *ctx, PatchHier *h)
+{
+    for (int l = 1; l < h->nlev; ++l)
+        if (!h->mk[l]) {
+            RET(ctx_alloc(ctx, (void **)&h->mk[l], int_cells(h->q[l])));
+            h->bytes += int_cells(h->q[l]);
+        }
+    return MG5_OK;
 }
 
 // A patch hierarchy owned by a captured graph (plain allocations, counted by the entry).
@@ -1288,6 +1302,8 @@ struct RunPatch {
     LevelScal *lsp = nullptr;
     SolveCounters *cntb = nullptr;
     double2 *partb = nullptr;
+    // masked relaxation (Sec. 3.3): the caller's mask on grid 0, its restrictions below
+    const unsigned char *mk[kMaxLevels] = {};
 
     void bind_ctx_scratch()
     {
@@ -1312,7 +1328,7 @@ struct RunPatch {
             ProfScope ps(&ctx->prof, l == 0 ? PK_PATCH_SWEEP : PK_PATCH_SWEEPC, st, cells);
             CK(launch_patch_sweep(h->v[l], h->tmp[l], h->f[l], 0.0, h->q[l],
                                   make_coef<double>(hl[l], p->alpha, omega_of(p)), &cntb->clamped, st,
-                                  l > 0 ? h->v0[l] : nullptr, l > 0 ? ghost_w(l) : 0.0));
+                                  l > 0 ? h->v0[l] : nullptr, l > 0 ? ghost_w(l) : 0.0, mk[l]));
         }
         std::swap(h->v[l], h->tmp[l]);
         cu += (long long)cells;
@@ -1326,7 +1342,7 @@ struct RunPatch {
         CK(launch_pbox_coarsest(h->v[l], h->tmp[l], h->f[l], h->q[l],
                                 make_coef<double>(hl[l], p->alpha, omega_of(p)), p->nu_coarse, kCoarseRtol,
                                 &cntb->clamped, &cntb->coarse_sweeps, st,
-                                l > 0 ? h->v0[l] : nullptr, l > 0 ? ghost_w(l) : 0.0));
+                                l > 0 ? h->v0[l] : nullptr, l > 0 ? ghost_w(l) : 0.0, mk[l]));
         return MG5_OK;
     }
 
@@ -1338,7 +1354,7 @@ struct RunPatch {
             ProfScope ps(&ctx->prof, PK_PATCH_RESID, st, (double)int_cells(h->q[l]));
             CK(launch_pbox_resid_restrict(h->v[l], h->f[l], h->q[l],
                                           make_coef<double>(hl[l], p->alpha), h->v[l + 1],
-                                          h->v0[l + 1], h->f[l + 1], partb, &nb, st));
+                                          h->v0[l + 1], h->f[l + 1], partb, &nb, st, mk[l]));
         }
         if (finalize)
             CK(launch_finalize(partb, nb, (double)int_cells(h->q[l]), lsp,
@@ -1358,7 +1374,7 @@ struct RunPatch {
             RET(sweep(l));
         RET(resid_restrict(l, false));
         RET(coarse_visit(l + 1));
-        CK(launch_pbox_prolong(h->v[l + 1], h->v0[l + 1], h->q[l + 1], h->v[l], st));
+        CK(launch_pbox_prolong(h->v[l + 1], h->v0[l + 1], h->q[l + 1], h->v[l], st, mk[l]));
         for (int s = 0; s < p->nu2; ++s)
             RET(sweep(l));
         return MG5_OK;
@@ -1367,8 +1383,10 @@ struct RunPatch {
 
 }  // namespace
 
-int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const mg5_params *p,
-                    double compat_c, double *phi, mg5_info *info, void *stream)
+// The host-driven patch relaxation; mask (device, interior-indexed) or nullptr for every cell.
+static int relax_patch_impl(mg5_ctx *ctx, const double *delta_f, const int pf[3],
+                            const unsigned char *mask, const mg5_params *p, double compat_c,
+                            double *phi, mg5_info *info, void *stream)
 {
     if (!ctx || !delta_f || !pf || !phi)
         return MG5_E_ARG;
@@ -1384,6 +1402,8 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
         std::memset(info, 0, sizeof(*info));
     PatchHier *h = nullptr;
     RET(get_patch(ctx, pf, &h));
+    if (mask)
+        RET(get_patch_masks(ctx, h));
     const long long ni = (long long)int_cells(pf);
     const long long nbox = (long long)box_cells(pf);
     CK(cudaEventRecord(ctx->ev0, st));
@@ -1391,8 +1411,14 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
     CK(cudaMemsetAsync(ls, 0, sizeof(LevelScal), st));
     CK(cudaMemsetAsync(ctx->cnt, 0, sizeof(SolveCounters), st));
     int nb = 0;
-    // f0 = s delta + c; the tolerance is relative to ||s delta||
-    CK(launch_scale(delta_f, p->s, h->f[0], ni, ctx->partials, &nb, st, compat_c));
+    // f0 = s delta + c; the tolerance is relative to ||s delta|| (over the masked cells)
+    if (mask) {
+        CK(launch_scale_masked(delta_f, p->s, h->f[0], ni, mask, ctx->partials, &nb, st, compat_c));
+        for (int l = 1; l < h->nlev; ++l)
+            CK(launch_mask_restrict(l == 1 ? mask : h->mk[l - 1], h->q[l - 1], h->mk[l], st));
+    } else {
+        CK(launch_scale(delta_f, p->s, h->f[0], ni, ctx->partials, &nb, st, compat_c));
+    }
     CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_FNORM, st));
     // the ping-pong partner of the caller's box carries the same ghost shell
     CK(cudaMemcpyAsync(h->tmp[0], phi, nbox * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1415,6 +1441,11 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
         ctx->err = "relax_patch: context scratch not allocated";
         return MG5_E_ARG;
     }
+    if (mask) {
+        R.mk[0] = mask;
+        for (int l = 1; l < h->nlev; ++l)
+            R.mk[l] = h->mk[l];
+    }
     for (int l = 0; l < h->nlev; ++l)
         R.hl[l] = p->h * (double)(1 << l);
     int status = MG5_E_NOT_CONVERGED;
@@ -1424,7 +1455,7 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
         if (h->nlev == 1) {
             RET(R.coarsest(0));
             CK(launch_patch_residual(h->v[0], h->f[0], 0.0, pf, make_coef<double>(p->h, p->alpha),
-                                     ctx->partials, &nb, st));
+                                     ctx->partials, &nb, st, mask));
             CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_NORM, st));
         } else {
             for (int s = 0; s < p->nu1; ++s)
@@ -1459,7 +1490,7 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
         if (h->nlev == 1)
             continue;
         RET(R.coarse_visit(1));
-        CK(launch_pbox_prolong(h->v[1], h->v0[1], h->q[1], h->v[0], st));
+        CK(launch_pbox_prolong(h->v[1], h->v0[1], h->q[1], h->v[0], st, mask));
         for (int s = 0; s < p->nu2; ++s)
             RET(R.sweep(0));
     }
@@ -1486,6 +1517,52 @@ int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const 
         info->compat_c = compat_c;
     }
     return status;
+}
+
+int mg5_relax_patch(mg5_ctx *ctx, const double *delta_f, const int pf[3], const mg5_params *p,
+                    double compat_c, double *phi, mg5_info *info, void *stream)
+{
+    return relax_patch_impl(ctx, delta_f, pf, nullptr, p, compat_c, phi, info, stream);
+}
+
+int mg5_relax_patch_masked(mg5_ctx *ctx, const double *delta_f, const int pf[3],
+                           const unsigned char *mask, const mg5_params *p, double compat_c,
+                           double *phi, mg5_info *info, void *stream)
+{
+    if (!mask)
+        return MG5_E_ARG;
+    return relax_patch_impl(ctx, delta_f, pf, mask, p, compat_c, phi, info, stream);
+}
+
+int mg5_parent_force_mask(mg5_ctx *ctx, const double *grad_phi, const double *grad_gr,
+                          const int pd[3], int periodic, const int o[3], const int pn[3],
+                          double theta, unsigned char *mask, long long *count, void *stream)
+{
+    if (!ctx || !grad_phi || !grad_gr || !pd || !o || !pn || !mask || !(theta >= 0.0) ||
+        !std::isfinite(theta))
+        return MG5_E_ARG;
+    for (int a = 0; a < 3; ++a) {
+        if (pd[a] < 1 || pn[a] < 1 || o[a] < 0)
+            return MG5_E_ARG;
+        if (periodic ? (o[a] >= pd[a] || pn[a] > pd[a]) : ((long long)o[a] + pn[a] > pd[a]))
+            return MG5_E_ARG;
+    }
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *dcount = nullptr;
+    if (count) {
+        dcount = &ctx->cnt->clamped;   // the counters are free between solves on this stream
+        CK(cudaMemsetAsync(dcount, 0, sizeof(*dcount), st));
+    }
+    CK(launch_parent_force_mask(grad_phi, grad_gr, pd, periodic, o, pn, theta, mask, dcount, st));
+    if (count) {
+        CK(cudaMemcpyAsync(ctx->h_rel, dcount, sizeof(*dcount), cudaMemcpyDeviceToHost, st));
+        CK(ctx_wait(ctx, st));
+        unsigned long long c = 0;
+        std::memcpy(&c, ctx->h_rel, sizeof(c));
+        *count = (long long)c;
+    }
+    return MG5_OK;
 }
 
 static size_t patch_entry_bytes(const int pf[3], size_t hier_bytes)

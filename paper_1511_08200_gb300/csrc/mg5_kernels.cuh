@@ -165,30 +165,50 @@ cudaError_t launch_refine_box(const double *box, const int bd[3], int pg, const 
                               const int pn[3], int ghost, double *fine, cudaStream_t st);
 // Dirichlet patch (interior pf, box pf + 2): one full sweep in -> out (out must hold the ghosts).
 // With v0 (coarse patch grids) the ghosts of out are refreshed after each half-sweep by the
-// extrapolated boundary condition of weight w (k_patch.cu).
+// extrapolated boundary condition of weight w (k_patch.cu).  mask (interior-indexed, optional):
+// cells with mask 0 are not relaxed and keep their values.
 cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint, double rhs_add,
                                const int pf[3], CoefT<double> cf, unsigned long long *clamp,
-                               cudaStream_t st, const double *v0 = nullptr, double w = 0.0);
-// partial sums (r, r^2) of r = fint + rhs_add - op(phi) over the interior
+                               cudaStream_t st, const double *v0 = nullptr, double w = 0.0,
+                               const unsigned char *mask = nullptr);
+// partial sums (r, r^2) of r = fint + rhs_add - op(phi) over the interior (the cells of mask)
 cudaError_t launch_patch_residual(const double *phi, const double *fint, double rhs_add,
                                   const int pf[3], CoefT<double> cf, double2 *partials, int *nblocks,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const unsigned char *mask = nullptr);
 
 // ---- Dirichlet patch multigrid (k_patch.cu); p = fine interior dims, q = coarse interior dims
+// mask (fine, optional): the residual of cells with mask 0 counts as zero
 cudaError_t launch_pbox_resid_restrict(const double *v, const double *f, const int p[3],
                                        CoefT<double> cf, double *vc, double *v0c, double *fc,
-                                       double2 *partials, int *nblocks, cudaStream_t st);
+                                       double2 *partials, int *nblocks, cudaStream_t st,
+                                       const unsigned char *mask = nullptr);
 cudaError_t launch_pbox_coarse_rhs(const double *vc, double *fc, const int q[3], CoefT<double> cf,
                                    cudaStream_t st);
+// mask (fine, optional): only cells with mask != 0 take the correction
 cudaError_t launch_pbox_prolong(const double *vc, const double *v0c, const int q[3], double *vf,
-                                cudaStream_t st);
+                                cudaStream_t st, const unsigned char *mask = nullptr);
 cudaError_t launch_pbox_ghosts(const double *fine_box, const int p[3], double *g1, double *g2,
                                double *g3, cudaStream_t st);
 cudaError_t launch_pbox_coarsest(double *A, double *B, const double *f, const int p[3],
                                  CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
                                  int *sweeps, cudaStream_t st, const double *v0 = nullptr,
-                                 double w = 0.0);
+                                 double w = 0.0, const unsigned char *mask = nullptr);
 cudaError_t launch_pbox_ghost_refresh(double *v, const double *v0, const int q[3], double w,
                                       cudaStream_t st);
+
+// ---- position-dependent truncation (k_mask.cu)
+// coarse mask (interior q = p/2) = 1 where all 8 children have mask != 0
+cudaError_t launch_mask_restrict(const unsigned char *mf, const int p[3], unsigned char *mc,
+                                 cudaStream_t st);
+// f = s delta + add on every cell; partial sums (0, (s delta)^2) over the cells of mask
+cudaError_t launch_scale_masked(const double *delta, double s, double *f, long long n,
+                                const unsigned char *mask, double2 *partials, int *nblocks,
+                                cudaStream_t st, double add);
+// mask of the (2 pn) fine interior: |grad phi / 2| > theta |grad Psi_GR| at the parent cell
+// (parent grid of dims pd, periodic or a refinement's interior)
+cudaError_t launch_parent_force_mask(const double *grad_phi, const double *grad_gr, const int pd[3],
+                                     int periodic, const int o[3], const int pn[3], double theta,
+                                     unsigned char *mask, unsigned long long *count,
+                                     cudaStream_t st);
 
 }  // namespace mg5
