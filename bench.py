@@ -192,7 +192,10 @@ class Step:
         self.box_full = torch.empty_like(self.box)
         self.g_tr = torch.empty((3,) + (pf,) * 3, dtype=f64, device=dev)
         self.g_full = torch.empty_like(self.g_tr)
-        self.p64 = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE, tol=TOL64)
+        # V(3,1): with the over-relaxed smoother it reaches 1e-10 in 5 cycles instead of V(2,2)'s
+        # 6 (time to tolerance 12% lower at 128^3; the paper fixes no cycle shape)
+        self.p64 = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE, tol=TOL64, nu1=3,
+                                     nu2=1)
         self.pmix = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE, tol=TOLMIX,
                                       precision="mixed")
         self.ppatch = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE / 2, tol=TOL64)

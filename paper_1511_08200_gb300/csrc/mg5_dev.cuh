@@ -219,13 +219,15 @@ __device__ __forceinline__ void stencil_parts(const St<T> &s, T &S, T &t, T &d2)
 // FP32 inner solve of the mixed mode needs ~1e-6, not correct rounding).
 // FP64: GB300 executes FP64 at 1/64 of the FP32 rate, and the IEEE square root
 // and divide sequences would be ~40% of the cell's FP64 instructions.  The root
-// is instead estimated in FP32 and refined by two Newton steps of the quadratic
+// is instead estimated in FP32 and refined by one Newton step of the quadratic
 // q(L) = (2 alpha/3) L^2 + L - b (the update of Eq. newton) in FP64, with the
-// FP32 reciprocal of q'(L) held fixed: the relative error goes ~1e-7 -> ~1e-14
-// -> below FP64 rounding.  The branch tests also run in FP32: the FP32
-// discriminant is within ~1e-7 of the FP64 one, so df >= 4e-3 guarantees the
-// FP64 discriminant is above 1e-3, where Newton converges as stated; below it
-// (near the double root, or clamped) the closed form runs in FP64.
+// FP32 reciprocal of q'(L) held fixed.  With e the estimate's error (~3e-7 of L)
+// the step leaves |1 - q'(L) r| e + (2 alpha/3) e^2 / q', q' = sqrt(disc): about
+// 3e-7 (6e-8 + 1.5e-7 |q' - 1| / q') of L, 2e-14 for q' near 1 and at most 1e-13 for
+// q' >= 0.5; a cell's update then moves phi by that fraction of h^2 L / 6, far below
+// the solves' tolerances.  The branch test runs in FP32 (the FP32 discriminant is
+// within ~1e-7 of the FP64 one): below df = 0.25 (q' < 0.5: strongly nonlinear cells,
+// near the double root, or clamped) the closed form runs in FP64 instead.
 __device__ __forceinline__ float physical_root(float b, float k8, bool &clamped)
 {
     float disc = fmaf(k8, b, 1.0f);
@@ -253,7 +255,7 @@ __device__ __forceinline__ double physical_root(double b, const CoefT<double> &c
 #else
     const float bf = (float)b;
     const float df = fmaf(cf.k8f, bf, 1.0f);
-    if (df < 4e-3f) {
+    if (df < 0.25f) {
         const double disc = fma(cf.k8, b, 1.0);
         if (disc < 0.0) {
             clamped = true;
@@ -263,10 +265,8 @@ __device__ __forceinline__ double physical_root(double b, const CoefT<double> &c
     }
     const float Lf = __fdividef(2.0f * bf, 1.0f + sqrtf(df));
     const double r = (double)__frcp_rn(fmaf(cf.k43f, Lf, 1.0f));
-    double L = (double)Lf;
-    L = fma(-fma(fma(cf.k23, L, 1.0), L, -b), r, L);
-    L = fma(-fma(fma(cf.k23, L, 1.0), L, -b), r, L);
-    return L;
+    const double L = (double)Lf;
+    return fma(-fma(fma(cf.k23, L, 1.0), L, -b), r, L);
 #endif
 }
 
