@@ -61,20 +61,48 @@ __device__ __forceinline__ Ring ring(int q)
     return Ring{m, z, z == K - 1 ? 0 : z + 1};
 }
 
-// issue the 16-byte copies of plane q (rows j0-2 .. j0+17, k0-4 .. k0+35)
+// The 16-byte copies of one plane (rows j0-2 .. j0+17, k0-4 .. k0+35) that this thread
+// issues: the same (row, chunk) positions for every plane and array, so their shared and
+// global offsets within a plane are computed once per CTA.
 template <typename T>
-__device__ __forceinline__ void issue_plane(T *dst, const T *__restrict__ src, int n, int q, int j0,
-                                            int k0)
+struct CopyPlan {
+    static constexpr int EPC = 16 / sizeof(T);                  // elements per chunk
+    static constexpr int CPR = OROW / EPC;                      // chunks per row
+    static constexpr int NCH = OJ_ * CPR;                       // chunks per plane
+    static constexpr int PER = (NCH + FT_THREADS - 1) / FT_THREADS;
+    int soff[PER];   // shared offset within a plane
+    int goff[PER];   // global offset within a plane (j n + k); -1: no chunk
+};
+
+template <typename T>
+__device__ __forceinline__ CopyPlan<T> make_plan(int n, int j0, int k0)
 {
-    constexpr int EPC = 16 / sizeof(T);      // elements per chunk
-    constexpr int CPR = OROW / EPC;          // chunks per row
-    const long long pb = (long long)wrap1(q, n) * n * n;
-    for (int c = threadIdx.x; c < OJ_ * CPR; c += FT_THREADS) {
-        const int r = c / CPR, cc = c - r * CPR;
-        const int j = wrap1(j0 - 2 + r, n);
-        const int k = wrap1(k0 - 4 + cc * EPC, n);
-        cp_async16(dst + r * OROW + cc * EPC, src + pb + (long long)j * n + k);
+    CopyPlan<T> pl;
+#pragma unroll
+    for (int m = 0; m < CopyPlan<T>::PER; ++m) {
+        const int c = threadIdx.x + m * FT_THREADS;
+        pl.goff[m] = -1;
+        pl.soff[m] = 0;
+        if (c < CopyPlan<T>::NCH) {
+            const int r = c / CopyPlan<T>::CPR, cc = c - r * CopyPlan<T>::CPR;
+            const int j = wrap1(j0 - 2 + r, n);
+            const int k = wrap1(k0 - 4 + cc * CopyPlan<T>::EPC, n);
+            pl.soff[m] = r * OROW + cc * CopyPlan<T>::EPC;
+            pl.goff[m] = j * n + k;
+        }
     }
+    return pl;
+}
+
+// issue this thread's copies of the plane that starts at global offset pb
+template <typename T>
+__device__ __forceinline__ void issue_plane(T *dst, const T *__restrict__ src, long long pb,
+                                            const CopyPlan<T> &pl)
+{
+#pragma unroll
+    for (int m = 0; m < CopyPlan<T>::PER; ++m)
+        if (pl.goff[m] >= 0)
+            cp_async16(dst + pl.soff[m], src + pb + pl.goff[m]);
 }
 
 // 19-point stencil around old-plane row jr, column kc
@@ -117,6 +145,9 @@ __global__ void __launch_bounds__(FT_THREADS)
     const int i1 = min(i0 + ichunk, n);
     const T cval = (T)(*cptr);
     bool clamped = false;
+    const CopyPlan<T> plan = make_plan<T>(n, j0, k0);
+    const long long n2 = (long long)n * n;
+    auto plane_at = [&](int q) { return (long long)wrap1(q, n) * n2; };
 
     // red cells of plane q on the tile + 1 halo -> rnew[slot3(q)]
     auto red_plane = [&](int q) {
@@ -144,17 +175,21 @@ __global__ void __launch_bounds__(FT_THREADS)
 
     // prologue: planes i0-2 .. i0+1 (group 1), plane i0+2 (group 2)
     for (int q = i0 - 2; q <= i0 + 1; ++q) {
-        issue_plane(S.old[slot5(q)], in, n, q, j0, k0);
+        const long long pb = plane_at(q);
+        issue_plane(S.old[slot5(q)], in, pb, plan);
         if (q >= i0 - 1)
-            issue_plane(S.fr[slot5(q)], f, n, q, j0, k0);
+            issue_plane(S.fr[slot5(q)], f, pb, plan);
         if constexpr (BASE)
-            issue_plane(S.base[slot5(q)], B, n, q, j0, k0);
+            issue_plane(S.base[slot5(q)], B, pb, plan);
     }
     cp_async_commit();
-    issue_plane(S.old[slot5(i0 + 2)], in, n, i0 + 2, j0, k0);
-    issue_plane(S.fr[slot5(i0 + 2)], f, n, i0 + 2, j0, k0);
-    if constexpr (BASE)
-        issue_plane(S.base[slot5(i0 + 2)], B, n, i0 + 2, j0, k0);
+    {
+        const long long pb = plane_at(i0 + 2);
+        issue_plane(S.old[slot5(i0 + 2)], in, pb, plan);
+        issue_plane(S.fr[slot5(i0 + 2)], f, pb, plan);
+        if constexpr (BASE)
+            issue_plane(S.base[slot5(i0 + 2)], B, pb, plan);
+    }
     cp_async_commit();
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     __syncthreads();
@@ -164,10 +199,14 @@ __global__ void __launch_bounds__(FT_THREADS)
     for (int p = i0; p < i1; ++p) {
         cp_async_wait_all();   // plane p+2 has landed
         __syncthreads();       // ... for every thread; iteration p-1 is finished everywhere
-        issue_plane(S.old[slot5(p + 3)], in, n, p + 3, j0, k0);
-        issue_plane(S.fr[slot5(p + 3)], f, n, p + 3, j0, k0);
-        if constexpr (BASE)
-            issue_plane(S.base[slot5(p + 3)], B, n, p + 3, j0, k0);
+        {
+            const long long pb = plane_at(p + 3);
+            const int sl = slot5(p + 3);
+            issue_plane(S.old[sl], in, pb, plan);
+            issue_plane(S.fr[sl], f, pb, plan);
+            if constexpr (BASE)
+                issue_plane(S.base[sl], B, pb, plan);
+        }
         cp_async_commit();
         red_plane(p + 1);
         __syncthreads();
