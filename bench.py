@@ -39,6 +39,7 @@ N_FINE, SIGMA, SEED, PN = 256, 1.5, 2, 32
 N_COARSE = N_FINE // 2
 H_COARSE = L_BOX / N_COARSE    # the 128^3 grid of a 256^3-cell field: 1.95 Mpc/h
 TOL64, TOLMIX = 1e-10, 1e-8
+NU_COARSE_CAP = 4        # coarsest-grid sweeps a visit in the FP64 solves of the step
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop
 
 # algorithmic work per cell of each kernel class: (bound, bytes, flops)
@@ -193,12 +194,15 @@ class Step:
         self.g_tr = torch.empty((3,) + (pf,) * 3, dtype=f64, device=dev)
         self.g_full = torch.empty_like(self.g_tr)
         # V(3,1): with the over-relaxed smoother it reaches 1e-10 in 5 cycles instead of V(2,2)'s
-        # 6 (time to tolerance 12% lower at 128^3; the paper fixes no cycle shape)
+        # 6 (time to tolerance 12% lower at 128^3; the paper fixes no cycle shape).  Both FP64
+        # solves cap the 4^3 coarsest-grid solve at 4 sweeps a visit: the V-cycle counts stay
+        # 5 and 6, and the latency-bound single-CTA sweeps drop from ~14 a visit.
         self.p64 = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE, tol=TOL64, nu1=3,
-                                     nu2=1)
+                                     nu2=1, nu_coarse=NU_COARSE_CAP)
         self.pmix = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE, tol=TOLMIX,
                                       precision="mixed")
-        self.ppatch = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE / 2, tol=TOL64)
+        self.ppatch = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE / 2, tol=TOL64,
+                                        nu_coarse=NU_COARSE_CAP)
         self.graph = True
         torch.cuda.synchronize()
 

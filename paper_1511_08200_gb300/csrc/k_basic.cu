@@ -865,12 +865,56 @@ cudaError_t launch_refine_box(const double *box, const int bd[3], int pg, const 
 // --------------------------------------------------------------------------
 // Dirichlet patch: interior pf, box pf + 2, colour = parity of the interior index.
 // --------------------------------------------------------------------------
-// MASKED: interior cells with mask 0 are not relaxed (they keep their values)
+// Coarse patch grids keep their ghosts on the extrapolated boundary condition
+// g = v0(g) + w^m (v(a) - v0(a)) (k_patch.cu), where a is the one interior cell nearest g.
+// The thread that writes interior cell a writes every ghost anchored at it, so the
+// ghosts of `out` follow each half-sweep without a separate pass: in the red pass every
+// interior cell is written (relaxed or copied), in the black pass the relaxed cells are,
+// and a ghost is only ever read by its own anchor's thread among the cells that write.
+__device__ __forceinline__ void write_anchored_ghosts(double *dst, const double *__restrict__ v0,
+                                                      double w, double val, int i, int j, int k,
+                                                      int p0, int p1, int p2, int d1, int d2)
+{
+    int gi[2], gj[2], gk[2];
+    int ni = 0, nj = 0, nk = 0;
+    if (i == 0)
+        gi[ni++] = 0;
+    if (i == p0 - 1)
+        gi[ni++] = p0 + 1;
+    if (j == 0)
+        gj[nj++] = 0;
+    if (j == p1 - 1)
+        gj[nj++] = p1 + 1;
+    if (k == 0)
+        gk[nk++] = 0;
+    if (k == p2 - 1)
+        gk[nk++] = p2 + 1;
+    if (ni + nj + nk == 0)
+        return;
+    const long long ab = ((long long)(i + 1) * d1 + (j + 1)) * d2 + (k + 1);
+    const double da = val - v0[ab];
+    for (int a = 0; a <= ni; ++a)
+        for (int b = 0; b <= nj; ++b)
+            for (int c = 0; c <= nk; ++c) {
+                const int m = (a > 0) + (b > 0) + (c > 0);
+                if (m == 0)
+                    continue;
+                const int I = a ? gi[a - 1] : i + 1, J = b ? gj[b - 1] : j + 1,
+                          K = c ? gk[c - 1] : k + 1;
+                const double wm = m == 1 ? w : (m == 2 ? w * w : w * w * w);
+                const long long g = ((long long)I * d1 + J) * d2 + K;
+                dst[g] = v0[g] + wm * da;
+            }
+}
+
+// MASKED: interior cells with mask 0 are not relaxed (they keep their values).
+// v0 (coarse patch grids): also refresh the ghosts anchored at the cells written.
 template <bool MASKED>
 __global__ void k_patch_half(const double *__restrict__ src_faces, const double *__restrict__ src_edges,
                              double *dst, const double *__restrict__ fint, double rhs_add, int p0,
                              int p1, int p2, CoefT<double> cf, int colour, int copy_other,
-                             unsigned long long *clamp, const unsigned char *__restrict__ mask)
+                             unsigned long long *clamp, const unsigned char *__restrict__ mask,
+                             const double *__restrict__ v0, double w)
 {
     const long long total = (long long)p0 * p1 * p2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -884,14 +928,21 @@ __global__ void k_patch_half(const double *__restrict__ src_faces, const double 
     const int K = k + 1;
     // the red pass (copy_other) carries every cell it does not relax into dst
     if (((i + j + k) & 1) != colour || (MASKED && !mask[t])) {
-        if (copy_other)
-            dst[r.r00 + K] = src_faces[r.r00 + K];
+        if (copy_other) {
+            const double v = src_faces[r.r00 + K];
+            dst[r.r00 + K] = v;
+            if (v0)
+                write_anchored_ghosts(dst, v0, w, v, i, j, k, p0, p1, p2, d1, d2);
+        }
         return;
     }
     St<double> s;
     gather(src_faces, src_edges, r, K, K + 1, K - 1, s);
     bool cl = false;
-    dst[r.r00 + K] = cell_update(s, fint[t] + rhs_add, cf, cl);
+    const double v = cell_update(s, fint[t] + rhs_add, cf, cl);
+    dst[r.r00 + K] = v;
+    if (v0)
+        write_anchored_ghosts(dst, v0, w, v, i, j, k, p0, p1, p2, d1, d2);
     if (cl)
         atomicAdd(clamp, 1ull);
 }
@@ -906,24 +957,16 @@ cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint
     auto half = [&](const double *faces, int colour, int copy_other) {
         if (mask)
             k_patch_half<true><<<g, kBlock, 0, st>>>(faces, in, out, fint, rhs_add, pf[0], pf[1],
-                                                     pf[2], cf, colour, copy_other, clamp, mask);
+                                                     pf[2], cf, colour, copy_other, clamp, mask, v0,
+                                                     w);
         else
             k_patch_half<false><<<g, kBlock, 0, st>>>(faces, in, out, fint, rhs_add, pf[0], pf[1],
-                                                      pf[2], cf, colour, copy_other, clamp, mask);
+                                                      pf[2], cf, colour, copy_other, clamp, mask, v0,
+                                                      w);
     };
     // red: from in (all), black copied; black: faces from out (new red), edges from in (old black)
     half(in, 0, 1);
-    if (v0) {
-        cudaError_t e = launch_pbox_ghost_refresh(out, v0, pf, w, st);
-        if (e != cudaSuccess)
-            return e;
-    }
     half(out, 1, 0);
-    if (v0) {
-        cudaError_t e = launch_pbox_ghost_refresh(out, v0, pf, w, st);
-        if (e != cudaSuccess)
-            return e;
-    }
     count_launch(2);
     return cudaGetLastError();
 }

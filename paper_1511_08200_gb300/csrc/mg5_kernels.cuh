@@ -164,8 +164,8 @@ cudaError_t launch_refine_cubic(const double *phic, int nc, const int o[3], cons
 cudaError_t launch_refine_box(const double *box, const int bd[3], int pg, const int o[3],
                               const int pn[3], int ghost, double *fine, cudaStream_t st);
 // Dirichlet patch (interior pf, box pf + 2): one full sweep in -> out (out must hold the ghosts).
-// With v0 (coarse patch grids) the ghosts of out are refreshed after each half-sweep by the
-// extrapolated boundary condition of weight w (k_patch.cu).  mask (interior-indexed, optional):
+// With v0 (coarse patch grids) the ghosts of out follow each half-sweep by the extrapolated
+// boundary condition of weight w (k_patch.cu), written by the threads of their anchor cells.  mask (interior-indexed, optional):
 // cells with mask 0 are not relaxed and keep their values.
 cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint, double rhs_add,
                                const int pf[3], CoefT<double> cf, unsigned long long *clamp,
