@@ -44,21 +44,22 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x
 
 # algorithmic work per cell of each kernel class: (bound, bytes, flops)
 #   sweep: read phi + f, write phi (the full red+black sweep of one cell);
-#   ~42 FP64 flops (FMA = 2) + 1 sqrt + 1 div per cell update
-# FP64 smoother flops per cell: the stencil parts, the root (FP32 seed + two FP64 Newton steps)
-# and the relaxed final update (omega v_root + (1 - omega) v)
+#   FP64 smoother: 40 flops per cell update, the method's operations counted one by one
+#   (FMA = 2; sqrt and divide 1 each): face sums 5, a, b, c 3, a^2 + bc 3, the three mixed
+#   differences 9, their squares 5, b = rhs + alpha Sigma 4, the closed-form root 6,
+#   S - h^2 L 2, the relaxed update omega v_root + (1 - omega) v 3
 WORK = {
-    "sweep64": ("alu", 24.0, 44.0),
-    "patch_sweep64": ("alu", 24.0, 44.0),
+    "sweep64": ("alu", 24.0, 40.0),
+    "patch_sweep64": ("alu", 24.0, 40.0),
     "resid_restrict64": ("alu", 18.0, 38.0),
     "sweep32": ("hbm", 16.0, 60.0),          # correction form: read e, B, f; write e
     "resid_restrict32": ("hbm", 12.5, 60.0),
     "resid64_mixed": ("alu", 24.0, 36.0),     # read phi64, f64; write r32, B32
     "update_mixed": ("hbm", 20.0, 1.0),
     "force64": ("hbm", 32.0, 6.0),
-    "sweep64_coarse": ("alu", 24.0, 44.0),
+    "sweep64_coarse": ("alu", 24.0, 40.0),
     "sweep32_coarse": ("hbm", 16.0, 60.0),
-    "patch_sweep64_coarse": ("alu", 24.0, 44.0),
+    "patch_sweep64_coarse": ("alu", 24.0, 40.0),
     "refine64": ("hbm", 9.0, 25.0),
     "prolong64": ("hbm", 18.0, 20.0),
     "prolong32": ("hbm", 9.0, 20.0),
