@@ -77,6 +77,20 @@ TRAFFIC_PER_CELL = {
 }
 
 
+def step_params(mg, alpha, s):
+    """Parameters of the step's three solves: (FP64 128^3 domain solve, mixed 128^3 solve,
+    FP64 64^3 patch relaxation).  V(3,1) for the domain solve: with the over-relaxed smoother it
+    reaches 1e-10 in 5 cycles instead of V(2,2)'s 6 (time to tolerance 12% lower at 128^3; the
+    paper fixes no cycle shape).  Both FP64 solves cap the 4^3 coarsest-grid solve at 4 sweeps a
+    visit: the V-cycle counts stay 5 and 6, and the latency-bound single-CTA sweeps drop from
+    ~14 a visit."""
+    p64 = mg.default_params(alpha=alpha, s=s, h=H_COARSE, tol=TOL64, nu1=3, nu2=1,
+                            nu_coarse=NU_COARSE_CAP)
+    pmix = mg.default_params(alpha=alpha, s=s, h=H_COARSE, tol=TOLMIX, precision="mixed")
+    ppatch = mg.default_params(alpha=alpha, s=s, h=H_COARSE / 2, tol=TOL64, nu_coarse=NU_COARSE_CAP)
+    return p64, pmix, ppatch
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -194,16 +208,7 @@ class Step:
         self.box_full = torch.empty_like(self.box)
         self.g_tr = torch.empty((3,) + (pf,) * 3, dtype=f64, device=dev)
         self.g_full = torch.empty_like(self.g_tr)
-        # V(3,1): with the over-relaxed smoother it reaches 1e-10 in 5 cycles instead of V(2,2)'s
-        # 6 (time to tolerance 12% lower at 128^3; the paper fixes no cycle shape).  Both FP64
-        # solves cap the 4^3 coarsest-grid solve at 4 sweeps a visit: the V-cycle counts stay
-        # 5 and 6, and the latency-bound single-CTA sweeps drop from ~14 a visit.
-        self.p64 = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE, tol=TOL64, nu1=3,
-                                     nu2=1, nu_coarse=NU_COARSE_CAP)
-        self.pmix = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE, tol=TOLMIX,
-                                      precision="mixed")
-        self.ppatch = mg.default_params(alpha=self.alpha, s=self.s, h=H_COARSE / 2, tol=TOL64,
-                                        nu_coarse=NU_COARSE_CAP)
+        self.p64, self.pmix, self.ppatch = step_params(mg, self.alpha, self.s)
         self.graph = True
         torch.cuda.synchronize()
 

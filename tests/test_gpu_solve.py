@@ -460,3 +460,38 @@ def test_spectral_coarsest_grid(ctx, n, prec, tol, bar):
     assert info.cycles <= (10 if prec == "fp64" else 12)
     ref, _ = oracle.solve(delta, alpha, s, h, tol=1e-11)
     assert rel_l2(phi, ref) <= bar
+
+
+def test_bench_step_configuration_matches_oracle(ctx):
+    """The refinement step in the launch configuration bench.py times: the 128^3 FP64 solve
+    (full-multigrid start, V(3,1), coarsest capped at 4 sweeps a visit) and the 64^3 patch
+    relaxation (same cap), both as graph replays, plus the mixed 128^3 solve, against the
+    oracle's converged solutions.  The FP64 runs stop at 1e-10, which leaves phi within a few
+    1e-10 of the discrete solution; the mixed run at 1e-8 within the 1e-6 bar."""
+    import bench
+    mg = _mg()
+    beta, alpha, s = mg.ndgp_coefficients(1.0, 0.3, 1.0)
+    coarse, patch, o = workload.patch_workload(bench.N_FINE, bench.SIGMA, bench.SEED, bench.PN)
+    h = bench.H_COARSE
+    p64, pmix, ppatch = bench.step_params(mg, alpha, s)
+    import torch
+    grad = torch.empty((3,) + coarse.shape, dtype=torch.float64, device="cuda")
+    phi, grad, info = ctx.solve_fifth_force(dev(coarse), p64, grad=grad, fmg=True, graph=True)
+    assert info.status == 0 and info.rel_residual <= 1e-10 and info.cycles <= 6
+    ref, rinfo = oracle.solve(coarse, alpha, s, h, tol=1e-13)
+    assert rel_l2(host(phi), ref) <= 5e-10
+    assert rel_l2(host(grad), oracle.force(ref, h)) <= 5e-10
+    pn = (bench.PN,) * 3
+    box = ctx.refine_interpolate(phi, o, pn, 1)
+    box_ref = oracle.refine_interpolate(ref, o, pn, 1)
+    assert rel_l2(host(box), box_ref) <= 5e-10
+    relaxed, pinfo = ctx.relax_patch(dev(patch), ppatch, info.compat_c, box.clone(), graph=True)
+    assert pinfo.status == 0 and pinfo.rel_residual <= 1e-10 and pinfo.cycles <= 8
+    ref_relaxed, nsw, rel = oracle.relax_patch(patch, box_ref, alpha, s, h / 2, rinfo.compat_c,
+                                               tol=1e-11)
+    assert rel <= 1e-11
+    got = host(relaxed)
+    assert rel_l2(got[1:-1, 1:-1, 1:-1], ref_relaxed[1:-1, 1:-1, 1:-1]) <= 1e-9
+    phim, gm, im = ctx.solve_fifth_force(dev(coarse), pmix)
+    assert im.status == 0 and im.rel_residual <= 1e-8
+    assert rel_l2(host(phim), ref) <= 1e-6
