@@ -1551,7 +1551,9 @@ int mg5_parent_force_mask(mg5_ctx *ctx, const double *grad_phi, const double *gr
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long *dcount = nullptr;
     if (count) {
-        dcount = &ctx->cnt->clamped;   // the counters are free between solves on this stream
+        // every solve of this context synchronises before it returns, and a context serves one
+        // host thread at a time: between calls its counters and pinned scalars are free
+        dcount = &ctx->cnt->clamped;
         CK(cudaMemsetAsync(dcount, 0, sizeof(*dcount), st));
     }
     CK(launch_parent_force_mask(grad_phi, grad_gr, pd, periodic, o, pn, theta, mask, dcount, st));
