@@ -131,3 +131,40 @@ def test_schedule_table_host_logic(lib, tmp_path):
     with pytest.raises(mg.MG5Error):
         mg.tune_load(tmp_path / "bad.jsonl")
     mg.tune_clear()
+
+
+def test_masked_truncation_argument_checks(lib):
+    """mg5_parent_force_mask and mg5_relax_patch_masked reject bad arguments before they touch
+    the context or the device (the pointers below are never dereferenced)."""
+    import paper_1511_08200_gb300 as mg
+    I3 = ctypes.c_int * 3
+    P = ctypes.c_void_p
+    fm = lib.mg5_parent_force_mask
+    fm.argtypes = [P, P, P, I3, ctypes.c_int, I3, I3, ctypes.c_double, P, P, P]
+    fm.restype = ctypes.c_int
+    ctx = ctypes.create_string_buffer(1 << 16)     # zero-filled stand-in, never read here
+    buf = ctypes.create_string_buffer(64)
+    c, g, m = ctypes.addressof(ctx), ctypes.addressof(buf), ctypes.addressof(buf)
+
+    def call(pd, per, o, pn, theta, ctxp=c):
+        return fm(ctxp, g, g, I3(*pd), per, I3(*o), I3(*pn), theta, m, None, None)
+
+    E_ARG = -1
+    assert call((8, 8, 8), 1, (0, 0, 0), (4, 4, 4), 0.1, ctxp=None) == E_ARG
+    assert call((8, 8, 8), 1, (0, 0, 0), (4, 4, 4), -0.1) == E_ARG
+    assert call((8, 8, 8), 1, (0, 0, 0), (4, 4, 4), float("nan")) == E_ARG
+    assert call((8, 8, 8), 1, (0, 8, 0), (4, 4, 4), 0.1) == E_ARG        # o >= pd (periodic)
+    assert call((8, 8, 8), 1, (0, 0, 0), (4, 9, 4), 0.1) == E_ARG        # pn > pd
+    assert call((8, 8, 8), 0, (0, 6, 0), (4, 4, 4), 0.1) == E_ARG        # o + pn > pd (box)
+    assert call((8, 0, 8), 1, (0, 0, 0), (4, 1, 4), 0.1) == E_ARG        # empty parent
+    assert call((8, 8, 8), 1, (0, 0, 0), (4, 0, 4), 0.1) == E_ARG        # empty patch
+    rm = lib.mg5_relax_patch_masked
+    rm.argtypes = [P, P, I3, P, P, ctypes.c_double, P, P, P]
+    rm.restype = ctypes.c_int
+    prm = mg.default_params(alpha=1.0, s=1.0, h=0.5)
+    pp = ctypes.addressof(prm)
+    assert rm(c, g, I3(4, 4, 4), None, pp, 0.0, g, None, None) == E_ARG   # no mask
+    assert rm(c, g, I3(4, 5, 4), m, pp, 0.0, g, None, None) == E_ARG      # odd side
+    assert rm(c, g, I3(4, 4, 4), m, pp, float("inf"), g, None, None) == E_ARG
+    bad = mg.default_params(alpha=1.0, s=1.0, h=0.5, omega=2.5)
+    assert rm(c, g, I3(4, 4, 4), m, ctypes.addressof(bad), 0.0, g, None, None) == E_ARG
