@@ -661,10 +661,10 @@ def schedules(mg, device, prec, n):
     return out
 
 
-def run_batch(mg, torch, dev, alpha, s, reps=5, autotune=True):
-    """The batched workload: 96 boxes, sizes uniform from {32,48,64,96,128}, seeds 1000 + b,
-    alpha log-uniform in [0.1, 10] x nominal, mixed precision to 1e-8, solved as ONE
-    CUDA-graph launch; compared with the same boxes solved one after another."""
+def batch_boxes(mg, dev, alpha, s):
+    """The 96 boxes of the batched workload: sizes uniform from {32,48,64,96,128}, lognormal
+    sigma = 1 with seeds 1000 + b, alpha log-uniform in [0.1, 10] x nominal, mixed precision to
+    1e-8.  Returns (sizes, alpha scales, device deltas, params)."""
     import workload
     rng = np.random.Generator(np.random.PCG64(4))
     sizes = rng.choice(np.asarray([32, 48, 64, 96, 128]), size=96)
@@ -672,6 +672,14 @@ def run_batch(mg, torch, dev, alpha, s, reps=5, autotune=True):
     deltas = [workload.lognormal_delta_torch(int(n), 1.0, 1000 + b, dev) for b, n in enumerate(sizes)]
     params = [mg.default_params(alpha=alpha * float(a), s=s, h=L_BOX / 512, tol=TOLMIX,
                                 precision="mixed") for a in scales]
+    return sizes, scales, deltas, params
+
+
+def run_batch(mg, torch, dev, alpha, s, reps=5, autotune=True):
+    """The batched workload: 96 boxes, sizes uniform from {32,48,64,96,128}, seeds 1000 + b,
+    alpha log-uniform in [0.1, 10] x nominal, mixed precision to 1e-8, solved as ONE
+    CUDA-graph launch; compared with the same boxes solved one after another."""
+    sizes, scales, deltas, params = batch_boxes(mg, dev, alpha, s)
     phis = [torch.zeros_like(d) for d in deltas]
     grads = [torch.empty((3,) + d.shape, dtype=torch.float64, device=dev) for d in deltas]
     ctx = mg.Context(dev.index or 0)

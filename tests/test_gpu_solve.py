@@ -495,3 +495,26 @@ def test_bench_step_configuration_matches_oracle(ctx):
     phim, gm, im = ctx.solve_fifth_force(dev(coarse), pmix)
     assert im.status == 0 and im.rel_residual <= 1e-8
     assert rel_l2(host(phim), ref) <= 1e-6
+
+
+def test_bench_batch_configuration_matches_oracle(ctx):
+    """The 96-box batched workload as bench.py runs it (tuned schedules, one graph launch):
+    every box converges, and for every grid size the boxes with the smallest and the largest
+    alpha match the FP64 oracle within the mixed-precision bar 1e-6."""
+    import torch
+    import bench
+    mg = _mg()
+    beta, alpha, s = mg.ndgp_coefficients(1.0, 0.3, 1.0)
+    sizes, scales, deltas, params = bench.batch_boxes(mg, torch.device("cuda"), alpha, s)
+    for n in sorted(set(int(x) for x in sizes)):
+        ctx.autotune(n, "mixed")
+    phis, _, infos = ctx.solve_batch(deltas, params)
+    assert all(i.status == 0 and i.rel_residual <= 1e-8 for i in infos)
+    h = bench.L_BOX / 512
+    for n in sorted(set(int(x) for x in sizes)):
+        idx = [b for b in range(len(sizes)) if int(sizes[b]) == n]
+        for b in {min(idx, key=lambda q: scales[q]), max(idx, key=lambda q: scales[q])}:
+            d = host(deltas[b])
+            ref, rinfo = oracle.solve(d, params[b].alpha, s, h, tol=1e-12)
+            assert rinfo.status == 0
+            assert rel_l2(host(phis[b]), ref) <= 1e-6, (n, b, scales[b])
