@@ -721,22 +721,30 @@ def run_batch(mg, torch, dev, alpha, s, reps=5, autotune=True):
             "outer_iters": [i.outer_iters for i in infos][:8], "dtype": "f32+f64"}
 
 
-def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=None,
-                autotune=True):
-    """Poisson arrivals at `rate` req/s for `seconds`: sides 16 round(10^U(log 32, log 256)/16),
-    sigma ~ U(0.5, 2), tol 1e-6 or 1e-8 with p = 1/2, mixed precision; admitted by HBM footprint.
-    Latency = completion - arrival (server clock); the first fifth of the run is discarded."""
+def serving_stream(dev, count, rate=200.0):
+    """The serving stream's requests: exponential gaps at `rate`, sides 16 round(10^U(log 32,
+    log 256)/16), sigma in {0.5, 1, 1.5, 2} (bucket b: sigma = 0.5 + 0.5 b), tol 1e-6 or 1e-8
+    with p = 1/2.  Returns (gaps, sizes, sigma buckets, tols, device delta per (side, bucket))."""
     import workload
     rng = np.random.Generator(np.random.PCG64(5))
-    count = int(rate * seconds * 1.2) + 8
     gaps = rng.exponential(1.0 / rate, size=count)
     sizes = workload.serving_sizes(rng, count)
-    sig_bucket = rng.integers(0, 4, size=count)            # sigma in {0.5, 1.0, 1.5, 2.0}
+    sig_bucket = rng.integers(0, 4, size=count)
     tols = np.where(rng.uniform(size=count) < 0.5, 1e-6, 1e-8)
     pool = {}
     for n in sorted(set(int(x) for x in sizes)):
         for b in range(4):
             pool[(n, b)] = workload.lognormal_delta_torch(n, 0.5 + 0.5 * b, 5000 + 7 * n + b, dev)
+    return gaps, sizes, sig_bucket, tols, pool
+
+
+def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=None,
+                autotune=True):
+    """Poisson arrivals at `rate` req/s for `seconds`: sides 16 round(10^U(log 32, log 256)/16),
+    sigma ~ U(0.5, 2), tol 1e-6 or 1e-8 with p = 1/2, mixed precision; admitted by HBM footprint.
+    Latency = completion - arrival (server clock); the first fifth of the run is discarded."""
+    count = int(rate * seconds * 1.2) + 8
+    gaps, sizes, sig_bucket, tols, pool = serving_stream(dev, count, rate)
     budget = int(torch.cuda.get_device_properties(dev).total_memory * 0.5)
     if autotune:   # the schedule table is process-wide: the server's captures read it
         tctx = mg.Context(dev.index or 0)

@@ -112,3 +112,47 @@ def test_server_shares_captured_graphs_between_workers():
     srv.close()
     for x in outs[1:]:
         assert torch.equal(x, outs[0])
+
+
+def test_bench_serving_stream_matches_oracle():
+    """The first requests of the serving stream bench.py offers (same generator: sides 16 k from
+    32 to 256, sigma 0.5 - 2, tol 1e-6 or 1e-8, mixed precision), all submitted to a server of 8
+    slots at once: every one converges, and those of side <= 128 match the FP64 oracle within
+    the bar their tolerance implies (phi within ~1.5 x tol of the discrete solution: 1e-5 for
+    1e-6, 1e-6 for 1e-8)."""
+    import torch
+    import bench
+    import oracle
+    from tests.gpu_common import host, rel_l2
+    mg = _mg()
+    beta, alpha, s = mg.ndgp_coefficients(1.0, 0.3, 1.0)
+    h = bench.L_BOX / 512
+    count = 24
+    gaps, sizes, bucket, tols, pool = bench.serving_stream(torch.device("cuda"), count)
+    srv = mg.Server(0, slots=8)
+    phis = {}
+    for i in range(count):
+        d = pool[(int(sizes[i]), int(bucket[i]))]
+        p = mg.default_params(alpha=alpha, s=s, h=h, tol=float(tols[i]), precision="mixed")
+        phis[i] = torch.full_like(d, float("nan"))
+        srv.submit(d, p, phis[i], tag=i)
+    got = {}
+    while len(got) < count:
+        for c in srv.poll(wait_ms=5000):
+            got[c.tag] = c
+    srv.close()
+    checked = 0
+    for i in range(count):
+        c = got[i]
+        assert c.status in (0, 1), c
+        assert c.info.rel_residual <= tols[i]
+        n = int(sizes[i])
+        if n > 128:
+            continue
+        d = host(pool[(n, int(bucket[i]))])
+        ref, rinfo = oracle.solve(d, alpha, s, h, tol=1e-12)
+        assert rinfo.status == 0
+        bar = 1e-5 if tols[i] > 1e-7 else 1e-6
+        assert rel_l2(host(phis[i]), ref) <= bar, (i, n, tols[i])
+        checked += 1
+    assert checked >= 8
