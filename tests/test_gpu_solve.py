@@ -322,17 +322,19 @@ def test_batch_mixed_status_per_box(ctx):
 
 
 def test_mixed_512_full_size():
-    """The 512^3 sigma = 2 mixed-precision workload: the FP64 oracle recomputes the
-    residual of the GPU result cell by cell over the whole grid (<= 1e-8), and the
-    result matches the GPU FP64 solve (itself oracle-parity tested) within 1e-6,
-    over the whole grid and on the 128^3 subvolume at the origin."""
+    """The 512^3 sigma = 2 mixed-precision workload as `bench.py --workload mixed --n 512` runs
+    it (the same input field, tuned sweep schedules): the FP64 oracle recomputes the residual
+    of the GPU result cell by cell over the whole grid (<= 1e-8), and the result matches the
+    GPU FP64 solve (itself oracle-parity tested) within 1e-6, over the whole grid and on the
+    128^3 subvolume at the origin."""
     import torch
     mg = _mg()
     alpha, s, h = nominal()
     n = 512
-    delta = workload.lognormal_delta(n, 2.0, 3)
     ctx = mg.Context(0)
-    d = dev(delta)
+    d = workload.lognormal_delta_torch(n, 2.0, 3, torch.device("cuda"))
+    delta = host(d)
+    ctx.autotune(n, "mixed")
     pm = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-8, precision="mixed")
     phim, _, im = ctx.solve_fifth_force(d, pm)
     assert im.status == 0 and im.rel_residual <= 1e-8
