@@ -73,7 +73,10 @@ extern "C" {
                              kernels as the host-driven solve, without a host round trip per cycle.
                              Not with MG5_WARM (with MG5_HOST_IO the host buffers are staged in and
                              out around the replay); MG5_FP64 needs nu1 + nu2 even and
-                             N with two grids or more (MG5_E_ARG otherwise). */
+                             N with two grids or more (MG5_E_ARG otherwise).  A change of the
+                             sweep-schedule table (mg5_autotune, mg5_schedule_set,
+                             mg5_tune_clear, mg5_tune_load) retires the captured solves and
+                             batches: the next call captures again under the new schedules. */
 
 typedef struct mg5_ctx mg5_ctx;  /* opaque; owns the device hierarchy, resident between calls */
 

@@ -129,6 +129,7 @@ struct BatchSet {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     size_t bytes = 0;
+    unsigned long long sched = 0;   // schedule-table version at capture
 };
 
 // A mixed solve of one size and parameter set captured as a graph (defect-correction
@@ -162,6 +163,10 @@ struct GraphEntry {
     CaptureStats stats{};
     size_t bytes = 0;              // device bytes, hierarchy included
     unsigned long long last_use = 0;
+    unsigned long long sched = 0;  // schedule-table version at capture (see current())
+    // replayable: the sweep schedules it was captured with are still the table's (patch
+    // relaxations use no schedule)
+    bool current() const { return hierp || sched == schedule_version(); }
 };
 
 constexpr size_t kGraphCacheMax = 48;   // entries per context on the single-caller path
@@ -1041,7 +1046,8 @@ int mg5_graph_cached_bytes(mg5_ctx *ctx, int N, const mg5_params *p, int with_gr
     *extra = p->precision == MG5_FP64 ? graph_entry_bytes64(N, with_grad != 0)
                                        : graph_entry_bytes(N, with_grad != 0);
     for (GraphEntry *g : ctx->graphs)
-        if (!g->busy && g->N == N && g->grad == (with_grad != 0) && same_params(g->prm, *p))
+        if (!g->busy && g->N == N && g->grad == (with_grad != 0) && same_params(g->prm, *p) &&
+            g->current())
             *extra = 0;
     return MG5_OK;
 }
@@ -1853,7 +1859,7 @@ size_t graph_held(mg5_ctx *ctx)
 GraphEntry *graph_checkout(mg5_ctx *ctx, int N, const mg5_params *p, bool grad)
 {
     for (GraphEntry *g : ctx->graphs)
-        if (!g->busy && g->N == N && g->grad == grad && same_params(g->prm, *p)) {
+        if (!g->busy && g->N == N && g->grad == grad && same_params(g->prm, *p) && g->current()) {
             g->busy = true;
             g->last_use = ++ctx->graph_clock;
             return g;
@@ -1865,7 +1871,7 @@ int graph_count(mg5_ctx *ctx, int N, const mg5_params *p, bool grad)
 {
     int c = 0;
     for (GraphEntry *g : ctx->graphs)
-        c += g->N == N && g->grad == grad && same_params(g->prm, *p);
+        c += g->N == N && g->grad == grad && same_params(g->prm, *p) && g->current();
     return c;
 }
 
@@ -1926,6 +1932,7 @@ int graph_build(int device, int N, const mg5_params *p, bool grad, GraphEntry **
     g->N = N;
     g->prm = *p;
     g->grad = grad;
+    g->sched = schedule_version();   // read before the capture reads the schedules
     size_t hb = 0;
     int rc = alloc_mixed(N, 0, &hb, &g->hier, err);
     const size_t n3 = (size_t)N * N * N;
@@ -2172,6 +2179,7 @@ static int graph_build64(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, bo
     g->prm = *p;
     g->grad = grad;
     g->fmg = fmg;
+    g->sched = schedule_version();   // read before the capture reads the schedules
     const size_t n3 = (size_t)N * N * N;
     cudaError_t e = alloc_hier_raw(N, &g->hier64);
     if (e == cudaSuccess)
@@ -2243,8 +2251,21 @@ static int graph_build64(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, bo
 static int get_graph_entry(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, bool fmg,
                            GraphEntry **out)
 {
+    // entries captured under an older schedule table are not replayed again: free them (every
+    // entry is idle here, this context's solves have synchronised)
+    for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
+        GraphEntry *g = *it;
+        if (!g->busy && !g->current()) {
+            it = ctx->graphs.erase(it);
+            ctx->held -= g->bytes;
+            graph_free(g);
+        } else {
+            ++it;
+        }
+    }
     for (GraphEntry *g : ctx->graphs)
-        if (!g->busy && g->N == N && g->grad == grad && g->fmg == fmg && same_params(g->prm, *p)) {
+        if (!g->busy && g->N == N && g->grad == grad && g->fmg == fmg && same_params(g->prm, *p) &&
+            g->current()) {
             g->busy = true;
             g->last_use = ++ctx->graph_clock;
             *out = g;
@@ -2299,7 +2320,7 @@ static int solve_graph(mg5_ctx *ctx, const double *delta, int N, const mg5_param
 static bool batch_matches(const BatchSet *b, int nbox, const double *const *delta, const int *N,
                           const mg5_params *p, double *const *phi, double *const *grad)
 {
-    if (!b || b->nbox != nbox)
+    if (!b || b->nbox != nbox || b->sched != schedule_version())
         return false;
     for (int i = 0; i < nbox; ++i)
         if (b->N[i] != N[i] || !same_params(b->prm[i], p[i]) || b->delta[i] != delta[i] ||
@@ -2314,6 +2335,7 @@ static int build_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const
     free_batch(ctx);
     BatchSet *b = new BatchSet();
     ctx->batch = b;
+    b->sched = schedule_version();   // read before the capture reads the schedules
     b->nbox = nbox;
     b->N.assign(N, N + nbox);
     b->prm.assign(p, p + nbox);

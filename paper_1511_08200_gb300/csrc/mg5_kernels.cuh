@@ -91,6 +91,8 @@ struct SweepSchedule {
 // The schedule of (device, precision, side): the tuned one, else the default
 // (FP64 two-pass; the mixed mode's FP32 correction form fused where it fits).
 SweepSchedule sweep_schedule(int device, int precision, int n);
+// Changes with every change of the schedule table (captured solves record it; mg5_tune.cu).
+unsigned long long schedule_version();
 bool sweep_tuned(int device, int precision, int n);
 // time the candidates for (device, precision, n) on st and record the fastest (mg5_tune.cu)
 cudaError_t tune_side(int device, int precision, int n, cudaStream_t st, SweepSchedule *out);

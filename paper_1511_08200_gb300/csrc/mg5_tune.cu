@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -32,6 +33,10 @@ namespace {
 using Key = std::tuple<int, int, int>;   // device, precision, side
 std::mutex g_tune_mu;
 std::map<Key, SweepSchedule> g_tuned;
+// bumped on every change of the table: a captured solve records the version it was captured
+// under and is not replayed once the table has changed (its launches would follow the old
+// schedules, and the schedules change the rounding, not the method)
+std::atomic<unsigned long long> g_sched_version{1};
 
 SweepSchedule default_schedule(int precision, int n)
 {
@@ -149,6 +154,8 @@ cudaError_t time_candidates(int n, int precision, cudaStream_t st, std::vector<S
 
 }  // namespace
 
+unsigned long long schedule_version() { return g_sched_version.load(); }
+
 SweepSchedule sweep_schedule(int device, int precision, int n)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -176,6 +183,7 @@ cudaError_t tune_side(int device, int precision, int n, cudaStream_t st, SweepSc
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[Key{device, precision, n}] = best;
+        ++g_sched_version;
     }
     if (out)
         *out = best;
@@ -232,6 +240,7 @@ int mg5_schedule_set(int device, int precision, int n, const mg5_schedule *s)
     v.ms = s->ms;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[Key{device, precision, n}] = v;
+    ++g_sched_version;
     return MG5_OK;
 }
 
@@ -239,6 +248,7 @@ int mg5_tune_clear(void)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned.clear();
+    ++g_sched_version;
     return MG5_OK;
 }
 

@@ -378,6 +378,39 @@ def test_graph_solve_equals_host_driven(ctx):
         ctx.solve_fifth_force(d2, mg.default_params(alpha=alpha, s=s, h=h, nu1=1), graph=True)
 
 
+def test_graph_recaptured_after_schedule_change(ctx):
+    """A captured solve follows the sweep schedules of its capture; after the schedule table
+    changes, the next graph call captures again, so replay and host-driven solve stay
+    bit-identical (for mixed and FP64, and for a batch)."""
+    import torch
+    mg = _mg()
+    alpha, s, h = nominal()
+    d = dev(workload.lognormal_delta(64, 1.0, 23))
+    for prec, tol in (("mixed", 1e-8), ("fp64", 1e-10)):
+        p = mg.default_params(alpha=alpha, s=s, h=h, tol=tol, precision=prec)
+        old, tuned = mg.schedule_get(0, prec, 64)
+        try:
+            for form in (old.form, 1 - old.form):
+                mg.schedule_set(0, prec, 64, form)
+                ref, _, _ = ctx.solve_fifth_force(d, p, fmg=(prec == "fp64"))
+                got, _, _ = ctx.solve_fifth_force(d, p, fmg=(prec == "fp64"), graph=True)
+                assert torch.equal(got, ref), (prec, form)
+        finally:
+            mg.schedule_set(0, prec, 64, old.form, old.block, old.chunk)
+    # a batch captured under one table and relaunched under another
+    p = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-8, precision="mixed")
+    old, _ = mg.schedule_get(0, "mixed", 64)
+    outs = [torch.zeros_like(d), torch.zeros_like(d)]   # the same pointers: the cached batch
+    try:
+        for form in (old.form, 1 - old.form):
+            mg.schedule_set(0, "mixed", 64, form)
+            phis, _, _ = ctx.solve_batch([d, d], [p, p], phis=outs)
+            ref, _, _ = ctx.solve_fifth_force(d, p)
+            assert torch.equal(phis[0], ref) and torch.equal(phis[1], ref), form
+    finally:
+        mg.schedule_set(0, "mixed", 64, old.form, old.block, old.chunk)
+
+
 @pytest.mark.parametrize("n,fmg", [(32, False), (64, True), (128, True)])
 def test_fp64_graph_solve_equals_host_driven(ctx, n, fmg):
     """The FP64 solve captured with its V-cycle loop as a WHILE node runs the same kernels as
