@@ -307,8 +307,12 @@ int mg5_relax_patch_graph(mg5_ctx *ctx, const double *delta_fine, const int pf[3
  * the masked cells (an empty mask returns at once with 0 cycles).  The V-cycle
  * keeps a mask per grid: a coarse cell is relaxed only if all 8 of its children
  * are, residuals of unmasked cells restrict as zero and corrections reach masked
- * cells only.  Same other arguments, errors and synchronisation as
- * mg5_relax_patch; info->cell_updates counts every interior cell the sweeps visit.
+ * cells only.  When fewer than 10% of the cells are masked, masked sweeps alone
+ * run first (the residual checked every 4, at most 64) and V-cycles take over only
+ * if those have not converged; info->cycles counts V-cycles (0 when the sweeps
+ * alone converged) and info->history every check.  Same other arguments, errors
+ * and synchronisation as mg5_relax_patch (plus one synchronisation to read the
+ * masked fraction); info->cell_updates counts every interior cell the sweeps visit.
  */
 int mg5_parent_force_mask(mg5_ctx *ctx, const double *grad_phi, const double *grad_gr,
                           const int pd[3], int periodic, const int o[3], const int pn[3],

@@ -46,7 +46,7 @@ cudaError_t launch_mask_restrict(const unsigned char *mf, const int p[3], unsign
     return cudaGetLastError();
 }
 
-// f = s delta + add on every cell; partial sums (0, (s delta)^2) over the masked cells
+// f = s delta + add on every cell; partial sums (number of masked cells, (s delta)^2 over them)
 __global__ void k_scale_masked(const double *__restrict__ delta, double s, double *__restrict__ f,
                                long long n, const unsigned char *__restrict__ mask,
                                double2 *__restrict__ partials, double add)
@@ -56,8 +56,10 @@ __global__ void k_scale_masked(const double *__restrict__ delta, double s, doubl
          t += (long long)gridDim.x * blockDim.x) {
         const double v = s * delta[t];
         f[t] = v + add;
-        if (mask[t])
+        if (mask[t]) {
+            acc.x += 1.0;
             acc.y += v * v;
+        }
     }
     acc = block_sum2(acc);
     if (threadIdx.x == 0)

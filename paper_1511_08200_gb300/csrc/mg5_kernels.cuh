@@ -202,7 +202,7 @@ cudaError_t launch_pbox_ghost_refresh(double *v, const double *v0, const int q[3
 // coarse mask (interior q = p/2) = 1 where all 8 children have mask != 0
 cudaError_t launch_mask_restrict(const unsigned char *mf, const int p[3], unsigned char *mc,
                                  cudaStream_t st);
-// f = s delta + add on every cell; partial sums (0, (s delta)^2) over the cells of mask
+// f = s delta + add on every cell; partial sums (number of cells of mask, (s delta)^2 over them)
 cudaError_t launch_scale_masked(const double *delta, double s, double *f, long long n,
                                 const unsigned char *mask, double2 *partials, int *nblocks,
                                 cudaStream_t st, double add);

@@ -196,3 +196,34 @@ def test_relax_patch_masked_full_size_64(ctx):
     on[1:-1, 1:-1, 1:-1] = mask != 0
     assert rel_l2(got[on], ref[on]) <= 1e-9
     assert np.array_equal(got[~on], box[~on])
+
+
+@pytest.mark.parametrize("frac", [0.002, 0.03, 0.08])
+def test_relax_patch_masked_sparse_mask(ctx, frac):
+    """Masks of a few percent of the cells (the deep levels of Sec. 3.3's criterion) go through
+    masked sweeps first: the same solution as the oracle's masked relaxation, and for the
+    sparsest mask without a V-cycle."""
+    mg = _mg()
+    alpha, s, h = nominal()
+    pf = (32, 32, 32)
+    rng = np.random.default_rng(int(frac * 1000) + 40)
+    hf = h / 2
+    dims = tuple(x + 2 for x in pf)
+    box = s * hf * hf * rng.standard_normal(dims)
+    delta = np.exp(rng.standard_normal(pf)) - 1.0
+    par = rng.random(tuple(x // 2 for x in pf)) < frac
+    par.flat[int(rng.integers(par.size))] = True
+    mask = np.repeat(np.repeat(np.repeat(par, 2, 0), 2, 1), 2, 2).astype(np.uint8)
+    c = 0.01 * s
+    p = mg.default_params(alpha=alpha, s=s, h=hf, tol=1e-12, max_cycles=200)
+    got, info = ctx.relax_patch_masked(dev(delta), _u8(mask), p, c, dev(box))
+    assert info.status == 0 and info.rel_residual <= 1e-12
+    if frac < 0.01:
+        assert info.cycles == 0
+    ref, nsw, rel = oracle.relax_patch_masked(delta, box, mask, alpha, s, hf, c, tol=1e-12)
+    assert rel <= 1e-12
+    got = host(got)
+    on = np.zeros(dims, bool)
+    on[1:-1, 1:-1, 1:-1] = mask != 0
+    assert rel_l2(got[on], ref[on]) <= 1e-10
+    assert np.array_equal(got[~on], box[~on])
