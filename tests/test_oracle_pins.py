@@ -644,3 +644,15 @@ def test_parent_force_mask_box_parent_places_children():
     want = np.zeros((6, 4, 8), np.uint8)
     want[2:4, 2:4, 2:4] = 1
     assert np.array_equal(m, want)
+
+
+def test_vcycle_reduction_factor_poisson():
+    """P:L242's observation turned into a bound: for the Poisson limit (alpha = 0) each FAS
+    V(2,2) cycle of the oracle reduces the residual by a factor <= 0.2, from the first cycle on
+    (the smoothing-plus-coarse-correction rate, not a slow tail)."""
+    delta = workload.lognormal_delta(32, 1.0, 9)
+    phi, info = oracle.solve(delta, 0.0, 1.0, 1.0, tol=1e-12)
+    h = [x for x in info.history if x > 0]
+    assert info.status == 0 and len(h) >= 5
+    ratios = [b / a for a, b in zip(h, h[1:])]
+    assert max(ratios) <= 0.2, ratios

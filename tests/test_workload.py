@@ -1,0 +1,46 @@
+"""The seeded synthetic inputs have the statistics their recipe states (the stand-in for the
+paper's N-body densities): the Gaussian field's sample std, zero mean and k^-2 spectrum cut at
+the Nyquist sphere, and the lognormal contrast's mean zero and delta > -1."""
+import numpy as np
+
+import workload
+
+
+def test_gaussian_field_spectrum_and_moments():
+    n, sigma = 48, 1.3
+    g = workload.gaussian_random_field(n, sigma, 11)
+    assert abs(g.mean()) < 1e-12 and abs(g.std() - sigma) < 1e-12
+    gk = np.abs(np.fft.fftn(g)) ** 2
+    f = np.fft.fftfreq(n) * n
+    kk = 2 * np.pi * np.sqrt(f[:, None, None] ** 2 + f[None, :, None] ** 2 + f[None, None, :] ** 2) / n
+    assert gk[0, 0, 0] < 1e-20 * gk.sum()
+    assert gk[kk > np.pi * 1.0001].max() < 1e-20 * gk.sum()       # nothing beyond Nyquist
+    # shell-averaged power against k: slope -2 (white noise filtered by 1/k)
+    edges = np.linspace(0.2, 2.5, 12)
+    kc, pk = [], []
+    for a, b in zip(edges[:-1], edges[1:]):
+        sel = (kk >= a) & (kk < b)
+        kc.append(kk[sel].mean())
+        pk.append(gk[sel].mean())
+    slope = np.polyfit(np.log(kc), np.log(pk), 1)[0]
+    assert -2.2 < slope < -1.8, slope
+
+
+def test_lognormal_delta_recipe():
+    a = workload.lognormal_delta(32, 1.5, 3)
+    b = workload.lognormal_delta(32, 1.5, 3)
+    c = workload.lognormal_delta(32, 1.5, 4)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)      # seeded
+    assert abs(a.mean()) < 1e-12 and a.min() > -1.0
+    g = workload.gaussian_random_field(32, 1.5, 3)
+    # 1 + delta is exp(g - sigma^2/2) up to the renormalising constant
+    r = (1.0 + a) / np.exp(g - 0.5 * 1.5 ** 2)
+    assert np.ptp(r) < 1e-12 * r.mean()
+
+
+def test_block_mean_conserves_mass():
+    f = workload.lognormal_delta(16, 1.0, 5)
+    c = workload.block_mean(f, 2)
+    assert c.shape == (8, 8, 8)
+    assert abs(c.sum() * 8 - f.sum()) < 1e-9
+    assert np.isclose(c[1, 2, 3], f[2:4, 4:6, 6:8].mean())
