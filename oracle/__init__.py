@@ -16,7 +16,8 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
                      own equation against the start-of-half-sweep state)
   restrict/prolong   pinned: closed forms on Fourier modes, constants
   solve              pinned: FFT Poisson (alpha = 0), dense Newton on 4^3 and 8^3,
-                     manufactured solutions, spherical Vainshtein profile
+                     manufactured solutions, spherical Vainshtein profile, V-cycle
+                     reduction factor <= 0.2 at alpha = 0
   force              pinned: closed form on Fourier modes
   refine_interpolate pinned: constants, linear fields, 1-D closed form
   relax_patch        pinned: manufactured Dirichlet solution
