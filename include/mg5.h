@@ -120,6 +120,7 @@ typedef struct {
 
 /* ------------------------------------------------------------ utilities */
 
+/* Library version, major * 100 + minor (1.00 = 100). */
 int mg5_version(void);
 const char *mg5_status_string(int status);
 /* Number of CUDA kernel launches the library has enqueued in this process. */
@@ -404,25 +405,32 @@ typedef struct {
     mg5_info info;
 } mg5_completion;
 
+/* Start a server on `device` with `slots` workers (1..256) and an HBM cap (0 = none); *srv
+ * receives the handle.  MG5_E_ARG for a bad device or slot count, MG5_E_CUDA if no device
+ * can be queried; the workers start at once and wait for requests. */
 int mg5_server_create(mg5_server **srv, int device, int slots, size_t hbm_budget_bytes);
 /* Enqueue (thread-safe, non-blocking).  MG5_E_OOM if the request alone exceeds the budget
  * (a request that cannot fit even with every worker idle and empty completes with MG5_E_OOM). */
 int mg5_server_submit(mg5_server *srv, const mg5_request *req);
 /* Move up to max completions into out, waiting up to wait_ms for the first; returns the count. */
 int mg5_server_poll(mg5_server *srv, mg5_completion *out, int max, int wait_ms);
+/* Requests waiting for a worker and requests running (either pointer may be NULL). */
 int mg5_server_pending(mg5_server *srv, int *queued, int *running);
+/* Seconds since the server started: the clock of the completions' timestamps. */
 double mg5_server_clock(mg5_server *srv);
+/* Device bytes the server holds now (hierarchies, captured solves, staging). */
 size_t mg5_server_bytes_held(mg5_server *srv);
-/* Finish every queued request, stop the workers, free everything. */
 /* Counters of a server since creation: captured graphs built, the seconds spent
  * building them (allocation + capture + instantiation), idle entries evicted for
- * memory, requests that ran host-driven because no graph could be built, and
- * admissions that had to wait for memory. */
+ * memory, requests that ran host-driven because no graph could be built,
+ * admissions that had to wait for memory, and requests completed. */
 typedef struct {
     long long builds, evictions, fallbacks, memory_waits, completed;
     double build_seconds;
 } mg5_server_stats;
+/* Copy the counters into *out (thread-safe). */
 int mg5_server_get_stats(mg5_server *s, mg5_server_stats *out);
+/* Finish every queued request, stop the workers, free everything. */
 int mg5_server_destroy(mg5_server *srv);
 
 /* ------------------------------------------------------------ without allocation

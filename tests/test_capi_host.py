@@ -168,3 +168,29 @@ def test_masked_truncation_argument_checks(lib):
     assert rm(c, g, I3(4, 4, 4), m, pp, float("inf"), g, None, None) == E_ARG
     bad = mg.default_params(alpha=1.0, s=1.0, h=0.5, omega=2.5)
     assert rm(c, g, I3(4, 4, 4), m, ctypes.addressof(bad), 0.0, g, None, None) == E_ARG
+
+
+def test_every_entry_point_is_documented():
+    """Each function include/mg5.h declares has a comment directly above it (or above the
+    group of declarations it belongs to)."""
+    txt = open(os.path.join(ROOT, "include", "mg5.h")).read().split("\n")
+    decl = re.compile(r"^(?:int|long long|const char \*|double|size_t|void)\s+\*?(mg5_[a-z0-9_]+)\s*\(")
+    undocumented = []
+    for i, line in enumerate(txt):
+        m = decl.match(line)
+        if not m:
+            continue
+        j, found = i - 1, False
+        while j >= 0:
+            s = txt[j].strip()
+            if s.endswith("*/") or s.startswith("/*") or s.startswith("*"):
+                found = True
+                break
+            if s.endswith(");") or s.endswith(",") or decl.match(s) or s.startswith("const ") \
+                    or s.startswith("double ") or s.startswith("mg5_"):
+                j -= 1
+                continue
+            break
+        if not found:
+            undocumented.append(m.group(1))
+    assert not undocumented, undocumented
