@@ -281,6 +281,10 @@ def parent_force_mask(grad_phi, grad_gr, origin, pn, theta, periodic=True) -> np
     grad_phi, grad_gr = _f64(grad_phi), _f64(grad_gr)
     pd = _i3(grad_phi.shape[1:])
     o, pn_ = _i3(origin), _i3(pn)
+    assert grad_gr.shape == grad_phi.shape and grad_phi.shape[0] == 3
+    assert all(0 <= o[a] and 1 <= pn_[a] for a in range(3))
+    if not periodic:
+        assert all(o[a] + pn_[a] <= pd[a] for a in range(3)), "window outside the parent"
     out = np.empty(tuple(2 * int(x) for x in pn_), dtype=np.uint8)
     _load().or_parent_force_mask(_p(grad_phi), _p(grad_gr), _p(pd), 1 if periodic else 0, _p(o),
                                  _p(pn_), theta, _p(out))
@@ -293,7 +297,7 @@ def relax_patch_masked(delta_f, phi_box, mask, alpha, s, h, c, tol=1e-10, max_sw
     delta_f = _f64(delta_f)
     out = _f64(phi_box).copy()
     m = np.ascontiguousarray(mask, dtype=np.uint8)
-    assert m.shape == delta_f.shape
+    assert m.shape == delta_f.shape and out.shape == tuple(x + 2 for x in delta_f.shape)
     pf = _i3(delta_f.shape)
     rel = np.zeros(1)
     nsw = _load().or_relax_patch_masked(_p(delta_f), _p(pf), alpha, s, h, c, _p(m), tol,
