@@ -44,3 +44,27 @@ def test_block_mean_conserves_mass():
     assert c.shape == (8, 8, 8)
     assert abs(c.sum() * 8 - f.sum()) < 1e-9
     assert np.isclose(c[1, 2, 3], f[2:4, 4:6, 6:8].mean())
+
+
+def test_densest_window_brute_force():
+    """The FFT box filter finds the periodic window a direct scan finds (wrapping windows
+    included), and the refinement workload's patch is the fine block under it."""
+    n, w = 12, 4
+    d = workload.lognormal_delta(n, 1.5, 8)
+    best, arg = -np.inf, None
+    for i in range(n):
+        for j in range(n):
+            for k in range(n):
+                idx = [(np.arange(w) + o) % n for o in (i, j, k)]
+                v = d[np.ix_(*idx)].sum()
+                if v > best + 1e-9:
+                    best, arg = v, (i, j, k)
+    assert workload.densest_window(d, w) == arg
+    coarse, patch, o = workload.patch_workload(24, 1.5, 2, 4)
+    fine = workload.lognormal_delta(24, 1.5, 2)
+    assert np.array_equal(coarse, workload.block_mean(fine, 2))
+    assert o == workload.densest_window(coarse, 4)
+    idx = [(2 * o[a] + np.arange(8)) % 24 for a in range(3)]
+    assert np.array_equal(patch, fine[np.ix_(*idx)])
+    assert np.isclose(workload.block_mean(patch, 2).sum(),
+                      coarse[np.ix_(*[(o[a] + np.arange(4)) % 12 for a in range(3)])].sum())
