@@ -68,3 +68,22 @@ def test_densest_window_brute_force():
     assert np.array_equal(patch, fine[np.ix_(*idx)])
     assert np.isclose(workload.block_mean(patch, 2).sum(),
                       coarse[np.ix_(*[(o[a] + np.arange(4)) % 12 for a in range(3)])].sum())
+
+
+def test_nested_halo_workload_geometry():
+    """The nested refinements halve the spacing per level, sit inside their parents, keep the
+    domain's mean density contrast at zero, and zoom into the halo: each level's mean density
+    contrast is above its parent's."""
+    deltas, origins, spacings = workload.nested_halo_workload(n_dom=32, levels=3, pn=8)
+    assert len(deltas) == 4 and origins[0] is None
+    assert abs(deltas[0].mean()) < 1e-12 and deltas[0].shape == (32, 32, 32)
+    for lev in range(1, 4):
+        assert deltas[lev].shape == (16, 16, 16)
+        assert np.isclose(spacings[lev], spacings[0] / 2 ** lev)
+        o = origins[lev]
+        assert all(0 <= x for x in o)
+        if lev >= 2:                      # inside the parent's interior (no wrap)
+            assert all(x + 8 <= 16 for x in o)
+        assert deltas[lev].min() > -1.0
+    means = [float(d.mean()) for d in deltas]
+    assert all(b > a for a, b in zip(means, means[1:])), means
