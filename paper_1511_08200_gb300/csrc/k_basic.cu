@@ -907,6 +907,11 @@ __device__ __forceinline__ void write_anchored_ghosts(double *dst, const double 
             }
 }
 
+// One thread per pair of cells (k = 2m, 2m + 1) of a row: one of the two has the colour of
+// the pass and is relaxed; in the red pass (copy_other) the other is carried into dst.  Every
+// lane of a warp thus relaxes a cell (a thread per cell would leave half the lanes of each
+// FP64 instruction idle, the colours alternating along k).  The sides are even on every grid
+// the patch sweeps (the coarsest, possibly odd, is solved by k_pbox_coarsest).
 // MASKED: interior cells with mask 0 are not relaxed (they keep their values).
 // v0 (coarse patch grids): also refresh the ghosts anchored at the cells written.
 template <bool MASKED>
@@ -916,18 +921,27 @@ __global__ void k_patch_half(const double *__restrict__ src_faces, const double 
                              unsigned long long *clamp, const unsigned char *__restrict__ mask,
                              const double *__restrict__ v0, double w)
 {
-    const long long total = (long long)p0 * p1 * p2;
+    const int h2 = p2 >> 1;
+    const long long total = (long long)p0 * p1 * h2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total)
         return;
-    const int k = (int)(t % p2);
-    const long long q = t / p2;
+    const int m = (int)(t % h2);
+    const long long q = t / h2;
     const int j = (int)(q % p1), i = (int)(q / p1);
     const int d1 = p1 + 2, d2 = p2 + 2;
     const Rows r = box_rows(d1, d2, i + 1, j + 1);
+    const int k = 2 * m + ((i + j + colour) & 1);   // (i + j + k) & 1 == colour
     const int K = k + 1;
-    // the red pass (copy_other) carries every cell it does not relax into dst
-    if (((i + j + k) & 1) != colour || (MASKED && !mask[t])) {
+    if (copy_other) {
+        const int ko = k ^ 1;                        // the pair's cell of the other colour
+        const double vo = src_faces[r.r00 + ko + 1];
+        dst[r.r00 + ko + 1] = vo;
+        if (v0)
+            write_anchored_ghosts(dst, v0, w, vo, i, j, ko, p0, p1, p2, d1, d2);
+    }
+    const long long tk = ((long long)i * p1 + j) * p2 + k;
+    if (MASKED && !mask[tk]) {
         if (copy_other) {
             const double v = src_faces[r.r00 + K];
             dst[r.r00 + K] = v;
@@ -939,7 +953,7 @@ __global__ void k_patch_half(const double *__restrict__ src_faces, const double 
     St<double> s;
     gather(src_faces, src_edges, r, K, K + 1, K - 1, s);
     bool cl = false;
-    const double v = cell_update(s, fint[t] + rhs_add, cf, cl);
+    const double v = cell_update(s, fint[tk] + rhs_add, cf, cl);
     dst[r.r00 + K] = v;
     if (v0)
         write_anchored_ghosts(dst, v0, w, v, i, j, k, p0, p1, p2, d1, d2);
@@ -952,7 +966,9 @@ cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint
                                cudaStream_t st, const double *v0, double w,
                                const unsigned char *mask)
 {
-    const long long work = (long long)pf[0] * pf[1] * pf[2];
+    if ((pf[0] | pf[1] | pf[2]) & 1)
+        return cudaErrorInvalidValue;   // the pair mapping needs even sides
+    const long long work = (long long)pf[0] * pf[1] * (pf[2] / 2);
     const int g = blocks_for(work);
     auto half = [&](const double *faces, int colour, int copy_other) {
         if (mask)
