@@ -69,8 +69,7 @@ WORK = {
 # DRAM bytes per cell measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch / its cells), for the kernel as it stands; a launch's traffic = this x its cells.
 #   sweep32: k_sweep_fused<float,1>, 256^3 finest-grid launch: 280.3 MB / 16.78 M cells
-#            (profiles/sweep32_fused_mixed256.md)
-#   sweep64: k_sweep_red + k_sweep_black<double,0>, 128^3 finest grid (profiles/sweep64_refine128.md)
+#   sweep64: k_sweep_red + k_sweep_black<double,0>, 128^3 finest grid
 TRAFFIC_PER_CELL = {
     "sweep32": 280.3e6 / 256 ** 3,
     "sweep64": 84.4e6 / 128 ** 3,          # red + black launch, cold-cache ncu capture at 128^3

@@ -82,7 +82,9 @@ typedef struct mg5_ctx mg5_ctx;  /* opaque; owns the device hierarchy, resident 
 
 /* Solver parameters.  alpha, s: coefficients of Eq. (eomvarphi) (see
  * mg5_ndgp_coefficients); h: cell size; tol: stop when
- * ||r - mean r||_2 <= tol ||s delta||_2 on the finest grid.
+ * ||r - mean r||_2 <= tol ||s delta||_2 on the finest grid (the norm is reduced
+ * from per-block counts, means and sums of squared deviations combined pairwise,
+ * so it stays accurate when |mean r| is far above the spread of r).
  * nu1, nu2: pre-/post-smoothing sweeps; nu_coarse: sweep cap on the
  * coarsest grid (which sweeps until its residual falls 1e-3);
  * max_cycles: V-cycle cap (MG5_MIXED: cap on FP64 defect-correction steps);
@@ -108,7 +110,7 @@ typedef struct {
     int levels;              /* grids in the hierarchy */
     int coarsest_n;          /* side of the coarsest grid */
     int n_history;           /* valid entries of history */
-    double rel_residual;     /* final ||r||_2 / ||s delta||_2 (FP64) */
+    double rel_residual;     /* final ||r - mean r||_2 / ||s delta||_2 (FP64) */
     double compat_c;         /* compatibility constant c of the finest grid */
     double phi_mean_removed; /* mean subtracted from phi at the end */
     long long disc_clamped;  /* cells whose discriminant was clamped */
@@ -442,10 +444,14 @@ int mg5_server_destroy(mg5_server *srv);
  *   out (device, 3 doubles) = mean r, ||r - mean r||_2, ||r||_2 for
  *   r = f + c - op(phi) on the periodic N^3 grid, op the operator of Eq. (eomvarphi)
  *   (phi, f: device, N^3 doubles, row-major, not modified; c, h, alpha as in the solve).
- * Its block partial sums live in a fixed file-scope device array of 8192
- * double2 (128 KiB), held by every GPU that loads the library until the
- * process exits: N^3 may be at most mg5_residual_norm_noalloc_max_cells()
- * (2,097,152, i.e. N <= 128); larger grids return MG5_E_TOO_LARGE.  The first
+ * Each of at most 4096 blocks (256 threads, two cells a thread) reduces its
+ * cells to (count, mean, sum of squared deviations); the blocks are combined
+ * pairwise (Chan, Golub and LeVeque), so ||r - mean r|| keeps its accuracy when
+ * |mean r| is far above the spread of r.  The block results live in a fixed
+ * file-scope device array of 4096 x 32 bytes (128 KiB), held by every GPU that
+ * loads the library until the process exits: N^3 may be at most
+ * mg5_residual_norm_noalloc_max_cells() (2,097,152, i.e. N <= 128); larger grids
+ * return MG5_E_TOO_LARGE.  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture.  All calls share the array,
  * so calls that overlap on the GPU (different streams, concurrent threads)

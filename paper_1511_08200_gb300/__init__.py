@@ -256,15 +256,47 @@ def workspace_bytes(n: int, precision=FP64) -> int:
     return out.value
 
 
-def _ptr(t, dtype="float64") -> int:
-    """Device pointer of a contiguous torch CUDA tensor of the given dtype, or None."""
+def _ptr(t, dtype="float64", device=None) -> int:
+    """Device pointer of a contiguous torch CUDA tensor of the given dtype (on `device`
+    when given), or None."""
     if t is None:
         return None
     import torch
     want = getattr(torch, dtype)
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == want and t.is_contiguous()):
         raise TypeError("expected a contiguous %s CUDA tensor" % dtype)
+    if device is not None and (t.device.index or 0) != device:
+        raise MG5Error(E_ARG, "tensor on cuda:%d, the context is on cuda:%d"
+                       % (t.device.index or 0, device))
     return t.data_ptr()
+
+
+# Shape checks, made before any pointer reaches the library: a buffer of the wrong size
+# would make the kernels read or write past its end.
+def _dims(t) -> tuple:
+    return tuple(int(x) for x in t.shape)
+
+
+def _want(t, shape, name: str):
+    """MG5Error(E_ARG) unless t (tensor or array; None passes) has exactly `shape`."""
+    if t is not None and _dims(t) != tuple(int(x) for x in shape):
+        raise MG5Error(E_ARG, "%s has shape %s, expected %s" % (name, _dims(t), tuple(shape)))
+
+
+def _cube(t, name: str) -> int:
+    """Side N of an N x N x N tensor or array; MG5Error(E_ARG) otherwise."""
+    d = _dims(t)
+    if len(d) != 3 or d[0] != d[1] or d[1] != d[2]:
+        raise MG5Error(E_ARG, "%s must be a cube N x N x N, got shape %s" % (name, d))
+    return d[0]
+
+
+def _box(t, name: str) -> tuple:
+    """Dims of a 3-D tensor or array; MG5Error(E_ARG) otherwise."""
+    d = _dims(t)
+    if len(d) != 3:
+        raise MG5Error(E_ARG, "%s must be 3-D, got shape %s" % (name, d))
+    return d
 
 
 def _stream(stream) -> int:
@@ -352,13 +384,17 @@ class Context:
         """mg5_solve_fifth_force on device tensors.  phi (out, N^3) and grad
         (out, 3 x N^3, optional) are allocated if not given.  Returns (phi, grad, Info)."""
         import torch
-        n = int(delta.shape[0])
+        n = _cube(delta, "delta")
+        _want(phi, (n, n, n), "phi")
+        _want(grad, (3, n, n, n), "grad")
         if phi is None:
             phi = torch.zeros_like(delta)
         info = _Info()
         flags = (WARM if warm else 0) | (FMG_START if fmg else 0) | (GRAPH if graph else 0)
-        rc = _lib.mg5_solve_fifth_force(self._h, _ptr(delta), n, ctypes.byref(params), flags,
-                                        _ptr(phi), _ptr(grad), ctypes.byref(info), _stream(stream))
+        dv = self.device
+        rc = _lib.mg5_solve_fifth_force(self._h, _ptr(delta, device=dv), n, ctypes.byref(params),
+                                        flags, _ptr(phi, device=dv), _ptr(grad, device=dv),
+                                        ctypes.byref(info), _stream(stream))
         if raise_on_status:
             self._check(rc, (OK, W_DISC_CLAMP))
         elif rc in (E_ARG, E_OOM, E_CUDA):
@@ -370,7 +406,11 @@ class Context:
         """Same call with HOST buffers (numpy float64 or pinned CPU tensors): the
         library copies delta in and phi / grad out (MG5_HOST_IO); graph=True replays
         the captured solve between the copies (MG5_GRAPH)."""
-        n = int(delta.shape[0])
+        n = _cube(delta, "delta")
+        if phi is None:
+            raise MG5Error(E_ARG, "phi (host, N^3) is required with host buffers")
+        _want(phi, (n, n, n), "phi")
+        _want(grad, (3, n, n, n), "grad")
         info = _Info()
         flags = HOST_IO | (WARM if warm else 0) | (FMG_START if fmg else 0) | (GRAPH if graph else 0)
         rc = _lib.mg5_solve_fifth_force(self._h, _host_ptr(delta), n, ctypes.byref(params), flags,
@@ -387,15 +427,24 @@ class Context:
         nb = len(deltas)
         if isinstance(params, Params):
             params = [params] * nb
+        ns = [_cube(d, "deltas[%d]" % b) for b, d in enumerate(deltas)]
+        for name, lst in (("params", params), ("phis", phis), ("grads", grads)):
+            if lst is not None and len(lst) != nb:
+                raise MG5Error(E_ARG, "%s has %d entries for %d boxes" % (name, len(lst), nb))
+        for b, n in enumerate(ns):
+            _want(phis[b] if phis is not None else None, (n, n, n), "phis[%d]" % b)
+            _want(grads[b] if grads is not None else None, (3, n, n, n), "grads[%d]" % b)
         if phis is None:
             phis = [torch.zeros_like(d) for d in deltas]
+        dv = self.device
         P = ctypes.c_void_p * nb
         parr = (Params * nb)(*params)
-        narr = (_c_int * nb)(*[int(d.shape[0]) for d in deltas])
-        garr = P(*[_ptr(g) for g in grads]) if grads is not None else None
+        narr = (_c_int * nb)(*ns)
+        garr = P(*[_ptr(g, device=dv) for g in grads]) if grads is not None else None
         infos = (_Info * nb)()
-        rc = _lib.mg5_solve_batch(self._h, nb, P(*[_ptr(d) for d in deltas]), narr, parr,
-                                  P(*[_ptr(x) for x in phis]), garr, infos, _stream(stream))
+        rc = _lib.mg5_solve_batch(self._h, nb, P(*[_ptr(d, device=dv) for d in deltas]), narr, parr,
+                                  P(*[_ptr(x, device=dv) for x in phis]), garr, infos,
+                                  _stream(stream))
         if raise_on_status:
             self._check(rc, (OK, W_DISC_CLAMP))
         elif rc in (E_ARG, E_OOM, E_CUDA):
@@ -404,32 +453,40 @@ class Context:
 
     def force(self, phi, h: float, ghost: int = 0, periodic: bool = True, grad=None, stream=None):
         import torch
-        dims = [int(x) for x in phi.shape]
+        dims = list(_box(phi, "phi"))
         inner = [d - 2 * ghost for d in dims]
+        if ghost < 0 or min(inner) < 1:
+            raise MG5Error(E_ARG, "ghost %d leaves no interior in %s" % (ghost, tuple(dims)))
+        _want(grad, [3] + inner, "grad")
         if grad is None:
             grad = torch.empty([3] + inner, dtype=phi.dtype, device=phi.device)
-        self._check(_lib.mg5_force(self._h, _ptr(phi), _I3(*dims), ghost, h, 1 if periodic else 0,
-                                   _ptr(grad), _stream(stream)))
+        dv = self.device
+        self._check(_lib.mg5_force(self._h, _ptr(phi, device=dv), _I3(*dims), ghost, h,
+                                   1 if periodic else 0, _ptr(grad, device=dv), _stream(stream)))
         return grad
 
     def refine_interpolate(self, phi_coarse, origin, pn, ghost: int, out=None, stream=None):
         import torch
-        nc = int(phi_coarse.shape[0])
+        nc = _cube(phi_coarse, "phi_coarse")
         dims = [2 * int(p) + 2 * ghost for p in pn]
+        _want(out, dims, "out")
         if out is None:
             out = torch.empty(dims, dtype=phi_coarse.dtype, device=phi_coarse.device)
-        self._check(_lib.mg5_refine_interpolate(self._h, _ptr(phi_coarse), nc, _I3(*origin),
+        _ptr(out, device=self.device)
+        self._check(_lib.mg5_refine_interpolate(self._h, _ptr(phi_coarse, device=self.device), nc, _I3(*origin),
                                                 _I3(*pn), ghost, _ptr(out), _stream(stream)))
         return out
 
     def refine_interpolate_cubic(self, phi_coarse, origin, pn, ghost: int, out=None, stream=None):
         """mg5_refine_interpolate_cubic: the tricubic variant of refine_interpolate."""
         import torch
-        nc = int(phi_coarse.shape[0])
+        nc = _cube(phi_coarse, "phi_coarse")
         dims = [2 * int(p) + 2 * ghost for p in pn]
+        _want(out, dims, "out")
         if out is None:
             out = torch.empty(dims, dtype=phi_coarse.dtype, device=phi_coarse.device)
-        self._check(_lib.mg5_refine_interpolate_cubic(self._h, _ptr(phi_coarse), nc, _I3(*origin),
+        _ptr(out, device=self.device)
+        self._check(_lib.mg5_refine_interpolate_cubic(self._h, _ptr(phi_coarse, device=self.device), nc, _I3(*origin),
                                                       _I3(*pn), ghost, _ptr(out), _stream(stream)))
         return out
 
@@ -437,10 +494,13 @@ class Context:
         """mg5_refine_interpolate_box: child window [origin, origin + pn) of a parent box
         (dims box.shape, interior offset pg) -> fine box (2 pn + 2 ghost per axis)."""
         import torch
+        bd = _box(box, "box")
         dims = [2 * int(p) + 2 * ghost for p in pn]
+        _want(out, dims, "out")
         if out is None:
             out = torch.empty(dims, dtype=box.dtype, device=box.device)
-        self._check(_lib.mg5_refine_interpolate_box(self._h, _ptr(box), _I3(*[int(x) for x in box.shape]),
+        _ptr(out, device=self.device)
+        self._check(_lib.mg5_refine_interpolate_box(self._h, _ptr(box, device=self.device), _I3(*bd),
                                                     pg, _I3(*origin), _I3(*pn), ghost, _ptr(out),
                                                     _stream(stream)))
         return out
@@ -449,11 +509,15 @@ class Context:
                     raise_on_status=True, graph=False):
         """mg5_relax_patch (graph=True: mg5_relax_patch_graph): phi_box ((pf + 2)^3, ghosts
         fixed) is relaxed in place."""
-        pf = [int(x) for x in delta_fine.shape]
+        pf = list(_box(delta_fine, "delta_fine"))
+        if phi_box is None:
+            raise MG5Error(E_ARG, "phi_box is required")
+        _want(phi_box, [x + 2 for x in pf], "phi_box")
         info = _Info()
         fn = _lib.mg5_relax_patch_graph if graph else _lib.mg5_relax_patch
-        rc = fn(self._h, _ptr(delta_fine), _I3(*pf), ctypes.byref(params),
-                compat_c, _ptr(phi_box), ctypes.byref(info), _stream(stream))
+        dv = self.device
+        rc = fn(self._h, _ptr(delta_fine, device=dv), _I3(*pf), ctypes.byref(params),
+                compat_c, _ptr(phi_box, device=dv), ctypes.byref(info), _stream(stream))
         if raise_on_status:
             self._check(rc, (OK, W_DISC_CLAMP))
         return phi_box, Info._from(info)
@@ -462,13 +526,17 @@ class Context:
                            stream=None, raise_on_status=True):
         """mg5_relax_patch_masked: relax only the cells of `mask` (uint8, shape of delta_fine);
         the others keep their values (Sec. 3.3)."""
-        pf = [int(x) for x in delta_fine.shape]
-        if tuple(mask.shape) != tuple(pf):
-            raise ValueError("mask must have the shape of delta_fine")
+        pf = list(_box(delta_fine, "delta_fine"))
+        if mask is None or phi_box is None:
+            raise MG5Error(E_ARG, "mask and phi_box are required")
+        _want(mask, pf, "mask")
+        _want(phi_box, [x + 2 for x in pf], "phi_box")
         info = _Info()
-        rc = _lib.mg5_relax_patch_masked(self._h, _ptr(delta_fine), _I3(*pf), _ptr(mask, "uint8"),
-                                         ctypes.byref(params), compat_c, _ptr(phi_box),
-                                         ctypes.byref(info), _stream(stream))
+        dv = self.device
+        rc = _lib.mg5_relax_patch_masked(self._h, _ptr(delta_fine, device=dv), _I3(*pf),
+                                         _ptr(mask, "uint8", device=dv), ctypes.byref(params),
+                                         compat_c, _ptr(phi_box, device=dv), ctypes.byref(info),
+                                         _stream(stream))
         if raise_on_status:
             self._check(rc, (OK, W_DISC_CLAMP))
         return phi_box, Info._from(info)
@@ -480,67 +548,103 @@ class Context:
         periodic domain, or on a refinement's interior with periodic=False).  Returns the
         mask, or (mask, number of ones) with count=True."""
         import torch
-        pd = [int(x) for x in grad_phi.shape[1:]]
+        gd = _dims(grad_phi)
+        if len(gd) != 4 or gd[0] != 3:
+            raise MG5Error(E_ARG, "grad_phi must have shape (3, d0, d1, d2), got %s" % (gd,))
+        _want(grad_gr, gd, "grad_gr")
+        pd = list(gd[1:])
         dims = [2 * int(p) for p in pn]
+        _want(out, dims, "out")
         if out is None:
             out = torch.empty(dims, dtype=torch.uint8, device=grad_phi.device)
         n = ctypes.c_longlong(0)
-        self._check(_lib.mg5_parent_force_mask(self._h, _ptr(grad_phi), _ptr(grad_gr), _I3(*pd),
+        dv = self.device
+        self._check(_lib.mg5_parent_force_mask(self._h, _ptr(grad_phi, device=dv),
+                                               _ptr(grad_gr, device=dv), _I3(*pd),
                                                1 if periodic else 0, _I3(*origin), _I3(*pn),
-                                               theta, _ptr(out, "uint8"),
+                                               theta, _ptr(out, "uint8", device=dv),
                                                ctypes.byref(n) if count else None,
                                                _stream(stream)))
         return (out, int(n.value)) if count else out
 
     # ------------------------------------------------------------ single steps
+    def _cubes(self, n, **tensors):
+        """Every given tensor (None passes) must be n x n x n."""
+        for name, t in tensors.items():
+            _want(t, (n, n, n), name)
+
     def step_sweep(self, phi_in, f, c: float, h: float, alpha: float, out=None, stream=None):
         import torch
+        n = _cube(phi_in, "phi_in")
+        self._cubes(n, f=f, out=out)
         out = torch.empty_like(phi_in) if out is None else out
-        self._check(_lib.mg5_step_sweep(self._h, _ptr(phi_in), _ptr(out), _ptr(f), c,
-                                        int(phi_in.shape[0]), h, alpha, _stream(stream)))
+        dv = self.device
+        self._check(_lib.mg5_step_sweep(self._h, _ptr(phi_in, device=dv), _ptr(out, device=dv),
+                                        _ptr(f, device=dv), c, n, h, alpha, _stream(stream)))
         return out
 
     def step_sweep_fused(self, phi_in, f, c: float, h: float, alpha: float, out=None, stream=None):
         import torch
+        n = _cube(phi_in, "phi_in")
+        self._cubes(n, f=f, out=out)
         out = torch.empty_like(phi_in) if out is None else out
-        self._check(_lib.mg5_step_sweep_fused(self._h, _ptr(phi_in), _ptr(out), _ptr(f), c,
-                                              int(phi_in.shape[0]), h, alpha, _stream(stream)))
+        dv = self.device
+        self._check(_lib.mg5_step_sweep_fused(self._h, _ptr(phi_in, device=dv),
+                                              _ptr(out, device=dv), _ptr(f, device=dv), c, n, h,
+                                              alpha, _stream(stream)))
         return out
 
     def step_sweep_f32(self, e_in, f, c: float, h: float, alpha: float, base=None, fused=False,
                        out=None, stream=None):
         import torch
+        n = _cube(e_in, "e_in")
+        self._cubes(n, f=f, base=base, out=out)
         out = torch.empty_like(e_in) if out is None else out
-        self._check(_lib.mg5_step_sweep_f32(self._h, _ptr(e_in, "float32"), _ptr(out, "float32"),
-                                            _ptr(f, "float32"), _ptr(base, "float32"), c,
-                                            int(e_in.shape[0]), h, alpha, 1 if fused else 0,
-                                            _stream(stream)))
+        dv = self.device
+        self._check(_lib.mg5_step_sweep_f32(self._h, _ptr(e_in, "float32", dv),
+                                            _ptr(out, "float32", dv), _ptr(f, "float32", dv),
+                                            _ptr(base, "float32", dv), c, n, h, alpha,
+                                            1 if fused else 0, _stream(stream)))
         return out
 
     def step_operator(self, phi, h: float, alpha: float, out=None, stream=None):
         import torch
+        n = _cube(phi, "phi")
+        self._cubes(n, out=out)
         out = torch.empty_like(phi) if out is None else out
-        self._check(_lib.mg5_step_operator(self._h, _ptr(phi), int(phi.shape[0]), h, alpha,
-                                           _ptr(out), _stream(stream)))
+        dv = self.device
+        self._check(_lib.mg5_step_operator(self._h, _ptr(phi, device=dv), n, h, alpha,
+                                           _ptr(out, device=dv), _stream(stream)))
         return out
 
     def step_residual(self, phi, f, c: float, h: float, alpha: float, out=None, stream=None):
         import torch
+        n = _cube(phi, "phi")
+        self._cubes(n, f=f, out=out)
         out = torch.empty_like(phi) if out is None else out
-        self._check(_lib.mg5_step_residual(self._h, _ptr(phi), _ptr(f), c, int(phi.shape[0]), h,
-                                           alpha, _ptr(out), _stream(stream)))
+        dv = self.device
+        self._check(_lib.mg5_step_residual(self._h, _ptr(phi, device=dv), _ptr(f, device=dv), c, n,
+                                           h, alpha, _ptr(out, device=dv), _stream(stream)))
         return out
 
     def step_restrict(self, fine, out=None, stream=None):
         import torch
-        n = int(fine.shape[0])
+        n = _cube(fine, "fine")
+        if n % 2:
+            raise MG5Error(E_ARG, "fine grid side %d is odd" % n)
+        self._cubes(n // 2, out=out)
         out = torch.empty((n // 2,) * 3, dtype=fine.dtype, device=fine.device) if out is None else out
-        self._check(_lib.mg5_step_restrict(self._h, _ptr(fine), n, _ptr(out), _stream(stream)))
+        dv = self.device
+        self._check(_lib.mg5_step_restrict(self._h, _ptr(fine, device=dv), n, _ptr(out, device=dv),
+                                           _stream(stream)))
         return out
 
     def step_prolong_add(self, coarse, fine, stream=None):
-        self._check(_lib.mg5_step_prolong_add(self._h, _ptr(coarse), int(coarse.shape[0]),
-                                              _ptr(fine), _stream(stream)))
+        nc = _cube(coarse, "coarse")
+        self._cubes(2 * nc, fine=fine)
+        dv = self.device
+        self._check(_lib.mg5_step_prolong_add(self._h, _ptr(coarse, device=dv), nc,
+                                              _ptr(fine, device=dv), _stream(stream)))
         return fine
 
 
@@ -564,10 +668,18 @@ class Server:
         rc = _lib.mg5_server_create(ctypes.byref(self._h), device, slots, hbm_budget_bytes)
         if rc != OK:
             raise MG5Error(rc, "mg5_server_create failed")
+        self.device = device
         self._keep = {}
 
     def submit(self, delta, params: Params, phi, grad=None, tag: int = 0):
-        req = _Request(_ptr(delta), int(delta.shape[0]), params, _ptr(phi), _ptr(grad), tag)
+        n = _cube(delta, "delta")
+        if phi is None:
+            raise MG5Error(E_ARG, "phi is required")
+        _want(phi, (n, n, n), "phi")
+        _want(grad, (3, n, n, n), "grad")
+        dv = self.device
+        req = _Request(_ptr(delta, device=dv), n, params, _ptr(phi, device=dv),
+                       _ptr(grad, device=dv), tag)
         rc = _lib.mg5_server_submit(self._h, ctypes.byref(req))
         if rc != OK:
             raise MG5Error(rc, "submit rejected")
@@ -620,10 +732,14 @@ def residual_norm_noalloc(phi, f, c: float, h: float, alpha: float, out=None, st
     3-element float64 device tensor, with no device allocation by the library (its partial
     sums live in a fixed device array; N^3 <= residual_norm_noalloc_max_cells())."""
     import torch
+    n = _cube(phi, "phi")
+    _want(f, (n, n, n), "f")
+    _want(out, (3,), "out")
     if out is None:
         out = torch.empty(3, dtype=torch.float64, device=phi.device)
-    rc = _lib.mg5_residual_norm_noalloc(_ptr(phi), _ptr(f), c, int(phi.shape[0]), h, alpha,
-                                        _ptr(out), _stream(stream))
+    dv = phi.device.index or 0
+    rc = _lib.mg5_residual_norm_noalloc(_ptr(phi), _ptr(f, device=dv), c, n, h, alpha,
+                                        _ptr(out, device=dv), _stream(stream))
     if rc != OK:
         raise MG5Error(rc, "residual_norm_noalloc")
     return out

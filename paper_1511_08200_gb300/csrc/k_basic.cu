@@ -126,11 +126,11 @@ cudaError_t launch_operator(const T *phi, int n, CoefT<T> cf, T *out, cudaStream
 template <typename T>
 __global__ void k_residual(const T *__restrict__ phi, const T *__restrict__ f,
                            const double *__restrict__ cptr, int n, CoefT<T> cf, T *__restrict__ r_out,
-                           double2 *__restrict__ partials)
+                           Moments *__restrict__ partials)
 {
     const long long total = (long long)n * n * n;
     const double c = *cptr;
-    double2 acc = make_double2(0.0, 0.0);
+    MomAcc<T> acc;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(t % n);
@@ -143,12 +143,11 @@ __global__ void k_residual(const T *__restrict__ phi, const T *__restrict__ f,
         const T res = f[t] + (T)c - cell_op(s, cf);
         if (r_out)
             r_out[t] = res;
-        acc.x += (double)res;
-        acc.y += (double)res * (double)res;
+        acc.add(res);
     }
-    acc = block_sum2(acc);
+    const Moments m = block_moments(acc.get());
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = acc;
+        partials[blockIdx.x] = m;
 }
 
 template <typename T>
@@ -157,9 +156,9 @@ cudaError_t launch_residual(const T *phi, const T *f, const double *cptr, int n,
 {
     const long long work = (long long)n * n * n;
     int g = blocks_for(work);
-    if (g > kReduceGrid)
-        g = kReduceGrid;
-    k_residual<T><<<g, kBlock, 0, st>>>(phi, f, cptr, n, cf, r, partials);
+    if (g > kMomentBlocks)
+        g = kMomentBlocks;
+    k_residual<T><<<g, kBlock, 0, st>>>(phi, f, cptr, n, cf, r, reinterpret_cast<Moments *>(partials));
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();
@@ -170,12 +169,12 @@ template <typename T, bool BASE>
 __global__ void k_resid_restrict(const T *__restrict__ v, const T *__restrict__ f,
                                  const double *__restrict__ cptr, int n, CoefT<T> cf,
                                  T *__restrict__ vc, T *__restrict__ v0c, T *__restrict__ rc,
-                                 double2 *__restrict__ partials, const T *__restrict__ B)
+                                 Moments *__restrict__ partials, const T *__restrict__ B)
 {
     const int nc = n >> 1;
     const long long total = (long long)nc * nc * nc;
     const double c = *cptr;
-    double2 acc = make_double2(0.0, 0.0);
+    MomAcc<T> acc;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const int K = (int)(t % nc);
@@ -194,17 +193,16 @@ __global__ void k_resid_restrict(const T *__restrict__ v, const T *__restrict__ 
             const T res = f[r.r00 + k] + (T)c - opr<T, BASE>(s, sb, cf);
             sv += s.c;
             sr += res;
-            acc.x += (double)res;
-            acc.y += (double)res * (double)res;
+            acc.add(res);
         }
         const T mv = sv * (T)0.125;
         vc[t] = mv;
         v0c[t] = mv;
         rc[t] = sr * (T)0.125;
     }
-    acc = block_sum2(acc);
+    const Moments m = block_moments(acc.get());
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = acc;
+        partials[blockIdx.x] = m;
 }
 
 template <typename T>
@@ -214,12 +212,13 @@ cudaError_t launch_resid_restrict(const T *v, const T *f, const double *cptr, in
 {
     const long long work = (long long)(n / 2) * (n / 2) * (n / 2);
     int g = blocks_for(work);
-    if (g > kReduceGrid)
-        g = kReduceGrid;
+    if (g > kMomentBlocks)
+        g = kMomentBlocks;
+    Moments *mp = reinterpret_cast<Moments *>(partials);
     if (B)
-        k_resid_restrict<T, true><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, partials, B);
+        k_resid_restrict<T, true><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, mp, B);
     else
-        k_resid_restrict<T, false><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, partials, B);
+        k_resid_restrict<T, false><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, mp, B);
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();
@@ -566,6 +565,25 @@ cudaError_t launch_coarsest(T *v, T *tmp, const T *f, int n, CoefT<T> cf, double
 __global__ void k_finalize(const double2 *__restrict__ partials, int nb, double ncells,
                            LevelScal *ls, int mode)
 {
+    if (mode == FIN_RESID || mode == FIN_STATS) {
+        // per-block Moments, combined in a fixed order (deterministic)
+        const Moments *mp = reinterpret_cast<const Moments *>(partials);
+        Moments v{0.0, 0.0, 0.0, 0.0};
+        for (int b = threadIdx.x; b < nb; b += blockDim.x)
+            v = mom_combine(v, mp[b]);
+        v = block_moments(v);
+        if (threadIdx.x != 0)
+            return;
+        const double m = v.mean;
+        ls->m = m;
+        if (mode == FIN_RESID)
+            ls->c -= m;
+        ls->rnorm = sqrt(v.m2);
+        ls->rel = ls->fnorm > 0.0 ? ls->rnorm / ls->fnorm : ls->rnorm;
+        if (!isfinite(v.mean) || !isfinite(v.m2))
+            ls->rel = v.mean + v.m2;  // propagates NaN / Inf to the host check
+        return;
+    }
     double2 acc = make_double2(0.0, 0.0);
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         acc.x += partials[b].x;
@@ -574,24 +592,7 @@ __global__ void k_finalize(const double2 *__restrict__ partials, int nb, double 
     acc = block_sum2(acc);
     if (threadIdx.x != 0)
         return;
-    if (mode == FIN_RESID) {
-        const double m = acc.x / ncells;
-        const double q2 = acc.y - ncells * m * m;
-        ls->m = m;
-        ls->c -= m;
-        ls->rnorm = sqrt(q2 > 0.0 ? q2 : 0.0);
-        ls->rel = ls->fnorm > 0.0 ? ls->rnorm / ls->fnorm : ls->rnorm;
-        if (!isfinite(acc.x) || !isfinite(acc.y))
-            ls->rel = acc.y + acc.x;  // propagates NaN / Inf to the host check
-    } else if (mode == FIN_STATS) {
-        const double m = acc.x / ncells;
-        const double q2 = acc.y - ncells * m * m;
-        ls->m = m;
-        ls->rnorm = sqrt(q2 > 0.0 ? q2 : 0.0);
-        ls->rel = ls->fnorm > 0.0 ? ls->rnorm / ls->fnorm : ls->rnorm;
-        if (!isfinite(acc.x) || !isfinite(acc.y))
-            ls->rel = acc.y + acc.x;
-    } else if (mode == FIN_NORM) {
+    if (mode == FIN_NORM) {
         ls->m = acc.x / ncells;
         ls->rnorm = sqrt(acc.y);
         ls->rel = ls->fnorm > 0.0 ? ls->rnorm / ls->fnorm : ls->rnorm;

@@ -35,11 +35,11 @@ template <typename T, bool BASE>
 __global__ void k_spec_residual(const T *__restrict__ v, const T *__restrict__ f,
                                 const double *__restrict__ cptr, int n, CoefT<T> cf,
                                 const T *__restrict__ B, typename Cplx<T>::type *__restrict__ out,
-                                double2 *__restrict__ partials, int *sweeps)
+                                Moments *__restrict__ partials, int *sweeps)
 {
     const int n3 = n * n * n;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    double2 acc = make_double2(0.0, 0.0);
+    MomAcc<T> acc;
     if (t < n3) {
         const int k = t % n, j = (t / n) % n, i = t / (n * n);
         const Rows r = periodic_rows(n, i, j);
@@ -51,12 +51,11 @@ __global__ void k_spec_residual(const T *__restrict__ v, const T *__restrict__ f
         const T res = f[t] + (T)(*cptr) - opr<T, BASE>(s, sb, cf);
         out[t].x = res;
         out[t].y = (T)0;
-        acc.x = (double)res;
-        acc.y = (double)res * (double)res;
+        acc.add(res);
     }
-    acc = block_sum2(acc);
+    const Moments m = block_moments(acc.get());
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = acc;
+        partials[blockIdx.x] = m;
         if (blockIdx.x == 0 && sweeps)
             atomicAdd(sweeps, 2);
     }
@@ -131,15 +130,15 @@ cudaError_t launch_coarsest_spectral(T *v, T *tmp, const T *f, int n, CoefT<T> c
     C *w0 = static_cast<C *>(w0v), *w1 = static_cast<C *>(w1v);
     const int n3 = n * n * n;
     const int g = (n3 + kBlock - 1) / kBlock;
-    if (g > kMaxPartials)
+    if (g > kMomentBlocks)
         return cudaErrorInvalidValue;
+    Moments *mp = reinterpret_cast<Moments *>(partials);
     const T inv_n3 = (T)1 / (T)n3;
     for (int it = 0; it < iters; ++it) {
         if (B)
-            k_spec_residual<T, true><<<g, kBlock, 0, st>>>(v, f, &ls->c, n, cf, B, w0, partials, sweeps);
+            k_spec_residual<T, true><<<g, kBlock, 0, st>>>(v, f, &ls->c, n, cf, B, w0, mp, sweeps);
         else
-            k_spec_residual<T, false><<<g, kBlock, 0, st>>>(v, f, &ls->c, n, cf, B, w0, partials,
-                                                            sweeps);
+            k_spec_residual<T, false><<<g, kBlock, 0, st>>>(v, f, &ls->c, n, cf, B, w0, mp, sweeps);
         count_launch(1);
         cudaError_t e = launch_finalize(partials, g, (double)n3, ls, FIN_RESID, st);   // c -= mean r
         if (e != cudaSuccess)

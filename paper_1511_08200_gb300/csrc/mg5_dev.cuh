@@ -456,6 +456,99 @@ __device__ __forceinline__ T opr(const St<T> &s, const St<T> &B, const CoefT<T> 
         return cell_op(s, cf);
 }
 
+// ---- residual statistics -----------------------------------------------------
+// Count, mean and M2 = sum (r - mean)^2 of a set of residual values.  The stopping
+// test needs ||r - mean r||; forming it as sum r^2 - N mean^2 cancels when |mean| is
+// far above the spread (a stale compatibility constant, a warm start, a source with a
+// non-zero mean), so sets are combined by the pairwise update of Chan, Golub and
+// LeVeque (1979) instead:  n = na + nb, d = mean_b - mean_a,
+// mean = mean_a + d nb / n, M2 = M2_a + M2_b + d^2 na nb / n.
+// Two double2 slots of a partial-sum buffer hold one Moments.
+struct __align__(16) Moments {
+    double n, mean, m2, pad;
+};
+
+__device__ __forceinline__ Moments mom_combine(const Moments &a, const Moments &b)
+{
+    if (b.n == 0.0)
+        return a;
+    if (a.n == 0.0)
+        return b;
+    const double n = a.n + b.n, w = b.n / n, d = b.mean - a.mean;
+    Moments r;
+    r.n = n;
+    r.mean = fma(d, w, a.mean);
+    r.m2 = a.m2 + b.m2 + d * d * (a.n * w);
+    r.pad = 0.0;
+    return r;
+}
+
+// One thread's values, taken relative to its first value (the shifted-data form:
+// the squares carry the spread, not the mean), in the kernel's own precision T.
+template <typename T>
+struct MomAcc {
+    int n = 0;
+    T k = 0, s = 0, q = 0;
+    __device__ __forceinline__ void add(T x)
+    {
+        if (n == 0)
+            k = x;
+        const T d = x - k;
+        s += d;
+        q = fma(d, d, q);
+        ++n;
+    }
+    __device__ __forceinline__ Moments get() const
+    {
+        Moments m{0.0, 0.0, 0.0, 0.0};
+        if (n > 0) {
+            m.n = (double)n;
+            const double sd = (double)s, md = sd / m.n;
+            m.mean = (double)k + md;
+            const double m2 = fma(-sd, md, (double)q);
+            m.m2 = m2 > 0.0 ? m2 : (m2 == m2 ? 0.0 : m2);   // keeps a NaN
+        }
+        return m;
+    }
+};
+
+__device__ __forceinline__ Moments mom_shfl_down(const Moments &v, int o)
+{
+    Moments r;
+    r.n = __shfl_down_sync(0xffffffffu, v.n, o);
+    r.mean = __shfl_down_sync(0xffffffffu, v.mean, o);
+    r.m2 = __shfl_down_sync(0xffffffffu, v.m2, o);
+    r.pad = 0.0;
+    return r;
+}
+
+// Deterministic combination over the block; the result is valid in thread 0.
+// Every thread of the block must call it.
+__device__ __forceinline__ Moments block_moments(Moments v)
+{
+    __shared__ Moments smem_mom[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const Moments u = mom_shfl_down(v, o);
+        if ((threadIdx.x & 31) + o < 32)
+            v = mom_combine(v, u);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0)
+        smem_mom[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < nw ? smem_mom[lane] : Moments{0.0, 0.0, 0.0, 0.0};
+        for (int o = 16; o > 0; o >>= 1) {
+            const Moments u = mom_shfl_down(v, o);
+            if (lane + o < 32)
+                v = mom_combine(v, u);
+        }
+    }
+    return v;
+}
+
 // Deterministic sum of a double2 over the block; the result is valid in thread 0.
 // Every thread of the block must call it.
 __device__ __forceinline__ double2 block_sum2(double2 v)

@@ -32,7 +32,9 @@ constexpr int kScalSlots = 48;   // LevelScal slots held by a context
 constexpr int kPatchSlot = 16;   // slot used by the patch relaxation
 constexpr int kStepSlot = 17;    // slot used by the single-step entry points
 constexpr int kInnerBase = 20;   // first slot of the mixed solve's FP32 grids
-constexpr int kMaxPartials = 8192;  // partial-sum slots per reduction
+constexpr int kMaxPartials = 8192;  // partial-sum slots (double2) per reduction
+// blocks of a residual-statistics reduction: each writes one Moments (two slots)
+constexpr int kMomentBlocks = kMaxPartials / 2;
 
 // Number of blocks of kBlock threads to cover `work` items (capped for reductions).
 inline int blocks_for(long long work) { return (int)((work + kBlock - 1) / kBlock); }
@@ -52,7 +54,8 @@ void count_launch(long long n);
 long long launches_total();
 
 // finalize modes
-// FIN_RESID: m = mean r, c -= m, rnorm = ||r - m||, rel = rnorm / fnorm
+// FIN_RESID: m = mean r, c -= m, rnorm = ||r - m||, rel = rnorm / fnorm; the partials
+//            are Moments (count, mean, M2) per block, combined pairwise
 // FIN_STATS: as FIN_RESID but c is left alone
 // FIN_NORM:  rnorm = ||r|| (no projection), rel = rnorm / fnorm
 // FIN_FNORM: fnorm = sqrt(sum of the second component)

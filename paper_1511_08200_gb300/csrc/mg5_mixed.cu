@@ -38,19 +38,18 @@ template <bool ZERO>
 __global__ void k_resid64_mixed(const double *__restrict__ phi, const double *__restrict__ f,
                                 const double *__restrict__ cptr, int n, CoefT<double> cf,
                                 float *__restrict__ r32, float *__restrict__ B,
-                                double2 *__restrict__ partials)
+                                Moments *__restrict__ partials)
 {
     const long long total = (long long)n * n * n;
     const double c = *cptr;
-    double2 acc = make_double2(0.0, 0.0);
+    MomAcc<double> acc;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         if constexpr (ZERO) {
             const double res = f[t] + c;
             r32[t] = (float)res;
             B[t] = 0.0f;
-            acc.x += res;
-            acc.y += res * res;
+            acc.add(res);
             continue;
         }
         const int k = (int)(t % n);
@@ -63,12 +62,11 @@ __global__ void k_resid64_mixed(const double *__restrict__ phi, const double *__
         const double res = f[t] + c - cell_op(s, cf);
         r32[t] = (float)res;
         B[t] = (float)s.c;
-        acc.x += res;
-        acc.y += res * res;
+        acc.add(res);
     }
-    acc = block_sum2(acc);
+    const Moments m = block_moments(acc.get());
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = acc;
+        partials[blockIdx.x] = m;
 }
 
 __global__ void k_update_mixed(double *__restrict__ phi, const float *__restrict__ e, long long n3)
@@ -324,17 +322,18 @@ int phase_residual(MixedHier *h, const MixedShared &sh, const mg5_params *p, dou
     const int N = h->N;
     const long long n3 = (long long)N * N * N;
     int grid = blocks_for(n3);
-    if (grid > kMaxPartials)
-        grid = kMaxPartials;
+    if (grid > kMomentBlocks)
+        grid = kMomentBlocks;
     {
         ProfScope ps(sh.prof, PK_RESID64_MIXED, st, (double)n3);
         const CoefT<double> cf = make_coef<double>(p->h, p->alpha);
+        Moments *mp = reinterpret_cast<Moments *>(sh.partials);
         if (zero)
             k_resid64_mixed<true><<<grid, kBlock, 0, st>>>(phi, h->f64, &sh.ls[0].c, N, cf,
-                                                           h->f[0], h->B[0], sh.partials);
+                                                           h->f[0], h->B[0], mp);
         else
             k_resid64_mixed<false><<<grid, kBlock, 0, st>>>(phi, h->f64, &sh.ls[0].c, N, cf,
-                                                            h->f[0], h->B[0], sh.partials);
+                                                            h->f[0], h->B[0], mp);
     }
     count_launch(1);
     CKM(cudaGetLastError());

@@ -18,25 +18,26 @@
 namespace {
 
 constexpr int kNoAllocThreads = 256;
-constexpr int kNoAllocMaxBlocks = 8192;   // one block per 256 cells: N^3 <= 2,097,152 (N <= 128)
+constexpr int kNoAllocMaxBlocks = 4096;       // one Moments slot per block
+constexpr int kNoAllocCellsPerThread = 2;     // N^3 <= 4096 * 256 * 2 = 2,097,152 (N <= 128)
 constexpr int kNoAllocMaxDevices = 64;
 
-// Shared by every call on a device and kept until the process exits; a call
+// Shared by every call on a device and kept until the process exits (128 KiB); a call
 // overwrites exactly the slots it reads, so nothing needs clearing.
-static __device__ __align__(256) double2 g_noalloc_partials[kNoAllocMaxBlocks];
+static __device__ __align__(256) mg5::Moments g_noalloc_partials[kNoAllocMaxBlocks];
 
 std::mutex g_noalloc_mu;
-double2 *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+mg5::Moments *g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
-// r = f + c - op(phi) on the periodic cube; block partial sums (sum r, sum r^2)
+// r = f + c - op(phi) on the periodic cube; per block (count, mean, M2) of r
 __global__ void k_residual_partials(const double *__restrict__ phi, const double *__restrict__ f,
-                                    double c, int n, mg5::CoefT<double> cf, double2 *partials)
+                                    double c, int n, mg5::CoefT<double> cf, mg5::Moments *partials)
 {
     using namespace mg5;
     const long long total = (long long)n * n * n;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double2 acc = make_double2(0.0, 0.0);
-    if (t < total) {
+    MomAcc<double> acc;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(t % n);
         const long long q = t / n;
         const int j = (int)(q % n), i = (int)(q / n);
@@ -44,36 +45,31 @@ __global__ void k_residual_partials(const double *__restrict__ phi, const double
         const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
         St<double> s;
         gather(phi, phi, r, k, kp, km, s);
-        const double res = f[t] + c - cell_op(s, cf);
-        acc.x = res;
-        acc.y = res * res;
+        acc.add(f[t] + c - cell_op(s, cf));
     }
-    acc = block_sum2(acc);
+    const Moments m = block_moments(acc.get());
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = acc;
+        partials[blockIdx.x] = m;
 }
 
-// out[0] = mean r, out[1] = ||r - mean r||_2, out[2] = ||r||_2 (fixed summation order)
-__global__ void k_norm_finalize(const double2 *__restrict__ partials, int nb, double ncells,
-                                double *out)
+// out[0] = mean r, out[1] = ||r - mean r||_2, out[2] = ||r||_2, the block moments
+// combined pairwise in a fixed order (no cancellation when |mean r| >> its spread)
+__global__ void k_norm_finalize(const mg5::Moments *__restrict__ partials, int nb, double *out)
 {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        acc.x += partials[b].x;
-        acc.y += partials[b].y;
-    }
-    acc = mg5::block_sum2(acc);
+    using namespace mg5;
+    Moments v{0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        v = mom_combine(v, partials[b]);
+    v = block_moments(v);
     if (threadIdx.x == 0) {
-        const double m = acc.x / ncells;
-        const double q2 = acc.y - ncells * m * m;
-        out[0] = m;
-        out[1] = sqrt(q2 > 0.0 ? q2 : 0.0);
-        out[2] = sqrt(acc.y);
+        out[0] = v.mean;
+        out[1] = sqrt(v.m2);
+        out[2] = sqrt(fma(v.n * v.mean, v.mean, v.m2));   // sum r^2 = M2 + n mean^2
     }
 }
 
-// Device address of this device's partial-sum array, looked up once per device.
-cudaError_t partials_address(double2 **out)
+// Device address of this device's partial array, looked up once per device.
+cudaError_t partials_address(mg5::Moments **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -87,7 +83,7 @@ cudaError_t partials_address(double2 **out)
         e = cudaGetSymbolAddress(&p, g_noalloc_partials);
         if (e != cudaSuccess)
             return e;
-        g_noalloc_ptr[dev] = static_cast<double2 *>(p);
+        g_noalloc_ptr[dev] = static_cast<mg5::Moments *>(p);
     }
     *out = g_noalloc_ptr[dev];
     return cudaSuccess;
@@ -99,7 +95,7 @@ extern "C" {
 
 long long mg5_residual_norm_noalloc_max_cells(void)
 {
-    return (long long)kNoAllocMaxBlocks * kNoAllocThreads;
+    return (long long)kNoAllocMaxBlocks * kNoAllocThreads * kNoAllocCellsPerThread;
 }
 
 int mg5_residual_norm_noalloc(const double *phi, const double *f, double c, int N, double h,
@@ -110,16 +106,18 @@ int mg5_residual_norm_noalloc(const double *phi, const double *f, double c, int 
     const long long n3 = (long long)N * N * N;
     if (n3 > mg5_residual_norm_noalloc_max_cells())
         return MG5_E_TOO_LARGE;
-    double2 *partials = nullptr;
+    mg5::Moments *partials = nullptr;
     if (partials_address(&partials) != cudaSuccess) {
         cudaGetLastError();
         return MG5_E_CUDA;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const int nb = (int)((n3 + kNoAllocThreads - 1) / kNoAllocThreads);
-    k_residual_partials<<<nb, kNoAllocThreads, 0, st>>>(phi, f, c, N, mg5::make_coef<double>(h, alpha),
-                                                        partials);
-    k_norm_finalize<<<1, 1024, 0, st>>>(partials, nb, (double)n3, out);
+    long long nb = (n3 + kNoAllocThreads - 1) / kNoAllocThreads;
+    if (nb > kNoAllocMaxBlocks)
+        nb = kNoAllocMaxBlocks;
+    k_residual_partials<<<(int)nb, kNoAllocThreads, 0, st>>>(phi, f, c, N,
+                                                             mg5::make_coef<double>(h, alpha), partials);
+    k_norm_finalize<<<1, 1024, 0, st>>>(partials, (int)nb, out);
     mg5::count_launch(2);
     return cudaGetLastError() == cudaSuccess ? MG5_OK : MG5_E_CUDA;
 }

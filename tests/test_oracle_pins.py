@@ -647,7 +647,8 @@ def test_parent_force_mask_box_parent_places_children():
 
 
 def test_vcycle_reduction_factor_poisson():
-    """P:L242's observation turned into a bound: for the Poisson limit (alpha = 0) each FAS
+    """Sec. 3.1's point about multigrid (coarse grids remove the long-wavelength error that
+    plain relaxation leaves behind) turned into a bound: for the Poisson limit (alpha = 0) each FAS
     V(2,2) cycle of the oracle reduces the residual by a factor <= 0.2, from the first cycle on
     (the smoothing-plus-coarse-correction rate, not a slow tail)."""
     delta = workload.lognormal_delta(32, 1.0, 9)
