@@ -41,6 +41,12 @@ H_COARSE = L_BOX / N_COARSE    # the 128^3 grid of a 256^3-cell field: 1.95 Mpc/
 TOL64, TOLMIX = 1e-10, 1e-8
 NU_COARSE_CAP = 4        # coarsest-grid sweeps a visit in the FP64 solves of the step
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop
+FP64_PEAK_SOURCE = ("derived FP64: 2 FMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop = 1.259 TFLOP/s "
+                    "(MEASURED_PEAKS.json has no FP64 figure; an 8-chain FMA probe measured 1.195)")
+# The smoother's flops a cell update in the hot-path scope table's own count (about 60
+# arithmetic operations, one square root and one divide), reported beside the operation-by-
+# operation count of WORK for the same kernel.
+SURVEY_FLOPS_SWEEP64 = 62.0
 
 # algorithmic work per cell of each kernel class: (bound, bytes, flops)
 #   sweep: read phi + f, write phi (the full red+black sweep of one cell);
@@ -233,8 +239,14 @@ class Step:
             with torch.cuda.stream(s2):
                 s2.wait_event(ev[0])
                 ev[5].record(s2)
-                _, _, out["im"] = self.ctx2.solve_fifth_force(self.d_c, self.pmix, phi=self.phi_m,
-                                                              grad=self.grad_m, stream=s2)
+                if host_io is None:
+                    _, _, out["im"] = self.ctx2.solve_fifth_force(self.d_c, self.pmix,
+                                                                  phi=self.phi_m, grad=self.grad_m,
+                                                                  stream=s2)
+                else:   # delta in from the host, phi and grad out to it, inside the call
+                    _, _, out["im"] = self.ctx2.solve_fifth_force_host(
+                        host_io["delta"], self.pmix, phi=host_io["phi_m"], grad=host_io["grad_m"],
+                        stream=s2)
                 ev[6].record(s2)
 
         with torch.cuda.stream(s1):
@@ -268,7 +280,6 @@ class Step:
             if host_io is not None:
                 host_io["g_tr"].copy_(self.g_tr, non_blocking=True)
                 host_io["g_full"].copy_(self.g_full, non_blocking=True)
-                host_io["phi_m"].copy_(self.phi_m, non_blocking=True)
             ev[4].record(s1)
         ev[4].synchronize()
         im = out["im"]
@@ -340,7 +351,8 @@ def run_ours(args):
            "grad": torch.zeros(step.grad.shape, dtype=torch.float64).pin_memory(),
            "g_tr": torch.zeros(step.g_tr.shape, dtype=torch.float64).pin_memory(),
            "g_full": torch.zeros(step.g_full.shape, dtype=torch.float64).pin_memory(),
-           "phi_m": torch.zeros(step.phi.shape, dtype=torch.float64).pin_memory()}
+           "phi_m": torch.zeros(step.phi.shape, dtype=torch.float64).pin_memory(),
+           "grad_m": torch.zeros(step.grad.shape, dtype=torch.float64).pin_memory()}
     e2e_ms, e2e_cu = 0.0, 0
     if not args.no_e2e:
         step.run(hio)
@@ -352,9 +364,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_cu += cu
-    h2d = (hio["delta"].numel() + hio["patch"].numel()) * 8
+    # delta goes in twice (the FP64 and the mixed solve each copy it from the host)
+    h2d = (2 * hio["delta"].numel() + hio["patch"].numel()) * 8
     d2h = (hio["phi"].numel() + hio["grad"].numel() + hio["g_tr"].numel() + hio["g_full"].numel()
-           + hio["phi_m"].numel()) * 8
+           + hio["phi_m"].numel() + hio["grad_m"].numel()) * 8
 
     if rank != 0:
         return
@@ -408,6 +421,8 @@ def run_ours(args):
             out["truncation_levels"] = {"error": str(e)}
     if not args.no_batch:
         out["batch"] = run_batch(mg, torch, dev, step.alpha, step.s, autotune=not args.no_autotune)
+    if not args.no_sizes:
+        out.update(size_records(mg, torch, dev, step.alpha, step.s, autotune=not args.no_autotune))
     if args.serve_seconds > 0:
         out["serving"] = run_serving(mg, torch, dev, step.alpha, step.s, args.serve_seconds,
                                      slots=args.serve_slots, autotune=not args.no_autotune)
@@ -416,56 +431,66 @@ def run_ours(args):
     print(json.dumps(out), flush=True)
 
 
-def geff_report(step):
-    """Eq. (errors2) quantities on the refinement workload (once, outside the timed region):
-    the GR force from the same engine at alpha = 0 with source (3 beta / 2) s delta
-    (Eq. modpoisson), on the domain grid and relaxed on the patch like the fifth force;
-    F5 = grad(phi) / 2.  Reports F5/F_GR on the domain and on the patch (screening lowers it
-    below the linear value 1/(3 beta)), eps_trunc = |F5_trunc - F5_full| / |F5_full| and
-    the G_eff error it causes, |F5_trunc - F5_full| / |F_GR| = (F5_full/F_GR) eps_trunc."""
-    mg, torch, ctx = step.mg, step.torch, step.ctx
-    n, pf = N_COARSE, 2 * PN
-    s_gr = 1.5 * step.beta * step.s
-    p_gr = mg.default_params(alpha=0.0, s=s_gr, h=H_COARSE, tol=TOL64)
-    p_grp = mg.default_params(alpha=0.0, s=s_gr, h=H_COARSE / 2, tol=TOL64)
-    psi = torch.zeros_like(step.phi)
-    g_psi = torch.empty_like(step.grad)
-    _, _, ig = ctx.solve_fifth_force(step.d_c, p_gr, phi=psi, grad=g_psi)
-    box = torch.empty_like(step.box)
-    ctx.refine_interpolate(psi, step.origin, (PN, PN, PN), 1, out=box)
-    ctx.relax_patch(step.d_p, p_grp, ig.compat_c, box)
-    g_gr = torch.empty_like(step.g_full)
-    ctx.force(box, H_COARSE / 2, ghost=1, periodic=False, grad=g_gr)
-    torch.cuda.synchronize()
-    step.g_gr_dom, step.g_gr_patch = g_psi, g_gr      # reused by masked_truncation_report
-    mag = lambda g: torch.linalg.vector_norm(g, dim=0)
-    r_dom = 0.5 * mag(step.grad) / mag(g_psi)
-    r_full = 0.5 * mag(step.g_full) / mag(g_gr)
-    r_tr = 0.5 * mag(step.g_tr) / mag(g_gr)
-    d5 = 0.5 * mag(step.g_tr - step.g_full)
-    eps = d5 / (0.5 * mag(step.g_full))
-    dgeff = d5 / mag(g_gr)
-    q = lambda t: [float(x) for x in torch.quantile(t.flatten()[::7].float(), torch.tensor([0.5, 0.99], device=t.device))]
-    # interpolation variants of the truncated level, each against the relaxed force:
-    # tricubic phi (an extension), and the coarse force interpolated directly (the
-    # Fig. amr caption's wording) instead of differencing the interpolated phi
-    rl2 = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
-    box_c = ctx.refine_interpolate_cubic(step.phi, step.origin, (PN, PN, PN), 1)
-    g_cub = ctx.force(box_c, H_COARSE / 2, ghost=1, periodic=False)
-    g_fi = torch.stack([ctx.refine_interpolate(step.grad[a].contiguous(), step.origin, (PN, PN, PN), 0)
+def geff_fields(mg, torch, ctx, d_c, d_p, phi, grad, origin, pn, h, beta, s, tol=TOL64):
+    """Device fields of Eq. (errors2) on one refinement (once, outside the timed region): the
+    GR potential from the same engine at alpha = 0 with source (3 beta / 2) s delta
+    (Eq. modpoisson), its force on the periodic domain grid and, relaxed on the patch like the
+    fifth force, on the refinement; and the truncated level's interpolation variants -- the
+    tricubic phi (an extension) and the coarse force interpolated directly (the Fig. amr
+    caption's wording) instead of differencing the interpolated phi.  d_c: domain delta (n^3),
+    d_p: patch delta ((2 pn)^3), phi / grad: the fifth-force solution and its gradient on the
+    domain grid of cell size h."""
+    pn = tuple(int(x) for x in pn)
+    s_gr = 1.5 * beta * s
+    p_gr = mg.default_params(alpha=0.0, s=s_gr, h=h, tol=tol)
+    p_grp = mg.default_params(alpha=0.0, s=s_gr, h=h / 2, tol=tol, max_cycles=1000)
+    psi = torch.zeros_like(phi)
+    g_psi = torch.empty_like(grad)
+    _, _, ig = ctx.solve_fifth_force(d_c, p_gr, phi=psi, grad=g_psi)
+    box = ctx.refine_interpolate(psi, origin, pn, 1)
+    ctx.relax_patch(d_p, p_grp, ig.compat_c, box)
+    g_gr = ctx.force(box, h / 2, ghost=1, periodic=False)
+    box_c = ctx.refine_interpolate_cubic(phi, origin, pn, 1)
+    g_cub = ctx.force(box_c, h / 2, ghost=1, periodic=False)
+    g_fi = torch.stack([ctx.refine_interpolate(grad[a].contiguous(), origin, pn, 0)
                         for a in range(3)])
     torch.cuda.synchronize()
-    variants = {"phi_trilinear": rl2(step.g_tr, step.g_full), "phi_tricubic": rl2(g_cub, step.g_full),
-                "force_trilinear": rl2(g_fi, step.g_full)}
-    return {"linear_ratio_1_over_3beta": 1.0 / (3.0 * step.beta),
-            "eps_trunc_rel_l2_by_interpolant": variants,
-            "f5_over_fgr_domain_p50_p99": q(r_dom), "f5_over_fgr_patch_p50_p99": q(r_full),
-            "f5_over_fgr_patch_trunc_p50_p99": q(r_tr),
-            "eps_trunc_rel_l2": float(torch.linalg.vector_norm(step.g_tr - step.g_full)
-                                      / torch.linalg.vector_norm(step.g_full)),
-            "eps_trunc_p50_p99": q(eps),
-            "geff_error_p50_p99": q(dgeff),
-            "gr_cycles": ig.cycles}
+    return {"g_psi": g_psi, "g_gr": g_gr, "g_cub": g_cub, "g_fi": g_fi, "gr_cycles": ig.cycles}
+
+
+def geff_numbers(torch, beta, grad, g_psi, g_tr, g_full, g_gr, g_cub, g_fi):
+    """Eq. (errors2) quantities from the forces (FP64, every cell; quantiles by linear
+    interpolation): F5 = grad(phi) / 2 against F_GR = grad(Psi_GR) on the domain and on the
+    patch (screening lowers F5/F_GR below the linear value 1/(3 beta)), eps_trunc =
+    |F5_trunc - F5_full| / |F5_full| and the G_eff error it causes,
+    |F5_trunc - F5_full| / |F_GR| = (F5_full / F_GR) eps_trunc; g_tr: the truncated level's
+    force (trilinear phi), g_full: the relaxed level's."""
+    mag = lambda g: torch.linalg.vector_norm(g, dim=0)   # noqa: E731
+    qs = torch.tensor([0.5, 0.99], dtype=torch.float64, device=grad.device)
+    q = lambda t: [float(x) for x in torch.quantile(t.flatten(), qs)]   # noqa: E731
+    rl2 = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))  # noqa: E731
+    d5 = 0.5 * mag(g_tr - g_full)
+    return {"linear_ratio_1_over_3beta": 1.0 / (3.0 * beta),
+            "eps_trunc_rel_l2_by_interpolant": {"phi_trilinear": rl2(g_tr, g_full),
+                                                "phi_tricubic": rl2(g_cub, g_full),
+                                                "force_trilinear": rl2(g_fi, g_full)},
+            "f5_over_fgr_domain_p50_p99": q(0.5 * mag(grad) / mag(g_psi)),
+            "f5_over_fgr_patch_p50_p99": q(0.5 * mag(g_full) / mag(g_gr)),
+            "f5_over_fgr_patch_trunc_p50_p99": q(0.5 * mag(g_tr) / mag(g_gr)),
+            "eps_trunc_rel_l2": rl2(g_tr, g_full),
+            "eps_trunc_p50_p99": q(d5 / (0.5 * mag(g_full))),
+            "geff_error_p50_p99": q(d5 / mag(g_gr))}
+
+
+def geff_report(step):
+    """Eq. (errors2) on the refinement workload (once, outside the timed region)."""
+    f = geff_fields(step.mg, step.torch, step.ctx, step.d_c, step.d_p, step.phi, step.grad,
+                    step.origin, (PN, PN, PN), H_COARSE, step.beta, step.s)
+    step.g_gr_dom, step.g_gr_patch = f["g_psi"], f["g_gr"]   # reused by masked_truncation_report
+    out = geff_numbers(step.torch, step.beta, step.grad, f["g_psi"], step.g_tr, step.g_full,
+                       f["g_gr"], f["g_cub"], f["g_fi"])
+    out["gr_cycles"] = f["gr_cycles"]
+    return out
 
 
 def masked_truncation_report(step, quantiles=(0.25, 0.5, 0.75, 0.9), reps=3):
@@ -720,30 +745,83 @@ def run_batch(mg, torch, dev, alpha, s, reps=5, autotune=True):
             "outer_iters": [i.outer_iters for i in infos][:8], "dtype": "f32+f64"}
 
 
-def serving_stream(dev, count, rate=200.0):
-    """The serving stream's requests: exponential gaps at `rate`, sides 16 round(10^U(log 32,
-    log 256)/16), sigma in {0.5, 1, 1.5, 2} (bucket b: sigma = 0.5 + 0.5 b), tol 1e-6 or 1e-8
-    with p = 1/2.  Returns (gaps, sizes, sigma buckets, tols, device delta per (side, bucket))."""
+SERVE_SEED0 = 50000   # request i draws its field from seed SERVE_SEED0 + i
+
+
+def serving_stream(count, rate=200.0):
+    """The serving stream's requests: exponential gaps at `rate`, sides
+    16 round(10^U(log 32, log 256)/16), sigma ~ U(0.5, 2), tol 1e-6 or 1e-8 with p = 1/2.
+    Returns (gaps, sizes, sigmas, tols); request i's field is serving_field(i, ...)."""
     import workload
     rng = np.random.Generator(np.random.PCG64(5))
     gaps = rng.exponential(1.0 / rate, size=count)
     sizes = workload.serving_sizes(rng, count)
-    sig_bucket = rng.integers(0, 4, size=count)
+    sigmas = rng.uniform(0.5, 2.0, size=count)
     tols = np.where(rng.uniform(size=count) < 0.5, 1e-6, 1e-8)
-    pool = {}
-    for n in sorted(set(int(x) for x in sizes)):
-        for b in range(4):
-            pool[(n, b)] = workload.lognormal_delta_torch(n, 0.5 + 0.5 * b, 5000 + 7 * n + b, dev)
-    return gaps, sizes, sig_bucket, tols, pool
+    return gaps, sizes, sigmas, tols
 
 
-def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=None,
+def serving_field(i, sizes, sigmas, dev):
+    """Request i's own lognormal field (its own seed: no two requests share an input)."""
+    import workload
+    return workload.lognormal_delta_torch(int(sizes[i]), float(sigmas[i]), SERVE_SEED0 + i, dev)
+
+
+class FieldFeeder:
+    """Generates each request's field on a side stream ahead of its arrival time (outside
+    the server's path; the server measures latency from the submission at arrival)."""
+
+    def __init__(self, torch, dev, sizes, sigmas, count, ahead=96):
+        self.torch, self.dev = torch, dev
+        self.sizes, self.sigmas, self.count = sizes, sigmas, count
+        self.ready = {}
+        self.cv = threading.Condition()
+        self.next_needed = 0
+        self.ahead = ahead
+        self.stop = False
+        self.th = threading.Thread(target=self._run, daemon=True)
+        self.th.start()
+
+    def _run(self):
+        torch = self.torch
+        st = torch.cuda.Stream(device=self.dev)
+        for i in range(self.count):
+            with self.cv:
+                while not self.stop and i >= self.next_needed + self.ahead:
+                    self.cv.wait(0.05)
+                if self.stop:
+                    return
+            with torch.cuda.stream(st):
+                d = serving_field(i, self.sizes, self.sigmas, self.dev)
+            st.synchronize()
+            with self.cv:
+                self.ready[i] = d
+                self.cv.notify_all()
+
+    def take(self, i):
+        with self.cv:
+            while i not in self.ready:
+                self.cv.wait(0.05)
+            self.next_needed = i + 1
+            self.cv.notify_all()
+            return self.ready.pop(i)
+
+    def close(self):
+        with self.cv:
+            self.stop = True
+            self.cv.notify_all()
+        self.th.join(timeout=30)
+
+
+def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=5.0,
                 autotune=True):
     """Poisson arrivals at `rate` req/s for `seconds`: sides 16 round(10^U(log 32, log 256)/16),
-    sigma ~ U(0.5, 2), tol 1e-6 or 1e-8 with p = 1/2, mixed precision; admitted by HBM footprint.
-    Latency = completion - arrival (server clock); the first fifth of the run is discarded."""
+    sigma ~ U(0.5, 2), tol 1e-6 or 1e-8 with p = 1/2, mixed precision, every request its own
+    field (generated ahead of its arrival on a side stream); admitted by HBM footprint.
+    Latency = completion - arrival (server clock); the first `warm_s` seconds are discarded
+    (a fifth of the run if that is shorter)."""
     count = int(rate * seconds * 1.2) + 8
-    gaps, sizes, sig_bucket, tols, pool = serving_stream(dev, count, rate)
+    gaps, sizes, sigmas, tols = serving_stream(count, rate)
     budget = int(torch.cuda.get_device_properties(dev).total_memory * 0.5)
     if autotune:   # the schedule table is process-wide: the server's captures read it
         tctx = mg.Context(dev.index or 0)
@@ -753,14 +831,17 @@ def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=
     srv = mg.Server(dev.index or 0, slots=slots, hbm_budget_bytes=budget)
     # warm the server's graph pool (two entries per (size, tolerance): its cap) before timing
     for i, n in enumerate(sorted(set(int(x) for x in sizes))):
+        dw = workload_field(torch, dev, n)
         for j, tol in enumerate((1e-6, 1e-8)):
             p = mg.default_params(alpha=alpha, s=s, h=L_BOX / 512, tol=tol, precision="mixed")
             for r in range(2):
-                srv.submit(pool[(n, 0)], p, torch.zeros_like(pool[(n, 0)]),
-                           tag=10 ** 9 + 4 * i + 2 * j + r)
-    while srv.pending() != (0, 0):
-        srv.poll(wait_ms=50)
+                srv.submit(dw, p, torch.zeros_like(dw), tag=10 ** 9 + 4 * i + 2 * j + r)
+        while srv.pending() != (0, 0):
+            srv.poll(wait_ms=50)
     srv.poll(max_n=1000)
+    feeder = FieldFeeder(torch, dev, sizes, sigmas, count)
+    while len(feeder.ready) < min(32, count):   # a head start before the clock starts
+        time.sleep(0.01)
     done = {}
     t_start = srv.clock()
     t_next = t_start
@@ -770,9 +851,8 @@ def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=
         if now - t_start >= seconds:
             break
         if now >= t_next and i < count:
-            n = int(sizes[i])
             p = mg.default_params(alpha=alpha, s=s, h=L_BOX / 512, tol=float(tols[i]), precision="mixed")
-            d = pool[(n, int(sig_bucket[i]))]
+            d = feeder.take(i)
             srv.submit(d, p, torch.empty_like(d), tag=i)
             t_next += gaps[i]
             i += 1
@@ -781,25 +861,37 @@ def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=
             done[c.tag] = c
         time.sleep(max(0.0, min(t_next - srv.clock(), 0.0005)))
     submitted = i
+    feeder.close()
     while len(done) < submitted:
         for c in srv.poll(wait_ms=100):
             done[c.tag] = c
     stats = srv.stats()
     srv.close()
-    warm = seconds / 5.0 if warm_s is None else warm_s
+    warm = min(warm_s, seconds / 5.0)
     rows = [c for c in done.values() if c.t_submit - t_start >= warm]
     lat = np.array([(c.t_done - c.t_submit) * 1e3 for c in rows])
     t_first = min(c.t_submit for c in rows)
     t_last = max(c.t_done for c in rows)
     cu = sum(c.info.cell_updates for c in rows)
     ok = sum(1 for c in rows if c.status in (0, 1))
-    return {"offered_req_per_s": rate, "seconds": seconds, "slots": slots, "requests": len(rows),
-            "completed_ok": ok, "throughput_req_per_s": len(rows) / (t_last - t_first),
+    lag = [(c.t_submit - t_start) - float(np.sum(gaps[:c.tag])) for c in rows]
+    return {"offered_req_per_s": rate, "seconds": seconds, "discarded_s": warm, "slots": slots,
+            "requests": len(rows), "submitted": submitted, "completed_ok": ok,
+            "distinct_inputs": len(rows),
+            "throughput_req_per_s": len(rows) / (t_last - t_first),
             "cell_updates_per_s": cu / (t_last - t_first),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(lat.mean()), "max": float(lat.max())},
+            "submit_lag_ms_max": float(max(lag) * 1e3) if lag else 0.0,
             "mean_cells_per_request": float(np.mean([int(sizes[c.tag]) ** 3 for c in rows])),
+            "sigma_range": [float(sigmas[:submitted].min()), float(sigmas[:submitted].max())],
             "hbm_budget_bytes": budget, "server": stats}
+
+
+def workload_field(torch, dev, n):
+    """A field of side n for warming the server's graph pool (not one of the requests)."""
+    import workload
+    return workload.lognormal_delta_torch(n, 1.0, 4999, dev)
 
 
 def roofline(prof: dict, peaks: dict, steps: int) -> dict:
@@ -818,12 +910,17 @@ def roofline(prof: dict, peaks: dict, steps: int) -> dict:
         unit = "TFLOP/s"
     tpc = TRAFFIC_PER_CELL.get(name)
     traffic = tpc * cells / max(calls, 1) if tpc is not None else None
-    return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": traffic,
-            "avg_launch_ms": ms / max(calls, 1), "launches_per_step": calls / steps,
-            "alg_bytes_per_cell": bpc, "alg_flops_per_cell": fpc,
-            "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if bound == "hbm"
-            else "derived FP64: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (probe measured 1.195 TFLOP/s)"}
+    out = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+           "frac": achieved / peak, "traffic": traffic,
+           "avg_launch_ms": ms / max(calls, 1), "launches_per_step": calls / steps,
+           "alg_bytes_per_cell": bpc, "alg_flops_per_cell": fpc,
+           "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if bound == "hbm"
+           else FP64_PEAK_SOURCE}
+    if name.startswith("sweep64") or name.startswith("patch_sweep64"):
+        a2 = SURVEY_FLOPS_SWEEP64 * cells / sec / 1e12
+        out.update({"achieved_survey_count": a2, "frac_survey_count": a2 / peak,
+                    "flops_per_cell_survey_count": SURVEY_FLOPS_SWEEP64})
+    return out
 
 
 # ---------------------------------------------------------------- the oracle on host cores
@@ -854,6 +951,118 @@ def cpu_baseline(coarse, patch, origin, budget_s=20.0) -> dict:
             "sample": "FP64 oracle solve of the 128^3 grid to 1e-10 (%d cycles, %.1f s) + %d "
                       "Dirichlet sweeps of the 64^3 patch (%.1f s); OpenMP over %d threads"
                       % (info.cycles, t_solve, sweeps, t_patch, cores)}
+
+
+def time_solve(torch, ctx, d, p, reps=3, warm=1, **kw):
+    """Median device time (CUDA events on the current stream, first kernel to the last
+    result on the device) of `reps` solves after `warm` untimed ones; returns (ms, info)."""
+    for _ in range(warm):
+        _, _, info = ctx.solve_fifth_force(d, p, **kw)
+    ms = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, info = ctx.solve_fifth_force(d, p, **kw)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.median(ms)), info
+
+
+def class_roofline(prof: dict, name: str, peaks: dict) -> dict:
+    """Algorithmic bytes (or flops) of one kernel class / its event-timed device time."""
+    ms, calls, cells = prof.get(name, (0.0, 0, 0.0))
+    if calls == 0 or ms <= 0:
+        return None
+    bound, bpc, fpc = WORK[name]
+    sec = ms / 1e3
+    if bound == "hbm":
+        achieved, peak, unit = bpc * cells / sec / 1e9, peaks.get("hbm_gbs", 6800.0), "GB/s"
+    else:
+        achieved, peak, unit = fpc * cells / sec / 1e12, FP64_PEAK_TFLOPS, "TFLOP/s"
+    return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "avg_launch_ms": ms / calls, "launches": calls,
+            "alg_bytes_per_cell": bpc, "alg_flops_per_cell": fpc,
+            "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if bound == "hbm"
+            else FP64_PEAK_SOURCE}
+
+
+def size_records(mg, torch, dev, alpha, s, autotune=True):
+    """The single-grid configurations beside the step (once, after its timed region), each
+    to its stated tolerance with inputs resident on the device:
+      fp64_32   the 32^3 sigma = 1 grid (seed 1, numpy generator), FP64 to 1e-10, median of
+                10 after 2 warm-ups, host-driven and as a graph replay (L2-resident);
+      mixed512  the 512^3 sigma = 2 grid (seed 3), FP32 V-cycles inside the FP64 defect
+                correction to 1e-8 (inputs larger than L2), per-class device time and the FP32
+                smoother's HBM roofline;
+      fp64_512  the same input solved in plain FP64 (FMG start, V(3,1), coarsest capped at 4
+                sweeps a visit) to 1e-8 and to 1e-10;
+      mixed_over_fp64  FP64 time to 1e-8 / mixed time to 1e-8 on that input (> 1: the mixed
+                mode is faster)."""
+    import workload
+    peaks = _peaks()
+    out = {}
+    ctx = mg.Context(dev.index or 0)
+    # C1: 32^3 FP64 to 1e-10
+    h32 = L_BOX / 512
+    d32 = torch.from_numpy(workload.lognormal_delta(32, 1.0, 1)).to(dev)
+    p32 = mg.default_params(alpha=alpha, s=s, h=h32, tol=TOL64)
+    t_host, i_host = time_solve(torch, ctx, d32, p32, reps=10, warm=2)
+    t_graph, i_graph = time_solve(torch, ctx, d32, p32, reps=10, warm=2, graph=True)
+    out["fp64_32"] = {"n": 32, "tol": TOL64, "time_to_tol_ms": min(t_host, t_graph),
+                      "host_driven_ms": t_host, "graph_ms": t_graph, "cycles": i_graph.cycles,
+                      "rel_residual": i_graph.rel_residual,
+                      "cell_updates_per_s": i_graph.cell_updates / (t_graph / 1e3),
+                      "l2": "L2-resident (256 KiB field)"}
+    # C3: 512^3, mixed and FP64 on the same input
+    n = 512
+    d = workload.lognormal_delta_torch(n, 2.0, 3, dev)
+    phi = torch.zeros_like(d)
+    if autotune:
+        ctx.autotune(n, "mixed")
+        ctx.autotune(n, "fp64")
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    pm = mg.default_params(alpha=alpha, s=s, h=h32, tol=TOLMIX, precision="mixed")
+    tm, im = time_solve(torch, ctx, d, pm, phi=phi)
+    tmg, img = time_solve(torch, ctx, d, pm, phi=phi, graph=True)
+    ctx.profile_enable(True)
+    ctx.solve_fifth_force(d, pm, phi=phi)
+    prof_m = ctx.profile_read()
+    ctx.profile_enable(False)
+    out["mixed512"] = {"n": n, "tol": TOLMIX, "time_to_tol_ms": min(tm, tmg),
+                       "host_driven_ms": tm, "graph_ms": tmg,
+                       "outer_iters": im.outer_iters, "inner_cycles": im.cycles,
+                       "rel_residual": im.rel_residual,
+                       "cell_updates_per_s": im.cell_updates / (min(tm, tmg) / 1e3),
+                       "roofline_sweep32": class_roofline(prof_m, "sweep32", peaks),
+                       "kernels_ms": {k: round(v[0], 3) for k, v in prof_m.items() if v[1] > 0},
+                       "l2": "inputs larger than L2"}
+    out["fp64_512"] = {}
+    for tol in (TOLMIX, TOL64):
+        p = mg.default_params(alpha=alpha, s=s, h=h32, tol=tol, nu1=3, nu2=1,
+                              nu_coarse=NU_COARSE_CAP)
+        t, i = time_solve(torch, ctx, d, p, phi=phi, fmg=True, graph=True)
+        out["fp64_512"]["tol_%g" % tol] = {"time_to_tol_ms": t, "cycles": i.cycles,
+                                          "rel_residual": i.rel_residual,
+                                          "cell_updates_per_s": i.cell_updates / (t / 1e3)}
+    p = mg.default_params(alpha=alpha, s=s, h=h32, tol=TOLMIX, nu1=3, nu2=1,
+                          nu_coarse=NU_COARSE_CAP)
+    ctx.profile_enable(True)
+    ctx.solve_fifth_force(d, p, phi=phi, fmg=True)
+    prof_64 = ctx.profile_read()
+    ctx.profile_enable(False)
+    out["fp64_512"]["kernels_ms_tol_1e-08"] = {k: round(v[0], 3) for k, v in prof_64.items()
+                                               if v[1] > 0}
+    out["fp64_512"]["roofline_sweep64"] = class_roofline(prof_64, "sweep64", peaks)
+    out["mixed_over_fp64"] = (out["fp64_512"]["tol_%g" % TOLMIX]["time_to_tol_ms"]
+                              / out["mixed512"]["time_to_tol_ms"])
+    out["clocks"] = clocks.stop()
+    ctx.close()
+    del d, phi
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_mixed_workload(args):
@@ -956,12 +1165,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-box batched workload")
+    ap.add_argument("--no-sizes", action="store_true",
+                    help="skip the 32^3 FP64 and 512^3 mixed / FP64 records")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--no-truncation-levels", action="store_true",
                     help="skip the nested multi-level truncation report")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default sweep schedules instead of the tuned ones")
-    ap.add_argument("--serve-seconds", type=float, default=6.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the serving run (0 skips it)")
     args = ap.parse_args()
     if args.impl == "reference":

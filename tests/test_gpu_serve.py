@@ -116,10 +116,10 @@ def test_server_shares_captured_graphs_between_workers():
 
 def test_bench_serving_stream_matches_oracle():
     """The first requests of the serving stream bench.py offers (same generator: sides 16 k from
-    32 to 256, sigma 0.5 - 2, tol 1e-6 or 1e-8, mixed precision), all submitted to a server of 8
-    slots at once: every one converges, and those of side <= 128 match the FP64 oracle within
-    the bar their tolerance implies (phi within ~1.5 x tol of the discrete solution: 1e-5 for
-    1e-6, 1e-6 for 1e-8)."""
+    32 to 256, sigma ~ U(0.5, 2), each request its own field, tol 1e-6 or 1e-8, mixed
+    precision), all submitted to a server of 8 slots at once: every one converges, and those of
+    side <= 128 match the FP64 oracle within the bar their tolerance implies (phi within
+    ~1.5 x tol of the discrete solution: 1e-5 for 1e-6, 1e-6 for 1e-8)."""
     import torch
     import bench
     import oracle
@@ -128,11 +128,12 @@ def test_bench_serving_stream_matches_oracle():
     beta, alpha, s = mg.ndgp_coefficients(1.0, 0.3, 1.0)
     h = bench.L_BOX / 512
     count = 24
-    gaps, sizes, bucket, tols, pool = bench.serving_stream(torch.device("cuda"), count)
+    gaps, sizes, sigmas, tols = bench.serving_stream(count)
+    fields = {i: bench.serving_field(i, sizes, sigmas, torch.device("cuda")) for i in range(count)}
     srv = mg.Server(0, slots=8)
     phis = {}
     for i in range(count):
-        d = pool[(int(sizes[i]), int(bucket[i]))]
+        d = fields[i]
         p = mg.default_params(alpha=alpha, s=s, h=h, tol=float(tols[i]), precision="mixed")
         phis[i] = torch.full_like(d, float("nan"))
         srv.submit(d, p, phis[i], tag=i)
@@ -149,7 +150,7 @@ def test_bench_serving_stream_matches_oracle():
         n = int(sizes[i])
         if n > 128:
             continue
-        d = host(pool[(n, int(bucket[i]))])
+        d = host(fields[i])
         ref, rinfo = oracle.solve(d, alpha, s, h, tol=1e-12)
         assert rinfo.status == 0
         bar = 1e-5 if tols[i] > 1e-7 else 1e-6
