@@ -117,7 +117,8 @@ typedef struct {
     long long cell_updates;  /* cells relaxed: one per cell per full sweep, every grid */
     double ms_total;         /* wall time of the call on the stream, ms */
     long long coarse_sweeps; /* sweeps of the coarsest-grid solves, summed over its visits */
-    double history[64];      /* relative residual per finest-level check */
+    double history[64];      /* relative residual per finest-level check, in order (an
+                                MG5_WARM solve's check of the initial guess comes first) */
 } mg5_info;
 
 /* ------------------------------------------------------------ utilities */

@@ -11,7 +11,6 @@
 
 namespace mg5 {
 
-constexpr int kReduceGrid = kMaxPartials;  // reduction kernels use at most this many blocks
 
 // --------------------------------------------------------------------------
 // snapshot red-black sweep: two passes.
@@ -145,7 +144,7 @@ __global__ void k_residual(const T *__restrict__ phi, const T *__restrict__ f,
             r_out[t] = res;
         acc.add(res);
     }
-    const Moments m = block_moments(acc.get());
+    const Moments m = block_moments(acc);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = m;
 }
@@ -155,9 +154,10 @@ cudaError_t launch_residual(const T *phi, const T *f, const double *cptr, int n,
                             double2 *partials, int *nblocks, cudaStream_t st)
 {
     const long long work = (long long)n * n * n;
+    const int cap = sizeof(T) == 8 ? kReduceBlocksFp64 : kReduceBlocks;
     int g = blocks_for(work);
-    if (g > kMomentBlocks)
-        g = kMomentBlocks;
+    if (g > cap)
+        g = cap;
     k_residual<T><<<g, kBlock, 0, st>>>(phi, f, cptr, n, cf, r, reinterpret_cast<Moments *>(partials));
     *nblocks = g;
     count_launch(1);
@@ -200,7 +200,7 @@ __global__ void k_resid_restrict(const T *__restrict__ v, const T *__restrict__ 
         v0c[t] = mv;
         rc[t] = sr * (T)0.125;
     }
-    const Moments m = block_moments(acc.get());
+    const Moments m = block_moments(acc);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = m;
 }
@@ -211,9 +211,10 @@ cudaError_t launch_resid_restrict(const T *v, const T *f, const double *cptr, in
                                   cudaStream_t st, const T *B)
 {
     const long long work = (long long)(n / 2) * (n / 2) * (n / 2);
+    const int cap = sizeof(T) == 8 ? kReduceBlocksFp64 : kReduceBlocks;
     int g = blocks_for(work);
-    if (g > kMomentBlocks)
-        g = kMomentBlocks;
+    if (g > cap)
+        g = cap;
     Moments *mp = reinterpret_cast<Moments *>(partials);
     if (B)
         k_resid_restrict<T, true><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, mp, B);
@@ -566,22 +567,29 @@ __global__ void k_finalize(const double2 *__restrict__ partials, int nb, double 
                            LevelScal *ls, int mode)
 {
     if (mode == FIN_RESID || mode == FIN_STATS) {
-        // per-block Moments, combined in a fixed order (deterministic)
+        // per-block shifted sums moved onto block 0's shift, summed in a fixed order
         const Moments *mp = reinterpret_cast<const Moments *>(partials);
-        Moments v{0.0, 0.0, 0.0, 0.0};
-        for (int b = threadIdx.x; b < nb; b += blockDim.x)
-            v = mom_combine(v, mp[b]);
-        v = block_moments(v);
+        const double k0 = mp[0].k;
+        Moments v{0.0, k0, 0.0, 0.0};
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const Moments u = mom_shift(mp[b], k0);
+            v.n += u.n;
+            v.s += u.s;
+            v.q += u.q;
+        }
+        v = block_sum_shared_shift(v);
         if (threadIdx.x != 0)
             return;
-        const double m = v.mean;
+        double m = 0.0, m2 = 0.0;
+        if (v.n > 0.0)
+            mom_mean_m2(v, &m, &m2);
         ls->m = m;
         if (mode == FIN_RESID)
             ls->c -= m;
-        ls->rnorm = sqrt(v.m2);
+        ls->rnorm = sqrt(m2);
         ls->rel = ls->fnorm > 0.0 ? ls->rnorm / ls->fnorm : ls->rnorm;
-        if (!isfinite(v.mean) || !isfinite(v.m2))
-            ls->rel = v.mean + v.m2;  // propagates NaN / Inf to the host check
+        if (!isfinite(m) || !isfinite(m2))
+            ls->rel = m + m2;  // propagates NaN / Inf to the host check
         return;
     }
     double2 acc = make_double2(0.0, 0.0);
@@ -608,7 +616,7 @@ __global__ void k_finalize(const double2 *__restrict__ partials, int nb, double 
 cudaError_t launch_finalize(const double2 *partials, int nb, double ncells, LevelScal *ls, int mode,
                             cudaStream_t st)
 {
-    k_finalize<<<1, 1024, 0, st>>>(partials, nb, ncells, ls, mode);
+    k_finalize<<<1, 256, 0, st>>>(partials, nb, ncells, ls, mode);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -635,8 +643,8 @@ cudaError_t launch_scale(const double *delta, double s, double *f, long long n3,
                          int *nblocks, cudaStream_t st, double add, const double *add_dev)
 {
     int g = blocks_for(n3);
-    if (g > kReduceGrid)
-        g = kReduceGrid;
+    if (g > kReduceBlocks)
+        g = kReduceBlocks;
     k_scale<<<g, kBlock, 0, st>>>(delta, s, f, n3, partials, add, add_dev);
     *nblocks = g;
     count_launch(1);
@@ -658,8 +666,8 @@ cudaError_t launch_sum(const double *phi, long long n3, double2 *partials, int *
                        cudaStream_t st)
 {
     int g = blocks_for(n3);
-    if (g > kReduceGrid)
-        g = kReduceGrid;
+    if (g > kReduceBlocks)
+        g = kReduceBlocks;
     k_sum<<<g, kBlock, 0, st>>>(phi, n3, partials);
     *nblocks = g;
     count_launch(1);
@@ -1020,8 +1028,8 @@ cudaError_t launch_patch_residual(const double *phi, const double *fint, double 
 {
     const long long work = (long long)pf[0] * pf[1] * pf[2];
     int g = blocks_for(work);
-    if (g > kReduceGrid)
-        g = kReduceGrid;
+    if (g > kReduceBlocksFp64)
+        g = kReduceBlocksFp64;
     if (mask)
         k_patch_residual<true><<<g, kBlock, 0, st>>>(phi, fint, rhs_add, pf[0], pf[1], pf[2], cf,
                                                      partials, mask);

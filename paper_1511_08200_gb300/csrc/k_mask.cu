@@ -71,8 +71,8 @@ cudaError_t launch_scale_masked(const double *delta, double s, double *f, long l
                                 cudaStream_t st, double add)
 {
     int g = blocks_for(n);
-    if (g > kMaxPartials)
-        g = kMaxPartials;
+    if (g > kReduceBlocks)
+        g = kReduceBlocks;
     k_scale_masked<<<g, kBlock, 0, st>>>(delta, s, f, n, mask, partials, add);
     *nblocks = g;
     count_launch(1);

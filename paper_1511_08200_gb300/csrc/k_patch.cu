@@ -398,8 +398,8 @@ cudaError_t launch_pbox_resid_restrict(const double *v, const double *f, const i
 {
     const long long work = (long long)(p[0] / 2) * (p[1] / 2) * (p[2] / 2);
     int g = blocks_for(work);
-    if (g > kMaxPartials)
-        g = kMaxPartials;
+    if (g > kReduceBlocksFp64)
+        g = kReduceBlocksFp64;
     if (mask)
         k_pbox_resid_restrict<true><<<g, kBlock, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc, v0c, fc,
                                                           partials, mask);

@@ -53,7 +53,7 @@ __global__ void k_spec_residual(const T *__restrict__ v, const T *__restrict__ f
         out[t].y = (T)0;
         acc.add(res);
     }
-    const Moments m = block_moments(acc.get());
+    const Moments m = block_moments(acc);
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = m;
         if (blockIdx.x == 0 && sweeps)

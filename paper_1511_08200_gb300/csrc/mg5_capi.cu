@@ -745,7 +745,7 @@ static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p
         RET(R.fmg());
     int status = MG5_E_NOT_CONVERGED;
     double best = INFINITY;
-    int cyc = 0;
+    int cyc = 0, nh = 0;    // nh: residual checks recorded (a warm start's check comes first)
     bool pre_check = warm;  // a warm start is tested (and c set) before any smoothing
     for (;; ++cyc) {
         if (pre_check) {
@@ -761,10 +761,11 @@ static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p
         CK(cudaMemcpyAsync(ctx->h_rel, &ctx->ls[0].rel, sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(ctx_wait(ctx, st));
         const double rel = *ctx->h_rel;
-        if (info && cyc < 64) {
-            info->history[cyc] = rel;
-            info->n_history = cyc + 1;
+        if (info && nh < 64) {
+            info->history[nh] = rel;
+            info->n_history = nh + 1;
         }
+        ++nh;
         if (info)
             info->rel_residual = rel;
         if (!std::isfinite(rel)) {

@@ -457,34 +457,41 @@ __device__ __forceinline__ T opr(const St<T> &s, const St<T> &B, const CoefT<T> 
 }
 
 // ---- residual statistics -----------------------------------------------------
-// Count, mean and M2 = sum (r - mean)^2 of a set of residual values.  The stopping
-// test needs ||r - mean r||; forming it as sum r^2 - N mean^2 cancels when |mean| is
-// far above the spread (a stale compatibility constant, a warm start, a source with a
-// non-zero mean), so sets are combined by the pairwise update of Chan, Golub and
-// LeVeque (1979) instead:  n = na + nb, d = mean_b - mean_a,
-// mean = mean_a + d nb / n, M2 = M2_a + M2_b + d^2 na nb / n.
+// The stopping test needs ||r - mean r||; forming it as sum r^2 - N mean^2 cancels when
+// |mean| is far above the spread of r (a stale compatibility constant, a warm start, a
+// source with a non-zero mean).  A set of values is therefore kept as shifted sums: the
+// count n, a shift K that is one of the values, S = sum (x - K) and Q = sum (x - K)^2;
+// then mean = K + S / n and M2 = sum (x - mean)^2 = Q - S^2 / n, and since K lies
+// within the data, S / n is of the order of the spread and the subtraction keeps its
+// digits.  Two sets are combined after moving one onto the other's shift K':
+//   S' = S + n (K - K'),  Q' = Q + (K - K') (2 S + n (K - K'))
+// (plain multiply-adds: no division on the reduction's critical path).
 // Two double2 slots of a partial-sum buffer hold one Moments.
 struct __align__(16) Moments {
-    double n, mean, m2, pad;
+    double n, k, s, q;
 };
 
-__device__ __forceinline__ Moments mom_combine(const Moments &a, const Moments &b)
+__device__ __forceinline__ Moments mom_shift(const Moments &a, double k2)
 {
-    if (b.n == 0.0)
-        return a;
-    if (a.n == 0.0)
-        return b;
-    const double n = a.n + b.n, w = b.n / n, d = b.mean - a.mean;
+    const double dk = a.k - k2;
     Moments r;
-    r.n = n;
-    r.mean = fma(d, w, a.mean);
-    r.m2 = a.m2 + b.m2 + d * d * (a.n * w);
-    r.pad = 0.0;
+    r.n = a.n;
+    r.k = k2;
+    r.s = fma(a.n, dk, a.s);
+    r.q = fma(dk, fma(a.n, dk, 2.0 * a.s), a.q);
     return r;
 }
 
-// One thread's values, taken relative to its first value (the shifted-data form:
-// the squares carry the spread, not the mean), in the kernel's own precision T.
+// mean and M2 of a set (n > 0)
+__device__ __forceinline__ void mom_mean_m2(const Moments &a, double *mean, double *m2)
+{
+    const double md = a.s / a.n;
+    *mean = a.k + md;
+    const double q = fma(-a.s, md, a.q);
+    *m2 = q > 0.0 ? q : (q == q ? 0.0 : q);   // keeps a NaN
+}
+
+// One thread's values, shifted by its first value, in the kernel's own precision T.
 template <typename T>
 struct MomAcc {
     int n = 0;
@@ -498,52 +505,83 @@ struct MomAcc {
         q = fma(d, d, q);
         ++n;
     }
-    __device__ __forceinline__ Moments get() const
-    {
-        Moments m{0.0, 0.0, 0.0, 0.0};
-        if (n > 0) {
-            m.n = (double)n;
-            const double sd = (double)s, md = sd / m.n;
-            m.mean = (double)k + md;
-            const double m2 = fma(-sd, md, (double)q);
-            m.m2 = m2 > 0.0 ? m2 : (m2 == m2 ? 0.0 : m2);   // keeps a NaN
-        }
-        return m;
-    }
 };
 
-__device__ __forceinline__ Moments mom_shfl_down(const Moments &v, int o)
+// The same shifted sums in precision T, for the warp-level part of a block reduction
+// (FP32 kernels keep it in FP32: on this part an FP64 instruction costs the issue
+// slots of 64 FP32 ones).  n stays exact in FP32 up to 2^24 values a warp.
+template <typename T>
+struct MomT {
+    T n, k, s, q;
+};
+
+template <typename T>
+__device__ __forceinline__ MomT<T> momt_shift(const MomT<T> &a, T k2)
 {
-    Moments r;
-    r.n = __shfl_down_sync(0xffffffffu, v.n, o);
-    r.mean = __shfl_down_sync(0xffffffffu, v.mean, o);
-    r.m2 = __shfl_down_sync(0xffffffffu, v.m2, o);
-    r.pad = 0.0;
+    const T dk = a.k - k2;
+    return MomT<T>{a.n, k2, fma(a.n, dk, a.s), fma(dk, fma(a.n, dk, a.s + a.s), a.q)};
+}
+
+// Deterministic combination over the block, on the shift of thread 0 (which holds the
+// block's first value whenever the block has any): each warp moves its lanes onto its
+// lane 0's shift and sums them in T; warp 0 moves the warps onto warp 0's shift and
+// sums them in FP64.  The result is valid in thread 0.  Every thread must call it.
+template <typename T>
+__device__ __forceinline__ Moments block_moments(const MomAcc<T> &acc)
+{
+    __shared__ Moments smem_mom[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    MomT<T> v{(T)acc.n, acc.k, acc.s, acc.q};
+    v = momt_shift(v, __shfl_sync(0xffffffffu, v.k, 0));
+    for (int o = 16; o > 0; o >>= 1) {
+        v.n += __shfl_down_sync(0xffffffffu, v.n, o);
+        v.s += __shfl_down_sync(0xffffffffu, v.s, o);
+        v.q += __shfl_down_sync(0xffffffffu, v.q, o);
+    }
+    __syncthreads();
+    if (lane == 0)
+        smem_mom[w] = Moments{(double)v.n, (double)v.k, (double)v.s, (double)v.q};
+    __syncthreads();
+    Moments r{0.0, 0.0, 0.0, 0.0};
+    if (w == 0) {
+        const double kb = smem_mom[0].k;
+        r = lane < nw ? mom_shift(smem_mom[lane], kb) : Moments{0.0, kb, 0.0, 0.0};
+        for (int o = 16; o > 0; o >>= 1) {
+            if (o >= nw)   // lanes >= nw hold zeros (uniform test)
+                continue;
+            r.n += __shfl_down_sync(0xffffffffu, r.n, o);
+            r.s += __shfl_down_sync(0xffffffffu, r.s, o);
+            r.q += __shfl_down_sync(0xffffffffu, r.q, o);
+        }
+    }
     return r;
 }
 
-// Deterministic combination over the block; the result is valid in thread 0.
-// Every thread of the block must call it.
-__device__ __forceinline__ Moments block_moments(Moments v)
+// Sets that already share one shift k (the finalize): plain sums over the block in
+// FP64; the result is valid in thread 0.  Every thread must call it.
+__device__ __forceinline__ Moments block_sum_shared_shift(Moments v)
 {
-    __shared__ Moments smem_mom[32];
-    for (int o = 16; o > 0; o >>= 1) {
-        const Moments u = mom_shfl_down(v, o);
-        if ((threadIdx.x & 31) + o < 32)
-            v = mom_combine(v, u);
-    }
+    __shared__ Moments smem_mss[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        v.n += __shfl_down_sync(0xffffffffu, v.n, o);
+        v.s += __shfl_down_sync(0xffffffffu, v.s, o);
+        v.q += __shfl_down_sync(0xffffffffu, v.q, o);
+    }
     __syncthreads();
     if (lane == 0)
-        smem_mom[w] = v;
+        smem_mss[w] = v;
     __syncthreads();
     if (w == 0) {
-        v = lane < nw ? smem_mom[lane] : Moments{0.0, 0.0, 0.0, 0.0};
+        v = lane < nw ? smem_mss[lane] : Moments{0.0, v.k, 0.0, 0.0};
         for (int o = 16; o > 0; o >>= 1) {
-            const Moments u = mom_shfl_down(v, o);
-            if (lane + o < 32)
-                v = mom_combine(v, u);
+            if (o >= nw)
+                continue;
+            v.n += __shfl_down_sync(0xffffffffu, v.n, o);
+            v.s += __shfl_down_sync(0xffffffffu, v.s, o);
+            v.q += __shfl_down_sync(0xffffffffu, v.q, o);
         }
     }
     return v;

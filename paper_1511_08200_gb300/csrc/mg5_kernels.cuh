@@ -35,6 +35,13 @@ constexpr int kInnerBase = 20;   // first slot of the mixed solve's FP32 grids
 constexpr int kMaxPartials = 8192;  // partial-sum slots (double2) per reduction
 // blocks of a residual-statistics reduction: each writes one Moments (two slots)
 constexpr int kMomentBlocks = kMaxPartials / 2;
+// Grid caps of the reduction kernels (grid-stride loops).  The one-block finalize spends
+// FP64 instructions on every partial, and FP64 runs at 1/64 of the FP32 rate here, so
+// the partials are kept few: FP64-bound producers use 4 blocks of 256 per SM (152 SMs),
+// the others 8 (one full wave).
+constexpr int kReduceBlocksFp64 = 4 * 152;
+constexpr int kReduceBlocks = 8 * 152;
+static_assert(kReduceBlocks <= kMomentBlocks, "partials buffer too small");
 
 // Number of blocks of kBlock threads to cover `work` items (capped for reductions).
 inline int blocks_for(long long work) { return (int)((work + kBlock - 1) / kBlock); }

@@ -64,7 +64,7 @@ __global__ void k_resid64_mixed(const double *__restrict__ phi, const double *__
         B[t] = (float)s.c;
         acc.add(res);
     }
-    const Moments m = block_moments(acc.get());
+    const Moments m = block_moments(acc);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = m;
 }
@@ -321,9 +321,10 @@ int phase_residual(MixedHier *h, const MixedShared &sh, const mg5_params *p, dou
 {
     const int N = h->N;
     const long long n3 = (long long)N * N * N;
+    const int cap = zero ? kReduceBlocks : kReduceBlocksFp64;   // ZERO: memory-bound
     int grid = blocks_for(n3);
-    if (grid > kMomentBlocks)
-        grid = kMomentBlocks;
+    if (grid > cap)
+        grid = cap;
     {
         ProfScope ps(sh.prof, PK_RESID64_MIXED, st, (double)n3);
         const CoefT<double> cf = make_coef<double>(p->h, p->alpha);

@@ -29,7 +29,7 @@ static __device__ __align__(256) mg5::Moments g_noalloc_partials[kNoAllocMaxBloc
 std::mutex g_noalloc_mu;
 mg5::Moments *g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
-// r = f + c - op(phi) on the periodic cube; per block (count, mean, M2) of r
+// r = f + c - op(phi) on the periodic cube; per block the shifted sums of r
 __global__ void k_residual_partials(const double *__restrict__ phi, const double *__restrict__ f,
                                     double c, int n, mg5::CoefT<double> cf, mg5::Moments *partials)
 {
@@ -47,24 +47,33 @@ __global__ void k_residual_partials(const double *__restrict__ phi, const double
         gather(phi, phi, r, k, kp, km, s);
         acc.add(f[t] + c - cell_op(s, cf));
     }
-    const Moments m = block_moments(acc.get());
+    const Moments m = block_moments(acc);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = m;
 }
 
-// out[0] = mean r, out[1] = ||r - mean r||_2, out[2] = ||r||_2, the block moments
-// combined pairwise in a fixed order (no cancellation when |mean r| >> its spread)
+// out[0] = mean r, out[1] = ||r - mean r||_2, out[2] = ||r||_2 from the blocks' shifted
+// sums, moved onto block 0's shift and summed in a fixed order (no cancellation when
+// |mean r| is far above its spread)
 __global__ void k_norm_finalize(const mg5::Moments *__restrict__ partials, int nb, double *out)
 {
     using namespace mg5;
-    Moments v{0.0, 0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < nb; b += blockDim.x)
-        v = mom_combine(v, partials[b]);
-    v = block_moments(v);
+    const double k0 = partials[0].k;
+    Moments v{0.0, k0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const Moments u = mom_shift(partials[b], k0);
+        v.n += u.n;
+        v.s += u.s;
+        v.q += u.q;
+    }
+    v = block_sum_shared_shift(v);
     if (threadIdx.x == 0) {
-        out[0] = v.mean;
-        out[1] = sqrt(v.m2);
-        out[2] = sqrt(fma(v.n * v.mean, v.mean, v.m2));   // sum r^2 = M2 + n mean^2
+        double m = 0.0, m2 = 0.0;
+        if (v.n > 0.0)
+            mom_mean_m2(v, &m, &m2);
+        out[0] = m;
+        out[1] = sqrt(m2);
+        out[2] = sqrt(fma(v.n * m, m, m2));   // sum r^2 = M2 + n mean^2
     }
 }
 
