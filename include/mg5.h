@@ -83,8 +83,8 @@ typedef struct mg5_ctx mg5_ctx;  /* opaque; owns the device hierarchy, resident 
 /* Solver parameters.  alpha, s: coefficients of Eq. (eomvarphi) (see
  * mg5_ndgp_coefficients); h: cell size; tol: stop when
  * ||r - mean r||_2 <= tol ||s delta||_2 on the finest grid (the norm is reduced
- * from per-block counts, means and sums of squared deviations combined pairwise,
- * so it stays accurate when |mean r| is far above the spread of r).
+ * from sums of deviations from a residual value of the same set, so it stays
+ * accurate when |mean r| is far above the spread of r).
  * nu1, nu2: pre-/post-smoothing sweeps; nu_coarse: sweep cap on the
  * coarsest grid (which sweeps until its residual falls 1e-3);
  * max_cycles: V-cycle cap (MG5_MIXED: cap on FP64 defect-correction steps);
@@ -350,18 +350,22 @@ int mg5_solve_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const in
  * The table is process-wide, keyed by (device, precision, grid side n); solves,
  * batch captures and MG5_GRAPH captures read it when they start (a captured
  * graph keeps the schedule it was captured with).  Defaults: FP64 two-pass with
- * 256 threads; the mixed mode's FP32 correction form fused where n >= 32 and
- * n % 4 == 0. */
+ * 256 threads; the mixed mode's FP32 correction form as a column march where n is
+ * a multiple of 32, else fused where n >= 32 and n % 4 == 0. */
 #define MG5_SWEEP_TWO_PASS 0
 #define MG5_SWEEP_FUSED    1
+#define MG5_SWEEP_MARCH    2   /* MG5_MIXED's FP32 correction-form sweep as a column march
+                                  (grid sides that are multiples of 32; others use the fused
+                                  kernel); in MG5_FP64 it reads as MG5_SWEEP_FUSED */
 typedef struct {
-    int form;    /* MG5_SWEEP_TWO_PASS or MG5_SWEEP_FUSED */
+    int form;    /* MG5_SWEEP_TWO_PASS, MG5_SWEEP_FUSED or MG5_SWEEP_MARCH */
     int block;   /* threads per block of the two-pass kernels (32 .. 1024, a multiple of 32) */
-    int chunk;   /* planes per CTA of the fused kernel (0 = automatic) */
+    int chunk;   /* planes per CTA of the fused or march kernel (0 = automatic) */
     float ms;    /* the tuner's median time of one sweep (0 when set by hand) */
 } mg5_schedule;
 /* Time every candidate schedule (two-pass with 64/128/256/512 threads, fused with
- * 8/16/32 planes where it fits) on a synthetic field of each grid side of the
+ * 8/16/32 planes where it fits, and for MG5_MIXED the column march with automatic,
+ * 16, 32, 64 or 128 planes where it fits) on a synthetic field of each grid side of the
  * hierarchy of N (coarsest excluded) on ctx's device and stream, and record the
  * fastest; sides already in the table are kept.  Synchronises `stream`; must not
  * run during a stream capture.  Allocates (and frees) 3-4 grids of the side. */
@@ -488,7 +492,8 @@ int mg5_step_sweep_fused(mg5_ctx *ctx, const double *phi_in, double *phi_out, co
 /* FP32 sweep of the mixed-precision inner solve.  With B == NULL it is the
  * sweep above in FP32; with a base B it relaxes the correction e of
  * op(B + e) - op(B) = f + c (B fixed).  variant 0: two-pass kernel,
- * 1: fused kernel.  e_in and e_out must not alias. */
+ * 1: fused kernel, 2: column-march kernel (needs B and N a multiple of 32).
+ * Every variant computes the same values.  e_in and e_out must not alias. */
 int mg5_step_sweep_f32(mg5_ctx *ctx, const float *e_in, float *e_out, const float *f,
                        const float *B, double c, int N, double h, double alpha, int variant,
                        void *stream);

@@ -24,7 +24,7 @@ if not os.path.exists(_LIB_PATH):
 _lib = ctypes.CDLL(_LIB_PATH)
 
 OK, W_DISC_CLAMP, W_UNTUNED = 0, 1, 2
-SWEEP_TWO_PASS, SWEEP_FUSED = 0, 1
+SWEEP_TWO_PASS, SWEEP_FUSED, SWEEP_MARCH = 0, 1, 2
 E_ARG, E_OOM, E_CUDA, E_NOT_CONVERGED, E_DIVERGED, E_NONFINITE, E_TOO_LARGE = -1, -2, -3, -4, -5, -6, -7
 FP64, MIXED = 0, 1
 WARM, HOST_IO, FMG_START, GRAPH = 1, 2, 4, 8
@@ -596,6 +596,7 @@ class Context:
 
     def step_sweep_f32(self, e_in, f, c: float, h: float, alpha: float, base=None, fused=False,
                        out=None, stream=None):
+        """mg5_step_sweep_f32; fused: False/0 two-pass, True/1 fused, 2 column march."""
         import torch
         n = _cube(e_in, "e_in")
         self._cubes(n, f=f, base=base, out=out)
@@ -604,7 +605,7 @@ class Context:
         self._check(_lib.mg5_step_sweep_f32(self._h, _ptr(e_in, "float32", dv),
                                             _ptr(out, "float32", dv), _ptr(f, "float32", dv),
                                             _ptr(base, "float32", dv), c, n, h, alpha,
-                                            1 if fused else 0, _stream(stream)))
+                                            int(fused), _stream(stream)))
         return out
 
     def step_operator(self, phi, h: float, alpha: float, out=None, stream=None):

@@ -315,6 +315,8 @@ cudaError_t prepare_fused_kernels()
         e = cudaFuncSetAttribute(k_sweep_fused<double, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(FusedSmem<double, false>));
+    if (e == cudaSuccess)
+        e = prepare_march_kernel();
     return e;
 }
 

@@ -1199,7 +1199,10 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
     CK(cudaMemcpyAsync(tail + 1, &ctx->ls[0].mean, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(ctx_wait(ctx, st));
     ctx->prof.resolve();
-    if (status == MG5_OK && cnt.clamped > 0)
+    if (cnt.clamped & kSweepFaultBit) {
+        ctx->err = "a sweep's wait for its input planes gave up";
+        status = MG5_E_CUDA;
+    } else if (status == MG5_OK && cnt.clamped > 0)
         status = MG5_W_DISC_CLAMP;
     if (info) {
         float ms = 0.f;
@@ -1547,7 +1550,10 @@ static int relax_patch_impl(mg5_ctx *ctx, const double *delta_f, const int pf[3]
     CK(cudaMemcpyAsync(&cnt, ctx->cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     CK(ctx_wait(ctx, st));
     ctx->prof.resolve();
-    if (status == MG5_OK && cnt.clamped > 0)
+    if (cnt.clamped & kSweepFaultBit) {
+        ctx->err = "a sweep's wait for its input planes gave up";
+        status = MG5_E_CUDA;
+    } else if (status == MG5_OK && cnt.clamped > 0)
         status = MG5_W_DISC_CLAMP;
     if (info) {
         float ms = 0.f;
@@ -2095,7 +2101,9 @@ int graph_finish(GraphEntry *g, mg5_info *info)
         info->coarse_sweeps = cnt.coarse_sweeps;
         info->disc_clamped = (long long)cnt.clamped;
     }
-    if (status == MG5_OK && cnt.clamped > 0)
+    if (cnt.clamped & kSweepFaultBit)
+        status = MG5_E_CUDA;   // a sweep's wait for its input planes gave up
+    else if (status == MG5_OK && cnt.clamped > 0)
         status = MG5_W_DISC_CLAMP;
     g->busy = false;
     return status;
@@ -2543,7 +2551,10 @@ int mg5_solve_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const in
         const CaptureStats &cs = b->stats[i];
         count_launch(cs.launches_fixed + cs.launches_per_iter * ctl[i].outer);
         int status = ctl[i].status;
-        if (status == MG5_OK && cnt[i].clamped > 0)
+        if (cnt[i].clamped & kSweepFaultBit) {
+            ctx->err = "a sweep's wait for its input planes gave up";
+            status = MG5_E_CUDA;
+        } else if (status == MG5_OK && cnt[i].clamped > 0)
             status = MG5_W_DISC_CLAMP;
         if (status < 0 || (worst == MG5_OK && status > 0))
             worst = status;
@@ -2588,14 +2599,16 @@ int mg5_step_sweep_f32(mg5_ctx *ctx, const float *in, float *out, const float *f
                        double c, int N, double h, double alpha, int variant, void *stream)
 {
     if (!ctx || !in || !out || !f || in == out || N < 2 || (N & 1) || !(h > 0.0) ||
-        (variant != 0 && variant != 1))
+        variant < 0 || variant > 2 || (variant == 2 && (!B || !march_ok(N))))
         return MG5_E_ARG;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     double *cd = &ctx->ls[kStepSlot].c;
     CK(cudaMemcpyAsync(cd, &c, sizeof(double), cudaMemcpyHostToDevice, st));
     const CoefT<float> cf = make_coef<float>(h, alpha);
-    if (variant == 1)
+    if (variant == 2)
+        CK(launch_sweep_march(in, out, f, B, cd, N, cf, &ctx->cnt->clamped, st));
+    else if (variant == 1)
         CK(launch_sweep_fused<float>(in, out, f, cd, N, cf, &ctx->cnt->clamped, st, B));
     else
         CK(launch_sweep<float>(in, out, f, cd, N, cf, &ctx->cnt->clamped, st, B));

@@ -399,11 +399,11 @@ __device__ __forceinline__ float sigma_corr(const Parts2 &q, const CoefT<float> 
     return cf.s3 * X + cf.s8 * Y;
 }
 
-__device__ __forceinline__ float cell_update_corr(const St<float> &e, const St<float> &B, float rhs,
-                                                  const CoefT<float> &cf, bool &clamped)
+// The update from the (e, B) parts, B's centre Bc and e's centre ec (used by omega != 1).
+__device__ __forceinline__ float cell_update_corr_parts(const Parts2 &q, float Bc, float ec, float rhs,
+                                                        const CoefT<float> &cf, bool &clamped)
 {
-    const Parts2 q = parts2_of(e, B);
-    const float bp = fmaf(cf.k43h, fmaf(-6.0f, B.c, q.S.y), 1.0f);   // beta' = 1 + (4 alpha/3) L_B
+    const float bp = fmaf(cf.k43h, fmaf(-6.0f, Bc, q.S.y), 1.0f);   // beta' = 1 + (4 alpha/3) L_B
     const float bq = rhs + sigma_corr(q, cf);                        // b'
     float disc = fmaf(bp, bp, cf.k8 * bq);
     if (disc < 0.0f) {
@@ -413,7 +413,13 @@ __device__ __forceinline__ float cell_update_corr(const St<float> &e, const St<f
     const float sq = disc > 0.0f ? disc * rsqrtf(disc) : 0.0f;
     const float L = bp >= 0.0f ? __fdividef(2.0f * bq, bp + sq) : (sq - bp) * cf.inv2k23;
     const float r6 = q.S.x - cf.h2 * L;
-    return cf.om1 != 0.0f ? cf.w6 * r6 + cf.omc * e.c : r6 * (1.0f / 6.0f);
+    return cf.om1 != 0.0f ? cf.w6 * r6 + cf.omc * ec : r6 * (1.0f / 6.0f);
+}
+
+__device__ __forceinline__ float cell_update_corr(const St<float> &e, const St<float> &B, float rhs,
+                                                  const CoefT<float> &cf, bool &clamped)
+{
+    return cell_update_corr_parts(parts2_of(e, B), B.c, e.c, rhs, cf, clamped);
 }
 
 // op(B + e) - op(B) in FP32: L_e + (2 alpha / 3) L_e (2 L_B + L_e) - alpha (2 Sigma(B, e) + Sigma(e))

@@ -90,10 +90,19 @@ inline bool fused_ok(int n)
     return n >= kFusedMinN && n % (int)(16 / sizeof(T)) == 0;
 }
 cudaError_t prepare_fused_kernels();
+// FP32 correction-form sweep as a column march (k_march.cu): 32 x 32 tiles, n a multiple
+// of 32, B required; `chunk` planes per CTA (0: about three waves over 152 SMs)
+bool march_ok(int n);
+cudaError_t launch_sweep_march(const float *in, float *out, const float *f, const float *B,
+                               const double *cptr, int n, CoefT<float> cf,
+                               unsigned long long *clamp, cudaStream_t st, int chunk = 0);
+cudaError_t prepare_march_kernel();
+// set in a clamp counter by a sweep whose wait for its input planes gave up (never expected)
+constexpr unsigned long long kSweepFaultBit = 1ull << 63;
 
 // How one grid side is swept (speed only: every schedule computes the same values).
 struct SweepSchedule {
-    int form = 0;     // 0: two-pass, 1: fused
+    int form = 0;     // 0: two-pass, 1: fused, 2: column march (FP32 correction form)
     int block = kBlock;
     int chunk = 0;
     float ms = 0.f;   // tuned time of one sweep (0: not measured)
@@ -111,8 +120,12 @@ cudaError_t launch_sweep_sched(const SweepSchedule &s, const T *in, T *out, cons
                                const double *cptr, int n, CoefT<T> cf, unsigned long long *clamp,
                                cudaStream_t st, const T *B = nullptr)
 {
-    if (s.form == 1 && fused_ok<T>(n))
-        return launch_sweep_fused<T>(in, out, f, cptr, n, cf, clamp, st, B, s.chunk);
+    if constexpr (sizeof(T) == 4) {
+        if (s.form == 2 && B && march_ok(n))
+            return launch_sweep_march(in, out, f, B, cptr, n, cf, clamp, st, s.chunk);
+    }
+    if ((s.form == 1 || s.form == 2) && fused_ok<T>(n))
+        return launch_sweep_fused<T>(in, out, f, cptr, n, cf, clamp, st, B, s.form == 1 ? s.chunk : 0);
     return launch_sweep<T>(in, out, f, cptr, n, cf, clamp, st, B, s.block);
 }
 template <typename T>

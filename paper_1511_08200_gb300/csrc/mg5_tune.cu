@@ -1,7 +1,8 @@
 // mg5_tune.cu -- autotuner of the sweep schedule (host runtime, C ABI in mg5.h).
 //
 // The smoother's schedule changes speed, not values: the two-pass sweep with
-// 64 .. 512 threads per block, or the fused plane-march with 8 .. 32 planes per
+// 64 .. 512 threads per block, the column march of the mixed mode's FP32 sweep
+// (k_march.cu), or the fused plane-march with 8 .. 32 planes per
 // CTA, all apply the same cell update to the same snapshot (the sweep of
 // Sec. 3.1).  Which is fastest depends on the grid side (waves over the 152
 // SMs, shared-memory rings vs L2 reuse) and on the precision (the FP64 sweep
@@ -41,7 +42,9 @@ std::atomic<unsigned long long> g_sched_version{1};
 SweepSchedule default_schedule(int precision, int n)
 {
     SweepSchedule s;
-    if (precision == MG5_MIXED && fused_ok<float>(n))
+    if (precision == MG5_MIXED && march_ok(n))
+        s.form = 2;
+    else if (precision == MG5_MIXED && fused_ok<float>(n))
         s.form = 1;
     return s;
 }
@@ -88,6 +91,14 @@ std::vector<SweepSchedule> candidates(int precision, int n)
             if (c <= n) {
                 SweepSchedule s;
                 s.form = 1;
+                s.chunk = c;
+                v.push_back(s);
+            }
+    if (precision == MG5_MIXED && march_ok(n))
+        for (int c : {0, 16, 32, 64, 128})
+            if (c <= n) {
+                SweepSchedule s;
+                s.form = 2;
                 s.chunk = c;
                 v.push_back(s);
             }
@@ -230,7 +241,8 @@ int mg5_schedule_set(int device, int precision, int n, const mg5_schedule *s)
 {
     if (!s || (precision != MG5_FP64 && precision != MG5_MIXED) || n < 1)
         return MG5_E_ARG;
-    if ((s->form != MG5_SWEEP_TWO_PASS && s->form != MG5_SWEEP_FUSED) || s->block < 32 ||
+    if ((s->form != MG5_SWEEP_TWO_PASS && s->form != MG5_SWEEP_FUSED &&
+         s->form != MG5_SWEEP_MARCH) || s->block < 32 ||
         s->block > 1024 || s->block % 32 || s->chunk < 0)
         return MG5_E_ARG;
     SweepSchedule v;
@@ -271,7 +283,8 @@ int mg5_tune_save(const char *path)
                      "\"block\": %d, \"chunk\": %d, \"ms\": %.6g}\n",
                      device_name(std::get<0>(r.first)).c_str(),
                      std::get<1>(r.first) == MG5_MIXED ? "mixed" : "fp64", std::get<2>(r.first),
-                     s.form == 1 ? "fused" : "two-pass", s.block, s.chunk, (double)s.ms);
+                     s.form == 2 ? "march" : (s.form == 1 ? "fused" : "two-pass"), s.block,
+                     s.chunk, (double)s.ms);
     }
     return std::fclose(fp) == 0 ? MG5_OK : MG5_E_ARG;
 }
@@ -309,7 +322,9 @@ int mg5_tune_load(const char *path)
             continue;
         }
         mg5_schedule s;
-        s.form = std::strcmp(form, "fused") == 0 ? MG5_SWEEP_FUSED : MG5_SWEEP_TWO_PASS;
+        s.form = std::strcmp(form, "march") == 0
+                     ? MG5_SWEEP_MARCH
+                     : (std::strcmp(form, "fused") == 0 ? MG5_SWEEP_FUSED : MG5_SWEEP_TWO_PASS);
         s.block = block;
         s.chunk = chunk;
         s.ms = (float)ms;

@@ -108,7 +108,9 @@ def test_schedule_table_host_logic(lib, tmp_path):
     s, tuned = mg.schedule_get(0, "fp64", 64)
     assert not tuned and (s.form, s.block) == (mg.SWEEP_TWO_PASS, 256)
     s, tuned = mg.schedule_get(0, "mixed", 64)
-    assert not tuned and s.form == mg.SWEEP_FUSED          # fits the fused kernel
+    assert not tuned and s.form == mg.SWEEP_MARCH          # a multiple of 32: the column march
+    s, tuned = mg.schedule_get(0, "mixed", 48)
+    assert not tuned and s.form == mg.SWEEP_FUSED          # fits the fused kernel only
     s, _ = mg.schedule_get(0, "mixed", 16)
     assert s.form == mg.SWEEP_TWO_PASS                     # below the fused kernel's minimum
     mg.schedule_set(0, "mixed", 64, mg.SWEEP_TWO_PASS, block=128)
@@ -118,10 +120,13 @@ def test_schedule_table_host_logic(lib, tmp_path):
         with pytest.raises(mg.MG5Error):
             mg.schedule_set(0, "fp64", 32, **bad)
     path = tmp_path / "tune.jsonl"
+    mg.schedule_set(0, "mixed", 96, mg.SWEEP_MARCH, chunk=24)
     mg.tune_save(path)
     rows = [json.loads(x) for x in path.read_text().splitlines()]
     assert rows == [{"gpu": rows[0]["gpu"], "precision": "mixed", "n": 64, "form": "two-pass",
-                     "block": 128, "chunk": 0, "ms": 0}]
+                     "block": 128, "chunk": 0, "ms": 0},
+                    {"gpu": rows[0]["gpu"], "precision": "mixed", "n": 96, "form": "march",
+                     "block": 256, "chunk": 24, "ms": 0}]
     mg.tune_clear()
     assert not mg.schedule_get(0, "mixed", 64)[1]
     import torch

@@ -207,3 +207,43 @@ def test_fused_matches_two_pass_fp32(ctx, n):
     a = host(ctx.step_sweep_f32(_f32(e), _f32(rhs), 0.0, h, alpha, base=_f32(B), fused=False))
     b = host(ctx.step_sweep_f32(_f32(e), _f32(rhs), 0.0, h, alpha, base=_f32(B), fused=True))
     assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("n", [32, 64, 96, 160])
+@pytest.mark.parametrize("rough", [0.0, 1.0])
+def test_march_equals_fused_fp32(ctx, n, rough):
+    """The column-march FP32 sweep applies the same update to the same operands in the same
+    order as the gather-based fused and two-pass kernels: equal to the bit (fused), and to
+    FP32 rounding (two-pass); and it is the oracle's sweep of B + e (correction form)."""
+    alpha, s, h = nominal()
+    B = _base_field(n, 31, rough)
+    e = 1e-2 * B * (1.0 + 0.1 * workload.lognormal_delta(n, 1.0, 32))
+    rhs = 1e-2 * s * workload.lognormal_delta(n, 1.0, 33)
+    c = 2e-12
+    args = (_f32(e), _f32(rhs), c, h, alpha)
+    m = host(ctx.step_sweep_f32(*args, base=_f32(B), fused=2))
+    f1 = host(ctx.step_sweep_f32(*args, base=_f32(B), fused=1))
+    f0 = host(ctx.step_sweep_f32(*args, base=_f32(B), fused=0))
+    assert np.array_equal(m, f1)
+    assert np.abs(m - f0).max() <= 1e-6 * np.abs(f0).max()
+    if n <= 64:
+        Bq = np.asarray(B, dtype=np.float32).astype(np.float64)
+        eq = np.asarray(e, dtype=np.float32).astype(np.float64)
+        fq = np.asarray(rhs, dtype=np.float32).astype(np.float64)
+        u = oracle.sweep(Bq + eq, oracle.operator(Bq, h, alpha) + fq, c, h, alpha)
+        ref = u - Bq
+        assert np.abs(m.astype(np.float64) - ref).max() < 1e-4 * np.abs(ref).max()
+
+
+def test_march_refuses_sizes_it_does_not_tile(ctx):
+    import torch
+    import paper_1511_08200_gb300 as mg
+    alpha, s, h = nominal()
+    for n in (16, 48):
+        z = torch.zeros((n,) * 3, dtype=torch.float32, device="cuda")
+        with pytest.raises(mg.MG5Error) as e:
+            ctx.step_sweep_f32(z, z, 0.0, h, alpha, base=z, fused=2)
+        assert e.value.code == mg.E_ARG
+    z = torch.zeros((32,) * 3, dtype=torch.float32, device="cuda")
+    with pytest.raises(mg.MG5Error):
+        ctx.step_sweep_f32(z, z, 0.0, h, alpha, fused=2)   # no base

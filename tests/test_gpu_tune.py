@@ -59,6 +59,7 @@ def test_every_schedule_gives_the_same_solution(mg, prec, tol, bar):
     scale = np.abs(ref).max()
     schedules = [dict(form=mg.SWEEP_TWO_PASS, block=b) for b in (64, 128, 512)]
     schedules += [dict(form=mg.SWEEP_FUSED, chunk=c) for c in (8, 16, 32)]
+    schedules += [dict(form=mg.SWEEP_MARCH, chunk=c) for c in (0, 7, 20, 64)]
     for sch in schedules:
         mg.tune_clear()
         for m in _sides(n):
@@ -85,4 +86,22 @@ def test_autotune_on_first_use_and_in_batch(mg):
     assert all(i.status in (0, 1) for i in infos)
     assert all(mg.schedule_get(0, "mixed", m)[1] for m in _sides(32) + _sides(64))
     assert not mg.schedule_get(0, "fp64", 64)[1]     # only the precision that ran
+    ctx.close()
+
+
+@pytest.mark.parametrize("n", [64, 96])
+def test_march_schedule_solve_is_bit_identical(mg, n):
+    """A mixed solve whose FP32 sweeps run as column marches (chunks of 7, 20 and 64 planes,
+    and the automatic one) equals, to the bit, the same solve with the fused sweep."""
+    ctx = ctx_fixture()
+    d = dev(workload.lognormal_delta(n, 1.5, 41))
+    for m in _sides(n):
+        mg.schedule_set(0, "mixed", m, form=mg.SWEEP_FUSED, chunk=16)
+    ref, iref = _solve(ctx, mg, d, "mixed", 1e-8)
+    for c in (0, 7, 20, 64):
+        mg.tune_clear()
+        for m in _sides(n):
+            mg.schedule_set(0, "mixed", m, form=mg.SWEEP_MARCH, chunk=c)
+        got, info = _solve(ctx, mg, d, "mixed", 1e-8)
+        assert np.array_equal(got, ref) and info.cycles == iref.cycles, c
     ctx.close()
