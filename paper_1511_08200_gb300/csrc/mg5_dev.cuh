@@ -391,29 +391,34 @@ __device__ __forceinline__ Parts2 parts2_of(const St<float> &e, const St<float> 
 }
 
 // alpha (2 Sigma(B, e) + Sigma(e)), the weights folded into s3 = alpha / (3 h^4), s8 = alpha / (8 h^4)
+// Every operation of the update is written as an explicitly rounded intrinsic, so the compiler
+// cannot contract it differently in different kernels: every kernel that calls it (gather,
+// fused, column march) computes the same sweep to the bit.
 __device__ __forceinline__ float sigma_corr(const Parts2 &q, const CoefT<float> &cf)
 {
-    const auto t = [](float2 v) { return v.x * fmaf(2.0f, v.y, v.x); };
-    const float X = t(q.a) + t(q.b) + t(q.c);
-    const float Y = t(q.dxy) + t(q.dxz) + t(q.dyz);
-    return cf.s3 * X + cf.s8 * Y;
+    const auto t = [](float2 v) { return __fmul_rn(v.x, __fmaf_rn(2.0f, v.y, v.x)); };
+    const float X = __fadd_rn(__fadd_rn(t(q.a), t(q.b)), t(q.c));
+    const float Y = __fadd_rn(__fadd_rn(t(q.dxy), t(q.dxz)), t(q.dyz));
+    return __fmaf_rn(cf.s3, X, __fmul_rn(cf.s8, Y));
 }
 
 // The update from the (e, B) parts, B's centre Bc and e's centre ec (used by omega != 1).
 __device__ __forceinline__ float cell_update_corr_parts(const Parts2 &q, float Bc, float ec, float rhs,
                                                         const CoefT<float> &cf, bool &clamped)
 {
-    const float bp = fmaf(cf.k43h, fmaf(-6.0f, Bc, q.S.y), 1.0f);   // beta' = 1 + (4 alpha/3) L_B
-    const float bq = rhs + sigma_corr(q, cf);                        // b'
-    float disc = fmaf(bp, bp, cf.k8 * bq);
+    const float bp = __fmaf_rn(cf.k43h, __fmaf_rn(-6.0f, Bc, q.S.y), 1.0f);   // beta' = 1 + (4 alpha/3) L_B
+    const float bq = __fadd_rn(rhs, sigma_corr(q, cf));                        // b'
+    float disc = __fmaf_rn(bp, bp, __fmul_rn(cf.k8, bq));
     if (disc < 0.0f) {
         disc = 0.0f;
         clamped = true;
     }
-    const float sq = disc > 0.0f ? disc * rsqrtf(disc) : 0.0f;
-    const float L = bp >= 0.0f ? __fdividef(2.0f * bq, bp + sq) : (sq - bp) * cf.inv2k23;
-    const float r6 = q.S.x - cf.h2 * L;
-    return cf.om1 != 0.0f ? cf.w6 * r6 + cf.omc * ec : r6 * (1.0f / 6.0f);
+    const float sq = disc > 0.0f ? __fmul_rn(disc, rsqrtf(disc)) : 0.0f;
+    const float L = bp >= 0.0f ? __fdividef(__fmul_rn(2.0f, bq), __fadd_rn(bp, sq))
+                               : __fmul_rn(__fsub_rn(sq, bp), cf.inv2k23);
+    const float r6 = __fmaf_rn(-cf.h2, L, q.S.x);
+    return cf.om1 != 0.0f ? __fmaf_rn(cf.w6, r6, __fmul_rn(cf.omc, ec))
+                          : __fmul_rn(r6, 1.0f / 6.0f);
 }
 
 __device__ __forceinline__ float cell_update_corr(const St<float> &e, const St<float> &B, float rhs,

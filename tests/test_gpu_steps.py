@@ -224,7 +224,8 @@ def test_march_equals_fused_fp32(ctx, n, rough):
     m = host(ctx.step_sweep_f32(*args, base=_f32(B), fused=2))
     f1 = host(ctx.step_sweep_f32(*args, base=_f32(B), fused=1))
     f0 = host(ctx.step_sweep_f32(*args, base=_f32(B), fused=0))
-    assert np.array_equal(m, f1)
+    assert np.array_equal(m, f1), (float(np.abs(m - f1).max() / np.abs(f1).max()),
+                                   int((m != f1).sum()), np.argwhere(m != f1)[:8].tolist())
     assert np.abs(m - f0).max() <= 1e-6 * np.abs(f0).max()
     if n <= 64:
         Bq = np.asarray(B, dtype=np.float32).astype(np.float64)
