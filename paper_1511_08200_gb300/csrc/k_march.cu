@@ -2,28 +2,30 @@
 // of the mixed-precision solve) as a column march: one read and one write of e per
 // cell per full sweep, with most of the stencil reused from registers.
 //
-// A CTA owns a 32 x 32 (j, k) tile and marches along i over a chunk of planes.  Its
-// 512 tile threads each own a pair of columns (j, k0 + 2 pp + {0, 1}); at plane step p
-// the pair's column c with (p + 1 + j + c) even relaxes its red cell on plane p + 1 and
-// its black cell on plane p (in the same column: red on p + 1 <=> black on p), and the
-// other column rests.  The snapshot semantics split the stencil cleanly:
+// A CTA owns a 16 x 32 (j, k) tile and marches along i over a chunk of planes.  Each of
+// its 256 tile threads owns a pair of adjacent positions (j, k0 + 2 pp + {0, 1}); at plane
+// step p the pair's position with (p + 1 + j + k) even relaxes its red cell on plane p + 1
+// and its black cell on plane p (red on p + 1 <=> black on p in one position), and the
+// other position rests.  The snapshot semantics split the stencil cleanly:
 //   * a red cell reads only old values;
 //   * a black cell reads new red values at its 6 faces and old (black) values at its
 //     12 edges;
 // and the edge terms of a cell are differences of per-plane differences of the same
-// column: with Dy_q = e(q, j+1) - e(q, j-1) and Dz_q = e(q, k+1) - e(q, k-1),
+// position: with Dy_q = e(q, j+1) - e(q, j-1) and Dz_q = e(q, k+1) - e(q, k-1),
 //   dxy(p) = Dy_{p+1} - Dy_{p-1},  dxz(p) = Dz_{p+1} - Dz_{p-1},
-// and dyz(p), the face sums and B's parts come from the plane itself.  Each plane of a
-// column is therefore read once per sweep (9 values of e, 9 of B, around the column),
-// its differences are kept in registers for the two steps that need them, and the new
-// red values of the black cells' in-plane faces come through shared memory.  The
-// black cells' x-faces are the thread's own red values of the planes above and below.
+// while dyz(p), the face sums and B's parts come from the plane itself.  Each plane of a
+// position is therefore read once per sweep (9 values of e, 9 of B around it), its sums
+// and differences stay in registers for the two steps that use them, and the new red
+// values of the black cells' in-plane faces pass through shared memory; a black cell's
+// x-faces are the thread's own red values of the planes above and below.
 //
-// The new red values on the ring around the tile (the black cells at the tile's edge
-// need them) are computed by three extra warps from full gathers; the same warps bring
-// the planes of e, B and f into a ring of 6 shared-memory slots with bulk asynchronous
-// copies (cp.async.bulk, one per row segment, completion counted on an mbarrier per
-// slot), 3 plane steps ahead of use.
+// The black cells at the tile's edge need the new red values of the ring of positions
+// around the tile; 50 more threads own pairs of ring positions and compute their red
+// cells the same way (red only).  Threads past the tile also bring the planes of e, B
+// and f into a ring of 6 shared-memory slots with bulk asynchronous copies
+// (cp.async.bulk, one per row segment, completion counted on one mbarrier per slot),
+// three plane steps ahead of use.  320 threads and 62 KB of shared memory a CTA: two
+// CTAs per SM, so one CTA's barrier waits overlap the other's work.
 //
 // Every cell is updated by the same arithmetic on the same operands, in the same order,
 // as the gather-based kernels (cell_update_corr_parts), so the result is the same sweep
@@ -34,19 +36,20 @@ namespace mg5 {
 
 namespace {
 
-constexpr int MT_J = 32, MT_K = 32;           // tile (j, k)
+constexpr int MT_J = 16, MT_K = 32;           // tile (j, k)
 constexpr int MT_TILE = MT_J * MT_K / 2;      // tile threads: one per column pair
-constexpr int MT_RING = 96;                   // ring warps: ring red cells and copies
-constexpr int MT_THREADS = MT_TILE + MT_RING;
-constexpr int MR = MT_J + 4;                  // plane rows j0-2 .. j0+33
+constexpr int MT_RINGP = (MT_K + 2) + MT_J;   // ring threads: pairs of ring positions (50)
+constexpr int MT_THREADS = 320;               // 256 tile + 50 ring + 14 that only copy
+constexpr int MR = MT_J + 4;                  // plane rows j0-2 .. j0+17
 constexpr int MO = MT_K + 8;                  // plane row: k0-4 .. k0+35 (16-byte aligned)
 constexpr int MPL = MR * MO;                  // floats of one plane
 constexpr int MNS = 6;                        // plane slots
-constexpr int RNR = MT_J + 2, RNO = MT_K + 2; // new red values: j0-1 .. j0+32, k0-1 .. k0+32
+constexpr int RNR = MT_J + 2, RNO = MT_K + 2; // new red values: j0-1 .. j0+16, k0-1 .. k0+32
 constexpr int RNP = RNR * RNO;
-constexpr int MT_RINGCELLS = 2 * (MT_K + 2) / 2 + 2 * MT_J / 2;   // 66 red cells per plane
+constexpr int MT_COPIERS = 3 * MR;            // one thread per copied row (60)
 constexpr unsigned MT_PLANE_BYTES = 3u * MR * MO * 4u;           // e, B, f rows of a plane
 constexpr long long kWaitLimit = 1ll << 26;   // mbarrier polls before giving up
+static_assert(MT_TILE + MT_RINGP <= MT_THREADS && MT_COPIERS <= MT_THREADS - MT_TILE, "roles");
 
 struct MarchSmem {
     float E[MNS][MPL];
@@ -98,14 +101,14 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 
 __device__ __forceinline__ int wrapn(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
-// values a column keeps between its two active steps (plane p: read two steps earlier as
+// values a position keeps between its two active steps (plane p: read two steps earlier as
 // plane p + 2; plane p - 1: read two steps earlier as plane p + 1)
 struct ColCache {
     float cE0, DyE0, DzE0, dyzE0, cB0, DyB0, DzB0, dyzB0, YB0, ZB0;   // plane p
     float DyEm, DzEm, DyBm, DzBm, cBm, rm;                            // plane p - 1, red(p - 1)
 };
 
-// 3 x 3 neighbourhood of a column on one plane, reduced to what the cell arithmetic uses
+// 3 x 3 neighbourhood of a position on one plane, reduced to what the cell arithmetic uses
 struct PlaneCol {
     float c, Y, Z, Dy, Dz, dyz;
 };
@@ -141,7 +144,13 @@ __device__ __forceinline__ Parts2 parts_from(float2 sx, float2 sy, float2 sz, fl
     return q;
 }
 
-__global__ void __launch_bounds__(MT_THREADS, 1)
+// A thread's two positions (adjacent cells, so of opposite colours): plane offsets, offsets
+// in the new-red array, and for tile threads the output offset within a plane.
+struct Pos {
+    int off, rn;
+};
+
+__global__ void __launch_bounds__(MT_THREADS, 2)
     k_sweep_march(const float *__restrict__ in, float *__restrict__ out, const float *__restrict__ f,
                   const float *__restrict__ Bg, const double *__restrict__ cptr, int n, int ichunk,
                   CoefT<float> cf, unsigned long long *clamp)
@@ -151,12 +160,14 @@ __global__ void __launch_bounds__(MT_THREADS, 1)
     const int k0 = blockIdx.x * MT_K, j0 = blockIdx.y * MT_J;
     const int i0 = blockIdx.z * ichunk;
     const int i1 = min(i0 + ichunk, n);
-    const int q0 = i0 - 2;   // first plane brought in; plane q lives in slot (q - q0) % MNS
+    const int q0 = i0 - 2;        // first plane brought in; plane q lives in slot (q - q0) % MNS
+    const int last = i1 + 1;      // the last plane any step reads
     const float cval = (float)(*cptr);
     const long long n2 = (long long)n * n;
     const int tid = threadIdx.x;
     const bool tile = tid < MT_TILE;
-    const int rt = tid - MT_TILE;   // ring thread index (tile threads: negative)
+    const bool ring = !tile && tid < MT_TILE + MT_RINGP;
+    const int ct = tid - MT_TILE;   // copier index (threads past the tile)
     bool clamped = false, fault = false;
 
     if (tid == 0) {
@@ -166,68 +177,91 @@ __global__ void __launch_bounds__(MT_THREADS, 1)
     }
     __syncthreads();
 
-    // ring threads: bring plane q (its rows of e, B, f) into its slot
-    auto issue_plane = [&](int q) {
-        const int s = (q - q0) % MNS;
-        if (rt == 0) {
+    // copier threads: row `ct` of e, B or f of plane q into slot s
+    const float *csrc = nullptr;
+    float *cdst0 = nullptr;
+    long long crow = 0;
+    if (ct >= 0 && ct < MT_COPIERS) {
+        const int a = ct / MR, jr = ct - a * MR;
+        csrc = a == 0 ? in : (a == 1 ? Bg : f);
+        cdst0 = (a == 0 ? S.E[0] : (a == 1 ? S.B[0] : S.F[0])) + jr * MO;
+        crow = (long long)wrapn(j0 - 2 + jr, n) * n;
+    }
+    const bool kwrap = !(k0 > 0 && k0 + MT_K < n);
+    const int kl = k0 > 0 ? k0 - 4 : n - 4, kr = k0 + MT_K < n ? k0 + MT_K : 0;
+    auto issue_plane = [&](int q, int s) {
+        if (ct == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive_expect_tx(&S.bar[s], MT_PLANE_BYTES);
         }
-        const long long pb = (long long)wrapn(q, n) * n2;
-        for (int idx = rt; idx < 3 * MR; idx += MT_RING) {
-            const int a = idx / MR, jr = idx - a * MR;
-            const float *src = a == 0 ? in : (a == 1 ? Bg : f);
-            float *dst = (a == 0 ? S.E[s] : (a == 1 ? S.B[s] : S.F[s])) + jr * MO;
-            const float *row = src + pb + (long long)wrapn(j0 - 2 + jr, n) * n;
-            if (k0 > 0 && k0 + MT_K < n) {
+        if (csrc) {
+            const float *row = csrc + (long long)wrapn(q, n) * n2 + crow;
+            float *dst = cdst0 + s * MPL;
+            if (!kwrap) {
                 bulk_g2s(dst, row + k0 - 4, MO * 4, &S.bar[s]);
             } else {
-                bulk_g2s(dst, row + (k0 > 0 ? k0 - 4 : n - 4), 16, &S.bar[s]);
+                bulk_g2s(dst, row + kl, 16, &S.bar[s]);
                 bulk_g2s(dst + 4, row + k0, MT_K * 4, &S.bar[s]);
-                bulk_g2s(dst + 4 + MT_K, row + (k0 + MT_K < n ? k0 + MT_K : 0), 16, &S.bar[s]);
+                bulk_g2s(dst + 4 + MT_K, row + kr, 16, &S.bar[s]);
             }
         }
     };
-    // every thread: wait until plane q has landed
-    auto wait_plane = [&](int q) {
-        const int u = q - q0;
-        unsigned long long *bar = &S.bar[u % MNS];
-        const unsigned par = (unsigned)((u / MNS) & 1);
+    auto wait_slot = [&](int s, unsigned par) {
         long long it = 0;
-        while (!mbar_try_wait(bar, par)) {
+        while (!mbar_try_wait(&S.bar[s], par)) {
             if (++it > kWaitLimit) {   // never expected: record it and go on
                 fault = true;
                 break;
             }
         }
     };
-    auto slot = [&](int q) { return (q - q0) % MNS; };
+    if (ct >= 0)
+        for (int q = q0; q < q0 + MNS && q <= last; ++q)
+            issue_plane(q, q - q0);
 
-    const int last_plane = i1 + 1;   // the last plane any step reads
-    if (!tile)
-        for (int q = q0; q < q0 + MNS && q <= last_plane; ++q)
-            issue_plane(q);
+    // the thread's two positions (j, k global; A and B adjacent)
+    int jA, kA, jB, kB;
+    if (tile) {
+        jA = jB = j0 + (tid >> 4);
+        kA = k0 + 2 * (tid & 15);
+        kB = kA + 1;
+    } else if (ring) {
+        const int r = tid - MT_TILE;
+        if (r < MT_K + 2) {   // top and bottom rows: pairs along k
+            const int m = r < (MT_K + 2) / 2 ? r : r - (MT_K + 2) / 2;
+            jA = jB = r < (MT_K + 2) / 2 ? j0 - 1 : j0 + MT_J;
+            kA = k0 - 1 + 2 * m;
+            kB = kA + 1;
+        } else {              // left and right columns: pairs along j
+            const int r2 = r - (MT_K + 2);
+            const int m = r2 < MT_J / 2 ? r2 : r2 - MT_J / 2;
+            kA = kB = r2 < MT_J / 2 ? k0 - 1 : k0 + MT_K;
+            jA = j0 + 2 * m;
+            jB = jA + 1;
+        }
+    } else {
+        jA = jB = j0;
+        kA = k0;
+        kB = k0 + 1;
+    }
+    const Pos pA{(jA - j0 + 2) * MO + (kA - k0 + 4), (jA - j0 + 1) * RNO + (kA - k0 + 1)};
+    const Pos pB{(jB - j0 + 2) * MO + (kB - k0 + 4), (jB - j0 + 1) * RNO + (kB - k0 + 1)};
+    // step p relaxes the position with (p + 1 + j + k) even: A on steps of one parity
+    const bool a_even = ((q0 + 1 + jA + kA) & 1) == 0;   // A active on steps q0, q0 + 2, ...
+    const Pos p0 = a_even ? pA : pB, p1 = a_even ? pB : pA;
+    const bool first0 = a_even ? (kA < kB || jA < jB) : (kB < kA || jB < jA);
+    float *orow = out + (long long)(tile ? jA : j0) * n + (tile ? kA : k0);
+    ColCache c0{}, c1{};
+    float rprev = 0.0f;   // red value of the step before (its plane's red cell)
 
-    // tile thread geometry
-    const int jj = tile ? tid >> 4 : 0;   // row in the tile
-    const int pp = tid & 15;              // column pair
-    const int rowE = (jj + 2) * MO;       // plane offset of the thread's row
-    ColCache ca{}, cb{};                  // column sets of even / odd steps from i0
-    float rprev = 0.0f;                   // red value of the step before (plane p's red cell)
-
-    // One step p.  warm: a step before the chunk (no black cell, no output; plane p's
-    // column values are read here instead of two steps earlier).
-    auto step = [&](int p, ColCache &cc, bool warm) {
-        wait_plane(p + 2);
-        if (warm && p == q0)
-            for (int q = q0; q < q0 + 2; ++q)
-                wait_plane(q);
-        if (tile) {
-            const int j = j0 + jj;
-            const int cl = 2 * pp + ((p + 1 + j) & 1);   // local k of the active column
-            const int off = rowE + cl + 4;
-            const int s0 = slot(p), s1 = slot(p + 1), s2 = slot(p + 2);
-            if (warm) {   // plane p of the column, normally kept from two steps earlier
+    // One step p with slots s0 (plane p), s1 (p + 1), s2 (p + 2) and the active position's
+    // cache.  warm: a step before the chunk (no black cell, no output; plane p's values are
+    // read here instead of two steps earlier).
+    auto step = [&](int p, int s0, int s1, int s2, const Pos &ps, bool pfirst, ColCache &cc,
+                    bool warm) {
+        if (tile || ring) {
+            const int off = ps.off;
+            if (warm) {
                 const PlaneCol e0 = plane_col(S.E[s0] + off), b0 = plane_col(S.B[s0] + off);
                 cc.cE0 = e0.c;
                 cc.DyE0 = e0.Dy;
@@ -242,17 +276,17 @@ __global__ void __launch_bounds__(MT_THREADS, 1)
             }
             const PlaneCol e2 = plane_col(S.E[s2] + off), b2 = plane_col(S.B[s2] + off);
             const PlaneCol e1 = plane_col(S.E[s1] + off), b1 = plane_col(S.B[s1] + off);
-            // red cell (p + 1, j, c): old values throughout
+            // red cell (p + 1) of the position: old values throughout
             const Parts2 qr = parts_from(pk_add(pr2(e2.c, b2.c), pr2(cc.cE0, cc.cB0)),
                                          pr2(e1.Y, b1.Y), pr2(e1.Z, b1.Z),
                                          pk_sub(pr2(e2.Dy, b2.Dy), pr2(cc.DyE0, cc.DyB0)),
                                          pk_sub(pr2(e2.Dz, b2.Dz), pr2(cc.DzE0, cc.DzB0)),
                                          pr2(e1.dyz, b1.dyz));
             const float r1 = cell_update_corr_parts(qr, b1.c, e1.c, S.F[s1][off] + cval, cf, clamped);
-            S.RN[(p + 1) & 1][(jj + 1) * RNO + cl + 1] = r1;
-            if (!warm) {
-                // black cell (p, j, c): new red faces, old edges
-                const float *rn = S.RN[p & 1] + (jj + 1) * RNO + cl + 1;
+            S.RN[(p + 1) & 1][ps.rn] = r1;
+            if (tile && !warm) {
+                // black cell (p) of the position: new red faces, old edges
+                const float *rn = S.RN[p & 1] + ps.rn;
                 const float sye = rn[RNO] + rn[-RNO], sze = rn[1] + rn[-1];
                 const Parts2 qb = parts_from(pk_add(pr2(r1, b1.c), pr2(cc.rm, cc.cBm)),
                                              pr2(sye, cc.YB0), pr2(sze, cc.ZB0),
@@ -261,13 +295,12 @@ __global__ void __launch_bounds__(MT_THREADS, 1)
                                              pr2(cc.dyzE0, cc.dyzB0));
                 const float b0v = cell_update_corr_parts(qb, cc.cB0, cc.cE0, S.F[s0][off] + cval,
                                                          cf, clamped);
-                const bool bfirst = (cl & 1) == 0;   // the black cell is the pair's first
                 float2 v;
-                v.x = bfirst ? b0v : rprev;
-                v.y = bfirst ? rprev : b0v;
-                *reinterpret_cast<float2 *>(out + (long long)p * n2 + (long long)j * n + k0 + 2 * pp) = v;
+                v.x = pfirst ? b0v : rprev;
+                v.y = pfirst ? rprev : b0v;
+                *reinterpret_cast<float2 *>(orow + (long long)p * n2) = v;
             }
-            // keep plane p + 2 as the column's plane p, plane p + 1 as its plane p - 1
+            // keep plane p + 2 as the position's plane p, plane p + 1 as its plane p - 1
             cc.cE0 = e2.c;
             cc.DyE0 = e2.Dy;
             cc.DzE0 = e2.Dz;
@@ -285,66 +318,44 @@ __global__ void __launch_bounds__(MT_THREADS, 1)
             cc.cBm = b1.c;
             cc.rm = r1;
             rprev = r1;
-        } else if (rt < MT_RINGCELLS && !(warm && p == q0)) {
-            // red cell of plane p + 1 on the ring around the tile, from a full gather
-            const int P = p + 1;
-            int j, k;
-            if (rt < 34) {
-                const int m = rt < 17 ? rt : rt - 17;
-                j = rt < 17 ? j0 - 1 : j0 + MT_J;
-                k = k0 - 1 + ((P + j + k0 - 1) & 1) + 2 * m;
-            } else {
-                const int m = rt < 50 ? rt - 34 : rt - 50;
-                k = rt < 50 ? k0 - 1 : k0 + MT_K;
-                j = j0 + ((P + k + j0) & 1) + 2 * m;
-            }
-            const int jr = j - j0 + 2, kc = k - k0 + 4;
-            const int o = jr * MO + kc;
-            const float *em = S.E[slot(p)], *e0 = S.E[slot(P)], *ep = S.E[slot(P + 1)];
-            const float *bm = S.B[slot(p)], *b0 = S.B[slot(P)], *bp = S.B[slot(P + 1)];
-            St<float> se, sb;
-            auto g = [&](const float *xm, const float *x0, const float *xp, St<float> &t) {
-                t.c = x0[o];
-                t.xp = xp[o];
-                t.xm = xm[o];
-                t.yp = x0[o + MO];
-                t.ym = x0[o - MO];
-                t.zp = x0[o + 1];
-                t.zm = x0[o - 1];
-                t.xpyp = xp[o + MO];
-                t.xpym = xp[o - MO];
-                t.xmyp = xm[o + MO];
-                t.xmym = xm[o - MO];
-                t.xpzp = xp[o + 1];
-                t.xpzm = xp[o - 1];
-                t.xmzp = xm[o + 1];
-                t.xmzm = xm[o - 1];
-                t.ypzp = x0[o + MO + 1];
-                t.ypzm = x0[o + MO - 1];
-                t.ymzp = x0[o - MO + 1];
-                t.ymzm = x0[o - MO - 1];
-            };
-            g(em, e0, ep, se);
-            g(bm, b0, bp, sb);
-            const float v = cell_update_corr(se, sb, S.F[slot(P)][o] + cval, cf, clamped);
-            S.RN[P & 1][(j - j0 + 1) * RNO + (k - k0 + 1)] = v;
         }
-        __syncthreads();
-        // plane p - 1's slot is free now: bring in plane p + 5 (3 steps before its use)
-        if (!tile && p + 5 <= last_plane && p - 1 >= q0)
-            issue_plane(p + 5);
     };
 
-    // warm-up: red of planes i0 - 1 and i0 (tile columns), ring red of plane i0
-    step(i0 - 2, ca, true);
-    step(i0 - 1, cb, true);
+    // slots and mbarrier phases of planes p, p + 1, p + 2, kept incrementally
+    int s0 = 0, s1 = 1, s2 = 2;
+    unsigned ph2 = 0;   // phase parity of slot s2's current plane
+    auto advance = [&]() {
+        s0 = s1;
+        s1 = s2;
+        s2 = s2 == MNS - 1 ? 0 : s2 + 1;
+        if (s2 == 0)
+            ph2 ^= 1u;
+    };
+    // warm-up: steps q0 and q0 + 1 compute the red cells of planes i0 - 1 and i0
+    wait_slot(0, 0);
+    wait_slot(1, 0);
+    wait_slot(2, 0);
+    step(q0, s0, s1, s2, p0, first0, c0, true);
+    __syncthreads();
+    advance();
+    wait_slot(s2, ph2);
+    step(q0 + 1, s0, s1, s2, p1, !first0, c1, true);
+    __syncthreads();
+    // plane p - 1's slot is free after step p: plane p + 5 goes there (3 steps before use)
+    if (ct >= 0 && q0 + 6 <= last)
+        issue_plane(q0 + 6, 0);
     int p = i0;
-    for (; p + 1 < i1; p += 2) {
-        step(p, ca, false);
-        step(p + 1, cb, false);
+    for (; p < i1; ++p) {
+        advance();
+        wait_slot(s2, ph2);
+        if (((p - i0) & 1) == 0)
+            step(p, s0, s1, s2, p0, first0, c0, false);
+        else
+            step(p, s0, s1, s2, p1, !first0, c1, false);
+        __syncthreads();
+        if (ct >= 0 && p + 5 <= last)
+            issue_plane(p + 5, s0 == 0 ? MNS - 1 : s0 - 1);
     }
-    if (p < i1)
-        step(p, ca, false);
     if (clamped)
         atomicAdd(clamp, 1ull);
     if (fault)
@@ -364,8 +375,8 @@ cudaError_t launch_sweep_march(const float *in, float *out, const float *f, cons
     const int tiles = (n / MT_K) * (n / MT_J);
     int ichunk = chunk;
     if (ichunk <= 0) {
-        // about three waves of one CTA per SM, chunks of at least 16 planes
-        int chunks = (3 * 152 + tiles - 1) / tiles;
+        // about six waves of two CTAs per SM over 152 SMs, chunks of at least 16 planes
+        int chunks = (6 * 2 * 152 + tiles - 1) / tiles;
         if (chunks > n / 16)
             chunks = n / 16;
         if (chunks < 1)

@@ -429,7 +429,8 @@ def test_graph_recaptured_after_schedule_change(ctx):
         p = mg.default_params(alpha=alpha, s=s, h=h, tol=tol, precision=prec)
         old, tuned = mg.schedule_get(0, prec, 64)
         try:
-            for form in (old.form, 1 - old.form):
+            other = mg.SWEEP_TWO_PASS if old.form != mg.SWEEP_TWO_PASS else mg.SWEEP_FUSED
+            for form in (old.form, other):
                 mg.schedule_set(0, prec, 64, form)
                 ref, _, _ = ctx.solve_fifth_force(d, p, fmg=(prec == "fp64"))
                 got, _, _ = ctx.solve_fifth_force(d, p, fmg=(prec == "fp64"), graph=True)
@@ -441,7 +442,8 @@ def test_graph_recaptured_after_schedule_change(ctx):
     old, _ = mg.schedule_get(0, "mixed", 64)
     outs = [torch.zeros_like(d), torch.zeros_like(d)]   # the same pointers: the cached batch
     try:
-        for form in (old.form, 1 - old.form):
+        other = mg.SWEEP_TWO_PASS if old.form != mg.SWEEP_TWO_PASS else mg.SWEEP_FUSED
+        for form in (old.form, other):
             mg.schedule_set(0, "mixed", 64, form)
             phis, _, _ = ctx.solve_batch([d, d], [p, p], phis=outs)
             ref, _, _ = ctx.solve_fifth_force(d, p)
