@@ -21,11 +21,11 @@
 //
 // The black cells at the tile's edge need the new red values of the ring of positions
 // around the tile; 50 more threads own pairs of ring positions and compute their red
-// cells the same way (red only).  Threads past the tile also bring the planes of e, B
-// and f into a ring of 6 shared-memory slots with bulk asynchronous copies
-// (cp.async.bulk, one per row segment, completion counted on one mbarrier per slot),
-// three plane steps ahead of use.  320 threads and 62 KB of shared memory a CTA: two
-// CTAs per SM, so one CTA's barrier waits overlap the other's work.
+// cells the same way (red only).  All 320 threads bring the planes of e, B and f into a
+// ring of 6 shared-memory slots with 16-byte cp.async copies (two a thread a plane),
+// three plane steps ahead of use; each thread waits for its own copies before the step's
+// barrier.  320 threads and 62 KB of shared memory a CTA: two CTAs per SM, so one CTA's
+// barrier waits overlap the other's work.
 //
 // Every cell is updated by the same arithmetic on the same operands, in the same order,
 // as the gather-based kernels (cell_update_corr_parts), so the result is the same sweep
@@ -37,67 +37,32 @@ namespace mg5 {
 namespace {
 
 constexpr int MT_J = 16, MT_K = 32;           // tile (j, k)
-constexpr int MT_TILE = MT_J * MT_K / 2;      // tile threads: one per column pair
+constexpr int MT_TILE = MT_J * MT_K / 2;      // tile threads: one per position pair
 constexpr int MT_RINGP = (MT_K + 2) + MT_J;   // ring threads: pairs of ring positions (50)
 constexpr int MT_THREADS = 320;               // 256 tile + 50 ring + 14 that only copy
 constexpr int MR = MT_J + 4;                  // plane rows j0-2 .. j0+17
-constexpr int MO = MT_K + 8;                  // plane row: k0-4 .. k0+35 (16-byte aligned)
+constexpr int MO = MT_K + 8;                  // plane row: k0-4 .. k0+35 (16-byte chunks)
 constexpr int MPL = MR * MO;                  // floats of one plane
 constexpr int MNS = 6;                        // plane slots
 constexpr int RNR = MT_J + 2, RNO = MT_K + 2; // new red values: j0-1 .. j0+16, k0-1 .. k0+32
 constexpr int RNP = RNR * RNO;
-constexpr int MT_COPIERS = 3 * MR;            // one thread per copied row (60)
-constexpr unsigned MT_PLANE_BYTES = 3u * MR * MO * 4u;           // e, B, f rows of a plane
-constexpr long long kWaitLimit = 1ll << 26;   // mbarrier polls before giving up
-static_assert(MT_TILE + MT_RINGP <= MT_THREADS && MT_COPIERS <= MT_THREADS - MT_TILE, "roles");
+constexpr int MT_CHUNKS = 3 * MR * (MO / 4);  // 16-byte chunks of one plane of e, B and f
+constexpr int MT_CPT = (MT_CHUNKS + MT_THREADS - 1) / MT_THREADS;   // chunks a thread copies
+static_assert(MT_TILE + MT_RINGP <= MT_THREADS, "roles");
 
 struct MarchSmem {
-    float E[MNS][MPL];
-    float B[MNS][MPL];
-    float F[MNS][MPL];
-    float RN[2][RNP];
-    unsigned long long bar[MNS];
+    float P[3][MNS][MPL];   // e (old values), B, f: plane slots
+    float RN[2][RNP];       // new red values of planes p and p + 1
 };
 
-__device__ __forceinline__ unsigned smem_u32(const void *p)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
-    return (unsigned)__cvta_generic_to_shared(p);
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, P;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// global -> shared bulk copy of `bytes` (multiple of 16, both ends 16-byte aligned)
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
-                                         unsigned long long *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ int wrapn(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
@@ -119,33 +84,32 @@ __device__ __forceinline__ PlaneCol plane_col(const float *base)
     r.c = base[0];
     const float yp = base[MO], ym = base[-MO], zp = base[1], zm = base[-1];
     const float pp = base[MO + 1], pm = base[MO - 1], mp = base[-MO + 1], mm = base[-MO - 1];
-    r.Y = yp + ym;
-    r.Z = zp + zm;
-    r.Dy = yp - ym;
-    r.Dz = zp - zm;
-    r.dyz = (pp - pm) - (mp - mm);
+    r.Y = __fadd_rn(yp, ym);
+    r.Z = __fadd_rn(zp, zm);
+    r.Dy = __fsub_rn(yp, ym);
+    r.Dz = __fsub_rn(zp, zm);
+    r.dyz = __fsub_rn(__fsub_rn(pp, pm), __fsub_rn(mp, mm));
     return r;
 }
 
-__device__ __forceinline__ float2 pr2(float x, float y) { return make_float2(x, y); }
-
-// (e, B) parts of a cell from its face sums and its mixed differences
-__device__ __forceinline__ Parts2 parts_from(float2 sx, float2 sy, float2 sz, float2 dxy,
-                                             float2 dxz, float2 dyz)
+// (e, B) parts of a cell from its face sums and mixed differences, each half in scalar
+// arithmetic (the same roundings as the packed pairs of parts2_of)
+__device__ __forceinline__ Parts2 parts_from(float sxe, float sxb, float sye, float syb, float sze,
+                                             float szb, float dxye, float dxyb, float dxze,
+                                             float dxzb, float dyze, float dyzb)
 {
     Parts2 q;
-    q.S = pk_add(pk_add(sx, sy), sz);
-    q.a = pk_sub(sx, sy);
-    q.b = pk_sub(sx, sz);
-    q.c = pk_sub(sy, sz);
-    q.dxy = dxy;
-    q.dxz = dxz;
-    q.dyz = dyz;
+    q.S = make_float2(__fadd_rn(__fadd_rn(sxe, sye), sze), __fadd_rn(__fadd_rn(sxb, syb), szb));
+    q.a = make_float2(__fsub_rn(sxe, sye), __fsub_rn(sxb, syb));
+    q.b = make_float2(__fsub_rn(sxe, sze), __fsub_rn(sxb, szb));
+    q.c = make_float2(__fsub_rn(sye, sze), __fsub_rn(syb, szb));
+    q.dxy = make_float2(dxye, dxyb);
+    q.dxz = make_float2(dxze, dxzb);
+    q.dyz = make_float2(dyze, dyzb);
     return q;
 }
 
-// A thread's two positions (adjacent cells, so of opposite colours): plane offsets, offsets
-// in the new-red array, and for tile threads the output offset within a plane.
+// A thread's position: its plane offset and its offset in the new-red array.
 struct Pos {
     int off, rn;
 };
@@ -167,57 +131,39 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
     const int tid = threadIdx.x;
     const bool tile = tid < MT_TILE;
     const bool ring = !tile && tid < MT_TILE + MT_RINGP;
-    const int ct = tid - MT_TILE;   // copier index (threads past the tile)
-    bool clamped = false, fault = false;
+    bool clamped = false;
 
-    if (tid == 0) {
-        for (int s = 0; s < MNS; ++s)
-            mbar_init(&S.bar[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // this thread's 16-byte chunks of a plane: shared offset (slot 0) and global offset
+    int soff[MT_CPT];
+    int goff[MT_CPT];
+    const float *gsrc[MT_CPT];
+#pragma unroll
+    for (int m = 0; m < MT_CPT; ++m) {
+        const int c = tid + m * MT_THREADS;
+        gsrc[m] = nullptr;
+        soff[m] = 0;
+        goff[m] = 0;
+        if (c < MT_CHUNKS) {
+            const int a = c / (MR * (MO / 4)), w = c - a * (MR * (MO / 4));
+            const int r = w / (MO / 4), cc = w - r * (MO / 4);
+            gsrc[m] = a == 0 ? in : (a == 1 ? Bg : f);
+            soff[m] = a * (MNS * MPL) + r * MO + cc * 4;
+            goff[m] = wrapn(j0 - 2 + r, n) * n + wrapn(k0 - 4 + cc * 4, n);
+        }
     }
-    __syncthreads();
-
-    // copier threads: row `ct` of e, B or f of plane q into slot s
-    const float *csrc = nullptr;
-    float *cdst0 = nullptr;
-    long long crow = 0;
-    if (ct >= 0 && ct < MT_COPIERS) {
-        const int a = ct / MR, jr = ct - a * MR;
-        csrc = a == 0 ? in : (a == 1 ? Bg : f);
-        cdst0 = (a == 0 ? S.E[0] : (a == 1 ? S.B[0] : S.F[0])) + jr * MO;
-        crow = (long long)wrapn(j0 - 2 + jr, n) * n;
-    }
-    const bool kwrap = !(k0 > 0 && k0 + MT_K < n);
-    const int kl = k0 > 0 ? k0 - 4 : n - 4, kr = k0 + MT_K < n ? k0 + MT_K : 0;
+    float *sbase = &S.P[0][0][0];
     auto issue_plane = [&](int q, int s) {
-        if (ct == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive_expect_tx(&S.bar[s], MT_PLANE_BYTES);
-        }
-        if (csrc) {
-            const float *row = csrc + (long long)wrapn(q, n) * n2 + crow;
-            float *dst = cdst0 + s * MPL;
-            if (!kwrap) {
-                bulk_g2s(dst, row + k0 - 4, MO * 4, &S.bar[s]);
-            } else {
-                bulk_g2s(dst, row + kl, 16, &S.bar[s]);
-                bulk_g2s(dst + 4, row + k0, MT_K * 4, &S.bar[s]);
-                bulk_g2s(dst + 4 + MT_K, row + kr, 16, &S.bar[s]);
-            }
-        }
+        const long long pb = (long long)wrapn(q, n) * n2;
+#pragma unroll
+        for (int m = 0; m < MT_CPT; ++m)
+            if (gsrc[m])
+                cp_async16(sbase + soff[m] + s * MPL, gsrc[m] + pb + goff[m]);
     };
-    auto wait_slot = [&](int s, unsigned par) {
-        long long it = 0;
-        while (!mbar_try_wait(&S.bar[s], par)) {
-            if (++it > kWaitLimit) {   // never expected: record it and go on
-                fault = true;
-                break;
-            }
-        }
-    };
-    if (ct >= 0)
-        for (int q = q0; q < q0 + MNS && q <= last; ++q)
+    for (int q = q0; q < q0 + MNS; ++q) {
+        if (q <= last)
             issue_plane(q, q - q0);
+        cp_async_commit();
+    }
 
     // the thread's two positions (j, k global; A and B adjacent)
     int jA, kA, jB, kB;
@@ -249,117 +195,114 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
     // step p relaxes the position with (p + 1 + j + k) even: A on steps of one parity
     const bool a_even = ((q0 + 1 + jA + kA) & 1) == 0;   // A active on steps q0, q0 + 2, ...
     const Pos p0 = a_even ? pA : pB, p1 = a_even ? pB : pA;
-    const bool first0 = a_even ? (kA < kB || jA < jB) : (kB < kA || jB < jA);
+    const bool first0 = a_even;   // tile pairs: A is the pair's first (lower k) cell
     float *orow = out + (long long)(tile ? jA : j0) * n + (tile ? kA : k0);
     ColCache c0{}, c1{};
     float rprev = 0.0f;   // red value of the step before (its plane's red cell)
+    const float *E = S.P[0][0], *Bs = S.P[1][0], *F = S.P[2][0];
 
     // One step p with slots s0 (plane p), s1 (p + 1), s2 (p + 2) and the active position's
     // cache.  warm: a step before the chunk (no black cell, no output; plane p's values are
     // read here instead of two steps earlier).
     auto step = [&](int p, int s0, int s1, int s2, const Pos &ps, bool pfirst, ColCache &cc,
                     bool warm) {
-        if (tile || ring) {
-            const int off = ps.off;
-            if (warm) {
-                const PlaneCol e0 = plane_col(S.E[s0] + off), b0 = plane_col(S.B[s0] + off);
-                cc.cE0 = e0.c;
-                cc.DyE0 = e0.Dy;
-                cc.DzE0 = e0.Dz;
-                cc.dyzE0 = e0.dyz;
-                cc.cB0 = b0.c;
-                cc.DyB0 = b0.Dy;
-                cc.DzB0 = b0.Dz;
-                cc.dyzB0 = b0.dyz;
-                cc.YB0 = b0.Y;
-                cc.ZB0 = b0.Z;
-            }
-            const PlaneCol e2 = plane_col(S.E[s2] + off), b2 = plane_col(S.B[s2] + off);
-            const PlaneCol e1 = plane_col(S.E[s1] + off), b1 = plane_col(S.B[s1] + off);
-            // red cell (p + 1) of the position: old values throughout
-            const Parts2 qr = parts_from(pk_add(pr2(e2.c, b2.c), pr2(cc.cE0, cc.cB0)),
-                                         pr2(e1.Y, b1.Y), pr2(e1.Z, b1.Z),
-                                         pk_sub(pr2(e2.Dy, b2.Dy), pr2(cc.DyE0, cc.DyB0)),
-                                         pk_sub(pr2(e2.Dz, b2.Dz), pr2(cc.DzE0, cc.DzB0)),
-                                         pr2(e1.dyz, b1.dyz));
-            const float r1 = cell_update_corr_parts(qr, b1.c, e1.c, S.F[s1][off] + cval, cf, clamped);
-            S.RN[(p + 1) & 1][ps.rn] = r1;
-            if (tile && !warm) {
-                // black cell (p) of the position: new red faces, old edges
-                const float *rn = S.RN[p & 1] + ps.rn;
-                const float sye = rn[RNO] + rn[-RNO], sze = rn[1] + rn[-1];
-                const Parts2 qb = parts_from(pk_add(pr2(r1, b1.c), pr2(cc.rm, cc.cBm)),
-                                             pr2(sye, cc.YB0), pr2(sze, cc.ZB0),
-                                             pk_sub(pr2(e1.Dy, b1.Dy), pr2(cc.DyEm, cc.DyBm)),
-                                             pk_sub(pr2(e1.Dz, b1.Dz), pr2(cc.DzEm, cc.DzBm)),
-                                             pr2(cc.dyzE0, cc.dyzB0));
-                const float b0v = cell_update_corr_parts(qb, cc.cB0, cc.cE0, S.F[s0][off] + cval,
-                                                         cf, clamped);
-                float2 v;
-                v.x = pfirst ? b0v : rprev;
-                v.y = pfirst ? rprev : b0v;
-                *reinterpret_cast<float2 *>(orow + (long long)p * n2) = v;
-            }
-            // keep plane p + 2 as the position's plane p, plane p + 1 as its plane p - 1
-            cc.cE0 = e2.c;
-            cc.DyE0 = e2.Dy;
-            cc.DzE0 = e2.Dz;
-            cc.dyzE0 = e2.dyz;
-            cc.cB0 = b2.c;
-            cc.DyB0 = b2.Dy;
-            cc.DzB0 = b2.Dz;
-            cc.dyzB0 = b2.dyz;
-            cc.YB0 = b2.Y;
-            cc.ZB0 = b2.Z;
-            cc.DyEm = e1.Dy;
-            cc.DzEm = e1.Dz;
-            cc.DyBm = b1.Dy;
-            cc.DzBm = b1.Dz;
-            cc.cBm = b1.c;
-            cc.rm = r1;
-            rprev = r1;
+        if (!(tile || ring))
+            return;
+        const int o0 = s0 * MPL + ps.off, o1 = s1 * MPL + ps.off, o2 = s2 * MPL + ps.off;
+        if (warm) {
+            const PlaneCol e0 = plane_col(E + o0), b0 = plane_col(Bs + o0);
+            cc.cE0 = e0.c;
+            cc.DyE0 = e0.Dy;
+            cc.DzE0 = e0.Dz;
+            cc.dyzE0 = e0.dyz;
+            cc.cB0 = b0.c;
+            cc.DyB0 = b0.Dy;
+            cc.DzB0 = b0.Dz;
+            cc.dyzB0 = b0.dyz;
+            cc.YB0 = b0.Y;
+            cc.ZB0 = b0.Z;
         }
+        const PlaneCol e2 = plane_col(E + o2), b2 = plane_col(Bs + o2);
+        const PlaneCol e1 = plane_col(E + o1), b1 = plane_col(Bs + o1);
+        // red cell (p + 1) of the position: old values throughout (x faces: planes p + 2, p)
+        const Parts2 qr =
+            parts_from(__fadd_rn(e2.c, cc.cE0), __fadd_rn(b2.c, cc.cB0), e1.Y, b1.Y, e1.Z, b1.Z,
+                       __fsub_rn(e2.Dy, cc.DyE0), __fsub_rn(b2.Dy, cc.DyB0),
+                       __fsub_rn(e2.Dz, cc.DzE0), __fsub_rn(b2.Dz, cc.DzB0), e1.dyz, b1.dyz);
+        const float r1 = cell_update_corr_parts(qr, b1.c, e1.c, F[o1] + cval, cf, clamped);
+        S.RN[(p + 1) & 1][ps.rn] = r1;
+        if (tile && !warm) {
+            // black cell (p) of the position: new red faces, old edges
+            const float *rn = S.RN[p & 1] + ps.rn;
+            const float sye = __fadd_rn(rn[RNO], rn[-RNO]), sze = __fadd_rn(rn[1], rn[-1]);
+            const Parts2 qb = parts_from(__fadd_rn(r1, cc.rm), __fadd_rn(b1.c, cc.cBm), sye,
+                                         cc.YB0, sze, cc.ZB0, __fsub_rn(e1.Dy, cc.DyEm),
+                                         __fsub_rn(b1.Dy, cc.DyBm), __fsub_rn(e1.Dz, cc.DzEm),
+                                         __fsub_rn(b1.Dz, cc.DzBm), cc.dyzE0, cc.dyzB0);
+            const float b0v = cell_update_corr_parts(qb, cc.cB0, cc.cE0, F[o0] + cval, cf, clamped);
+            float2 v;
+            v.x = pfirst ? b0v : rprev;
+            v.y = pfirst ? rprev : b0v;
+            *reinterpret_cast<float2 *>(orow + (long long)p * n2) = v;
+        }
+        // keep plane p + 2 as the position's plane p, plane p + 1 as its plane p - 1
+        cc.cE0 = e2.c;
+        cc.DyE0 = e2.Dy;
+        cc.DzE0 = e2.Dz;
+        cc.dyzE0 = e2.dyz;
+        cc.cB0 = b2.c;
+        cc.DyB0 = b2.Dy;
+        cc.DzB0 = b2.Dz;
+        cc.dyzB0 = b2.dyz;
+        cc.YB0 = b2.Y;
+        cc.ZB0 = b2.Z;
+        cc.DyEm = e1.Dy;
+        cc.DzEm = e1.Dz;
+        cc.DyBm = b1.Dy;
+        cc.DzBm = b1.Dz;
+        cc.cBm = b1.c;
+        cc.rm = r1;
+        rprev = r1;
     };
 
-    // slots and mbarrier phases of planes p, p + 1, p + 2, kept incrementally
+    // slots of planes p, p + 1, p + 2, kept incrementally
     int s0 = 0, s1 = 1, s2 = 2;
-    unsigned ph2 = 0;   // phase parity of slot s2's current plane
     auto advance = [&]() {
         s0 = s1;
         s1 = s2;
         s2 = s2 == MNS - 1 ? 0 : s2 + 1;
-        if (s2 == 0)
-            ph2 ^= 1u;
     };
-    // warm-up: steps q0 and q0 + 1 compute the red cells of planes i0 - 1 and i0
-    wait_slot(0, 0);
-    wait_slot(1, 0);
-    wait_slot(2, 0);
+    // Every step commits one copy group (plane p + 5, or none), then waits until at most two
+    // groups are pending: the plane the next step reads last has landed (for this thread's
+    // chunks; the barrier that follows makes every thread's chunks visible).
+    cp_async_wait<3>();   // planes q0 .. q0 + 2
+    __syncthreads();
     step(q0, s0, s1, s2, p0, first0, c0, true);
+    cp_async_commit();    // (plane q0 + 5 went in with the prologue)
+    cp_async_wait<2>();
     __syncthreads();
     advance();
-    wait_slot(s2, ph2);
     step(q0 + 1, s0, s1, s2, p1, !first0, c1, true);
-    __syncthreads();
-    // plane p - 1's slot is free after step p: plane p + 5 goes there (3 steps before use)
-    if (ct >= 0 && q0 + 6 <= last)
+    // plane p - 1's slot is free during step p: plane p + 5 goes there (3 steps before use)
+    if (q0 + 6 <= last)
         issue_plane(q0 + 6, 0);
-    int p = i0;
-    for (; p < i1; ++p) {
+    cp_async_commit();
+    cp_async_wait<2>();
+    __syncthreads();
+    for (int p = i0; p < i1; ++p) {
         advance();
-        wait_slot(s2, ph2);
         if (((p - i0) & 1) == 0)
             step(p, s0, s1, s2, p0, first0, c0, false);
         else
             step(p, s0, s1, s2, p1, !first0, c1, false);
-        __syncthreads();
-        if (ct >= 0 && p + 5 <= last)
+        if (p + 5 <= last)
             issue_plane(p + 5, s0 == 0 ? MNS - 1 : s0 - 1);
+        cp_async_commit();
+        cp_async_wait<2>();
+        __syncthreads();
     }
     if (clamped)
         atomicAdd(clamp, 1ull);
-    if (fault)
-        atomicOr(clamp, kSweepFaultBit);
 }
 
 }  // namespace

@@ -396,9 +396,11 @@ __device__ __forceinline__ Parts2 parts2_of(const St<float> &e, const St<float> 
 // fused, column march) computes the same sweep to the bit.
 __device__ __forceinline__ float sigma_corr(const Parts2 &q, const CoefT<float> &cf)
 {
-    const auto t = [](float2 v) { return __fmul_rn(v.x, __fmaf_rn(2.0f, v.y, v.x)); };
-    const float X = __fadd_rn(__fadd_rn(t(q.a), t(q.b)), t(q.c));
-    const float Y = __fadd_rn(__fadd_rn(t(q.dxy), t(q.dxz)), t(q.dyz));
+    // sum_t e_t (2 B_t + e_t) as a chain of multiply-adds
+    const auto u = [](float2 v) { return __fmaf_rn(2.0f, v.y, v.x); };
+    const float X = __fmaf_rn(q.a.x, u(q.a), __fmaf_rn(q.b.x, u(q.b), __fmul_rn(q.c.x, u(q.c))));
+    const float Y =
+        __fmaf_rn(q.dxy.x, u(q.dxy), __fmaf_rn(q.dxz.x, u(q.dxz), __fmul_rn(q.dyz.x, u(q.dyz))));
     return __fmaf_rn(cf.s3, X, __fmul_rn(cf.s8, Y));
 }
 
