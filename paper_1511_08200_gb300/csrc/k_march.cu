@@ -289,17 +289,28 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
     cp_async_commit();
     cp_async_wait<2>();
     __syncthreads();
-    for (int p = i0; p < i1; ++p) {
-        advance();
-        if (((p - i0) & 1) == 0)
-            step(p, s0, s1, s2, p0, first0, c0, false);
-        else
-            step(p, s0, s1, s2, p1, !first0, c1, false);
+    // steps i0, i0 + 2, ... use position set 0, the others set 1 (unrolled by two so that
+    // each set's cache stays in the same registers)
+    auto tail_of_step = [&](int p) {
         if (p + 5 <= last)
             issue_plane(p + 5, s0 == 0 ? MNS - 1 : s0 - 1);
         cp_async_commit();
         cp_async_wait<2>();
         __syncthreads();
+    };
+    int p = i0;
+    for (; p + 1 < i1; p += 2) {
+        advance();
+        step(p, s0, s1, s2, p0, first0, c0, false);
+        tail_of_step(p);
+        advance();
+        step(p + 1, s0, s1, s2, p1, !first0, c1, false);
+        tail_of_step(p + 1);
+    }
+    if (p < i1) {
+        advance();
+        step(p, s0, s1, s2, p0, first0, c0, false);
+        tail_of_step(p);
     }
     if (clamped)
         atomicAdd(clamp, 1ull);

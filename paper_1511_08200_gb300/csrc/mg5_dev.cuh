@@ -411,16 +411,16 @@ __device__ __forceinline__ float cell_update_corr_parts(const Parts2 &q, float B
     const float bp = __fmaf_rn(cf.k43h, __fmaf_rn(-6.0f, Bc, q.S.y), 1.0f);   // beta' = 1 + (4 alpha/3) L_B
     const float bq = __fadd_rn(rhs, sigma_corr(q, cf));                        // b'
     float disc = __fmaf_rn(bp, bp, __fmul_rn(cf.k8, bq));
-    if (disc < 0.0f) {
-        disc = 0.0f;
-        clamped = true;
-    }
+    clamped = clamped || disc < 0.0f;
+    disc = fmaxf(disc, 0.0f);
+    // both root forms evaluated and one selected: no branch
     const float sq = disc > 0.0f ? __fmul_rn(disc, rsqrtf(disc)) : 0.0f;
-    const float L = bp >= 0.0f ? __fdividef(__fmul_rn(2.0f, bq), __fadd_rn(bp, sq))
-                               : __fmul_rn(__fsub_rn(sq, bp), cf.inv2k23);
+    const float Lp = __fdividef(__fmul_rn(2.0f, bq), __fadd_rn(bp, sq));
+    const float Lm = __fmul_rn(__fsub_rn(sq, bp), cf.inv2k23);
+    const float L = bp >= 0.0f ? Lp : Lm;
     const float r6 = __fmaf_rn(-cf.h2, L, q.S.x);
-    return cf.om1 != 0.0f ? __fmaf_rn(cf.w6, r6, __fmul_rn(cf.omc, ec))
-                          : __fmul_rn(r6, 1.0f / 6.0f);
+    // (omega / 6) r6 + (1 - omega) e_c; for omega = 1 it is r6 / 6 rounded once
+    return __fmaf_rn(cf.w6, r6, __fmul_rn(cf.omc, ec));
 }
 
 __device__ __forceinline__ float cell_update_corr(const St<float> &e, const St<float> &B, float rhs,
