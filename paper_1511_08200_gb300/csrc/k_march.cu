@@ -30,6 +30,8 @@
 // Every cell is updated by the same arithmetic on the same operands, in the same order,
 // as the gather-based kernels (cell_update_corr_parts), so the result is the same sweep
 // to the bit.  Periodic in i, j, k; n a multiple of 32; out of place.
+#include <type_traits>
+
 #include "mg5_kernels.cuh"
 
 namespace mg5 {
@@ -55,11 +57,6 @@ struct MarchSmem {
     float RN[2][RNP];       // new red values of planes p and p + 1
 };
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -114,6 +111,9 @@ struct Pos {
     int off, rn;
 };
 
+template <int V>
+using IC = std::integral_constant<int, V>;
+
 __global__ void __launch_bounds__(MT_THREADS, 2)
     k_sweep_march(const float *__restrict__ in, float *__restrict__ out, const float *__restrict__ f,
                   const float *__restrict__ Bg, const double *__restrict__ cptr, int n, int ichunk,
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
     const int k0 = blockIdx.x * MT_K, j0 = blockIdx.y * MT_J;
     const int i0 = blockIdx.z * ichunk;
     const int i1 = min(i0 + ichunk, n);
-    const int q0 = i0 - 2;        // first plane brought in; plane q lives in slot (q - q0) % MNS
+    const int q0 = i0 - 2;        // first plane brought in; plane q lives in slot (q - q0) % 6
     const int last = i1 + 1;      // the last plane any step reads
     const float cval = (float)(*cptr);
     const long long n2 = (long long)n * n;
@@ -133,35 +133,48 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
     const bool ring = !tile && tid < MT_TILE + MT_RINGP;
     bool clamped = false;
 
-    // this thread's 16-byte chunks of a plane: shared offset (slot 0) and global offset
-    int soff[MT_CPT];
-    int goff[MT_CPT];
-    const float *gsrc[MT_CPT];
+    // This thread's 16-byte chunks of a plane: the shared address in slot 0 and a global
+    // pointer into the next plane to bring in (advanced one plane per copy, wrapped at n).
+    unsigned sdst[MT_CPT];
+    const float *gp[MT_CPT];
+    bool has[MT_CPT];
 #pragma unroll
     for (int m = 0; m < MT_CPT; ++m) {
         const int c = tid + m * MT_THREADS;
-        gsrc[m] = nullptr;
-        soff[m] = 0;
-        goff[m] = 0;
-        if (c < MT_CHUNKS) {
-            const int a = c / (MR * (MO / 4)), w = c - a * (MR * (MO / 4));
-            const int r = w / (MO / 4), cc = w - r * (MO / 4);
-            gsrc[m] = a == 0 ? in : (a == 1 ? Bg : f);
-            soff[m] = a * (MNS * MPL) + r * MO + cc * 4;
-            goff[m] = wrapn(j0 - 2 + r, n) * n + wrapn(k0 - 4 + cc * 4, n);
-        }
+        has[m] = c < MT_CHUNKS;
+        const int cm = has[m] ? c : 0;
+        const int a = cm / (MR * (MO / 4)), w = cm - a * (MR * (MO / 4));
+        const int r = w / (MO / 4), cc = w - r * (MO / 4);
+        const float *src = a == 0 ? in : (a == 1 ? Bg : f);
+        sdst[m] = (unsigned)__cvta_generic_to_shared(&S.P[a][0][r * MO + cc * 4]);
+        gp[m] = src + (long long)wrapn(q0, n) * n2 + (long long)wrapn(j0 - 2 + r, n) * n +
+                wrapn(k0 - 4 + cc * 4, n);
     }
-    float *sbase = &S.P[0][0][0];
-    auto issue_plane = [&](int q, int s) {
-        const long long pb = (long long)wrapn(q, n) * n2;
+    int qn = wrapn(q0, n);   // wrapped index of the next plane to bring in
+    auto issue_next = [&](int s) {
 #pragma unroll
         for (int m = 0; m < MT_CPT; ++m)
-            if (gsrc[m])
-                cp_async16(sbase + soff[m] + s * MPL, gsrc[m] + pb + goff[m]);
+            if (has[m])
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                                 sdst[m] + (unsigned)(s * MPL * 4)),
+                             "l"(gp[m])
+                             : "memory");
+        if (++qn == n) {
+            qn = 0;
+#pragma unroll
+            for (int m = 0; m < MT_CPT; ++m)
+                gp[m] += n2 - (long long)n * n2;
+        } else {
+#pragma unroll
+            for (int m = 0; m < MT_CPT; ++m)
+                gp[m] += n2;
+        }
     };
-    for (int q = q0; q < q0 + MNS; ++q) {
-        if (q <= last)
-            issue_plane(q, q - q0);
+    // planes q0 .. q0 + 4 now; every step then brings in plane p + 5 (three steps ahead)
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        if (q0 + s <= last)
+            issue_next(s);
         cp_async_commit();
     }
 
@@ -194,123 +207,134 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
     const Pos pB{(jB - j0 + 2) * MO + (kB - k0 + 4), (jB - j0 + 1) * RNO + (kB - k0 + 1)};
     // step p relaxes the position with (p + 1 + j + k) even: A on steps of one parity
     const bool a_even = ((q0 + 1 + jA + kA) & 1) == 0;   // A active on steps q0, q0 + 2, ...
-    const Pos p0 = a_even ? pA : pB, p1 = a_even ? pB : pA;
-    const bool first0 = a_even;   // tile pairs: A is the pair's first (lower k) cell
-    float *orow = out + (long long)(tile ? jA : j0) * n + (tile ? kA : k0);
-    ColCache c0{}, c1{};
+    const Pos pos[2] = {a_even ? pA : pB, a_even ? pB : pA};
+    const bool first[2] = {a_even, !a_even};   // tile pairs: A is the pair's first cell
+    float *optr = out + (long long)i0 * n2 + (long long)(tile ? jA : j0) * n + (tile ? kA : k0);
+    ColCache cc[2] = {};
     float rprev = 0.0f;   // red value of the step before (its plane's red cell)
     const float *E = S.P[0][0], *Bs = S.P[1][0], *F = S.P[2][0];
 
-    // One step p with slots s0 (plane p), s1 (p + 1), s2 (p + 2) and the active position's
-    // cache.  warm: a step before the chunk (no black cell, no output; plane p's values are
+    // One step p: planes p, p + 1, p + 2 in slots S0, S0 + 1, S0 + 2 (mod 6), position set
+    // SET.  warm: a step before the chunk (no black cell, no output; plane p's values are
     // read here instead of two steps earlier).
-    auto step = [&](int p, int s0, int s1, int s2, const Pos &ps, bool pfirst, ColCache &cc,
-                    bool warm) {
-        if (!(tile || ring))
-            return;
-        const int o0 = s0 * MPL + ps.off, o1 = s1 * MPL + ps.off, o2 = s2 * MPL + ps.off;
-        if (warm) {
-            const PlaneCol e0 = plane_col(E + o0), b0 = plane_col(Bs + o0);
-            cc.cE0 = e0.c;
-            cc.DyE0 = e0.Dy;
-            cc.DzE0 = e0.Dz;
-            cc.dyzE0 = e0.dyz;
-            cc.cB0 = b0.c;
-            cc.DyB0 = b0.Dy;
-            cc.DzB0 = b0.Dz;
-            cc.dyzB0 = b0.dyz;
-            cc.YB0 = b0.Y;
-            cc.ZB0 = b0.Z;
+    auto step = [&](auto S0c, auto SETc, bool warm) {
+        constexpr int s0 = decltype(S0c)::value, set = decltype(SETc)::value;
+        constexpr int s1 = (s0 + 1) % MNS, s2 = (s0 + 2) % MNS;
+        if (tile || ring) {
+            ColCache &c = cc[set];
+            const Pos ps = pos[set];
+            const float *E0 = E + s0 * MPL + ps.off, *E1 = E + s1 * MPL + ps.off,
+                        *E2 = E + s2 * MPL + ps.off;
+            const float *B0 = Bs + s0 * MPL + ps.off, *B1 = Bs + s1 * MPL + ps.off,
+                        *B2 = Bs + s2 * MPL + ps.off;
+            if (warm) {
+                const PlaneCol e0 = plane_col(E0), b0 = plane_col(B0);
+                c.cE0 = e0.c;
+                c.DyE0 = e0.Dy;
+                c.DzE0 = e0.Dz;
+                c.dyzE0 = e0.dyz;
+                c.cB0 = b0.c;
+                c.DyB0 = b0.Dy;
+                c.DzB0 = b0.Dz;
+                c.dyzB0 = b0.dyz;
+                c.YB0 = b0.Y;
+                c.ZB0 = b0.Z;
+            }
+            const PlaneCol e2 = plane_col(E2), b2 = plane_col(B2);
+            const PlaneCol e1 = plane_col(E1), b1 = plane_col(B1);
+            // red cell (p + 1) of the position: old values throughout (x faces: p + 2, p)
+            const Parts2 qr =
+                parts_from(__fadd_rn(e2.c, c.cE0), __fadd_rn(b2.c, c.cB0), e1.Y, b1.Y, e1.Z, b1.Z,
+                           __fsub_rn(e2.Dy, c.DyE0), __fsub_rn(b2.Dy, c.DyB0),
+                           __fsub_rn(e2.Dz, c.DzE0), __fsub_rn(b2.Dz, c.DzB0), e1.dyz, b1.dyz);
+            const float r1 = cell_update_corr_parts(qr, b1.c, e1.c, F[s1 * MPL + ps.off] + cval, cf,
+                                                    clamped);
+            S.RN[(set + 1) & 1][ps.rn] = r1;   // plane p + 1 (p - i0 has the parity of set)
+            if (tile && !warm) {
+                // black cell (p) of the position: new red faces, old edges
+                const float *rn = S.RN[set & 1] + ps.rn;
+                const float sye = __fadd_rn(rn[RNO], rn[-RNO]), sze = __fadd_rn(rn[1], rn[-1]);
+                const Parts2 qb = parts_from(__fadd_rn(r1, c.rm), __fadd_rn(b1.c, c.cBm), sye,
+                                             c.YB0, sze, c.ZB0, __fsub_rn(e1.Dy, c.DyEm),
+                                             __fsub_rn(b1.Dy, c.DyBm), __fsub_rn(e1.Dz, c.DzEm),
+                                             __fsub_rn(b1.Dz, c.DzBm), c.dyzE0, c.dyzB0);
+                const float b0v = cell_update_corr_parts(qb, c.cB0, c.cE0,
+                                                         F[s0 * MPL + ps.off] + cval, cf, clamped);
+                float2 v;
+                v.x = first[set] ? b0v : rprev;
+                v.y = first[set] ? rprev : b0v;
+                *reinterpret_cast<float2 *>(optr) = v;
+            }
+            // keep plane p + 2 as the position's plane p, plane p + 1 as its plane p - 1
+            c.cE0 = e2.c;
+            c.DyE0 = e2.Dy;
+            c.DzE0 = e2.Dz;
+            c.dyzE0 = e2.dyz;
+            c.cB0 = b2.c;
+            c.DyB0 = b2.Dy;
+            c.DzB0 = b2.Dz;
+            c.dyzB0 = b2.dyz;
+            c.YB0 = b2.Y;
+            c.ZB0 = b2.Z;
+            c.DyEm = e1.Dy;
+            c.DzEm = e1.Dz;
+            c.DyBm = b1.Dy;
+            c.DzBm = b1.Dz;
+            c.cBm = b1.c;
+            c.rm = r1;
+            rprev = r1;
         }
-        const PlaneCol e2 = plane_col(E + o2), b2 = plane_col(Bs + o2);
-        const PlaneCol e1 = plane_col(E + o1), b1 = plane_col(Bs + o1);
-        // red cell (p + 1) of the position: old values throughout (x faces: planes p + 2, p)
-        const Parts2 qr =
-            parts_from(__fadd_rn(e2.c, cc.cE0), __fadd_rn(b2.c, cc.cB0), e1.Y, b1.Y, e1.Z, b1.Z,
-                       __fsub_rn(e2.Dy, cc.DyE0), __fsub_rn(b2.Dy, cc.DyB0),
-                       __fsub_rn(e2.Dz, cc.DzE0), __fsub_rn(b2.Dz, cc.DzB0), e1.dyz, b1.dyz);
-        const float r1 = cell_update_corr_parts(qr, b1.c, e1.c, F[o1] + cval, cf, clamped);
-        S.RN[(p + 1) & 1][ps.rn] = r1;
-        if (tile && !warm) {
-            // black cell (p) of the position: new red faces, old edges
-            const float *rn = S.RN[p & 1] + ps.rn;
-            const float sye = __fadd_rn(rn[RNO], rn[-RNO]), sze = __fadd_rn(rn[1], rn[-1]);
-            const Parts2 qb = parts_from(__fadd_rn(r1, cc.rm), __fadd_rn(b1.c, cc.cBm), sye,
-                                         cc.YB0, sze, cc.ZB0, __fsub_rn(e1.Dy, cc.DyEm),
-                                         __fsub_rn(b1.Dy, cc.DyBm), __fsub_rn(e1.Dz, cc.DzEm),
-                                         __fsub_rn(b1.Dz, cc.DzBm), cc.dyzE0, cc.dyzB0);
-            const float b0v = cell_update_corr_parts(qb, cc.cB0, cc.cE0, F[o0] + cval, cf, clamped);
-            float2 v;
-            v.x = pfirst ? b0v : rprev;
-            v.y = pfirst ? rprev : b0v;
-            *reinterpret_cast<float2 *>(orow + (long long)p * n2) = v;
-        }
-        // keep plane p + 2 as the position's plane p, plane p + 1 as its plane p - 1
-        cc.cE0 = e2.c;
-        cc.DyE0 = e2.Dy;
-        cc.DzE0 = e2.Dz;
-        cc.dyzE0 = e2.dyz;
-        cc.cB0 = b2.c;
-        cc.DyB0 = b2.Dy;
-        cc.DzB0 = b2.Dz;
-        cc.dyzB0 = b2.dyz;
-        cc.YB0 = b2.Y;
-        cc.ZB0 = b2.Z;
-        cc.DyEm = e1.Dy;
-        cc.DzEm = e1.Dz;
-        cc.DyBm = b1.Dy;
-        cc.DzBm = b1.Dz;
-        cc.cBm = b1.c;
-        cc.rm = r1;
-        rprev = r1;
     };
-
-    // slots of planes p, p + 1, p + 2, kept incrementally
-    int s0 = 0, s1 = 1, s2 = 2;
-    auto advance = [&]() {
-        s0 = s1;
-        s1 = s2;
-        s2 = s2 == MNS - 1 ? 0 : s2 + 1;
-    };
-    // Every step commits one copy group (plane p + 5, or none), then waits until at most two
-    // groups are pending: the plane the next step reads last has landed (for this thread's
-    // chunks; the barrier that follows makes every thread's chunks visible).
-    cp_async_wait<3>();   // planes q0 .. q0 + 2
-    __syncthreads();
-    step(q0, s0, s1, s2, p0, first0, c0, true);
-    cp_async_commit();    // (plane q0 + 5 went in with the prologue)
-    cp_async_wait<2>();
-    __syncthreads();
-    advance();
-    step(q0 + 1, s0, s1, s2, p1, !first0, c1, true);
-    // plane p - 1's slot is free during step p: plane p + 5 goes there (3 steps before use)
-    if (q0 + 6 <= last)
-        issue_plane(q0 + 6, 0);
-    cp_async_commit();
-    cp_async_wait<2>();
-    __syncthreads();
-    // steps i0, i0 + 2, ... use position set 0, the others set 1 (unrolled by two so that
-    // each set's cache stays in the same registers)
-    auto tail_of_step = [&](int p) {
+    // after step p: bring in plane p + 5 (into plane p - 1's slot, free during step p), then
+    // wait until at most two copy groups are pending: the plane the next step reads last has
+    // landed (this thread's chunks; the barrier makes every thread's chunks visible)
+    auto finish = [&](auto S0c, int p) {
+        constexpr int s0 = decltype(S0c)::value;
         if (p + 5 <= last)
-            issue_plane(p + 5, s0 == 0 ? MNS - 1 : s0 - 1);
+            issue_next((s0 + 5) % MNS);
         cp_async_commit();
         cp_async_wait<2>();
         __syncthreads();
     };
-    int p = i0;
-    for (; p + 1 < i1; p += 2) {
-        advance();
-        step(p, s0, s1, s2, p0, first0, c0, false);
-        tail_of_step(p);
-        advance();
-        step(p + 1, s0, s1, s2, p1, !first0, c1, false);
-        tail_of_step(p + 1);
-    }
-    if (p < i1) {
-        advance();
-        step(p, s0, s1, s2, p0, first0, c0, false);
-        tail_of_step(p);
+    cp_async_wait<2>();   // planes q0 .. q0 + 2
+    __syncthreads();
+    // warm-up: the red cells of planes i0 - 1 and i0
+    step(IC<0>{}, IC<0>{}, true);
+    finish(IC<0>{}, q0);
+    step(IC<1>{}, IC<1>{}, true);
+    finish(IC<1>{}, q0 + 1);
+    // plane p's slot is (p - q0) % 6: steps i0, i0 + 1, ... use slots 2, 3, 4, 5, 0, 1 and
+    // position sets 0, 1, 0, 1, 0, 1 (unrolled by six: every slot offset is a constant)
+    for (int p = i0; p < i1;) {
+        step(IC<2>{}, IC<0>{}, false);
+        finish(IC<2>{}, p);
+        optr += n2;
+        if (++p >= i1)
+            break;
+        step(IC<3>{}, IC<1>{}, false);
+        finish(IC<3>{}, p);
+        optr += n2;
+        if (++p >= i1)
+            break;
+        step(IC<4>{}, IC<0>{}, false);
+        finish(IC<4>{}, p);
+        optr += n2;
+        if (++p >= i1)
+            break;
+        step(IC<5>{}, IC<1>{}, false);
+        finish(IC<5>{}, p);
+        optr += n2;
+        if (++p >= i1)
+            break;
+        step(IC<0>{}, IC<0>{}, false);
+        finish(IC<0>{}, p);
+        optr += n2;
+        if (++p >= i1)
+            break;
+        step(IC<1>{}, IC<1>{}, false);
+        finish(IC<1>{}, p);
+        optr += n2;
+        ++p;
     }
     if (clamped)
         atomicAdd(clamp, 1ull);
