@@ -24,7 +24,7 @@
 // cells the same way (red only).  All 320 threads bring the planes of e, B and f into a
 // ring of 6 shared-memory slots with 16-byte cp.async copies (two a thread a plane),
 // three plane steps ahead of use; each thread waits for its own copies before the step's
-// barrier.  320 threads and 62 KB of shared memory a CTA: two CTAs per SM, so one CTA's
+// barrier.  320 threads and 67 KB of shared memory a CTA: two CTAs per SM, so one CTA's
 // barrier waits overlap the other's work.
 //
 // Every cell is updated by the same arithmetic on the same operands, in the same order,
@@ -43,12 +43,15 @@ constexpr int MT_TILE = MT_J * MT_K / 2;      // tile threads: one per position 
 constexpr int MT_RINGP = (MT_K + 2) + MT_J;   // ring threads: pairs of ring positions (50)
 constexpr int MT_THREADS = 320;               // 256 tile + 50 ring + 14 that only copy
 constexpr int MR = MT_J + 4;                  // plane rows j0-2 .. j0+17
-constexpr int MO = MT_K + 8;                  // plane row: k0-4 .. k0+35 (16-byte chunks)
+constexpr int MW = MT_K + 8;                  // copied row: k0-4 .. k0+35 (16-byte chunks)
+constexpr int MO = MW + 4;                    // row stride: 4 floats of padding, so that the
+                                              // ring's column cells (rows 2 apart) spread over
+                                              // 4 banks instead of 2
 constexpr int MPL = MR * MO;                  // floats of one plane
 constexpr int MNS = 6;                        // plane slots
 constexpr int RNR = MT_J + 2, RNO = MT_K + 2; // new red values: j0-1 .. j0+16, k0-1 .. k0+32
 constexpr int RNP = RNR * RNO;
-constexpr int MT_CHUNKS = 3 * MR * (MO / 4);  // 16-byte chunks of one plane of e, B and f
+constexpr int MT_CHUNKS = 3 * MR * (MW / 4);  // 16-byte chunks of one plane of e, B and f
 constexpr int MT_CPT = (MT_CHUNKS + MT_THREADS - 1) / MT_THREADS;   // chunks a thread copies
 static_assert(MT_TILE + MT_RINGP <= MT_THREADS, "roles");
 
@@ -143,8 +146,8 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
         const int c = tid + m * MT_THREADS;
         has[m] = c < MT_CHUNKS;
         const int cm = has[m] ? c : 0;
-        const int a = cm / (MR * (MO / 4)), w = cm - a * (MR * (MO / 4));
-        const int r = w / (MO / 4), cc = w - r * (MO / 4);
+        const int a = cm / (MR * (MW / 4)), w = cm - a * (MR * (MW / 4));
+        const int r = w / (MW / 4), cc = w - r * (MW / 4);
         const float *src = a == 0 ? in : (a == 1 ? Bg : f);
         sdst[m] = (unsigned)__cvta_generic_to_shared(&S.P[a][0][r * MO + cc * 4]);
         gp[m] = src + (long long)wrapn(q0, n) * n2 + (long long)wrapn(j0 - 2 + r, n) * n +
