@@ -679,7 +679,8 @@ def schedules(mg, device, prec, n):
     out = {}
     while n % 2 == 0 and n // 2 >= 4:
         sch, tuned = mg.schedule_get(device, prec, n)
-        txt = ("fused/%d" % sch.chunk) if sch.form == mg.SWEEP_FUSED else ("two-pass/%d" % sch.block)
+        txt = {mg.SWEEP_FUSED: "fused/%d" % sch.chunk, mg.SWEEP_MARCH: "march/%d" % sch.chunk}.get(
+            sch.form, "two-pass/%d" % sch.block)
         out[str(n)] = txt + ("" if tuned else " (default)")
         n //= 2
     return out
