@@ -7,7 +7,7 @@
 // Paper: arXiv:1511.08200, Eq. (eomvarphi), Eq. (newton), Sec. 3.1 (level
 // solve, V-cycles, boundary values from the coarser level), Sec. 3.2
 // (interpolated fine phi, force by central differences).
-#include "mg5_kernels.cuh"
+#include "mg5_fin.cuh"
 
 namespace mg5 {
 
@@ -125,7 +125,7 @@ cudaError_t launch_operator(const T *phi, int n, CoefT<T> cf, T *out, cudaStream
 template <typename T>
 __global__ void k_residual(const T *__restrict__ phi, const T *__restrict__ f,
                            const double *__restrict__ cptr, int n, CoefT<T> cf, T *__restrict__ r_out,
-                           Moments *__restrict__ partials)
+                           Moments *__restrict__ partials, Fin fin)
 {
     const long long total = (long long)n * n * n;
     const double c = *cptr;
@@ -147,18 +147,21 @@ __global__ void k_residual(const T *__restrict__ phi, const T *__restrict__ f,
     const Moments m = block_moments(acc);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = m;
+    if (fin.ls)
+        finalize_if_last(reinterpret_cast<double2 *>(partials), fin);
 }
 
 template <typename T>
 cudaError_t launch_residual(const T *phi, const T *f, const double *cptr, int n, CoefT<T> cf, T *r,
-                            double2 *partials, int *nblocks, cudaStream_t st)
+                            double2 *partials, int *nblocks, cudaStream_t st, const Fin &fin)
 {
     const long long work = (long long)n * n * n;
     const int cap = sizeof(T) == 8 ? kReduceBlocksFp64 : kReduceBlocks;
     int g = blocks_for(work);
     if (g > cap)
         g = cap;
-    k_residual<T><<<g, kBlock, 0, st>>>(phi, f, cptr, n, cf, r, reinterpret_cast<Moments *>(partials));
+    k_residual<T><<<g, kBlock, 0, st>>>(phi, f, cptr, n, cf, r, reinterpret_cast<Moments *>(partials),
+                                        fin);
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();
@@ -169,7 +172,7 @@ template <typename T, bool BASE>
 __global__ void k_resid_restrict(const T *__restrict__ v, const T *__restrict__ f,
                                  const double *__restrict__ cptr, int n, CoefT<T> cf,
                                  T *__restrict__ vc, T *__restrict__ v0c, T *__restrict__ rc,
-                                 Moments *__restrict__ partials, const T *__restrict__ B)
+                                 Moments *__restrict__ partials, const T *__restrict__ B, Fin fin)
 {
     const int nc = n >> 1;
     const long long total = (long long)nc * nc * nc;
@@ -203,12 +206,14 @@ __global__ void k_resid_restrict(const T *__restrict__ v, const T *__restrict__ 
     const Moments m = block_moments(acc);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = m;
+    if (fin.ls)
+        finalize_if_last(reinterpret_cast<double2 *>(partials), fin);
 }
 
 template <typename T>
 cudaError_t launch_resid_restrict(const T *v, const T *f, const double *cptr, int n, CoefT<T> cf,
                                   T *vc, T *v0c, T *rc, double2 *partials, int *nblocks,
-                                  cudaStream_t st, const T *B)
+                                  cudaStream_t st, const T *B, const Fin &fin)
 {
     const long long work = (long long)(n / 2) * (n / 2) * (n / 2);
     const int cap = sizeof(T) == 8 ? kReduceBlocksFp64 : kReduceBlocks;
@@ -217,9 +222,9 @@ cudaError_t launch_resid_restrict(const T *v, const T *f, const double *cptr, in
         g = cap;
     Moments *mp = reinterpret_cast<Moments *>(partials);
     if (B)
-        k_resid_restrict<T, true><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, mp, B);
+        k_resid_restrict<T, true><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, mp, B, fin);
     else
-        k_resid_restrict<T, false><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, mp, B);
+        k_resid_restrict<T, false><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, mp, B, fin);
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();
@@ -566,51 +571,7 @@ cudaError_t launch_coarsest(T *v, T *tmp, const T *f, int n, CoefT<T> cf, double
 __global__ void k_finalize(const double2 *__restrict__ partials, int nb, double ncells,
                            LevelScal *ls, int mode)
 {
-    if (mode == FIN_RESID || mode == FIN_STATS) {
-        // per-block shifted sums moved onto block 0's shift, summed in a fixed order
-        const Moments *mp = reinterpret_cast<const Moments *>(partials);
-        const double k0 = mp[0].k;
-        Moments v{0.0, k0, 0.0, 0.0};
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            const Moments u = mom_shift(mp[b], k0);
-            v.n += u.n;
-            v.s += u.s;
-            v.q += u.q;
-        }
-        v = block_sum_shared_shift(v);
-        if (threadIdx.x != 0)
-            return;
-        double m = 0.0, m2 = 0.0;
-        if (v.n > 0.0)
-            mom_mean_m2(v, &m, &m2);
-        ls->m = m;
-        if (mode == FIN_RESID)
-            ls->c -= m;
-        ls->rnorm = sqrt(m2);
-        ls->rel = ls->fnorm > 0.0 ? ls->rnorm / ls->fnorm : ls->rnorm;
-        if (!isfinite(m) || !isfinite(m2))
-            ls->rel = m + m2;  // propagates NaN / Inf to the host check
-        return;
-    }
-    double2 acc = make_double2(0.0, 0.0);
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        acc.x += partials[b].x;
-        acc.y += partials[b].y;
-    }
-    acc = block_sum2(acc);
-    if (threadIdx.x != 0)
-        return;
-    if (mode == FIN_NORM) {
-        ls->m = acc.x / ncells;
-        ls->rnorm = sqrt(acc.y);
-        ls->rel = ls->fnorm > 0.0 ? ls->rnorm / ls->fnorm : ls->rnorm;
-        if (!isfinite(acc.x) || !isfinite(acc.y))
-            ls->rel = acc.y + acc.x;
-    } else if (mode == FIN_FNORM) {
-        ls->fnorm = sqrt(acc.y);
-    } else {
-        ls->mean = acc.x / ncells;
-    }
+    finalize_body(partials, nb, ncells, ls, mode);
 }
 
 cudaError_t launch_finalize(const double2 *partials, int nb, double ncells, LevelScal *ls, int mode,
@@ -623,7 +584,7 @@ cudaError_t launch_finalize(const double2 *partials, int nb, double ncells, Leve
 
 __global__ void k_scale(const double *__restrict__ delta, double s, double *__restrict__ f,
                         long long n3, double2 *__restrict__ partials, double add,
-                        const double *__restrict__ add_dev)
+                        const double *__restrict__ add_dev, Fin fin)
 {
     if (add_dev)
         add = *add_dev;
@@ -637,21 +598,25 @@ __global__ void k_scale(const double *__restrict__ delta, double s, double *__re
     acc = block_sum2(acc);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = acc;
+    if (fin.ls)
+        finalize_if_last(partials, fin);
 }
 
 cudaError_t launch_scale(const double *delta, double s, double *f, long long n3, double2 *partials,
-                         int *nblocks, cudaStream_t st, double add, const double *add_dev)
+                         int *nblocks, cudaStream_t st, double add, const double *add_dev,
+                         const Fin &fin)
 {
     int g = blocks_for(n3);
     if (g > kReduceBlocks)
         g = kReduceBlocks;
-    k_scale<<<g, kBlock, 0, st>>>(delta, s, f, n3, partials, add, add_dev);
+    k_scale<<<g, kBlock, 0, st>>>(delta, s, f, n3, partials, add, add_dev, fin);
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();
 }
 
-__global__ void k_sum(const double *__restrict__ a, long long n3, double2 *__restrict__ partials)
+__global__ void k_sum(const double *__restrict__ a, long long n3, double2 *__restrict__ partials,
+                      Fin fin)
 {
     double2 acc = make_double2(0.0, 0.0);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n3;
@@ -660,15 +625,17 @@ __global__ void k_sum(const double *__restrict__ a, long long n3, double2 *__res
     acc = block_sum2(acc);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = acc;
+    if (fin.ls)
+        finalize_if_last(partials, fin);
 }
 
 cudaError_t launch_sum(const double *phi, long long n3, double2 *partials, int *nblocks,
-                       cudaStream_t st)
+                       cudaStream_t st, const Fin &fin)
 {
     int g = blocks_for(n3);
     if (g > kReduceBlocks)
         g = kReduceBlocks;
-    k_sum<<<g, kBlock, 0, st>>>(phi, n3, partials);
+    k_sum<<<g, kBlock, 0, st>>>(phi, n3, partials, fin);
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();
@@ -999,7 +966,8 @@ cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint
 template <bool MASKED>
 __global__ void k_patch_residual(const double *__restrict__ phi, const double *__restrict__ fint,
                                  double rhs_add, int p0, int p1, int p2, CoefT<double> cf,
-                                 double2 *__restrict__ partials, const unsigned char *__restrict__ mask)
+                                 double2 *__restrict__ partials, const unsigned char *__restrict__ mask,
+                                 Fin fin)
 {
     const long long total = (long long)p0 * p1 * p2;
     double2 acc = make_double2(0.0, 0.0);
@@ -1020,11 +988,14 @@ __global__ void k_patch_residual(const double *__restrict__ phi, const double *_
     acc = block_sum2(acc);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = acc;
+    if (fin.ls)
+        finalize_if_last(partials, fin);
 }
 
 cudaError_t launch_patch_residual(const double *phi, const double *fint, double rhs_add,
                                   const int pf[3], CoefT<double> cf, double2 *partials, int *nblocks,
-                                  cudaStream_t st, const unsigned char *mask)
+                                  cudaStream_t st, const unsigned char *mask,
+                                  const Fin &fin)
 {
     const long long work = (long long)pf[0] * pf[1] * pf[2];
     int g = blocks_for(work);
@@ -1032,10 +1003,10 @@ cudaError_t launch_patch_residual(const double *phi, const double *fint, double 
         g = kReduceBlocksFp64;
     if (mask)
         k_patch_residual<true><<<g, kBlock, 0, st>>>(phi, fint, rhs_add, pf[0], pf[1], pf[2], cf,
-                                                     partials, mask);
+                                                     partials, mask, fin);
     else
         k_patch_residual<false><<<g, kBlock, 0, st>>>(phi, fint, rhs_add, pf[0], pf[1], pf[2], cf,
-                                                      partials, mask);
+                                                      partials, mask, fin);
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();
@@ -1047,10 +1018,10 @@ cudaError_t launch_patch_residual(const double *phi, const double *fint, double 
                                          unsigned long long *, cudaStream_t, const T *, int);      \
     template cudaError_t launch_operator<T>(const T *, int, CoefT<T>, T *, cudaStream_t);          \
     template cudaError_t launch_residual<T>(const T *, const T *, const double *, int, CoefT<T>,   \
-                                            T *, double2 *, int *, cudaStream_t);                  \
+                                            T *, double2 *, int *, cudaStream_t, const Fin &);     \
     template cudaError_t launch_resid_restrict<T>(const T *, const T *, const double *, int,       \
                                                   CoefT<T>, T *, T *, T *, double2 *, int *,       \
-                                                  cudaStream_t, const T *);                        \
+                                                  cudaStream_t, const T *, const Fin &);           \
     template cudaError_t launch_restrict<T>(const T *, int, T *, cudaStream_t);                    \
     template cudaError_t launch_coarse_rhs<T>(const T *, T *, const double *, double *, int,       \
                                               CoefT<T>, cudaStream_t, const T *);                  \

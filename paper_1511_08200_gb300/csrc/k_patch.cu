@@ -21,7 +21,7 @@
 //
 // Box layout: interior dims (p0, p1, p2), box dims (p + 2), interior index
 // i <-> box index i + 1, C order.  Right-hand sides are interior-indexed.
-#include "mg5_kernels.cuh"
+#include "mg5_fin.cuh"
 
 namespace mg5 {
 
@@ -38,7 +38,7 @@ __global__ void k_pbox_resid_restrict(const double *__restrict__ v, const double
                                       int p0, int p1, int p2, CoefT<double> cf,
                                       double *__restrict__ vc, double *__restrict__ v0c,
                                       double *__restrict__ fc, double2 *__restrict__ partials,
-                                      const unsigned char *__restrict__ mask)
+                                      const unsigned char *__restrict__ mask, Fin fin)
 {
     const int q0 = p0 >> 1, q1 = p1 >> 1, q2 = p2 >> 1;
     const long long total = (long long)q0 * q1 * q2;
@@ -69,6 +69,8 @@ __global__ void k_pbox_resid_restrict(const double *__restrict__ v, const double
     acc = block_sum2(acc);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = acc;
+    if (fin.ls)
+        finalize_if_last(partials, fin);
 }
 
 // fc = op(vc) + fc on the coarse interior (fc holds the restricted residual)
@@ -394,7 +396,7 @@ __global__ void __launch_bounds__(kPboxThreads)
 cudaError_t launch_pbox_resid_restrict(const double *v, const double *f, const int p[3],
                                        CoefT<double> cf, double *vc, double *v0c, double *fc,
                                        double2 *partials, int *nblocks, cudaStream_t st,
-                                       const unsigned char *mask)
+                                       const unsigned char *mask, const Fin &fin)
 {
     const long long work = (long long)(p[0] / 2) * (p[1] / 2) * (p[2] / 2);
     int g = blocks_for(work);
@@ -402,10 +404,10 @@ cudaError_t launch_pbox_resid_restrict(const double *v, const double *f, const i
         g = kReduceBlocksFp64;
     if (mask)
         k_pbox_resid_restrict<true><<<g, kBlock, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc, v0c, fc,
-                                                          partials, mask);
+                                                          partials, mask, fin);
     else
         k_pbox_resid_restrict<false><<<g, kBlock, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc, v0c, fc,
-                                                           partials, mask);
+                                                           partials, mask, fin);
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();

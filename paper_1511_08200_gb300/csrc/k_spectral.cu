@@ -11,7 +11,7 @@
 // error the sweeps cannot, and the sweeps the local nonlinear part.  A fixed number of
 // iterations keeps the launch sequence fixed (the same in captured graphs).  Multi-CTA
 // kernels: the grid is at most 32^3.
-#include "mg5_kernels.cuh"
+#include "mg5_fin.cuh"
 
 namespace mg5 {
 
@@ -35,7 +35,7 @@ template <typename T, bool BASE>
 __global__ void k_spec_residual(const T *__restrict__ v, const T *__restrict__ f,
                                 const double *__restrict__ cptr, int n, CoefT<T> cf,
                                 const T *__restrict__ B, typename Cplx<T>::type *__restrict__ out,
-                                Moments *__restrict__ partials, int *sweeps)
+                                Moments *__restrict__ partials, int *sweeps, Fin fin)
 {
     const int n3 = n * n * n;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -59,6 +59,7 @@ __global__ void k_spec_residual(const T *__restrict__ v, const T *__restrict__ f
         if (blockIdx.x == 0 && sweeps)
             atomicAdd(sweeps, 2);
     }
+    finalize_if_last(reinterpret_cast<double2 *>(partials), fin);   // c -= mean r
 }
 
 // One-dimensional DFT along `axis` (0: i, 1: j, 2: k) of every line:
@@ -135,14 +136,13 @@ cudaError_t launch_coarsest_spectral(T *v, T *tmp, const T *f, int n, CoefT<T> c
     Moments *mp = reinterpret_cast<Moments *>(partials);
     const T inv_n3 = (T)1 / (T)n3;
     for (int it = 0; it < iters; ++it) {
+        const Fin fin{ls, FIN_RESID, (double)n3};
         if (B)
-            k_spec_residual<T, true><<<g, kBlock, 0, st>>>(v, f, &ls->c, n, cf, B, w0, mp, sweeps);
+            k_spec_residual<T, true><<<g, kBlock, 0, st>>>(v, f, &ls->c, n, cf, B, w0, mp, sweeps, fin);
         else
-            k_spec_residual<T, false><<<g, kBlock, 0, st>>>(v, f, &ls->c, n, cf, B, w0, mp, sweeps);
+            k_spec_residual<T, false><<<g, kBlock, 0, st>>>(v, f, &ls->c, n, cf, B, w0, mp, sweeps, fin);
         count_launch(1);
-        cudaError_t e = launch_finalize(partials, g, (double)n3, ls, FIN_RESID, st);   // c -= mean r
-        if (e != cudaSuccess)
-            return e;
+        cudaError_t e;
         k_dft_axis<T><<<g, kBlock, 0, st>>>(w0, w1, n, 2, 0, nullptr, (T)0);
         k_dft_axis<T><<<g, kBlock, 0, st>>>(w1, w0, n, 1, 0, nullptr, (T)0);
         k_dft_axis<T><<<g, kBlock, 0, st>>>(w0, w1, n, 0, 0, nullptr, (T)0);

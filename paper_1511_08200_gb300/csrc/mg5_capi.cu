@@ -200,6 +200,16 @@ struct mg5_ctx {
 
 // ------------------------------------------------------------ helpers
 
+// A reduction's partial-sum buffer, zeroed: its last slot is the blocks-done counter of the
+// reductions that finalize in their own last block (mg5_fin.cuh).
+static cudaError_t alloc_partials(double2 **p)
+{
+    cudaError_t e = cudaMalloc((void **)p, sizeof(double2) * kMaxPartials);
+    if (e == cudaSuccess)
+        e = cudaMemset(*p, 0, sizeof(double2) * kMaxPartials);
+    return e;
+}
+
 extern "C" {  // defined further down, inside the ABI block
 static bool same_params(const mg5_params &a, const mg5_params &b);
 static int solve_graph(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p, double *phi,
@@ -604,11 +614,11 @@ struct Run64 {
         mg5_ctx *ctx = this->ctx;
         {
             ProfScope ps(&ctx->prof, PK_RESTRICT64, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
+            const double n3 = (double)h->n[l] * h->n[l] * h->n[l];
             CK(launch_resid_restrict<double>(h->v[l], h->f[l], c(l), h->n[l], cf, h->v[l + 1],
-                                             h->v0[l + 1], h->f[l + 1], partb, &nb, st));
+                                             h->v0[l + 1], h->f[l + 1], partb, &nb, st, nullptr,
+                                             Fin{ls(l), FIN_RESID, n3}));
         }
-        const double n3 = (double)h->n[l] * h->n[l] * h->n[l];
-        CK(launch_finalize(partb, nb, n3, ls(l), FIN_RESID, st));
         return MG5_OK;
     }
 
@@ -617,10 +627,9 @@ struct Run64 {
         const CoefT<double> cf = make_coef<double>(hl[l], p->alpha);
         int nb = 0;
         mg5_ctx *ctx = this->ctx;
-        CK(launch_residual<double>(h->v[l], h->f[l], c(l), h->n[l], cf, nullptr, partb,
-                                   &nb, st));
         const double n3 = (double)h->n[l] * h->n[l] * h->n[l];
-        CK(launch_finalize(partb, nb, n3, ls(l), FIN_RESID, st));
+        CK(launch_residual<double>(h->v[l], h->f[l], c(l), h->n[l], cf, nullptr, partb,
+                                   &nb, st, Fin{ls(l), FIN_RESID, n3}));
         return MG5_OK;
     }
 
@@ -726,8 +735,8 @@ static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p
     CK(cudaMemsetAsync(ctx->ls, 0, sizeof(LevelScal) * kScalSlots, st));
     CK(cudaMemsetAsync(ctx->cnt, 0, sizeof(SolveCounters), st));
     int nb = 0;
-    CK(launch_scale(delta, p->s, h->f[0], n3, ctx->partials, &nb, st));
-    CK(launch_finalize(ctx->partials, nb, (double)n3, ctx->ls, FIN_FNORM, st));
+    CK(launch_scale(delta, p->s, h->f[0], n3, ctx->partials, &nb, st, 0.0, nullptr,
+                    Fin{ctx->ls, FIN_FNORM, (double)n3}));
     double *caller_phi = phi;
     h->v[0] = phi;
     // tmp[0] is the context's; v/tmp swap on every sweep.  Every exit path
@@ -803,8 +812,7 @@ static int solve64(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p
     if (h->v[0] != caller_phi)
         CK(cudaMemcpyAsync(caller_phi, h->v[0], n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     // gauge: subtract mean(phi)
-    CK(launch_sum(caller_phi, n3, ctx->partials, &nb, st));
-    CK(launch_finalize(ctx->partials, nb, (double)n3, ctx->ls, FIN_MEAN, st));
+    CK(launch_sum(caller_phi, n3, ctx->partials, &nb, st, Fin{ctx->ls, FIN_MEAN, (double)n3}));
     CK(launch_sub_mean(caller_phi, n3, &ctx->ls[0].mean, st));
     if (info) {
         info->cycles = cyc;
@@ -906,7 +914,7 @@ int mg5_create(mg5_ctx **out, int device, size_t budget)
     ctx->budget = budget;
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess)
-        e = cudaMalloc((void **)&ctx->partials, sizeof(double2) * kMaxPartials);
+        e = alloc_partials(&ctx->partials);
     if (e == cudaSuccess)
         e = cudaMalloc((void **)&ctx->ls, sizeof(LevelScal) * kScalSlots);
     if (e == cudaSuccess)
@@ -1364,11 +1372,10 @@ struct RunPatch {
             ProfScope ps(&ctx->prof, PK_PATCH_RESID, st, (double)int_cells(h->q[l]));
             CK(launch_pbox_resid_restrict(h->v[l], h->f[l], h->q[l],
                                           make_coef<double>(hl[l], p->alpha), h->v[l + 1],
-                                          h->v0[l + 1], h->f[l + 1], partb, &nb, st, mk[l]));
+                                          h->v0[l + 1], h->f[l + 1], partb, &nb, st, mk[l],
+                                          Fin{finalize ? lsp : nullptr, FIN_NORM,
+                                              (double)int_cells(h->q[l])}));
         }
-        if (finalize)
-            CK(launch_finalize(partb, nb, (double)int_cells(h->q[l]), lsp,
-                               FIN_NORM, st));
         return MG5_OK;
     }
 
@@ -1430,10 +1437,11 @@ static int relax_patch_impl(mg5_ctx *ctx, const double *delta_f, const int pf[3]
         CK(launch_scale_masked(delta_f, p->s, h->f[0], ni, mask, ctx->partials, &nb, st, compat_c));
         for (int l = 1; l < h->nlev; ++l)
             CK(launch_mask_restrict(l == 1 ? mask : h->mk[l - 1], h->q[l - 1], h->mk[l], st));
+        CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_FNORM, st));
     } else {
-        CK(launch_scale(delta_f, p->s, h->f[0], ni, ctx->partials, &nb, st, compat_c));
+        CK(launch_scale(delta_f, p->s, h->f[0], ni, ctx->partials, &nb, st, compat_c, nullptr,
+                        Fin{ls, FIN_FNORM, (double)ni}));
     }
-    CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_FNORM, st));
     double masked_fraction = 1.0;
     if (mask) {
         CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_MEAN, st));   // mean = fraction
@@ -1489,8 +1497,8 @@ static int relax_patch_impl(mg5_ctx *ctx, const double *delta_f, const int pf[3]
     if (mask && masked_fraction < kMaskGsFraction) {
         const CoefT<double> cf0 = make_coef<double>(p->h, p->alpha);
         for (int gs = 0;;) {
-            CK(launch_patch_residual(h->v[0], h->f[0], 0.0, pf, cf0, ctx->partials, &nb, st, mask));
-            CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_NORM, st));
+            CK(launch_patch_residual(h->v[0], h->f[0], 0.0, pf, cf0, ctx->partials, &nb, st, mask,
+                                     Fin{ls, FIN_NORM, (double)ni}));
             CK(cudaMemcpyAsync(ctx->h_rel, &ls->rel, sizeof(double), cudaMemcpyDeviceToHost, st));
             CK(ctx_wait(ctx, st));
             const double rel = *ctx->h_rel;
@@ -1510,8 +1518,7 @@ static int relax_patch_impl(mg5_ctx *ctx, const double *delta_f, const int pf[3]
         if (h->nlev == 1) {
             RET(R.coarsest(0));
             CK(launch_patch_residual(h->v[0], h->f[0], 0.0, pf, make_coef<double>(p->h, p->alpha),
-                                     ctx->partials, &nb, st, mask));
-            CK(launch_finalize(ctx->partials, nb, (double)ni, ls, FIN_NORM, st));
+                                     ctx->partials, &nb, st, mask, Fin{ls, FIN_NORM, (double)ni}));
         } else {
             for (int s = 0; s < p->nu1; ++s)
                 RET(R.sweep(0));
@@ -1667,8 +1674,8 @@ int capture_patch_impl(mg5_ctx *ctx, GraphEntry *g, const mg5_params *p, cudaStr
     CK(cudaMemsetAsync(g->ls, 0, sizeof(LevelScal) * kScalSlots, st));
     CK(cudaMemsetAsync(g->cnt, 0, sizeof(SolveCounters), st));
     int nb = 0;
-    CK(launch_scale(g->delta, p->s, h->f[0], ni, g->partials, &nb, st, 0.0, g->cdev));
-    CK(launch_finalize(g->partials, nb, (double)ni, g->ls, FIN_FNORM, st));
+    CK(launch_scale(g->delta, p->s, h->f[0], ni, g->partials, &nb, st, 0.0, g->cdev,
+                    Fin{g->ls, FIN_FNORM, (double)ni}));
     CK(cudaMemcpyAsync(h->tmp[0], g->phi, nbox * sizeof(double), cudaMemcpyDeviceToDevice, st));
     for (int l = 1; l < h->nlev; ++l)
         CK(launch_pbox_ghosts(l == 1 ? g->phi : h->v[l - 1], h->q[l - 1], h->v[l], h->tmp[l],
@@ -1794,6 +1801,8 @@ int mg5_relax_patch_graph(mg5_ctx *ctx, const double *delta_f, const int pf[3], 
                                                    : sizeof(double);
             e = cudaMalloc(q2, b);
         }
+        if (e == cudaSuccess)
+            e = cudaMemset(g->partials, 0, sizeof(double2) * kMaxPartials);
         if (e == cudaSuccess)
             e = cudaMallocHost((void **)&g->rb, sizeof(GraphReadback));
         g->bytes = need;
@@ -1984,7 +1993,7 @@ int graph_build(int device, int N, const mg5_params *p, bool grad, GraphEntry **
     const size_t n3 = (size_t)N * N * N;
     cudaError_t e = rc == MG5_OK ? cudaSuccess : cudaErrorMemoryAllocation;
     if (e == cudaSuccess)
-        e = cudaMalloc((void **)&g->partials, sizeof(double2) * kMaxPartials);
+        e = alloc_partials(&g->partials);
     if (e == cudaSuccess)
         e = cudaMalloc((void **)&g->ls, sizeof(LevelScal) * kScalSlots);
     if (e == cudaSuccess)
@@ -2148,8 +2157,8 @@ static int capture_fp64(mg5_ctx *ctx, GraphEntry *g, const mg5_params *p, cudaSt
     CK(cudaMemsetAsync(g->ls, 0, sizeof(LevelScal) * kScalSlots, st));
     CK(cudaMemsetAsync(g->cnt, 0, sizeof(SolveCounters), st));
     int nb = 0;
-    CK(launch_scale(g->delta, p->s, h->f[0], n3, g->partials, &nb, st));
-    CK(launch_finalize(g->partials, nb, (double)n3, g->ls, FIN_FNORM, st));
+    CK(launch_scale(g->delta, p->s, h->f[0], n3, g->partials, &nb, st, 0.0, nullptr,
+                    Fin{g->ls, FIN_FNORM, (double)n3}));
     CK(cudaMemsetAsync(g->phi, 0, n3 * sizeof(double), st));
     h->v[0] = g->phi;
     if (g->fmg)
@@ -2204,8 +2213,7 @@ static int capture_fp64(mg5_ctx *ctx, GraphEntry *g, const mg5_params *p, cudaSt
     // the iterate is in h->v[0]: bring it to the entry's phi, then the gauge and the force
     if (h->v[0] != g->phi)
         CK(cudaMemcpyAsync(g->phi, h->v[0], n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CK(launch_sum(g->phi, n3, g->partials, &nb, st));
-    CK(launch_finalize(g->partials, nb, (double)n3, g->ls, FIN_MEAN, st));
+    CK(launch_sum(g->phi, n3, g->partials, &nb, st, Fin{g->ls, FIN_MEAN, (double)n3}));
     CK(launch_sub_mean(g->phi, n3, &g->ls[0].mean, st));
     if (g->gout)
         CK(launch_force(g->phi, N, N, N, 0, p->h, 1, g->gout, st));
@@ -2231,7 +2239,7 @@ static int graph_build64(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, bo
     const size_t n3 = (size_t)N * N * N;
     cudaError_t e = alloc_hier_raw(N, &g->hier64);
     if (e == cudaSuccess)
-        e = cudaMalloc((void **)&g->partials, sizeof(double2) * kMaxPartials);
+        e = alloc_partials(&g->partials);
     if (e == cudaSuccess)
         e = cudaMalloc((void **)&g->ls, sizeof(LevelScal) * kScalSlots);
     if (e == cudaSuccess)
@@ -2413,7 +2421,7 @@ static int build_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const
             free_batch(ctx);
             return rc;
         }
-        CK(cudaMalloc((void **)&b->partials[i], sizeof(double2) * kMaxPartials));
+        CK(alloc_partials(&b->partials[i]));
         CK(cudaMalloc((void **)&b->ls[i], sizeof(LevelScal) * kScalSlots));
         CK(cudaMalloc((void **)&b->cnt[i], sizeof(SolveCounters)));
     }

@@ -69,6 +69,16 @@ long long launches_total();
 // FIN_MEAN:  mean = sum of the first component / ncells
 enum FinalizeMode { FIN_RESID = 0, FIN_FNORM = 1, FIN_MEAN = 2, FIN_STATS = 3, FIN_NORM = 4 };
 
+// A reduction finalized by the last block of its own kernel (mg5_fin.cuh) instead of a
+// separate launch_finalize: the grid size is the number of partials.  ls == nullptr: no
+// finalize in the kernel.  The partial buffer's last slot holds the blocks-done counter
+// (zero between launches; buffers are zeroed when allocated).
+struct Fin {
+    LevelScal *ls = nullptr;
+    int mode = 0;
+    double ncells = 0.0;
+};
+
 // ---- FP64/FP32 periodic kernels (templates instantiated for double and float)
 // B (optional): base field of the correction form (mixed precision)
 // two-pass sweep (red kernel, black kernel) with `block` threads per block
@@ -133,12 +143,14 @@ cudaError_t launch_operator(const T *phi, int n, CoefT<T> cf, T *out, cudaStream
 // r (nullable) = f + c - op(phi); partial sums (sum r, sum r^2) per block.
 template <typename T>
 cudaError_t launch_residual(const T *phi, const T *f, const double *cptr, int n, CoefT<T> cf,
-                            T *r, double2 *partials, int *nblocks, cudaStream_t st);
+                            T *r, double2 *partials, int *nblocks, cudaStream_t st,
+                            const Fin &fin = Fin());
 // fused residual + 8-child restriction of v and r (vc and v0c get R v, rc gets R r).
 template <typename T>
 cudaError_t launch_resid_restrict(const T *v, const T *f, const double *cptr, int n,
                                   CoefT<T> cf, T *vc, T *v0c, T *rc, double2 *partials,
-                                  int *nblocks, cudaStream_t st, const T *B = nullptr);
+                                  int *nblocks, cudaStream_t st, const T *B = nullptr,
+                                  const Fin &fin = Fin());
 // coarse = 8-child mean of fine
 template <typename T>
 cudaError_t launch_restrict(const T *fine, int n, T *coarse, cudaStream_t st);
@@ -172,10 +184,10 @@ cudaError_t launch_finalize(const double2 *partials, int nb, double ncells, Leve
 // f = s * delta + add (add read from add_dev on the device when given), partial sums (0, (s delta)^2)
 cudaError_t launch_scale(const double *delta, double s, double *f, long long n3, double2 *partials,
                          int *nblocks, cudaStream_t st, double add = 0.0,
-                         const double *add_dev = nullptr);
+                         const double *add_dev = nullptr, const Fin &fin = Fin());
 // partial sums (phi, 0)
 cudaError_t launch_sum(const double *phi, long long n3, double2 *partials, int *nblocks,
-                       cudaStream_t st);
+                       cudaStream_t st, const Fin &fin = Fin());
 // phi -= *mean
 cudaError_t launch_sub_mean(double *phi, long long n3, const double *mean, cudaStream_t st);
 cudaError_t launch_force(const double *phi, int d0, int d1, int d2, int ghost, double h,
@@ -199,14 +211,16 @@ cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint
 // partial sums (r, r^2) of r = fint + rhs_add - op(phi) over the interior (the cells of mask)
 cudaError_t launch_patch_residual(const double *phi, const double *fint, double rhs_add,
                                   const int pf[3], CoefT<double> cf, double2 *partials, int *nblocks,
-                                  cudaStream_t st, const unsigned char *mask = nullptr);
+                                  cudaStream_t st, const unsigned char *mask = nullptr,
+                                  const Fin &fin = Fin());
 
 // ---- Dirichlet patch multigrid (k_patch.cu); p = fine interior dims, q = coarse interior dims
 // mask (fine, optional): the residual of cells with mask 0 counts as zero
 cudaError_t launch_pbox_resid_restrict(const double *v, const double *f, const int p[3],
                                        CoefT<double> cf, double *vc, double *v0c, double *fc,
                                        double2 *partials, int *nblocks, cudaStream_t st,
-                                       const unsigned char *mask = nullptr);
+                                       const unsigned char *mask = nullptr,
+                                       const Fin &fin = Fin());
 cudaError_t launch_pbox_coarse_rhs(const double *vc, double *fc, const int q[3], CoefT<double> cf,
                                    cudaStream_t st);
 // mask (fine, optional): only cells with mask != 0 take the correction

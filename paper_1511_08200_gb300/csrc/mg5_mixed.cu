@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "mg5_fin.cuh"
 #include "mg5_mixed.cuh"
 
 namespace mg5 {
@@ -38,7 +39,7 @@ template <bool ZERO>
 __global__ void k_resid64_mixed(const double *__restrict__ phi, const double *__restrict__ f,
                                 const double *__restrict__ cptr, int n, CoefT<double> cf,
                                 float *__restrict__ r32, float *__restrict__ B,
-                                Moments *__restrict__ partials)
+                                Moments *__restrict__ partials, Fin fin)
 {
     const long long total = (long long)n * n * n;
     const double c = *cptr;
@@ -67,6 +68,7 @@ __global__ void k_resid64_mixed(const double *__restrict__ phi, const double *__
     const Moments m = block_moments(acc);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = m;
+    finalize_if_last(reinterpret_cast<double2 *>(partials), fin);
 }
 
 __global__ void k_update_mixed(double *__restrict__ phi, const float *__restrict__ e, long long n3)
@@ -143,14 +145,11 @@ struct RunMix {
     {
         int nb = 0;
         ProfScope ps(sh.prof, PK_RESTRICT32, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
+        const double n3 = (double)h->n[l] * h->n[l] * h->n[l];
         cudaError_t e = launch_resid_restrict<float>(h->e[l], h->f[l], c(l), h->n[l],
                                                      make_coef<float>(hl[l], p->alpha), h->e[l + 1],
                                                      h->e0[l + 1], h->f[l + 1], sh.partials, &nb,
-                                                     st, h->B[l]);
-        if (e == cudaSuccess) {
-            const double n3 = (double)h->n[l] * h->n[l] * h->n[l];
-            e = launch_finalize(sh.partials, nb, n3, ls(l), FIN_RESID, st);
-        }
+                                                     st, h->B[l], Fin{ls(l), FIN_RESID, n3});
         return e == cudaSuccess ? MG5_OK : fail("resid_restrict32", e);
     }
 
@@ -310,8 +309,8 @@ int phase_setup(MixedHier *h, const MixedShared &sh, const double *delta, const 
     CKM(cudaMemsetAsync(sh.ls, 0, sizeof(LevelScal) * kScalSlots, st));
     CKM(cudaMemsetAsync(sh.cnt, 0, sizeof(SolveCounters), st));
     int nb = 0;
-    CKM(launch_scale(delta, p->s, h->f64, n3, sh.partials, &nb, st));
-    CKM(launch_finalize(sh.partials, nb, (double)n3, sh.ls, FIN_FNORM, st));
+    CKM(launch_scale(delta, p->s, h->f64, n3, sh.partials, &nb, st, 0.0, nullptr,
+                     Fin{sh.ls, FIN_FNORM, (double)n3}));
     return MG5_OK;
 }
 
@@ -329,16 +328,16 @@ int phase_residual(MixedHier *h, const MixedShared &sh, const mg5_params *p, dou
         ProfScope ps(sh.prof, PK_RESID64_MIXED, st, (double)n3);
         const CoefT<double> cf = make_coef<double>(p->h, p->alpha);
         Moments *mp = reinterpret_cast<Moments *>(sh.partials);
+        const Fin fin{sh.ls, FIN_STATS, (double)n3};
         if (zero)
             k_resid64_mixed<true><<<grid, kBlock, 0, st>>>(phi, h->f64, &sh.ls[0].c, N, cf,
-                                                           h->f[0], h->B[0], mp);
+                                                           h->f[0], h->B[0], mp, fin);
         else
             k_resid64_mixed<false><<<grid, kBlock, 0, st>>>(phi, h->f64, &sh.ls[0].c, N, cf,
-                                                            h->f[0], h->B[0], mp);
+                                                            h->f[0], h->B[0], mp, fin);
     }
     count_launch(1);
     CKM(cudaGetLastError());
-    CKM(launch_finalize(sh.partials, grid, (double)n3, sh.ls, FIN_STATS, st));
     return MG5_OK;
 }
 
@@ -378,8 +377,7 @@ int phase_finish(MixedHier *h, const MixedShared &sh, double *phi, cudaStream_t 
     count_launch(1);
     CKM(cudaGetLastError());
     int nb = 0;
-    CKM(launch_sum(phi, n3, sh.partials, &nb, st));
-    CKM(launch_finalize(sh.partials, nb, (double)n3, sh.ls, FIN_MEAN, st));
+    CKM(launch_sum(phi, n3, sh.partials, &nb, st, Fin{sh.ls, FIN_MEAN, (double)n3}));
     CKM(launch_sub_mean(phi, n3, &sh.ls[0].mean, st));
     return MG5_OK;
 }
