@@ -486,6 +486,15 @@ const char *mg5_profile_name(int k);
  * phi_out = sweep(phi_in).  phi_in and phi_out must not alias. */
 int mg5_step_sweep(mg5_ctx *ctx, const double *phi_in, double *phi_out, const double *f,
                    double c, int N, double h, double alpha, void *stream);
+/* Residual of the mixed mode's FP32 correction equation, r = f + c - (op(B + e) - op(B)),
+ * restricted by 8-child means: ec = R e and rc = R r ((N/2)^3 floats each, device), with
+ * stats (host, 2 doubles, may be NULL) = mean r and ||r - mean r||_2.  e, f, B: device,
+ * N^3 floats.  variant 0: gather kernel; 1: column-march kernel (N a multiple of 32).
+ * Both give the same ec and rc to the bit; the statistics agree to FP32 summation order.
+ * Synchronises the stream. */
+int mg5_step_resid_restrict_f32(mg5_ctx *ctx, const float *e, const float *f, const float *B,
+                                double c, int N, double h, double alpha, int variant, float *ec,
+                                float *rc, double *stats, void *stream);
 /* The same sweep by the fused kernel (one read and one write of phi per cell). */
 int mg5_step_sweep_fused(mg5_ctx *ctx, const double *phi_in, double *phi_out, const double *f,
                          double c, int N, double h, double alpha, void *stream);

@@ -148,6 +148,8 @@ _sigs = {
     "mg5_step_sweep_f32": ([_P, _P, _P, _P, _P, _c_double, _c_int, _c_double, _c_double, _c_int, _P],
                            _c_int),
     "mg5_step_operator": ([_P, _P, _c_int, _c_double, _c_double, _P, _P], _c_int),
+    "mg5_step_resid_restrict_f32": ([_P, _P, _P, _P, _c_double, _c_int, _c_double, _c_double, _c_int,
+                                     _P, _P, _P, _P], _c_int),
     "mg5_step_residual": ([_P, _P, _P, _c_double, _c_int, _c_double, _c_double, _P, _P], _c_int),
     "mg5_step_restrict": ([_P, _P, _c_int, _P, _P], _c_int),
     "mg5_step_prolong_add": ([_P, _P, _c_int, _P, _P], _c_int),
@@ -607,6 +609,25 @@ class Context:
                                             _ptr(base, "float32", dv), c, n, h, alpha,
                                             int(fused), _stream(stream)))
         return out
+
+    def step_resid_restrict_f32(self, e, f, base, c: float, h: float, alpha: float, march=False,
+                                stream=None):
+        """mg5_step_resid_restrict_f32: (R e, R r, (mean r, ||r - mean r||)) of the FP32
+        correction equation's residual r = f + c - (op(B + e) - op(B))."""
+        import torch
+        n = _cube(e, "e")
+        self._cubes(n, f=f, base=base)
+        if base is None:
+            raise MG5Error(E_ARG, "base is required")
+        ec = torch.empty((n // 2,) * 3, dtype=torch.float32, device=e.device)
+        rc = torch.empty_like(ec)
+        st = (_c_double * 2)()
+        dv = self.device
+        self._check(_lib.mg5_step_resid_restrict_f32(
+            self._h, _ptr(e, "float32", dv), _ptr(f, "float32", dv), _ptr(base, "float32", dv), c,
+            n, h, alpha, 1 if march else 0, _ptr(ec, "float32", dv), _ptr(rc, "float32", dv), st,
+            _stream(stream)))
+        return ec, rc, (st[0], st[1])
 
     def step_operator(self, phi, h: float, alpha: float, out=None, stream=None):
         import torch

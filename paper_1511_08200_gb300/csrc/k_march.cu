@@ -32,6 +32,7 @@
 // to the bit.  Periodic in i, j, k; n a multiple of 32; out of place.
 #include <type_traits>
 
+#include "mg5_async.cuh"
 #include "mg5_kernels.cuh"
 
 namespace mg5 {
@@ -60,11 +61,6 @@ struct MarchSmem {
     float RN[2][RNP];       // new red values of planes p and p + 1
 };
 
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-__device__ __forceinline__ int wrapn(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
 // values a position keeps between its two active steps (plane p: read two steps earlier as
 // plane p + 2; plane p - 1: read two steps earlier as plane p + 1)
@@ -90,23 +86,6 @@ __device__ __forceinline__ PlaneCol plane_col(const float *base)
     r.Dz = __fsub_rn(zp, zm);
     r.dyz = __fsub_rn(__fsub_rn(pp, pm), __fsub_rn(mp, mm));
     return r;
-}
-
-// (e, B) parts of a cell from its face sums and mixed differences, each half in scalar
-// arithmetic (the same roundings as the packed pairs of parts2_of)
-__device__ __forceinline__ Parts2 parts_from(float sxe, float sxb, float sye, float syb, float sze,
-                                             float szb, float dxye, float dxyb, float dxze,
-                                             float dxzb, float dyze, float dyzb)
-{
-    Parts2 q;
-    q.S = make_float2(__fadd_rn(__fadd_rn(sxe, sye), sze), __fadd_rn(__fadd_rn(sxb, syb), szb));
-    q.a = make_float2(__fsub_rn(sxe, sye), __fsub_rn(sxb, syb));
-    q.b = make_float2(__fsub_rn(sxe, sze), __fsub_rn(sxb, szb));
-    q.c = make_float2(__fsub_rn(sye, sze), __fsub_rn(syb, szb));
-    q.dxy = make_float2(dxye, dxyb);
-    q.dxz = make_float2(dxze, dxzb);
-    q.dyz = make_float2(dyze, dyzb);
-    return q;
 }
 
 // A thread's position: its plane offset and its offset in the new-red array.
@@ -150,18 +129,15 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
         const int r = w / (MW / 4), cc = w - r * (MW / 4);
         const float *src = a == 0 ? in : (a == 1 ? Bg : f);
         sdst[m] = (unsigned)__cvta_generic_to_shared(&S.P[a][0][r * MO + cc * 4]);
-        gp[m] = src + (long long)wrapn(q0, n) * n2 + (long long)wrapn(j0 - 2 + r, n) * n +
-                wrapn(k0 - 4 + cc * 4, n);
+        gp[m] = src + (long long)wrap_once(q0, n) * n2 + (long long)wrap_once(j0 - 2 + r, n) * n +
+                wrap_once(k0 - 4 + cc * 4, n);
     }
-    int qn = wrapn(q0, n);   // wrapped index of the next plane to bring in
+    int qn = wrap_once(q0, n);   // wrapped index of the next plane to bring in
     auto issue_next = [&](int s) {
 #pragma unroll
         for (int m = 0; m < MT_CPT; ++m)
             if (has[m])
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
-                                 sdst[m] + (unsigned)(s * MPL * 4)),
-                             "l"(gp[m])
-                             : "memory");
+                acopy::copy16(sdst[m] + (unsigned)(s * MPL * 4), gp[m]);
         if (++qn == n) {
             qn = 0;
 #pragma unroll
@@ -178,7 +154,7 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
     for (int s = 0; s < 5; ++s) {
         if (q0 + s <= last)
             issue_next(s);
-        cp_async_commit();
+        acopy::commit();
     }
 
     // the thread's two positions (j, k global; A and B adjacent)
@@ -247,7 +223,7 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
             const PlaneCol e1 = plane_col(E1), b1 = plane_col(B1);
             // red cell (p + 1) of the position: old values throughout (x faces: p + 2, p)
             const Parts2 qr =
-                parts_from(__fadd_rn(e2.c, c.cE0), __fadd_rn(b2.c, c.cB0), e1.Y, b1.Y, e1.Z, b1.Z,
+                parts2_from_sums(__fadd_rn(e2.c, c.cE0), __fadd_rn(b2.c, c.cB0), e1.Y, b1.Y, e1.Z, b1.Z,
                            __fsub_rn(e2.Dy, c.DyE0), __fsub_rn(b2.Dy, c.DyB0),
                            __fsub_rn(e2.Dz, c.DzE0), __fsub_rn(b2.Dz, c.DzB0), e1.dyz, b1.dyz);
             const float r1 = cell_update_corr_parts(qr, b1.c, e1.c, F[s1 * MPL + ps.off] + cval, cf,
@@ -257,7 +233,7 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
                 // black cell (p) of the position: new red faces, old edges
                 const float *rn = S.RN[set & 1] + ps.rn;
                 const float sye = __fadd_rn(rn[RNO], rn[-RNO]), sze = __fadd_rn(rn[1], rn[-1]);
-                const Parts2 qb = parts_from(__fadd_rn(r1, c.rm), __fadd_rn(b1.c, c.cBm), sye,
+                const Parts2 qb = parts2_from_sums(__fadd_rn(r1, c.rm), __fadd_rn(b1.c, c.cBm), sye,
                                              c.YB0, sze, c.ZB0, __fsub_rn(e1.Dy, c.DyEm),
                                              __fsub_rn(b1.Dy, c.DyBm), __fsub_rn(e1.Dz, c.DzEm),
                                              __fsub_rn(b1.Dz, c.DzBm), c.dyzE0, c.dyzB0);
@@ -295,11 +271,11 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
         constexpr int s0 = decltype(S0c)::value;
         if (p + 5 <= last)
             issue_next((s0 + 5) % MNS);
-        cp_async_commit();
-        cp_async_wait<2>();
+        acopy::commit();
+        acopy::wait<2>();
         __syncthreads();
     };
-    cp_async_wait<2>();   // planes q0 .. q0 + 2
+    acopy::wait<2>();   // planes q0 .. q0 + 2
     __syncthreads();
     // warm-up: the red cells of planes i0 - 1 and i0
     step(IC<0>{}, IC<0>{}, true);

@@ -2624,6 +2624,37 @@ int mg5_step_sweep_f32(mg5_ctx *ctx, const float *in, float *out, const float *f
     return MG5_OK;
 }
 
+int mg5_step_resid_restrict_f32(mg5_ctx *ctx, const float *e, const float *f, const float *B,
+                                double c, int N, double h, double alpha, int variant, float *ec,
+                                float *rc, double *stats, void *stream)
+{
+    if (!ctx || !e || !f || !B || !ec || !rc || N < 2 || (N & 1) || !(h > 0.0) || variant < 0 ||
+        variant > 1 || (variant == 1 && !resid_march_ok(N)))
+        return MG5_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    LevelScal *ls = ctx->ls + kStepSlot;
+    CK(cudaMemsetAsync(ls, 0, sizeof(LevelScal), st));
+    CK(cudaMemcpyAsync(&ls->c, &c, sizeof(double), cudaMemcpyHostToDevice, st));
+    const CoefT<float> cf = make_coef<float>(h, alpha);
+    const Fin fin{ls, FIN_STATS, (double)N * N * N};
+    int nb = 0;
+    if (variant == 1)
+        CK(launch_resid_restrict_march(e, f, &ls->c, N, cf, ec, ec, rc, ctx->partials, &nb, st, B,
+                                       fin));
+    else
+        CK(launch_resid_restrict<float>(e, f, &ls->c, N, cf, ec, ec, rc, ctx->partials, &nb, st, B,
+                                        fin));
+    LevelScal out;
+    CK(cudaMemcpyAsync(&out, ls, sizeof(LevelScal), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (stats) {
+        stats[0] = out.m;
+        stats[1] = out.rnorm;
+    }
+    return MG5_OK;
+}
+
 int mg5_step_sweep_fused(mg5_ctx *ctx, const double *in, double *out, const double *f, double c,
                          int N, double h, double alpha, void *stream)
 {

@@ -404,6 +404,24 @@ __device__ __forceinline__ float sigma_corr(const Parts2 &q, const CoefT<float> 
     return __fmaf_rn(cf.s3, X, __fmul_rn(cf.s8, Y));
 }
 
+// (e, B) parts of a cell from its face sums sx, sy, sz and mixed differences, each half in
+// scalar arithmetic: the same roundings as the packed pairs of parts2_of (kernels that build
+// the sums from cached plane values use this).
+__device__ __forceinline__ Parts2 parts2_from_sums(float sxe, float sxb, float sye, float syb,
+                                                   float sze, float szb, float dxye, float dxyb,
+                                                   float dxze, float dxzb, float dyze, float dyzb)
+{
+    Parts2 q;
+    q.S = make_float2(__fadd_rn(__fadd_rn(sxe, sye), sze), __fadd_rn(__fadd_rn(sxb, syb), szb));
+    q.a = make_float2(__fsub_rn(sxe, sye), __fsub_rn(sxb, syb));
+    q.b = make_float2(__fsub_rn(sxe, sze), __fsub_rn(sxb, szb));
+    q.c = make_float2(__fsub_rn(sye, sze), __fsub_rn(syb, szb));
+    q.dxy = make_float2(dxye, dxyb);
+    q.dxz = make_float2(dxze, dxzb);
+    q.dyz = make_float2(dyze, dyzb);
+    return q;
+}
+
 // The update from the (e, B) parts, B's centre Bc and e's centre ec (used by omega != 1).
 __device__ __forceinline__ float cell_update_corr_parts(const Parts2 &q, float Bc, float ec, float rhs,
                                                         const CoefT<float> &cf, bool &clamped)
@@ -429,14 +447,21 @@ __device__ __forceinline__ float cell_update_corr(const St<float> &e, const St<f
     return cell_update_corr_parts(parts2_of(e, B), B.c, e.c, rhs, cf, clamped);
 }
 
-// op(B + e) - op(B) in FP32: L_e + (2 alpha / 3) L_e (2 L_B + L_e) - alpha (2 Sigma(B, e) + Sigma(e))
+// op(B + e) - op(B) in FP32: L_e + (2 alpha / 3) L_e (2 L_B + L_e) - alpha (2 Sigma(B, e) + Sigma(e)),
+// from the (e, B) parts and the centres (explicitly rounded: every residual kernel agrees)
+__device__ __forceinline__ float cell_op_corr_parts(const Parts2 &q, float Bc, float ec,
+                                                    const CoefT<float> &cf)
+{
+    const float LB = __fmul_rn(__fmaf_rn(-6.0f, Bc, q.S.y), cf.inv_h2);
+    const float Le = __fmul_rn(__fmaf_rn(-6.0f, ec, q.S.x), cf.inv_h2);
+    return __fsub_rn(__fmaf_rn(__fmul_rn(cf.k23, Le), __fmaf_rn(2.0f, LB, Le), Le),
+                     sigma_corr(q, cf));
+}
+
 __device__ __forceinline__ float cell_op_corr(const St<float> &e, const St<float> &B,
                                               const CoefT<float> &cf)
 {
-    const Parts2 q = parts2_of(e, B);
-    const float LB = fmaf(-6.0f, B.c, q.S.y) * cf.inv_h2;
-    const float Le = fmaf(-6.0f, e.c, q.S.x) * cf.inv_h2;
-    return Le + cf.k23 * Le * fmaf(2.0f, LB, Le) - sigma_corr(q, cf);
+    return cell_op_corr_parts(parts2_of(e, B), B.c, e.c, cf);
 }
 
 template <typename T>

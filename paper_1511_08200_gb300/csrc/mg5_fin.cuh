@@ -74,18 +74,20 @@ __device__ __forceinline__ void finalize_body(const double2 *partials, int nb, d
 }
 
 // Called by every thread of every block after thread 0 has written the block's partial.
+// The partials are indexed by the linear block index (x fastest).
 __device__ __forceinline__ void finalize_if_last(double2 *partials, const Fin &fin)
 {
     __shared__ int s_last;
+    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
     if (threadIdx.x == 0) {
         __threadfence();   // the partial before the count
-        s_last = atomicAdd(fin_counter(partials), 1u) == gridDim.x - 1;
+        s_last = atomicAdd(fin_counter(partials), 1u) == nblk - 1;
     }
     __syncthreads();
     if (!s_last)
         return;
     __threadfence();
-    finalize_body(partials, gridDim.x, fin.ncells, fin.ls, fin.mode);
+    finalize_body(partials, (int)nblk, fin.ncells, fin.ls, fin.mode);
     if (threadIdx.x == 0)
         *fin_counter(partials) = 0u;
 }

@@ -151,6 +151,13 @@ cudaError_t launch_resid_restrict(const T *v, const T *f, const double *cptr, in
                                   CoefT<T> cf, T *vc, T *v0c, T *rc, double2 *partials,
                                   int *nblocks, cudaStream_t st, const T *B = nullptr,
                                   const Fin &fin = Fin());
+// the same for the FP32 correction form (B required) as a column march (k_march_resid.cu):
+// n a multiple of 32; the coarse values equal the gather kernel's to the bit
+bool resid_march_ok(int n);
+cudaError_t launch_resid_restrict_march(const float *e, const float *f, const double *cptr, int n,
+                                        CoefT<float> cf, float *vc, float *v0c, float *rc,
+                                        double2 *partials, int *nblocks, cudaStream_t st,
+                                        const float *B, const Fin &fin = Fin());
 // coarse = 8-child mean of fine
 template <typename T>
 cudaError_t launch_restrict(const T *fine, int n, T *coarse, cudaStream_t st);

@@ -146,10 +146,16 @@ struct RunMix {
         int nb = 0;
         ProfScope ps(sh.prof, PK_RESTRICT32, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
         const double n3 = (double)h->n[l] * h->n[l] * h->n[l];
-        cudaError_t e = launch_resid_restrict<float>(h->e[l], h->f[l], c(l), h->n[l],
-                                                     make_coef<float>(hl[l], p->alpha), h->e[l + 1],
-                                                     h->e0[l + 1], h->f[l + 1], sh.partials, &nb,
-                                                     st, h->B[l], Fin{ls(l), FIN_RESID, n3});
+        const CoefT<float> cf = make_coef<float>(hl[l], p->alpha);
+        const Fin fin{ls(l), FIN_RESID, n3};
+        cudaError_t e =
+            resid_march_ok(h->n[l])
+                ? launch_resid_restrict_march(h->e[l], h->f[l], c(l), h->n[l], cf, h->e[l + 1],
+                                              h->e0[l + 1], h->f[l + 1], sh.partials, &nb, st,
+                                              h->B[l], fin)
+                : launch_resid_restrict<float>(h->e[l], h->f[l], c(l), h->n[l], cf, h->e[l + 1],
+                                               h->e0[l + 1], h->f[l + 1], sh.partials, &nb, st,
+                                               h->B[l], fin);
         return e == cudaSuccess ? MG5_OK : fail("resid_restrict32", e);
     }
 

@@ -248,3 +248,29 @@ def test_march_refuses_sizes_it_does_not_tile(ctx):
     z = torch.zeros((32,) * 3, dtype=torch.float32, device="cuda")
     with pytest.raises(mg.MG5Error):
         ctx.step_sweep_f32(z, z, 0.0, h, alpha, fused=2)   # no base
+
+
+@pytest.mark.parametrize("n", [32, 64, 96])
+def test_resid_restrict_march_equals_gather_fp32(ctx, n):
+    """The column-march residual + restriction of the FP32 correction equation gives the gather
+    kernel's coarse e and coarse r to the bit, the residual statistics to FP32 summation order;
+    and the coarse residual is the 8-child mean of the oracle's residual of B + e."""
+    alpha, s, h = nominal()
+    B = _base_field(n, 34, 1.0)
+    e = 1e-2 * B * (1.0 + 0.1 * workload.lognormal_delta(n, 1.0, 35))
+    rhs = 1e-2 * s * workload.lognormal_delta(n, 1.0, 36)
+    c = 3e-12
+    args = (_f32(e), _f32(rhs), _f32(B), c, h, alpha)
+    ec0, rc0, st0 = ctx.step_resid_restrict_f32(*args, march=False)
+    ec1, rc1, st1 = ctx.step_resid_restrict_f32(*args, march=True)
+    assert np.array_equal(host(ec0), host(ec1)) and np.array_equal(host(rc0), host(rc1))
+    assert st1[0] == pytest.approx(st0[0], rel=1e-5, abs=1e-6 * st0[1] / n ** 1.5)
+    assert st1[1] == pytest.approx(st0[1], rel=1e-5)
+    Bq = np.asarray(B, dtype=np.float32).astype(np.float64)
+    eq = np.asarray(e, dtype=np.float32).astype(np.float64)
+    fq = np.asarray(rhs, dtype=np.float32).astype(np.float64)
+    r = oracle.residual(Bq + eq, oracle.operator(Bq, h, alpha) + fq, c, h, alpha)
+    rref = oracle.restrict(r)
+    got = host(rc1).astype(np.float64)
+    assert np.abs(got - rref).max() <= 2e-3 * np.abs(rref).max()
+    assert np.abs(host(ec1) - oracle.restrict(eq)).max() <= 1e-6 * np.abs(eq).max()
