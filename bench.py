@@ -57,9 +57,9 @@ SURVEY_FLOPS_SWEEP64 = 62.0
 WORK = {
     "sweep64": ("alu", 24.0, 40.0),
     "patch_sweep64": ("alu", 24.0, 40.0),
-    "resid_restrict64": ("alu", 18.0, 38.0),
+    "resid_restrict64": ("alu", 19.0, 38.0),    # read v, f; write vc, v0c, rc (1/8 each)
     "sweep32": ("hbm", 16.0, 60.0),          # correction form: read e, B, f; write e
-    "resid_restrict32": ("hbm", 12.5, 60.0),
+    "resid_restrict32": ("hbm", 13.5, 60.0),    # read e, B, f; write vc, v0c, rc
     "resid64_mixed": ("alu", 24.0, 36.0),     # read phi64, f64; write r32, B32
     "update_mixed": ("hbm", 20.0, 1.0),
     "force64": ("hbm", 32.0, 6.0),
@@ -74,10 +74,12 @@ WORK = {
 
 # DRAM bytes per cell measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch / its cells), for the kernel as it stands; a launch's traffic = this x its cells.
-#   sweep32: k_sweep_fused<float,1>, 256^3 finest-grid launch: 280.3 MB / 16.78 M cells
+#   sweep32: k_sweep_march, 256^3 finest-grid launch: 204.6 + 50.9 MB / 16.78 M cells
+#   resid_restrict32: k_resid_restrict_march, 256^3 finest grid: 203.1 + 19.5 MB / 16.78 M cells
 #   sweep64: k_sweep_red + k_sweep_black<double,0>, 128^3 finest grid
 TRAFFIC_PER_CELL = {
-    "sweep32": 280.3e6 / 256 ** 3,
+    "sweep32": 255.4e6 / 256 ** 3,
+    "resid_restrict32": 222.6e6 / 256 ** 3,
     "sweep64": 84.4e6 / 128 ** 3,          # red + black launch, cold-cache ncu capture at 128^3
 }
 

@@ -32,9 +32,11 @@ constexpr int kScalSlots = 48;   // LevelScal slots held by a context
 constexpr int kPatchSlot = 16;   // slot used by the patch relaxation
 constexpr int kStepSlot = 17;    // slot used by the single-step entry points
 constexpr int kInnerBase = 20;   // first slot of the mixed solve's FP32 grids
-constexpr int kMaxPartials = 8192;  // partial-sum slots (double2) per reduction
-// blocks of a residual-statistics reduction: each writes one Moments (two slots)
-constexpr int kMomentBlocks = kMaxPartials / 2;
+constexpr int kMaxPartials = 8192;  // partial-sum slots (double2) per reduction; the last one
+                                    // holds the last-block counter of the in-kernel finalize
+// blocks of a residual-statistics reduction: each writes one Moments (two slots), and the
+// Moments that would share the counter's slot is left out
+constexpr int kMomentBlocks = kMaxPartials / 2 - 1;
 // Grid caps of the reduction kernels (grid-stride loops).  The one-block finalize spends
 // FP64 instructions on every partial, and FP64 runs at 1/64 of the FP32 rate here, so
 // the partials are kept few: FP64-bound producers use 4 blocks of 256 per SM (152 SMs),
