@@ -139,7 +139,7 @@ __global__ void k_residual(const T *__restrict__ phi, const T *__restrict__ f,
         const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
         St<T> s;
         gather(phi, phi, r, k, kp, km, s);
-        const T res = f[t] + (T)c - cell_op(s, cf);
+        const T res = cell_residual(s, f[t] + (T)c, cf);
         if (r_out)
             r_out[t] = res;
         acc.add(res);
@@ -193,7 +193,7 @@ __global__ void k_resid_restrict(const T *__restrict__ v, const T *__restrict__ 
             gather(v, v, r, k, kp, km, s);
             if constexpr (BASE)
                 gather(B, B, r, k, kp, km, sb);
-            const T res = f[r.r00 + k] + (T)c - opr<T, BASE>(s, sb, cf);
+            const T res = resid_of<T, BASE>(s, sb, f[r.r00 + k] + (T)c, cf);
             sv += s.c;
             sr += res;
             acc.add(res);
@@ -280,7 +280,10 @@ __global__ void k_coarse_rhs(const T *__restrict__ vc, T *__restrict__ fc,
     gather(vc, vc, r, k, kp, km, s);
     if constexpr (BASE)
         gather(B, B, r, k, kp, km, sb);
-    fc[t] = opr<T, BASE>(s, sb, cf) + fc[t] - (T)(*m_fine);
+    if constexpr (BASE)
+        fc[t] = opr<T, BASE>(s, sb, cf) + fc[t] - (T)(*m_fine);
+    else   // op + fc - m as -(m - fc - op): the residual chain's FP64 operation count
+        fc[t] = -cell_residual(s, (T)(*m_fine) - fc[t], cf);
 }
 
 template <typename T>
@@ -331,8 +334,10 @@ __global__ void k_prolong_add(const T *__restrict__ vc, const T *__restrict__ v0
     ii[0] = I == 0 ? nc - 1 : I - 1, ii[1] = I, ii[2] = I == nc - 1 ? 0 : I + 1;
     jj[0] = J == 0 ? nc - 1 : J - 1, jj[1] = J, jj[2] = J == nc - 1 ? 0 : J + 1;
     kk[0] = K == 0 ? nc - 1 : K - 1, kk[1] = K, kk[2] = K == nc - 1 ? 0 : K + 1;
-    const T w0 = (T)0.75, w1 = (T)0.25;
-    // along k: Z[a][b][c] for child c (0: 2K, 1: 2K+1)
+    // Weights (3/4, 1/4) per axis, applied as 3 x + y with the three factors 1/4 folded into
+    // one 1/64 at the end: one FP64 multiply-add a stage instead of a multiply and an add
+    // (the FP64 correction is FP64-pipe bound on GB300).  Along k: Z[a][b][c] for child c
+    // (0: 2K, 1: 2K+1).
     T Z[3][3][2];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -343,29 +348,34 @@ __global__ void k_prolong_add(const T *__restrict__ vc, const T *__restrict__ v0
 #pragma unroll
             for (int c = 0; c < 3; ++c)
                 e[c] = v0c ? vc[row + kk[c]] - v0c[row + kk[c]] : vc[row + kk[c]];
-            Z[a][b][0] = w0 * e[1] + w1 * e[0];
-            Z[a][b][1] = w0 * e[1] + w1 * e[2];
+            Z[a][b][0] = fma((T)3, e[1], e[0]);
+            Z[a][b][1] = fma((T)3, e[1], e[2]);
         }
+    // along j: Y[a][cj][ck], shared by both children along i
+    T Y[3][2][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int cj = 0; cj < 2; ++cj)
+#pragma unroll
+            for (int ck = 0; ck < 2; ++ck)
+                Y[a][cj][ck] = fma((T)3, Z[a][1][ck], Z[a][cj ? 2 : 0][ck]);
     const int n = 2 * nc;
+    const T w = (T)(1.0 / 64.0);
 #pragma unroll
     for (int ci = 0; ci < 2; ++ci)
 #pragma unroll
         for (int cj = 0; cj < 2; ++cj) {
             T out[2];
 #pragma unroll
-            for (int ck = 0; ck < 2; ++ck) {
-                T y[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    y[a] = w0 * Z[a][1][ck] + w1 * Z[a][cj ? 2 : 0][ck];
-                out[ck] = w0 * y[1] + w1 * y[ci ? 2 : 0];
-            }
+            for (int ck = 0; ck < 2; ++ck)
+                out[ck] = fma((T)3, Y[1][cj][ck], Y[ci ? 2 : 0][cj][ck]);
             const long long f = ((long long)(2 * I + ci) * n + (2 * J + cj)) * n + 2 * K;
             using V = typename Vec2<T>::type;
             V *p = reinterpret_cast<V *>(vf + f);
             V v = *p;
-            v.x += out[0];
-            v.y += out[1];
+            v.x = fma(out[0], w, v.x);
+            v.y = fma(out[1], w, v.y);
             *p = v;
         }
 }
@@ -442,7 +452,7 @@ __global__ void __launch_bounds__(kCoarsestThreads)
                 gather_nbr((const T *)a, nb, s);
                 if constexpr (BASE)
                     gather_nbr(bs, nb, sb);
-                const double res = (double)(fme - opr<T, BASE>(s, sb, cf));
+                const double res = (double)resid_of<T, BASE>(s, sb, fme, cf);
                 acc.x = res;
                 acc.y = res * res;
             }
@@ -492,7 +502,7 @@ __global__ void __launch_bounds__(kCoarsestThreads)
             gather((const T *)a, (const T *)a, r, k, kp, km, s);
             if constexpr (BASE)
                 gather(bs, bs, r, k, kp, km, sb);
-            const double res = (double)(ff[p] - opr<T, BASE>(s, sb, cf));
+            const double res = (double)resid_of<T, BASE>(s, sb, ff[p], cf);
             acc.x += res;
             acc.y += res * res;
         }
@@ -981,7 +991,7 @@ __global__ void k_patch_residual(const double *__restrict__ phi, const double *_
         const Rows r = box_rows(p1 + 2, p2 + 2, i + 1, j + 1);
         St<double> s;
         gather(phi, phi, r, k + 1, k + 2, k, s);
-        const double res = fint[t] + rhs_add - cell_op(s, cf);
+        const double res = cell_residual(s, fint[t] + rhs_add, cf);
         acc.x += res;
         acc.y += res * res;
     }

@@ -55,7 +55,7 @@ __global__ void k_pbox_resid_restrict(const double *__restrict__ v, const double
             St<double> s;
             gather(v, v, r, k + 1, k + 2, k, s);
             const long long fi = ((long long)i * p1 + j) * p2 + k;
-            const double res = (MASKED && !mask[fi]) ? 0.0 : f[fi] - cell_op(s, cf);
+            const double res = (MASKED && !mask[fi]) ? 0.0 : cell_residual(s, f[fi], cf);
             sv += s.c;
             sr += res;
             acc.x += res;
@@ -87,7 +87,7 @@ __global__ void k_pbox_coarse_rhs(const double *__restrict__ vc, double *__restr
     const Rows r = box_rows(q1 + 2, q2 + 2, i + 1, j + 1);
     St<double> s;
     gather(vc, vc, r, k + 1, k + 2, k, s);
-    fc[t] = cell_op(s, cf) + fc[t];
+    fc[t] = -cell_residual(s, -fc[t], cf);   // op + fc
 }
 
 // fine interior += trilinear interpolation of (vc - v0c), ghosts included (the
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kPboxThreads)
             if (active) {
                 St<double> s;
                 gather_nbr((const double *)a, nb, s);
-                const double res = fme - cell_op(s, cf);
+                const double res = cell_residual(s, fme, cf);
                 acc.y = res * res;
             }
             acc = block_sum2(acc);
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kPboxThreads)
             const Rows r = box_rows(d1, d2, i + 1, j + 1);
             St<double> s;
             gather((const double *)a, (const double *)a, r, k + 1, k + 2, k, s);
-            const double res = ff[p] - cell_op(s, cf);
+            const double res = cell_residual(s, ff[p], cf);
             acc.y += res * res;
         }
         acc = block_sum2(acc);

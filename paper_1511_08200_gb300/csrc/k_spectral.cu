@@ -48,7 +48,7 @@ __global__ void k_spec_residual(const T *__restrict__ v, const T *__restrict__ f
         gather(v, v, r, k, kp, km, s);
         if constexpr (BASE)
             gather(B, B, r, k, kp, km, sb);
-        const T res = f[t] + (T)(*cptr) - opr<T, BASE>(s, sb, cf);
+        const T res = resid_of<T, BASE>(s, sb, f[t] + (T)(*cptr), cf);
         out[t].x = res;
         out[t].y = (T)0;
         acc.add(res);

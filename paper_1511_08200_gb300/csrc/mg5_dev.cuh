@@ -34,6 +34,9 @@ struct CoefT {
     T k43h;      // (4 alpha / 3) / h^2: beta' = 1 + k43h (S_B - 6 B_c)
     T inv2k23;   // 1 / (2 k23) (0 when alpha = 0, where it is never used)
     T om1;       // omega - 1: a smoothing update is v + omega (v_root - v)
+    int relaxed;   // om1 != 0, as an integer: the FP64 sweeps test it per cell, and an FP64
+                   // compare would run on the FP64 pipe
+    T k23i4;     // (2 alpha / 3) / h^4: op = Lh (1/h^2 + k23i4 Lh) - ..., Lh = h^2 L
     T w6;        // omega / 6: ... = (omega / 6) (S - h^2 L) + (1 - omega) v
     T omc;       // 1 - omega
 };
@@ -56,6 +59,8 @@ __host__ __device__ inline CoefT<T> make_coef(double h, double alpha, double ome
     c.k43h = (T)(4.0 * alpha / (3.0 * h * h));
     c.inv2k23 = (T)(alpha > 0.0 ? 3.0 / (4.0 * alpha) : 0.0);
     c.om1 = (T)(omega - 1.0);
+    c.relaxed = omega != 1.0;
+    c.k23i4 = (T)(2.0 * alpha / (3.0 * h4));
     c.w6 = (T)(omega / 6.0);
     c.omc = (T)(1.0 - omega);
     return c;
@@ -243,6 +248,39 @@ __device__ __forceinline__ float physical_root(float b, const CoefT<float> &cf, 
     return physical_root(b, cf.k8, clamped);
 }
 
+// ---- FP64 <-> FP32 conversions on the integer pipes ---------------------------
+// GB300 executes the F2F conversions between FP64 and FP32 on the FP64 pipe at the FP64
+// rate, so in the FP64-bound kernels (the FP64 smoother, the mixed mode's FP64 residual)
+// each conversion costs as much as an FP64 add.  These give the same values from the bit
+// patterns with a few integer instructions, for every input in FP32's normal range (and
+// zero, infinities and NaN); FP32 subnormals are flushed to zero (values below 1.2e-38,
+// which the fields and residuals here do not reach).
+__device__ __forceinline__ float f64_to_f32_rn(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned ed = (hi >> 20) & 0x7ffu;
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // the 23 kept fraction bits
+    const unsigned rest = lo & 0x1fffffffu;                     // the 29 dropped ones
+    // round to nearest, ties to even; a carry out of the fraction steps the exponent
+    // (up to infinity), as rounding does
+    const unsigned up = (rest > 0x10000000u) | ((rest == 0x10000000u) & m);
+    unsigned bits = (((ed - 896u) << 23) | m) + up;
+    bits = ed <= 896u ? 0u : bits;
+    bits = ed >= 1151u ? ((ed == 2047u && (m | rest) != 0u) ? 0x7fc00000u : 0x7f800000u) : bits;
+    return __uint_as_float((hi & 0x80000000u) | bits);
+}
+
+__device__ __forceinline__ double f32_to_f64(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    unsigned hi = ((u & 0x7fffffffu) >> 3) + (896u << 20);   // exponent + 1023 - 127
+    hi = e == 0u ? 0u : hi;
+    hi = e == 255u ? hi + (896u << 20) : hi;                  // infinity, NaN: exponent 2047
+    const unsigned lo = e == 0u ? 0u : (u << 29);
+    return __hiloint2double((int)((u & 0x80000000u) | hi), (int)lo);
+}
+
 __device__ __forceinline__ double physical_root(double b, const CoefT<double> &cf, bool &clamped)
 {
 #ifdef MG5_IEEE_ROOT
@@ -253,7 +291,7 @@ __device__ __forceinline__ double physical_root(double b, const CoefT<double> &c
     }
     return 2.0 * b / (1.0 + sqrt(disc));
 #else
-    const float bf = (float)b;
+    const float bf = f64_to_f32_rn(b);
     const float df = fmaf(cf.k8f, bf, 1.0f);
     if (df < 0.25f) {
         const double disc = fma(cf.k8, b, 1.0);
@@ -264,8 +302,8 @@ __device__ __forceinline__ double physical_root(double b, const CoefT<double> &c
         return 2.0 * b / (1.0 + sqrt(disc));
     }
     const float Lf = __fdividef(2.0f * bf, 1.0f + sqrtf(df));
-    const double r = (double)__frcp_rn(fmaf(cf.k43f, Lf, 1.0f));
-    const double L = (double)Lf;
+    const double r = f32_to_f64(__frcp_rn(fmaf(cf.k43f, Lf, 1.0f)));
+    const double L = f32_to_f64(Lf);
     return fma(-fma(fma(cf.k23, L, 1.0), L, -b), r, L);
 #endif
 }
@@ -279,7 +317,7 @@ __device__ __forceinline__ T cell_update(const St<T> &s, T rhs, const CoefT<T> &
     const T b = rhs + cf.s8 * d2 + cf.s23 * t;   // rhs + alpha Sigma
     const T L = physical_root(b, cf, clamped);
     const T r6 = S - cf.h2 * L;   // 6 v_root
-    return cf.om1 != (T)0 ? cf.w6 * r6 + cf.omc * s.c : r6 * (T)(1.0 / 6.0);
+    return cf.relaxed ? cf.w6 * r6 + cf.omc * s.c : r6 * (T)(1.0 / 6.0);
 }
 
 // op(phi) at the cell = L + alpha((2/3) L^2 - Sigma).
@@ -290,6 +328,20 @@ __device__ __forceinline__ T cell_op(const St<T> &s, const CoefT<T> &cf)
     stencil_parts(s, S, t, d2);
     const T L = (S - (T)6 * s.c) * cf.inv_h2;
     return L + cf.k23 * L * L - cf.s8 * d2 - cf.s23 * t;
+}
+
+// fc - op(phi) at the cell (fc = f + c), op in units of Lh = h^2 L = S - 6 v:
+// op = Lh (1/h^2 + k23i4 Lh) - s8 d2 - s23 t, so that after the stencil parts the residual
+// is one FP64 add and five fused multiply-adds (cell_op then a subtraction take eight).
+template <typename T>
+__device__ __forceinline__ T cell_residual(const St<T> &s, T fc, const CoefT<T> &cf)
+{
+    T S, t, d2;
+    stencil_parts(s, S, t, d2);
+    const T Lh = fma((T)-6, s.c, S);
+    const T u = fma(cf.k23i4, Lh, cf.inv_h2);
+    const T r = fma(cf.s8, d2, fma(-Lh, u, fc));
+    return fma(cf.s23, t, r);
 }
 
 // ---- correction form (mixed precision) -------------------------------------
@@ -349,7 +401,7 @@ __device__ __forceinline__ T cell_update_corr(const St<T> &e, const St<T> &B, T 
     const T sq = sqrt(disc);
     const T L = bp >= (T)0 ? (T)2 * b / (bp + sq) : (sq - bp) / ((T)2 * cf.k23);
     const T r6 = pe.S - cf.h2 * L;
-    return cf.om1 != (T)0 ? cf.w6 * r6 + cf.omc * e.c : r6 * (T)(1.0 / 6.0);
+    return cf.relaxed ? cf.w6 * r6 + cf.omc * e.c : r6 * (T)(1.0 / 6.0);
 }
 
 // FP32 correction form, the inner sweep of the mixed mode.  The same update as the
@@ -492,6 +544,16 @@ __device__ __forceinline__ T opr(const St<T> &s, const St<T> &B, const CoefT<T> 
         return cell_op_corr(s, B, cf);
     else
         return cell_op(s, cf);
+}
+
+// fc - opr: the residual of a cell with right-hand side fc
+template <typename T, bool BASE>
+__device__ __forceinline__ T resid_of(const St<T> &s, const St<T> &B, T fc, const CoefT<T> &cf)
+{
+    if constexpr (BASE)
+        return fc - cell_op_corr(s, B, cf);
+    else
+        return cell_residual(s, fc, cf);
 }
 
 // ---- residual statistics -----------------------------------------------------

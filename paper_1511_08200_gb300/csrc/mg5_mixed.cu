@@ -48,7 +48,7 @@ __global__ void k_resid64_mixed(const double *__restrict__ phi, const double *__
          t += (long long)gridDim.x * blockDim.x) {
         if constexpr (ZERO) {
             const double res = f[t] + c;
-            r32[t] = (float)res;
+            r32[t] = f64_to_f32_rn(res);
             B[t] = 0.0f;
             acc.add(res);
             continue;
@@ -60,9 +60,9 @@ __global__ void k_resid64_mixed(const double *__restrict__ phi, const double *__
         const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
         St<double> s;
         gather(phi, phi, r, k, kp, km, s);
-        const double res = f[t] + c - cell_op(s, cf);
-        r32[t] = (float)res;
-        B[t] = (float)s.c;
+        const double res = cell_residual(s, f[t] + c, cf);
+        r32[t] = f64_to_f32_rn(res);
+        B[t] = f64_to_f32_rn(s.c);
         acc.add(res);
     }
     const Moments m = block_moments(acc);
@@ -75,7 +75,7 @@ __global__ void k_update_mixed(double *__restrict__ phi, const float *__restrict
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n3)
-        phi[t] += (double)e[t];
+        phi[t] += f32_to_f64(e[t]);
 }
 
 // scalar bookkeeping: 0: a.c -= a.m ; 1: b.c = -a.m ; 2: a.c += b.c

@@ -45,7 +45,7 @@ __global__ void k_residual_partials(const double *__restrict__ phi, const double
         const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
         St<double> s;
         gather(phi, phi, r, k, kp, km, s);
-        acc.add(f[t] + c - cell_op(s, cf));
+        acc.add(cell_residual(s, f[t] + c, cf));
     }
     const Moments m = block_moments(acc);
     if (threadIdx.x == 0)
