@@ -317,6 +317,8 @@ cudaError_t prepare_fused_kernels()
                                  (int)sizeof(FusedSmem<double, false>));
     if (e == cudaSuccess)
         e = prepare_march_kernel();
+    if (e == cudaSuccess)
+        e = prepare_resid_march_kernel();
     return e;
 }
 

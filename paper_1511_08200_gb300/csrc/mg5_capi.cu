@@ -1207,10 +1207,7 @@ int mg5_solve_fifth_force(mg5_ctx *ctx, const double *delta, int N, const mg5_pa
     CK(cudaMemcpyAsync(tail + 1, &ctx->ls[0].mean, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(ctx_wait(ctx, st));
     ctx->prof.resolve();
-    if (cnt.clamped & kSweepFaultBit) {
-        ctx->err = "a sweep's wait for its input planes gave up";
-        status = MG5_E_CUDA;
-    } else if (status == MG5_OK && cnt.clamped > 0)
+    if (status == MG5_OK && cnt.clamped > 0)
         status = MG5_W_DISC_CLAMP;
     if (info) {
         float ms = 0.f;
@@ -1557,10 +1554,7 @@ static int relax_patch_impl(mg5_ctx *ctx, const double *delta_f, const int pf[3]
     CK(cudaMemcpyAsync(&cnt, ctx->cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     CK(ctx_wait(ctx, st));
     ctx->prof.resolve();
-    if (cnt.clamped & kSweepFaultBit) {
-        ctx->err = "a sweep's wait for its input planes gave up";
-        status = MG5_E_CUDA;
-    } else if (status == MG5_OK && cnt.clamped > 0)
+    if (status == MG5_OK && cnt.clamped > 0)
         status = MG5_W_DISC_CLAMP;
     if (info) {
         float ms = 0.f;
@@ -2110,9 +2104,7 @@ int graph_finish(GraphEntry *g, mg5_info *info)
         info->coarse_sweeps = cnt.coarse_sweeps;
         info->disc_clamped = (long long)cnt.clamped;
     }
-    if (cnt.clamped & kSweepFaultBit)
-        status = MG5_E_CUDA;   // a sweep's wait for its input planes gave up
-    else if (status == MG5_OK && cnt.clamped > 0)
+    if (status == MG5_OK && cnt.clamped > 0)
         status = MG5_W_DISC_CLAMP;
     g->busy = false;
     return status;
@@ -2559,10 +2551,7 @@ int mg5_solve_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const in
         const CaptureStats &cs = b->stats[i];
         count_launch(cs.launches_fixed + cs.launches_per_iter * ctl[i].outer);
         int status = ctl[i].status;
-        if (cnt[i].clamped & kSweepFaultBit) {
-            ctx->err = "a sweep's wait for its input planes gave up";
-            status = MG5_E_CUDA;
-        } else if (status == MG5_OK && cnt[i].clamped > 0)
+        if (status == MG5_OK && cnt[i].clamped > 0)
             status = MG5_W_DISC_CLAMP;
         if (status < 0 || (worst == MG5_OK && status > 0))
             worst = status;

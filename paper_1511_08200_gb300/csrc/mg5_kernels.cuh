@@ -102,15 +102,13 @@ inline bool fused_ok(int n)
     return n >= kFusedMinN && n % (int)(16 / sizeof(T)) == 0;
 }
 cudaError_t prepare_fused_kernels();
-// FP32 correction-form sweep as a column march (k_march.cu): 32 x 32 tiles, n a multiple
-// of 32, B required; `chunk` planes per CTA (0: about three waves over 152 SMs)
+// FP32 correction-form sweep as a column march (k_march.cu): 16 x 32 tiles, n a multiple
+// of 32, B required; `chunk` planes per CTA (0: about six waves of two CTAs per SM)
 bool march_ok(int n);
 cudaError_t launch_sweep_march(const float *in, float *out, const float *f, const float *B,
                                const double *cptr, int n, CoefT<float> cf,
                                unsigned long long *clamp, cudaStream_t st, int chunk = 0);
 cudaError_t prepare_march_kernel();
-// set in a clamp counter by a sweep whose wait for its input planes gave up (never expected)
-constexpr unsigned long long kSweepFaultBit = 1ull << 63;
 
 // How one grid side is swept (speed only: every schedule computes the same values).
 struct SweepSchedule {
@@ -156,6 +154,7 @@ cudaError_t launch_resid_restrict(const T *v, const T *f, const double *cptr, in
 // the same for the FP32 correction form (B required) as a column march (k_march_resid.cu):
 // n a multiple of 32; the coarse values equal the gather kernel's to the bit
 bool resid_march_ok(int n);
+cudaError_t prepare_resid_march_kernel();
 cudaError_t launch_resid_restrict_march(const float *e, const float *f, const double *cptr, int n,
                                         CoefT<float> cf, float *vc, float *v0c, float *rc,
                                         double2 *partials, int *nblocks, cudaStream_t st,

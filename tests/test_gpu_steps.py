@@ -250,11 +250,12 @@ def test_march_refuses_sizes_it_does_not_tile(ctx):
         ctx.step_sweep_f32(z, z, 0.0, h, alpha, fused=2)   # no base
 
 
-@pytest.mark.parametrize("n", [32, 64, 96])
+@pytest.mark.parametrize("n", [32, 64, 96, 128, 160])
 def test_resid_restrict_march_equals_gather_fp32(ctx, n):
     """The column-march residual + restriction of the FP32 correction equation gives the gather
     kernel's coarse e and coarse r to the bit, the residual statistics to FP32 summation order;
-    and the coarse residual is the 8-child mean of the oracle's residual of B + e."""
+    and the coarse residual is the 8-child mean of the oracle's residual of B + e.  At 128 and
+    160 the CTAs' shares of (tile, plane pair) units cross tile boundaries."""
     alpha, s, h = nominal()
     B = _base_field(n, 34, 1.0)
     e = 1e-2 * B * (1.0 + 0.1 * workload.lognormal_delta(n, 1.0, 35))
