@@ -450,9 +450,10 @@ int mg5_server_destroy(mg5_server *srv);
  *   r = f + c - op(phi) on the periodic N^3 grid, op the operator of Eq. (eomvarphi)
  *   (phi, f: device, N^3 doubles, row-major, not modified; c, h, alpha as in the solve).
  * Each of at most 4096 blocks (256 threads, two cells a thread) reduces its
- * cells to (count, mean, sum of squared deviations); the blocks are combined
- * pairwise (Chan, Golub and LeVeque), so ||r - mean r|| keeps its accuracy when
- * |mean r| is far above the spread of r.  The block results live in a fixed
+ * cells to (count, shift, sum and sum of squares of the deviations from the
+ * shift), the shift one of its own residuals; the blocks are moved onto one shift
+ * and summed in block order, so ||r - mean r|| keeps its accuracy when |mean r| is
+ * far above the spread of r.  The block results live in a fixed
  * file-scope device array of 4096 x 32 bytes (128 KiB), held by every GPU that
  * loads the library until the process exits: N^3 may be at most
  * mg5_residual_norm_noalloc_max_cells() (2,097,152, i.e. N <= 128); larger grids
@@ -517,6 +518,27 @@ int mg5_step_restrict(mg5_ctx *ctx, const double *fine, int N, double *coarse, v
 /* fine += cell-centred trilinear interpolation of coarse; Nc = coarse side */
 int mg5_step_prolong_add(mg5_ctx *ctx, const double *coarse, int Nc, double *fine,
                          void *stream);
+
+/* ------------------------------------------------------------ range-checked build
+ * Debugging aids with no counterpart in the paper.  The library can be built with
+ * -DMG5_BOUNDS (libmg5_bounds.so): every element a kernel reads or writes in global
+ * memory is checked against the device allocations the library knows -- its own, each
+ * registered at allocation, and the caller buffers noted with mg5_bounds_note -- and
+ * shared-memory elements against the CTA's shared memory.  A violation does not fault:
+ * the access is redirected to a scratch word (an asynchronous copy is skipped) and the
+ * first violation per source file is recorded on the device.  The checks slow every
+ * kernel by a large factor; results of a run without violations are those of the
+ * ordinary build.  In the ordinary build these entry points do nothing. */
+/* 1 in the range-checked build, 0 otherwise. */
+int mg5_bounds_build(void);
+/* Note the device allocation that contains p (a caller buffer) as readable and writable
+ * by the kernels; MG5_E_ARG if p is not device memory.  MG5_OK (nothing done) in the
+ * ordinary build. */
+int mg5_bounds_note(const void *p);
+/* Read and clear the recorded violations: 1 if any, with "file: line L: kind out of
+ * range" for the first one written to msg (cap bytes, NUL-terminated), else 0.  Call it
+ * after the device work has finished (a stream or device synchronisation). */
+int mg5_bounds_check(char *msg, int cap);
 
 #ifdef __cplusplus
 }

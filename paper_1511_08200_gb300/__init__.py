@@ -6,6 +6,11 @@ arguments: every step of the solve runs in the library's CUDA kernels.
 Device fields are torch CUDA tensors (float64, C-contiguous); PyTorch is used
 for device memory and streams only.  There is no CPU fallback: if the
 library has not been built, importing this package raises.
+
+With MG5_BOUNDS=1 in the environment the range-checked build libmg5_bounds.so
+is loaded instead (``python -m paper_1511_08200_gb300._build --bounds``); every
+tensor handed to it is noted as a buffer its kernels may touch, and
+``bounds_check()`` reports the first out-of-range access since the last call.
 """
 from __future__ import annotations
 
@@ -14,12 +19,15 @@ import os
 from dataclasses import dataclass, field
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libmg5.so")
+_BOUNDS = os.environ.get("MG5_BOUNDS", "0") == "1"
+_LIB_PATH = os.path.join(_HERE, "libmg5_bounds.so" if _BOUNDS else "libmg5.so")
 
 if not os.path.exists(_LIB_PATH):
     raise ImportError(
-        "libmg5.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
-        "(nvcc, sm_103a) before importing paper_1511_08200_gb300")
+        "%s is not built; run %s (nvcc, sm_103a) before importing paper_1511_08200_gb300"
+        % (os.path.basename(_LIB_PATH),
+           "`python -m paper_1511_08200_gb300._build --bounds`" if _BOUNDS
+           else "`python -c 'import __graft_entry__ as g; g.build()'`"))
 
 _lib = ctypes.CDLL(_LIB_PATH)
 
@@ -139,6 +147,9 @@ _sigs = {
     "mg5_tune_load": ([ctypes.c_char_p], _c_int),
     "mg5_residual_norm_noalloc": ([_P, _P, _c_double, _c_int, _c_double, _c_double, _P, _P], _c_int),
     "mg5_residual_norm_noalloc_max_cells": ([], ctypes.c_longlong),
+    "mg5_bounds_build": ([], _c_int),
+    "mg5_bounds_note": ([_P], _c_int),
+    "mg5_bounds_check": ([ctypes.c_char_p, _c_int], _c_int),
     "mg5_profile_enable": ([_P, _c_int], _c_int),
     "mg5_profile_read": ([_P, _P, _P, _c_int], _c_int),
     "mg5_profile_name": ([_c_int], ctypes.c_char_p),
@@ -270,7 +281,22 @@ def _ptr(t, dtype="float64", device=None) -> int:
     if device is not None and (t.device.index or 0) != device:
         raise MG5Error(E_ARG, "tensor on cuda:%d, the context is on cuda:%d"
                        % (t.device.index or 0, device))
+    if _BOUNDS:
+        _lib.mg5_bounds_note(t.data_ptr())
     return t.data_ptr()
+
+
+def bounds_build() -> bool:
+    """True when the loaded library is the range-checked build."""
+    return bool(_lib.mg5_bounds_build())
+
+
+def bounds_check():
+    """The first out-of-range access the range-checked build recorded since the last call
+    ("file: line L: kind out of range"), or None; clears the record.  Synchronise the device
+    first.  Always None in the ordinary build."""
+    buf = ctypes.create_string_buffer(256)
+    return buf.value.decode() if _lib.mg5_bounds_check(buf, 256) else None
 
 
 # Shape checks, made before any pointer reaches the library: a buffer of the wrong size

@@ -4,6 +4,11 @@ Every .cu file under csrc/ is compiled in parallel to an object file, then
 linked into paper_1511_08200_gb300/libmg5.so with the CUDA runtime linked
 statically (no rpath needed; torch and the library share the driver's primary
 context, so torch streams and device pointers pass straight through).
+
+`build(bounds=True)` (or `python -m paper_1511_08200_gb300._build --bounds`) makes the
+range-checked variant libmg5_bounds.so (-DMG5_BOUNDS: every kernel's global and shared
+element accesses checked against the known allocations, violations recorded in a device
+error word instead of faulting); the binding loads it when MG5_BOUNDS=1.
 """
 from __future__ import annotations
 
@@ -19,6 +24,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build", platform.machine())   # objects per host architecture
 LIB = os.path.join(PKG, "libmg5.so")
+LIB_BOUNDS = os.path.join(PKG, "libmg5_bounds.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
@@ -35,19 +41,22 @@ def _needs(obj: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, bounds: bool = False) -> str:
+    obj_dir = OBJ + ("-bounds" if bounds else "")
+    lib = LIB_BOUNDS if bounds else LIB
+    extra = ["-DMG5_BOUNDS"] if bounds else []
+    os.makedirs(obj_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdrs = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "mg5.h")]
     jobs = []
     for s in srcs:
-        o = os.path.join(OBJ, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(obj_dir, os.path.basename(s)[:-3] + ".o")
         if force or _needs(o, [s] + hdrs):
             jobs.append((s, o))
 
     def compile_one(so):
         s, o = so
-        cmd = [NVCC] + _flags() + ["-c", s, "-o", o]
+        cmd = [NVCC] + _flags() + extra + ["-c", s, "-o", o]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,16 +68,16 @@ def build(verbose: bool = False, force: bool = False) -> str:
         for msg in ex.map(compile_one, jobs):
             if verbose and msg:
                 print(msg, file=sys.stderr)
-    objs = [os.path.join(OBJ, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    if force or jobs or not os.path.exists(LIB) or _needs(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    objs = [os.path.join(obj_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    if force or jobs or not os.path.exists(lib) or _needs(lib, objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, bounds="--bounds" in sys.argv))

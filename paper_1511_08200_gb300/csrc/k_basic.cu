@@ -34,17 +34,17 @@ __global__ void k_sweep_red(const T *__restrict__ in, T *__restrict__ out, const
     const int par = (i + j) & 1;
     const int kr = 2 * kk + par, kb = 2 * kk + 1 - par;
     const Rows r = periodic_rows(n, i, j);
-    out[r.r00 + kb] = in[r.r00 + kb];
+    MG5_AT(out, r.r00 + kb) = MG5_AT(in, r.r00 + kb);
     const int kp = (kr == n - 1) ? 0 : kr + 1, km = (kr == 0) ? n - 1 : kr - 1;
     St<T> s, sb;
     gather(in, in, r, kr, kp, km, s);
     if constexpr (BASE)
         gather(B, B, r, kr, kp, km, sb);
     bool cl = false;
-    const T v = upd<T, BASE>(s, sb, f[r.r00 + kr] + (T)(*cptr), cf, cl);
-    out[r.r00 + kr] = v;
+    const T v = upd<T, BASE>(s, sb, MG5_AT(f, r.r00 + kr) + (T)(MG5_AT(cptr, 0)), cf, cl);
+    MG5_AT(out, r.r00 + kr) = v;
     if (cl)
-        atomicAdd(clamp, 1ull);
+        atomicAdd(&MG5_AT(clamp, 0), 1ull);
 }
 
 template <typename T, bool BASE>
@@ -68,10 +68,10 @@ __global__ void k_sweep_black(const T *__restrict__ in, T *out, const T *__restr
     if constexpr (BASE)
         gather(B, B, r, kb, kp, km, sb);
     bool cl = false;
-    const T v = upd<T, BASE>(s, sb, f[r.r00 + kb] + (T)(*cptr), cf, cl);
-    out[r.r00 + kb] = v;
+    const T v = upd<T, BASE>(s, sb, MG5_AT(f, r.r00 + kb) + (T)(MG5_AT(cptr, 0)), cf, cl);
+    MG5_AT(out, r.r00 + kb) = v;
     if (cl)
-        atomicAdd(clamp, 1ull);
+        atomicAdd(&MG5_AT(clamp, 0), 1ull);
 }
 
 template <typename T>
@@ -110,7 +110,7 @@ __global__ void k_operator(const T *__restrict__ phi, int n, CoefT<T> cf, T *__r
     const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
     St<T> s;
     gather(phi, phi, r, k, kp, km, s);
-    out[t] = cell_op(s, cf);
+    MG5_AT(out, t) = cell_op(s, cf);
 }
 
 template <typename T>
@@ -128,7 +128,7 @@ __global__ void k_residual(const T *__restrict__ phi, const T *__restrict__ f,
                            Moments *__restrict__ partials, Fin fin)
 {
     const long long total = (long long)n * n * n;
-    const double c = *cptr;
+    const double c = MG5_AT(cptr, 0);
     MomAcc<T> acc;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
@@ -139,14 +139,14 @@ __global__ void k_residual(const T *__restrict__ phi, const T *__restrict__ f,
         const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
         St<T> s;
         gather(phi, phi, r, k, kp, km, s);
-        const T res = cell_residual(s, f[t] + (T)c, cf);
+        const T res = cell_residual(s, MG5_AT(f, t) + (T)c, cf);
         if (r_out)
-            r_out[t] = res;
+            MG5_AT(r_out, t) = res;
         acc.add(res);
     }
     const Moments m = block_moments(acc);
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = m;
+        MG5_AT(partials, blockIdx.x) = m;
     if (fin.ls)
         finalize_if_last(reinterpret_cast<double2 *>(partials), fin);
 }
@@ -176,7 +176,7 @@ __global__ void k_resid_restrict(const T *__restrict__ v, const T *__restrict__ 
 {
     const int nc = n >> 1;
     const long long total = (long long)nc * nc * nc;
-    const double c = *cptr;
+    const double c = MG5_AT(cptr, 0);
     MomAcc<T> acc;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
@@ -193,19 +193,19 @@ __global__ void k_resid_restrict(const T *__restrict__ v, const T *__restrict__ 
             gather(v, v, r, k, kp, km, s);
             if constexpr (BASE)
                 gather(B, B, r, k, kp, km, sb);
-            const T res = resid_of<T, BASE>(s, sb, f[r.r00 + k] + (T)c, cf);
+            const T res = resid_of<T, BASE>(s, sb, MG5_AT(f, r.r00 + k) + (T)c, cf);
             sv += s.c;
             sr += res;
             acc.add(res);
         }
         const T mv = sv * (T)0.125;
-        vc[t] = mv;
-        v0c[t] = mv;
-        rc[t] = sr * (T)0.125;
+        MG5_AT(vc, t) = mv;
+        MG5_AT(v0c, t) = mv;
+        MG5_AT(rc, t) = sr * (T)0.125;
     }
     const Moments m = block_moments(acc);
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = m;
+        MG5_AT(partials, blockIdx.x) = m;
     if (fin.ls)
         finalize_if_last(reinterpret_cast<double2 *>(partials), fin);
 }
@@ -245,9 +245,9 @@ __global__ void k_restrict(const T *__restrict__ fine, int n, T *__restrict__ co
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
         const long long i = 2 * I + (ch >> 2), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch & 1);
-        s += fine[(i * n + j) * n + k];
+        s += MG5_AT(fine, (i * n + j) * n + k);
     }
-    coarse[t] = s * (T)0.125;
+    MG5_AT(coarse, t) = s * (T)0.125;
 }
 
 template <typename T>
@@ -268,7 +268,7 @@ __global__ void k_coarse_rhs(const T *__restrict__ vc, T *__restrict__ fc,
     const long long total = (long long)nc * nc * nc;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0)
-        *c_coarse = 0.0;
+        MG5_AT(c_coarse, 0) = 0.0;
     if (t >= total)
         return;
     const int k = (int)(t % nc);
@@ -281,9 +281,9 @@ __global__ void k_coarse_rhs(const T *__restrict__ vc, T *__restrict__ fc,
     if constexpr (BASE)
         gather(B, B, r, k, kp, km, sb);
     if constexpr (BASE)
-        fc[t] = opr<T, BASE>(s, sb, cf) + fc[t] - (T)(*m_fine);
+        MG5_AT(fc, t) = opr<T, BASE>(s, sb, cf) + MG5_AT(fc, t) - (T)(MG5_AT(m_fine, 0));
     else   // op + fc - m as -(m - fc - op): the residual chain's FP64 operation count
-        fc[t] = -cell_residual(s, (T)(*m_fine) - fc[t], cf);
+        MG5_AT(fc, t) = -cell_residual(s, (T)(MG5_AT(m_fine, 0)) - MG5_AT(fc, t), cf);
 }
 
 template <typename T>
@@ -323,7 +323,7 @@ __global__ void k_prolong_add(const T *__restrict__ vc, const T *__restrict__ v0
     const long long total = (long long)nc * nc * nc;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0 && c_fine && c_coarse)
-        *c_fine += *c_coarse;
+        MG5_AT(c_fine, 0) += MG5_AT(c_coarse, 0);
     if (t >= total)
         return;
     const int K = (int)(t % nc);
@@ -347,7 +347,7 @@ __global__ void k_prolong_add(const T *__restrict__ vc, const T *__restrict__ v0
             T e[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                e[c] = v0c ? vc[row + kk[c]] - v0c[row + kk[c]] : vc[row + kk[c]];
+                e[c] = v0c ? MG5_AT(vc, row + kk[c]) - MG5_AT(v0c, row + kk[c]) : MG5_AT(vc, row + kk[c]);
             Z[a][b][0] = fma((T)3, e[1], e[0]);
             Z[a][b][1] = fma((T)3, e[1], e[2]);
         }
@@ -372,7 +372,7 @@ __global__ void k_prolong_add(const T *__restrict__ vc, const T *__restrict__ v0
                 out[ck] = fma((T)3, Y[1][cj][ck], Y[ci ? 2 : 0][cj][ck]);
             const long long f = ((long long)(2 * I + ci) * n + (2 * J + cj)) * n + 2 * K;
             using V = typename Vec2<T>::type;
-            V *p = reinterpret_cast<V *>(vf + f);
+            V *p = &MG5_AT(reinterpret_cast<V *>(vf + f), 0);
             V v = *p;
             v.x = fma(out[0], w, v.x);
             v.y = fma(out[1], w, v.y);
@@ -417,10 +417,10 @@ __global__ void __launch_bounds__(kCoarsestThreads)
         T *sf = sm + 2 * n3;
         T *sbase = sm + 3 * n3;
         for (int p = threadIdx.x; p < n3; p += blockDim.x) {
-            a[p] = A[p];
-            sf[p] = f[p];
+            MG5_AT(a, p) = MG5_AT(A, p);
+            MG5_AT(sf, p) = MG5_AT(f, p);
             if constexpr (BASE)
-                sbase[p] = base[p];
+                MG5_AT(sbase, p) = MG5_AT(base, p);
         }
         ff = sf;
         bs = sbase;
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(kCoarsestThreads)
             const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
             nb = nbr_of(periodic_rows(n, i, j), k, kp, km);
             colour_me = (i + j + k) & 1;
-            fme = ff[p];
+            fme = MG5_AT(ff, p);
         }
         for (; it < nu_max; ++it) {
             double2 acc = make_double2(0.0, 0.0);
@@ -476,14 +476,14 @@ __global__ void __launch_bounds__(kCoarsestThreads)
                 T *dst = colour == 0 ? b : a;
                 if (mine) {
                     if (colour_me != colour) {
-                        dst[p] = src[p];
+                        MG5_AT(dst, p) = MG5_AT(src, p);
                     } else {
                         St<T> s, sb;
                         gather_nbr(src, nb, s);
                         if constexpr (BASE)
                             gather_nbr(bs, nb, sb);
                         bool cl = false;
-                        dst[p] = upd<T, BASE>(s, sb, fme + (T)c, cf, cl);
+                        MG5_AT(dst, p) = upd<T, BASE>(s, sb, fme + (T)c, cf, cl);
                         my_clamps += cl ? 1ull : 0ull;
                     }
                 }
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(kCoarsestThreads)
             gather((const T *)a, (const T *)a, r, k, kp, km, s);
             if constexpr (BASE)
                 gather(bs, bs, r, k, kp, km, sb);
-            const double res = (double)resid_of<T, BASE>(s, sb, ff[p], cf);
+            const double res = (double)resid_of<T, BASE>(s, sb, MG5_AT(ff, p), cf);
             acc.x += res;
             acc.y += res * res;
         }
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(kCoarsestThreads)
             for (int p = threadIdx.x; p < n3; p += blockDim.x) {
                 const int k = p % n, j = (p / n) % n, i = p / (n * n);
                 if (((i + j + k) & 1) != colour) {
-                    dst[p] = src[p];
+                    MG5_AT(dst, p) = MG5_AT(src, p);
                     continue;
                 }
                 const Rows r = periodic_rows(n, i, j);
@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(kCoarsestThreads)
                 if constexpr (BASE)
                     gather(bs, bs, r, k, kp, km, sb);
                 bool cl = false;
-                dst[p] = upd<T, BASE>(s, sb, ff[p] + (T)c, cf, cl);
+                MG5_AT(dst, p) = upd<T, BASE>(s, sb, MG5_AT(ff, p) + (T)c, cf, cl);
                 my_clamps += cl ? 1ull : 0ull;
             }
             __syncthreads();
@@ -545,13 +545,13 @@ __global__ void __launch_bounds__(kCoarsestThreads)
     }
     if (in_smem)
         for (int p = threadIdx.x; p < n3; p += blockDim.x)
-            A[p] = a[p];
+            MG5_AT(A, p) = MG5_AT(a, p);
     if (my_clamps)
-        atomicAdd(clamp, my_clamps);
+        atomicAdd(&MG5_AT(clamp, 0), my_clamps);
     if (threadIdx.x == 0) {
-        *cptr = c;
+        MG5_AT(cptr, 0) = c;
         if (sweeps_out)
-            atomicAdd(sweeps_out, it);
+            atomicAdd(&MG5_AT(sweeps_out, 0), it);
     }
 }
 
@@ -601,13 +601,13 @@ __global__ void k_scale(const double *__restrict__ delta, double s, double *__re
     double2 acc = make_double2(0.0, 0.0);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n3;
          t += (long long)gridDim.x * blockDim.x) {
-        const double v = s * delta[t];
-        f[t] = v + add;
+        const double v = s * MG5_AT(delta, t);
+        MG5_AT(f, t) = v + add;
         acc.y += v * v;
     }
     acc = block_sum2(acc);
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = acc;
+        MG5_AT(partials, blockIdx.x) = acc;
     if (fin.ls)
         finalize_if_last(partials, fin);
 }
@@ -631,10 +631,10 @@ __global__ void k_sum(const double *__restrict__ a, long long n3, double2 *__res
     double2 acc = make_double2(0.0, 0.0);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n3;
          t += (long long)gridDim.x * blockDim.x)
-        acc.x += a[t];
+        acc.x += MG5_AT(a, t);
     acc = block_sum2(acc);
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = acc;
+        MG5_AT(partials, blockIdx.x) = acc;
     if (fin.ls)
         finalize_if_last(partials, fin);
 }
@@ -655,7 +655,7 @@ __global__ void k_sub_mean(double *__restrict__ a, long long n3, const double *_
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n3)
-        a[t] -= *mean;
+        MG5_AT(a, t) -= MG5_AT(mean, 0);
 }
 
 cudaError_t launch_sub_mean(double *phi, long long n3, const double *mean, cudaStream_t st)
@@ -690,10 +690,10 @@ __global__ void k_force(const double *__restrict__ phi, int d0, int d1, int d2, 
         km = km < 0 ? d2 - 1 : km;
     }
     const long long D1 = d1, D2 = d2;
-    auto at = [&](int a, int b, int c) { return phi[((long long)a * D1 + b) * D2 + c]; };
-    grad[t] = (at(ip, J, K) - at(im, J, K)) * inv2h;
-    grad[total + t] = (at(I, jp, K) - at(I, jm, K)) * inv2h;
-    grad[2 * total + t] = (at(I, J, kp) - at(I, J, km)) * inv2h;
+    auto at = [&](int a, int b, int c) { return MG5_AT(phi, ((long long)a * D1 + b) * D2 + c); };
+    MG5_AT(grad, t) = (at(ip, J, K) - at(im, J, K)) * inv2h;
+    MG5_AT(grad, total + t) = (at(I, jp, K) - at(I, jm, K)) * inv2h;
+    MG5_AT(grad, 2 * total + t) = (at(I, J, kp) - at(I, J, km)) * inv2h;
 }
 
 cudaError_t launch_force(const double *phi, int d0, int d1, int d2, int ghost, double h, int periodic,
@@ -763,9 +763,9 @@ __global__ void k_refine(const double *__restrict__ phic, RefineSrc src, int o0,
                 const long long idx =
                     ((long long)(a ? hi[0] : lo[0]) * C1 + (b ? hi[1] : lo[1])) * C2 +
                     (c ? hi[2] : lo[2]);
-                v += wt * phic[idx];
+                v += wt * MG5_AT(phic, idx);
             }
-    fine[t] = v;
+    MG5_AT(fine, t) = v;
 }
 
 cudaError_t launch_refine(const double *phic, int nc, const int o[3], const int pn[3], int ghost,
@@ -820,9 +820,9 @@ __global__ void k_refine_cubic(const double *__restrict__ phic, int nc, int o0, 
             const double wab = w[0][a] * w[1][b];
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-                v += wab * w[2][c] * phic[row + idx[2][c]];
+                v += wab * w[2][c] * MG5_AT(phic, row + idx[2][c]);
         }
-    fine[t] = v;
+    MG5_AT(fine, t) = v;
 }
 
 cudaError_t launch_refine_cubic(const double *phic, int nc, const int o[3], const int pn[3], int ghost,
@@ -878,7 +878,7 @@ __device__ __forceinline__ void write_anchored_ghosts(double *dst, const double 
     if (ni + nj + nk == 0)
         return;
     const long long ab = ((long long)(i + 1) * d1 + (j + 1)) * d2 + (k + 1);
-    const double da = val - v0[ab];
+    const double da = val - MG5_AT(v0, ab);
     for (int a = 0; a <= ni; ++a)
         for (int b = 0; b <= nj; ++b)
             for (int c = 0; c <= nk; ++c) {
@@ -889,7 +889,7 @@ __device__ __forceinline__ void write_anchored_ghosts(double *dst, const double 
                           K = c ? gk[c - 1] : k + 1;
                 const double wm = m == 1 ? w : (m == 2 ? w * w : w * w * w);
                 const long long g = ((long long)I * d1 + J) * d2 + K;
-                dst[g] = v0[g] + wm * da;
+                MG5_AT(dst, g) = MG5_AT(v0, g) + wm * da;
             }
 }
 
@@ -921,16 +921,16 @@ __global__ void k_patch_half(const double *__restrict__ src_faces, const double 
     const int K = k + 1;
     if (copy_other) {
         const int ko = k ^ 1;                        // the pair's cell of the other colour
-        const double vo = src_faces[r.r00 + ko + 1];
-        dst[r.r00 + ko + 1] = vo;
+        const double vo = MG5_AT(src_faces, r.r00 + ko + 1);
+        MG5_AT(dst, r.r00 + ko + 1) = vo;
         if (v0)
             write_anchored_ghosts(dst, v0, w, vo, i, j, ko, p0, p1, p2, d1, d2);
     }
     const long long tk = ((long long)i * p1 + j) * p2 + k;
-    if (MASKED && !mask[tk]) {
+    if (MASKED && !MG5_AT(mask, tk)) {
         if (copy_other) {
-            const double v = src_faces[r.r00 + K];
-            dst[r.r00 + K] = v;
+            const double v = MG5_AT(src_faces, r.r00 + K);
+            MG5_AT(dst, r.r00 + K) = v;
             if (v0)
                 write_anchored_ghosts(dst, v0, w, v, i, j, k, p0, p1, p2, d1, d2);
         }
@@ -939,12 +939,12 @@ __global__ void k_patch_half(const double *__restrict__ src_faces, const double 
     St<double> s;
     gather(src_faces, src_edges, r, K, K + 1, K - 1, s);
     bool cl = false;
-    const double v = cell_update(s, fint[tk] + rhs_add, cf, cl);
-    dst[r.r00 + K] = v;
+    const double v = cell_update(s, MG5_AT(fint, tk) + rhs_add, cf, cl);
+    MG5_AT(dst, r.r00 + K) = v;
     if (v0)
         write_anchored_ghosts(dst, v0, w, v, i, j, k, p0, p1, p2, d1, d2);
     if (cl)
-        atomicAdd(clamp, 1ull);
+        atomicAdd(&MG5_AT(clamp, 0), 1ull);
 }
 
 cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint, double rhs_add,
@@ -983,7 +983,7 @@ __global__ void k_patch_residual(const double *__restrict__ phi, const double *_
     double2 acc = make_double2(0.0, 0.0);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        if (MASKED && !mask[t])
+        if (MASKED && !MG5_AT(mask, t))
             continue;
         const int k = (int)(t % p2);
         const long long q = t / p2;
@@ -991,13 +991,13 @@ __global__ void k_patch_residual(const double *__restrict__ phi, const double *_
         const Rows r = box_rows(p1 + 2, p2 + 2, i + 1, j + 1);
         St<double> s;
         gather(phi, phi, r, k + 1, k + 2, k, s);
-        const double res = cell_residual(s, fint[t] + rhs_add, cf);
+        const double res = cell_residual(s, MG5_AT(fint, t) + rhs_add, cf);
         acc.x += res;
         acc.y += res * res;
     }
     acc = block_sum2(acc);
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = acc;
+        MG5_AT(partials, blockIdx.x) = acc;
     if (fin.ls)
         finalize_if_last(partials, fin);
 }

@@ -41,6 +41,10 @@ struct FusedSmem {
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+#ifdef MG5_BOUNDS
+    if (!::mg5::bnd::copy_ok(s, gmem, __LINE__))
+        return;
+#endif
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -111,25 +115,25 @@ __device__ __forceinline__ void gather_old(const T *pm, const T *p0, const T *pp
                                            St<T> &s)
 {
     const int c = jr * OROW + kc;
-    s.c = p0[c];
-    s.xp = pp[c];
-    s.xm = pm[c];
-    s.yp = p0[c + OROW];
-    s.ym = p0[c - OROW];
-    s.zp = p0[c + 1];
-    s.zm = p0[c - 1];
-    s.xpyp = pp[c + OROW];
-    s.xpym = pp[c - OROW];
-    s.xmyp = pm[c + OROW];
-    s.xmym = pm[c - OROW];
-    s.xpzp = pp[c + 1];
-    s.xpzm = pp[c - 1];
-    s.xmzp = pm[c + 1];
-    s.xmzm = pm[c - 1];
-    s.ypzp = p0[c + OROW + 1];
-    s.ypzm = p0[c + OROW - 1];
-    s.ymzp = p0[c - OROW + 1];
-    s.ymzm = p0[c - OROW - 1];
+    s.c = MG5_AT(p0, c);
+    s.xp = MG5_AT(pp, c);
+    s.xm = MG5_AT(pm, c);
+    s.yp = MG5_AT(p0, c + OROW);
+    s.ym = MG5_AT(p0, c - OROW);
+    s.zp = MG5_AT(p0, c + 1);
+    s.zm = MG5_AT(p0, c - 1);
+    s.xpyp = MG5_AT(pp, c + OROW);
+    s.xpym = MG5_AT(pp, c - OROW);
+    s.xmyp = MG5_AT(pm, c + OROW);
+    s.xmym = MG5_AT(pm, c - OROW);
+    s.xpzp = MG5_AT(pp, c + 1);
+    s.xpzm = MG5_AT(pp, c - 1);
+    s.xmzp = MG5_AT(pm, c + 1);
+    s.xmzm = MG5_AT(pm, c - 1);
+    s.ypzp = MG5_AT(p0, c + OROW + 1);
+    s.ypzm = MG5_AT(p0, c + OROW - 1);
+    s.ymzp = MG5_AT(p0, c - OROW + 1);
+    s.ymzm = MG5_AT(p0, c - OROW - 1);
 }
 
 template <typename T, bool BASE>
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(FT_THREADS)
     const int k0 = blockIdx.x * FT_K, j0 = blockIdx.y * FT_J;
     const int i0 = blockIdx.z * ichunk;
     const int i1 = min(i0 + ichunk, n);
-    const T cval = (T)(*cptr);
+    const T cval = (T)(MG5_AT(cptr, 0));
     bool clamped = false;
     const CopyPlan<T> plan = make_plan<T>(n, j0, k0);
     const long long n2 = (long long)n * n;
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(FT_THREADS)
             if constexpr (BASE)
                 gather_old(S.base[r5.m], S.base[r5.z], S.base[r5.p], jj + 1, kk + 3, sb);
             const T rhs = S.fr[r5.z][(jj + 1) * OROW + kk + 3] + cval;
-            rn[jj * RK_ + kk] = upd<T, BASE>(s, sb, rhs, cf, clamped);
+            MG5_AT(rn, jj * RK_ + kk) = upd<T, BASE>(s, sb, rhs, cf, clamped);
         }
     };
 
@@ -222,45 +226,45 @@ __global__ void __launch_bounds__(FT_THREADS)
             const int cr = (jj + 1) * RK_ + (kk + 1);   // rnew coordinates of the black cell
             const int co = (jj + 2) * OROW + (kk + 4);  // old coordinates
             St<T> s;
-            s.c = o0[co];
-            s.xp = rp[cr];
-            s.xm = rm[cr];
-            s.yp = r0[cr + RK_];
-            s.ym = r0[cr - RK_];
-            s.zp = r0[cr + 1];
-            s.zm = r0[cr - 1];
-            s.xpyp = op[co + OROW];
-            s.xpym = op[co - OROW];
-            s.xmyp = om[co + OROW];
-            s.xmym = om[co - OROW];
-            s.xpzp = op[co + 1];
-            s.xpzm = op[co - 1];
-            s.xmzp = om[co + 1];
-            s.xmzm = om[co - 1];
-            s.ypzp = o0[co + OROW + 1];
-            s.ypzm = o0[co + OROW - 1];
-            s.ymzp = o0[co - OROW + 1];
-            s.ymzm = o0[co - OROW - 1];
+            s.c = MG5_AT(o0, co);
+            s.xp = MG5_AT(rp, cr);
+            s.xm = MG5_AT(rm, cr);
+            s.yp = MG5_AT(r0, cr + RK_);
+            s.ym = MG5_AT(r0, cr - RK_);
+            s.zp = MG5_AT(r0, cr + 1);
+            s.zm = MG5_AT(r0, cr - 1);
+            s.xpyp = MG5_AT(op, co + OROW);
+            s.xpym = MG5_AT(op, co - OROW);
+            s.xmyp = MG5_AT(om, co + OROW);
+            s.xmym = MG5_AT(om, co - OROW);
+            s.xpzp = MG5_AT(op, co + 1);
+            s.xpzm = MG5_AT(op, co - 1);
+            s.xmzp = MG5_AT(om, co + 1);
+            s.xmzm = MG5_AT(om, co - 1);
+            s.ypzp = MG5_AT(o0, co + OROW + 1);
+            s.ypzm = MG5_AT(o0, co + OROW - 1);
+            s.ymzp = MG5_AT(o0, co - OROW + 1);
+            s.ymzm = MG5_AT(o0, co - OROW - 1);
             St<T> sb;
             if constexpr (BASE)
                 gather_old(S.base[r5.m], S.base[r5.z], S.base[r5.p], jj + 2, kk + 4, sb);
             if (j < n && kp0 < n) {
                 const long long row = ((long long)p * n + j) * n;
                 const T vb = upd<T, BASE>(s, sb, S.fr[r5.z][co] + cval, cf, clamped);
-                const T vr = r0[(jj + 1) * RK_ + (2 * pr + 1 - bodd) + 1];
+                const T vr = MG5_AT(r0, (jj + 1) * RK_ + (2 * pr + 1 - bodd) + 1);
                 const T v0 = bodd ? vr : vb;
                 const T v1 = bodd ? vb : vr;
                 if constexpr (sizeof(T) == 4) {
-                    *reinterpret_cast<float2 *>(out + row + kp0) = make_float2((float)v0, (float)v1);
+                    MG5_AT(reinterpret_cast<float2 *>(out + row + kp0), 0) = make_float2((float)v0, (float)v1);
                 } else {
-                    *reinterpret_cast<double2 *>(out + row + kp0) = make_double2((double)v0, (double)v1);
+                    MG5_AT(reinterpret_cast<double2 *>(out + row + kp0), 0) = make_double2((double)v0, (double)v1);
                 }
             }
         }
     }
     cp_async_wait_all();
     if (clamped)
-        atomicAdd(clamp, 1ull);
+        atomicAdd(&MG5_AT(clamp, 0), 1ull);
 }
 
 template <typename T>

@@ -77,9 +77,9 @@ struct PlaneCol {
 __device__ __forceinline__ PlaneCol plane_col(const float *base)
 {
     PlaneCol r;
-    r.c = base[0];
-    const float yp = base[MO], ym = base[-MO], zp = base[1], zm = base[-1];
-    const float pp = base[MO + 1], pm = base[MO - 1], mp = base[-MO + 1], mm = base[-MO - 1];
+    r.c = MG5_AT(base, 0);
+    const float yp = MG5_AT(base, MO), ym = MG5_AT(base, -MO), zp = MG5_AT(base, 1), zm = MG5_AT(base, -1);
+    const float pp = MG5_AT(base, MO + 1), pm = MG5_AT(base, MO - 1), mp = MG5_AT(base, -MO + 1), mm = MG5_AT(base, -MO - 1);
     r.Y = __fadd_rn(yp, ym);
     r.Z = __fadd_rn(zp, zm);
     r.Dy = __fsub_rn(yp, ym);
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
     const int i1 = min(i0 + ichunk, n);
     const int q0 = i0 - 2;        // first plane brought in; plane q lives in slot (q - q0) % 6
     const int last = i1 + 1;      // the last plane any step reads
-    const float cval = (float)(*cptr);
+    const float cval = (float)(MG5_AT(cptr, 0));
     const long long n2 = (long long)n * n;
     const int tid = threadIdx.x;
     const bool tile = tid < MT_TILE;
@@ -226,23 +226,23 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
                 parts2_from_sums(__fadd_rn(e2.c, c.cE0), __fadd_rn(b2.c, c.cB0), e1.Y, b1.Y, e1.Z, b1.Z,
                            __fsub_rn(e2.Dy, c.DyE0), __fsub_rn(b2.Dy, c.DyB0),
                            __fsub_rn(e2.Dz, c.DzE0), __fsub_rn(b2.Dz, c.DzB0), e1.dyz, b1.dyz);
-            const float r1 = cell_update_corr_parts(qr, b1.c, e1.c, F[s1 * MPL + ps.off] + cval, cf,
+            const float r1 = cell_update_corr_parts(qr, b1.c, e1.c, MG5_AT(F, s1 * MPL + ps.off) + cval, cf,
                                                     clamped);
-            S.RN[(set + 1) & 1][ps.rn] = r1;   // plane p + 1 (p - i0 has the parity of set)
+            MG5_AT(S.RN[(set + 1) & 1], ps.rn) = r1;   // plane p + 1 (p - i0 has the parity of set)
             if (tile && !warm) {
                 // black cell (p) of the position: new red faces, old edges
                 const float *rn = S.RN[set & 1] + ps.rn;
-                const float sye = __fadd_rn(rn[RNO], rn[-RNO]), sze = __fadd_rn(rn[1], rn[-1]);
+                const float sye = __fadd_rn(MG5_AT(rn, RNO), MG5_AT(rn, -RNO)), sze = __fadd_rn(MG5_AT(rn, 1), MG5_AT(rn, -1));
                 const Parts2 qb = parts2_from_sums(__fadd_rn(r1, c.rm), __fadd_rn(b1.c, c.cBm), sye,
                                              c.YB0, sze, c.ZB0, __fsub_rn(e1.Dy, c.DyEm),
                                              __fsub_rn(b1.Dy, c.DyBm), __fsub_rn(e1.Dz, c.DzEm),
                                              __fsub_rn(b1.Dz, c.DzBm), c.dyzE0, c.dyzB0);
                 const float b0v = cell_update_corr_parts(qb, c.cB0, c.cE0,
-                                                         F[s0 * MPL + ps.off] + cval, cf, clamped);
+                                                         MG5_AT(F, s0 * MPL + ps.off) + cval, cf, clamped);
                 float2 v;
                 v.x = first[set] ? b0v : rprev;
                 v.y = first[set] ? rprev : b0v;
-                *reinterpret_cast<float2 *>(optr) = v;
+                MG5_AT(reinterpret_cast<float2 *>(optr), 0) = v;
             }
             // keep plane p + 2 as the position's plane p, plane p + 1 as its plane p - 1
             c.cE0 = e2.c;
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
         ++p;
     }
     if (clamped)
-        atomicAdd(clamp, 1ull);
+        atomicAdd(&MG5_AT(clamp, 0), 1ull);
 }
 
 }  // namespace

@@ -70,11 +70,11 @@ __device__ __forceinline__ void plane_pair(const float *base, PC &a, PC &b)
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         const float *row = base + (r - 1) * RW;
-        const float2 v = *reinterpret_cast<const float2 *>(row);
-        m[r] = row[-1];
+        const float2 v = MG5_AT(reinterpret_cast<const float2 *>(row), 0);
+        m[r] = MG5_AT(row, -1);
         x0[r] = v.x;
         x1[r] = v.y;
-        p2[r] = row[2];
+        p2[r] = MG5_AT(row, 2);
     }
     // column kA: k-1 = m, k = x0, k+1 = x1; column kA + 1: k-1 = x0, k = x1, k+1 = p2
     a.c = x0[1];
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(RT_THREADS, 2)
     ResidSmem &S = *reinterpret_cast<ResidSmem *>(smem_raw);
     const long long n2 = (long long)n * n;
     const int nc = n >> 1;
-    const float cval = (float)(*cptr);
+    const float cval = (float)(MG5_AT(cptr, 0));
     const int tid = threadIdx.x;
     const int jj = tid >> 4, pp = tid & 15;        // warp w: rows 2w (lanes 0-15), 2w+1
     const int tk = n / RT_K, tiles = tk * (n / RT_J);
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(RT_THREADS, 2)
             PC ea, eb, ba, bb;
             plane_pair(S.E[s1] + offE, ea, eb);
             plane_pair(S.B[s1] + offE, ba, bb);
-            const float2 fv = *reinterpret_cast<const float2 *>(S.F[s0] + offF);
+            const float2 fv = MG5_AT(reinterpret_cast<const float2 *>(S.F[s0] + offF), 0);
             const float ra = cell_resid(ca, ea, ba, __fadd_rn(fv.x, cval), cf);
             const float rb = cell_resid(cb, eb, bb, __fadd_rn(fv.y, cval), cf);
             acc.add(ra);
@@ -276,9 +276,9 @@ __global__ void __launch_bounds__(RT_THREADS, 2)
                     sr = __fadd_rn(sr, s7);
                     const long long t = ((long long)(p >> 1) * nc + J) * nc + K;
                     const float mv = __fmul_rn(sv, 0.125f);
-                    vc[t] = mv;
-                    v0c[t] = mv;
-                    rc[t] = __fmul_rn(sr, 0.125f);
+                    MG5_AT(vc, t) = mv;
+                    MG5_AT(v0c, t) = mv;
+                    MG5_AT(rc, t) = __fmul_rn(sr, 0.125f);
                 }
             }
             shift(ca, ea, ba);
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(RT_THREADS, 2)
     }
     const Moments mom = block_moments(acc);
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = mom;
+        MG5_AT(partials, blockIdx.x) = mom;
     if (fin.ls)
         finalize_if_last(reinterpret_cast<double2 *>(partials), fin);
 }

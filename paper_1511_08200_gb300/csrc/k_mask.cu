@@ -32,9 +32,9 @@ __global__ void k_mask_restrict(const unsigned char *__restrict__ mf, int p0, in
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
         const int i = 2 * I + (ch >> 2), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch & 1);
-        all &= mf[((long long)i * p1 + j) * p2 + k] ? 1 : 0;
+        all &= MG5_AT(mf, ((long long)i * p1 + j) * p2 + k) ? 1 : 0;
     }
-    mc[t] = all;
+    MG5_AT(mc, t) = all;
 }
 
 cudaError_t launch_mask_restrict(const unsigned char *mf, const int p[3], unsigned char *mc,
@@ -54,16 +54,16 @@ __global__ void k_scale_masked(const double *__restrict__ delta, double s, doubl
     double2 acc = make_double2(0.0, 0.0);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
-        const double v = s * delta[t];
-        f[t] = v + add;
-        if (mask[t]) {
+        const double v = s * MG5_AT(delta, t);
+        MG5_AT(f, t) = v + add;
+        if (MG5_AT(mask, t)) {
             acc.x += 1.0;
             acc.y += v * v;
         }
     }
     acc = block_sum2(acc);
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = acc;
+        MG5_AT(partials, blockIdx.x) = acc;
 }
 
 cudaError_t launch_scale_masked(const double *delta, double s, double *f, long long n,
@@ -108,17 +108,17 @@ __global__ void k_parent_force_mask(const double *__restrict__ gphi, const doubl
         double f5 = 0.0, fg = 0.0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double x = 0.5 * gphi[a * n3 + pc], y = ggr[a * n3 + pc];
+            const double x = 0.5 * MG5_AT(gphi, a * n3 + pc), y = MG5_AT(ggr, a * n3 + pc);
             f5 = __dadd_rn(f5, __dmul_rn(x, x));
             fg = __dadd_rn(fg, __dmul_rn(y, y));
         }
         on = sqrt(f5) > __dmul_rn(theta, sqrt(fg));
-        mask[t] = on ? 1 : 0;
+        MG5_AT(mask, t) = on ? 1 : 0;
     }
     if (count) {
         const unsigned ballot = __ballot_sync(0xffffffffu, on);
         if ((threadIdx.x & 31) == 0 && ballot)
-            atomicAdd(count, (unsigned long long)__popc(ballot));
+            atomicAdd(&MG5_AT(count, 0), (unsigned long long)__popc(ballot));
     }
 }
 

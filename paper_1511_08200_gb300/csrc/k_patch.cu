@@ -55,20 +55,20 @@ __global__ void k_pbox_resid_restrict(const double *__restrict__ v, const double
             St<double> s;
             gather(v, v, r, k + 1, k + 2, k, s);
             const long long fi = ((long long)i * p1 + j) * p2 + k;
-            const double res = (MASKED && !mask[fi]) ? 0.0 : cell_residual(s, f[fi], cf);
+            const double res = (MASKED && !MG5_AT(mask, fi)) ? 0.0 : cell_residual(s, MG5_AT(f, fi), cf);
             sv += s.c;
             sr += res;
             acc.x += res;
             acc.y += res * res;
         }
         const long long cb = bidx(I + 1, J + 1, K + 1, q1 + 2, q2 + 2);
-        vc[cb] = 0.125 * sv;
-        v0c[cb] = 0.125 * sv;
-        fc[t] = 0.125 * sr;
+        MG5_AT(vc, cb) = 0.125 * sv;
+        MG5_AT(v0c, cb) = 0.125 * sv;
+        MG5_AT(fc, t) = 0.125 * sr;
     }
     acc = block_sum2(acc);
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = acc;
+        MG5_AT(partials, blockIdx.x) = acc;
     if (fin.ls)
         finalize_if_last(partials, fin);
 }
@@ -87,7 +87,7 @@ __global__ void k_pbox_coarse_rhs(const double *__restrict__ vc, double *__restr
     const Rows r = box_rows(q1 + 2, q2 + 2, i + 1, j + 1);
     St<double> s;
     gather(vc, vc, r, k + 1, k + 2, k, s);
-    fc[t] = -cell_residual(s, -fc[t], cf);   // op + fc
+    MG5_AT(fc, t) = -cell_residual(s, -MG5_AT(fc, t), cf);   // op + fc
 }
 
 // fine interior += trilinear interpolation of (vc - v0c), ghosts included (the
@@ -101,7 +101,7 @@ __global__ void k_pbox_prolong(const double *__restrict__ vc, const double *__re
     const int p0 = 2 * q0, p1 = 2 * q1, p2 = 2 * q2;
     const long long total = (long long)p0 * p1 * p2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total || (MASKED && !mask[t]))
+    if (t >= total || (MASKED && !MG5_AT(mask, t)))
         return;
     const int k = (int)(t % p2);
     const long long q = t / p2;
@@ -120,9 +120,9 @@ __global__ void k_pbox_prolong(const double *__restrict__ vc, const double *__re
             for (int c = 0; c < 2; ++c) {
                 const long long idx = bidx(a ? Q[0] : P[0], b ? Q[1] : P[1], c ? Q[2] : P[2], d1, d2);
                 const double w = (a ? 0.25 : 0.75) * (b ? 0.25 : 0.75) * (c ? 0.25 : 0.75);
-                acc += w * (vc[idx] - v0c[idx]);
+                acc += w * (MG5_AT(vc, idx) - MG5_AT(v0c, idx));
             }
-    vf[bidx(i + 1, j + 1, k + 1, p1 + 2, p2 + 2)] += acc;
+    MG5_AT(vf, bidx(i + 1, j + 1, k + 1, p1 + 2, p2 + 2)) += acc;
 }
 
 // coarse box ghost cells: mean of the fine ghost cells each one covers
@@ -163,11 +163,11 @@ __global__ void k_pbox_ghosts(const double *__restrict__ fb, int p0, int p1, int
     for (int a = 0; a < cnt[0]; ++a)
         for (int b = 0; b < cnt[1]; ++b)
             for (int c = 0; c < cnt[2]; ++c)
-                s += fb[bidx(lo[0] + a + 1, lo[1] + b + 1, lo[2] + c + 1, p1 + 2, p2 + 2)];
+                s += MG5_AT(fb, bidx(lo[0] + a + 1, lo[1] + b + 1, lo[2] + c + 1, p1 + 2, p2 + 2));
     const double g = s / (double)(cnt[0] * cnt[1] * cnt[2]);
-    g1[t] = g;
-    g2[t] = g;
-    g3[t] = g;
+    MG5_AT(g1, t) = g;
+    MG5_AT(g2, t) = g;
+    MG5_AT(g3, t) = g;
 }
 
 // ghost refresh of a coarse box: v(g) = v0(g) + w^m (v(a) - v0(a))
@@ -184,7 +184,7 @@ __device__ __forceinline__ void ghost_refresh_cell(double *v, const double *v0, 
         return;
     const double wm = m == 1 ? w : (m == 2 ? w * w : w * w * w);
     const long long g = bidx(I, J, K, d1, d2), a = bidx(a0, a1, a2, d1, d2);
-    v[g] = v0[g] + wm * (v[a] - v0[a]);
+    MG5_AT(v, g) = MG5_AT(v0, g) + wm * (MG5_AT(v, a) - MG5_AT(v0, a));
 }
 
 __global__ void k_pbox_ghost_refresh(double *__restrict__ v, const double *__restrict__ v0, int q0,
@@ -229,12 +229,12 @@ __global__ void __launch_bounds__(kPboxThreads)
         double *sf = sm + 2 * nbox;
         double *sv0 = sm + 3 * nbox;
         for (int q = threadIdx.x; q < nbox; q += blockDim.x) {
-            a[q] = A[q];
-            b[q] = B[q];
+            MG5_AT(a, q) = MG5_AT(A, q);
+            MG5_AT(b, q) = MG5_AT(B, q);
             if (v0)
-                sv0[q] = v0[q];
+                MG5_AT(sv0, q) = MG5_AT(v0, q);
             if (q < n3)
-                sf[q] = f[q];
+                MG5_AT(sf, q) = MG5_AT(f, q);
         }
         ff = sf;
         g0 = v0 ? sv0 : nullptr;
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kPboxThreads)
         // colour, f and the ghost-refresh terms once (the same values as the loop below)
         const int p = threadIdx.x;
         const bool mine = p < n3;
-        const bool active = mine && (!MASKED || mask[p]);
+        const bool active = mine && (!MASKED || MG5_AT(mask, p));
         Nbr nb{};
         int colour_me = 0, cbox = 0;
         double fme = 0.0;
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kPboxThreads)
             nb = nbr_of(box_rows(d1, d2, i + 1, j + 1), k + 1, k + 2, k);
             colour_me = (i + j + k) & 1;
             cbox = nb.o[0];
-            fme = ff[p];
+            fme = MG5_AT(ff, p);
         }
         // slot e covers box cell threadIdx.x + e * blockDim.x; gi < 0: not a ghost (or none)
         int gi[kOwnGhosts], ga[kOwnGhosts];
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kPboxThreads)
 #pragma unroll
             for (int e = 0; e < kOwnGhosts; ++e)
                 if (gi[e] >= 0)
-                    X[gi[e]] = g0[gi[e]] + gw[e] * (X[ga[e]] - g0[ga[e]]);
+                    MG5_AT(X, gi[e]) = MG5_AT(g0, gi[e]) + gw[e] * (MG5_AT(X, ga[e]) - MG5_AT(g0, ga[e]));
             __syncthreads();
         };
         for (; it < nu_max; ++it) {
@@ -323,12 +323,12 @@ __global__ void __launch_bounds__(kPboxThreads)
                 double *dst = colour == 0 ? b : a;
                 if (mine) {
                     if (colour_me != colour || !active) {
-                        dst[cbox] = src[cbox];
+                        MG5_AT(dst, cbox) = MG5_AT(src, cbox);
                     } else {
                         St<double> s;
                         gather_nbr(src, nb, s);
                         bool cl = false;
-                        dst[cbox] = cell_update(s, fme, cf, cl);
+                        MG5_AT(dst, cbox) = cell_update(s, fme, cf, cl);
                         my_clamps += cl ? 1ull : 0ull;
                     }
                 }
@@ -342,13 +342,13 @@ __global__ void __launch_bounds__(kPboxThreads)
     for (; it < nu_max; ++it) {
         double2 acc = make_double2(0.0, 0.0);
         for (int p = threadIdx.x; p < n3; p += blockDim.x) {
-            if (MASKED && !mask[p])
+            if (MASKED && !MG5_AT(mask, p))
                 continue;
             const int k = p % p2, j = (p / p2) % p1, i = p / (p1 * p2);
             const Rows r = box_rows(d1, d2, i + 1, j + 1);
             St<double> s;
             gather((const double *)a, (const double *)a, r, k + 1, k + 2, k, s);
-            const double res = cell_residual(s, ff[p], cf);
+            const double res = cell_residual(s, MG5_AT(ff, p), cf);
             acc.y += res * res;
         }
         acc = block_sum2(acc);
@@ -367,14 +367,14 @@ __global__ void __launch_bounds__(kPboxThreads)
             for (int p = threadIdx.x; p < n3; p += blockDim.x) {
                 const int k = p % p2, j = (p / p2) % p1, i = p / (p1 * p2);
                 const Rows r = box_rows(d1, d2, i + 1, j + 1);
-                if (((i + j + k) & 1) != colour || (MASKED && !mask[p])) {
-                    dst[r.r00 + k + 1] = src[r.r00 + k + 1];
+                if (((i + j + k) & 1) != colour || (MASKED && !MG5_AT(mask, p))) {
+                    MG5_AT(dst, r.r00 + k + 1) = MG5_AT(src, r.r00 + k + 1);
                     continue;
                 }
                 St<double> s;
                 gather(src, src, r, k + 1, k + 2, k, s);
                 bool cl = false;
-                dst[r.r00 + k + 1] = cell_update(s, ff[p], cf, cl);
+                MG5_AT(dst, r.r00 + k + 1) = cell_update(s, MG5_AT(ff, p), cf, cl);
                 my_clamps += cl ? 1ull : 0ull;
             }
             __syncthreads();
@@ -383,12 +383,12 @@ __global__ void __launch_bounds__(kPboxThreads)
     }
     if (in_smem) {
         for (int q = threadIdx.x; q < nbox; q += blockDim.x)
-            A[q] = a[q];
+            MG5_AT(A, q) = MG5_AT(a, q);
     }
     if (my_clamps)
-        atomicAdd(clamp, my_clamps);
+        atomicAdd(&MG5_AT(clamp, 0), my_clamps);
     if (threadIdx.x == 0 && sweeps_out)
-        atomicAdd(sweeps_out, it);
+        atomicAdd(&MG5_AT(sweeps_out, 0), it);
 }
 
 // ---------------------------------------------------------------- launchers

@@ -48,16 +48,16 @@ __global__ void k_spec_residual(const T *__restrict__ v, const T *__restrict__ f
         gather(v, v, r, k, kp, km, s);
         if constexpr (BASE)
             gather(B, B, r, k, kp, km, sb);
-        const T res = resid_of<T, BASE>(s, sb, f[t] + (T)(*cptr), cf);
-        out[t].x = res;
-        out[t].y = (T)0;
+        const T res = resid_of<T, BASE>(s, sb, MG5_AT(f, t) + (T)(MG5_AT(cptr, 0)), cf);
+        MG5_AT(out, t).x = res;
+        MG5_AT(out, t).y = (T)0;
         acc.add(res);
     }
     const Moments m = block_moments(acc);
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = m;
+        MG5_AT(partials, blockIdx.x) = m;
         if (blockIdx.x == 0 && sweeps)
-            atomicAdd(sweeps, 2);
+            atomicAdd(&MG5_AT(sweeps, 0), 2);
     }
     finalize_if_last(reinterpret_cast<double2 *>(partials), fin);   // c -= mean r
 }
@@ -85,15 +85,15 @@ __global__ void k_dft_axis(const typename Cplx<T>::type *__restrict__ in,
         T sn, cs;
         sincos_pi((T)(2 * q) / (T)n, &sn, &cs);
         sn *= sgn;
-        const typename Cplx<T>::type a = in[base + m * stride];
+        const typename Cplx<T>::type a = MG5_AT(in, base + m * stride);
         re += a.x * cs - a.y * sn;
         im += a.x * sn + a.y * cs;
     }
     if (addto) {
-        addto[t] += re * scale;
+        MG5_AT(addto, t) += re * scale;
     } else {
-        out[t].x = re;
-        out[t].y = im;
+        MG5_AT(out, t).x = re;
+        MG5_AT(out, t).y = im;
     }
 }
 
@@ -108,8 +108,8 @@ __global__ void k_spec_divide(typename Cplx<T>::type *__restrict__ a, int n, T h
         return;
     const int k = t % n, j = (t / n) % n, i = t / (n * n);
     if (i == 0 && j == 0 && k == 0) {
-        a[t].x = (T)0;
-        a[t].y = (T)0;
+        MG5_AT(a, t).x = (T)0;
+        MG5_AT(a, t).y = (T)0;
         return;
     }
     T s, ci, cj, ck;
@@ -117,8 +117,8 @@ __global__ void k_spec_divide(typename Cplx<T>::type *__restrict__ a, int n, T h
     sincos_pi((T)(2 * j) / (T)n, &s, &cj);
     sincos_pi((T)(2 * k) / (T)n, &s, &ck);
     const T inv = h2 / ((T)2 * (ci + cj + ck) - (T)6);
-    a[t].x *= inv;
-    a[t].y *= inv;
+    MG5_AT(a, t).x *= inv;
+    MG5_AT(a, t).y *= inv;
 }
 
 template <typename T>

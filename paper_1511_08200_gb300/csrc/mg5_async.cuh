@@ -4,11 +4,17 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "mg5_bounds.cuh"
+
 namespace mg5 {
 namespace acopy {
 
 __device__ __forceinline__ void copy16(unsigned smem_addr, const void *gmem)
 {
+#ifdef MG5_BOUNDS
+    if (!::mg5::bnd::copy_ok(smem_addr, gmem, __LINE__))
+        return;
+#endif
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr), "l"(gmem)
                  : "memory");
 }

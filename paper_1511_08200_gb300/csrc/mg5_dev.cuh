@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "mg5_bounds.cuh"
+
 namespace mg5 {
 
 // Per-grid constants of the cell arithmetic.
@@ -120,25 +122,25 @@ template <typename T>
 __device__ __forceinline__ void gather(const T *F, const T *E, const Rows &r, int k, int kp,
                                        int km, St<T> &s)
 {
-    s.c = F[r.r00 + k];
-    s.xp = F[r.rp0 + k];
-    s.xm = F[r.rm0 + k];
-    s.yp = F[r.r0p + k];
-    s.ym = F[r.r0m + k];
-    s.zp = F[r.r00 + kp];
-    s.zm = F[r.r00 + km];
-    s.xpyp = E[r.rpp + k];
-    s.xpym = E[r.rpm + k];
-    s.xmyp = E[r.rmp + k];
-    s.xmym = E[r.rmm + k];
-    s.xpzp = E[r.rp0 + kp];
-    s.xpzm = E[r.rp0 + km];
-    s.xmzp = E[r.rm0 + kp];
-    s.xmzm = E[r.rm0 + km];
-    s.ypzp = E[r.r0p + kp];
-    s.ypzm = E[r.r0p + km];
-    s.ymzp = E[r.r0m + kp];
-    s.ymzm = E[r.r0m + km];
+    s.c = MG5_AT(F, r.r00 + k);
+    s.xp = MG5_AT(F, r.rp0 + k);
+    s.xm = MG5_AT(F, r.rm0 + k);
+    s.yp = MG5_AT(F, r.r0p + k);
+    s.ym = MG5_AT(F, r.r0m + k);
+    s.zp = MG5_AT(F, r.r00 + kp);
+    s.zm = MG5_AT(F, r.r00 + km);
+    s.xpyp = MG5_AT(E, r.rpp + k);
+    s.xpym = MG5_AT(E, r.rpm + k);
+    s.xmyp = MG5_AT(E, r.rmp + k);
+    s.xmym = MG5_AT(E, r.rmm + k);
+    s.xpzp = MG5_AT(E, r.rp0 + kp);
+    s.xpzm = MG5_AT(E, r.rp0 + km);
+    s.xmzp = MG5_AT(E, r.rm0 + kp);
+    s.xmzm = MG5_AT(E, r.rm0 + km);
+    s.ypzp = MG5_AT(E, r.r0p + kp);
+    s.ypzm = MG5_AT(E, r.r0p + km);
+    s.ymzp = MG5_AT(E, r.r0m + kp);
+    s.ymzm = MG5_AT(E, r.r0m + km);
 }
 
 // The 19 offsets of a cell's stencil within one array (St order), for kernels that
@@ -178,25 +180,25 @@ __device__ __forceinline__ Nbr nbr_of(const Rows &r, int k, int kp, int km)
 template <typename T>
 __device__ __forceinline__ void gather_nbr(const T *a, const Nbr &b, St<T> &s)
 {
-    s.c = a[b.o[0]];
-    s.xp = a[b.o[1]];
-    s.xm = a[b.o[2]];
-    s.yp = a[b.o[3]];
-    s.ym = a[b.o[4]];
-    s.zp = a[b.o[5]];
-    s.zm = a[b.o[6]];
-    s.xpyp = a[b.o[7]];
-    s.xpym = a[b.o[8]];
-    s.xmyp = a[b.o[9]];
-    s.xmym = a[b.o[10]];
-    s.xpzp = a[b.o[11]];
-    s.xpzm = a[b.o[12]];
-    s.xmzp = a[b.o[13]];
-    s.xmzm = a[b.o[14]];
-    s.ypzp = a[b.o[15]];
-    s.ypzm = a[b.o[16]];
-    s.ymzp = a[b.o[17]];
-    s.ymzm = a[b.o[18]];
+    s.c = MG5_AT(a, b.o[0]);
+    s.xp = MG5_AT(a, b.o[1]);
+    s.xm = MG5_AT(a, b.o[2]);
+    s.yp = MG5_AT(a, b.o[3]);
+    s.ym = MG5_AT(a, b.o[4]);
+    s.zp = MG5_AT(a, b.o[5]);
+    s.zm = MG5_AT(a, b.o[6]);
+    s.xpyp = MG5_AT(a, b.o[7]);
+    s.xpym = MG5_AT(a, b.o[8]);
+    s.xmyp = MG5_AT(a, b.o[9]);
+    s.xmym = MG5_AT(a, b.o[10]);
+    s.xpzp = MG5_AT(a, b.o[11]);
+    s.xpzm = MG5_AT(a, b.o[12]);
+    s.xmzp = MG5_AT(a, b.o[13]);
+    s.xmzm = MG5_AT(a, b.o[14]);
+    s.ypzp = MG5_AT(a, b.o[15]);
+    s.ypzm = MG5_AT(a, b.o[16]);
+    s.ymzp = MG5_AT(a, b.o[17]);
+    s.ymzm = MG5_AT(a, b.o[18]);
 }
 
 // S = sum of the 6 faces; t and d2 with Sigma h^4 = (2/3) t + d2 / 8:

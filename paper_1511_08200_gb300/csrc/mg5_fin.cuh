@@ -15,17 +15,18 @@ namespace mg5 {
 
 __device__ __forceinline__ unsigned *fin_counter(double2 *partials)
 {
-    return reinterpret_cast<unsigned *>(partials + kMaxPartials - 1);
+    return &MG5_AT(reinterpret_cast<unsigned *>(partials + kMaxPartials - 1), 0);
 }
 
 // Apply `mode` to nb partials (all threads of the block must call it).
 __device__ __forceinline__ void finalize_body(const double2 *partials, int nb, double ncells,
                                               LevelScal *ls, int mode)
 {
+    ls = &MG5_AT(ls, 0);
     if (mode == FIN_RESID || mode == FIN_STATS) {
         // per-block shifted sums moved onto block 0's shift, summed in a fixed order
         auto ld = [&](int b) {
-            const double2 u = __ldcg(partials + 2 * b), w = __ldcg(partials + 2 * b + 1);
+            const double2 u = __ldcg(&MG5_AT(partials, 2 * b)), w = __ldcg(&MG5_AT(partials, 2 * b + 1));
             return Moments{u.x, u.y, w.x, w.y};
         };
         const double k0 = ld(0).k;
@@ -53,7 +54,7 @@ __device__ __forceinline__ void finalize_body(const double2 *partials, int nb, d
     }
     double2 acc = make_double2(0.0, 0.0);
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const double2 u = __ldcg(partials + b);
+        const double2 u = __ldcg(&MG5_AT(partials, b));
         acc.x += u.x;
         acc.y += u.y;
     }

@@ -42,14 +42,14 @@ __global__ void k_resid64_mixed(const double *__restrict__ phi, const double *__
                                 Moments *__restrict__ partials, Fin fin)
 {
     const long long total = (long long)n * n * n;
-    const double c = *cptr;
+    const double c = MG5_AT(cptr, 0);
     MomAcc<double> acc;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         if constexpr (ZERO) {
-            const double res = f[t] + c;
-            r32[t] = f64_to_f32_rn(res);
-            B[t] = 0.0f;
+            const double res = MG5_AT(f, t) + c;
+            MG5_AT(r32, t) = f64_to_f32_rn(res);
+            MG5_AT(B, t) = 0.0f;
             acc.add(res);
             continue;
         }
@@ -60,14 +60,14 @@ __global__ void k_resid64_mixed(const double *__restrict__ phi, const double *__
         const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
         St<double> s;
         gather(phi, phi, r, k, kp, km, s);
-        const double res = cell_residual(s, f[t] + c, cf);
-        r32[t] = f64_to_f32_rn(res);
-        B[t] = f64_to_f32_rn(s.c);
+        const double res = cell_residual(s, MG5_AT(f, t) + c, cf);
+        MG5_AT(r32, t) = f64_to_f32_rn(res);
+        MG5_AT(B, t) = f64_to_f32_rn(s.c);
         acc.add(res);
     }
     const Moments m = block_moments(acc);
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = m;
+        MG5_AT(partials, blockIdx.x) = m;
     finalize_if_last(reinterpret_cast<double2 *>(partials), fin);
 }
 
@@ -75,12 +75,14 @@ __global__ void k_update_mixed(double *__restrict__ phi, const float *__restrict
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n3)
-        phi[t] += f32_to_f64(e[t]);
+        MG5_AT(phi, t) += f32_to_f64(MG5_AT(e, t));
 }
 
 // scalar bookkeeping: 0: a.c -= a.m ; 1: b.c = -a.m ; 2: a.c += b.c
 __global__ void k_scal(LevelScal *a, LevelScal *b, int op)
 {
+    a = &MG5_AT(a, 0);
+    b = &MG5_AT(b, 0);
     if (op == 0)
         a->c -= a->m;
     else if (op == 1)
@@ -454,6 +456,8 @@ int solve_mixed(MixedHier *h, const MixedShared &sh, const double *delta, const 
 __global__ void k_mixed_check(const LevelScal *__restrict__ ls0, BoxCtl *ctl,
                               cudaGraphConditionalHandle hnd)
 {
+    ls0 = &MG5_AT(ls0, 0);
+    ctl = &MG5_AT(ctl, 0);
     const double rel = ls0->rel;
     const int k = ctl->outer;
     if (k < 64) {
@@ -490,6 +494,7 @@ __global__ void k_mixed_check(const LevelScal *__restrict__ ls0, BoxCtl *ctl,
 
 __global__ void k_ctl_init(BoxCtl *ctl, double tol, int max_outer)
 {
+    ctl = &MG5_AT(ctl, 0);
     ctl->tol = tol;
     ctl->max_outer = max_outer;
     ctl->outer = 0;

@@ -45,11 +45,11 @@ __global__ void k_residual_partials(const double *__restrict__ phi, const double
         const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
         St<double> s;
         gather(phi, phi, r, k, kp, km, s);
-        acc.add(cell_residual(s, f[t] + c, cf));
+        acc.add(cell_residual(s, MG5_AT(f, t) + c, cf));
     }
     const Moments m = block_moments(acc);
     if (threadIdx.x == 0)
-        partials[blockIdx.x] = m;
+        MG5_AT(partials, blockIdx.x) = m;
 }
 
 // out[0] = mean r, out[1] = ||r - mean r||_2, out[2] = ||r||_2 from the blocks' shifted
@@ -58,10 +58,10 @@ __global__ void k_residual_partials(const double *__restrict__ phi, const double
 __global__ void k_norm_finalize(const mg5::Moments *__restrict__ partials, int nb, double *out)
 {
     using namespace mg5;
-    const double k0 = partials[0].k;
+    const double k0 = MG5_AT(partials, 0).k;
     Moments v{0.0, k0, 0.0, 0.0};
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const Moments u = mom_shift(partials[b], k0);
+        const Moments u = mom_shift(MG5_AT(partials, b), k0);
         v.n += u.n;
         v.s += u.s;
         v.q += u.q;
@@ -71,9 +71,9 @@ __global__ void k_norm_finalize(const mg5::Moments *__restrict__ partials, int n
         double m = 0.0, m2 = 0.0;
         if (v.n > 0.0)
             mom_mean_m2(v, &m, &m2);
-        out[0] = m;
-        out[1] = sqrt(m2);
-        out[2] = sqrt(fma(v.n * m, m, m2));   // sum r^2 = M2 + n mean^2
+        MG5_AT(out, 0) = m;
+        MG5_AT(out, 1) = sqrt(m2);
+        MG5_AT(out, 2) = sqrt(fma(v.n * m, m, m2));   // sum r^2 = M2 + n mean^2
     }
 }
 
@@ -93,6 +93,9 @@ cudaError_t partials_address(mg5::Moments **out)
         if (e != cudaSuccess)
             return e;
         g_noalloc_ptr[dev] = static_cast<mg5::Moments *>(p);
+#ifdef MG5_BOUNDS
+        mg5::bnd::note_range(p, sizeof(g_noalloc_partials));
+#endif
     }
     *out = g_noalloc_ptr[dev];
     return cudaSuccess;

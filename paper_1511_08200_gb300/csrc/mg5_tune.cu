@@ -61,7 +61,7 @@ __global__ void k_tune_fill(T *a, int n, double amp, int salt)
     const double w = 6.283185307179586 / n;
     const double v = sin(w * (i + salt)) * cos(w * j) + 0.5 * sin(w * (k + 2 * salt)) +
                      0.01 * (((i + j + k) & 1) ? 1.0 : -1.0);
-    a[t] = (T)(amp * v);
+    MG5_AT(a, t) = (T)(amp * v);
 }
 
 struct TuneBufs {
