@@ -14,8 +14,9 @@ namespace mg5 {
 
 // --------------------------------------------------------------------------
 // snapshot red-black sweep: two passes.
-// Red pass: red cells ((i+j+k) even) from `in`; black cells copied.
-// Black pass: faces (red, new) from `out`, edges (black, old) from `in`.
+// Red pass: red cells ((i+j+k) even) from `in` into `out`.
+// Black pass: faces (red, new) from `out`, the centre and the edges (black, old) from `in`,
+// into `out`; between them the two passes write every cell of `out` once.
 // Each thread owns the pair (2kk, 2kk+1) of one row, one cell of each colour.
 // --------------------------------------------------------------------------
 template <typename T, bool BASE>
@@ -32,9 +33,8 @@ __global__ void k_sweep_red(const T *__restrict__ in, T *__restrict__ out, const
     const long long q = t / half;
     const int j = (int)(q % n), i = (int)(q / n);
     const int par = (i + j) & 1;
-    const int kr = 2 * kk + par, kb = 2 * kk + 1 - par;
+    const int kr = 2 * kk + par;
     const Rows r = periodic_rows(n, i, j);
-    MG5_AT(out, r.r00 + kb) = MG5_AT(in, r.r00 + kb);
     const int kp = (kr == n - 1) ? 0 : kr + 1, km = (kr == 0) ? n - 1 : kr - 1;
     St<T> s, sb;
     gather(in, in, r, kr, kp, km, s);
@@ -64,7 +64,7 @@ __global__ void k_sweep_black(const T *__restrict__ in, T *out, const T *__restr
     const Rows r = periodic_rows(n, i, j);
     const int kp = (kb == n - 1) ? 0 : kb + 1, km = (kb == 0) ? n - 1 : kb - 1;
     St<T> s, sb;
-    gather((const T *)out, in, r, kb, kp, km, s);
+    gather3((const T *)out, in, in, r, kb, kp, km, s);
     if constexpr (BASE)
         gather(B, B, r, kb, kp, km, sb);
     bool cl = false;

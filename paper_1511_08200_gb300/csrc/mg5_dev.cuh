@@ -117,12 +117,12 @@ __device__ __forceinline__ Rows box_rows(int d1, int d2, int i, int j)
     return r;
 }
 
-// Faces (and the centre) from F, edges from E.
+// Faces from F, edges from E, the centre from C.
 template <typename T>
-__device__ __forceinline__ void gather(const T *F, const T *E, const Rows &r, int k, int kp,
-                                       int km, St<T> &s)
+__device__ __forceinline__ void gather3(const T *F, const T *E, const T *C, const Rows &r, int k,
+                                        int kp, int km, St<T> &s)
 {
-    s.c = MG5_AT(F, r.r00 + k);
+    s.c = MG5_AT(C, r.r00 + k);
     s.xp = MG5_AT(F, r.rp0 + k);
     s.xm = MG5_AT(F, r.rm0 + k);
     s.yp = MG5_AT(F, r.r0p + k);
@@ -141,6 +141,14 @@ __device__ __forceinline__ void gather(const T *F, const T *E, const Rows &r, in
     s.ypzm = MG5_AT(E, r.r0p + km);
     s.ymzp = MG5_AT(E, r.r0m + kp);
     s.ymzm = MG5_AT(E, r.r0m + km);
+}
+
+// Faces (and the centre) from F, edges from E.
+template <typename T>
+__device__ __forceinline__ void gather(const T *F, const T *E, const Rows &r, int k, int kp,
+                                       int km, St<T> &s)
+{
+    gather3(F, E, F, r, k, kp, km, s);
 }
 
 // The 19 offsets of a cell's stencil within one array (St order), for kernels that
