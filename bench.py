@@ -80,7 +80,7 @@ WORK = {
 TRAFFIC_PER_CELL = {
     "sweep32": 255.4e6 / 256 ** 3,
     "resid_restrict32": 221.9e6 / 256 ** 3,
-    "sweep64": 84.4e6 / 128 ** 3,          # red + black launch, cold-cache ncu capture at 128^3
+    "sweep64": 89.6e6 / 128 ** 3,          # red + black launch, cold-cache ncu capture at 128^3
 }
 
 
