@@ -118,7 +118,8 @@ struct SweepSchedule {
     float ms = 0.f;   // tuned time of one sweep (0: not measured)
 };
 // The schedule of (device, precision, side): the tuned one, else the default
-// (FP64 two-pass; the mixed mode's FP32 correction form fused where it fits).
+// (FP64 two-pass; the mixed mode's FP32 correction form as a column march on sides that are
+// multiples of 32, else fused where it fits).
 SweepSchedule sweep_schedule(int device, int precision, int n);
 // Changes with every change of the schedule table (captured solves record it; mg5_tune.cu).
 unsigned long long schedule_version();
