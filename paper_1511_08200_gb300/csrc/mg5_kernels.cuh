@@ -154,6 +154,15 @@ cudaError_t launch_resid_restrict(const T *v, const T *f, const double *cptr, in
                                   const Fin &fin = Fin());
 // the same for the FP32 correction form (B required) as a column march (k_march_resid.cu):
 // n a multiple of 32; the coarse values equal the gather kernel's to the bit
+// The bottom of a V-cycle in one CTA (k_bottom.cu): the visit of grid a (side na <= 8) and
+// the solve of the coarsest grid b = na / 2 below it, for periodic grids; Ba/Bb the bases of
+// the mixed mode's correction form (both or neither).
+bool bottom_ok(int na);
+template <typename T>
+cudaError_t launch_bottom(T *va, const T *fa, const T *Ba, const T *Bb, int na, CoefT<T> cfa,
+                          CoefT<T> cfb, const LevelScal *ls_up, LevelScal *lsa, LevelScal *lsb,
+                          int nu1, int nu2, int nu_coarse, double rtol, unsigned long long *clamp,
+                          int *sweeps, cudaStream_t st);
 bool resid_march_ok(int n);
 cudaError_t prepare_resid_march_kernel();
 cudaError_t launch_resid_restrict_march(const float *e, const float *f, const double *cptr, int n,

@@ -164,6 +164,19 @@ struct RunMix {
     int coarse_visit(int l)
     {
         cudaError_t e;
+        if (l == h->nlev - 2 && bottom_ok(h->n[l]) && h->n[l + 1] < kSpectralMinSide) {
+            // this grid and the coarsest one in a single launch (k_bottom.cu)
+            ProfScope ps(sh.prof, PK_COARSEST32, st);
+            e = launch_bottom<float>(h->e[l], h->f[l], h->B[l], h->B[l + 1], h->n[l],
+                                     make_coef<float>(hl[l], p->alpha, omega_of(p)),
+                                     make_coef<float>(hl[l + 1], p->alpha, omega_of(p)), ls(l - 1),
+                                     ls(l), ls(l + 1), p->nu1, p->nu2, p->nu_coarse, kCoarseRtol,
+                                     &sh.cnt->clamped, &sh.cnt->coarse_sweeps, st);
+            if (e != cudaSuccess)
+                return fail("bottom32", e);
+            cu += (long long)(p->nu1 + p->nu2) * h->n[l] * h->n[l] * h->n[l];
+            return MG5_OK;
+        }
         {
             ProfScope ps(sh.prof, PK_COARSE_RHS32, st, (double)(h->n[l]) * (h->n[l]) * (h->n[l]));
             e = launch_coarse_rhs<float>(h->e[l], h->f[l], m(l - 1), c(l), h->n[l],
