@@ -60,6 +60,49 @@ __device__ __forceinline__ void bsweep(T *v, T *w, const T *f, const T *B, bool 
     }
 }
 
+// the coarsest grid (at most 64 cells) is iterated by the first two warps alone: a barrier
+// over those 64 threads and their sum of a double2 (fixed order: warp 0, then warp 1)
+__device__ __forceinline__ void bar64() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+__device__ __forceinline__ double2 sum64(double2 v, double2 *sm)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    if ((threadIdx.x & 31) == 0)
+        sm[threadIdx.x >> 5] = v;
+    bar64();
+    const double2 r = make_double2(sm[0].x + sm[1].x, sm[0].y + sm[1].y);
+    bar64();
+    return r;
+}
+
+template <typename T, bool BASE>
+__device__ __forceinline__ void bsweep64(T *v, T *w, const T *f, const T *B, bool mine, int p,
+                                         const Nbr &nb, int colour_me, T c, const CoefT<T> &cf,
+                                         unsigned long long &clamps)
+{
+    for (int colour = 0; colour < 2; ++colour) {
+        const T *src = colour == 0 ? v : w;
+        T *dst = colour == 0 ? w : v;
+        if (mine) {
+            if (colour_me != colour) {
+                MG5_AT(dst, p) = MG5_AT(src, p);
+            } else {
+                St<T> s, sb;
+                gather_nbr(src, nb, s);
+                if constexpr (BASE)
+                    gather_nbr(B, nb, sb);
+                bool cl = false;
+                MG5_AT(dst, p) = upd<T, BASE>(s, sb, MG5_AT(f, p) + c, cf, cl);
+                clamps += cl ? 1ull : 0ull;
+            }
+        }
+        bar64();
+    }
+}
+
 template <typename T, bool BASE>
 __global__ void __launch_bounds__(kBottomThreads)
     k_bottom(T *__restrict__ va_g, const T *__restrict__ fa_g, const T *__restrict__ Ba_g,
@@ -70,6 +113,7 @@ __global__ void __launch_bounds__(kBottomThreads)
 {
     __shared__ BottomSmem<T> S;
     __shared__ double bc_s[2];
+    __shared__ double2 s64[2];
     const int nb = na >> 1;
     const int na3 = na * na * na, nb3 = nb * nb * nb;
     const int p = threadIdx.x;
@@ -169,34 +213,35 @@ __global__ void __launch_bounds__(kBottomThreads)
     const double inv_nb3 = 1.0 / (double)nb3;
     double r0 = -1.0, cb = 0.0;
     int it = 0;
-    for (; it < nu_coarse; ++it) {
-        double2 a2 = make_double2(0.0, 0.0);
-        if (mine_b) {
-            St<T> s, sb;
-            gather_nbr((const T *)S.bv, nbr_b, s);
-            if constexpr (BASE)
-                gather_nbr((const T *)S.bB, nbr_b, sb);
-            const double res = (double)resid_of<T, BASE>(s, sb, S.bf[p], cfb);
-            a2.x = res;
-            a2.y = res * res;
+    if (p < 64) {
+        for (; it < nu_coarse; ++it) {
+            double2 a2 = make_double2(0.0, 0.0);
+            if (mine_b) {
+                St<T> s, sb;
+                gather_nbr((const T *)S.bv, nbr_b, s);
+                if constexpr (BASE)
+                    gather_nbr((const T *)S.bB, nbr_b, sb);
+                const double res = (double)resid_of<T, BASE>(s, sb, S.bf[p], cfb);
+                a2.x = res;
+                a2.y = res * res;
+            }
+            a2 = sum64(a2, s64);
+            const double m = a2.x * inv_nb3;
+            const double q2 = a2.y - (double)nb3 * m * m;
+            const double rn = sqrt(q2 > 0.0 ? q2 : 0.0);
+            cb = -m;
+            if (r0 < 0.0)
+                r0 = rn;
+            if (rn <= rtol * r0)
+                break;
+            bsweep64<T, BASE>(S.bv, S.bw, S.bf, S.bB, mine_b, p, nbr_b, colour_b, (T)cb, cfb,
+                              clamps);
         }
-        a2 = block_sum2(a2);
-        if (p == 0) {
-            bc_s[0] = a2.x;
-            bc_s[1] = a2.y;
-        }
-        __syncthreads();
-        const double m = bc_s[0] * inv_nb3;
-        const double q2 = bc_s[1] - (double)nb3 * m * m;
-        const double rn = sqrt(q2 > 0.0 ? q2 : 0.0);
-        __syncthreads();
-        cb = -m;
-        if (r0 < 0.0)
-            r0 = rn;
-        if (rn <= rtol * r0)
-            break;
-        bsweep<T, BASE>(S.bv, S.bw, S.bf, S.bB, mine_b, p, nbr_b, colour_b, (T)cb, cfb, clamps);
+        if (p == 0)
+            bc_s[1] = cb;
     }
+    __syncthreads();
+    cb = bc_s[1];
 
     // prolongation of b's correction onto a (cell-centred trilinear, periodic), c_a += c_b
     if (mine) {
