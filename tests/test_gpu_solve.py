@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import workload
-from tests.gpu_common import ctx_fixture, dev, host, nominal, rel_l2
+from tests.gpu_common import ctx_fixture, dev, host, need_gpu, nominal, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -212,6 +212,7 @@ def test_stopping_norm_when_the_mean_dominates(ctx, precision):
 
 
 def test_budget_is_enforced():
+    need_gpu()
     import torch
     mg = _mg()
     alpha, s, h = nominal()
@@ -354,7 +355,24 @@ def _window(a, o, w):
     return a[..., ix[0][:, None, None], ix[1][None, :, None], ix[2][None, None, :]]
 
 
-def test_mixed_512_full_size():
+@pytest.fixture(scope="module")
+def oracle512():
+    """The 512^3 sigma = 2 input of the mixed512 / fp64_512 records and the FP64 oracle's own
+    solve of it (tolerance 1e-11, on the host cores; a few minutes), shared by the tests below."""
+    need_gpu()
+    import torch
+    alpha, s, h = nominal()
+    n = 512
+    d = workload.lognormal_delta_torch(n, 2.0, 3, torch.device("cuda"))   # bench.py's field
+    delta = host(d)
+    del d
+    torch.cuda.empty_cache()
+    ref, rinfo = oracle.solve(delta, alpha, s, h, tol=1e-11)
+    assert rinfo.rel_residual <= 1e-11
+    return delta, ref, oracle.force(ref, h), workload.densest_window(delta, 128)
+
+
+def test_mixed_512_full_size(oracle512):
     """The 512^3 sigma = 2 mixed-precision workload as bench.py runs it (the same input field,
     tuned sweep schedules) against the FP64 oracle's own 512^3 solve (tolerance 1e-11, on the
     host cores): phi and the force within relative L2 1e-6 on the 128^3 subvolume at the
@@ -364,9 +382,9 @@ def test_mixed_512_full_size():
     mg = _mg()
     alpha, s, h = nominal()
     n = 512
+    delta, ref, ref_g, dense = oracle512
     ctx = mg.Context(0)
-    d = workload.lognormal_delta_torch(n, 2.0, 3, torch.device("cuda"))
-    delta = host(d)
+    d = dev(delta)
     ctx.autotune(n, "mixed")
     pm = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-8, precision="mixed")
     grad = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
@@ -379,15 +397,36 @@ def test_mixed_512_full_size():
     r = oracle.residual(got, s * delta, im.compat_c, h, alpha)
     assert np.linalg.norm(r) / np.linalg.norm(s * delta) <= 1e-8
     del r
-    ref, rinfo = oracle.solve(delta, alpha, s, h, tol=1e-11)
-    assert rinfo.rel_residual <= 1e-11
-    ref_g = oracle.force(ref, h)
-    dense = workload.densest_window(delta, 128)
     for o in ((0, 0, 0), dense):
         assert rel_l2(_window(got, o, 128), _window(ref, o, 128)) <= 1e-6, o
         assert rel_l2(_window(got_g, o, 128), _window(ref_g, o, 128)) <= 1e-6, o
     assert rel_l2(got, ref) <= 1e-6
     assert rel_l2(got_g, ref_g) <= 1e-6
+
+
+def test_fp64_512_full_size(oracle512):
+    """The fp64_512 record's configuration (the same 512^3 input, FP64 mode, full-multigrid
+    start, graph replay) solved to 1e-12 against the oracle's 512^3 solution: phi and the force
+    within relative L2 1e-10 over the whole grid and on the densest 128^3 window."""
+    import torch
+    mg = _mg()
+    alpha, s, h = nominal()
+    n = 512
+    delta, ref, ref_g, dense = oracle512
+    ctx = mg.Context(0)
+    d = dev(delta)
+    p = mg.default_params(alpha=alpha, s=s, h=h, tol=1e-12)
+    grad = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+    phi, _, info = ctx.solve_fifth_force(d, p, grad=grad, fmg=True, graph=True)
+    assert info.status == 0 and info.rel_residual <= 1e-12
+    got, got_g = host(phi), host(grad)
+    ctx.close()
+    del phi, grad, d
+    torch.cuda.empty_cache()
+    assert rel_l2(got, ref) <= 1e-10
+    assert rel_l2(got_g, ref_g) <= 1e-10
+    assert rel_l2(_window(got, dense, 128), _window(ref, dense, 128)) <= 1e-10
+    assert rel_l2(_window(got_g, dense, 128), _window(ref_g, dense, 128)) <= 1e-10
 
 
 def test_graph_solve_equals_host_driven(ctx):
