@@ -436,6 +436,10 @@ def run_ours(args):
     if args.serve_seconds > 0:
         out["serving"] = run_serving(mg, torch, dev, step.alpha, step.s, args.serve_seconds,
                                      slots=args.serve_slots, autotune=not args.no_autotune)
+    if args.serve_seconds > 0 and args.serve_compare_seconds > 0:
+        out["serving_vs_fp64"] = serving_vs_fp64(mg, torch, dev, step.alpha, step.s,
+                                                 args.serve_compare_seconds, args.serve_slots,
+                                                 autotune=not args.no_autotune)
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(coarse, patch, origin, budget_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
@@ -825,26 +829,28 @@ class FieldFeeder:
 
 
 def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=5.0,
-                autotune=True):
+                autotune=True, precision="mixed", max_backlog=1024):
     """Poisson arrivals at `rate` req/s for `seconds`: sides 16 round(10^U(log 32, log 256)/16),
-    sigma ~ U(0.5, 2), tol 1e-6 or 1e-8 with p = 1/2, mixed precision, every request its own
-    field (generated ahead of its arrival on a side stream); admitted by HBM footprint.
-    Latency = completion - arrival (server clock); the first `warm_s` seconds are discarded
-    (a fifth of the run if that is shorter)."""
+    sigma ~ U(0.5, 2), tol 1e-6 or 1e-8 with p = 1/2, every request its own field (generated
+    ahead of its arrival on a side stream), all in one `precision` ("mixed": captured graphs
+    from the server's pool; "fp64": host-driven solves on the workers' contexts); admitted by
+    HBM footprint.  Latency = completion - arrival (server clock); the first `warm_s` seconds
+    are discarded (a fifth of the run if that is shorter).  A server that falls behind (more
+    than `max_backlog` requests submitted and not done) ends the run early: saturated."""
     count = int(rate * seconds * 1.2) + 8
     gaps, sizes, sigmas, tols = serving_stream(count, rate)
     budget = int(torch.cuda.get_device_properties(dev).total_memory * 0.5)
-    if autotune:   # the schedule table is process-wide: the server's captures read it
+    if autotune:   # the schedule table is process-wide: the server's solves read it
         tctx = mg.Context(dev.index or 0)
         for n in sorted(set(int(x) for x in sizes)):
-            tctx.autotune(n, "mixed")
+            tctx.autotune(n, precision)
         tctx.close()
     srv = mg.Server(dev.index or 0, slots=slots, hbm_budget_bytes=budget)
     # warm the server's graph pool (two entries per (size, tolerance): its cap) before timing
     for i, n in enumerate(sorted(set(int(x) for x in sizes))):
         dw = workload_field(torch, dev, n)
         for j, tol in enumerate((1e-6, 1e-8)):
-            p = mg.default_params(alpha=alpha, s=s, h=L_BOX / 512, tol=tol, precision="mixed")
+            p = mg.default_params(alpha=alpha, s=s, h=L_BOX / 512, tol=tol, precision=precision)
             for r in range(2):
                 srv.submit(dw, p, torch.zeros_like(dw), tag=10 ** 9 + 4 * i + 2 * j + r)
         while srv.pending() != (0, 0):
@@ -857,12 +863,17 @@ def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=
     t_start = srv.clock()
     t_next = t_start
     i = 0
+    saturated = False
     while True:
         now = srv.clock()
         if now - t_start >= seconds:
             break
+        if i - len(done) > max_backlog:
+            saturated = True
+            break
         if now >= t_next and i < count:
-            p = mg.default_params(alpha=alpha, s=s, h=L_BOX / 512, tol=float(tols[i]), precision="mixed")
+            p = mg.default_params(alpha=alpha, s=s, h=L_BOX / 512, tol=float(tols[i]),
+                                  precision=precision)
             d = feeder.take(i)
             srv.submit(d, p, torch.empty_like(d), tag=i)
             t_next += gaps[i]
@@ -872,13 +883,14 @@ def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=
             done[c.tag] = c
         time.sleep(max(0.0, min(t_next - srv.clock(), 0.0005)))
     submitted = i
+    srv_end = srv.clock()
     feeder.close()
     while len(done) < submitted:
         for c in srv.poll(wait_ms=100):
             done[c.tag] = c
     stats = srv.stats()
     srv.close()
-    warm = min(warm_s, seconds / 5.0)
+    warm = min(warm_s, (srv_end - t_start) / 5.0)
     rows = [c for c in done.values() if c.t_submit - t_start >= warm]
     lat = np.array([(c.t_done - c.t_submit) * 1e3 for c in rows])
     t_first = min(c.t_submit for c in rows)
@@ -886,7 +898,9 @@ def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=
     cu = sum(c.info.cell_updates for c in rows)
     ok = sum(1 for c in rows if c.status in (0, 1))
     lag = [(c.t_submit - t_start) - float(np.sum(gaps[:c.tag])) for c in rows]
-    return {"offered_req_per_s": rate, "seconds": seconds, "discarded_s": warm, "slots": slots,
+    return {"precision": precision, "offered_req_per_s": rate, "seconds": seconds,
+            "ran_s": float(srv_end - t_start), "saturated": saturated,
+            "discarded_s": warm, "slots": slots,
             "requests": len(rows), "submitted": submitted, "completed_ok": ok,
             "distinct_inputs": len(rows),
             "throughput_req_per_s": len(rows) / (t_last - t_first),
@@ -897,6 +911,24 @@ def run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=16, warm_s=
             "mean_cells_per_request": float(np.mean([int(sizes[c.tag]) ** 3 for c in rows])),
             "sigma_range": [float(sigmas[:submitted].min()), float(sigmas[:submitted].max())],
             "hbm_budget_bytes": budget, "server": stats}
+
+
+def serving_vs_fp64(mg, torch, dev, alpha, s, seconds, slots, rate=100.0, autotune=True):
+    """The serving stream in mixed precision and in plain FP64 on the same server, at `rate`
+    req/s (half the main run's) for `seconds` each, and FP64 at the main run's 200 req/s until
+    it falls behind (more than 512 requests outstanding): its capacity."""
+    keys = ("saturated", "ran_s", "requests", "throughput_req_per_s", "cell_updates_per_s",
+            "latency_ms", "completed_ok")
+    out = {"offered_req_per_s": rate, "seconds": seconds, "slots": slots}
+    for prec in ("mixed", "fp64"):
+        r = run_serving(mg, torch, dev, alpha, s, seconds, rate=rate, slots=slots,
+                        autotune=autotune, precision=prec, max_backlog=512)
+        out[prec] = {k: r[k] for k in keys}
+    r = run_serving(mg, torch, dev, alpha, s, seconds, rate=200.0, slots=slots,
+                    autotune=autotune, precision="fp64", max_backlog=512)
+    out["fp64_at_200"] = {k: r[k] for k in keys}
+    out["p99_fp64_over_mixed"] = out["fp64"]["latency_ms"]["p99"] / out["mixed"]["latency_ms"]["p99"]
+    return out
 
 
 def workload_field(torch, dev, n):
@@ -1188,6 +1220,9 @@ def main():
                     help="default sweep schedules instead of the tuned ones")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the serving run (0 skips it)")
+    ap.add_argument("--serve-compare-seconds", type=float, default=12.0,
+                    help="length of each leg of the mixed-vs-FP64 serving comparison "
+                         "(0 skips it, as --serve-seconds 0 does)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

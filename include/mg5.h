@@ -392,7 +392,10 @@ int mg5_tune_load(const char *path);
  * in arrival order when a worker is free and the HBM the request adds fits
  * hbm_budget_bytes next to what all workers hold (0 = no cap); idle workers
  * drop cached hierarchies when an admission waits for memory.  Admitted solves
- * run concurrently.  Results are deterministic: the same alone and in the mix. */
+ * run concurrently, as replays of captured solves from a pool the workers share
+ * (MG5_MIXED; MG5_FP64 with two grids or more and nu1 + nu2 even), else
+ * host-driven on the worker's context.  Results are deterministic: the same
+ * alone and in the mix. */
 typedef struct mg5_server mg5_server;
 
 typedef struct {

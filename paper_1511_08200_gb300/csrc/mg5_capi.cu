@@ -1895,7 +1895,10 @@ static bool same_params(const mg5_params &a, const mg5_params &b)
 
 namespace mg5 {
 
-size_t graph_bytes(int N, bool grad) { return graph_entry_bytes(N, grad); }
+size_t graph_bytes(int N, int precision, bool grad)
+{
+    return precision == MG5_FP64 ? graph_entry_bytes64(N, grad) : graph_entry_bytes(N, grad);
+}
 
 size_t graph_held(mg5_ctx *ctx)
 {
@@ -2347,7 +2350,40 @@ static int get_graph_entry(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, 
     return MG5_OK;
 }
 
-// MG5_MIXED from zero through the cached graph: copy in, one graph launch, copy out.
+}  // extern "C"
+
+namespace mg5 {
+
+bool graph_capturable(int N, const mg5_params *p)
+{
+    if (p->precision != MG5_FP64)
+        return true;
+    int sz[kMaxLevels];
+    return num_levels(N, sz) >= 2 && (p->nu1 + p->nu2) % 2 == 0;
+}
+
+int graph_build_in(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, GraphEntry **out,
+                   std::string *err)
+{
+    if (p->precision != MG5_FP64)
+        return graph_build(ctx->device, N, p, grad, out, err);
+    *out = nullptr;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        *err = "graph solve: cannot select the device";
+        return MG5_E_CUDA;
+    }
+    const int rc = graph_build64(ctx, N, p, grad, false, out);
+    if (rc != MG5_OK)
+        *err = ctx->err;
+    return rc;
+}
+
+}  // namespace mg5
+
+extern "C" {
+
+// A solve from zero through the cached graph: copy in, one graph launch, copy out.
 static int solve_graph(mg5_ctx *ctx, const double *delta, int N, const mg5_params *p, double *phi,
                        double *grad, bool fmg, mg5_info *info, cudaStream_t st)
 {

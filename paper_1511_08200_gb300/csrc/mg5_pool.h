@@ -1,6 +1,7 @@
-// mg5_pool.h -- captured mixed-precision solves as reusable entries (library-internal).
+// mg5_pool.h -- captured solves as reusable entries (library-internal).
 //
-// An entry is one mixed solve of one grid size and parameter set captured as a
+// An entry is one solve from zero (MG5_MIXED, or MG5_FP64 without the
+// full-multigrid start) of one grid size and parameter set captured as a
 // CUDA graph, with its own hierarchy, scalars, staging buffers and a pinned
 // host block the solve's control state is copied into.  A context keeps its
 // entries in a list; an entry is busy from checkout until its result has been
@@ -22,13 +23,20 @@ struct GraphEntry;
 
 namespace mg5 {
 
-// Device bytes one entry holds.
-size_t graph_bytes(int N, bool grad);
+// Device bytes one entry of that precision holds.
+size_t graph_bytes(int N, int precision, bool grad);
+// Whether a solve of (N, p) can be captured: MG5_MIXED always; MG5_FP64 with two grids or
+// more and nu1 + nu2 even (the loop body must return every grid to its buffer).
+bool graph_capturable(int N, const mg5_params *p);
 // An idle entry of ctx for (N, p, grad), marked busy; nullptr if there is none.
 GraphEntry *graph_checkout(mg5_ctx *ctx, int N, const mg5_params *p, bool grad);
-// Build (allocate + capture + instantiate) a new entry on `device`, not yet in any list.
+// Build (allocate + capture + instantiate) a new MG5_MIXED entry on `device`, not yet in any list.
 int graph_build(int device, int N, const mg5_params *p, bool grad, GraphEntry **out,
                 std::string *err);
+// Build a new entry of p's precision on ctx's device (MG5_FP64 reads ctx's profiler switch and
+// writes its error text: the caller serialises builds on one ctx), not yet in any list.
+int graph_build_in(mg5_ctx *ctx, int N, const mg5_params *p, bool grad, GraphEntry **out,
+                   std::string *err);
 // Add a built entry to ctx's list (busy) and count its bytes in ctx.
 void graph_insert(mg5_ctx *ctx, GraphEntry *g);
 // Remove ctx's least recently used idle entry from its list (bytes uncounted); nullptr if none.

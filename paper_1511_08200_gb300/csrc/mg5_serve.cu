@@ -1,25 +1,26 @@
 // mg5_serve.cu -- continuous-batching solve server (host runtime, C ABI in mg5.h).
 //
 // `slots` worker threads each own a non-blocking CUDA stream and a context
-// (for FP64 solves, which run host-driven).  Requests queue in arrival order
-// and a free worker takes the oldest.  Mixed-precision solves run as captured
-// CUDA graphs from a pool shared by all workers: a worker checks out an idle
+// (for the solves that run host-driven).  Requests queue in arrival order and
+// a free worker takes the oldest.  Solves run as captured CUDA graphs from a
+// pool shared by all workers (MG5_MIXED always; MG5_FP64 when the V-cycle can
+// be captured: two grids or more, nu1 + nu2 even): a worker checks out an idle
 // entry for the request's (grid size, parameters, gradient), replays it on
 // its own stream and returns it, so a capture is paid once per key and per
 // concurrent use, not per worker.  Up to `slots` solves are on the GPU at
 // once, overlapping on the workers' streams.
 //
-// Memory: the server budget covers the pool's entries, the workers' FP64
+// Memory: the server budget covers the pool's entries, the workers' own
 // hierarchies and entries being built.  A request that does not fit evicts
 // idle pool entries (least recently used first) and asks idle workers to drop
-// their cached FP64 hierarchies; otherwise it waits for running solves to
+// their cached hierarchies; otherwise it waits for running solves to
 // return theirs.  A request larger than the whole budget is refused at submit.
 //
 // A key holds at most kDupCap entries: when they are all busy, the request runs
 // host-driven on the worker's own context (as fast, measured) instead of
 // building another, since building allocates and instantiates, which stalls the
 // solves in flight.  Captures and device frees are serialised by one gate that
-// FP64 solves hold shared: a free or a device-wide synchronisation in another
+// host-driven solves hold shared: a free or a device-wide synchronisation in another
 // thread can end a capture in progress.  A capture that fails anyway is retried once, then the
 // request runs host-driven on the worker's own context.  Every solve is
 // deterministic (fixed-order reductions, nothing shared between solves in
@@ -59,9 +60,10 @@ struct Job {
 // The footprint a request needs on a server that holds nothing.
 int request_bytes(const mg5_request &r, size_t *need)
 {
-    if (r.params.precision == MG5_MIXED)
-        return mg5_graph_workspace_bytes(r.N, r.grad != nullptr, need);
-    return mg5_workspace_bytes(r.N, r.params.precision, need);
+    const int rc = mg5_workspace_bytes(r.N, r.params.precision, need);   // checks N
+    if (rc == MG5_OK && mg5::graph_capturable(r.N, &r.params))
+        *need = mg5::graph_bytes(r.N, r.params.precision, r.grad != nullptr);
+    return rc;
 }
 
 }  // namespace
@@ -78,7 +80,7 @@ struct mg5_server {
     std::vector<size_t> held;          // bytes of each worker's own context
     mg5_ctx *pool = nullptr;           // graph entries shared by the workers
     size_t reserved = 0;               // bytes of entries being built
-    std::shared_mutex gate;            // exclusive: capture, free; shared: FP64 solves
+    std::shared_mutex gate;            // exclusive: capture, free; shared: host-driven solves
     int running = 0;
     bool stop = false;
     bool pressure = false;             // a worker waits for memory
@@ -151,8 +153,8 @@ bool wait_for_bytes(mg5_server *srv, int w, mg5_ctx *ctx, size_t need,
 int run_on_worker(mg5_server *srv, int w, mg5_ctx *ctx, cudaStream_t st, const mg5_request &r,
              mg5_completion *c);
 
-int run_mixed(mg5_server *srv, int w, mg5_ctx *ctx, cudaStream_t st, cudaEvent_t ev,
-              const mg5_request &r, mg5_completion *c)
+int run_pooled(mg5_server *srv, int w, mg5_ctx *ctx, cudaStream_t st, cudaEvent_t ev,
+               const mg5_request &r, mg5_completion *c)
 {
     const bool grad = r.grad != nullptr;
     GraphEntry *g = nullptr;
@@ -167,7 +169,7 @@ int run_mixed(mg5_server *srv, int w, mg5_ctx *ctx, cudaStream_t st, cudaEvent_t
                 host_driven = true;   // every entry of this key is busy
                 break;
             }
-            need = mg5::graph_bytes(r.N, grad);
+            need = mg5::graph_bytes(r.N, r.params.precision, grad);
             if (!srv->budget || srv->total_locked() + need <= srv->budget) {
                 srv->reserved += need;   // built below, outside the lock
                 break;
@@ -197,7 +199,7 @@ int run_mixed(mg5_server *srv, int w, mg5_ctx *ctx, cudaStream_t st, cudaEvent_t
         const double tb = now_s();
         for (int attempt = 0; attempt < 2 && rc != MG5_OK && rc != MG5_E_OOM; ++attempt) {
             std::unique_lock<std::shared_mutex> gl(srv->gate);
-            rc = mg5::graph_build(srv->device, r.N, &r.params, grad, &g, &err);
+            rc = mg5::graph_build_in(srv->pool, r.N, &r.params, grad, &g, &err);
         }
         {
             std::lock_guard<std::mutex> lk(srv->mu);
@@ -234,8 +236,8 @@ int run_mixed(mg5_server *srv, int w, mg5_ctx *ctx, cudaStream_t st, cudaEvent_t
     return rc;
 }
 
-// A solve on the worker's own context, host-driven (FP64 requests, and mixed ones whose
-// pooled graphs are all busy): its hierarchy stays cached there.
+// A solve on the worker's own context, host-driven (requests that cannot be captured, and
+// those whose pooled graphs are all busy): its hierarchy stays cached there.
 int run_on_worker(mg5_server *srv, int w, mg5_ctx *ctx, cudaStream_t st, const mg5_request &r,
              mg5_completion *c)
 {
@@ -295,8 +297,8 @@ void worker_main(mg5_server *srv, int w)
         if (rc_init != MG5_OK) {
             c.status = rc_init;
             c.t_admit = now_s() - srv->t0;
-        } else if (job.req.params.precision == MG5_MIXED) {
-            c.status = run_mixed(srv, w, ctx, st, ev, job.req, &c);
+        } else if (mg5::graph_capturable(job.req.N, &job.req.params)) {
+            c.status = run_pooled(srv, w, ctx, st, ev, job.req, &c);
         } else {
             c.status = run_on_worker(srv, w, ctx, st, job.req, &c);
         }

@@ -54,6 +54,36 @@ def test_server_same_alone_and_in_mix():
     ctx.close()
 
 
+def test_server_fp64_and_mixed_same_alone_and_in_mix():
+    """FP64 requests (host-driven on the workers' contexts) interleaved with mixed ones
+    (captured graphs): every result is bit-identical to the same solve alone."""
+    import torch
+    mg = _mg()
+    ctx = ctx_fixture()
+    reqs, alpha, s, h = _requests(seed=8)
+    srv = mg.Server(0, slots=4)
+    deltas, phis, params = {}, {}, {}
+    for tag, n, d, tol in reqs:
+        prec = "fp64" if tag % 2 == 0 else "mixed"
+        deltas[tag] = dev(d)
+        phis[tag] = torch.full_like(deltas[tag], float("nan"))
+        params[tag] = mg.default_params(alpha=alpha, s=s, h=h, tol=tol, precision=prec)
+        srv.submit(deltas[tag], params[tag], phis[tag], tag=tag)
+    got = {}
+    while len(got) < len(reqs):
+        for c in srv.poll(wait_ms=2000):
+            got[c.tag] = c
+    srv.close()
+    for tag, n, d, tol in reqs:
+        c = got[tag]
+        assert c.status == 0, c
+        assert c.info.rel_residual <= tol
+        alone, _, ia = ctx.solve_fifth_force(deltas[tag], params[tag])
+        assert torch.equal(alone, phis[tag]), tag
+        assert ia.cycles == c.info.cycles
+    ctx.close()
+
+
 def test_server_respects_hbm_budget():
     """With a budget below two 96^3 hierarchies, requests still all complete, one
     at a time, and the held bytes never exceed the budget at the end."""
