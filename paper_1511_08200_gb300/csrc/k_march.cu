@@ -27,9 +27,10 @@
 // barrier.  320 threads and 67 KB of shared memory a CTA: two CTAs per SM, so one CTA's
 // barrier waits overlap the other's work.
 //
-// Every cell is updated by the same arithmetic on the same operands, in the same order,
-// as the gather-based kernels (cell_update_corr_parts), so the result is the same sweep
-// to the bit.  Periodic in i, j, k; n a multiple of 32; out of place.
+// The plane values, sums and differences of e and B travel as (e, B) pairs through the
+// packed FP32 instructions (two lanes an instruction).  Every cell is updated by the same
+// arithmetic on the same operands, in the same order, as the gather-based kernels
+// (parts2_of, cell_update_corr_parts), so the result is the same sweep to the bit.  Periodic in i, j, k; n a multiple of 32; out of place.
 #include <type_traits>
 
 #include "mg5_async.cuh"
@@ -62,29 +63,34 @@ struct MarchSmem {
 };
 
 
-// values a position keeps between its two active steps (plane p: read two steps earlier as
-// plane p + 2; plane p - 1: read two steps earlier as plane p + 1)
+// values a position keeps between its two active steps, (e, B) pairs where both are used
+// (plane p: read two steps earlier as plane p + 2; plane p - 1: read two steps earlier as
+// plane p + 1)
 struct ColCache {
-    float cE0, DyE0, DzE0, dyzE0, cB0, DyB0, DzB0, dyzB0, YB0, ZB0;   // plane p
-    float DyEm, DzEm, DyBm, DzBm, cBm, rm;                            // plane p - 1, red(p - 1)
+    float2 c0, Dy0, Dz0, dyz0;   // plane p
+    float YB0, ZB0;              // plane p, B only (the black cell's e faces are new red values)
+    float2 Dym, Dzm;             // plane p - 1
+    float cBm, rm;               // plane p - 1: B's centre, the red value
 };
 
-// 3 x 3 neighbourhood of a position on one plane, reduced to what the cell arithmetic uses
-struct PlaneCol {
-    float c, Y, Z, Dy, Dz, dyz;
+// 3 x 3 neighbourhood of a position on one plane as (e, B) pairs, reduced to what the cell
+// arithmetic uses; the packed FP32 instructions do e and B together
+struct PlaneCol2 {
+    float2 c, Y, Z, Dy, Dz, dyz;
 };
 
-__device__ __forceinline__ PlaneCol plane_col(const float *base)
+__device__ __forceinline__ PlaneCol2 plane_col2(const float *be, const float *bb)
 {
-    PlaneCol r;
-    r.c = MG5_AT(base, 0);
-    const float yp = MG5_AT(base, MO), ym = MG5_AT(base, -MO), zp = MG5_AT(base, 1), zm = MG5_AT(base, -1);
-    const float pp = MG5_AT(base, MO + 1), pm = MG5_AT(base, MO - 1), mp = MG5_AT(base, -MO + 1), mm = MG5_AT(base, -MO - 1);
-    r.Y = __fadd_rn(yp, ym);
-    r.Z = __fadd_rn(zp, zm);
-    r.Dy = __fsub_rn(yp, ym);
-    r.Dz = __fsub_rn(zp, zm);
-    r.dyz = __fsub_rn(__fsub_rn(pp, pm), __fsub_rn(mp, mm));
+    const auto ld = [&](int o) { return make_float2(MG5_AT(be, o), MG5_AT(bb, o)); };
+    PlaneCol2 r;
+    r.c = ld(0);
+    const float2 yp = ld(MO), ym = ld(-MO), zp = ld(1), zm = ld(-1);
+    const float2 pp = ld(MO + 1), pm = ld(MO - 1), mp = ld(-MO + 1), mm = ld(-MO - 1);
+    r.Y = pk_add(yp, ym);
+    r.Z = pk_add(zp, zm);
+    r.Dy = pk_sub(yp, ym);
+    r.Dz = pk_sub(zp, zm);
+    r.dyz = pk_sub(pk_sub(pp, pm), pk_sub(mp, mm));
     return r;
 }
 
@@ -207,37 +213,29 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
             const float *B0 = Bs + s0 * MPL + ps.off, *B1 = Bs + s1 * MPL + ps.off,
                         *B2 = Bs + s2 * MPL + ps.off;
             if (warm) {
-                const PlaneCol e0 = plane_col(E0), b0 = plane_col(B0);
-                c.cE0 = e0.c;
-                c.DyE0 = e0.Dy;
-                c.DzE0 = e0.Dz;
-                c.dyzE0 = e0.dyz;
-                c.cB0 = b0.c;
-                c.DyB0 = b0.Dy;
-                c.DzB0 = b0.Dz;
-                c.dyzB0 = b0.dyz;
-                c.YB0 = b0.Y;
-                c.ZB0 = b0.Z;
+                const PlaneCol2 q0 = plane_col2(E0, B0);
+                c.c0 = q0.c;
+                c.Dy0 = q0.Dy;
+                c.Dz0 = q0.Dz;
+                c.dyz0 = q0.dyz;
+                c.YB0 = q0.Y.y;
+                c.ZB0 = q0.Z.y;
             }
-            const PlaneCol e2 = plane_col(E2), b2 = plane_col(B2);
-            const PlaneCol e1 = plane_col(E1), b1 = plane_col(B1);
+            const PlaneCol2 q2 = plane_col2(E2, B2), q1 = plane_col2(E1, B1);
             // red cell (p + 1) of the position: old values throughout (x faces: p + 2, p)
-            const Parts2 qr =
-                parts2_from_sums(__fadd_rn(e2.c, c.cE0), __fadd_rn(b2.c, c.cB0), e1.Y, b1.Y, e1.Z, b1.Z,
-                           __fsub_rn(e2.Dy, c.DyE0), __fsub_rn(b2.Dy, c.DyB0),
-                           __fsub_rn(e2.Dz, c.DzE0), __fsub_rn(b2.Dz, c.DzB0), e1.dyz, b1.dyz);
-            const float r1 = cell_update_corr_parts(qr, b1.c, e1.c, MG5_AT(F, s1 * MPL + ps.off) + cval, cf,
-                                                    clamped);
+            const Parts2 qr = parts2_from_pairs(pk_add(q2.c, c.c0), q1.Y, q1.Z, pk_sub(q2.Dy, c.Dy0),
+                                                pk_sub(q2.Dz, c.Dz0), q1.dyz);
+            const float r1 = cell_update_corr_parts(qr, q1.c.y, q1.c.x, MG5_AT(F, s1 * MPL + ps.off) + cval,
+                                                    cf, clamped);
             MG5_AT(S.RN[(set + 1) & 1], ps.rn) = r1;   // plane p + 1 (p - i0 has the parity of set)
             if (tile && !warm) {
                 // black cell (p) of the position: new red faces, old edges
                 const float *rn = S.RN[set & 1] + ps.rn;
                 const float sye = __fadd_rn(MG5_AT(rn, RNO), MG5_AT(rn, -RNO)), sze = __fadd_rn(MG5_AT(rn, 1), MG5_AT(rn, -1));
-                const Parts2 qb = parts2_from_sums(__fadd_rn(r1, c.rm), __fadd_rn(b1.c, c.cBm), sye,
-                                             c.YB0, sze, c.ZB0, __fsub_rn(e1.Dy, c.DyEm),
-                                             __fsub_rn(b1.Dy, c.DyBm), __fsub_rn(e1.Dz, c.DzEm),
-                                             __fsub_rn(b1.Dz, c.DzBm), c.dyzE0, c.dyzB0);
-                const float b0v = cell_update_corr_parts(qb, c.cB0, c.cE0,
+                const Parts2 qb = parts2_from_pairs(
+                    pk_add(make_float2(r1, q1.c.y), make_float2(c.rm, c.cBm)), make_float2(sye, c.YB0),
+                    make_float2(sze, c.ZB0), pk_sub(q1.Dy, c.Dym), pk_sub(q1.Dz, c.Dzm), c.dyz0);
+                const float b0v = cell_update_corr_parts(qb, c.c0.y, c.c0.x,
                                                          MG5_AT(F, s0 * MPL + ps.off) + cval, cf, clamped);
                 float2 v;
                 v.x = first[set] ? b0v : rprev;
@@ -245,21 +243,15 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
                 MG5_AT(reinterpret_cast<float2 *>(optr), 0) = v;
             }
             // keep plane p + 2 as the position's plane p, plane p + 1 as its plane p - 1
-            c.cE0 = e2.c;
-            c.DyE0 = e2.Dy;
-            c.DzE0 = e2.Dz;
-            c.dyzE0 = e2.dyz;
-            c.cB0 = b2.c;
-            c.DyB0 = b2.Dy;
-            c.DzB0 = b2.Dz;
-            c.dyzB0 = b2.dyz;
-            c.YB0 = b2.Y;
-            c.ZB0 = b2.Z;
-            c.DyEm = e1.Dy;
-            c.DzEm = e1.Dz;
-            c.DyBm = b1.Dy;
-            c.DzBm = b1.Dz;
-            c.cBm = b1.c;
+            c.c0 = q2.c;
+            c.Dy0 = q2.Dy;
+            c.Dz0 = q2.Dz;
+            c.dyz0 = q2.dyz;
+            c.YB0 = q2.Y.y;
+            c.ZB0 = q2.Z.y;
+            c.Dym = q1.Dy;
+            c.Dzm = q1.Dz;
+            c.cBm = q1.c.y;
             c.rm = r1;
             rprev = r1;
         }

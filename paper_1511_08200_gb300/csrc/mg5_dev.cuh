@@ -468,7 +468,7 @@ __device__ __forceinline__ float sigma_corr(const Parts2 &q, const CoefT<float> 
 
 // (e, B) parts of a cell from its face sums sx, sy, sz and mixed differences, each half in
 // scalar arithmetic: the same roundings as the packed pairs of parts2_of (kernels that build
-// the sums from cached plane values use this).
+// the sums from separately cached e and B plane values use this).
 __device__ __forceinline__ Parts2 parts2_from_sums(float sxe, float sxb, float sye, float syb,
                                                    float sze, float szb, float dxye, float dxyb,
                                                    float dxze, float dxzb, float dyze, float dyzb)
@@ -481,6 +481,23 @@ __device__ __forceinline__ Parts2 parts2_from_sums(float sxe, float sxb, float s
     q.dxy = make_float2(dxye, dxyb);
     q.dxz = make_float2(dxze, dxzb);
     q.dyz = make_float2(dyze, dyzb);
+    return q;
+}
+
+// (e, B) parts of a cell from its packed face sums sx, sy, sz and mixed differences: the
+// packed operations of parts2_of in the same order (kernels that build the sums from cached
+// plane values, two lanes an instruction).
+__device__ __forceinline__ Parts2 parts2_from_pairs(float2 sx, float2 sy, float2 sz, float2 dxy,
+                                                    float2 dxz, float2 dyz)
+{
+    Parts2 q;
+    q.S = pk_add(pk_add(sx, sy), sz);
+    q.a = pk_sub(sx, sy);
+    q.b = pk_sub(sx, sz);
+    q.c = pk_sub(sy, sz);
+    q.dxy = dxy;
+    q.dxz = dxz;
+    q.dyz = dyz;
     return q;
 }
 
