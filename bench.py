@@ -74,11 +74,11 @@ WORK = {
 
 # DRAM bytes per cell measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch / its cells), for the kernel as it stands; a launch's traffic = this x its cells.
-#   sweep32: k_sweep_march, 256^3 finest-grid launch: 204.6 + 50.9 MB / 16.78 M cells
+#   sweep32: k_sweep_march, 256^3 finest-grid launch: 204.6 + 50.7 MB / 16.78 M cells
 #   resid_restrict32: k_resid_restrict_march, 256^3 finest grid: 203.2 + 18.7 MB / 16.78 M cells
 #   sweep64: k_sweep_red + k_sweep_black<double,0>, 128^3 finest grid
 TRAFFIC_PER_CELL = {
-    "sweep32": 255.4e6 / 256 ** 3,
+    "sweep32": 255.2e6 / 256 ** 3,
     "resid_restrict32": 221.9e6 / 256 ** 3,
     "sweep64": 89.6e6 / 128 ** 3,          # red + black launch, cold-cache ncu capture at 128^3
 }

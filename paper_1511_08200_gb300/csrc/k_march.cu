@@ -70,7 +70,7 @@ struct ColCache {
     float2 c0, Dy0, Dz0, dyz0;   // plane p
     float YB0, ZB0;              // plane p, B only (the black cell's e faces are new red values)
     float2 Dym, Dzm;             // plane p - 1
-    float cBm, rm;               // plane p - 1: B's centre, the red value
+    float2 rBm;                  // plane p - 1: (the red value, B's centre)
 };
 
 // 3 x 3 neighbourhood of a position on one plane as (e, B) pairs, reduced to what the cell
@@ -228,12 +228,13 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
             const float r1 = cell_update_corr_parts(qr, q1.c.y, q1.c.x, MG5_AT(F, s1 * MPL + ps.off) + cval,
                                                     cf, clamped);
             MG5_AT(S.RN[(set + 1) & 1], ps.rn) = r1;   // plane p + 1 (p - i0 has the parity of set)
+            const float2 rB1 = make_float2(r1, q1.c.y);
             if (tile && !warm) {
                 // black cell (p) of the position: new red faces, old edges
                 const float *rn = S.RN[set & 1] + ps.rn;
                 const float sye = __fadd_rn(MG5_AT(rn, RNO), MG5_AT(rn, -RNO)), sze = __fadd_rn(MG5_AT(rn, 1), MG5_AT(rn, -1));
                 const Parts2 qb = parts2_from_pairs(
-                    pk_add(make_float2(r1, q1.c.y), make_float2(c.rm, c.cBm)), make_float2(sye, c.YB0),
+                    pk_add(rB1, c.rBm), make_float2(sye, c.YB0),
                     make_float2(sze, c.ZB0), pk_sub(q1.Dy, c.Dym), pk_sub(q1.Dz, c.Dzm), c.dyz0);
                 const float b0v = cell_update_corr_parts(qb, c.c0.y, c.c0.x,
                                                          MG5_AT(F, s0 * MPL + ps.off) + cval, cf, clamped);
@@ -251,8 +252,7 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
             c.ZB0 = q2.Z.y;
             c.Dym = q1.Dy;
             c.Dzm = q1.Dz;
-            c.cBm = q1.c.y;
-            c.rm = r1;
+            c.rBm = rB1;
             rprev = r1;
         }
     };
@@ -275,8 +275,40 @@ __global__ void __launch_bounds__(MT_THREADS, 2)
     step(IC<1>{}, IC<1>{}, true);
     finish(IC<1>{}, q0 + 1);
     // plane p's slot is (p - q0) % 6: steps i0, i0 + 1, ... use slots 2, 3, 4, 5, 0, 1 and
-    // position sets 0, 1, 0, 1, 0, 1 (unrolled by six: every slot offset is a constant)
+    // position sets 0, 1, 0, 1, 0, 1 (unrolled by twelve: every slot offset is a constant)
     for (int p = i0; p < i1;) {
+        step(IC<2>{}, IC<0>{}, false);
+        finish(IC<2>{}, p);
+        optr += n2;
+        if (++p >= i1)
+            break;
+        step(IC<3>{}, IC<1>{}, false);
+        finish(IC<3>{}, p);
+        optr += n2;
+        if (++p >= i1)
+            break;
+        step(IC<4>{}, IC<0>{}, false);
+        finish(IC<4>{}, p);
+        optr += n2;
+        if (++p >= i1)
+            break;
+        step(IC<5>{}, IC<1>{}, false);
+        finish(IC<5>{}, p);
+        optr += n2;
+        if (++p >= i1)
+            break;
+        step(IC<0>{}, IC<0>{}, false);
+        finish(IC<0>{}, p);
+        optr += n2;
+        if (++p >= i1)
+            break;
+        step(IC<1>{}, IC<1>{}, false);
+        finish(IC<1>{}, p);
+        optr += n2;
+        if (++p >= i1)
+            break;
+        // the same six again: each position set's cached values are replaced an even number
+        // of times a loop pass, so they can alternate between two register sets
         step(IC<2>{}, IC<0>{}, false);
         finish(IC<2>{}, p);
         optr += n2;

@@ -423,7 +423,12 @@ __device__ __forceinline__ T cell_update_corr(const St<T> &e, const St<T> &B, T 
 __device__ __forceinline__ float2 pk_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 pk_sub(float2 a, float2 b)
 {
-    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const unsigned long long *>(&a)),
+          "l"(*reinterpret_cast<const unsigned long long *>(&b)));
+    return *reinterpret_cast<const float2 *>(&d);
 }
 
 // Parts of e and B as (e, B) pairs, and the merged form
