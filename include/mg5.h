@@ -350,7 +350,8 @@ int mg5_solve_batch(mg5_ctx *ctx, int nbox, const double *const *delta, const in
  * The table is process-wide, keyed by (device, precision, grid side n); solves,
  * batch captures and MG5_GRAPH captures read it when they start (a captured
  * graph keeps the schedule it was captured with).  Defaults: FP64 two-pass with
- * 256 threads; the mixed mode's FP32 correction form as a column march where n is
+ * 256 threads a block, or on grids too small to give each of the 152 SMs two such
+ * blocks the multiple of 32 (at least 32) that does; the mixed mode's FP32 correction form as a column march where n is
  * a multiple of 32, else fused where n >= 32 and n % 4 == 0. */
 #define MG5_SWEEP_TWO_PASS 0
 #define MG5_SWEEP_FUSED    1
@@ -363,7 +364,7 @@ typedef struct {
     int chunk;   /* planes per CTA of the fused or march kernel (0 = automatic) */
     float ms;    /* the tuner's median time of one sweep (0 when set by hand) */
 } mg5_schedule;
-/* Time every candidate schedule (two-pass with 64/128/256/512 threads, fused with
+/* Time every candidate schedule (two-pass with 32/64/128/256/512 threads, fused with
  * 8/16/32 planes where it fits, and for MG5_MIXED the column march with automatic,
  * 16, 32, 64 or 128 planes where it fits) on a synthetic field of each grid side of the
  * hierarchy of N (coarsest excluded) on ctx's device and stream, and record the

@@ -117,7 +117,7 @@ template <typename T>
 cudaError_t launch_operator(const T *phi, int n, CoefT<T> cf, T *out, cudaStream_t st)
 {
     const long long work = (long long)n * n * n;
-    k_operator<T><<<blocks_for(work), kBlock, 0, st>>>(phi, n, cf, out);
+    k_operator<T><<<grid_spread(work), block_spread(work), 0, st>>>(phi, n, cf, out);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -157,10 +157,11 @@ cudaError_t launch_residual(const T *phi, const T *f, const double *cptr, int n,
 {
     const long long work = (long long)n * n * n;
     const int cap = sizeof(T) == 8 ? kReduceBlocksFp64 : kReduceBlocks;
-    int g = blocks_for(work);
+    const int bs = block_spread(work);
+    int g = grid_spread(work);
     if (g > cap)
         g = cap;
-    k_residual<T><<<g, kBlock, 0, st>>>(phi, f, cptr, n, cf, r, reinterpret_cast<Moments *>(partials),
+    k_residual<T><<<g, bs, 0, st>>>(phi, f, cptr, n, cf, r, reinterpret_cast<Moments *>(partials),
                                         fin);
     *nblocks = g;
     count_launch(1);
@@ -210,6 +211,65 @@ __global__ void k_resid_restrict(const T *__restrict__ v, const T *__restrict__ 
         finalize_if_last(reinterpret_cast<double2 *>(partials), fin);
 }
 
+// The same residual and restriction with a thread per fine cell, for the coarse grids of the
+// FP64 solves (up to kChildMaxFine fine cells; above that the FP64 pipe, not the chain, sets
+// the time, and the butterfly's extra adds made the 64^3 and 128^3 launches slower): eight
+// consecutive lanes hold the eight children of one coarse cell (child ch = lane & 7, its i, j
+// and k offsets ch >> 2, (ch >> 1) & 1 and ch & 1) and sum their centres and residuals by
+// three butterfly shuffles, ((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7)).  A thread
+// computes one FP64 residual instead of a chain of eight: GB300 runs FP64 at 2 lanes a clock
+// per SM, and on the coarse grids, whose blocks reach few SMs, that chain set the time.  The
+// loop runs over whole warps (four coarse cells a warp a pass), so every lane reaches the
+// shuffles.
+__global__ void k_resid_restrict_child(const double *__restrict__ v, const double *__restrict__ f,
+                                       const double *__restrict__ cptr, int n, CoefT<double> cf,
+                                       double *__restrict__ vc, double *__restrict__ v0c,
+                                       double *__restrict__ rc, Moments *__restrict__ partials,
+                                       Fin fin)
+{
+    const int nc = n >> 1;
+    const long long total = (long long)nc * nc * nc;
+    const double c = MG5_AT(cptr, 0);
+    const int lane = threadIdx.x & 31, ch = lane & 7;
+    const long long stride = (long long)gridDim.x * blockDim.x / 8;   // coarse cells a pass
+    MomAcc<double> acc;
+    for (long long t0 = ((long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / 8; t0 < total;
+         t0 += stride) {
+        const long long t = t0 + (lane >> 3);
+        const bool live = t < total;
+        double cv = 0.0, res = 0.0;
+        if (live) {
+            const int K = (int)(t % nc);
+            const long long q = t / nc;
+            const int J = (int)(q % nc), I = (int)(q / nc);
+            const int i = 2 * I + (ch >> 2), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch & 1);
+            const Rows r = periodic_rows(n, i, j);
+            const int kp = (k == n - 1) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
+            St<double> s;
+            gather(v, v, r, k, kp, km, s);
+            res = resid_of<double, false>(s, s, MG5_AT(f, r.r00 + k) + c, cf);
+            cv = s.c;
+            acc.add(res);
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            cv += __shfl_xor_sync(0xffffffffu, cv, o);
+            res += __shfl_xor_sync(0xffffffffu, res, o);
+        }
+        if (live && ch == 0) {
+            const double mv = cv * 0.125;
+            MG5_AT(vc, t) = mv;
+            MG5_AT(v0c, t) = mv;
+            MG5_AT(rc, t) = res * 0.125;
+        }
+    }
+    const Moments m = block_moments(acc);
+    if (threadIdx.x == 0)
+        MG5_AT(partials, blockIdx.x) = m;
+    if (fin.ls)
+        finalize_if_last(reinterpret_cast<double2 *>(partials), fin);
+}
+
 template <typename T>
 cudaError_t launch_resid_restrict(const T *v, const T *f, const double *cptr, int n, CoefT<T> cf,
                                   T *vc, T *v0c, T *rc, double2 *partials, int *nblocks,
@@ -217,14 +277,31 @@ cudaError_t launch_resid_restrict(const T *v, const T *f, const double *cptr, in
 {
     const long long work = (long long)(n / 2) * (n / 2) * (n / 2);
     const int cap = sizeof(T) == 8 ? kReduceBlocksFp64 : kReduceBlocks;
+    if constexpr (sizeof(T) == 8) {
+        if (!B && 8 * work <= kChildMaxFine) {   // coarse grids of the FP64 solves
+            const long long fine = 8 * work;
+            const int bf = block_spread(fine);
+            int gf = grid_spread(fine);
+            if (gf > cap)
+                gf = cap;
+            k_resid_restrict_child<<<gf, bf, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc,
+                                                      reinterpret_cast<Moments *>(partials), fin);
+            *nblocks = gf;
+            count_launch(1);
+            return cudaGetLastError();
+        }
+    }
+    // blocks of kBlock: spreading the coarse cells over more, smaller blocks measured slower
+    // here (more partials for the last block to combine)
     int g = blocks_for(work);
     if (g > cap)
         g = cap;
+    const int bs = kBlock;
     Moments *mp = reinterpret_cast<Moments *>(partials);
     if (B)
-        k_resid_restrict<T, true><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, mp, B, fin);
+        k_resid_restrict<T, true><<<g, bs, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, mp, B, fin);
     else
-        k_resid_restrict<T, false><<<g, kBlock, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, mp, B, fin);
+        k_resid_restrict<T, false><<<g, bs, 0, st>>>(v, f, cptr, n, cf, vc, v0c, rc, mp, B, fin);
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();
@@ -254,7 +331,7 @@ template <typename T>
 cudaError_t launch_restrict(const T *fine, int n, T *coarse, cudaStream_t st)
 {
     const long long work = (long long)(n / 2) * (n / 2) * (n / 2);
-    k_restrict<T><<<blocks_for(work), kBlock, 0, st>>>(fine, n, coarse);
+    k_restrict<T><<<grid_spread(work), block_spread(work), 0, st>>>(fine, n, coarse);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -292,9 +369,9 @@ cudaError_t launch_coarse_rhs(const T *vc, T *fc, const double *m_fine, double *
 {
     const long long work = (long long)nc * nc * nc;
     if (B)
-        k_coarse_rhs<T, true><<<blocks_for(work), kBlock, 0, st>>>(vc, fc, m_fine, c_coarse, nc, cfc, B);
+        k_coarse_rhs<T, true><<<grid_spread(work), block_spread(work), 0, st>>>(vc, fc, m_fine, c_coarse, nc, cfc, B);
     else
-        k_coarse_rhs<T, false><<<blocks_for(work), kBlock, 0, st>>>(vc, fc, m_fine, c_coarse, nc, cfc, B);
+        k_coarse_rhs<T, false><<<grid_spread(work), block_spread(work), 0, st>>>(vc, fc, m_fine, c_coarse, nc, cfc, B);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -474,7 +551,7 @@ cudaError_t launch_prolong_add(const T *vc, const T *v0c, int nc, T *vf, double 
         k_prolong_march<T><<<grid, tx, 0, st>>>(vc, v0c, nc, ichunk, vf, c_fine, c_coarse);
     } else {
         const long long work = (long long)nc * nc * nc;
-        k_prolong_add<T><<<blocks_for(work), kBlock, 0, st>>>(vc, v0c, nc, vf, c_fine, c_coarse);
+        k_prolong_add<T><<<grid_spread(work), block_spread(work), 0, st>>>(vc, v0c, nc, vf, c_fine, c_coarse);
     }
     count_launch(1);
     return cudaGetLastError();
@@ -790,7 +867,7 @@ cudaError_t launch_force(const double *phi, int d0, int d1, int d2, int ghost, d
                          double *grad, cudaStream_t st)
 {
     const long long work = (long long)(d0 - 2 * ghost) * (d1 - 2 * ghost) * (d2 - 2 * ghost);
-    k_force<<<blocks_for(work), kBlock, 0, st>>>(phi, d0, d1, d2, ghost, 0.5 / h, periodic, grad);
+    k_force<<<grid_spread(work), block_spread(work), 0, st>>>(phi, d0, d1, d2, ghost, 0.5 / h, periodic, grad);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -864,7 +941,7 @@ cudaError_t launch_refine(const double *phic, int nc, const int o[3], const int 
     const int d0 = 2 * pn[0] + 2 * ghost, d1 = 2 * pn[1] + 2 * ghost, d2 = 2 * pn[2] + 2 * ghost;
     const long long work = (long long)d0 * d1 * d2;
     const RefineSrc src{nc, nc, nc, 0, 1};
-    k_refine<<<blocks_for(work), kBlock, 0, st>>>(phic, src, o[0], o[1], o[2], d0, d1, d2, ghost,
+    k_refine<<<grid_spread(work), block_spread(work), 0, st>>>(phic, src, o[0], o[1], o[2], d0, d1, d2, ghost,
                                                   fine);
     count_launch(1);
     return cudaGetLastError();
@@ -920,7 +997,7 @@ cudaError_t launch_refine_cubic(const double *phic, int nc, const int o[3], cons
 {
     const int d0 = 2 * pn[0] + 2 * ghost, d1 = 2 * pn[1] + 2 * ghost, d2 = 2 * pn[2] + 2 * ghost;
     const long long work = (long long)d0 * d1 * d2;
-    k_refine_cubic<<<blocks_for(work), kBlock, 0, st>>>(phic, nc, o[0], o[1], o[2], d0, d1, d2,
+    k_refine_cubic<<<grid_spread(work), block_spread(work), 0, st>>>(phic, nc, o[0], o[1], o[2], d0, d1, d2,
                                                         ghost, fine);
     count_launch(1);
     return cudaGetLastError();
@@ -932,7 +1009,7 @@ cudaError_t launch_refine_box(const double *box, const int bd[3], int pg, const 
     const int d0 = 2 * pn[0] + 2 * ghost, d1 = 2 * pn[1] + 2 * ghost, d2 = 2 * pn[2] + 2 * ghost;
     const long long work = (long long)d0 * d1 * d2;
     const RefineSrc src{bd[0], bd[1], bd[2], pg, 0};
-    k_refine<<<blocks_for(work), kBlock, 0, st>>>(box, src, o[0], o[1], o[2], d0, d1, d2, ghost,
+    k_refine<<<grid_spread(work), block_spread(work), 0, st>>>(box, src, o[0], o[1], o[2], d0, d1, d2, ghost,
                                                   fine);
     count_launch(1);
     return cudaGetLastError();
@@ -1045,14 +1122,14 @@ cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint
     if ((pf[0] | pf[1] | pf[2]) & 1)
         return cudaErrorInvalidValue;   // the pair mapping needs even sides
     const long long work = (long long)pf[0] * pf[1] * (pf[2] / 2);
-    const int g = blocks_for(work);
+    const int bs = block_spread(work), g = grid_spread(work);
     auto half = [&](const double *faces, int colour, int copy_other) {
         if (mask)
-            k_patch_half<true><<<g, kBlock, 0, st>>>(faces, in, out, fint, rhs_add, pf[0], pf[1],
+            k_patch_half<true><<<g, bs, 0, st>>>(faces, in, out, fint, rhs_add, pf[0], pf[1],
                                                      pf[2], cf, colour, copy_other, clamp, mask, v0,
                                                      w);
         else
-            k_patch_half<false><<<g, kBlock, 0, st>>>(faces, in, out, fint, rhs_add, pf[0], pf[1],
+            k_patch_half<false><<<g, bs, 0, st>>>(faces, in, out, fint, rhs_add, pf[0], pf[1],
                                                       pf[2], cf, colour, copy_other, clamp, mask, v0,
                                                       w);
     };
@@ -1098,14 +1175,15 @@ cudaError_t launch_patch_residual(const double *phi, const double *fint, double 
                                   const Fin &fin)
 {
     const long long work = (long long)pf[0] * pf[1] * pf[2];
-    int g = blocks_for(work);
+    const int bs = block_spread(work);
+    int g = grid_spread(work);
     if (g > kReduceBlocksFp64)
         g = kReduceBlocksFp64;
     if (mask)
-        k_patch_residual<true><<<g, kBlock, 0, st>>>(phi, fint, rhs_add, pf[0], pf[1], pf[2], cf,
+        k_patch_residual<true><<<g, bs, 0, st>>>(phi, fint, rhs_add, pf[0], pf[1], pf[2], cf,
                                                      partials, mask, fin);
     else
-        k_patch_residual<false><<<g, kBlock, 0, st>>>(phi, fint, rhs_add, pf[0], pf[1], pf[2], cf,
+        k_patch_residual<false><<<g, bs, 0, st>>>(phi, fint, rhs_add, pf[0], pf[1], pf[2], cf,
                                                       partials, mask, fin);
     *nblocks = g;
     count_launch(1);

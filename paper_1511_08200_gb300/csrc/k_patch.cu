@@ -73,6 +73,66 @@ __global__ void k_pbox_resid_restrict(const double *__restrict__ v, const double
         finalize_if_last(partials, fin);
 }
 
+// The same with a thread per fine cell, for the patch's coarse grids (up to kChildMaxFine fine
+// cells; above that the FP64 pipe, not the chain, sets the time): eight consecutive lanes
+// hold the eight children of one coarse cell (child ch = lane & 7, offsets ch >> 2,
+// (ch >> 1) & 1, ch & 1) and sum their centres and residuals by three butterfly shuffles,
+// ((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7)): one FP64 residual a thread instead of a
+// chain of eight, which set the time of the patch's coarse grids (FP64 runs at 2 lanes a clock
+// per SM on GB300).  The loop runs over whole warps, so every lane reaches the shuffles.
+template <bool MASKED>
+__global__ void k_pbox_resid_restrict_child(const double *__restrict__ v,
+                                            const double *__restrict__ f, int p0, int p1, int p2,
+                                            CoefT<double> cf, double *__restrict__ vc,
+                                            double *__restrict__ v0c, double *__restrict__ fc,
+                                            double2 *__restrict__ partials,
+                                            const unsigned char *__restrict__ mask, Fin fin)
+{
+    const int q0 = p0 >> 1, q1 = p1 >> 1, q2 = p2 >> 1;
+    const long long total = (long long)q0 * q1 * q2;
+    const int lane = threadIdx.x & 31, ch = lane & 7;
+    const long long stride = (long long)gridDim.x * blockDim.x / 8;   // coarse cells a pass
+    double2 acc = make_double2(0.0, 0.0);
+    for (long long t0 = ((long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / 8; t0 < total;
+         t0 += stride) {
+        const long long t = t0 + (lane >> 3);
+        const bool live = t < total;
+        double cv = 0.0, res = 0.0;
+        int I = 0, J = 0, K = 0;
+        if (live) {
+            K = (int)(t % q2);
+            const long long q = t / q2;
+            J = (int)(q % q1);
+            I = (int)(q / q1);
+            const int i = 2 * I + (ch >> 2), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch & 1);
+            const Rows r = box_rows(p1 + 2, p2 + 2, i + 1, j + 1);
+            St<double> s;
+            gather(v, v, r, k + 1, k + 2, k, s);
+            const long long fi = ((long long)i * p1 + j) * p2 + k;
+            res = (MASKED && !MG5_AT(mask, fi)) ? 0.0 : cell_residual(s, MG5_AT(f, fi), cf);
+            cv = s.c;
+            acc.x += res;
+            acc.y += res * res;
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            cv += __shfl_xor_sync(0xffffffffu, cv, o);
+            res += __shfl_xor_sync(0xffffffffu, res, o);
+        }
+        if (live && ch == 0) {
+            const long long cb = bidx(I + 1, J + 1, K + 1, q1 + 2, q2 + 2);
+            MG5_AT(vc, cb) = 0.125 * cv;
+            MG5_AT(v0c, cb) = 0.125 * cv;
+            MG5_AT(fc, t) = 0.125 * res;
+        }
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0)
+        MG5_AT(partials, blockIdx.x) = acc;
+    if (fin.ls)
+        finalize_if_last(partials, fin);
+}
+
 // fc = op(vc) + fc on the coarse interior (fc holds the restricted residual)
 __global__ void k_pbox_coarse_rhs(const double *__restrict__ vc, double *__restrict__ fc, int q0,
                                   int q1, int q2, CoefT<double> cf)
@@ -399,15 +459,29 @@ cudaError_t launch_pbox_resid_restrict(const double *v, const double *f, const i
                                        const unsigned char *mask, const Fin &fin)
 {
     const long long work = (long long)(p[0] / 2) * (p[1] / 2) * (p[2] / 2);
-    int g = blocks_for(work);
-    if (g > kReduceBlocksFp64)
-        g = kReduceBlocksFp64;
-    if (mask)
-        k_pbox_resid_restrict<true><<<g, kBlock, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc, v0c, fc,
-                                                          partials, mask, fin);
-    else
-        k_pbox_resid_restrict<false><<<g, kBlock, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc, v0c, fc,
-                                                           partials, mask, fin);
+    int g;
+    if (8 * work <= kChildMaxFine) {   // a thread per fine cell
+        const int bs = block_spread(8 * work);
+        g = grid_spread(8 * work);
+        if (g > kReduceBlocksFp64)
+            g = kReduceBlocksFp64;
+        if (mask)
+            k_pbox_resid_restrict_child<true><<<g, bs, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc,
+                                                                v0c, fc, partials, mask, fin);
+        else
+            k_pbox_resid_restrict_child<false><<<g, bs, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc,
+                                                                 v0c, fc, partials, mask, fin);
+    } else {   // a thread per coarse cell, blocks of kBlock (fewer partials to combine)
+        g = blocks_for(work);
+        if (g > kReduceBlocksFp64)
+            g = kReduceBlocksFp64;
+        if (mask)
+            k_pbox_resid_restrict<true><<<g, kBlock, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc, v0c,
+                                                              fc, partials, mask, fin);
+        else
+            k_pbox_resid_restrict<false><<<g, kBlock, 0, st>>>(v, f, p[0], p[1], p[2], cf, vc, v0c,
+                                                               fc, partials, mask, fin);
+    }
     *nblocks = g;
     count_launch(1);
     return cudaGetLastError();
@@ -417,7 +491,7 @@ cudaError_t launch_pbox_coarse_rhs(const double *vc, double *fc, const int q[3],
                                    cudaStream_t st)
 {
     const long long work = (long long)q[0] * q[1] * q[2];
-    k_pbox_coarse_rhs<<<blocks_for(work), kBlock, 0, st>>>(vc, fc, q[0], q[1], q[2], cf);
+    k_pbox_coarse_rhs<<<grid_spread(work), block_spread(work), 0, st>>>(vc, fc, q[0], q[1], q[2], cf);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -427,10 +501,10 @@ cudaError_t launch_pbox_prolong(const double *vc, const double *v0c, const int q
 {
     const long long work = 8ll * q[0] * q[1] * q[2];
     if (mask)
-        k_pbox_prolong<true><<<blocks_for(work), kBlock, 0, st>>>(vc, v0c, q[0], q[1], q[2], vf,
+        k_pbox_prolong<true><<<grid_spread(work), block_spread(work), 0, st>>>(vc, v0c, q[0], q[1], q[2], vf,
                                                                   mask);
     else
-        k_pbox_prolong<false><<<blocks_for(work), kBlock, 0, st>>>(vc, v0c, q[0], q[1], q[2], vf,
+        k_pbox_prolong<false><<<grid_spread(work), block_spread(work), 0, st>>>(vc, v0c, q[0], q[1], q[2], vf,
                                                                    mask);
     count_launch(1);
     return cudaGetLastError();
@@ -440,7 +514,7 @@ cudaError_t launch_pbox_ghosts(const double *fine_box, const int p[3], double *g
                                double *g3, cudaStream_t st)
 {
     const long long work = (long long)(p[0] / 2 + 2) * (p[1] / 2 + 2) * (p[2] / 2 + 2);
-    k_pbox_ghosts<<<blocks_for(work), kBlock, 0, st>>>(fine_box, p[0], p[1], p[2], g1, g2, g3);
+    k_pbox_ghosts<<<grid_spread(work), block_spread(work), 0, st>>>(fine_box, p[0], p[1], p[2], g1, g2, g3);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -470,7 +544,7 @@ cudaError_t launch_pbox_ghost_refresh(double *v, const double *v0, const int q[3
                                       cudaStream_t st)
 {
     const long long work = (long long)(q[0] + 2) * (q[1] + 2) * (q[2] + 2);
-    k_pbox_ghost_refresh<<<blocks_for(work), kBlock, 0, st>>>(v, v0, q[0], q[1], q[2], w);
+    k_pbox_ghost_refresh<<<grid_spread(work), block_spread(work), 0, st>>>(v, v0, q[0], q[1], q[2], w);
     count_launch(1);
     return cudaGetLastError();
 }

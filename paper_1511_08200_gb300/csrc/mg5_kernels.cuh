@@ -48,6 +48,31 @@ static_assert(kReduceBlocks <= kMomentBlocks, "partials buffer too small");
 // Number of blocks of kBlock threads to cover `work` items (capped for reductions).
 inline int blocks_for(long long work) { return (int)((work + kBlock - 1) / kBlock); }
 
+constexpr int kSMs = 152;   // GB300: 2 dies x 76 SMs
+
+// Threads per block for a grid of `work` threads: kBlock while that still gives every SM two
+// blocks, else fewer (a multiple of 32, at least one warp), so that a coarse grid's warps reach
+// more SMs.  GB300 runs FP64 at 2 lanes a clock per SM: an FP64 kernel on a small grid takes as
+// long as the warps its busiest SM holds need, not as long as its work needs over the GPU.
+inline int block_spread(long long work)
+{
+    const long long per = work / (2 * kSMs);
+    if (per >= kBlock)
+        return kBlock;
+    const int b = (int)(per & ~31ll);
+    return b < 32 ? 32 : b;
+}
+// The FP64 residual + restriction kernels (domain and patch) run a thread per fine cell on
+// grids of up to this many fine cells, a thread per coarse cell above.
+constexpr long long kChildMaxFine = 32 * 32 * 32;
+
+// Blocks of block_spread(work) threads that cover `work` threads.
+inline int grid_spread(long long work)
+{
+    const int b = block_spread(work);
+    return (int)((work + b - 1) / b);
+}
+
 // The smoother's relaxation weight of a parameter set (0 selects the default: 1.3 for the FP64
 // solves, whose V-cycle count it cuts; 1 for the mixed mode, whose inner cycle count is fixed
 // and whose FP32 correction sweeps gain nothing from it).

@@ -1,7 +1,8 @@
 // mg5_tune.cu -- autotuner of the sweep schedule (host runtime, C ABI in mg5.h).
 //
 // The smoother's schedule changes speed, not values: the two-pass sweep with
-// 64 .. 512 threads per block, the column march of the mixed mode's FP32 sweep
+// 32 .. 512 threads per block (by default 256, fewer on coarse grids so that their
+// warps reach more SMs), the column march of the mixed mode's FP32 sweep
 // (k_march.cu), or the fused plane-march with 8 .. 32 planes per
 // CTA, all apply the same cell update to the same snapshot (the sweep of
 // Sec. 3.1).  Which is fastest depends on the grid side (waves over the 152
@@ -42,6 +43,7 @@ std::atomic<unsigned long long> g_sched_version{1};
 SweepSchedule default_schedule(int precision, int n)
 {
     SweepSchedule s;
+    s.block = block_spread((long long)n * n * (n / 2));   // coarse grids: smaller blocks, more SMs
     if (precision == MG5_MIXED && march_ok(n))
         s.form = 2;
     else if (precision == MG5_MIXED && fused_ok<float>(n))
@@ -79,7 +81,7 @@ struct TuneBufs {
 std::vector<SweepSchedule> candidates(int precision, int n)
 {
     std::vector<SweepSchedule> v;
-    for (int b : {64, 128, 256, 512}) {
+    for (int b : {32, 64, 128, 256, 512}) {
         SweepSchedule s;
         s.form = 0;
         s.block = b;

@@ -107,6 +107,9 @@ def test_schedule_table_host_logic(lib, tmp_path):
     mg.tune_clear()
     s, tuned = mg.schedule_get(0, "fp64", 64)
     assert not tuned and (s.form, s.block) == (mg.SWEEP_TWO_PASS, 256)
+    # 32^3 / 2 = 16384 threads: 16384 / 304 = 53 -> one warp a block, 512 blocks
+    assert mg.schedule_get(0, "fp64", 32)[0].block == 32
+    assert mg.schedule_get(0, "fp64", 48)[0].block == 160   # 55296 / 304 = 181 -> 160
     s, tuned = mg.schedule_get(0, "mixed", 64)
     assert not tuned and s.form == mg.SWEEP_MARCH          # a multiple of 32: the column march
     s, tuned = mg.schedule_get(0, "mixed", 48)
