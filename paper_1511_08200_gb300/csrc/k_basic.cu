@@ -1021,53 +1021,51 @@ cudaError_t launch_refine_box(const double *box, const int bd[3], int pg, const 
 // Coarse patch grids keep their ghosts on the extrapolated boundary condition
 // g = v0(g) + w^m (v(a) - v0(a)) (k_patch.cu), where a is the one interior cell nearest g.
 // The thread that writes interior cell a writes every ghost anchored at it, so the
-// ghosts of `out` follow each half-sweep without a separate pass: in the red pass every
-// interior cell is written (relaxed or copied), in the black pass the relaxed cells are,
-// and a ghost is only ever read by its own anchor's thread among the cells that write.
+// ghosts of `out` follow each half-sweep without a separate pass: the red pass writes the
+// red cells and copies the black ones (except in the SPLIT form of k_patch_half), the black
+// pass the relaxed black cells, and a ghost is only ever read by its own anchor's thread among
+// the cells that write.
 __device__ __forceinline__ void write_anchored_ghosts(double *dst, const double *__restrict__ v0,
                                                       double w, double val, int i, int j, int k,
                                                       int p0, int p1, int p2, int d1, int d2)
 {
-    int gi[2], gj[2], gk[2];
-    int ni = 0, nj = 0, nk = 0;
-    if (i == 0)
-        gi[ni++] = 0;
-    if (i == p0 - 1)
-        gi[ni++] = p0 + 1;
-    if (j == 0)
-        gj[nj++] = 0;
-    if (j == p1 - 1)
-        gj[nj++] = p1 + 1;
-    if (k == 0)
-        gk[nk++] = 0;
-    if (k == p2 - 1)
-        gk[nk++] = p2 + 1;
-    if (ni + nj + nk == 0)
+    // per axis: the cell's own box index, and the ghost planes below (index 0, when the cell
+    // is the first interior one) and above (index p + 1, when it is the last) -- no arrays,
+    // so nothing goes to local memory
+    const bool li = i == 0, hi = i == p0 - 1, lj = j == 0, hj = j == p1 - 1, lk = k == 0,
+               hk = k == p2 - 1;
+    if (!(li | hi | lj | hj | lk | hk))
         return;
     const long long ab = ((long long)(i + 1) * d1 + (j + 1)) * d2 + (k + 1);
     const double da = val - MG5_AT(v0, ab);
-    for (int a = 0; a <= ni; ++a)
-        for (int b = 0; b <= nj; ++b)
-            for (int c = 0; c <= nk; ++c) {
+    const int Iv[3] = {i + 1, 0, p0 + 1}, Jv[3] = {j + 1, 0, p1 + 1}, Kv[3] = {k + 1, 0, p2 + 1};
+    const bool oi[3] = {true, li, hi}, oj[3] = {true, lj, hj}, ok[3] = {true, lk, hk};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
                 const int m = (a > 0) + (b > 0) + (c > 0);
-                if (m == 0)
+                if (m == 0 || !(oi[a] && oj[b] && ok[c]))
                     continue;
-                const int I = a ? gi[a - 1] : i + 1, J = b ? gj[b - 1] : j + 1,
-                          K = c ? gk[c - 1] : k + 1;
                 const double wm = m == 1 ? w : (m == 2 ? w * w : w * w * w);
-                const long long g = ((long long)I * d1 + J) * d2 + K;
+                const long long g = ((long long)Iv[a] * d1 + Jv[b]) * d2 + Kv[c];
                 MG5_AT(dst, g) = MG5_AT(v0, g) + wm * da;
             }
 }
 
 // One thread per pair of cells (k = 2m, 2m + 1) of a row: one of the two has the colour of
-// the pass and is relaxed; in the red pass (copy_other) the other is carried into dst.  Every
+// the pass and is relaxed; with copy_other (the red pass) the other is carried into dst.
+// SPLIT (unmasked coarse patch grids, whose half-sweeps are latency-bound): the red pass
+// copies nothing, and the black pass reads what it would have copied (the old black values,
+// and the ghosts anchored at black cells, rebuilt from them) from the sweep's input.  Every
 // lane of a warp thus relaxes a cell (a thread per cell would leave half the lanes of each
 // FP64 instruction idle, the colours alternating along k).  The sides are even on every grid
 // the patch sweeps (the coarsest, possibly odd, is solved by k_pbox_coarsest).
 // MASKED: interior cells with mask 0 are not relaxed (they keep their values).
 // v0 (coarse patch grids): also refresh the ghosts anchored at the cells written.
-template <bool MASKED>
+template <bool MASKED, bool SPLIT>
 __global__ void k_patch_half(const double *__restrict__ src_faces, const double *__restrict__ src_edges,
                              double *dst, const double *__restrict__ fint, double rhs_add, int p0,
                              int p1, int p2, CoefT<double> cf, int colour, int copy_other,
@@ -1104,7 +1102,34 @@ __global__ void k_patch_half(const double *__restrict__ src_faces, const double 
         return;
     }
     St<double> s;
-    gather(src_faces, src_edges, r, K, K + 1, K - 1, s);
+    if (SPLIT && colour == 1) {
+        // black pass after a red pass that copied nothing: the new red faces from src_faces;
+        // the centre and the edges from src_edges, the sweep's input.  A face that is a ghost
+        // is anchored at this cell: its boundary condition of the cell's input value,
+        // v0(g) + w (v - v0(a)), is the value the red pass would have copied (the input's own
+        // ghosts may predate a prolongation)
+        gather3(src_faces, src_edges, src_edges, r, K, K + 1, K - 1, s);
+        const bool gxm = i == 0, gxp = i == p0 - 1, gym = j == 0, gyp = j == p1 - 1, gzm = k == 0,
+                   gzp = k == p2 - 1;
+        if (gxm | gxp | gym | gyp | gzm | gzp) {
+            const double da = s.c - MG5_AT(v0, r.r00 + K);
+            const auto bc = [&](long long g) { return MG5_AT(v0, g) + w * da; };
+            if (gxm)
+                s.xm = bc(r.rm0 + K);
+            if (gxp)
+                s.xp = bc(r.rp0 + K);
+            if (gym)
+                s.ym = bc(r.r0m + K);
+            if (gyp)
+                s.yp = bc(r.r0p + K);
+            if (gzm)
+                s.zm = bc(r.r00 + K - 1);
+            if (gzp)
+                s.zp = bc(r.r00 + K + 1);
+        }
+    } else {
+        gather(src_faces, src_edges, r, K, K + 1, K - 1, s);
+    }
     bool cl = false;
     const double v = cell_update(s, MG5_AT(fint, tk) + rhs_add, cf, cl);
     MG5_AT(dst, r.r00 + K) = v;
@@ -1123,18 +1148,24 @@ cudaError_t launch_patch_sweep(const double *in, double *out, const double *fint
         return cudaErrorInvalidValue;   // the pair mapping needs even sides
     const long long work = (long long)pf[0] * pf[1] * (pf[2] / 2);
     const int bs = block_spread(work), g = grid_spread(work);
+    const bool split = !mask && v0;
     auto half = [&](const double *faces, int colour, int copy_other) {
         if (mask)
-            k_patch_half<true><<<g, bs, 0, st>>>(faces, in, out, fint, rhs_add, pf[0], pf[1],
-                                                     pf[2], cf, colour, copy_other, clamp, mask, v0,
-                                                     w);
+            k_patch_half<true, false><<<g, bs, 0, st>>>(faces, in, out, fint, rhs_add, pf[0],
+                                                        pf[1], pf[2], cf, colour, copy_other, clamp,
+                                                        mask, v0, w);
+        else if (split)
+            k_patch_half<false, true><<<g, bs, 0, st>>>(faces, in, out, fint, rhs_add, pf[0],
+                                                        pf[1], pf[2], cf, colour, copy_other, clamp,
+                                                        mask, v0, w);
         else
-            k_patch_half<false><<<g, bs, 0, st>>>(faces, in, out, fint, rhs_add, pf[0], pf[1],
-                                                      pf[2], cf, colour, copy_other, clamp, mask, v0,
-                                                      w);
+            k_patch_half<false, false><<<g, bs, 0, st>>>(faces, in, out, fint, rhs_add, pf[0],
+                                                         pf[1], pf[2], cf, colour, copy_other,
+                                                         clamp, mask, v0, w);
     };
-    // red: from in (all), black copied; black: faces from out (new red), edges from in (old black)
-    half(in, 0, 1);
+    // red: from in, the black cells carried into out (SPLIT: not carried); black: faces from
+    // out (new red), edges from in (old black), SPLIT: the centre and the ghost faces too
+    half(in, 0, split ? 0 : 1);
     half(out, 1, 0);
     count_launch(2);
     return cudaGetLastError();
