@@ -17,8 +17,8 @@
 // return theirs.  A request larger than the whole budget is refused at submit.
 //
 // A key holds at most kDupCap entries: when they are all busy, the request runs
-// host-driven on the worker's own context (as fast, measured) instead of
-// building another, since building allocates and instantiates, which stalls the
+// host-driven on the worker's own context (for mixed solves as fast as a replay
+// under concurrency, measured) instead of building another, since building allocates and instantiates, which stalls the
 // solves in flight.  Captures and device frees are serialised by one gate that
 // host-driven solves hold shared: a free or a device-wide synchronisation in another
 // thread can end a capture in progress.  A capture that fails anyway is retried once, then the
