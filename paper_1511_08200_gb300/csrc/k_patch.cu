@@ -30,8 +30,37 @@ __device__ __forceinline__ long long bidx(int i, int j, int k, int d1, int d2)
     return ((long long)i * d1 + j) * d2 + k;
 }
 
+// The ghosts of a coarse box anchored at its interior cell (I, J, K) (0-based), reset to v0's
+// fixed values: right after the restriction v = v0 in the interior, so the boundary condition
+// v0(g) + w^m (v(a) - v0(a)) of every ghost is v0(g) itself.  The restriction does this for the
+// cells it writes, instead of a refresh launch over the box before the coarse right-hand side.
+__device__ __forceinline__ void reset_anchored_ghosts(double *__restrict__ vc,
+                                                      const double *__restrict__ v0c, int I, int J,
+                                                      int K, int q0, int q1, int q2)
+{
+    const bool li = I == 0, hi = I == q0 - 1, lj = J == 0, hj = J == q1 - 1, lk = K == 0,
+               hk = K == q2 - 1;
+    if (!(li | hi | lj | hj | lk | hk))
+        return;
+    const int d1 = q1 + 2, d2 = q2 + 2;
+    const int Iv[3] = {I + 1, 0, q0 + 1}, Jv[3] = {J + 1, 0, q1 + 1}, Kv[3] = {K + 1, 0, q2 + 1};
+    const bool oi[3] = {true, li, hi}, oj[3] = {true, lj, hj}, ok[3] = {true, lk, hk};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if ((a | b | c) == 0 || !(oi[a] && oj[b] && ok[c]))
+                    continue;
+                const long long g = bidx(Iv[a], Jv[b], Kv[c], d1, d2);
+                MG5_AT(vc, g) = MG5_AT(v0c, g);
+            }
+}
+
 // residual of the 8 interior children of each coarse interior cell, restricted
-// with v onto the coarse box interior (vc and v0c) and into fc (interior-indexed).
+// with v onto the coarse box interior (vc and v0c, vc's ghosts reset to v0c's) and into fc
+// (interior-indexed).
 // MASKED: the residual of a child with mask 0 (not iterated) counts as zero.
 template <bool MASKED>
 __global__ void k_pbox_resid_restrict(const double *__restrict__ v, const double *__restrict__ f,
@@ -65,6 +94,7 @@ __global__ void k_pbox_resid_restrict(const double *__restrict__ v, const double
         MG5_AT(vc, cb) = 0.125 * sv;
         MG5_AT(v0c, cb) = 0.125 * sv;
         MG5_AT(fc, t) = 0.125 * sr;
+        reset_anchored_ghosts(vc, v0c, I, J, K, q0, q1, q2);
     }
     acc = block_sum2(acc);
     if (threadIdx.x == 0)
@@ -124,6 +154,7 @@ __global__ void k_pbox_resid_restrict_child(const double *__restrict__ v,
             MG5_AT(vc, cb) = 0.125 * cv;
             MG5_AT(v0c, cb) = 0.125 * cv;
             MG5_AT(fc, t) = 0.125 * res;
+            reset_anchored_ghosts(vc, v0c, I, J, K, q0, q1, q2);
         }
     }
     acc = block_sum2(acc);
@@ -245,19 +276,6 @@ __device__ __forceinline__ void ghost_refresh_cell(double *v, const double *v0, 
     const double wm = m == 1 ? w : (m == 2 ? w * w : w * w * w);
     const long long g = bidx(I, J, K, d1, d2), a = bidx(a0, a1, a2, d1, d2);
     MG5_AT(v, g) = MG5_AT(v0, g) + wm * (MG5_AT(v, a) - MG5_AT(v0, a));
-}
-
-__global__ void k_pbox_ghost_refresh(double *__restrict__ v, const double *__restrict__ v0, int q0,
-                                     int q1, int q2, double w)
-{
-    const long long total = (long long)(q0 + 2) * (q1 + 2) * (q2 + 2);
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total)
-        return;
-    const int K = (int)(t % (q2 + 2));
-    const long long qq = t / (q2 + 2);
-    const int J = (int)(qq % (q1 + 2)), I = (int)(qq / (q1 + 2));
-    ghost_refresh_cell(v, v0, I, J, K, q0, q1, q2, w);
 }
 
 // Coarsest patch grid, one CTA: before each sweep the residual norm; stop at
@@ -536,15 +554,6 @@ cudaError_t launch_pbox_coarsest(double *A, double *B, const double *f, const in
     else
         k_pbox_coarsest<false><<<1, threads, sm, st>>>(A, B, f, p[0], p[1], p[2], cf, nu_max, rtol,
                                                        clamp, sweeps, v0, w, mask);
-    count_launch(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pbox_ghost_refresh(double *v, const double *v0, const int q[3], double w,
-                                      cudaStream_t st)
-{
-    const long long work = (long long)(q[0] + 2) * (q[1] + 2) * (q[2] + 2);
-    k_pbox_ghost_refresh<<<grid_spread(work), block_spread(work), 0, st>>>(v, v0, q[0], q[1], q[2], w);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -1379,8 +1379,7 @@ struct RunPatch {
     int coarse_visit(int l)
     {
         mg5_ctx *ctx = this->ctx;
-        // v = v0 on entry: the refresh resets the ghosts to the fixed coarse values
-        CK(launch_pbox_ghost_refresh(h->v[l], h->v0[l], h->q[l], ghost_w(l), st));
+        // v = v0 on entry, its ghosts reset to the fixed coarse values by the restriction
         CK(launch_pbox_coarse_rhs(h->v[l], h->f[l], h->q[l], make_coef<double>(hl[l], p->alpha), st));
         if (l == h->nlev - 1)
             return coarsest(l);

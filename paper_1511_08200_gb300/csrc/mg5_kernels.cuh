@@ -275,8 +275,6 @@ cudaError_t launch_pbox_coarsest(double *A, double *B, const double *f, const in
                                  CoefT<double> cf, int nu_max, double rtol, unsigned long long *clamp,
                                  int *sweeps, cudaStream_t st, const double *v0 = nullptr,
                                  double w = 0.0, const unsigned char *mask = nullptr);
-cudaError_t launch_pbox_ghost_refresh(double *v, const double *v0, const int q[3], double w,
-                                      cudaStream_t st);
 
 // ---- position-dependent truncation (k_mask.cu)
 // coarse mask (interior q = p/2) = 1 where all 8 children have mask != 0
