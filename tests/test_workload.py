@@ -87,3 +87,20 @@ def test_nested_halo_workload_geometry():
         assert deltas[lev].min() > -1.0
     means = [float(d.mean()) for d in deltas]
     assert all(b > a for a, b in zip(means, means[1:])), means
+
+
+def test_serving_stream_recipe():
+    """The serving stream's requests: Poisson arrivals at the offered rate, sides
+    16 round(10^U(log 32, log 256)/16), sigma ~ U(0.5, 2), tolerance 1e-6 or 1e-8 with p = 1/2
+    (the same draws for every run: one generator, seed 5)."""
+    import bench
+    gaps, sizes, sigmas, tols = bench.serving_stream(12000, rate=200.0)
+    assert abs(gaps.mean() - 1 / 200.0) < 0.03 / 200.0
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.05          # exponential: cv = 1
+    assert sizes.min() >= 32 and sizes.max() <= 256 and np.all(sizes % 16 == 0)
+    # log-uniform sides: the median side near sqrt(32 * 256) = 90.5
+    assert 80 <= np.median(sizes) <= 100
+    assert sigmas.min() >= 0.5 and sigmas.max() <= 2.0
+    assert set(np.unique(tols)) == {1e-6, 1e-8} and abs((tols == 1e-6).mean() - 0.5) < 0.02
+    again = bench.serving_stream(12000, rate=200.0)
+    assert all(np.array_equal(a, b) for a, b in zip((gaps, sizes, sigmas, tols), again))
